@@ -1,0 +1,205 @@
+"""One coupled electromagnetic-thermal time step, solved exactly (oracle).
+
+Per-element circuit equation of loop e (Numerical Algorithm section: the field
+on each wire from all currents plus the background field, the transport part
+of J over each whole wire by the A-V formulation):
+
+    sum_j M_ej dI_j/dt + pi r_e^2 dB_a/dt + 2 pi r_e E_e(I_e) = u_w(e),
+
+u_w = loop voltage of turn w (the scalar-potential unknown of the A-V
+formulation; free loops have u = 0), with the transport constraint
+sum_{e in w} I_e = I_t(t) on every turn.  The time step is linearly-implicit
+Euler: E is linearised about the start-of-step state with its exact diagonal
+derivative G = d(2 pi r E)/dI (B and T frozen), giving per step
+
+    (M + dt G) Idot - P u = -R,      P^T Idot = c,
+    R_e = 2 pi r_e E_e + pi r_e^2 (B_a(t+dt) - B_a(t)) / dt,
+    c_w = (I_t(t + dt) - sum_{e in w} I_e) / dt,
+
+then I <- I + dt Idot and the heat equation advances with the Joule source
+q = E J of the start-of-step state.  The paper's own inner iteration
+(m = 1, 2 with 2.5 % / 0.1 % stopping thresholds) approximates the converged
+step; the oracle defines the converged step and solves it directly:
+Cholesky of A = M + dt G, Schur complement S = P^T A^-1 P for u, then
+Idot = A^-1 (P u - R).
+
+Pins (tests/test_oracle_step.py): constraint and KKT residual of the direct
+solve, closed-form two-loop recurrence, a 4-loop KKT solved by plain
+numpy.linalg.solve, Bean's critical-state moment -Jc a / 3, and the energy
+balance of the stepped circuit.
+"""
+
+import numpy as np
+import scipy.linalg as sla
+
+from .constitutive import critical_current, ej_terms, FILAMENT
+from .field import field_from_flux
+from .inductance import assemble_M
+from .thermal import ThermalGrid
+
+DIAG_FIELDS = ("t", "I_t", "V_term", "moment", "P_joule", "T_max", "max_jratio", "max_rho_frac")
+
+
+def drive_values(t, d):
+    """Transport current I_t(t) and applied axial field B_a(t) of a drive dict.
+
+    I_t = min(ramp_rate * t, I_max).  B_a: waveform 0 = none, 1 = linear ramp
+    at Ba_rate capped at Ba_max, 2 = triangle 0 -> +Ba_max -> -Ba_max -> 0 with
+    slope Ba_rate, repeated.
+    """
+    It = min(d["ramp_rate"] * t, d["I_max"])
+    wf = d.get("Ba_waveform", 0)
+    rate = d.get("Ba_rate", 0.0)
+    amp = d.get("Ba_max", 0.0)
+    if wf == 0 or rate == 0.0:
+        Ba = 0.0
+    elif wf == 1:
+        Ba = min(rate * t, amp)
+    else:
+        period = 4.0 * amp / rate
+        tau = t - period * np.floor(t / period)
+        if tau < 0.25 * period:
+            Ba = rate * tau
+        elif tau < 0.75 * period:
+            Ba = amp - rate * (tau - 0.25 * period)
+        else:
+            Ba = -amp + rate * (tau - 0.75 * period)
+    return It, Ba
+
+
+def kkt_solve(A, R, c, block, constrained):
+    """Exact solution of  A x - P u = -R,  P^T x = c.
+
+    P is the element-to-constrained-block incidence (blocks of ``block``
+    consecutive elements, ``constrained`` flags per block).  Returns (x, u)
+    with u = 0 on free blocks.
+    """
+    N = A.shape[0]
+    W = N // block
+    cho = sla.cho_factor(A, lower=True)
+    xR = sla.cho_solve(cho, R)
+    wires = np.nonzero(constrained)[0]
+    u = np.zeros(W)
+    if wires.size == 0:
+        return -xR, u
+    P = np.zeros((N, wires.size))
+    for k, w in enumerate(wires):
+        P[w * block:(w + 1) * block, k] = 1.0
+    Y = sla.cho_solve(cho, P)
+    S = P.T @ Y
+    uc = np.linalg.solve(S, c[wires] + P.T @ xR)
+    u[wires] = uc
+    x = Y @ uc - xR
+    return x, u
+
+
+class OracleCoil:
+    """State and step of one coil, every quantity in FP64."""
+
+    def __init__(self, geo, params, jc_factor, strain, mat, constrained=None, M=None):
+        self.geo = geo
+        self.p = dict(params)
+        N = geo["N"]
+        self.jc_factor = np.asarray(jc_factor, dtype=np.float64)
+        self.strain = np.asarray(strain, dtype=np.float64)
+        self.mat = np.asarray(mat).astype(np.int64)
+        W = geo["W"]
+        if constrained is None:
+            constrained = np.ones(W, dtype=bool)
+        self.constrained = np.asarray(constrained, dtype=bool)
+        self.M = assemble_M(geo["r"], geo["z"], geo["h"]) if M is None else M
+        self.I = np.zeros(N)
+        self.u_T = np.full(N, self.p["T_bath"] ** 4)
+        self.t = 0.0
+        self.steps = 0
+        self.diag = []
+        self.thermal = ThermalGrid(geo, self.p) if (geo["grid"] and self.p["thermal"]) else None
+        self.first_jump = np.full(W, -1, dtype=np.int64)
+        self.first_quench = np.full(W, -1, dtype=np.int64)
+        self.last = None
+
+    # -- the state's fields ----------------------------------------------------
+    def temperature(self):
+        return np.sqrt(np.sqrt(self.u_T))
+
+    def flux(self):
+        return self.M @ self.I
+
+    def field(self, Ba):
+        geo = self.geo
+        if not geo["grid"]:
+            z = np.zeros(geo["N"])
+            return z, z.copy()
+        phi_tot = self.flux() + np.pi * geo["r"] ** 2 * Ba
+        return field_from_flux(geo, phi_tot)
+
+    def pointwise(self, Ba):
+        Br, Bz = self.field(Ba)
+        Bmag = np.sqrt(Br * Br + Bz * Bz)
+        T = self.temperature()
+        Jc = critical_current(Bmag, T, self.strain, self.jc_factor, self.mat, self.p)
+        terms = ej_terms(self.I, Jc, self.mat, self.geo["r"], self.geo["area"], self.p)
+        terms.update(Br=Br, Bz=Bz, Bmag=Bmag, T=T, Jc=Jc)
+        return terms
+
+    # -- one step ------------------------------------------------------------
+    def step(self, drive):
+        geo, p = self.geo, self.p
+        dt = drive["dt"]
+        r, area = geo["r"], geo["area"]
+        B = geo["block"]
+        W = geo["W"]
+        t0, t1 = self.t, self.t + dt
+        _, Ba0 = drive_values(t0, drive)
+        It1, Ba1 = drive_values(t1, drive)
+        dBa = (Ba1 - Ba0) / dt
+        pw = self.pointwise(Ba0)
+        R = 2.0 * np.pi * r * pw["E"] + np.pi * r * r * dBa
+        c = (It1 - self.I.reshape(W, B).sum(axis=1)) / dt
+        A = self.M + np.diag(dt * pw["G"])
+        Idot, u = kkt_solve(A, R, c, B, self.constrained)
+        self.last = dict(pw, Idot=Idot, u=u, R=R, c=c, A=A)
+        # detectors on the start-of-step state (flux-jump |J/Jc| > 1, quench rho > 0.95 rho_n)
+        fil = (self.mat == FILAMENT).reshape(W, B)
+        jr = np.where(fil, pw["jratio"].reshape(W, B), 0.0)
+        rho_frac = np.where(fil, pw["rho"].reshape(W, B) / p["rho_n"], 0.0)
+        nfil = fil.sum(axis=1)
+        mean_rho = np.where(nfil > 0, rho_frac.sum(axis=1) / np.maximum(nfil, 1), 0.0)
+        wire_jr = jr.max(axis=1)
+        self.first_jump = np.where((self.first_jump < 0) & (wire_jr > 1.0), self.steps, self.first_jump)
+        self.first_quench = np.where((self.first_quench < 0) & (mean_rho > 0.95), self.steps, self.first_quench)
+        # advance
+        self.I = self.I + dt * Idot
+        if self.thermal is not None:
+            th = self.thermal
+            unew = th.adi_step(th.to_grid(self.u_T), th.to_grid(pw["q"]), dt)
+            self.u_T = th.to_elem(unew)
+        self.t = t1
+        self.steps += 1
+        rec = (t1, It1, float(u[self.constrained].sum()),
+               float(np.sum(np.pi * r * r * self.I)),
+               float(np.sum(pw["q"] * 2.0 * np.pi * r * area)),
+               float(self.temperature().max()),
+               float(wire_jr.max()), float(mean_rho.max()))
+        self.diag.append(rec)
+        return rec
+
+    def read(self, drive=None):
+        """J, B_r, B_z, T and moment of the current state."""
+        Ba = drive_values(self.t, drive)[1] if drive is not None else 0.0
+        pw = self.pointwise(Ba)
+        return {"J": pw["J"], "Br": pw["Br"], "Bz": pw["Bz"], "T": pw["T"],
+                "moment": float(np.sum(np.pi * self.geo["r"] ** 2 * self.I))}
+
+
+def build(geometry, material, jc_factor, strain, mat, constrained=None):
+    """OracleCoil from a plain geometry dict (solenoid parameters or a list)."""
+    from .geometry import solenoid_elements, list_elements
+    if geometry["kind"] == "solenoid":
+        geo = solenoid_elements(geometry["n_layers"], geometry["n_turns"], geometry["n_sub"],
+                                geometry["r_in"], geometry["pitch"], geometry["wire_d"])
+        if constrained is None:
+            constrained = np.full(geo["W"], bool(geometry.get("transport", 1)))
+    else:
+        geo = list_elements(geometry["r"], geometry["z"], geometry["h"], geometry["block"])
+    return OracleCoil(geo, material, jc_factor, strain, mat, constrained)
