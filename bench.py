@@ -1,0 +1,371 @@
+"""Benchmark of the coupled electromagnetic-thermal coil step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload real|mid|small] [--precision bf16|fp32|fp64]
+
+One step = one full pass of the hot path over every element of the coil:
+pointwise E-J/Jc/Joule, per-wire factorisation, the projected PCG solve of
+the transport-constrained circuit equations (dense operator applies), flux
+and current update, ADI heat step, diagnostics.  Metric: element-steps/s.
+
+Default workload: the 96,000-element real-size coil (60 x 100 turns, 4 x 4
+elements per wire), dense operator stored in BF16 (18.4 GB, larger than the
+126 MB L2, so no flush is needed between steps), transport ramp 2 A/s,
+dt = 1e-5 s, synthetic seeded inputs.  The FP64 form of the same coil is
+timed beside it for the mixed/FP64 ratio.
+
+Multi-GPU: the coil does not shard across GPUs in this build ("replicas
+only"): under torchrun each rank steps its own replica; value = all ranks'
+element-steps / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2403_07666_b300 import workloads as wl  # noqa: E402
+
+METRIC = "element-steps/s (EM+thermal)"
+UNIT = "element-steps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def pick_workload(name):
+    return {"real": wl.real_coil, "mid": wl.mid_coil, "small": wl.small_coil,
+            "prof": wl.profile_coil}[name]()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle (CPU)
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+class OracleSample:
+    """Bounded sample of the oracle's step on the full workload.
+
+    The oracle solves every step directly (Cholesky of M + dt G, Schur
+    complement for the loop voltages): O(N^3) per step, hours at N = 96,000.
+    The sample times the oracle's own routines on the leading k-element block
+    of the coil's operator (Cholesky, and the Schur solves with k / block
+    right-hand sides) and scales them to N by N^3 and N^2 W, and times the
+    O(N) parts (field stencil, Jc, E-J law, ADI heat step) on all N elements.
+    """
+
+    def __init__(self, w, k=2048):
+        import oracle
+        from oracle.thermal import ThermalGrid
+        g = w.geometry
+        self.w = w
+        self.geo = oracle.solenoid_elements(g["n_layers"], g["n_turns"], g["n_sub"], g["r_in"],
+                                            g["pitch"], g["wire_d"])
+        geo = self.geo
+        self.N = geo["N"]
+        self.k = min(k, self.N)
+        sl = slice(0, self.k)
+        self.Mk = oracle.assemble_M(geo["r"][sl], geo["z"][sl], geo["h"][sl])
+        self.th = ThermalGrid(geo, w.material)
+        self.oracle = oracle
+
+    def step_seconds(self):
+        import scipy.linalg as sla
+        o, geo, w = self.oracle, self.geo, self.w
+        N, k, B, W = self.N, self.k, geo["block"], geo["W"]
+        rng = np.random.default_rng(0)
+        t0 = time.perf_counter()
+        phi = np.pi * geo["r"] ** 2 * 0.01 + 1e-9 * rng.standard_normal(N)
+        Br, Bz = o.field_from_flux(geo, phi)
+        T = np.full(N, w.material["T_bath"])
+        Jc = o.critical_current(np.hypot(Br, Bz), T, w.strain, w.jc_factor, w.mat, w.material)
+        tm = o.ej_terms(1e-3 * rng.standard_normal(N), Jc, w.mat, geo["r"], geo["area"], w.material)
+        u = self.th.to_grid(T ** 4)
+        self.th.adi_step(u, self.th.to_grid(tm["q"]), w.drive["dt"])
+        t_lin = time.perf_counter() - t0
+        A = self.Mk + np.diag(w.drive["dt"] * tm["G"][:k])
+        t0 = time.perf_counter()
+        cho = sla.cho_factor(A, lower=True)
+        t_chol = time.perf_counter() - t0
+        nrhs = max(1, k // B)
+        P = np.zeros((k, nrhs))
+        for j in range(nrhs):
+            P[j * B:(j + 1) * B, j] = 1.0
+        t0 = time.perf_counter()
+        Y = sla.cho_solve(cho, P)
+        S = P.T @ Y
+        np.linalg.solve(S, np.ones(nrhs))
+        t_schur = time.perf_counter() - t0
+        scale3 = (N / k) ** 3
+        scale_schur = (N / k) ** 2 * (W / nrhs)
+        return t_lin + t_chol * scale3 + t_schur * scale_schur
+
+    def describe(self):
+        return (f"oracle direct step: Cholesky and Schur solves timed on the leading {self.k}-element "
+                f"block of the operator, scaled by (N/k)^3 and (N/k)^2 W/(k/B); field stencil, Jc, "
+                f"E-J law and ADI timed on all {self.N} elements")
+
+
+def cpu_baseline(w, budget_s=20.0):
+    smp = OracleSample(w)
+    times = []
+    t_start = time.perf_counter()
+    while not times or (time.perf_counter() - t_start < budget_s and len(times) < 5):
+        times.append(smp.step_seconds())
+    t = min(times)
+    return {"value": smp.N / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+            "sample": smp.describe() + f"; best of {len(times)} samples, {t:.1f} s per step"}
+
+
+# --------------------------------------------------------------- GPU arm
+
+def timed_steps(coil, drive, K, stream, torch):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    coil.step(K, drive)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2403_07666_b300.coil import Coil
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    w = pick_workload(args.workload)
+    drive = w.drive
+    stream = torch.cuda.Stream()
+    hbm, peak_kind = peaks()
+    t0 = time.perf_counter()
+    coil = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                              stream=stream.cuda_stream, profile=True)
+    setup_s = time.perf_counter() - t0
+    info = coil.info()
+    N = coil.N
+    coil.step(args.warmup, drive)
+    coil.reset_counters()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local_rank) as clk:
+        secs = timed_steps(coil, drive, args.steps, stream, torch)
+    inf = coil.info()
+    if dist:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    value = world * N * args.steps / secs
+    op_launches = int(inf.operator_launches)
+    gemv_ms = inf.operator_ms / max(op_launches, 1)
+    op_bytes = int(info.operator_bytes)
+    achieved = op_bytes / (gemv_ms / 1e3) / 1e9
+    applies = op_launches / args.steps
+    launches = int(inf.kernel_launches)
+
+    # end to end through the public API: host buffers, copies inside the region
+    import torch as _t
+    bufs = [_t.empty(N, dtype=_t.float64, pin_memory=True).numpy() for _ in range(4)]
+    Ke = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(Ke):
+        coil.step(1, drive)
+        coil.read_into(drive, *bufs)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * N * Ke / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(inf.descriptor_bytes) + 48,
+           "d2h_bytes_per_step": 4 * N * 8 + 8}
+
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision != "fp64":
+        coil.close()
+        c64 = Coil.from_workload(w, precision="fp64", rtol=args.rtol, device=local_rank,
+                                 stream=stream.cuda_stream)
+        c64.step(1, drive)
+        s64 = timed_steps(c64, drive, args.fp64_steps, stream, torch)
+        if dist:
+            t = torch.tensor([s64], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            s64 = float(t.item())
+        fp64 = {"value": world * N * args.fp64_steps / s64, "ms_per_step": 1e3 * s64 / args.fp64_steps,
+                "steps": args.fp64_steps}
+        c64.close()
+    else:
+        coil.close()
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16-stored operator, fp32 products, fp64 solve/accumulation",
+                  "fp32": "fp32-stored operator, fp32 products, fp64 solve/accumulation",
+                  "fp64": "f64"}[args.precision],
+        "data": "synthetic (seeded coil geometry, lognormal Jc factor, uniform strain)",
+        "config": {"workload": w.name, "n_elem": N, "n_layers": w.geometry["n_layers"],
+                   "n_turns": w.geometry["n_turns"], "n_sub": w.geometry["n_sub"],
+                   "precision": args.precision, "dt": drive["dt"], "ramp_A_per_s": drive["ramp_rate"],
+                   "rtol": args.rtol, "parallelism": f"replicas x{world}",
+                   "l2": f"operator {op_bytes / 1e9:.1f} GB > 126 MB L2 (no flush needed)"},
+        "applies_per_step": applies,
+        "setup_s": setup_s,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": f"k_gemv_{args.precision}",
+                     "peak_kind": peak_kind, "avg_launch_ms": gemv_ms,
+                     "bytes_per_launch": op_bytes},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if fp64 is not None:
+        line["fp64"] = fp64
+        line["mixed_over_fp64"] = value / fp64["value"]
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    return line
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = pick_workload(args.workload)
+    smp = OracleSample(w)
+    for _ in range(args.warmup):
+        smp.step_seconds()
+    total = 0.0
+    for _ in range(args.steps):
+        total += smp.step_seconds()
+    value = smp.N * args.steps / total
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded coil geometry, lognormal Jc factor, uniform strain)",
+            "config": {"workload": w.name, "n_elem": smp.N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": smp.describe()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="real", choices=["real", "mid", "small", "prof"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp32", "fp64"])
+    ap.add_argument("--rtol", type=float, default=1e-9)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

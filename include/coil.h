@@ -1,0 +1,216 @@
+/*
+ * coil.h -- C ABI of the B300 coupled electromagnetic-thermal coil stepper.
+ *
+ * The library advances the per-time-step coupled update of arXiv:2403.07666
+ * (Numerical Algorithm section and Fig. 2b; Methods, heat-diffusion and E-J
+ * paragraphs) over every conductor element of an axisymmetric coil:
+ *
+ *   1. the field on every element from the currents of all other elements
+ *      plus the applied field (the dense coaxial-loop mutual-inductance
+ *      operator M, complete elliptic integrals K and E);
+ *   2. the E-J law E = rho(J) J with Jc(B, T, eps) and Joule heating E.J;
+ *   3. the transport-current constraint of every turn (the A-V formulation:
+ *      one loop-voltage unknown per wire) solved with the circuit equations
+ *      (M + dt G) Idot - P u = -R,  P^T Idot = c  (linearly-implicit Euler);
+ *   4. heat diffusion c dT/dt = div(kappa grad T) + E.J with T^3 laws and the
+ *      bath sink -kappa grad T . n = h (T - T0) on the four borders, by ADI.
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a; there is no CPU
+ * fallback.  The library owns all device memory of a coil; the caller owns
+ * every host buffer passed in or out.  Arrays of per-element values are in
+ * the element order
+ *
+ *     e = (t * n_layers + l) * n_sub^2 + b * n_sub + a
+ *
+ * (wire of layer l and turn t, element column a and row b inside the wire).
+ * All functions return a coil_status by value; no C++ exception crosses the
+ * ABI.  One handle must not be used by two host threads at once.
+ */
+#ifndef COIL_H
+#define COIL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct coil coil_t;
+
+typedef enum {
+    COIL_OK = 0,
+    COIL_ERR_INVALID = -1,        /* bad argument; nothing was changed */
+    COIL_ERR_OOM = -2,            /* a device allocation failed */
+    COIL_ERR_CUDA = -3,           /* a CUDA call failed; text in coil_last_error */
+    COIL_ERR_NOT_CONVERGED = -4,  /* the per-step solve hit its iteration cap */
+    COIL_ERR_NONFINITE = -5       /* NaN/Inf or a non-positive pivot appeared */
+} coil_status;
+
+enum { COIL_GEOM_SOLENOID = 0, COIL_GEOM_LIST = 1 };
+
+/* Storage precision of the dense far part of M (row a3).  Near/self blocks,
+ * the per-wire constraint solve and the accumulation of flux and temperature
+ * are FP64 in every mode. */
+enum { COIL_PREC_FP64 = 0, COIL_PREC_FP32 = 1, COIL_PREC_BF16 = 2 };
+
+/*
+ * Geometry (Numerical Algorithm section, Fig. 2a: axisymmetric cross-section,
+ * square array of N_x x N_y turns, N_sub pieces per wire).
+ *
+ * COIL_GEOM_SOLENOID: n_layers x n_turns square wires of side wire_d on a
+ *   pitch (epoxy gap pitch - wire_d, centred), first wire's inner face at
+ *   r_in + gap/2, coil centred on z = 0, n_sub x n_sub square elements per
+ *   wire.  transport = 1: every wire is a series turn carrying I_t(t);
+ *   transport = 0: every element is a free loop.
+ * COIL_GEOM_LIST: n_elem explicit square elements (centres r, z; side h)
+ *   grouped in blocks of `block` consecutive elements; block_transport[w] = 1
+ *   makes block w a turn carrying I_t(t), 0 leaves its loops free.  A list has
+ *   no element grid: the stencil field (B = 0) and the thermal update are
+ *   unavailable, so the material must use jc_model = 1 and thermal = 0.
+ * Blocks (wires) hold at most 64 elements (n_sub <= 8).
+ */
+typedef struct {
+    int kind;
+    int n_layers, n_turns, n_sub;
+    double r_in, pitch, wire_d;
+    int transport;
+    int n_elem, block;
+    const double *r, *z, *h;
+    const int *block_transport;
+} coil_geometry;
+
+/*
+ * Material (Methods: E-J law, Kramer-type Jc, T^3 thermal laws).
+ *   Jc = f Jc0 (1-T/Tc)^1.5 (1-|B|/Bc2(T))^2 / sqrt(|B|+B_reg)
+ *        * max(0, 1 - C_eps |eps|^p_eps),  Bc2(T) = Bc2_0 (1 - (T/Tc)^2),
+ *   (jc_model = 1: Jc = f Jc0);  filament elements follow E0 (J/Jc)^n in
+ *   parallel with rho_n, Cu elements are ohmic (rho_n).
+ *   c = c0 T^3 [J/kg/K] at density rho_m, kappa = kappa_{cu,ep} (T/T_ref)^3,
+ *   bath coefficient h0 (T/T_ref)^3, bath temperature T_bath.
+ * jc_factor (f), strain (eps) and mat (1 = filament, 0 = Cu) are per-element
+ * host arrays of length N, copied at coil_create.
+ */
+typedef struct {
+    double E0, n, Jc0, Tc, Bc2_0, B_reg, C_eps, p_eps;
+    double rho_n, rho_m, c0, kappa_cu, kappa_ep, h0, T_ref, T_bath;
+    int jc_model;
+    int thermal;
+    const double *jc_factor;
+    const double *strain;
+    const int *mat;
+} coil_material;
+
+/*
+ * Options.  rtol: the per-step projected PCG stops when the preconditioned
+ * residual norm falls below rtol times the preconditioned norm of the step's
+ * right-hand side.  maxit: iteration cap (then COIL_ERR_NOT_CONVERGED).
+ * stream: a cudaStream_t to launch on (NULL: the library creates one).
+ * diag_capacity: per-step diagnostic records kept on the device (ring).
+ * profile: record a CUDA event pair around every dense-operator launch on the
+ * coil's stream (coil_info reports their summed duration).
+ */
+typedef struct {
+    int precision;
+    double rtol;
+    int maxit;
+    int device;
+    void *stream;
+    long diag_capacity;
+    int profile;        /* 1: time every operator apply with CUDA events */
+} coil_options;
+
+/*
+ * Drive (Numerical Algorithm section: ramping transport current I_a and
+ * ramping external field H_a).  I_t(t) = min(ramp_rate t, I_max).
+ * Ba_waveform 0: no applied field; 1: B_a = min(Ba_rate t, Ba_max);
+ * 2: triangle 0 -> +Ba_max -> -Ba_max -> 0 with slope Ba_rate, repeated.
+ */
+typedef struct {
+    double dt, ramp_rate, I_max, Ba_rate, Ba_max;
+    int Ba_waveform;
+} coil_drive;
+
+/* Number of doubles in one diagnostic record and their order:
+ * t, I_t, V_term (sum of loop voltages), moment sum(pi r^2 I), Joule power
+ * sum(q 2 pi r a) of the step's start state, T_max after the step,
+ * max |J|/Jc over filament elements (flux-jump criterion |J/Jc| > 1,
+ * Flux Jumps Propagation section), max over wires of the mean rho/rho_n of
+ * their filament elements (quench criterion rho > 0.95 rho_n, Quenches
+ * Propagation section), PCG iterations, final relative residual. */
+#define COIL_DIAG_WIDTH 10
+
+typedef struct {
+    long n_elem, n_blocks, block, grid_r, grid_z;
+    int precision;
+    size_t operator_bytes;        /* bytes of the stored far operator */
+    size_t device_bytes;          /* all device memory held by the handle */
+    long steps;                   /* completed steps */
+    double t;                     /* simulated time after the last step */
+    double setup_ms;              /* operator assembly + upload */
+    long long kernel_launches;    /* kernels launched by coil_step so far */
+    long long operator_launches;  /* dense-operator (GEMV) launches so far */
+    double operator_ms;           /* their summed duration (profile = 1) */
+    long long pcg_iterations;     /* summed over all steps */
+    size_t descriptor_bytes;      /* host-to-device bytes uploaded per coil_step call */
+} coil_info_t;
+
+/* Zero the launch / timing counters of coil_info. */
+coil_status coil_reset_counters(coil_t *c);
+
+/* Create a coil: validate, upload, assemble M on the device (far part in the
+ * chosen precision, intra-wire blocks in FP64).  State: I = 0, T = T_bath,
+ * t = 0.  On failure *out is NULL and nothing is leaked. */
+coil_status coil_create(const coil_geometry *geom, const coil_material *mat,
+                        const coil_options *opt, coil_t **out);
+
+/* Advance n_steps time steps with the drive.  Runs entirely on the device;
+ * returns after the stream has finished.  A non-OK status leaves the state
+ * at the end of the last completed step (see coil_info.steps). */
+coil_status coil_step(coil_t *c, long n_steps, const coil_drive *drive);
+
+/* Copy the current state to host buffers of N doubles (NULL = skip): current
+ * density J [A/m^2], B_r, B_z [T] from the stencil of the loop flux, T [K];
+ * and the moment sum(pi r^2 I) [A m^2].  `Ba` is the applied field at the
+ * current time, needed for B (pass the drive used by coil_step, or NULL for
+ * B_a = 0). */
+coil_status coil_read(coil_t *c, const coil_drive *Ba, double *J, double *Br,
+                      double *Bz, double *T, double *moment);
+
+/* Same as coil_read but into DEVICE buffers of N doubles (NULL = skip). */
+coil_status coil_read_device(coil_t *c, const coil_drive *Ba, double *dJ,
+                             double *dBr, double *dBz, double *dT);
+
+/* Diagnostic records of steps [first, first + count) into out[count][10]. */
+coil_status coil_read_diag(coil_t *c, long first, long count, double *out);
+
+/* Per wire: first step index whose start state met the flux-jump criterion
+ * (max |J|/Jc > 1) and the quench criterion (mean rho/rho_n > 0.95); -1 if
+ * never.  Host arrays of n_blocks longs. */
+coil_status coil_read_onsets(coil_t *c, long *first_jump, long *first_quench);
+
+/* Element currents I [A] (host, N doubles) and set them (state injection for
+ * tests; also resets the accumulated flux to M I). */
+coil_status coil_get_currents(coil_t *c, double *I);
+coil_status coil_set_currents(coil_t *c, const double *I);
+
+/* Apply the assembled operator: y = M p (far part in the stored precision
+ * plus the FP64 intra-wire blocks), host vectors of N doubles. */
+coil_status coil_apply_operator(coil_t *c, const double *p, double *y);
+
+/* Read the dense operator row by row into a host N x N FP64 array
+ * (far part converted from its storage precision, near blocks added). */
+coil_status coil_read_operator(coil_t *c, double *M);
+
+/* Serialise / restore the FP64 state (I, flux, T^4, t, step, warm start).
+ * With buf == NULL, *bytes receives the required size. */
+coil_status coil_save_state(coil_t *c, void *buf, size_t *bytes);
+coil_status coil_load_state(coil_t *c, const void *buf, size_t bytes);
+
+coil_status coil_info(const coil_t *c, coil_info_t *info);
+const char *coil_last_error(const coil_t *c);
+void coil_destroy(coil_t *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COIL_H */

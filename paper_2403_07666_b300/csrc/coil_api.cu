@@ -1,0 +1,948 @@
+// C ABI of the coil stepper: handle life cycle, validation, host-side
+// geometry tables, operator assembly and the per-step launch sequence.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/coil.h"
+#include "common.cuh"
+
+namespace cq {
+cudaError_t upload_gl_rule(const double* x, const double* w);
+cudaError_t launch_table(const double* rc, const double* zc, const double* hc, int C, int NT,
+                         double pitch_t, double* tab, cudaStream_t s);
+cudaError_t launch_expand(const double* tab, int C, int NT, int wire_div, long long N, long long ld,
+                          int prec, void* M, cudaStream_t s);
+cudaError_t launch_near_blocks(const double* tab, int C, int NT, int B, int n_types, double* near,
+                               cudaStream_t s);
+cudaError_t launch_gemv(const CoilDev* cds, int n_coils, int prec, long long max_rows, int which,
+                        int n_sm, cudaStream_t s);
+
+__global__ void k_pointwise(const CoilDev* __restrict__ cds);
+__global__ void k_factor(const CoilDev* __restrict__ cds);
+__global__ void k_near(const CoilDev* __restrict__ cds, int which);
+__global__ void k_init(const CoilDev* __restrict__ cds);
+__global__ void k_update(const CoilDev* __restrict__ cds);
+__global__ void k_direction(const CoilDev* __restrict__ cds);
+__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode);
+__global__ void k_finalize(const CoilDev* __restrict__ cds);
+__global__ void k_adi_r(const CoilDev* __restrict__ cds);
+__global__ void k_adi_z(const CoilDev* __restrict__ cds);
+__global__ void k_step_end(const CoilDev* __restrict__ cds);
+__global__ void k_read(const CoilDev* __restrict__ cds, double Ba, double* J, double* Br, double* Bz,
+                       double* T);
+__global__ void k_moment(const CoilDev* __restrict__ cds, double* out);
+__global__ void k_to_float(const double* x, float* f, int n);
+}  // namespace cq
+
+using namespace cq;
+
+struct coil {
+    int device = 0;
+    int n_sm = 148;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    CoilDev h{};                 // host copy of the descriptor
+    CoilDev* d = nullptr;        // device copy
+    Scalars* pinned = nullptr;   // host-pinned mirror of the device scalars
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    size_t op_bytes = 0;
+    std::string err;
+    // host copies needed later
+    std::vector<double> r_host, area_host, Kr_host, Kz_host;
+    int n_sub = 0, gap_kind = 0;
+    double thomas_dt = -1.0;
+    long long steps = 0;
+    double t = 0.0;
+    int last_iters = 8;
+    double setup_ms = 0.0;
+    coil_drive drive{};
+    bool has_drive = false;
+    double* readbuf = nullptr;   // 5 N doubles for coil_read
+    // counters and optional operator timing
+    int profile = 0;
+    long long launches = 0, op_launches = 0, pcg_iters = 0;
+    double op_ms = 0.0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;          // event pairs recorded since the last harvest
+};
+
+namespace {
+
+const char* kNoHandle = "null coil handle";
+
+coil_status fail(coil_t* c, coil_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+coil_status cuda_fail(coil_t* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(c, COIL_ERR_OOM, m);
+    return fail(c, COIL_ERR_CUDA, m);
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e__ = (call);                         \
+        if (e__ != cudaSuccess) return cuda_fail(c, e__, where); \
+    } while (0)
+
+template <typename T>
+coil_status dalloc(coil_t* c, T** p, size_t count, const char* what) {
+    size_t nb = count * sizeof(T);
+    if (nb == 0) nb = 16;
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, COIL_ERR_OOM, std::string("device allocation of ") + what + " failed (" +
+                                         std::to_string(nb) + " bytes)");
+    }
+    c->allocs.push_back(v);
+    c->bytes += nb;
+    *p = static_cast<T*>(v);
+    CK(cudaMemsetAsync(v, 0, nb, c->stream), "memset");
+    return COIL_OK;
+}
+
+template <typename T>
+coil_status upload(coil_t* c, T** p, const std::vector<T>& host, const char* what) {
+    coil_status st = dalloc(c, p, host.size(), what);
+    if (st != COIL_OK) return st;
+    if (!host.empty())
+        CK(cudaMemcpyAsync(*p, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream),
+           what);
+    return COIL_OK;
+}
+
+#define TRY(x)                               \
+    do {                                     \
+        coil_status s__ = (x);               \
+        if (s__ != COIL_OK) return s__;      \
+    } while (0)
+
+bool is_fin(double v) { return isfinite(v) != 0; }
+
+// 3-point Lagrange derivative weights at x for nodes x0 < x1 < x2.
+void lagrange_weights(double x0, double x1, double x2, double x, double* w) {
+    w[0] = ((x - x1) + (x - x2)) / ((x0 - x1) * (x0 - x2));
+    w[1] = ((x - x0) + (x - x2)) / ((x1 - x0) * (x1 - x2));
+    w[2] = ((x - x0) + (x - x1)) / ((x2 - x0) * (x2 - x1));
+}
+
+void stencil_axis(const std::vector<double>& ax, std::vector<int>& j0, std::vector<double>& w) {
+    int G = (int)ax.size();
+    j0.assign(G, 0);
+    w.assign(3 * (size_t)G, 0.0);
+    for (int k = 0; k < G; ++k) {
+        if (G >= 3) {
+            int j = k - 1;
+            if (j < 0) j = 0;
+            if (j > G - 3) j = G - 3;
+            j0[k] = j;
+            lagrange_weights(ax[j], ax[j + 1], ax[j + 2], ax[k], &w[3 * (size_t)k]);
+        } else if (G == 2) {
+            double s = 1.0 / (ax[1] - ax[0]);
+            w[3 * (size_t)k] = -s;
+            w[3 * (size_t)k + 1] = s;
+        }
+    }
+}
+
+// Thomas factors of (I - hd/C A) for face conductances K (G - 1 faces).
+void thomas_factors(const std::vector<double>& K, double hd, double C, std::vector<double>& lo,
+                    std::vector<double>& inv, std::vector<double>& cp) {
+    int G = (int)K.size() + 1;
+    std::vector<double> diag(G, 1.0), up(G, 0.0);
+    lo.assign(G, 0.0);
+    double cf = hd / C;
+    for (int i = 0; i + 1 < G; ++i) {
+        lo[i + 1] = -cf * K[i];
+        up[i] = -cf * K[i];
+        diag[i] += cf * K[i];
+        diag[i + 1] += cf * K[i];
+    }
+    inv.assign(G, 0.0);
+    cp.assign(G, 0.0);
+    double den = diag[0];
+    inv[0] = 1.0 / den;
+    cp[0] = G > 1 ? up[0] / den : 0.0;
+    for (int i = 1; i < G; ++i) {
+        den = diag[i] - lo[i] * cp[i - 1];
+        inv[i] = 1.0 / den;
+        cp[i] = (i < G - 1) ? up[i] / den : 0.0;
+    }
+}
+
+double host_drive_field(const coil_drive* d, double t) {
+    if (!d || d->Ba_waveform == 0 || d->Ba_rate == 0.0) return 0.0;
+    if (d->Ba_waveform == 1) return fmin(d->Ba_rate * t, d->Ba_max);
+    double period = 4.0 * d->Ba_max / d->Ba_rate;
+    double tau = t - period * floor(t / period);
+    if (tau < 0.25 * period) return d->Ba_rate * tau;
+    if (tau < 0.75 * period) return d->Ba_max - d->Ba_rate * (tau - 0.25 * period);
+    return -d->Ba_max + d->Ba_rate * (tau - 0.75 * period);
+}
+
+coil_status validate(const coil_geometry* g, const coil_material* m, const coil_options* o, coil_t* c) {
+    if (!g || !m || !o) return fail(c, COIL_ERR_INVALID, "null geometry, material or options");
+    if (o->precision < 0 || o->precision > 2) return fail(c, COIL_ERR_INVALID, "unknown precision");
+    if (!(o->rtol > 0.0 && o->rtol < 1.0)) return fail(c, COIL_ERR_INVALID, "rtol must be in (0, 1)");
+    if (o->maxit < 1) return fail(c, COIL_ERR_INVALID, "maxit must be >= 1");
+    if (g->kind == COIL_GEOM_SOLENOID) {
+        if (g->n_layers < 1 || g->n_turns < 1 || g->n_sub < 1)
+            return fail(c, COIL_ERR_INVALID, "solenoid needs n_layers, n_turns, n_sub >= 1");
+        if (g->n_sub * g->n_sub > kMaxBlock)
+            return fail(c, COIL_ERR_INVALID, "n_sub^2 must not exceed 64 elements per wire");
+        if (!(g->wire_d > 0.0) || !(g->pitch >= g->wire_d) || !(g->r_in >= 0.0) || !is_fin(g->pitch) ||
+            !is_fin(g->r_in))
+            return fail(c, COIL_ERR_INVALID, "solenoid needs wire_d > 0, pitch >= wire_d, r_in >= 0");
+        double n_elem = (double)g->n_layers * g->n_turns * g->n_sub * g->n_sub;
+        if (n_elem > 2.0e8) return fail(c, COIL_ERR_INVALID, "too many elements");
+    } else if (g->kind == COIL_GEOM_LIST) {
+        if (g->n_elem < 1 || g->block < 1 || g->block > kMaxBlock || g->n_elem % g->block)
+            return fail(c, COIL_ERR_INVALID, "list needs n_elem a multiple of block, 1 <= block <= 64");
+        if (!g->r || !g->z || !g->h || !g->block_transport)
+            return fail(c, COIL_ERR_INVALID, "list needs r, z, h and block_transport");
+        for (int i = 0; i < g->n_elem; ++i) {
+            if (!(g->r[i] > 0.0) || !is_fin(g->r[i]) || !is_fin(g->z[i]) || !(g->h[i] > 0.0) ||
+                !is_fin(g->h[i]))
+                return fail(c, COIL_ERR_NONFINITE, "list element with non-finite or non-positive r/h");
+            if (!(g->h[i] < 2.0 * g->r[i])) return fail(c, COIL_ERR_INVALID, "element crosses the axis");
+        }
+        if (m->thermal || m->jc_model != 1)
+            return fail(c, COIL_ERR_INVALID, "list geometry has no grid: needs thermal = 0, jc_model = 1");
+    } else {
+        return fail(c, COIL_ERR_INVALID, "unknown geometry kind");
+    }
+    const double vals[] = {m->E0, m->n, m->Jc0, m->Tc, m->Bc2_0, m->B_reg, m->C_eps, m->p_eps,
+                           m->rho_n, m->rho_m, m->c0, m->kappa_cu, m->kappa_ep, m->h0, m->T_ref, m->T_bath};
+    for (double v : vals)
+        if (!is_fin(v)) return fail(c, COIL_ERR_NONFINITE, "non-finite material constant");
+    if (!(m->rho_n > 0.0) || !(m->E0 > 0.0) || !(m->n >= 1.0) || !(m->T_bath > 0.0) || !(m->T_ref > 0.0) ||
+        !(m->rho_m > 0.0) || !(m->c0 > 0.0) || !(m->kappa_cu > 0.0) || !(m->kappa_ep > 0.0) ||
+        !(m->Tc > 0.0) || !(m->Bc2_0 > 0.0) || !(m->B_reg > 0.0) || m->h0 < 0.0)
+        return fail(c, COIL_ERR_INVALID, "material constant out of range");
+    if (!m->jc_factor || !m->strain || !m->mat)
+        return fail(c, COIL_ERR_INVALID, "jc_factor, strain and mat arrays are required");
+    return COIL_OK;
+}
+
+coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, const coil_options* o) {
+    CoilDev& h = c->h;
+    const bool sol = g->kind == COIL_GEOM_SOLENOID;
+    int N, B, W, C, NT, n_types;
+    double pitch_t;
+    std::vector<double> r, z, hh;
+    std::vector<int> constrained, block_type;
+    std::vector<int> elem_grid, grid_elem;
+    int Gr = 0, Gz = 0, n = 0;
+    double gap = 0.0, hel = 0.0;
+    std::vector<double> r_axis, z_axis;
+    if (sol) {
+        n = g->n_sub;
+        int NL = g->n_layers;
+        NT = g->n_turns;
+        B = n * n;
+        W = NL * NT;
+        N = W * B;
+        C = NL * B;
+        n_types = NL;
+        pitch_t = g->pitch;
+        gap = g->pitch - g->wire_d;
+        hel = g->wire_d / n;
+        Gr = NL * n;
+        Gz = NT * n;
+        r.resize(N);
+        z.resize(N);
+        hh.assign(N, hel);
+        elem_grid.resize(N);
+        grid_elem.resize((size_t)Gr * Gz);
+        for (int e = 0; e < N; ++e) {
+            int a = e % n, b = (e / n) % n, w = e / B, l = w % NL, t = w / NL;
+            r[e] = g->r_in + 0.5 * gap + l * g->pitch + (a + 0.5) * hel;
+            z[e] = -0.5 * NT * g->pitch + 0.5 * gap + t * g->pitch + (b + 0.5) * hel;
+            int ir = l * n + a, iz = t * n + b;
+            elem_grid[e] = iz * Gr + ir;
+            grid_elem[(size_t)iz * Gr + ir] = e;
+        }
+        constrained.assign(W, g->transport ? 1 : 0);
+        block_type.resize(W);
+        for (int w = 0; w < W; ++w) block_type[w] = w % NL;
+        r_axis.resize(Gr);
+        z_axis.resize(Gz);
+        for (int i = 0; i < Gr; ++i) r_axis[i] = r[grid_elem[i]];
+        for (int j = 0; j < Gz; ++j) z_axis[j] = z[grid_elem[(size_t)j * Gr]];
+        c->n_sub = n;
+    } else {
+        N = g->n_elem;
+        B = g->block;
+        W = N / B;
+        C = N;
+        NT = 1;
+        n_types = W;
+        pitch_t = 0.0;
+        r.assign(g->r, g->r + N);
+        z.assign(g->z, g->z + N);
+        hh.assign(g->h, g->h + N);
+        constrained.resize(W);
+        block_type.resize(W);
+        for (int w = 0; w < W; ++w) {
+            constrained[w] = g->block_transport[w] ? 1 : 0;
+            block_type[w] = w;
+        }
+    }
+    for (int e = 0; e < N; ++e) {
+        if (!is_fin(m->jc_factor[e]) || !is_fin(m->strain[e]) || m->jc_factor[e] < 0.0)
+            return fail(c, COIL_ERR_NONFINITE, "non-finite or negative jc_factor / strain");
+        if (m->mat[e] != 0 && m->mat[e] != 1) return fail(c, COIL_ERR_INVALID, "mat must be 0 or 1");
+    }
+    h.N = N;
+    h.W = W;
+    h.B = B;
+    h.n_types = n_types;
+    h.has_grid = sol ? 1 : 0;
+    h.Gr = Gr;
+    h.Gz = Gz;
+    h.thermal = (sol && m->thermal) ? 1 : 0;
+    h.jc_model = m->jc_model;
+    h.precision = o->precision;
+    h.ld = ((long long)N + 63) / 64 * 64;
+    h.E0 = m->E0; h.nexp = m->n; h.Jc0 = m->Jc0; h.Tc = m->Tc; h.Bc2_0 = m->Bc2_0; h.B_reg = m->B_reg;
+    h.C_eps = m->C_eps; h.p_eps = m->p_eps; h.rho_n = m->rho_n; h.rho_m = m->rho_m; h.c0 = m->c0;
+    h.h0 = m->h0; h.T_ref = m->T_ref; h.T_bath = m->T_bath;
+    h.maxit = o->maxit;
+    h.rtol2 = o->rtol * o->rtol;
+    h.diag_cap = o->diag_capacity > 0 ? o->diag_capacity : 65536;
+
+    std::vector<double> area(N);
+    for (int e = 0; e < N; ++e) area[e] = hh[e] * hh[e];
+    c->r_host = r;
+    c->area_host = area;
+    std::vector<double> jf(m->jc_factor, m->jc_factor + N), st(m->strain, m->strain + N);
+    std::vector<int> mt(m->mat, m->mat + N);
+    double* dp;
+    int* ip;
+    TRY(upload(c, &dp, r, "r")); h.r = dp;
+    TRY(upload(c, &dp, area, "area")); h.area = dp;
+    TRY(upload(c, &dp, jf, "jc_factor")); h.jc_factor = dp;
+    TRY(upload(c, &dp, st, "strain")); h.strain = dp;
+    TRY(upload(c, &ip, mt, "mat")); h.mat = ip;
+    TRY(upload(c, &ip, constrained, "constrained")); h.constrained = ip;
+    TRY(upload(c, &ip, block_type, "block_type")); h.block_type = ip;
+
+    // thermal / stencil tables
+    if (sol) {
+        TRY(upload(c, &ip, elem_grid, "elem_grid")); h.elem_grid = ip;
+        TRY(upload(c, &ip, grid_elem, "grid_elem")); h.grid_elem = ip;
+        std::vector<int> j0r, j0z;
+        std::vector<double> wr, wz;
+        stencil_axis(r_axis, j0r, wr);
+        stencil_axis(z_axis, j0z, wz);
+        TRY(upload(c, &ip, j0r, "sr_j0")); h.sr_j0 = ip;
+        TRY(upload(c, &ip, j0z, "sz_j0")); h.sz_j0 = ip;
+        TRY(upload(c, &dp, wr, "sr_w")); h.sr_w = dp;
+        TRY(upload(c, &dp, wz, "sz_w")); h.sz_w = dp;
+        double T3 = 4.0 * m->T_ref * m->T_ref * m->T_ref;
+        double Kin = m->kappa_cu / T3;
+        double Kgap = gap > 0.0 ? hel / (hel / m->kappa_cu + gap / m->kappa_ep) / T3 : Kin;
+        c->Kr_host.assign(Gr > 1 ? Gr - 1 : 0, Kin);
+        c->Kz_host.assign(Gz > 1 ? Gz - 1 : 0, Kin);
+        for (int i = 0; i + 1 < Gr; ++i)
+            if ((i + 1) % n == 0) c->Kr_host[i] = Kgap;
+        for (int j = 0; j + 1 < Gz; ++j)
+            if ((j + 1) % n == 0) c->Kz_host[j] = Kgap;
+        TRY(upload(c, &dp, c->Kr_host, "Kr")); h.Kr = dp;
+        TRY(upload(c, &dp, c->Kz_host, "Kz")); h.Kz = dp;
+        std::vector<int> nb((size_t)Gr * Gz);
+        for (int j = 0; j < Gz; ++j)
+            for (int i = 0; i < Gr; ++i)
+                nb[(size_t)j * Gr + i] = (i == 0) + (i == Gr - 1) + (j == 0) + (j == Gz - 1);
+        TRY(upload(c, &ip, nb, "nborder")); h.nborder = ip;
+        h.Ccell = m->rho_m * m->c0 * hel * hel / 4.0;
+        h.helem = hel;
+        double* t6;
+        TRY(dalloc(c, &t6, 3 * (size_t)Gr + 3 * (size_t)Gz, "thomas"));
+        h.thr_lo = t6; h.thr_inv = t6 + Gr; h.thr_cp = t6 + 2 * Gr;
+        h.thz_lo = t6 + 3 * Gr; h.thz_inv = t6 + 3 * Gr + Gz; h.thz_cp = t6 + 3 * Gr + 2 * Gz;
+        std::vector<double> u0((size_t)Gr * Gz, m->T_bath * m->T_bath * m->T_bath * m->T_bath);
+        TRY(upload(c, &h.uT, u0, "uT"));
+        TRY(dalloc(c, &h.ustar, (size_t)Gr * Gz, "ustar"));
+        TRY(dalloc(c, &h.src, (size_t)Gr * Gz, "src"));
+        TRY(dalloc(c, &h.qgrid, (size_t)Gr * Gz, "qgrid"));
+        TRY(dalloc(c, &h.partT, (size_t)Gr, "partT"));
+    }
+
+    // state and work vectors (ld long, zero padded, for the operator input)
+    size_t ld = (size_t)h.ld;
+    TRY(dalloc(c, &h.I, N, "I"));
+    TRY(dalloc(c, &h.Phi, N, "Phi"));
+    TRY(dalloc(c, &h.x, ld, "x"));
+    TRY(dalloc(c, &h.res, N, "res"));
+    TRY(dalloc(c, &h.zv, N, "z"));
+    TRY(dalloc(c, &h.dv, ld, "d"));
+    TRY(dalloc(c, &h.qv, N, "q"));
+    TRY(dalloc(c, &h.R, N, "R"));
+    TRY(dalloc(c, &h.G, N, "G"));
+    TRY(dalloc(c, &h.pf, ld, "pf"));
+    TRY(dalloc(c, &h.L, (size_t)W * B * B, "L"));
+    TRY(dalloc(c, &h.y1, (size_t)W * B, "y1"));
+    TRY(dalloc(c, &h.sigma, W, "sigma"));
+    TRY(dalloc(c, &h.cw, W, "cw"));
+    TRY(dalloc(c, &h.uw, W, "uw"));
+    TRY(dalloc(c, &h.parts, 8 * (size_t)W, "parts"));
+    TRY(dalloc(c, &h.first_jump, W, "first_jump"));
+    TRY(dalloc(c, &h.first_quench, W, "first_quench"));
+    CK(cudaMemsetAsync(h.first_jump, 0xff, W * sizeof(long long), c->stream), "memset");
+    CK(cudaMemsetAsync(h.first_quench, 0xff, W * sizeof(long long), c->stream), "memset");
+    TRY(dalloc(c, &h.diag, (size_t)h.diag_cap * COIL_DIAG_WIDTH, "diag"));
+    TRY(dalloc(c, &h.sc, 1, "scalars"));
+    TRY(dalloc(c, &c->readbuf, 5 * (size_t)N, "read buffer"));
+
+    // operator: table of distinct entries, dense far part, FP64 near blocks
+    size_t esz = o->precision == PREC_FP64 ? 8 : (o->precision == PREC_FP32 ? 4 : 2);
+    void* M = nullptr;
+    {
+        cudaError_t e = cudaMalloc(&M, (size_t)N * ld * esz);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, COIL_ERR_OOM, "device allocation of the far operator failed (" +
+                                             std::to_string((size_t)N * ld * esz) + " bytes)");
+        }
+        c->allocs.push_back(M);
+        c->bytes += (size_t)N * ld * esz;
+        c->op_bytes = (size_t)N * ld * esz;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    CK(cudaEventRecord(e0, c->stream), "event");
+    double glx[4], glw[4];
+    double s65 = sqrt(6.0 / 5.0);
+    double xa = sqrt(3.0 / 7.0 - 2.0 / 7.0 * s65), xb = sqrt(3.0 / 7.0 + 2.0 / 7.0 * s65);
+    double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+    glx[0] = -xb; glx[1] = -xa; glx[2] = xa; glx[3] = xb;
+    glw[0] = wb; glw[1] = wa; glw[2] = wa; glw[3] = wb;
+    CK(upload_gl_rule(glx, glw), "gl rule");
+    std::vector<double> rc(r.begin(), r.begin() + C), zc(z.begin(), z.begin() + C), hc(hh.begin(), hh.begin() + C);
+    double *drc, *dzc, *dhc, *tab;
+    TRY(upload(c, &drc, rc, "rc"));
+    TRY(upload(c, &dzc, zc, "zc"));
+    TRY(upload(c, &dhc, hc, "hc"));
+    size_t tab_n = (size_t)C * C * (2 * (size_t)NT - 1);
+    TRY(dalloc(c, &tab, tab_n, "operator table"));
+    CK(launch_table(drc, dzc, dhc, C, NT, pitch_t, tab, c->stream), "table");
+    h.Mfar = M;
+    CK(launch_expand(tab, C, NT, B, N, h.ld, o->precision, M, c->stream), "expand");
+    double* nearp;
+    TRY(dalloc(c, &nearp, (size_t)n_types * B * B, "near blocks"));
+    CK(launch_near_blocks(tab, C, NT, B, n_types, nearp, c->stream), "near blocks");
+    h.near = nearp;
+    CK(cudaEventRecord(e1, c->stream), "event");
+    CK(cudaStreamSynchronize(c->stream), "assembly");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->setup_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the table and channel arrays are no longer needed
+    for (void* p : {(void*)tab, (void*)drc, (void*)dzc, (void*)dhc}) {
+        for (size_t i = 0; i < c->allocs.size(); ++i)
+            if (c->allocs[i] == p) { c->allocs.erase(c->allocs.begin() + i); break; }
+        cudaFree(p);
+    }
+    c->bytes -= tab_n * sizeof(double) + 3 * (size_t)C * sizeof(double);
+
+    CK(cudaMalloc(&c->d, sizeof(CoilDev)), "descriptor");
+    CK(cudaHostAlloc(&c->pinned, sizeof(Scalars), cudaHostAllocDefault), "pinned scalars");
+    memset(c->pinned, 0, sizeof(Scalars));
+    CK(cudaMemcpyAsync(c->d, &h, sizeof(CoilDev), cudaMemcpyHostToDevice, c->stream), "descriptor");
+    CK(cudaStreamSynchronize(c->stream), "create");
+    return COIL_OK;
+}
+
+coil_status sync_descriptor(coil_t* c) {
+    CK(cudaMemcpyAsync(c->d, &c->h, sizeof(CoilDev), cudaMemcpyHostToDevice, c->stream), "descriptor");
+    return COIL_OK;
+}
+
+coil_status set_drive(coil_t* c, const coil_drive* dr) {
+    if (!dr || !(dr->dt > 0.0) || !is_fin(dr->dt) || !is_fin(dr->ramp_rate) || !is_fin(dr->I_max) ||
+        !is_fin(dr->Ba_rate) || !is_fin(dr->Ba_max))
+        return fail(c, COIL_ERR_INVALID, "drive needs a finite dt > 0 and finite rates");
+    if (dr->Ba_waveform < 0 || dr->Ba_waveform > 2) return fail(c, COIL_ERR_INVALID, "unknown Ba_waveform");
+    if (dr->Ba_waveform == 2 && dr->Ba_rate != 0.0 && !(dr->Ba_max > 0.0))
+        return fail(c, COIL_ERR_INVALID, "triangle waveform needs Ba_max > 0");
+    CoilDev& h = c->h;
+    h.dt = dr->dt; h.ramp = dr->ramp_rate; h.Imax = dr->I_max;
+    h.Ba_rate = dr->Ba_rate; h.Ba_max = dr->Ba_max; h.Ba_wf = dr->Ba_waveform;
+    if (h.has_grid && c->thomas_dt != dr->dt) {
+        std::vector<double> lo, inv, cp, lz, iz, cz;
+        thomas_factors(c->Kr_host, 0.5 * dr->dt, h.Ccell, lo, inv, cp);
+        thomas_factors(c->Kz_host, 0.5 * dr->dt, h.Ccell, lz, iz, cz);
+        std::vector<double> all;
+        all.insert(all.end(), lo.begin(), lo.end());
+        all.insert(all.end(), inv.begin(), inv.end());
+        all.insert(all.end(), cp.begin(), cp.end());
+        all.insert(all.end(), lz.begin(), lz.end());
+        all.insert(all.end(), iz.begin(), iz.end());
+        all.insert(all.end(), cz.begin(), cz.end());
+        CK(cudaMemcpyAsync((void*)h.thr_lo, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream), "thomas");
+        CK(cudaStreamSynchronize(c->stream), "thomas");
+        c->thomas_dt = dr->dt;
+    }
+    c->drive = *dr;
+    c->has_drive = true;
+    return sync_descriptor(c);
+}
+
+coil_status read_scalars(coil_t* c) {
+    CK(cudaMemcpyAsync(c->pinned, c->h.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream), "scalars");
+    CK(cudaStreamSynchronize(c->stream), "step");
+    return COIL_OK;
+}
+
+size_t block_smem(const CoilDev& h) { return ((size_t)h.B * h.B + 2 * (size_t)h.B) * sizeof(double); }
+
+// Dense-operator launch, bracketed by an event pair when profiling.
+coil_status gemv(coil_t* c, int which) {
+    const CoilDev& h = c->h;
+    if (c->profile) {
+        if (c->ev_used * 2 + 2 > c->ev_pool.size()) {
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e), "event");
+                c->ev_pool.push_back(e);
+            }
+        }
+        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used], c->stream), "event");
+    }
+    CK(launch_gemv(c->d, 1, h.precision, h.N, which, c->n_sm, c->stream), "gemv");
+    if (c->profile) {
+        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], c->stream), "event");
+        c->ev_used += 1;
+    }
+    c->op_launches += 1;
+    c->launches += 1;
+    return COIL_OK;
+}
+
+// Sum the recorded operator intervals (call after a stream synchronize).
+void harvest_events(coil_t* c) {
+    for (size_t i = 0; i < c->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]) == cudaSuccess) c->op_ms += ms;
+    }
+    c->ev_used = 0;
+}
+
+coil_status one_iteration(coil_t* c) {
+    const CoilDev& h = c->h;
+    cudaStream_t s = c->stream;
+    unsigned wb = (unsigned)((h.W + 7) / 8);
+    TRY(gemv(c, 1));
+    c->launches += 5;
+    k_near<<<wb, 256, 0, s>>>(c->d, 1);
+    k_reduce<<<1, 256, 0, s>>>(c->d, 2);
+    k_update<<<h.W, 32, block_smem(h), s>>>(c->d);
+    k_reduce<<<1, 256, 0, s>>>(c->d, 3);
+    unsigned eb = (unsigned)((h.N + 255) / 256);
+    if (eb > (unsigned)c->n_sm * 16) eb = c->n_sm * 16;
+    k_direction<<<eb, 256, 0, s>>>(c->d);
+    CK(cudaGetLastError(), "iteration launch");
+    return COIL_OK;
+}
+
+coil_status run_step(coil_t* c) {
+    const CoilDev& h = c->h;
+    cudaStream_t s = c->stream;
+    unsigned wb = (unsigned)((h.W + 7) / 8);
+    k_pointwise<<<wb, 256, 0, s>>>(c->d);
+    k_factor<<<h.W, 32, block_smem(h), s>>>(c->d);
+    k_reduce<<<1, 256, 0, s>>>(c->d, 0);
+    TRY(gemv(c, 0));
+    k_near<<<wb, 256, 0, s>>>(c->d, 0);
+    k_init<<<h.W, 32, block_smem(h), s>>>(c->d);
+    k_reduce<<<1, 256, 0, s>>>(c->d, 1);
+    c->launches += 6;
+    CK(cudaGetLastError(), "step launch");
+    // PCG: enqueue the expected number of iterations, then one at a time
+    int chunk = c->last_iters > 1 ? c->last_iters : 1;
+    int total = 0;
+    for (;;) {
+        for (int i = 0; i < chunk; ++i) TRY(one_iteration(c));
+        total += chunk;
+        TRY(read_scalars(c));
+        if (c->pinned->done) break;
+        if (total > h.maxit + 2) break;
+        chunk = 1;
+    }
+    int st = c->pinned->status;
+    if (!c->pinned->done || st == ST_NOT_CONVERGED)
+        return fail(c, COIL_ERR_NOT_CONVERGED, "per-step solve did not converge within maxit iterations");
+    if (st == ST_NONFINITE)
+        return fail(c, COIL_ERR_NONFINITE, "non-finite value or non-positive pivot in the step solve");
+    c->last_iters = c->pinned->iter > 0 ? c->pinned->iter : 1;
+    c->pcg_iters += c->pinned->iter;
+    harvest_events(c);
+    k_finalize<<<wb, 256, 0, s>>>(c->d);
+    if (h.thermal) {
+        k_adi_r<<<h.Gz, 32, h.Gr * sizeof(double), s>>>(c->d);
+        k_adi_z<<<h.Gr, 32, h.Gz * sizeof(double), s>>>(c->d);
+        c->launches += 2;
+    }
+    k_step_end<<<1, 256, 0, s>>>(c->d);
+    c->launches += 2;
+    CK(cudaGetLastError(), "step end launch");
+    c->steps += 1;
+    c->t += h.dt;
+    return COIL_OK;
+}
+
+// y = M p with FP64 near blocks (no dt G term): p -> x (and its FP32 copy),
+// result in q.  Leaves x = 0 afterwards (cold warm start).
+coil_status apply_plain(coil_t* c, const double* dev_p) {
+    CoilDev& h = c->h;
+    cudaStream_t s = c->stream;
+    double dt_save = h.dt;
+    h.dt = 0.0;
+    TRY(sync_descriptor(c));
+    CK(cudaMemcpyAsync(h.x, dev_p, h.N * sizeof(double), cudaMemcpyDeviceToDevice, s), "apply");
+    CK(cudaMemsetAsync(&h.sc->done, 0, sizeof(int), s), "apply");
+    k_to_float<<<(h.N + 255) / 256, 256, 0, s>>>(h.x, h.pf, h.N);
+    CK(launch_gemv(c->d, 1, h.precision, h.N, 0, c->n_sm, s), "gemv");
+    k_near<<<(unsigned)((h.W + 7) / 8), 256, 0, s>>>(c->d, 0);
+    CK(cudaGetLastError(), "apply");
+    h.dt = dt_save;
+    TRY(sync_descriptor(c));
+    return COIL_OK;
+}
+
+}  // namespace
+
+namespace cq {
+__global__ void k_to_float(const double* x, float* f, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = (float)x[i];
+}
+
+__global__ void k_moment(const CoilDev* __restrict__ cds, double* out) {
+    const CoilDev& c = cds[blockIdx.x];
+    __shared__ double sh[32];
+    double m = 0.0;
+    for (int e = threadIdx.x; e < c.N; e += blockDim.x) {
+        double r = c.r[e];
+        m += kPi * r * r * c.I[e];
+    }
+    m = warp_sum(m);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        m = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        m = warp_sum(m);
+        if (lane == 0) *out = m;
+    }
+}
+}  // namespace cq
+
+// ============================================================== C ABI
+
+extern "C" {
+
+coil_status coil_create(const coil_geometry* geom, const coil_material* mat, const coil_options* opt,
+                        coil_t** out) {
+    if (!out) return COIL_ERR_INVALID;
+    *out = nullptr;
+    coil_t* c = new (std::nothrow) coil();
+    if (!c) return COIL_ERR_OOM;
+    coil_status st = validate(geom, mat, opt, c);
+    if (st == COIL_OK) {
+        cudaError_t e = cudaSetDevice(opt->device);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "cudaSetDevice");
+        } else {
+            c->device = opt->device;
+            c->profile = opt->profile ? 1 : 0;
+            cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, opt->device);
+            if (opt->stream) {
+                c->stream = (cudaStream_t)opt->stream;
+            } else {
+                e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+                if (e != cudaSuccess) st = cuda_fail(c, e, "stream");
+                else c->own_stream = true;
+            }
+            if (st == COIL_OK) st = setup(c, geom, mat, opt);
+        }
+    }
+    if (st != COIL_OK) {
+        fprintf(stderr, "coil_create: %s\n", c->err.c_str());
+        coil_destroy(c);
+        return st;
+    }
+    *out = c;
+    return COIL_OK;
+}
+
+coil_status coil_step(coil_t* c, long n_steps, const coil_drive* drive) {
+    if (!c) return COIL_ERR_INVALID;
+    if (n_steps < 0) return fail(c, COIL_ERR_INVALID, "n_steps must be >= 0");
+    cudaSetDevice(c->device);
+    TRY(set_drive(c, drive));
+    for (long k = 0; k < n_steps; ++k) TRY(run_step(c));
+    CK(cudaStreamSynchronize(c->stream), "coil_step");
+    return COIL_OK;
+}
+
+coil_status coil_read_device(coil_t* c, const coil_drive* dr, double* dJ, double* dBr, double* dBz,
+                             double* dT) {
+    if (!c) return COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    double Ba = host_drive_field(dr, c->t);
+    const CoilDev& h = c->h;
+    unsigned eb = (unsigned)((h.N + 255) / 256);
+    cq::k_read<<<eb, 256, 0, c->stream>>>(c->d, Ba, dJ, dBr, dBz, dT);
+    CK(cudaGetLastError(), "read");
+    CK(cudaStreamSynchronize(c->stream), "read");
+    return COIL_OK;
+}
+
+coil_status coil_read(coil_t* c, const coil_drive* dr, double* J, double* Br, double* Bz, double* T,
+                      double* moment) {
+    if (!c) return COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    const CoilDev& h = c->h;
+    double* buf = c->readbuf;
+    size_t N = h.N;
+    double Ba = host_drive_field(dr, c->t);
+    unsigned eb = (unsigned)((N + 255) / 256);
+    cq::k_read<<<eb, 256, 0, c->stream>>>(c->d, Ba, J ? buf : nullptr, Br ? buf + N : nullptr,
+                                            Bz ? buf + 2 * N : nullptr, T ? buf + 3 * N : nullptr);
+    cq::k_moment<<<1, 256, 0, c->stream>>>(c->d, buf + 4 * N);
+    cudaError_t e = cudaGetLastError();
+    double* outs[4] = {J, Br, Bz, T};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (outs[k]) e = cudaMemcpyAsync(outs[k], buf + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    double mom = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&mom, buf + 4 * N, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read");
+    if (moment) *moment = mom;
+    return COIL_OK;
+}
+
+coil_status coil_read_diag(coil_t* c, long first, long count, double* out) {
+    if (!c) return COIL_ERR_INVALID;
+    if (!out || first < 0 || count < 0 || first + count > c->steps)
+        return fail(c, COIL_ERR_INVALID, "diagnostic range outside the completed steps");
+    if (c->steps - first > c->h.diag_cap) return fail(c, COIL_ERR_INVALID, "records no longer in the ring");
+    cudaSetDevice(c->device);
+    for (long k = 0; k < count; ++k) {
+        long slot = (first + k) % c->h.diag_cap;
+        CK(cudaMemcpyAsync(out + k * COIL_DIAG_WIDTH, c->h.diag + slot * COIL_DIAG_WIDTH,
+                           COIL_DIAG_WIDTH * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "diag");
+    }
+    CK(cudaStreamSynchronize(c->stream), "diag");
+    return COIL_OK;
+}
+
+coil_status coil_read_onsets(coil_t* c, long* first_jump, long* first_quench) {
+    if (!c) return COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    size_t W = c->h.W;
+    std::vector<long long> a(W), b(W);
+    CK(cudaMemcpyAsync(a.data(), c->h.first_jump, W * 8, cudaMemcpyDeviceToHost, c->stream), "onsets");
+    CK(cudaMemcpyAsync(b.data(), c->h.first_quench, W * 8, cudaMemcpyDeviceToHost, c->stream), "onsets");
+    CK(cudaStreamSynchronize(c->stream), "onsets");
+    for (size_t w = 0; w < W; ++w) {
+        if (first_jump) first_jump[w] = (long)a[w];
+        if (first_quench) first_quench[w] = (long)b[w];
+    }
+    return COIL_OK;
+}
+
+coil_status coil_get_currents(coil_t* c, double* I) {
+    if (!c || !I) return c ? fail(c, COIL_ERR_INVALID, "null buffer") : COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(I, c->h.I, c->h.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "get");
+    CK(cudaStreamSynchronize(c->stream), "get");
+    return COIL_OK;
+}
+
+coil_status coil_set_currents(coil_t* c, const double* I) {
+    if (!c || !I) return c ? fail(c, COIL_ERR_INVALID, "null buffer") : COIL_ERR_INVALID;
+    for (int e = 0; e < c->h.N; ++e)
+        if (!is_fin(I[e])) return fail(c, COIL_ERR_NONFINITE, "non-finite current");
+    cudaSetDevice(c->device);
+    const CoilDev& h = c->h;
+    CK(cudaMemcpyAsync(h.I, I, h.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "set");
+    TRY(apply_plain(c, h.I));
+    CK(cudaMemcpyAsync(h.Phi, h.qv, h.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "set");
+    CK(cudaMemsetAsync(h.x, 0, h.ld * sizeof(double), c->stream), "set");
+    CK(cudaStreamSynchronize(c->stream), "set");
+    return COIL_OK;
+}
+
+coil_status coil_apply_operator(coil_t* c, const double* p, double* y) {
+    if (!c || !p || !y) return c ? fail(c, COIL_ERR_INVALID, "null buffer") : COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    const CoilDev& h = c->h;
+    // keep the warm start: stash x in res
+    CK(cudaMemcpyAsync(h.res, h.x, h.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "apply");
+    CK(cudaMemcpyAsync(h.zv, p, h.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "apply");
+    TRY(apply_plain(c, h.zv));
+    CK(cudaMemcpyAsync(y, h.qv, h.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "apply");
+    CK(cudaMemcpyAsync(h.x, h.res, h.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "apply");
+    CK(cudaStreamSynchronize(c->stream), "apply");
+    return COIL_OK;
+}
+
+coil_status coil_read_operator(coil_t* c, double* M) {
+    if (!c || !M) return c ? fail(c, COIL_ERR_INVALID, "null buffer") : COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    const CoilDev& h = c->h;
+    size_t N = h.N, ld = h.ld;
+    size_t esz = h.precision == PREC_FP64 ? 8 : (h.precision == PREC_FP32 ? 4 : 2);
+    std::vector<unsigned char> row(ld * esz);
+    for (size_t i = 0; i < N; ++i) {
+        CK(cudaMemcpy(row.data(), (const unsigned char*)h.Mfar + i * ld * esz, ld * esz, cudaMemcpyDeviceToHost),
+           "read operator");
+        for (size_t j = 0; j < N; ++j) {
+            double v;
+            if (esz == 8) {
+                memcpy(&v, &row[j * 8], 8);
+            } else if (esz == 4) {
+                float f;
+                memcpy(&f, &row[j * 4], 4);
+                v = f;
+            } else {
+                unsigned short b;
+                memcpy(&b, &row[j * 2], 2);
+                unsigned u = (unsigned)b << 16;
+                float f;
+                memcpy(&f, &u, 4);
+                v = f;
+            }
+            M[i * N + j] = v;
+        }
+    }
+    std::vector<double> nb((size_t)h.n_types * h.B * h.B);
+    std::vector<int> bt(h.W);
+    CK(cudaMemcpy(nb.data(), h.near, nb.size() * 8, cudaMemcpyDeviceToHost), "read operator");
+    CK(cudaMemcpy(bt.data(), h.block_type, bt.size() * 4, cudaMemcpyDeviceToHost), "read operator");
+    for (int w = 0; w < h.W; ++w)
+        for (int a = 0; a < h.B; ++a)
+            for (int b = 0; b < h.B; ++b)
+                M[(size_t)(w * h.B + a) * N + w * h.B + b] += nb[((size_t)bt[w] * h.B + a) * h.B + b];
+    return COIL_OK;
+}
+
+struct StateHeader {
+    unsigned long long magic;
+    long long N, W, G, steps;
+    double t;
+};
+
+coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
+    if (!c || !bytes) return c ? fail(c, COIL_ERR_INVALID, "null size pointer") : COIL_ERR_INVALID;
+    const CoilDev& h = c->h;
+    size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
+    size_t need = sizeof(StateHeader) + (3 * N + G) * sizeof(double) + 2 * W * sizeof(long long);
+    if (!buf) { *bytes = need; return COIL_OK; }
+    if (*bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
+    cudaSetDevice(c->device);
+    StateHeader hd{0x434f494c53543031ULL, (long long)N, (long long)W, (long long)G, c->steps, c->t};
+    unsigned char* p = (unsigned char*)buf;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    CK(cudaMemcpy(p, h.I, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
+    CK(cudaMemcpy(p, h.Phi, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
+    CK(cudaMemcpy(p, h.x, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
+    if (G) { CK(cudaMemcpy(p, h.uT, G * 8, cudaMemcpyDeviceToHost), "save"); p += G * 8; }
+    CK(cudaMemcpy(p, h.first_jump, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
+    CK(cudaMemcpy(p, h.first_quench, W * 8, cudaMemcpyDeviceToHost), "save");
+    *bytes = need;
+    return COIL_OK;
+}
+
+coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return c ? fail(c, COIL_ERR_INVALID, "null state buffer") : COIL_ERR_INVALID;
+    const CoilDev& h = c->h;
+    size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
+    size_t need = sizeof(StateHeader) + (3 * N + G) * sizeof(double) + 2 * W * sizeof(long long);
+    StateHeader hd;
+    if (bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
+    memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != 0x434f494c53543031ULL || hd.N != (long long)N || hd.W != (long long)W || hd.G != (long long)G)
+        return fail(c, COIL_ERR_INVALID, "state does not belong to a coil of this shape");
+    cudaSetDevice(c->device);
+    const unsigned char* p = (const unsigned char*)buf + sizeof(hd);
+    CK(cudaMemcpy(h.I, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
+    CK(cudaMemcpy(h.Phi, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
+    CK(cudaMemcpy(h.x, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
+    if (G) { CK(cudaMemcpy(h.uT, p, G * 8, cudaMemcpyHostToDevice), "load"); p += G * 8; }
+    CK(cudaMemcpy(h.first_jump, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
+    CK(cudaMemcpy(h.first_quench, p, W * 8, cudaMemcpyHostToDevice), "load");
+    Scalars sc;
+    CK(cudaMemcpy(&sc, h.sc, sizeof(sc), cudaMemcpyDeviceToHost), "load");
+    sc.t = hd.t;
+    sc.step = hd.steps;
+    CK(cudaMemcpy(h.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice), "load");
+    c->t = hd.t;
+    c->steps = hd.steps;
+    return COIL_OK;
+}
+
+coil_status coil_info(const coil_t* c, coil_info_t* info) {
+    if (!c || !info) return COIL_ERR_INVALID;
+    info->n_elem = c->h.N;
+    info->n_blocks = c->h.W;
+    info->block = c->h.B;
+    info->grid_r = c->h.Gr;
+    info->grid_z = c->h.Gz;
+    info->precision = c->h.precision;
+    info->operator_bytes = c->op_bytes;
+    info->device_bytes = c->bytes;
+    info->steps = c->steps;
+    info->t = c->t;
+    info->setup_ms = c->setup_ms;
+    info->kernel_launches = c->launches;
+    info->operator_launches = c->op_launches;
+    info->operator_ms = c->op_ms;
+    info->pcg_iterations = c->pcg_iters;
+    info->descriptor_bytes = sizeof(CoilDev);
+    return COIL_OK;
+}
+
+coil_status coil_reset_counters(coil_t* c) {
+    if (!c) return COIL_ERR_INVALID;
+    c->launches = c->op_launches = c->pcg_iters = 0;
+    c->op_ms = 0.0;
+    return COIL_OK;
+}
+
+const char* coil_last_error(const coil_t* c) {
+    if (!c) return kNoHandle;
+    return c->err.c_str();
+}
+
+void coil_destroy(coil_t* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocs) cudaFree(p);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->d) cudaFree(c->d);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Device-side descriptor of one coil and small helpers shared by the kernels.
+//
+// Every per-step kernel receives an array of CoilDev descriptors and picks its
+// coil from blockIdx.y, so one launch can serve a batch of coils of uneven
+// size (CTAs beyond a coil's extent return at once).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace cq {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4.0e-7 * kPi;
+constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one warp
+
+enum Prec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_BF16 = 2 };
+
+enum Status { ST_OK = 0, ST_NOT_CONVERGED = 4, ST_NONFINITE = 5 };
+
+// Per-coil scalars that live on the device (written by kernels, read back by
+// the host only between launches).
+struct Scalars {
+    double t;            // simulated time at the start of the current step
+    long long step;      // completed steps
+    double It1, Ba0, Ba1, dBa;
+    double scale2;       // preconditioned norm^2 of the step's right-hand side
+    double rz, dq, alpha, beta;
+    int iter, done, status, nonpd;
+    double last_resid;
+};
+
+struct CoilDev {
+    // sizes
+    int N, W, B, n_types;
+    int has_grid, Gr, Gz;
+    int thermal, jc_model, precision;
+    long long ld;                 // leading dimension (elements) of the far operator
+    // element data (element order)
+    const double *r, *area, *jc_factor, *strain;
+    const int *mat;               // 1 filament, 0 Cu
+    const int *elem_grid;         // i_z * Gr + i_r
+    const int *grid_elem;         // inverse map
+    const int *block_type;        // near-block type per block
+    const int *constrained;       // 1 if the block is a transport turn
+    const double *near;           // n_types x B x B, FP64 intra-wire blocks of M
+    const void *Mfar;             // N x ld far operator in `precision`
+    // stencil: per grid column (resp. row) the first node and three weights
+    const int *sr_j0, *sz_j0;
+    const double *sr_w, *sz_w;
+    // thermal grid: face conductances, capacity, Thomas factors of (I - dt/2 A)
+    const double *Kr, *Kz;
+    const int *nborder;           // border faces per grid cell
+    double Ccell, helem;
+    const double *thr_lo, *thr_inv, *thr_cp;
+    const double *thz_lo, *thz_inv, *thz_cp;
+    // material scalars
+    double E0, nexp, Jc0, Tc, Bc2_0, B_reg, C_eps, p_eps, rho_n, rho_m, c0, h0, T_ref, T_bath;
+    // drive of the current coil_step call
+    double dt, ramp, Imax, Ba_rate, Ba_max;
+    int Ba_wf;
+    int maxit;
+    double rtol2;
+    // state and work vectors (element order unless noted)
+    double *I, *Phi, *x, *res, *zv, *dv, *qv, *R, *G;
+    float *pf;                    // FP32 copy of the operator input (ld long)
+    double *uT, *ustar, *src, *qgrid;   // grid order [Gz][Gr]
+    double *L, *y1, *sigma, *cw, *uw;   // per block
+    double *parts;                // 8 x W per-block partials (see step.cu)
+    double *partT;                // per grid column partial of T_max
+    long long *first_jump, *first_quench;
+    double *diag;                 // ring [cap][10]
+    long long diag_cap;
+    Scalars *sc;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Transport current and applied field of the drive at time t.
+__device__ __forceinline__ double drive_current(const CoilDev& c, double t) {
+    return fmin(c.ramp * t, c.Imax);
+}
+
+__device__ __forceinline__ double drive_field(const CoilDev& c, double t) {
+    if (c.Ba_wf == 0 || c.Ba_rate == 0.0) return 0.0;
+    if (c.Ba_wf == 1) return fmin(c.Ba_rate * t, c.Ba_max);
+    double period = 4.0 * c.Ba_max / c.Ba_rate;
+    double tau = t - period * floor(t / period);
+    if (tau < 0.25 * period) return c.Ba_rate * tau;
+    if (tau < 0.75 * period) return c.Ba_max - c.Ba_rate * (tau - 0.25 * period);
+    return -c.Ba_max + c.Ba_rate * (tau - 0.75 * period);
+}
+
+}  // namespace cq

@@ -1,0 +1,617 @@
+// Per-step kernels of the coupled electromagnetic-thermal update.
+//
+// One step (linearly-implicit Euler of the loop circuit equations, Numerical
+// Algorithm section; heat equation by ADI, Methods):
+//   k_pointwise   field from the loop flux (3-point stencil), Jc(B,T,eps),
+//                 E-J law, Joule source, right-hand side R, diagonal G,
+//                 per-wire constraint right-hand side c_w, detectors
+//   k_factor      per wire: Cholesky of A_w = M_ww + dt G_w, y_w = A_w^-1 1,
+//                 warm start made feasible, norm of the right-hand side
+//   projected PCG (operator apply = dense far GEMV + k_near; k_init,
+//                 k_update, k_direction, k_reduce)
+//   k_finalize    loop voltages u_w, I += dt Idot, flux += dt M Idot
+//   k_adi_r/z     Peaceman-Rachford half steps in u = T^4
+//   k_step_end    diagnostic record, time advance
+#include "common.cuh"
+
+namespace cq {
+
+// ---------------------------------------------------------------- pointwise
+
+__device__ __forceinline__ double phi_total(const CoilDev& c, int g, double Ba) {
+    int e = c.grid_elem[g];
+    double r = c.r[e];
+    return c.Phi[e] + kPi * r * r * Ba;
+}
+
+// B_r, B_z at element e from the stencil of the total loop flux.
+__device__ void field_at(const CoilDev& c, int e, double Ba, double* Br, double* Bz) {
+    int g = c.elem_grid[e];
+    int iz = g / c.Gr, ir = g - iz * c.Gr;
+    double dr = 0.0, dz = 0.0;
+    int j0 = c.sr_j0[ir];
+    for (int k = 0; k < 3; ++k) {
+        double wk = c.sr_w[3 * ir + k];
+        if (wk != 0.0) dr += wk * phi_total(c, iz * c.Gr + j0 + k, Ba);
+    }
+    j0 = c.sz_j0[iz];
+    for (int k = 0; k < 3; ++k) {
+        double wk = c.sz_w[3 * iz + k];
+        if (wk != 0.0) dz += wk * phi_total(c, (j0 + k) * c.Gr + ir, Ba);
+    }
+    double r = c.r[e];
+    *Bz = dr / (2.0 * kPi * r);
+    *Br = -dz / (2.0 * kPi * r);
+}
+
+__device__ double critical_current(const CoilDev& c, double Bm, double T, double eps, double f) {
+    if (c.jc_model == 1) return f * c.Jc0;
+    double tr = T / c.Tc;
+    double Bc2 = c.Bc2_0 * (1.0 - tr * tr);
+    if (!(T < c.Tc && Bm < Bc2)) return 0.0;
+    double strain = fmax(0.0, 1.0 - c.C_eps * pow(fabs(eps), c.p_eps));
+    double bfac = 1.0 - Bm / Bc2;
+    return f * c.Jc0 * pow(1.0 - tr, 1.5) * (bfac * bfac) / sqrt(Bm + c.B_reg) * strain;
+}
+
+// rho/rho_n, (dE/dJ)/rho_n and |J|/Jc of the parallel power-law / normal law.
+__device__ void ej_law(const CoilDev& c, int fil, double J, double Jc, double* frac, double* dfac,
+                       double* jrat) {
+    if (!fil) { *frac = 1.0; *dfac = 1.0; *jrat = 0.0; return; }
+    double aJ = fabs(J);
+    if (Jc <= 0.0) { *frac = 1.0; *dfac = 1.0; *jrat = aJ > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0; return; }
+    *jrat = aJ / Jc;
+    if (aJ == 0.0) { *frac = 0.0; *dfac = 0.0; return; }
+    double n = c.nexp;
+    double ell = log(c.E0 / (Jc * c.rho_n)) + (n - 1.0) * log(aJ / Jc);
+    if (ell > 0.0) {
+        double t = exp(-ell);
+        double opt = 1.0 + t;
+        *frac = 1.0 / opt;
+        *dfac = (1.0 + n * t) / (opt * opt);
+    } else {
+        double s = exp(ell);
+        double ops = 1.0 + s;
+        *frac = s / ops;
+        *dfac = s * (s + n) / (ops * ops);
+    }
+}
+
+// One warp per block (wire).  Partials: P[0] Joule power, P[1] max |J|/Jc,
+// P[2] mean rho/rho_n of filament elements.
+__global__ void k_pointwise(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    double* parts = c.parts;
+    int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (w >= c.W) return;
+    Scalars* sc = c.sc;
+    double t0 = sc->t, dt = c.dt, t1 = t0 + dt;
+    double It1 = drive_current(c, t1);
+    double Ba0 = drive_field(c, t0), Ba1 = drive_field(c, t1);
+    double dBa = (Ba1 - Ba0) / dt;
+    if (w == 0 && lane == 0) {
+        sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
+        sc->nonpd = 0;                         // k_factor of this step sets it again if needed
+    }
+    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0;
+    for (int k = lane; k < c.B; k += 32) {
+        int e = w * c.B + k;
+        double r = c.r[e], a = c.area[e];
+        double Br = 0.0, Bz = 0.0, T = c.T_bath;
+        if (c.has_grid) {
+            field_at(c, e, Ba0, &Br, &Bz);
+            T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
+        }
+        double Bm = sqrt(Br * Br + Bz * Bz);
+        int fil = c.mat[e];
+        double Jc = fil ? critical_current(c, Bm, T, c.strain[e], c.jc_factor[e]) : 0.0;
+        double I = c.I[e];
+        double J = I / a;
+        double frac, dfac, jrat;
+        ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
+        double rho = c.rho_n * frac;
+        double E = rho * J;
+        double q = E * J;
+        c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
+        c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
+        if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
+        sumI += I;
+        pj += q * 2.0 * kPi * r * a;
+        if (fil) { jr = fmax(jr, jrat); rhof += frac; nfil += 1.0; }
+    }
+    sumI = warp_sum(sumI);
+    pj = warp_sum(pj);
+    jr = warp_max(jr);
+    rhof = warp_sum(rhof);
+    nfil = warp_sum(nfil);
+    if (lane == 0) {
+        c.cw[w] = c.constrained[w] ? (It1 - sumI) / dt : 0.0;
+        double mean_rho = nfil > 0.0 ? rhof / nfil : 0.0;
+        parts[0 * (size_t)c.W + w] = pj;
+        parts[1 * (size_t)c.W + w] = jr;
+        parts[2 * (size_t)c.W + w] = mean_rho;
+        long long st = sc->step;
+        if (c.first_jump[w] < 0 && jr > 1.0) c.first_jump[w] = st;
+        if (c.first_quench[w] < 0 && mean_rho > 0.95) c.first_quench[w] = st;
+    }
+}
+
+// --------------------------------------------------- per-wire block algebra
+
+// Solve L L^T v = v in place (L lower, B x B row-major in shared memory).
+__device__ void chol_solve_warp(const double* L, double* v, int B, int lane) {
+    for (int k = 0; k < B; ++k) {
+        if (lane == 0) v[k] /= L[k * B + k];
+        __syncwarp();
+        double vk = v[k];
+        for (int i = k + 1 + lane; i < B; i += 32) v[i] -= L[i * B + k] * vk;
+        __syncwarp();
+    }
+    for (int k = B - 1; k >= 0; --k) {
+        if (lane == 0) v[k] /= L[k * B + k];
+        __syncwarp();
+        double vk = v[k];
+        for (int i = lane; i < k; i += 32) v[i] -= L[k * B + i] * vk;
+        __syncwarp();
+    }
+}
+
+__device__ double warp_block_sum(const double* v, int B, int lane) {
+    double s = 0.0;
+    for (int k = lane; k < B; k += 32) s += v[k];
+    return warp_sum(s);
+}
+
+// Projected preconditioner of block w: v <- A_w^-1 v, then remove the
+// component that would change the wire's total current (constrained wires).
+__device__ void project_precond(const CoilDev& c, int w, const double* L, const double* y, double* v,
+                                int lane) {
+    int B = c.B;
+    chol_solve_warp(L, v, B, lane);
+    if (c.constrained[w]) {
+        double s = warp_block_sum(v, B, lane);
+        double f = s / c.sigma[w];
+        for (int k = lane; k < B; k += 32) v[k] -= y[k] * f;
+        __syncwarp();
+    }
+}
+
+// One warp per CTA, one CTA per block.  Shared: A (B*B), v (B), y (B).
+__global__ void k_factor(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    double* parts = c.parts;
+    int w = blockIdx.x;
+    if (w >= c.W) return;
+    extern __shared__ double sm[];
+    int B = c.B, lane = threadIdx.x;
+    double* A = sm;
+    double* v = sm + B * B;
+    double* y = v + B;
+    const double* nb = c.near + (size_t)c.block_type[w] * B * B;
+    for (int i = lane; i < B * B; i += 32) A[i] = nb[i];
+    __syncwarp();
+    for (int k = lane; k < B; k += 32) A[k * B + k] += c.dt * c.G[w * B + k];
+    __syncwarp();
+    int bad = 0;
+    for (int k = 0; k < B; ++k) {
+        double piv = A[k * B + k];
+        if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
+        double lkk = sqrt(piv);
+        __syncwarp();
+        if (lane == 0) A[k * B + k] = lkk;
+        for (int i = k + 1 + lane; i < B; i += 32) A[i * B + k] /= lkk;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < B; i += 32) {
+            double lik = A[i * B + k];
+            for (int j = k + 1; j <= i; ++j) A[i * B + j] -= lik * A[j * B + k];
+        }
+        __syncwarp();
+    }
+    if (bad && lane == 0) atomicExch(&c.sc->nonpd, 1);
+    double* Lg = c.L + (size_t)w * B * B;
+    for (int i = lane; i < B * B; i += 32) Lg[i] = A[i];
+    // y = A_w^-1 1, sigma = 1^T y
+    for (int k = lane; k < B; k += 32) y[k] = 1.0;
+    __syncwarp();
+    chol_solve_warp(A, y, B, lane);
+    double sig = warp_block_sum(y, B, lane);
+    for (int k = lane; k < B; k += 32) c.y1[w * B + k] = y[k];
+    if (lane == 0) c.sigma[w] = sig;
+    __syncwarp();
+    // preconditioned norm^2 of the right-hand side: R^T Pproj(R) + c_w^2 / sigma
+    for (int k = lane; k < B; k += 32) v[k] = c.R[w * B + k];
+    __syncwarp();
+    chol_solve_warp(A, v, B, lane);
+    double cw = c.cw[w];
+    int con = c.constrained[w];
+    if (con) {
+        double s = warp_block_sum(v, B, lane);
+        double f = s / sig;
+        for (int k = lane; k < B; k += 32) v[k] -= y[k] * f;
+        __syncwarp();
+    }
+    double rn = 0.0;
+    for (int k = lane; k < B; k += 32) rn += c.R[w * B + k] * v[k];
+    rn = warp_sum(rn);
+    // warm start from the previous step's Idot, moved onto this step's constraint
+    double sx = 0.0;
+    for (int k = lane; k < B; k += 32) sx += c.x[w * B + k];
+    sx = warp_sum(sx);
+    double corr = con ? (cw - sx) / sig : 0.0;
+    for (int k = lane; k < B; k += 32) {
+        int e = w * B + k;
+        double xe = c.x[e] + corr * y[k];
+        c.x[e] = xe;
+        c.pf[e] = (float)xe;
+    }
+    if (lane == 0) parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw / sig : 0.0);
+}
+
+// q_w += (M_ww + dt G_w) p_w for every block; optional partial p^T q.
+__global__ void k_near(const CoilDev* __restrict__ cds, int which) {
+    const CoilDev& c = cds[blockIdx.y];
+    double* parts = c.parts;
+    if (c.sc->done) return;
+    int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (w >= c.W) return;
+    const double* p = which == 0 ? c.x : c.dv;
+    int B = c.B;
+    const double* nb = c.near + (size_t)c.block_type[w] * B * B;
+    const double* pw = p + (size_t)w * B;
+    double dot = 0.0;
+    for (int i = lane; i < B; i += 32) {
+        double acc = 0.0;
+        for (int j = 0; j < B; ++j) acc += nb[i * B + j] * pw[j];
+        int e = w * B + i;
+        acc += c.dt * c.G[e] * pw[i];
+        double qe = c.qv[e] + acc;
+        c.qv[e] = qe;
+        dot += pw[i] * qe;
+    }
+    dot = warp_sum(dot);
+    if (which == 1 && lane == 0) parts[4 * (size_t)c.W + w] = dot;
+}
+
+// Residual update of a constrained block (residual held in v): remove the
+// multiplier component u 1 (u = y^T r / sigma, the loop-voltage estimate) and
+// accumulate it in uw[w].  The projected preconditioner ignores that
+// component in exact arithmetic; removing it keeps r small so that r^T z
+// does not drown in the rounding of the large loop-voltage term
+// (Gould, Hribar and Nocedal's residual update for constraint preconditioners).
+__device__ void project_residual(const CoilDev& c, int w, const double* y, double* v, int lane, bool first) {
+    if (!c.constrained[w]) return;
+    int B = c.B;
+    double s = 0.0;
+    for (int k = lane; k < B; k += 32) s += y[k] * v[k];
+    s = warp_sum(s);
+    double u = s / c.sigma[w];
+    for (int k = lane; k < B; k += 32) v[k] -= u;
+    __syncwarp();
+    if (lane == 0) c.uw[w] = first ? u : c.uw[w] + u;
+}
+
+// After q = A x0: r = q + R (projected), z = Pproj(r), d = -z; partial r^T z.
+__global__ void k_init(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    double* parts = c.parts;
+    if (c.sc->done) return;
+    int w = blockIdx.x;
+    if (w >= c.W) return;
+    extern __shared__ double sm[];
+    int B = c.B, lane = threadIdx.x;
+    double* L = sm;
+    double* v = sm + B * B;
+    double* y = v + B;
+    const double* Lg = c.L + (size_t)w * B * B;
+    for (int i = lane; i < B * B; i += 32) L[i] = Lg[i];
+    for (int k = lane; k < B; k += 32) {
+        int e = w * B + k;
+        v[k] = c.qv[e] + c.R[e];
+        y[k] = c.y1[e];
+    }
+    __syncwarp();
+    if (lane == 0) c.uw[w] = 0.0;
+    project_residual(c, w, y, v, lane, true);
+    for (int k = lane; k < B; k += 32) c.res[w * B + k] = v[k];
+    __syncwarp();
+    project_precond(c, w, L, y, v, lane);
+    double rz = 0.0;
+    for (int k = lane; k < B; k += 32) {
+        int e = w * B + k;
+        c.zv[e] = v[k];
+        c.dv[e] = -v[k];
+        c.pf[e] = (float)(-v[k]);
+        rz += c.res[e] * v[k];
+    }
+    rz = warp_sum(rz);
+    if (lane == 0) parts[4 * (size_t)c.W + w] = rz;
+}
+
+// x += alpha d, r += alpha q (projected), z = Pproj(r); partial r^T z.
+__global__ void k_update(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    double* parts = c.parts;
+    if (c.sc->done) return;
+    int w = blockIdx.x;
+    if (w >= c.W) return;
+    extern __shared__ double sm[];
+    int B = c.B, lane = threadIdx.x;
+    double* L = sm;
+    double* v = sm + B * B;
+    double* y = v + B;
+    double alpha = c.sc->alpha;
+    const double* Lg = c.L + (size_t)w * B * B;
+    for (int i = lane; i < B * B; i += 32) L[i] = Lg[i];
+    for (int k = lane; k < B; k += 32) {
+        int e = w * B + k;
+        c.x[e] += alpha * c.dv[e];
+        v[k] = c.res[e] + alpha * c.qv[e];
+        y[k] = c.y1[e];
+    }
+    __syncwarp();
+    project_residual(c, w, y, v, lane, false);
+    for (int k = lane; k < B; k += 32) c.res[w * B + k] = v[k];
+    __syncwarp();
+    project_precond(c, w, L, y, v, lane);
+    double rz = 0.0;
+    for (int k = lane; k < B; k += 32) {
+        int e = w * B + k;
+        c.zv[e] = v[k];
+        rz += c.res[e] * v[k];
+    }
+    rz = warp_sum(rz);
+    if (lane == 0) parts[4 * (size_t)c.W + w] = rz;
+}
+
+// d = -z + beta d (and its FP32 copy for the mixed-precision operator).
+__global__ void k_direction(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->done) return;
+    double beta = c.sc->beta;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c.N; e += gridDim.x * blockDim.x) {
+        double d = -c.zv[e] + beta * c.dv[e];
+        c.dv[e] = d;
+        c.pf[e] = (float)d;
+    }
+}
+
+enum ReduceMode { RED_SCALE = 0, RED_INIT = 1, RED_ALPHA = 2, RED_BETA = 3 };
+
+__device__ double block_reduce_sum(double v, double* sh) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+__device__ double block_reduce_max(double v, double* sh) {
+    v = warp_max(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : -1.0e308;
+    if (wid == 0) v = warp_max(v);
+    __syncthreads();
+    return v;
+}
+
+// One CTA per coil: deterministic sum of a per-block partial array and the
+// scalar update that follows it.
+__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode) {
+    const CoilDev& c = cds[blockIdx.x];
+    Scalars* sc = c.sc;
+    if ((mode == RED_ALPHA || mode == RED_BETA || mode == RED_INIT) && sc->done) return;
+    __shared__ double sh[32];
+    const double* parts = c.parts;
+    const double* a = parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < c.W; i += blockDim.x) s += a[i];
+    s = block_reduce_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    if (mode == RED_SCALE) {
+        sc->scale2 = s;
+        sc->done = 0;
+        sc->iter = 0;
+        sc->status = ST_OK;
+        if (sc->nonpd) { sc->status = ST_NONFINITE; sc->done = 1; }
+        if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
+    } else if (mode == RED_INIT) {
+        sc->rz = s;
+        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(s, 0.0) / sc->scale2) : 0.0;
+        if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
+        else if (s <= c.rtol2 * sc->scale2) sc->done = 1;
+    } else if (mode == RED_ALPHA) {
+        sc->dq = s;
+        if (!(s > 0.0)) {                      // A is SPD on the feasible subspace
+            sc->status = (s == s) ? ST_NONFINITE : ST_NONFINITE;
+            sc->done = 1;
+            return;
+        }
+        sc->alpha = sc->rz / s;
+    } else {
+        double rz_new = s;
+        sc->iter += 1;
+        sc->beta = rz_new / sc->rz;
+        sc->rz = rz_new;
+        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(rz_new, 0.0) / sc->scale2) : 0.0;
+        if (!(rz_new == rz_new)) { sc->status = ST_NONFINITE; sc->done = 1; }
+        else if (rz_new <= c.rtol2 * sc->scale2) sc->done = 1;
+        else if (sc->iter >= c.maxit) { sc->status = ST_NOT_CONVERGED; sc->done = 1; }
+    }
+}
+
+// u_w, I += dt x, flux += dt M x with M x = (r + U_w) - R - dt G x (r is the
+// projected residual, U_w the loop voltage removed from it); partials V
+// (parts[5]) and m (parts[6]).
+__global__ void k_finalize(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    double* parts = c.parts;
+    int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (w >= c.W) return;
+    int B = c.B;
+    double dt = c.dt;
+    int con = c.constrained[w];
+    double U = con ? c.uw[w] : 0.0;
+    double yr = 0.0, mom = 0.0;
+    for (int k = lane; k < B; k += 32) {
+        int e = w * B + k;
+        double xe = c.x[e];
+        yr += c.y1[e] * c.res[e];
+        double In = c.I[e] + dt * xe;
+        c.I[e] = In;
+        c.Phi[e] += dt * ((c.res[e] + U) - c.R[e] - dt * c.G[e] * xe);
+        double r = c.r[e];
+        mom += kPi * r * r * In;
+    }
+    yr = warp_sum(yr);
+    mom = warp_sum(mom);
+    if (lane == 0) {
+        double u = con ? U + yr / c.sigma[w] : 0.0;
+        c.uw[w] = u;
+        parts[5 * (size_t)c.W + w] = u;
+        parts[6 * (size_t)c.W + w] = mom;
+    }
+}
+
+// ------------------------------------------------------------------ thermal
+
+// Source s = 4/(rho_m c0) (q - border loss / h^2) of cell g with state u.
+__device__ __forceinline__ double thermal_source(const CoilDev& c, int g, double u) {
+    double T = sqrt(sqrt(u));
+    double tr = T / c.T_ref;
+    double loss = c.nborder[g] * c.helem * c.h0 * (tr * tr * tr) * (T - c.T_bath);
+    return 4.0 / (c.rho_m * c.c0) * (c.qgrid[g] - loss / (c.helem * c.helem));
+}
+
+// Tridiagonal solve of one line held in shared memory (lane 0 runs the sweep).
+__device__ void thomas_line(double* v, int G, const double* lo, const double* inv, const double* cp) {
+    v[0] = v[0] * inv[0];
+    for (int i = 1; i < G; ++i) v[i] = (v[i] - lo[i] * v[i - 1]) * inv[i];
+    for (int i = G - 2; i >= 0; --i) v[i] -= cp[i] * v[i + 1];
+}
+
+// r-lines: u* = (I - dt/2 A_r)^-1 [(I + dt/2 A_z) u + dt/2 s].  One warp per grid row.
+__global__ void k_adi_r(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    int j = blockIdx.x;
+    if (j >= c.Gz) return;
+    extern __shared__ double sm[];
+    int Gr = c.Gr, Gz = c.Gz, lane = threadIdx.x;
+    double hd = 0.5 * c.dt;
+    double invC = 1.0 / c.Ccell;
+    for (int i = lane; i < Gr; i += 32) {
+        int g = j * Gr + i;
+        double u = c.uT[g];
+        double s = thermal_source(c, g, u);
+        c.src[g] = s;
+        double az = 0.0;
+        if (j > 0) az += c.Kz[j - 1] * (c.uT[g - Gr] - u);
+        if (j < Gz - 1) az += c.Kz[j] * (c.uT[g + Gr] - u);
+        sm[i] = u + hd * (az * invC) + hd * s;
+    }
+    __syncwarp();
+    if (lane == 0) thomas_line(sm, Gr, c.thr_lo, c.thr_inv, c.thr_cp);
+    __syncwarp();
+    for (int i = lane; i < Gr; i += 32) c.ustar[j * Gr + i] = sm[i];
+}
+
+// z-lines: u' = (I - dt/2 A_z)^-1 [(I + dt/2 A_r) u* + dt/2 s].  One warp per column.
+__global__ void k_adi_z(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    int i = blockIdx.x;
+    if (i >= c.Gr) return;
+    extern __shared__ double sm[];
+    int Gr = c.Gr, Gz = c.Gz, lane = threadIdx.x;
+    double hd = 0.5 * c.dt;
+    double invC = 1.0 / c.Ccell;
+    for (int j = lane; j < Gz; j += 32) {
+        int g = j * Gr + i;
+        double us = c.ustar[g];
+        double ar = 0.0;
+        if (i > 0) ar += c.Kr[i - 1] * (c.ustar[g - 1] - us);
+        if (i < Gr - 1) ar += c.Kr[i] * (c.ustar[g + 1] - us);
+        sm[j] = us + hd * (ar * invC) + hd * c.src[g];
+    }
+    __syncwarp();
+    if (lane == 0) thomas_line(sm, Gz, c.thz_lo, c.thz_inv, c.thz_cp);
+    __syncwarp();
+    double um = 0.0;
+    for (int j = lane; j < Gz; j += 32) {
+        double u = sm[j];
+        c.uT[j * Gr + i] = u;
+        um = fmax(um, u);
+    }
+    um = warp_max(um);
+    if (lane == 0) c.partT[i] = um;
+}
+
+// One CTA per coil: the step's diagnostic record, then t += dt.
+__global__ void k_step_end(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.x];
+    __shared__ double sh[32];
+    const double* parts = c.parts;
+    size_t W = c.W;
+    double pj = 0.0, V = 0.0, m = 0.0, jr = 0.0, rh = 0.0;
+    for (int w = threadIdx.x; w < c.W; w += blockDim.x) {
+        pj += parts[0 * W + w];
+        jr = fmax(jr, parts[1 * W + w]);
+        rh = fmax(rh, parts[2 * W + w]);
+        V += parts[5 * W + w];
+        m += parts[6 * W + w];
+    }
+    double um = 0.0;
+    if (c.has_grid) {
+        if (c.thermal) {
+            for (int i = threadIdx.x; i < c.Gr; i += blockDim.x) um = fmax(um, c.partT[i]);
+        } else {
+            for (int g = threadIdx.x; g < c.Gr * c.Gz; g += blockDim.x) um = fmax(um, c.uT[g]);
+        }
+    }
+    pj = block_reduce_sum(pj, sh);
+    V = block_reduce_sum(V, sh);
+    m = block_reduce_sum(m, sh);
+    jr = block_reduce_max(jr, sh);
+    rh = block_reduce_max(rh, sh);
+    um = block_reduce_max(um, sh);
+    if (threadIdx.x != 0) return;
+    Scalars* sc = c.sc;
+    double t1 = sc->t + c.dt;
+    double* rec = c.diag + (size_t)(sc->step % c.diag_cap) * 10;
+    rec[0] = t1;
+    rec[1] = sc->It1;
+    rec[2] = V;
+    rec[3] = m;
+    rec[4] = pj;
+    rec[5] = c.has_grid ? sqrt(sqrt(um)) : c.T_bath;
+    rec[6] = jr;
+    rec[7] = rh;
+    rec[8] = (double)sc->iter;
+    rec[9] = sc->last_resid;
+    sc->t = t1;
+    sc->step += 1;
+}
+
+// J, B_r, B_z, T of the current state into element-order buffers.
+__global__ void k_read(const CoilDev* __restrict__ cds, double Ba, double* J, double* Br, double* Bz,
+                       double* T) {
+    const CoilDev& c = cds[blockIdx.y];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c.N; e += gridDim.x * blockDim.x) {
+        if (J) J[e] = c.I[e] / c.area[e];
+        double br = 0.0, bz = 0.0;
+        if (c.has_grid && (Br || Bz)) field_at(c, e, Ba, &br, &bz);
+        if (Br) Br[e] = br;
+        if (Bz) Bz[e] = bz;
+        if (T) T[e] = c.has_grid ? sqrt(sqrt(c.uT[c.elem_grid[e]])) : c.T_bath;
+    }
+}
+
+}  // namespace cq

@@ -94,6 +94,12 @@ def mid_coil():
                     I_max=600.0, steps=20000)
 
 
+def profile_coil():
+    """24 layers x 52 turns, 4 x 4 elements: 19,968 elements (operator > L2)."""
+    return solenoid("profile-1248turn-19968el", 24, 52, 4, SEED_BASE + 6, ramp_rate=2.0,
+                    I_max=800.0, steps=100)
+
+
 def adjoint_coil():
     """12 layers x 24 turns, 4 x 4 elements: 4,608 elements, field loop."""
     w = solenoid("adjoint-288turn-4608el", 12, 24, 4, SEED_BASE + 4, ramp_rate=0.0,
