@@ -168,6 +168,16 @@ coil_status coil_create(const coil_geometry *geom, const coil_material *mat,
  * at the end of the last completed step (see coil_info.steps). */
 coil_status coil_step(coil_t *c, long n_steps, const coil_drive *drive);
 
+/* Advance n_steps of n_coils coils together (batched sweep of coil variants
+ * and ramp rates of uneven size): every kernel of the step is launched once
+ * for the whole batch, one grid row (blockIdx.y) per coil, each coil with
+ * its own drive drives[i] and its own convergence test.  All coils must live
+ * on the same device and use the same operator precision; the launches go to
+ * the first coil's stream.  A coil whose solve fails stops advancing; the
+ * call returns the first failure after the others completed the step. */
+coil_status coil_batch_step(coil_t *const *coils, int n_coils, long n_steps,
+                            const coil_drive *drives);
+
 /* Copy the current state to host buffers of N doubles (NULL = skip): current
  * density J [A/m^2], B_r, B_z [T] from the stencil of the loop flux, T [K];
  * and the moment sum(pi r^2 I) [A m^2].  `Ba` is the applied field at the

@@ -68,6 +68,7 @@ def load_library(path=LIB_PATH):
     sig = {
         "coil_create": ([C.POINTER(Geometry), C.POINTER(Material), C.POINTER(Options), C.POINTER(P)], C.c_int),
         "coil_step": ([P, C.c_long, C.POINTER(Drive)], C.c_int),
+        "coil_batch_step": ([C.POINTER(P), C.c_int, C.c_long, C.POINTER(Drive)], C.c_int),
         "coil_read": ([P, C.POINTER(Drive), _dp, _dp, _dp, _dp, _dp], C.c_int),
         "coil_read_device": ([P, C.POINTER(Drive), P, P, P, P], C.c_int),
         "coil_read_diag": ([P, C.c_long, C.c_long, _dp], C.c_int),
@@ -270,6 +271,17 @@ class Coil:
         inf = Info()
         self._check(self._lib.coil_info(self._h, C.byref(inf)))
         return inf
+
+
+def batch_step(coils, n_steps, drives):
+    """coil_batch_step over several Coil objects (one drive dict per coil)."""
+    n = len(coils)
+    handles = (C.c_void_p * n)(*[c._h.value for c in coils])
+    drv = (Drive * n)(*[make_drive(d) for d in drives])
+    status = lib().coil_batch_step(handles, n, int(n_steps), drv)
+    if status != OK:
+        msgs = "; ".join(lib().coil_last_error(c._h).decode() for c in coils[:1])
+        raise CoilError(status, msgs)
 
 
 def header_symbols(path=HEADER):

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/coil.h"
@@ -37,6 +38,7 @@ __global__ void k_read(const CoilDev* __restrict__ cds, double Ba, double* J, do
                        double* T);
 __global__ void k_moment(const CoilDev* __restrict__ cds, double* out);
 __global__ void k_to_float(const double* x, float* f, int n);
+__global__ void k_gather_status(const CoilDev* __restrict__ cds, int n, int* out);
 }  // namespace cq
 
 using namespace cq;
@@ -511,9 +513,37 @@ coil_status read_scalars(coil_t* c) {
 
 size_t block_smem(const CoilDev& h) { return ((size_t)h.B * h.B + 2 * (size_t)h.B) * sizeof(double); }
 
-// Dense-operator launch, bracketed by an event pair when profiling.
-coil_status gemv(coil_t* c, int which) {
+// Launch geometry of one step for one coil or a batch (grid row y = coil).
+struct Launch {
+    const CoilDev* d = nullptr;
+    int n = 1;
+    int prec = 0;
+    int maxW = 0, maxN = 0, maxGr = 0, maxGz = 0;
+    bool thermal = false;
+    size_t smem = 0;
+    cudaStream_t s = nullptr;
+    int n_sm = 148;
+};
+
+Launch single_launch(coil_t* c) {
+    Launch L;
     const CoilDev& h = c->h;
+    L.d = c->d;
+    L.n = 1;
+    L.prec = h.precision;
+    L.maxW = h.W;
+    L.maxN = h.N;
+    L.maxGr = h.Gr;
+    L.maxGz = h.Gz;
+    L.thermal = h.thermal != 0;
+    L.smem = block_smem(h);
+    L.s = c->stream;
+    L.n_sm = c->n_sm;
+    return L;
+}
+
+// Dense-operator launch, bracketed by an event pair when profiling.
+coil_status gemv(coil_t* c, const Launch& L, int which) {
     if (c->profile) {
         if (c->ev_used * 2 + 2 > c->ev_pool.size()) {
             for (int k = 0; k < 2; ++k) {
@@ -522,11 +552,11 @@ coil_status gemv(coil_t* c, int which) {
                 c->ev_pool.push_back(e);
             }
         }
-        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used], c->stream), "event");
+        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used], L.s), "event");
     }
-    CK(launch_gemv(c->d, 1, h.precision, h.N, which, c->n_sm, c->stream), "gemv");
+    CK(launch_gemv(L.d, L.n, L.prec, L.maxN, which, L.n_sm, L.s), "gemv");
     if (c->profile) {
-        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], c->stream), "event");
+        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], L.s), "event");
         c->ev_used += 1;
     }
     c->op_launches += 1;
@@ -543,41 +573,60 @@ void harvest_events(coil_t* c) {
     c->ev_used = 0;
 }
 
-coil_status one_iteration(coil_t* c) {
-    const CoilDev& h = c->h;
-    cudaStream_t s = c->stream;
-    unsigned wb = (unsigned)((h.W + 7) / 8);
-    TRY(gemv(c, 1));
+dim3 warp_grid(const Launch& L) { return dim3((unsigned)((L.maxW + 7) / 8), L.n); }
+
+// Pointwise, factorisation, right-hand-side norm, initial residual.
+coil_status step_prologue(coil_t* c, const Launch& L) {
+    k_pointwise<<<warp_grid(L), 256, 0, L.s>>>(L.d);
+    k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 0);
+    TRY(gemv(c, L, 0));
+    k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, 0);
+    k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 1);
+    c->launches += 6;
+    CK(cudaGetLastError(), "step launch");
+    return COIL_OK;
+}
+
+// One projected-PCG iteration (kernels of converged coils return at once).
+coil_status step_iteration(coil_t* c, const Launch& L) {
+    TRY(gemv(c, L, 1));
+    k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, 1);
+    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 2);
+    k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 3);
+    unsigned eb = (unsigned)((L.maxN + 255) / 256);
+    if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
+    k_direction<<<dim3(eb, L.n), 256, 0, L.s>>>(L.d);
     c->launches += 5;
-    k_near<<<wb, 256, 0, s>>>(c->d, 1);
-    k_reduce<<<1, 256, 0, s>>>(c->d, 2);
-    k_update<<<h.W, 32, block_smem(h), s>>>(c->d);
-    k_reduce<<<1, 256, 0, s>>>(c->d, 3);
-    unsigned eb = (unsigned)((h.N + 255) / 256);
-    if (eb > (unsigned)c->n_sm * 16) eb = c->n_sm * 16;
-    k_direction<<<eb, 256, 0, s>>>(c->d);
     CK(cudaGetLastError(), "iteration launch");
+    return COIL_OK;
+}
+
+// Current/flux update, heat step, diagnostics (coils whose solve failed skip it).
+coil_status step_epilogue(coil_t* c, const Launch& L) {
+    k_finalize<<<warp_grid(L), 256, 0, L.s>>>(L.d);
+    if (L.thermal) {
+        k_adi_r<<<dim3(L.maxGz, L.n), 32, L.maxGr * sizeof(double), L.s>>>(L.d);
+        k_adi_z<<<dim3(L.maxGr, L.n), 32, L.maxGz * sizeof(double), L.s>>>(L.d);
+        c->launches += 2;
+    }
+    k_step_end<<<L.n, 256, 0, L.s>>>(L.d);
+    c->launches += 2;
+    CK(cudaGetLastError(), "step end launch");
     return COIL_OK;
 }
 
 coil_status run_step(coil_t* c) {
     const CoilDev& h = c->h;
-    cudaStream_t s = c->stream;
-    unsigned wb = (unsigned)((h.W + 7) / 8);
-    k_pointwise<<<wb, 256, 0, s>>>(c->d);
-    k_factor<<<h.W, 32, block_smem(h), s>>>(c->d);
-    k_reduce<<<1, 256, 0, s>>>(c->d, 0);
-    TRY(gemv(c, 0));
-    k_near<<<wb, 256, 0, s>>>(c->d, 0);
-    k_init<<<h.W, 32, block_smem(h), s>>>(c->d);
-    k_reduce<<<1, 256, 0, s>>>(c->d, 1);
-    c->launches += 6;
-    CK(cudaGetLastError(), "step launch");
+    Launch L = single_launch(c);
+    TRY(step_prologue(c, L));
     // PCG: enqueue the expected number of iterations, then one at a time
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
-        for (int i = 0; i < chunk; ++i) TRY(one_iteration(c));
+        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
         total += chunk;
         TRY(read_scalars(c));
         if (c->pinned->done) break;
@@ -592,15 +641,7 @@ coil_status run_step(coil_t* c) {
     c->last_iters = c->pinned->iter > 0 ? c->pinned->iter : 1;
     c->pcg_iters += c->pinned->iter;
     harvest_events(c);
-    k_finalize<<<wb, 256, 0, s>>>(c->d);
-    if (h.thermal) {
-        k_adi_r<<<h.Gz, 32, h.Gr * sizeof(double), s>>>(c->d);
-        k_adi_z<<<h.Gr, 32, h.Gz * sizeof(double), s>>>(c->d);
-        c->launches += 2;
-    }
-    k_step_end<<<1, 256, 0, s>>>(c->d);
-    c->launches += 2;
-    CK(cudaGetLastError(), "step end launch");
+    TRY(step_epilogue(c, L));
     c->steps += 1;
     c->t += h.dt;
     return COIL_OK;
@@ -631,6 +672,17 @@ namespace cq {
 __global__ void k_to_float(const double* x, float* f, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) f[i] = (float)x[i];
+}
+
+// done, status, iter of every coil of a batch into one small array.
+__global__ void k_gather_status(const CoilDev* __restrict__ cds, int n, int* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const Scalars* sc = cds[i].sc;
+        out[3 * i] = sc->done;
+        out[3 * i + 1] = sc->status;
+        out[3 * i + 2] = sc->iter;
+    }
 }
 
 __global__ void k_moment(const CoilDev* __restrict__ cds, double* out) {
@@ -699,6 +751,93 @@ coil_status coil_step(coil_t* c, long n_steps, const coil_drive* drive) {
     for (long k = 0; k < n_steps; ++k) TRY(run_step(c));
     CK(cudaStreamSynchronize(c->stream), "coil_step");
     return COIL_OK;
+}
+
+coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coil_drive* drives) {
+    if (!coils || n < 1 || !drives || n_steps < 0) return COIL_ERR_INVALID;
+    coil_t* c = coils[0];
+    for (int i = 0; i < n; ++i) {
+        if (!coils[i]) return COIL_ERR_INVALID;
+        if (coils[i]->device != c->device || coils[i]->h.precision != c->h.precision)
+            return fail(c, COIL_ERR_INVALID, "batched coils must share device and precision");
+        for (int j = 0; j < i; ++j)
+            if (coils[j] == coils[i]) return fail(c, COIL_ERR_INVALID, "a coil appears twice in the batch");
+    }
+    cudaSetDevice(c->device);
+    Launch L;
+    L.n = n;
+    L.prec = c->h.precision;
+    L.s = c->stream;
+    L.n_sm = c->n_sm;
+    std::vector<CoilDev> hd(n);
+    for (int i = 0; i < n; ++i) {
+        coil_t* ci = coils[i];
+        TRY(set_drive(ci, &drives[i]));
+        CK(cudaStreamSynchronize(ci->stream), "batch descriptor");
+        hd[i] = ci->h;
+        L.maxW = std::max(L.maxW, ci->h.W);
+        L.maxN = std::max(L.maxN, ci->h.N);
+        L.maxGr = std::max(L.maxGr, ci->h.Gr);
+        L.maxGz = std::max(L.maxGz, ci->h.Gz);
+        L.thermal = L.thermal || ci->h.thermal;
+        L.smem = std::max(L.smem, block_smem(ci->h));
+    }
+    // descriptors and the gathered status live in one device block per call
+    CoilDev* dd = nullptr;
+    int* dstat = nullptr;
+    CK(cudaMalloc(&dd, n * sizeof(CoilDev) + 3 * n * sizeof(int)), "batch descriptors");
+    dstat = reinterpret_cast<int*>(dd + n);
+    std::vector<int> hstat(3 * (size_t)n);
+    coil_status result = COIL_OK;
+    cudaError_t e = cudaMemcpyAsync(dd, hd.data(), n * sizeof(CoilDev), cudaMemcpyHostToDevice, L.s);
+    L.d = dd;
+    int maxit = 0;
+    for (int i = 0; i < n; ++i) maxit = std::max(maxit, coils[i]->h.maxit);
+    for (long k = 0; k < n_steps && e == cudaSuccess && result == COIL_OK; ++k) {
+        result = step_prologue(c, L);
+        int chunk = 1;
+        for (int i = 0; i < n; ++i) chunk = std::max(chunk, coils[i]->last_iters);
+        int total = 0;
+        bool all_done = false;
+        while (result == COIL_OK) {
+            for (int i = 0; i < chunk && result == COIL_OK; ++i) result = step_iteration(c, L);
+            total += chunk;
+            k_gather_status<<<(n + 127) / 128, 128, 0, L.s>>>(dd, n, dstat);
+            e = cudaMemcpyAsync(hstat.data(), dstat, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, L.s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(L.s);
+            if (e != cudaSuccess) break;
+            all_done = true;
+            for (int i = 0; i < n; ++i) all_done = all_done && hstat[3 * i];
+            if (all_done || total > maxit + 2) break;
+            chunk = 1;
+        }
+        if (e != cudaSuccess || result != COIL_OK) break;
+        harvest_events(c);
+        result = step_epilogue(c, L);
+        coil_status first_err = COIL_OK;
+        for (int i = 0; i < n; ++i) {
+            coil_t* ci = coils[i];
+            int done = hstat[3 * i], st = hstat[3 * i + 1], it = hstat[3 * i + 2];
+            if (done && st == ST_OK) {
+                ci->steps += 1;
+                ci->t += ci->h.dt;
+                ci->last_iters = it > 0 ? it : 1;
+                ci->pcg_iters += it;
+            } else if (first_err == COIL_OK) {
+                first_err = (!done || st == ST_NOT_CONVERGED) ? COIL_ERR_NOT_CONVERGED : COIL_ERR_NONFINITE;
+                fail(ci, first_err, "batched step: this coil's solve failed; its state was kept");
+            }
+        }
+        if (result == COIL_OK && first_err != COIL_OK) {
+            fail(c, first_err, "batched step: at least one coil's solve failed");
+            result = first_err;
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(L.s);
+    cudaFree(dd);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch step");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "batch step");
+    return result;
 }
 
 coil_status coil_read_device(coil_t* c, const coil_drive* dr, double* dJ, double* dBr, double* dBz,

@@ -54,7 +54,13 @@ k_gemv_f64(const CoilDev* __restrict__ cds, int which) {
     }
 }
 
-template <int R>
+// FP32 operator.  The inner loop is pure FP32: on B300 the FP64 pipe issues
+// two thread-operations per SM per clock (1/64 of FP32), so even an
+// occasional FP64 conversion per vector makes the kernel FP64-bound.  Lane
+// partials are kept in two FP32 levels (the inner pair is folded into the
+// outer one every 16 unrolled iterations) and meet FP64 only in the final
+// per-row warp reduction.
+template <int R, int U>
 __global__ void __launch_bounds__(kGemvWarps * 32)
 k_gemv_f32(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
@@ -70,13 +76,35 @@ k_gemv_f32(const CoilDev* __restrict__ cds) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
             rows[r] = reinterpret_cast<const float4*>(M + (size_t)min(row0 + r, N - 1) * c.ld);
-        double acc[R];
-        float f0[R], f1[R];
+        float f0[R], f1[R], s2[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { acc[r] = 0.0; f0[r] = 0.f; f1[r] = 0.f; }
-        int cnt = 0;
-#pragma unroll 2
-        for (int j = lane; j < nvec; j += 32) {
+        for (int r = 0; r < R; ++r) { f0[r] = 0.f; f1[r] = 0.f; s2[r] = 0.f; }
+        int j = lane, cnt = 0;
+        for (; j + 32 * (U - 1) < nvec; j += 32 * U) {
+            float4 pv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) pv[u] = __ldg(p4 + j + 32 * u);
+            float4 m[R][U];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int u = 0; u < U; ++u) m[r][u] = __ldcs(rows[r] + j + 32 * u);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    f0[r] = fmaf(m[r][u].x, pv[u].x, f0[r]);
+                    f1[r] = fmaf(m[r][u].y, pv[u].y, f1[r]);
+                    f0[r] = fmaf(m[r][u].z, pv[u].z, f0[r]);
+                    f1[r] = fmaf(m[r][u].w, pv[u].w, f1[r]);
+                }
+            if (++cnt == 16) {
+                cnt = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) { s2[r] += f0[r] + f1[r]; f0[r] = 0.f; f1[r] = 0.f; }
+            }
+        }
+        for (; j < nvec; j += 32) {
             float4 pv = __ldg(p4 + j);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -86,15 +114,10 @@ k_gemv_f32(const CoilDev* __restrict__ cds) {
                 f0[r] = fmaf(m.z, pv.z, f0[r]);
                 f1[r] = fmaf(m.w, pv.w, f1[r]);
             }
-            if (++cnt == 32) {
-                cnt = 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) { acc[r] += (double)f0[r] + (double)f1[r]; f0[r] = 0.f; f1[r] = 0.f; }
-            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            double s = warp_sum(acc[r] + (double)f0[r] + (double)f1[r]);
+            double s = warp_sum((double)s2[r] + (double)(f0[r] + f1[r]));
             if (lane == r && row0 + r < N) c.qv[row0 + r] = s;
         }
     }
@@ -103,7 +126,8 @@ k_gemv_f32(const CoilDev* __restrict__ cds) {
 __device__ __forceinline__ float bf16_lo(unsigned v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(unsigned v) { return __uint_as_float(v & 0xffff0000u); }
 
-template <int R>
+// BF16 operator, FP32 products and accumulation (same structure as FP32).
+template <int R, int U>
 __global__ void __launch_bounds__(kGemvWarps * 32)
 k_gemv_bf16(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
@@ -119,13 +143,42 @@ k_gemv_bf16(const CoilDev* __restrict__ cds) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
             rows[r] = reinterpret_cast<const uint4*>(M + (size_t)min(row0 + r, N - 1) * c.ld);
-        double acc[R];
-        float f0[R], f1[R];
+        float f0[R], f1[R], s2[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { acc[r] = 0.0; f0[r] = 0.f; f1[r] = 0.f; }
-        int cnt = 0;
-#pragma unroll 2
-        for (int j = lane; j < nvec; j += 32) {
+        for (int r = 0; r < R; ++r) { f0[r] = 0.f; f1[r] = 0.f; s2[r] = 0.f; }
+        int j = lane, cnt = 0;
+        for (; j + 32 * (U - 1) < nvec; j += 32 * U) {
+            float4 pa[U], pb[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                pa[u] = __ldg(p4 + 2 * (j + 32 * u));
+                pb[u] = __ldg(p4 + 2 * (j + 32 * u) + 1);
+            }
+            uint4 m[R][U];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int u = 0; u < U; ++u) m[r][u] = __ldcs(rows[r] + j + 32 * u);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    f0[r] = fmaf(bf16_lo(m[r][u].x), pa[u].x, f0[r]);
+                    f1[r] = fmaf(bf16_hi(m[r][u].x), pa[u].y, f1[r]);
+                    f0[r] = fmaf(bf16_lo(m[r][u].y), pa[u].z, f0[r]);
+                    f1[r] = fmaf(bf16_hi(m[r][u].y), pa[u].w, f1[r]);
+                    f0[r] = fmaf(bf16_lo(m[r][u].z), pb[u].x, f0[r]);
+                    f1[r] = fmaf(bf16_hi(m[r][u].z), pb[u].y, f1[r]);
+                    f0[r] = fmaf(bf16_lo(m[r][u].w), pb[u].z, f0[r]);
+                    f1[r] = fmaf(bf16_hi(m[r][u].w), pb[u].w, f1[r]);
+                }
+            if (++cnt == 16) {
+                cnt = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) { s2[r] += f0[r] + f1[r]; f0[r] = 0.f; f1[r] = 0.f; }
+            }
+        }
+        for (; j < nvec; j += 32) {
             float4 pa = __ldg(p4 + 2 * j);
             float4 pb = __ldg(p4 + 2 * j + 1);
 #pragma unroll
@@ -140,15 +193,10 @@ k_gemv_bf16(const CoilDev* __restrict__ cds) {
                 f0[r] = fmaf(bf16_lo(m.w), pb.z, f0[r]);
                 f1[r] = fmaf(bf16_hi(m.w), pb.w, f1[r]);
             }
-            if (++cnt == 32) {
-                cnt = 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) { acc[r] += (double)f0[r] + (double)f1[r]; f0[r] = 0.f; f1[r] = 0.f; }
-            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            double s = warp_sum(acc[r] + (double)f0[r] + (double)f1[r]);
+            double s = warp_sum((double)s2[r] + (double)(f0[r] + f1[r]));
             if (lane == r && row0 + r < N) c.qv[row0 + r] = s;
         }
     }
@@ -168,9 +216,9 @@ cudaError_t launch_gemv(const CoilDev* cds, int n_coils, int prec, long long max
     if (prec == PREC_FP64)
         k_gemv_f64<R><<<grid, kGemvWarps * 32, 0, s>>>(cds, which);
     else if (prec == PREC_FP32)
-        k_gemv_f32<R><<<grid, kGemvWarps * 32, 0, s>>>(cds);
+        k_gemv_f32<R, 4><<<grid, kGemvWarps * 32, 0, s>>>(cds);
     else
-        k_gemv_bf16<R><<<grid, kGemvWarps * 32, 0, s>>>(cds);
+        k_gemv_bf16<R, 2><<<grid, kGemvWarps * 32, 0, s>>>(cds);
     return cudaGetLastError();
 }
 

@@ -453,6 +453,7 @@ __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode) {
 // (parts[5]) and m (parts[6]).
 __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->status != ST_OK) return;          // a failed coil keeps its state
     double* parts = c.parts;
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -502,6 +503,7 @@ __device__ void thomas_line(double* v, int G, const double* lo, const double* in
 // r-lines: u* = (I - dt/2 A_r)^-1 [(I + dt/2 A_z) u + dt/2 s].  One warp per grid row.
 __global__ void k_adi_r(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->status != ST_OK) return;
     int j = blockIdx.x;
     if (j >= c.Gz) return;
     extern __shared__ double sm[];
@@ -527,6 +529,7 @@ __global__ void k_adi_r(const CoilDev* __restrict__ cds) {
 // z-lines: u' = (I - dt/2 A_z)^-1 [(I + dt/2 A_r) u* + dt/2 s].  One warp per column.
 __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->status != ST_OK) return;
     int i = blockIdx.x;
     if (i >= c.Gr) return;
     extern __shared__ double sm[];
@@ -557,6 +560,7 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
 // One CTA per coil: the step's diagnostic record, then t += dt.
 __global__ void k_step_end(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.x];
+    if (c.sc->status != ST_OK) return;
     __shared__ double sh[32];
     const double* parts = c.parts;
     size_t W = c.W;
