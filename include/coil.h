@@ -207,6 +207,28 @@ coil_status coil_set_currents(coil_t *c, const double *I);
  * plus the FP64 intra-wire blocks), host vectors of N doubles. */
 coil_status coil_apply_operator(coil_t *c, const double *p, double *y);
 
+/* Same product as coil_apply_operator, y = M p, for callers that must not
+ * allocate device memory after set-up: code running while a stream is being
+ * captured into a CUDA graph, real-time control loops that fix their memory
+ * at start-up, or processes whose device memory is capped by a scheduler.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * d_p (input) and d_y (output) are DEVICE arrays of n_elem doubles owned by
+ * the caller.  Nothing is allocated or freed: the zero-padded copy of p that
+ * the operator kernels read lives in one file-scope device array of
+ * 1,048,576 doubles (8 MiB), which every device that loads the library holds
+ * until the process exits.  Coils whose operator pitch (n_elem rounded up to
+ * 64) exceeds 1,048,576 get COIL_ERR_INVALID.  The first call on a device
+ * looks up that array's device address (one cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Launches go to `stream` (a
+ * cudaStream_t, NULL = default stream) and the call returns without waiting;
+ * d_y is ready when the stream reaches that point.  Every call shares the
+ * array and it keeps the last call's contents: two calls that overlap on the
+ * GPU (different streams or threads at the same time) race on it and give
+ * wrong results. */
+coil_status coil_apply_operator_static(coil_t *c, const double *d_p, double *d_y,
+                                       void *stream);
+
 /* Read the dense operator row by row into a host N x N FP64 array
  * (far part converted from its storage precision, near blocks added). */
 coil_status coil_read_operator(coil_t *c, double *M);

@@ -76,6 +76,7 @@ def load_library(path=LIB_PATH):
         "coil_get_currents": ([P, _dp], C.c_int),
         "coil_set_currents": ([P, _dp], C.c_int),
         "coil_apply_operator": ([P, _dp, _dp], C.c_int),
+        "coil_apply_operator_static": ([P, P, P, P], C.c_int),
         "coil_read_operator": ([P, _dp], C.c_int),
         "coil_save_state": ([P, P, C.POINTER(C.c_size_t)], C.c_int),
         "coil_load_state": ([P, P, C.c_size_t], C.c_int),
@@ -247,6 +248,12 @@ class Coil:
         y = np.empty(self.N)
         self._check(self._lib.coil_apply_operator(self._h, _ptr(p), _ptr(y)))
         return y
+
+    def apply_operator_static(self, d_p, d_y, stream=None):
+        """coil_apply_operator_static on raw device pointers (no allocation;
+        asynchronous on `stream`, a cudaStream_t handle or None)."""
+        self._check(self._lib.coil_apply_operator_static(self._h, C.c_void_p(d_p), C.c_void_p(d_y),
+                                                         C.c_void_p(stream) if stream else None))
 
     def operator(self):
         M = np.empty((self.N, self.N))

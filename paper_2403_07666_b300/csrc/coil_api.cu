@@ -1085,3 +1085,22 @@ void coil_destroy(coil_t* c) {
 }
 
 }  // extern "C"
+
+// ---- internal view for entry points in other translation units
+#include "internal.h"
+
+namespace cq {
+bool coil_view(const coil_t* c, CoilView* v) {
+    if (!c || !v) return false;
+    v->host = &c->h;
+    v->dev = c->d;
+    v->device = c->device;
+    v->n_sm = c->n_sm;
+    return true;
+}
+
+coil_status coil_set_error(coil_t* c, coil_status st, const char* msg) {
+    if (c) c->err = msg;
+    return st;
+}
+}  // namespace cq
