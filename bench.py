@@ -9,10 +9,13 @@ the transport-constrained circuit equations (dense operator applies), flux
 and current update, ADI heat step, diagnostics.  Metric: element-steps/s.
 
 Default workload: the 96,000-element real-size coil (60 x 100 turns, 4 x 4
-elements per wire), dense operator stored in BF16 (18.4 GB, larger than the
+elements per wire), dense operator stored in FP32 (36.9 GB, larger than the
 126 MB L2, so no flush is needed between steps), transport ramp 2 A/s,
 dt = 1e-5 s, synthetic seeded inputs.  The FP64 form of the same coil is
-timed beside it for the mixed/FP64 ratio.
+timed beside it for the mixed/FP64 ratio.  BF16 storage (--precision bf16)
+rounds the operator by 2^-9 per entry, which at this size is more than its
+smallest eigenvalue: the stored operator is no longer positive definite and
+the conjugate-gradient solve breaks down, so FP32 is the mixed form here.
 
 Multi-GPU: the coil does not shard across GPUs in this build ("replicas
 only"): under torchrun each rank steps its own replica; value = all ranks'
@@ -46,6 +49,16 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (profiles/k_gemv_f32_profile19968.md: dram__bytes_read.sum +
+# dram__bytes_write.sum on the 19,968-element coil).  The kernel streams the
+# operator once, so traffic scales with the operator bytes; it is scaled to
+# the bench launch by that ratio.  Kernels without a capture report null.
+PROFILED_TRAFFIC = {
+    "fp32": {"dram_bytes": 1.595007e9 + 3.258624e6, "operator_bytes": 1594884096},
+}
 
 
 def pick_workload(name):
@@ -244,6 +257,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = op_bytes / (gemv_ms / 1e3) / 1e9
     applies = op_launches / args.steps
     launches = int(inf.kernel_launches)
+    prof = PROFILED_TRAFFIC.get(args.precision)
+    traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
 
     # end to end through the public API: host buffers, copies inside the region
     import torch as _t
@@ -299,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
         "applies_per_step": applies,
         "setup_s": setup_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": f"k_gemv_{args.precision}",
+                     "frac": achieved / hbm, "traffic": traffic, "kernel": f"k_gemv_{args.precision}",
                      "peak_kind": peak_kind, "avg_launch_ms": gemv_ms,
                      "bytes_per_launch": op_bytes},
         "e2e": e2e,

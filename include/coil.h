@@ -178,6 +178,30 @@ coil_status coil_step(coil_t *c, long n_steps, const coil_drive *drive);
 coil_status coil_batch_step(coil_t *const *coils, int n_coils, long n_steps,
                             const coil_drive *drives);
 
+/* Replace the calibration parameters of the E-J / Jc laws (Methods: the laws
+ * are fitted to a measured magnetization loop): the per-element Jc factor
+ * (host array of N doubles, NULL = keep), the creep exponent n (>= 1) and the
+ * strain coefficient C_eps. */
+coil_status coil_set_params(coil_t *c, const double *jc_factor, double n, double C_eps);
+
+/* Discrete adjoint of n_steps coupled steps starting from the current state
+ * (gradients for calibrating the E-J / Jc laws against a magnetization loop).
+ * dL_dm[k] is the derivative of the caller's loss with respect to the moment
+ * sum(pi r^2 I) after step k+1 (host array of n_steps doubles).  The call runs
+ * the n_steps forward, keeping the state every ckpt_every steps, then sweeps
+ * backwards: each reverse step recomputes its segment's forward states from
+ * the last checkpoint and applies the hand-written reverse of every kernel of
+ * the step (transposed per-step solve with the same projected PCG, E-J and Jc
+ * Jacobians including the dependence of the solve's matrix on G, stencil
+ * transpose, one operator apply for M^T = M, reverse ADI).  Outputs (host,
+ * NULL = skip): g_jc_factor[N] = dL/d(jc_factor), *g_n = dL/dn,
+ * *g_C_eps = dL/dC_eps.  On return the state is the one after the n_steps
+ * forward steps.  Scratch device memory is allocated for the call and freed
+ * before it returns. */
+coil_status coil_adjoint(coil_t *c, long n_steps, const coil_drive *drive, int ckpt_every,
+                         const double *dL_dm, double *g_jc_factor, double *g_n,
+                         double *g_C_eps);
+
 /* Copy the current state to host buffers of N doubles (NULL = skip): current
  * density J [A/m^2], B_r, B_z [T] from the stencil of the loop flux, T [K];
  * and the moment sum(pi r^2 I) [A m^2].  `Ba` is the applied field at the

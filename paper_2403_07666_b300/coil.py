@@ -80,6 +80,8 @@ def load_library(path=LIB_PATH):
         "coil_read_operator": ([P, _dp], C.c_int),
         "coil_save_state": ([P, P, C.POINTER(C.c_size_t)], C.c_int),
         "coil_load_state": ([P, P, C.c_size_t], C.c_int),
+        "coil_set_params": ([P, _dp, C.c_double, C.c_double], C.c_int),
+        "coil_adjoint": ([P, C.c_long, C.POINTER(Drive), C.c_int, _dp, _dp, _dp, _dp], C.c_int),
         "coil_info": ([P, C.POINTER(Info)], C.c_int),
         "coil_reset_counters": ([P], C.c_int),
         "coil_last_error": ([P], C.c_char_p),
@@ -270,6 +272,22 @@ class Coil:
     def load_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(self._lib.coil_load_state(self._h, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def set_params(self, jc_factor=None, n=30.0, C_eps=900.0):
+        jf = None if jc_factor is None else np.ascontiguousarray(jc_factor, dtype=np.float64)
+        self._check(self._lib.coil_set_params(self._h, None if jf is None else _ptr(jf), float(n),
+                                              float(C_eps)))
+
+    def adjoint(self, n_steps, drive, dL_dm, ckpt_every=50):
+        """Gradients (dL/d jc_factor [N], dL/dn, dL/dC_eps) of a loss whose
+        derivative with respect to the moment after each step is dL_dm."""
+        dm = np.ascontiguousarray(dL_dm, dtype=np.float64)
+        gf = np.empty(self.N)
+        gn = C.c_double()
+        gc = C.c_double()
+        self._check(self._lib.coil_adjoint(self._h, int(n_steps), C.byref(make_drive(drive)),
+                                           int(ckpt_every), _ptr(dm), _ptr(gf), C.byref(gn), C.byref(gc)))
+        return gf, gn.value, gc.value
 
     def reset_counters(self):
         self._check(self._lib.coil_reset_counters(self._h))

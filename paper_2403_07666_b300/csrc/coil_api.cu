@@ -1104,3 +1104,246 @@ coil_status coil_set_error(coil_t* c, coil_status st, const char* msg) {
     return st;
 }
 }  // namespace cq
+
+// ---- adjoint driver -----------------------------------------------------
+namespace cq {
+struct AdjBufs {
+    double* lamI;
+    const double* lamI_next;
+    double* lamU;
+    const double* lamU_next;
+    double* a;
+    double* b;
+    double* lamQ;
+    double* lamBr;
+    double* lamBz;
+    const double* xk;
+    double* g_f;
+    double* gparts;
+};
+void launch_adj_thermal(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
+void launch_adj_setup(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
+void launch_adj_mult_pointwise(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
+void launch_adj_stencil_t(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
+void launch_adj_near(const CoilDev* d, const CoilDev& h, cudaStream_t s);
+void launch_adj_accum(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, double wk, int with_field,
+                      cudaStream_t s);
+void launch_adj_seed(const CoilDev* d, const CoilDev& h, double* lamI, double wk, cudaStream_t s);
+void launch_adj_reduce(const CoilDev* d, const double* gparts, double* out, cudaStream_t s);
+}  // namespace cq
+
+namespace {
+
+// Device scratch of one adjoint call, released when the call returns.
+struct AdjMem {
+    std::vector<void*> ptrs;
+    coil_t* c;
+    explicit AdjMem(coil_t* cc) : c(cc) {}
+    ~AdjMem() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    coil_status get(double** p, size_t n, const char* what) {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, (n ? n : 1) * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, COIL_ERR_OOM, std::string("adjoint: allocation of ") + what + " failed");
+        }
+        ptrs.push_back(v);
+        *p = static_cast<double*>(v);
+        CK(cudaMemsetAsync(v, 0, (n ? n : 1) * sizeof(double), c->stream), "adjoint memset");
+        return COIL_OK;
+    }
+};
+
+// Copy the stepping state (I, flux, warm start, T^4) to or from `slot`.
+coil_status state_copy(coil_t* c, double* slot, bool save, bool with_x) {
+    const CoilDev& h = c->h;
+    size_t N = h.N, G = (size_t)h.Gr * h.Gz;
+    cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    double* parts[4] = {h.I, h.Phi, h.x, h.uT};
+    size_t sizes[4] = {N, N, N, G};
+    size_t off = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (sizes[i] && (i != 2 || with_x)) {
+            if (save) CK(cudaMemcpyAsync(slot + off, parts[i], sizes[i] * 8, k, c->stream), "state copy");
+            else CK(cudaMemcpyAsync(parts[i], slot + off, sizes[i] * 8, k, c->stream), "state copy");
+        }
+        off += sizes[i];
+    }
+    return COIL_OK;
+}
+
+coil_status set_device_time(coil_t* c, double t, long long step) {
+    struct { double t; long long step; } ts = {t, step};
+    CK(cudaMemcpyAsync(c->h.sc, &ts, sizeof(ts), cudaMemcpyHostToDevice, c->stream), "time");
+    CK(cudaStreamSynchronize(c->stream), "time");
+    return COIL_OK;
+}
+
+// The transposed KKT solve of one reverse step: the same projected PCG with
+// the right-hand side prepared by k_adj_setup (k_pointwise already ran).
+coil_status adjoint_solve(coil_t* c) {
+    const CoilDev& h = c->h;
+    Launch L = single_launch(c);
+    k_factor<<<dim3(L.maxW, 1), 32, L.smem, L.s>>>(L.d);
+    k_reduce<<<1, 256, 0, L.s>>>(L.d, 0);
+    TRY(gemv(c, L, 0));
+    k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, 0);
+    k_init<<<dim3(L.maxW, 1), 32, L.smem, L.s>>>(L.d);
+    k_reduce<<<1, 256, 0, L.s>>>(L.d, 1);
+    c->launches += 5;
+    CK(cudaGetLastError(), "adjoint solve");
+    int chunk = c->last_iters > 1 ? c->last_iters : 1;
+    int total = 0;
+    for (;;) {
+        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
+        total += chunk;
+        TRY(read_scalars(c));
+        if (c->pinned->done) break;
+        if (total > h.maxit + 2) break;
+        chunk = 1;
+    }
+    int st = c->pinned->status;
+    if (!c->pinned->done || st == ST_NOT_CONVERGED)
+        return fail(c, COIL_ERR_NOT_CONVERGED, "adjoint solve did not converge within maxit iterations");
+    if (st == ST_NONFINITE) return fail(c, COIL_ERR_NONFINITE, "non-finite value in the adjoint solve");
+    c->pcg_iters += c->pinned->iter;
+    harvest_events(c);
+    return COIL_OK;
+}
+
+}  // namespace
+
+extern "C" coil_status coil_set_params(coil_t* c, const double* jc_factor, double n, double C_eps) {
+    if (!c) return COIL_ERR_INVALID;
+    if (!is_fin(n) || !(n >= 1.0) || !is_fin(C_eps)) return fail(c, COIL_ERR_INVALID, "n must be >= 1, C_eps finite");
+    cudaSetDevice(c->device);
+    if (jc_factor) {
+        for (int e = 0; e < c->h.N; ++e)
+            if (!is_fin(jc_factor[e]) || jc_factor[e] < 0.0)
+                return fail(c, COIL_ERR_NONFINITE, "non-finite or negative jc_factor");
+        CK(cudaMemcpyAsync((void*)c->h.jc_factor, jc_factor, c->h.N * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream), "set params");
+    }
+    c->h.nexp = n;
+    c->h.C_eps = C_eps;
+    TRY(sync_descriptor(c));
+    CK(cudaStreamSynchronize(c->stream), "set params");
+    return COIL_OK;
+}
+
+extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* drive, int ckpt_every,
+                                    const double* dL_dm, double* g_jc_factor, double* g_n, double* g_C_eps) {
+    if (!c) return COIL_ERR_INVALID;
+    if (n_steps < 1 || ckpt_every < 1 || !dL_dm) return fail(c, COIL_ERR_INVALID, "adjoint needs n_steps >= 1, ckpt_every >= 1, dL_dm");
+    for (long k = 0; k < n_steps; ++k)
+        if (!is_fin(dL_dm[k])) return fail(c, COIL_ERR_NONFINITE, "non-finite dL/dm");
+    cudaSetDevice(c->device);
+    TRY(set_drive(c, drive));
+    CoilDev& h = c->h;
+    const size_t N = h.N, G = (size_t)h.Gr * h.Gz, W = h.W;
+    const size_t S = 3 * N + G;                       // one stored state
+    const long nseg = (n_steps + ckpt_every - 1) / ckpt_every;
+    const bool grid = h.has_grid != 0, thermal = h.thermal != 0;
+    cudaStream_t s = c->stream;
+    AdjMem mem(c);
+    double *ck, *seg, *fin, *lamA, *lamB, *lamUA, *lamUB, *abuf, *bbuf, *lamQ, *lamBr, *lamBz, *gf, *gparts, *musave,
+        *out2;
+    TRY(mem.get(&ck, nseg * S, "checkpoints"));
+    TRY(mem.get(&seg, (size_t)ckpt_every * S, "segment states"));
+    TRY(mem.get(&fin, S, "final state"));
+    TRY(mem.get(&lamA, N, "lambda_I"));
+    TRY(mem.get(&lamB, N, "lambda_I"));
+    TRY(mem.get(&lamUA, G, "lambda_u"));
+    TRY(mem.get(&lamUB, G, "lambda_u"));
+    TRY(mem.get(&abuf, G, "reverse ADI"));
+    TRY(mem.get(&bbuf, G, "reverse ADI"));
+    TRY(mem.get(&lamQ, G, "lambda_q"));
+    TRY(mem.get(&lamBr, N, "lambda_B"));
+    TRY(mem.get(&lamBz, N, "lambda_B"));
+    TRY(mem.get(&gf, N, "dL/df"));
+    TRY(mem.get(&gparts, 2 * W, "partials"));
+    TRY(mem.get(&musave, N, "mu"));
+    TRY(mem.get(&out2, 2, "outputs"));
+
+    // forward pass, checkpoint every ckpt_every steps
+    std::vector<double> t_ck(nseg);
+    std::vector<long long> st_ck(nseg);
+    for (long k = 0; k < n_steps; ++k) {
+        if (k % ckpt_every == 0) {
+            TRY(state_copy(c, ck + (k / ckpt_every) * S, true, true));
+            t_ck[k / ckpt_every] = c->t;
+            st_ck[k / ckpt_every] = c->steps;
+        }
+        TRY(run_step(c));
+    }
+    TRY(state_copy(c, fin, true, true));
+    const double t_fin = c->t;
+    const long long st_fin = c->steps;
+    const int last_iters_fin = c->last_iters;
+
+    // reverse sweep
+    double* lamI_next = lamA;
+    double* lamI = lamB;
+    double* lamU_next = lamUA;
+    double* lamU = lamUB;
+    launch_adj_seed(c->d, h, lamI_next, dL_dm[n_steps - 1], s);
+    CK(cudaMemsetAsync(h.x, 0, h.ld * sizeof(double), s), "adjoint");
+    const size_t xoff = 2 * N;                      // position of the warm start / Idot in a slot
+    for (long sg = nseg - 1; sg >= 0; --sg) {
+        long k0 = sg * ckpt_every, k1 = std::min<long>(n_steps, k0 + ckpt_every);
+        CK(cudaMemcpyAsync(musave, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+        TRY(state_copy(c, ck + sg * S, false, true));
+        c->t = t_ck[sg];
+        c->steps = st_ck[sg];
+        TRY(set_device_time(c, c->t, c->steps));
+        std::vector<double> t_k(k1 - k0);
+        for (long k = k0; k < k1; ++k) {
+            double* slot = seg + (k - k0) * S;
+            TRY(state_copy(c, slot, true, false));
+            t_k[k - k0] = c->t;
+            TRY(run_step(c));
+            CK(cudaMemcpyAsync(slot + xoff, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+        }
+        CK(cudaMemcpyAsync(h.x, musave, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+        for (long k = k1 - 1; k >= k0; --k) {
+            double* slot = seg + (k - k0) * S;
+            TRY(state_copy(c, slot, false, false));
+            TRY(set_device_time(c, t_k[k - k0], st_ck[sg] + (k - k0)));
+            AdjBufs ab{lamI, lamI_next, lamU, lamU_next, abuf, bbuf, lamQ, lamBr, lamBz, slot + xoff, gf, gparts};
+            unsigned wb = (unsigned)((h.W + 7) / 8);
+            k_pointwise<<<dim3(wb, 1), 256, 0, s>>>(c->d);
+            if (thermal) launch_adj_thermal(c->d, h, ab, s);
+            launch_adj_setup(c->d, h, ab, s);
+            CK(cudaGetLastError(), "adjoint launch");
+            TRY(adjoint_solve(c));
+            launch_adj_mult_pointwise(c->d, h, ab, s);
+            if (grid) {
+                launch_adj_stencil_t(c->d, h, ab, s);
+                Launch L = single_launch(c);
+                TRY(gemv(c, L, 1));
+                launch_adj_near(c->d, h, s);
+            }
+            launch_adj_accum(c->d, h, ab, k >= 1 ? dL_dm[k - 1] : 0.0, grid ? 1 : 0, s);
+            c->launches += 6;
+            CK(cudaGetLastError(), "adjoint launch");
+            std::swap(lamI, lamI_next);
+            std::swap(lamU, lamU_next);
+        }
+    }
+    launch_adj_reduce(c->d, gparts, out2, s);
+    double g2[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(g2, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "adjoint");
+    if (g_jc_factor) CK(cudaMemcpyAsync(g_jc_factor, gf, N * 8, cudaMemcpyDeviceToHost, s), "adjoint");
+    CK(cudaStreamSynchronize(s), "adjoint");
+    if (g_n) *g_n = g2[0];
+    if (g_C_eps) *g_C_eps = g2[1];
+    // back to the state after the forward steps
+    TRY(state_copy(c, fin, false, true));
+    c->t = t_fin;
+    c->steps = st_fin;
+    c->last_iters = last_iters_fin;
+    TRY(set_device_time(c, t_fin, st_fin));
+    return COIL_OK;
+}

@@ -1,0 +1,70 @@
+// Pointwise pieces of the step shared by the forward and adjoint kernels:
+// the field from the loop-flux stencil, Jc(B, T, eps) and the E-J law.
+#pragma once
+
+#include "common.cuh"
+
+namespace cq {
+
+// ---------------------------------------------------------------- pointwise
+
+__device__ __forceinline__ double phi_total(const CoilDev& c, int g, double Ba) {
+    int e = c.grid_elem[g];
+    double r = c.r[e];
+    return c.Phi[e] + kPi * r * r * Ba;
+}
+
+// B_r, B_z at element e from the stencil of the total loop flux.
+__device__ __forceinline__ void field_at(const CoilDev& c, int e, double Ba, double* Br, double* Bz) {
+    int g = c.elem_grid[e];
+    int iz = g / c.Gr, ir = g - iz * c.Gr;
+    double dr = 0.0, dz = 0.0;
+    int j0 = c.sr_j0[ir];
+    for (int k = 0; k < 3; ++k) {
+        double wk = c.sr_w[3 * ir + k];
+        if (wk != 0.0) dr += wk * phi_total(c, iz * c.Gr + j0 + k, Ba);
+    }
+    j0 = c.sz_j0[iz];
+    for (int k = 0; k < 3; ++k) {
+        double wk = c.sz_w[3 * iz + k];
+        if (wk != 0.0) dz += wk * phi_total(c, (j0 + k) * c.Gr + ir, Ba);
+    }
+    double r = c.r[e];
+    *Bz = dr / (2.0 * kPi * r);
+    *Br = -dz / (2.0 * kPi * r);
+}
+
+__device__ __forceinline__ double critical_current(const CoilDev& c, double Bm, double T, double eps, double f) {
+    if (c.jc_model == 1) return f * c.Jc0;
+    double tr = T / c.Tc;
+    double Bc2 = c.Bc2_0 * (1.0 - tr * tr);
+    if (!(T < c.Tc && Bm < Bc2)) return 0.0;
+    double strain = fmax(0.0, 1.0 - c.C_eps * pow(fabs(eps), c.p_eps));
+    double bfac = 1.0 - Bm / Bc2;
+    return f * c.Jc0 * pow(1.0 - tr, 1.5) * (bfac * bfac) / sqrt(Bm + c.B_reg) * strain;
+}
+
+// rho/rho_n, (dE/dJ)/rho_n and |J|/Jc of the parallel power-law / normal law.
+__device__ __forceinline__ void ej_law(const CoilDev& c, int fil, double J, double Jc, double* frac, double* dfac,
+                       double* jrat) {
+    if (!fil) { *frac = 1.0; *dfac = 1.0; *jrat = 0.0; return; }
+    double aJ = fabs(J);
+    if (Jc <= 0.0) { *frac = 1.0; *dfac = 1.0; *jrat = aJ > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0; return; }
+    *jrat = aJ / Jc;
+    if (aJ == 0.0) { *frac = 0.0; *dfac = 0.0; return; }
+    double n = c.nexp;
+    double ell = log(c.E0 / (Jc * c.rho_n)) + (n - 1.0) * log(aJ / Jc);
+    if (ell > 0.0) {
+        double t = exp(-ell);
+        double opt = 1.0 + t;
+        *frac = 1.0 / opt;
+        *dfac = (1.0 + n * t) / (opt * opt);
+    } else {
+        double s = exp(ell);
+        double ops = 1.0 + s;
+        *frac = s / ops;
+        *dfac = s * (s + n) / (ops * ops);
+    }
+}
+
+}  // namespace cq

@@ -1,0 +1,98 @@
+"""GPU adjoint (coil_adjoint) against central finite differences of the FP64
+oracle: gradients of a magnetization-loop loss with respect to the creep
+exponent n, the strain coefficient C_eps and the per-element Jc factor."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_07666_b300 import build as B
+from paper_2403_07666_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+K = 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+
+
+def _loop_coil(thermal=1, transport=0):
+    """Free loops (or a transport ramp) under a triangular applied field, past
+    penetration, with heating: the field-loop calibration case."""
+    mtl = dict(wl.MATERIAL, Jc0=2e8, thermal=thermal)
+    w = wl.random_coil(81, 3, 4, 4, ramp_rate=2e4 if transport else 0.0, I_max=1e9, dt=1e-4,
+                       Ba_rate=4.0, Ba_max=0.02, Ba_waveform=2, material=mtl)
+    w.geometry["transport"] = transport
+    return w
+
+
+def _oracle_moments(w, f=None, n=None, ce=None):
+    o = oracle.build(w.geometry, w.material, w.jc_factor if f is None else f, w.strain, w.mat)
+    if n is not None:
+        o.p["n"] = n
+    if ce is not None:
+        o.p["C_eps"] = ce
+    return np.array([o.step(w.drive)[3] for _ in range(K)])
+
+
+@pytest.mark.parametrize("thermal,transport", [(1, 0), (0, 1)])
+def test_adjoint_matches_oracle_finite_differences(thermal, transport):
+    from paper_2403_07666_b300.coil import Coil
+    w = _loop_coil(thermal, transport)
+    target = _oracle_moments(w, f=w.jc_factor * 1.05, n=27.0)
+
+    def loss(m):
+        return np.sum((m - target) ** 2)
+
+    with Coil.from_workload(w, rtol=1e-11) as c:
+        s0 = c.save_state()
+        c.step(K, w.drive)
+        m = c.diag(0, K)[:, 3]
+        c.load_state(s0)
+        gf, gn, gc = c.adjoint(K, w.drive, 2.0 * (m - target), ckpt_every=10)
+        # a different checkpoint spacing (uneven last segment) gives the same gradient
+        c.load_state(s0)
+        gf2, gn2, gc2 = c.adjoint(K, w.drive, 2.0 * (m - target), ckpt_every=7)
+    assert np.array_equal(gf, gf2) and gn == gn2 and gc == gc2
+    # central differences of the oracle (direct solves, FP64)
+    n0, c0 = w.material["n"], w.material["C_eps"]
+    hn, hc = 1e-6 * n0, 1e-6 * c0
+    fd_n = (loss(_oracle_moments(w, n=n0 + hn)) - loss(_oracle_moments(w, n=n0 - hn))) / (2 * hn)
+    fd_c = (loss(_oracle_moments(w, ce=c0 + hc)) - loss(_oracle_moments(w, ce=c0 - hc))) / (2 * hc)
+    assert abs(gn / fd_n - 1) < 1e-4, (gn, fd_n)
+    assert abs(gc / fd_c - 1) < 1e-4, (gc, fd_c)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        v = rng.standard_normal(w.n_elem)
+        h = 1e-6
+        fd = (loss(_oracle_moments(w, f=w.jc_factor * (1 + h * v)))
+              - loss(_oracle_moments(w, f=w.jc_factor * (1 - h * v)))) / (2 * h)
+        ad = np.sum(gf * w.jc_factor * v)
+        assert abs(ad / fd - 1) < 1e-4, (ad, fd)
+
+
+def test_autograd_function_backward():
+    import torch
+    from paper_2403_07666_b300.autograd import CoilMoments
+    from paper_2403_07666_b300.coil import Coil
+    w = _loop_coil(1, 0)
+    target = torch.from_numpy(_oracle_moments(w, f=w.jc_factor * 1.05, n=27.0))
+    with Coil.from_workload(w, rtol=1e-11) as c:
+        f = torch.tensor(w.jc_factor, dtype=torch.float64, requires_grad=True)
+        n = torch.tensor(30.0, dtype=torch.float64, requires_grad=True)
+        ce = torch.tensor(900.0, dtype=torch.float64, requires_grad=True)
+        m = CoilMoments.apply(c, w.drive, K, 10, f, n, ce)
+        L = torch.sum((m - target) ** 2)
+        L.backward()
+        assert c.info().steps == K
+        c2 = Coil.from_workload(w, rtol=1e-11)
+        s0 = c2.save_state()
+        c2.step(K, w.drive)
+        mm = c2.diag(0, K)[:, 3]
+        c2.load_state(s0)
+        gf, gn, gc = c2.adjoint(K, w.drive, 2.0 * (mm - target.numpy()), ckpt_every=10)
+        c2.close()
+    assert np.allclose(f.grad.numpy(), gf, rtol=1e-12, atol=0)
+    assert abs(n.grad.item() - gn) <= 1e-12 * abs(gn)
