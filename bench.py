@@ -324,9 +324,67 @@ def run_ours(args, rank, world, local_rank):
     if fp64 is not None:
         line["fp64"] = fp64
         line["mixed_over_fp64"] = value / fp64["value"]
+    if args.adjoint_steps > 0:
+        line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
+    if args.batch_steps > 0:
+        line["batched"] = batch_leg(args, local_rank, stream, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     return line
+
+
+def adjoint_leg(args, local_rank, stream, torch):
+    """Adjoint / forward cost on the 4,608-element field-loop coil."""
+    from paper_2403_07666_b300.coil import Coil
+    w = wl.adjoint_coil()
+    K = args.adjoint_steps
+    c = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                           stream=stream.cuda_stream)
+    s0 = c.save_state()
+    c.step(3, w.drive)
+    c.load_state(s0)
+    fwd = timed_steps(c, w.drive, K, stream, torch)
+    m = c.diag(0, K)[:, 3]
+    c.load_state(s0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c.adjoint(K, w.drive, 2.0 * m, ckpt_every=50)
+    torch.cuda.synchronize()
+    adj = time.perf_counter() - t0
+    c.close()
+    return {"workload": w.name, "n_elem": w.n_elem, "steps": K, "checkpoint_every": 50,
+            "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd,
+            "note": "adjoint_s includes the checkpointed forward pass and the segment recomputation"}
+
+
+def batch_leg(args, local_rank, stream, torch):
+    """64 coils of uneven size (2k-41k elements) stepped together."""
+    from paper_2403_07666_b300.coil import Coil, batch_step
+    ws = wl.batch_coils()
+    coils = [Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                                stream=stream.cuda_stream) for w in ws]
+    drives = [w.drive for w in ws]
+    batch_step(coils, args.warmup, drives)
+    for c in coils:
+        c.reset_counters()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    batch_step(coils, args.batch_steps, drives)
+    end.record(stream)
+    torch.cuda.synchronize()
+    secs = start.elapsed_time(end) / 1e3
+    total_elem = sum(c.N for c in coils)
+    launches = int(coils[0].info().kernel_launches)
+    op_bytes = sum(int(c.info().operator_bytes) for c in coils)
+    for c in coils:
+        c.close()
+    return {"workload": f"batch of {len(ws)} coils", "n_elem_total": total_elem,
+            "n_elem_min": min(w.n_elem for w in ws), "n_elem_max": max(w.n_elem for w in ws),
+            "steps": args.batch_steps, "value": total_elem * args.batch_steps / secs, "unit": UNIT,
+            "ms_per_step": 1e3 * secs / args.batch_steps, "operator_bytes": op_bytes,
+            "gpu_launches": launches}
 
 
 def run_reference(args, rank, world):
@@ -361,6 +419,8 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-9)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -130,3 +130,27 @@ def loop_field(a, z0, I, r, z):
     with np.errstate(divide="ignore", invalid="ignore"):
         Br = np.where(r > 0.0, pref * dz / r * (-K + (a * a + r * r + dz * dz) / gap2 * E), 0.0)
     return Br, Bz
+
+
+def operator_rows(r, z, h, rows):
+    """Rows `rows` of the dense operator (same definition as assemble_M),
+    computed one row at a time for coils too large to assemble."""
+    r = np.asarray(r, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    rows = np.asarray(rows)
+    N = r.size
+    out = np.empty((rows.size, N))
+    for k, i in enumerate(rows):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out[k] = mutual_point(r[i], z[i], r, z)
+        hmax = np.maximum(h[i], h)
+        near = ((r[i] - r) ** 2 + (z[i] - z) ** 2) < (NEAR_RADIUS * hmax) ** 2
+        near[i] = False
+        j = np.nonzero(near)[0]
+        # average with the lower index first, as assemble_M does for each pair
+        lo = np.minimum(i, j)
+        hi = np.maximum(i, j)
+        out[k, j] = near_average(r[lo], z[lo], h[lo], r[hi], z[hi], h[hi])
+        out[k, i] = self_inductance(r[i], h[i])
+    return out

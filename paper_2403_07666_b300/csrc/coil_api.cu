@@ -1175,9 +1175,9 @@ coil_status state_copy(coil_t* c, double* slot, bool save, bool with_x) {
 }
 
 coil_status set_device_time(coil_t* c, double t, long long step) {
+    // a pageable source: the copy is staged before cudaMemcpyAsync returns
     struct { double t; long long step; } ts = {t, step};
     CK(cudaMemcpyAsync(c->h.sc, &ts, sizeof(ts), cudaMemcpyHostToDevice, c->stream), "time");
-    CK(cudaStreamSynchronize(c->stream), "time");
     return COIL_OK;
 }
 
@@ -1267,16 +1267,26 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     TRY(mem.get(&musave, N, "mu"));
     TRY(mem.get(&out2, 2, "outputs"));
 
-    // forward pass, checkpoint every ckpt_every steps
+    // forward pass, checkpoint every ckpt_every steps; the states of the last
+    // segment are kept as they are made, so that segment needs no recomputation
     std::vector<double> t_ck(nseg);
     std::vector<long long> st_ck(nseg);
+    const long k0_last = (nseg - 1) * ckpt_every;
+    std::vector<double> t_last(n_steps - k0_last);
+    const size_t xoff = 2 * N;                      // position of the warm start / Idot in a slot
     for (long k = 0; k < n_steps; ++k) {
         if (k % ckpt_every == 0) {
             TRY(state_copy(c, ck + (k / ckpt_every) * S, true, true));
             t_ck[k / ckpt_every] = c->t;
             st_ck[k / ckpt_every] = c->steps;
         }
+        double* slot = k >= k0_last ? seg + (k - k0_last) * S : nullptr;
+        if (slot) {
+            TRY(state_copy(c, slot, true, false));
+            t_last[k - k0_last] = c->t;
+        }
         TRY(run_step(c));
+        if (slot) CK(cudaMemcpyAsync(slot + xoff, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
     }
     TRY(state_copy(c, fin, true, true));
     const double t_fin = c->t;
@@ -1290,23 +1300,26 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     double* lamU = lamUB;
     launch_adj_seed(c->d, h, lamI_next, dL_dm[n_steps - 1], s);
     CK(cudaMemsetAsync(h.x, 0, h.ld * sizeof(double), s), "adjoint");
-    const size_t xoff = 2 * N;                      // position of the warm start / Idot in a slot
     for (long sg = nseg - 1; sg >= 0; --sg) {
         long k0 = sg * ckpt_every, k1 = std::min<long>(n_steps, k0 + ckpt_every);
-        CK(cudaMemcpyAsync(musave, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
-        TRY(state_copy(c, ck + sg * S, false, true));
-        c->t = t_ck[sg];
-        c->steps = st_ck[sg];
-        TRY(set_device_time(c, c->t, c->steps));
         std::vector<double> t_k(k1 - k0);
-        for (long k = k0; k < k1; ++k) {
-            double* slot = seg + (k - k0) * S;
-            TRY(state_copy(c, slot, true, false));
-            t_k[k - k0] = c->t;
-            TRY(run_step(c));
-            CK(cudaMemcpyAsync(slot + xoff, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+        if (sg == nseg - 1) {
+            t_k = t_last;                           // kept from the forward pass
+        } else {
+            CK(cudaMemcpyAsync(musave, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+            TRY(state_copy(c, ck + sg * S, false, true));
+            c->t = t_ck[sg];
+            c->steps = st_ck[sg];
+            TRY(set_device_time(c, c->t, c->steps));
+            for (long k = k0; k < k1; ++k) {
+                double* slot = seg + (k - k0) * S;
+                TRY(state_copy(c, slot, true, false));
+                t_k[k - k0] = c->t;
+                TRY(run_step(c));
+                CK(cudaMemcpyAsync(slot + xoff, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+            }
+            CK(cudaMemcpyAsync(h.x, musave, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
         }
-        CK(cudaMemcpyAsync(h.x, musave, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
         for (long k = k1 - 1; k >= k0; --k) {
             double* slot = seg + (k - k0) * S;
             TRY(state_copy(c, slot, false, false));

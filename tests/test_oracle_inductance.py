@@ -113,3 +113,12 @@ def test_full_operator_symmetric_positive_definite():
     ev = np.linalg.eigvalsh(M)
     assert ev.min() > 0
     assert np.all(np.diag(M) > 0) and np.all(M > 0)
+
+
+def test_operator_rows_equal_assembled_rows():
+    from oracle.inductance import operator_rows
+    geo = oracle.solenoid_elements(3, 4, 4, 0.02, 0.9e-3, 0.8e-3)
+    M = oracle.assemble_M(geo["r"], geo["z"], geo["h"])
+    rows = np.array([0, 17, 95, 191])
+    R = operator_rows(geo["r"], geo["z"], geo["h"], rows)
+    assert np.array_equal(R, M[rows])
