@@ -324,6 +324,8 @@ def run_ours(args, rank, world, local_rank):
     if fp64 is not None:
         line["fp64"] = fp64
         line["mixed_over_fp64"] = value / fp64["value"]
+    if args.toeplitz:
+        line["toeplitz"] = toeplitz_leg(args, local_rank, stream, torch)
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
     if args.batch_steps > 0:
@@ -331,6 +333,36 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     return line
+
+
+# FP32 CUDA-core peak of B300 from its unit counts: 148 SMs x 128 FP32 lanes x
+# 2 flops per FMA x 2.032 GHz maximum SM clock.
+FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def toeplitz_leg(args, local_rank, stream, torch):
+    """The same coil with the far operator in block-Toeplitz FP32 storage."""
+    from paper_2403_07666_b300.coil import Coil
+    w = pick_workload(args.workload)
+    c = Coil.from_workload(w, precision="fp32", rtol=args.rtol, device=local_rank,
+                           stream=stream.cuda_stream, profile=True, format="toeplitz")
+    c.step(args.warmup, w.drive)
+    c.reset_counters()
+    secs = timed_steps(c, w.drive, args.steps, stream, torch)
+    inf = c.info()
+    N = c.N
+    c.close()
+    op_ms = inf.operator_ms / max(int(inf.operator_launches), 1)
+    flops = 2.0 * N * N
+    achieved = flops / (op_ms / 1e3) / 1e12
+    return {"value": N * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
+            "applies_per_step": int(inf.operator_launches) / args.steps,
+            "operator_bytes": int(inf.operator_bytes),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_ALU_TFLOPS, "traffic": None,
+                         "kernel": "k_toeplitz_f32 (+transpose, reduce)", "avg_launch_ms": op_ms,
+                         "flops_per_launch": flops,
+                         "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz"}}
 
 
 def adjoint_leg(args, local_rank, stream, torch):
@@ -419,6 +451,7 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-9)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--toeplitz", type=int, default=1, help="also time the block-Toeplitz operator format")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()

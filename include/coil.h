@@ -117,7 +117,17 @@ typedef struct {
     void *stream;
     long diag_capacity;
     int profile;        /* 1: time every operator apply with CUDA events */
+    int format;         /* COIL_FORMAT_DENSE or COIL_FORMAT_TOEPLITZ */
 } coil_options;
+
+/* Storage format of the far operator.  DENSE: N x N rows in `precision`.
+ * TOEPLITZ (regular solenoids, FP32 only): the coaxial-loop inductance depends
+ * on r, r' and z - z' only, so between turn rows t and t' the operator is one
+ * C x C block of offset t - t' (C = n_layers n_sub^2); the 2 n_turns - 1
+ * distinct blocks are stored (C^2 (2 n_turns - 1) entries instead of N^2, the
+ * same FP32 values as the dense form) and applied as a Toeplitz-structured
+ * FP32 matrix product. */
+enum { COIL_FORMAT_DENSE = 0, COIL_FORMAT_TOEPLITZ = 1 };
 
 /*
  * Drive (Numerical Algorithm section: ramping transport current I_a and

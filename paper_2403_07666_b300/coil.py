@@ -18,6 +18,8 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2
 GEOM_SOLENOID, GEOM_LIST = 0, 1
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16}
+FORMAT_DENSE, FORMAT_TOEPLITZ = 0, 1
+FORMATS = {"dense": FORMAT_DENSE, "toeplitz": FORMAT_TOEPLITZ}
 DIAG_WIDTH = 10
 DIAG_FIELDS = ("t", "I_t", "V_term", "moment", "P_joule", "T_max", "max_jratio",
                "max_rho_frac", "pcg_iters", "resid")
@@ -43,7 +45,8 @@ class Material(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int), ("device", C.c_int),
-                ("stream", C.c_void_p), ("diag_capacity", C.c_long), ("profile", C.c_int)]
+                ("stream", C.c_void_p), ("diag_capacity", C.c_long), ("profile", C.c_int),
+                ("format", C.c_int)]
 
 
 class Drive(C.Structure):
@@ -124,7 +127,7 @@ class Coil:
 
     def __init__(self, geometry, material, jc_factor, strain, mat, precision="fp64", rtol=1e-10,
                  maxit=500, device=0, stream=None, diag_capacity=65536, block_transport=None,
-                 profile=False):
+                 profile=False, format="dense"):
         self._lib = lib()
         self._keep = []
         g = Geometry()
@@ -158,7 +161,8 @@ class Coil:
         self._keep += [jf, st, mt]
         m.jc_factor, m.strain, m.mat = _ptr(jf), _ptr(st), _ptr(mt, C.c_int)
         o = Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision), float(rtol),
-                    int(maxit), int(device), stream, int(diag_capacity), int(bool(profile)))
+                    int(maxit), int(device), stream, int(diag_capacity), int(bool(profile)),
+                    FORMATS[format] if isinstance(format, str) else int(format))
         h = C.c_void_p()
         status = self._lib.coil_create(C.byref(g), C.byref(m), C.byref(o), C.byref(h))
         if status != OK:

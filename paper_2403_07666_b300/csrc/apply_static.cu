@@ -111,6 +111,8 @@ extern "C" coil_status coil_apply_operator_static(coil_t* c, const double* d_p, 
     if (!coil_view(c, &v)) return COIL_ERR_INVALID;
     if (!d_p || !d_y) return coil_set_error(c, COIL_ERR_INVALID, "apply_operator_static: null device buffer");
     const CoilDev& h = *v.host;
+    if (h.op_format != 0)
+        return coil_set_error(c, COIL_ERR_INVALID, "apply_operator_static: dense operator format only");
     if (h.ld > kStaticMaxLd)
         return coil_set_error(c, COIL_ERR_INVALID,
                               "apply_operator_static: operator pitch exceeds the static scratch "

@@ -22,6 +22,10 @@ cudaError_t launch_near_blocks(const double* tab, int C, int NT, int B, int n_ty
                                cudaStream_t s);
 cudaError_t launch_gemv(const CoilDev* cds, int n_coils, int prec, long long max_rows, int which,
                         int n_sm, cudaStream_t s);
+size_t toeplitz_part_floats(int C, int NT);
+cudaError_t launch_toeplitz_table(const double* tab, int C, int NT, int wire_div, float* out, cudaStream_t s);
+cudaError_t launch_toeplitz(const CoilDev* cds, int n_coils, int max_C, int max_NT, long long max_N, int n_sm,
+                            cudaStream_t s);
 
 __global__ void k_pointwise(const CoilDev* __restrict__ cds);
 __global__ void k_factor(const CoilDev* __restrict__ cds);
@@ -197,6 +201,10 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
     if (o->precision < 0 || o->precision > 2) return fail(c, COIL_ERR_INVALID, "unknown precision");
     if (!(o->rtol > 0.0 && o->rtol < 1.0)) return fail(c, COIL_ERR_INVALID, "rtol must be in (0, 1)");
     if (o->maxit < 1) return fail(c, COIL_ERR_INVALID, "maxit must be >= 1");
+    if (o->format != COIL_FORMAT_DENSE && o->format != COIL_FORMAT_TOEPLITZ)
+        return fail(c, COIL_ERR_INVALID, "unknown operator format");
+    if (o->format == COIL_FORMAT_TOEPLITZ && (g->kind != COIL_GEOM_SOLENOID || o->precision != PREC_FP32))
+        return fail(c, COIL_ERR_INVALID, "the Toeplitz format needs a solenoid and FP32 precision");
     if (g->kind == COIL_GEOM_SOLENOID) {
         if (g->n_layers < 1 || g->n_turns < 1 || g->n_sub < 1)
             return fail(c, COIL_ERR_INVALID, "solenoid needs n_layers, n_turns, n_sub >= 1");
@@ -409,17 +417,27 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
 
     // operator: table of distinct entries, dense far part, FP64 near blocks
     size_t esz = o->precision == PREC_FP64 ? 8 : (o->precision == PREC_FP32 ? 4 : 2);
+    const bool toep = o->format == COIL_FORMAT_TOEPLITZ;
+    h.op_format = toep ? 1 : 0;
+    h.C = C;
+    h.NT = NT;
+    const size_t tab_entries = (size_t)C * C * (2 * (size_t)NT - 1);
+    const size_t op_alloc = toep ? tab_entries * sizeof(float) : (size_t)N * ld * esz;
     void* M = nullptr;
     {
-        cudaError_t e = cudaMalloc(&M, (size_t)N * ld * esz);
+        cudaError_t e = cudaMalloc(&M, op_alloc);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(c, COIL_ERR_OOM, "device allocation of the far operator failed (" +
-                                             std::to_string((size_t)N * ld * esz) + " bytes)");
+                                             std::to_string(op_alloc) + " bytes)");
         }
         c->allocs.push_back(M);
-        c->bytes += (size_t)N * ld * esz;
-        c->op_bytes = (size_t)N * ld * esz;
+        c->bytes += op_alloc;
+        c->op_bytes = op_alloc;
+    }
+    if (toep) {
+        TRY(dalloc(c, &h.tpart, toeplitz_part_floats(C, NT), "Toeplitz partial sums"));
+        TRY(dalloc(c, &h.pT, N, "transposed operator input"));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
@@ -440,8 +458,14 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     size_t tab_n = (size_t)C * C * (2 * (size_t)NT - 1);
     TRY(dalloc(c, &tab, tab_n, "operator table"));
     CK(launch_table(drc, dzc, dhc, C, NT, pitch_t, tab, c->stream), "table");
-    h.Mfar = M;
-    CK(launch_expand(tab, C, NT, B, N, h.ld, o->precision, M, c->stream), "expand");
+    if (toep) {
+        h.tab32 = static_cast<const float*>(M);
+        h.Mfar = nullptr;
+        CK(launch_toeplitz_table(tab, C, NT, B, static_cast<float*>(M), c->stream), "Toeplitz table");
+    } else {
+        h.Mfar = M;
+        CK(launch_expand(tab, C, NT, B, N, h.ld, o->precision, M, c->stream), "expand");
+    }
     double* nearp;
     TRY(dalloc(c, &nearp, (size_t)n_types * B * B, "near blocks"));
     CK(launch_near_blocks(tab, C, NT, B, n_types, nearp, c->stream), "near blocks");
@@ -523,6 +547,8 @@ struct Launch {
     size_t smem = 0;
     cudaStream_t s = nullptr;
     int n_sm = 148;
+    int format = 0;
+    int maxC = 0, maxNT = 0;
 };
 
 Launch single_launch(coil_t* c) {
@@ -539,7 +565,16 @@ Launch single_launch(coil_t* c) {
     L.smem = block_smem(h);
     L.s = c->stream;
     L.n_sm = c->n_sm;
+    L.format = h.op_format;
+    L.maxC = h.C;
+    L.maxNT = h.NT;
     return L;
+}
+
+// The far-operator apply of either storage format.
+cudaError_t launch_far(const Launch& L, int which) {
+    if (L.format == 1) return launch_toeplitz(L.d, L.n, L.maxC, L.maxNT, L.maxN, L.n_sm, L.s);
+    return launch_gemv(L.d, L.n, L.prec, L.maxN, which, L.n_sm, L.s);
 }
 
 // Dense-operator launch, bracketed by an event pair when profiling.
@@ -554,7 +589,7 @@ coil_status gemv(coil_t* c, const Launch& L, int which) {
         }
         CK(cudaEventRecord(c->ev_pool[2 * c->ev_used], L.s), "event");
     }
-    CK(launch_gemv(L.d, L.n, L.prec, L.maxN, which, L.n_sm, L.s), "gemv");
+    CK(launch_far(L, which), "operator apply");
     if (c->profile) {
         CK(cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], L.s), "event");
         c->ev_used += 1;
@@ -658,7 +693,7 @@ coil_status apply_plain(coil_t* c, const double* dev_p) {
     CK(cudaMemcpyAsync(h.x, dev_p, h.N * sizeof(double), cudaMemcpyDeviceToDevice, s), "apply");
     CK(cudaMemsetAsync(&h.sc->done, 0, sizeof(int), s), "apply");
     k_to_float<<<(h.N + 255) / 256, 256, 0, s>>>(h.x, h.pf, h.N);
-    CK(launch_gemv(c->d, 1, h.precision, h.N, 0, c->n_sm, s), "gemv");
+    CK(launch_far(single_launch(c), 0), "operator apply");
     k_near<<<(unsigned)((h.W + 7) / 8), 256, 0, s>>>(c->d, 0);
     CK(cudaGetLastError(), "apply");
     h.dt = dt_save;
@@ -758,8 +793,9 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
     coil_t* c = coils[0];
     for (int i = 0; i < n; ++i) {
         if (!coils[i]) return COIL_ERR_INVALID;
-        if (coils[i]->device != c->device || coils[i]->h.precision != c->h.precision)
-            return fail(c, COIL_ERR_INVALID, "batched coils must share device and precision");
+        if (coils[i]->device != c->device || coils[i]->h.precision != c->h.precision ||
+            coils[i]->h.op_format != c->h.op_format)
+            return fail(c, COIL_ERR_INVALID, "batched coils must share device, precision and operator format");
         for (int j = 0; j < i; ++j)
             if (coils[j] == coils[i]) return fail(c, COIL_ERR_INVALID, "a coil appears twice in the batch");
     }
@@ -769,6 +805,7 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
     L.prec = c->h.precision;
     L.s = c->stream;
     L.n_sm = c->n_sm;
+    L.format = c->h.op_format;
     std::vector<CoilDev> hd(n);
     for (int i = 0; i < n; ++i) {
         coil_t* ci = coils[i];
@@ -781,6 +818,8 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.maxGz = std::max(L.maxGz, ci->h.Gz);
         L.thermal = L.thermal || ci->h.thermal;
         L.smem = std::max(L.smem, block_smem(ci->h));
+        L.maxC = std::max(L.maxC, ci->h.C);
+        L.maxNT = std::max(L.maxNT, ci->h.NT);
     }
     // descriptors and the gathered status live in one device block per call
     CoilDev* dd = nullptr;
@@ -950,7 +989,17 @@ coil_status coil_read_operator(coil_t* c, double* M) {
     size_t N = h.N, ld = h.ld;
     size_t esz = h.precision == PREC_FP64 ? 8 : (h.precision == PREC_FP32 ? 4 : 2);
     std::vector<unsigned char> row(ld * esz);
-    for (size_t i = 0; i < N; ++i) {
+    if (h.op_format == 1) {
+        size_t C = h.C, NT = h.NT;
+        std::vector<float> tab(C * C * (2 * NT - 1));
+        CK(cudaMemcpy(tab.data(), h.tab32, tab.size() * sizeof(float), cudaMemcpyDeviceToHost), "read operator");
+        for (size_t i = 0; i < N; ++i)
+            for (size_t j = 0; j < N; ++j) {
+                long long d = (long long)(i / C) - (long long)(j / C);
+                M[i * N + j] = tab[(size_t)(d + (long long)NT - 1) * C * C + (i % C) * C + (j % C)];
+            }
+    }
+    for (size_t i = 0; i < N && h.op_format == 0; ++i) {
         CK(cudaMemcpy(row.data(), (const unsigned char*)h.Mfar + i * ld * esz, ld * esz, cudaMemcpyDeviceToHost),
            "read operator");
         for (size_t j = 0; j < N; ++j) {

@@ -45,7 +45,15 @@ struct CoilDev {
     const int *block_type;        // near-block type per block
     const int *constrained;       // 1 if the block is a transport turn
     const double *near;           // n_types x B x B, FP64 intra-wire blocks of M
-    const void *Mfar;             // N x ld far operator in `precision`
+    const void *Mfar;             // N x ld far operator in `precision` (dense format)
+    // block-Toeplitz format of a regular solenoid: far operator entries
+    // tab32[(t_i - t_j + NT - 1)][c_i][c_j] (FP32, intra-wire entries zero),
+    // element e = t * C + c; partial sums per (t tile, d chunk) in tpart
+    int op_format;                // 0 dense, 1 Toeplitz
+    int C, NT;
+    const float *tab32;
+    float *tpart;
+    float *pT;                    // operator input transposed to [c][t] (FP32)
     // stencil: per grid column (resp. row) the first node and three weights
     const int *sr_j0, *sz_j0;
     const double *sr_w, *sz_w;
