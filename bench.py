@@ -9,10 +9,13 @@ the transport-constrained circuit equations (dense operator applies), flux
 and current update, ADI heat step, diagnostics.  Metric: element-steps/s.
 
 Default workload: the 96,000-element real-size coil (60 x 100 turns, 4 x 4
-elements per wire), dense operator stored in FP32 (36.9 GB, larger than the
-126 MB L2, so no flush is needed between steps), transport ramp 2 A/s,
-dt = 1e-5 s, synthetic seeded inputs.  The FP64 form of the same coil is
-timed beside it for the mixed/FP64 ratio.  BF16 storage (--precision bf16)
+elements per wire), transport ramp 2 A/s, dt = 1e-5 s, synthetic seeded
+inputs, far operator in FP32.  Main leg: the operator in block-Toeplitz
+storage (the same FP32 entries as the dense 96,000^2 matrix, 0.73 GB, larger
+than the 126 MB L2, so no flush is needed between steps; the apply is bound
+by the FP32 pipe).  Beside it: the dense FP32 storage (36.9 GB, HBM-bound),
+the plain FP64 dense form (mixed/FP64 ratio), the adjoint/forward cost on the
+4,608-element field-loop coil and the 64-coil batch.  BF16 storage (--precision bf16)
 rounds the operator by 2^-9 per entry, which at this size is more than its
 smallest eigenvalue: the stored operator is no longer positive definite and
 the conjugate-gradient solve breaks down, so FP32 is the mixed form here.
@@ -234,8 +237,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     hbm, peak_kind = peaks()
     t0 = time.perf_counter()
+    toep = args.format == "toeplitz"
     coil = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
-                              stream=stream.cuda_stream, profile=True)
+                              stream=stream.cuda_stream, profile=True, format=args.format)
     setup_s = time.perf_counter() - t0
     info = coil.info()
     N = coil.N
@@ -254,11 +258,25 @@ def run_ours(args, rank, world, local_rank):
     op_launches = int(inf.operator_launches)
     gemv_ms = inf.operator_ms / max(op_launches, 1)
     op_bytes = int(info.operator_bytes)
-    achieved = op_bytes / (gemv_ms / 1e3) / 1e9
     applies = op_launches / args.steps
     launches = int(inf.kernel_launches)
-    prof = PROFILED_TRAFFIC.get(args.precision)
-    traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
+    if toep:
+        flops = 2.0 * N * N
+        achieved = flops / (gemv_ms / 1e3) / 1e12
+        prof = PROFILED_TRAFFIC.get("toeplitz")
+        traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic,
+                    "kernel": "k_toeplitz_f32 (+transpose, reduce)",
+                    "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                    "avg_launch_ms": gemv_ms, "flops_per_launch": flops, "table_bytes": op_bytes}
+    else:
+        achieved = op_bytes / (gemv_ms / 1e3) / 1e9
+        prof = PROFILED_TRAFFIC.get(args.precision)
+        traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": traffic, "kernel": f"k_gemv_{args.precision}",
+                    "peak_kind": peak_kind, "avg_launch_ms": gemv_ms, "bytes_per_launch": op_bytes}
 
     # end to end through the public API: host buffers, copies inside the region
     import torch as _t
@@ -310,13 +328,12 @@ def run_ours(args, rank, world, local_rank):
                    "n_turns": w.geometry["n_turns"], "n_sub": w.geometry["n_sub"],
                    "precision": args.precision, "dt": drive["dt"], "ramp_A_per_s": drive["ramp_rate"],
                    "rtol": args.rtol, "parallelism": f"replicas x{world}",
-                   "l2": f"operator {op_bytes / 1e9:.1f} GB > 126 MB L2 (no flush needed)"},
+                   "operator_format": args.format,
+                   "l2": (f"operator table {op_bytes / 1e9:.2f} GB > 126 MB L2 (no flush needed)" if toep else
+                          f"operator {op_bytes / 1e9:.1f} GB > 126 MB L2 (no flush needed)")},
         "applies_per_step": applies,
         "setup_s": setup_s,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "kernel": f"k_gemv_{args.precision}",
-                     "peak_kind": peak_kind, "avg_launch_ms": gemv_ms,
-                     "bytes_per_launch": op_bytes},
+        "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -324,8 +341,11 @@ def run_ours(args, rank, world, local_rank):
     if fp64 is not None:
         line["fp64"] = fp64
         line["mixed_over_fp64"] = value / fp64["value"]
-    if args.toeplitz:
-        line["toeplitz"] = toeplitz_leg(args, local_rank, stream, torch)
+    if args.other_format:
+        if toep:
+            line["dense"] = dense_leg(args, local_rank, stream, torch)
+        else:
+            line["toeplitz"] = toeplitz_leg(args, local_rank, stream, torch)
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
     if args.batch_steps > 0:
@@ -363,6 +383,32 @@ def toeplitz_leg(args, local_rank, stream, torch):
                          "kernel": "k_toeplitz_f32 (+transpose, reduce)", "avg_launch_ms": op_ms,
                          "flops_per_launch": flops,
                          "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz"}}
+
+
+def dense_leg(args, local_rank, stream, torch):
+    """The same coil with the far operator stored dense (FP32, HBM-bound apply)."""
+    from paper_2403_07666_b300.coil import Coil
+    w = pick_workload(args.workload)
+    hbm, peak_kind = peaks()
+    c = Coil.from_workload(w, precision="fp32", rtol=args.rtol, device=local_rank,
+                           stream=stream.cuda_stream, profile=True, format="dense")
+    c.step(args.warmup, w.drive)
+    c.reset_counters()
+    secs = timed_steps(c, w.drive, args.steps, stream, torch)
+    inf = c.info()
+    N = c.N
+    c.close()
+    op_ms = inf.operator_ms / max(int(inf.operator_launches), 1)
+    op_bytes = int(inf.operator_bytes)
+    achieved = op_bytes / (op_ms / 1e3) / 1e9
+    prof = PROFILED_TRAFFIC.get("fp32")
+    return {"value": N * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
+            "applies_per_step": int(inf.operator_launches) / args.steps, "operator_bytes": op_bytes,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm,
+                         "traffic": prof["dram_bytes"] * op_bytes / prof["operator_bytes"],
+                         "kernel": "k_gemv_fp32", "avg_launch_ms": op_ms, "bytes_per_launch": op_bytes,
+                         "peak_kind": peak_kind}}
 
 
 def adjoint_leg(args, local_rank, stream, torch):
@@ -451,7 +497,9 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-9)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--toeplitz", type=int, default=1, help="also time the block-Toeplitz operator format")
+    ap.add_argument("--format", default="toeplitz", choices=["toeplitz", "dense"],
+                    help="storage of the far operator in the main leg")
+    ap.add_argument("--other-format", type=int, default=1, help="also time the other operator format")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()

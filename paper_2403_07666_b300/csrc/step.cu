@@ -79,17 +79,37 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
 
 // --------------------------------------------------- per-wire block algebra
 
-// Solve L L^T v = v in place (L lower, B x B row-major in shared memory).
+// Solve L L^T v = v in place (L lower, B x B row-major in shared memory, its
+// diagonal stored as reciprocals: FP64 division is slow on B300's FP64 pipe).
+// Blocks of up to 32 elements keep v in registers, one element per lane,
+// and broadcast each solved entry with a shuffle.
 __device__ void chol_solve_warp(const double* L, double* v, int B, int lane) {
+    if (B <= 32) {
+        double x = lane < B ? v[lane] : 0.0;
+        for (int k = 0; k < B; ++k) {
+            double xk = __shfl_sync(0xffffffffu, x, k) * L[k * B + k];
+            if (lane == k) x = xk;
+            else if (lane > k && lane < B) x -= L[lane * B + k] * xk;
+        }
+        for (int k = B - 1; k >= 0; --k) {
+            double xk = __shfl_sync(0xffffffffu, x, k) * L[k * B + k];
+            if (lane == k) x = xk;
+            else if (lane < k) x -= L[k * B + lane] * xk;
+        }
+        __syncwarp();
+        if (lane < B) v[lane] = x;
+        __syncwarp();
+        return;
+    }
     for (int k = 0; k < B; ++k) {
-        if (lane == 0) v[k] /= L[k * B + k];
+        if (lane == 0) v[k] *= L[k * B + k];
         __syncwarp();
         double vk = v[k];
         for (int i = k + 1 + lane; i < B; i += 32) v[i] -= L[i * B + k] * vk;
         __syncwarp();
     }
     for (int k = B - 1; k >= 0; --k) {
-        if (lane == 0) v[k] /= L[k * B + k];
+        if (lane == 0) v[k] *= L[k * B + k];
         __syncwarp();
         double vk = v[k];
         for (int i = lane; i < k; i += 32) v[i] -= L[k * B + i] * vk;
@@ -137,10 +157,10 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
     for (int k = 0; k < B; ++k) {
         double piv = A[k * B + k];
         if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
-        double lkk = sqrt(piv);
+        double rkk = 1.0 / sqrt(piv);                  // the factor keeps 1 / L_kk on its diagonal
         __syncwarp();
-        if (lane == 0) A[k * B + k] = lkk;
-        for (int i = k + 1 + lane; i < B; i += 32) A[i * B + k] /= lkk;
+        if (lane == 0) A[k * B + k] = rkk;
+        for (int i = k + 1 + lane; i < B; i += 32) A[i * B + k] *= rkk;
         __syncwarp();
         for (int i = k + 1 + lane; i < B; i += 32) {
             double lik = A[i * B + k];
@@ -352,9 +372,17 @@ __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode) {
     __shared__ double sh[32];
     const double* parts = c.parts;
     const double* a = parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < c.W; i += blockDim.x) s += a[i];
-    s = block_reduce_sum(s, sh);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four loads in flight per thread
+    const int W = c.W, st = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 3 * st < W; i += 4 * st) {
+        s0 += a[i];
+        s1 += a[i + st];
+        s2 += a[i + 2 * st];
+        s3 += a[i + 3 * st];
+    }
+    for (; i < W; i += st) s0 += a[i];
+    double s = block_reduce_sum((s0 + s1) + (s2 + s3), sh);
     if (threadIdx.x != 0) return;
     if (mode == RED_SCALE) {
         sc->scale2 = s;
