@@ -61,6 +61,8 @@ def peaks():
 # the bench launch by that ratio.  Kernels without a capture report null.
 PROFILED_TRAFFIC = {
     "fp32": {"dram_bytes": 1.595007e9 + 3.258624e6, "operator_bytes": 1594884096},
+    # profiles/k_toeplitz_f32_real96k.md: the bench workload itself (table 0.73 GB)
+    "toeplitz": {"dram_bytes": 1.556434e9 + 14.971904e6, "operator_bytes": 733593600},
 }
 
 
