@@ -117,7 +117,7 @@ typedef struct {
     void *stream;
     long diag_capacity;
     int profile;        /* 1: time every operator apply with CUDA events */
-    int format;         /* COIL_FORMAT_DENSE or COIL_FORMAT_TOEPLITZ */
+    int format;         /* COIL_FORMAT_DENSE, _TOEPLITZ or _TOEPLITZ_TC */
 } coil_options;
 
 /* Storage format of the far operator.  DENSE: N x N rows in `precision`.
@@ -126,8 +126,16 @@ typedef struct {
  * C x C block of offset t - t' (C = n_layers n_sub^2); the 2 n_turns - 1
  * distinct blocks are stored (C^2 (2 n_turns - 1) entries instead of N^2, the
  * same FP32 values as the dense form) and applied as a Toeplitz-structured
- * FP32 matrix product. */
-enum { COIL_FORMAT_DENSE = 0, COIL_FORMAT_TOEPLITZ = 1 };
+ * FP32 matrix product.
+ * TOEPLITZ_TC (regular solenoids with n_turns <= 224, FP32 precision only):
+ * the same blocks, each entry stored as two FP16 numbers hi + lo after a
+ * power-of-two scaling (about 22 significant bits, 4 bytes per entry), applied
+ * on the tensor cores as hi*hi + hi*lo + lo*hi products of an equally split
+ * input with FP32 accumulation; chunk sums are added in FP64.  Unsupported
+ * shapes get COIL_ERR_INVALID.  A bounded wait inside the apply kernel that
+ * runs out makes the step return COIL_ERR_CUDA ("tensor-core apply timed
+ * out"). */
+enum { COIL_FORMAT_DENSE = 0, COIL_FORMAT_TOEPLITZ = 1, COIL_FORMAT_TOEPLITZ_TC = 2 };
 
 /*
  * Drive (Numerical Algorithm section: ramping transport current I_a and

@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcoil.so")
-SOURCES = ["assemble.cu", "gemv.cu", "toeplitz.cu", "step.cu", "adjoint.cu", "coil_api.cu", "apply_static.cu"]
+SOURCES = ["assemble.cu", "gemv.cu", "toeplitz.cu", "toeplitz_tc.cu", "step.cu", "adjoint.cu", "coil_api.cu", "apply_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

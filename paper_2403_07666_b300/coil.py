@@ -18,8 +18,8 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2
 GEOM_SOLENOID, GEOM_LIST = 0, 1
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16}
-FORMAT_DENSE, FORMAT_TOEPLITZ = 0, 1
-FORMATS = {"dense": FORMAT_DENSE, "toeplitz": FORMAT_TOEPLITZ}
+FORMAT_DENSE, FORMAT_TOEPLITZ, FORMAT_TOEPLITZ_TC = 0, 1, 2
+FORMATS = {"dense": FORMAT_DENSE, "toeplitz": FORMAT_TOEPLITZ, "toeplitz_tc": FORMAT_TOEPLITZ_TC}
 DIAG_WIDTH = 10
 DIAG_FIELDS = ("t", "I_t", "V_term", "moment", "P_joule", "T_max", "max_jratio",
                "max_rho_frac", "pcg_iters", "resid")

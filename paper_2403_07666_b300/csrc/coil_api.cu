@@ -11,6 +11,7 @@
 
 #include "../../include/coil.h"
 #include "common.cuh"
+#include "toeplitz_tc.h"
 
 namespace cq {
 cudaError_t upload_gl_rule(const double* x, const double* w);
@@ -76,6 +77,7 @@ struct coil {
     double op_ms = 0.0;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;          // event pairs recorded since the last harvest
+    cq::TcPlan* tc = nullptr;    // tensor-core Toeplitz apply (format 2)
 };
 
 namespace {
@@ -201,10 +203,12 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
     if (o->precision < 0 || o->precision > 2) return fail(c, COIL_ERR_INVALID, "unknown precision");
     if (!(o->rtol > 0.0 && o->rtol < 1.0)) return fail(c, COIL_ERR_INVALID, "rtol must be in (0, 1)");
     if (o->maxit < 1) return fail(c, COIL_ERR_INVALID, "maxit must be >= 1");
-    if (o->format != COIL_FORMAT_DENSE && o->format != COIL_FORMAT_TOEPLITZ)
+    if (o->format != COIL_FORMAT_DENSE && o->format != COIL_FORMAT_TOEPLITZ && o->format != COIL_FORMAT_TOEPLITZ_TC)
         return fail(c, COIL_ERR_INVALID, "unknown operator format");
-    if (o->format == COIL_FORMAT_TOEPLITZ && (g->kind != COIL_GEOM_SOLENOID || o->precision != PREC_FP32))
-        return fail(c, COIL_ERR_INVALID, "the Toeplitz format needs a solenoid and FP32 precision");
+    if (o->format != COIL_FORMAT_DENSE && (g->kind != COIL_GEOM_SOLENOID || o->precision != PREC_FP32))
+        return fail(c, COIL_ERR_INVALID, "the Toeplitz formats need a solenoid and FP32 precision");
+    if (o->format == COIL_FORMAT_TOEPLITZ_TC && g->n_turns > kTcMaxTurns)
+        return fail(c, COIL_ERR_INVALID, "the tensor-core Toeplitz format takes at most 224 turns");
     if (g->kind == COIL_GEOM_SOLENOID) {
         if (g->n_layers < 1 || g->n_turns < 1 || g->n_sub < 1)
             return fail(c, COIL_ERR_INVALID, "solenoid needs n_layers, n_turns, n_sub >= 1");
@@ -418,11 +422,16 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     // operator: table of distinct entries, dense far part, FP64 near blocks
     size_t esz = o->precision == PREC_FP64 ? 8 : (o->precision == PREC_FP32 ? 4 : 2);
     const bool toep = o->format == COIL_FORMAT_TOEPLITZ;
-    h.op_format = toep ? 1 : 0;
+    const bool tcf = o->format == COIL_FORMAT_TOEPLITZ_TC;
+    h.op_format = toep ? 1 : (tcf ? 2 : 0);
     h.C = C;
     h.NT = NT;
     const size_t tab_entries = (size_t)C * C * (2 * (size_t)NT - 1);
-    const size_t op_alloc = toep ? tab_entries * sizeof(float) : (size_t)N * ld * esz;
+    TcShape tsh{};
+    if (tcf && !tc_shape(C, NT, c->n_sm, &tsh))
+        return fail(c, COIL_ERR_INVALID, "coil shape not supported by the tensor-core Toeplitz format");
+    const size_t op_alloc = toep ? tab_entries * sizeof(float)
+                                 : (tcf ? tc_table_halves(tsh) * sizeof(__half) : (size_t)N * ld * esz);
     void* M = nullptr;
     {
         cudaError_t e = cudaMalloc(&M, op_alloc);
@@ -438,6 +447,17 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     if (toep) {
         TRY(dalloc(c, &h.tpart, toeplitz_part_floats(C, NT), "Toeplitz partial sums"));
         TRY(dalloc(c, &h.pT, N, "transposed operator input"));
+    }
+    if (tcf) {
+        c->tc = new (std::nothrow) TcPlan();
+        if (!c->tc) return fail(c, COIL_ERR_OOM, "host allocation of the tensor-core plan failed");
+        TcPlan& P = *c->tc;
+        P.sh = tsh;
+        P.smem = tc_smem_bytes(tsh);
+        P.t16 = static_cast<__half*>(M);
+        TRY(dalloc(c, &P.p16, 2 * (size_t)tsh.Cp * NT, "split operator input"));
+        TRY(dalloc(c, &P.part, (size_t)tsh.n_chunks * N, "tensor-core partial sums"));
+        TRY(dalloc(c, &P.pmax, (size_t)tsh.n_pmax, "input maxima"));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
@@ -462,6 +482,11 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         h.tab32 = static_cast<const float*>(M);
         h.Mfar = nullptr;
         CK(launch_toeplitz_table(tab, C, NT, B, static_cast<float*>(M), c->stream), "Toeplitz table");
+    } else if (tcf) {
+        h.Mfar = nullptr;
+        double* scratch;
+        TRY(dalloc(c, &scratch, 1024, "scratch"));
+        CK(tc_build_table(c->tc, tab, B, scratch, c->stream), "tensor-core Toeplitz table");
     } else {
         h.Mfar = M;
         CK(launch_expand(tab, C, NT, B, N, h.ld, o->precision, M, c->stream), "expand");
@@ -489,6 +514,14 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     CK(cudaHostAlloc(&c->pinned, sizeof(Scalars), cudaHostAllocDefault), "pinned scalars");
     memset(c->pinned, 0, sizeof(Scalars));
     CK(cudaMemcpyAsync(c->d, &h, sizeof(CoilDev), cudaMemcpyHostToDevice, c->stream), "descriptor");
+    if (c->tc) {
+        c->tc->d = c->d;
+        const char* why = "";
+        if (tc_encode_maps(c->tc, &why) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, COIL_ERR_CUDA, why);
+        }
+    }
     CK(cudaStreamSynchronize(c->stream), "create");
     return COIL_OK;
 }
@@ -540,6 +573,7 @@ size_t block_smem(const CoilDev& h) { return ((size_t)h.B * h.B + 2 * (size_t)h.
 // Launch geometry of one step for one coil or a batch (grid row y = coil).
 struct Launch {
     const CoilDev* d = nullptr;
+    std::vector<const TcPlan*> tc;   // format 2: one plan per coil
     int n = 1;
     int prec = 0;
     int maxW = 0, maxN = 0, maxGr = 0, maxGz = 0;
@@ -568,12 +602,20 @@ Launch single_launch(coil_t* c) {
     L.format = h.op_format;
     L.maxC = h.C;
     L.maxNT = h.NT;
+    if (c->tc) L.tc.push_back(c->tc);
     return L;
 }
 
 // The far-operator apply of either storage format.
 cudaError_t launch_far(const Launch& L, int which) {
     if (L.format == 1) return launch_toeplitz(L.d, L.n, L.maxC, L.maxNT, L.maxN, L.n_sm, L.s);
+    if (L.format == 2) {
+        for (const TcPlan* P : L.tc) {
+            cudaError_t e = launch_toeplitz_tc(*P, L.s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     return launch_gemv(L.d, L.n, L.prec, L.maxN, which, L.n_sm, L.s);
 }
 
@@ -669,6 +711,7 @@ coil_status run_step(coil_t* c) {
         chunk = 1;
     }
     int st = c->pinned->status;
+    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
     if (!c->pinned->done || st == ST_NOT_CONVERGED)
         return fail(c, COIL_ERR_NOT_CONVERGED, "per-step solve did not converge within maxit iterations");
     if (st == ST_NONFINITE)
@@ -698,6 +741,10 @@ coil_status apply_plain(coil_t* c, const double* dev_p) {
     CK(cudaGetLastError(), "apply");
     h.dt = dt_save;
     TRY(sync_descriptor(c));
+    if (h.op_format == 2) {
+        TRY(read_scalars(c));
+        if (c->pinned->status == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+    }
     return COIL_OK;
 }
 
@@ -820,6 +867,7 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.smem = std::max(L.smem, block_smem(ci->h));
         L.maxC = std::max(L.maxC, ci->h.C);
         L.maxNT = std::max(L.maxNT, ci->h.NT);
+        if (ci->tc) L.tc.push_back(ci->tc);
     }
     // descriptors and the gathered status live in one device block per call
     CoilDev* dd = nullptr;
@@ -863,7 +911,8 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
                 ci->last_iters = it > 0 ? it : 1;
                 ci->pcg_iters += it;
             } else if (first_err == COIL_OK) {
-                first_err = (!done || st == ST_NOT_CONVERGED) ? COIL_ERR_NOT_CONVERGED : COIL_ERR_NONFINITE;
+                first_err = st == ST_KERNEL ? COIL_ERR_CUDA
+                            : (!done || st == ST_NOT_CONVERGED) ? COIL_ERR_NOT_CONVERGED : COIL_ERR_NONFINITE;
                 fail(ci, first_err, "batched step: this coil's solve failed; its state was kept");
             }
         }
@@ -999,6 +1048,22 @@ coil_status coil_read_operator(coil_t* c, double* M) {
                 M[i * N + j] = tab[(size_t)(d + (long long)NT - 1) * C * C + (i % C) * C + (j % C)];
             }
     }
+    if (h.op_format == 2) {
+        // (hi + lo) 2^-exT of the split FP16 table [half][offset][c][c' < Cp]
+        const TcShape& sh = c->tc->sh;
+        size_t C = sh.C, Cp = sh.Cp, NT = sh.NT;
+        size_t half_n = tc_table_halves(sh) / 2;
+        std::vector<__half> t16(2 * half_n);
+        CK(cudaMemcpy(t16.data(), c->tc->t16, t16.size() * sizeof(__half), cudaMemcpyDeviceToHost),
+           "read operator");
+        const double inv = ldexp(1.0, -c->tc->exT);
+        for (size_t i = 0; i < N; ++i)
+            for (size_t j = 0; j < N; ++j) {
+                long long d = (long long)(i / C) - (long long)(j / C);
+                size_t k = ((size_t)(d + (long long)NT - 1) * C + (i % C)) * Cp + (j % C);
+                M[i * N + j] = ((double)__half2float(t16[k]) + (double)__half2float(t16[half_n + k])) * inv;
+            }
+    }
     for (size_t i = 0; i < N && h.op_format == 0; ++i) {
         CK(cudaMemcpy(row.data(), (const unsigned char*)h.Mfar + i * ld * esz, ld * esz, cudaMemcpyDeviceToHost),
            "read operator");
@@ -1128,6 +1193,7 @@ void coil_destroy(coil_t* c) {
     for (void* p : c->allocs) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->d) cudaFree(c->d);
+    delete c->tc;
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1254,6 +1320,7 @@ coil_status adjoint_solve(coil_t* c) {
         chunk = 1;
     }
     int st = c->pinned->status;
+    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
     if (!c->pinned->done || st == ST_NOT_CONVERGED)
         return fail(c, COIL_ERR_NOT_CONVERGED, "adjoint solve did not converge within maxit iterations");
     if (st == ST_NONFINITE) return fail(c, COIL_ERR_NONFINITE, "non-finite value in the adjoint solve");

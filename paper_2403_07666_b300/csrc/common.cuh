@@ -17,7 +17,8 @@ constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one
 
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_BF16 = 2 };
 
-enum Status { ST_OK = 0, ST_NOT_CONVERGED = 4, ST_NONFINITE = 5 };
+// ST_KERNEL: a bounded wait inside a kernel ran out (the kernel stopped early).
+enum Status { ST_OK = 0, ST_NOT_CONVERGED = 4, ST_NONFINITE = 5, ST_KERNEL = 6 };
 
 // Per-coil scalars that live on the device (written by kernels, read back by
 // the host only between launches).
@@ -49,7 +50,7 @@ struct CoilDev {
     // block-Toeplitz format of a regular solenoid: far operator entries
     // tab32[(t_i - t_j + NT - 1)][c_i][c_j] (FP32, intra-wire entries zero),
     // element e = t * C + c; partial sums per (t tile, d chunk) in tpart
-    int op_format;                // 0 dense, 1 Toeplitz
+    int op_format;                // 0 dense, 1 Toeplitz (FP32), 2 Toeplitz (tensor cores)
     int C, NT;
     const float *tab32;
     float *tpart;

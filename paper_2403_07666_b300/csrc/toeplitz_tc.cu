@@ -1,0 +1,617 @@
+// Tensor-core block-Toeplitz far-operator apply (tcgen05 MMA, TMA staging).
+//
+// The operator is the block-Toeplitz one of a regular solenoid (the coaxial-
+// loop inductance depends on r, r' and z - z' only):
+//
+//     y[t][c] = sum_d sum_c' T_d[c][c'] p[t - d][c'],   d = t_i - t_j,
+//
+// element e = t C + c.  For one turn offset d this is a (C x C) by
+// (C x valid turns) product, so a CTA that owns a tile of 128 channels c and a
+// chunk of offsets runs, on the tensor cores,
+//
+//     D[c][t] += A_d[c][k] B_d[t][k],   A_d = T_d tile,  B_d[t][.] = p[t - d][.],
+//
+// with the turn index t as the MMA's N dimension.  For offset d only turns
+// max(0, d) <= t < min(NT, NT + d) have a source row; each MMA covers exactly
+// those turns (rounded out to 16 columns), writes its accumulator at TMEM
+// column t, and reads its B operand as a window, starting at row t - d, of one
+// staged copy of p (rows -16 .. NT + 15, zero outside the winding).  So the
+// Toeplitz shift costs no copy and no padded work, and every table entry is
+// read from HBM once per apply.
+//
+// Precision: entries and inputs are scaled by powers of two (max |T| and
+// max |p| below 2^14) and split v = hi + lo into two FP16 numbers; the three
+// products hi*hi + hi*lo + lo*hi keep about 22 significant bits, the FP32
+// class.  The tensor cores' FP32 accumulation does not round to nearest, so
+// its error grows with the number of MMAs added into one accumulator; here an
+// accumulator takes only one stage (one offset, one 64-channel k block: 12
+// MMAs), after which the epilogue warps add it into FP32 registers (round to
+// nearest) and hand it back.  Up to four TMEM accumulators rotate so the MMAs
+// of the next stages run while one is drained.  The offset chunks are summed
+// in FP64 in a fixed order, so the result is deterministic.  The table takes
+// 2 x 2 bytes per entry, as many as FP32.
+//
+// CTA roles (320 threads): warp 0 issues the TMA loads, warp 1 owns the TMEM
+// accumulators and issues the MMAs, warps 2-9 drain the accumulators (lane
+// quadrant warp % 4, even or odd 16-column groups).  Every wait on an
+// mbarrier is bounded: on a timeout the CTA raises an abort flag, the others
+// stop issuing, the copies and MMAs already in flight are waited for (again
+// bounded), the TMEM is freed, and the coil's status word reports the failure
+// to the host.
+#include "toeplitz_tc.h"
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace cq {
+
+constexpr int kTcM = 128;                        // channels per tile (MMA M)
+constexpr int kTcK = 64;                         // channels per k block (one 128-byte FP16 row)
+constexpr int kTcPad = 16;                       // zero rows staged above and below the winding
+constexpr int kTcEpiWarps = 8;                   // epilogue warps: 4 lane quadrants x 2 column parities
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
+constexpr int kTcGroups = 7;                     // 16-column groups per epilogue warp (NT <= 224)
+constexpr uint32_t kTcAStage = 2u * kTcM * kTcK * 2u;   // hi + lo table tiles, 32 KB
+constexpr int kTcSmemLimit = 227 * 1024;         // dynamic shared memory per CTA (opt-in maximum)
+constexpr long long kTcWait = 1LL << 31;         // cycles before a wait gives up (~1 s)
+__host__ __device__ constexpr int kTcBars(int stages) { return 2 * stages + 13; }
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity; false on abort or after kTcWait
+// cycles (then the abort flag is raised).
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kTcWait) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+// The same, ignoring the abort flag (used to retire work already in flight).
+__device__ __noinline__ bool mbar_wait_final(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, layout 0 (no swizzle) or 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
+}
+// Instruction descriptor of kind::f16: FP16 A and B (both K-major), FP32 D,
+// M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16_zero(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// The apply
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const CoilDev* __restrict__ cd, const TcShape sh, float* __restrict__ part) {
+    const CoilDev& c = *cd;
+    if (c.sc->done) return;
+    extern __shared__ uint8_t tc_smem[];
+    const uint32_t raw = su32(tc_smem);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = tc_smem + (base - raw);
+    const uint32_t b_stage = 256u * (uint32_t)sh.NR;             // hi + lo staged p, bytes
+    const uint32_t b_pitch = (b_stage + 1023u) & ~1023u;
+    const uint32_t sB = base;                                     // 2 stages
+    const uint32_t sA = base + 2u * b_pitch;                      // sh.stages x 32 KB
+    const uint32_t bar_off = 2u * b_pitch + (uint32_t)sh.stages * kTcAStage;
+    const uint32_t sBar = base + bar_off;
+    const int S = sh.stages;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + bar_off + 8 * kTcBars(S));
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + bar_off + 8 * kTcBars(S) + 4);
+    // barriers: a_full[S], a_empty[S], b_full[2], b_empty[2], acc_full[4], acc_empty[4], mma_done
+    const uint32_t a_full = sBar, a_empty = sBar + 8u * S;
+    const uint32_t b_full = sBar + 16u * S, b_empty = b_full + 16u;
+    const uint32_t acc_full = b_empty + 16u, acc_empty = acc_full + 32u;
+    const uint32_t mma_done = acc_empty + 32u;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ct = blockIdx.x % sh.n_ct, chunk = blockIdx.x / sh.n_ct;
+    const int c0 = ct * kTcM;
+    const int ndist = 2 * sh.NT - 1;
+    const int d_lo = -(sh.NT - 1) + (int)((long long)chunk * ndist / sh.n_chunks);
+    const int d_hi = -(sh.NT - 1) + (int)((long long)(chunk + 1) * ndist / sh.n_chunks);
+    const int n_acc = sh.n_acc;
+    const uint32_t acc_cols = (uint32_t)sh.acc_cols;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kTcBars(S); ++b) {
+            const uint32_t bar = sBar + 8u * b;
+            // acc_empty: one arrival per epilogue warp; the others: one arrival (+ bytes)
+            mbar_init(bar, (bar >= acc_empty && bar < acc_empty + 32u) ? (uint32_t)kTcEpiWarps : 1u);
+        }
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(su32(tslot), (uint32_t)sh.ncols);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer: per k block one staged p copy, then the table tiles of every offset
+        int sa = 0, sb = 0;
+        uint32_t pa = 0, pb = 0;
+        uint32_t a_used = 0, a_par = 0, b_used = 0, b_par = 0;   // bit s: stage s loaded / its parity
+        bool ok = true;
+        for (int kb = 0; kb < sh.n_kb && ok; ++kb) {
+            ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
+            if (!ok) break;
+            mbar_expect_tx(b_full + 8u * sb, b_stage);
+            tma_load_4d(sB + (uint32_t)sb * b_pitch, &tmB, 0, -kTcPad, kb * (kTcK / 8), 0, b_full + 8u * sb);
+            b_used |= 1u << sb;
+            b_par = (b_par & ~(1u << sb)) | (pb << sb);
+            if (++sb == 2) { sb = 0; pb ^= 1u; }
+            for (int d = d_lo; d < d_hi; ++d) {
+                ok = mbar_wait(a_empty + 8u * sa, pa ^ 1u, abort_flag);
+                if (!ok) break;
+                mbar_expect_tx(a_full + 8u * sa, kTcAStage);
+                tma_load_4d(sA + (uint32_t)sa * kTcAStage, &tmA, kb * kTcK, c0, d + sh.NT - 1, 0, a_full + 8u * sa);
+                a_used |= 1u << sa;
+                a_par = (a_par & ~(1u << sa)) | (pa << sa);
+                if (++sa == S) { sa = 0; pa ^= 1u; }
+            }
+        }
+        // retire the copies in flight (only the latest load of a stage can be)
+        for (int s = 0; s < S; ++s)
+            if (a_used >> s & 1u) mbar_wait_final(a_full + 8u * s, a_par >> s & 1u, kTcWait);
+        for (int s = 0; s < 2; ++s)
+            if (b_used >> s & 1u) mbar_wait_final(b_full + 8u * s, b_par >> s & 1u, kTcWait);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer: stage (kb, d) accumulates into TMEM accumulator i (round robin),
+        // its first MMA overwriting the columns it covers
+        int sa = 0, sb = 0, ai = 0;
+        uint32_t pa = 0, pb = 0, pe = 0;   // pe bit i: phase of acc_empty[i]
+        bool ok = true;
+        for (int kb = 0; kb < sh.n_kb && ok; ++kb) {
+            ok = mbar_wait(b_full + 8u * sb, pb, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t bh = sB + (uint32_t)sb * b_pitch;
+            const uint32_t bl = bh + 128u * (uint32_t)sh.NR;
+            for (int d = d_lo; d < d_hi; ++d) {
+                ok = mbar_wait(a_full + 8u * sa, pa, abort_flag);
+                if (ok) ok = mbar_wait(acc_empty + 8u * ai, ((pe >> ai) & 1u) ^ 1u, abort_flag);
+                if (!ok) break;
+                pe ^= 1u << ai;
+                tc_fence_after();
+                const int t_first = d > 0 ? d : 0;
+                const int t_end = d < 0 ? sh.NT + d : sh.NT;
+                const int ts = t_first & ~15;
+                const int n = (t_end - ts + 15) & ~15;
+                const uint32_t idesc = idesc_f16(n);
+                const uint32_t dcol = tmem + (uint32_t)ai * acc_cols + (uint32_t)ts;
+                const uint32_t row0 = (uint32_t)(ts - d + kTcPad);
+                const uint32_t ah = sA + (uint32_t)sa * kTcAStage;
+                const uint32_t al = ah + (uint32_t)kTcM * 128u;
+#pragma unroll
+                for (int s = 0; s < kTcK / 16; ++s) {
+                    const uint64_t a_hi = sdesc(ah + 32u * s, 16u, 1024u, 2u);
+                    const uint64_t a_lo = sdesc(al + 32u * s, 16u, 1024u, 2u);
+                    const uint32_t boff = (uint32_t)(2 * s) * 16u * (uint32_t)sh.NR + 16u * row0;
+                    const uint64_t b_hi = sdesc(bh + boff, 16u * (uint32_t)sh.NR, 128u, 0u);
+                    const uint64_t b_lo = sdesc(bl + boff, 16u * (uint32_t)sh.NR, 128u, 0u);
+                    mma_f16(dcol, a_hi, b_hi, idesc, s > 0 ? 1u : 0u);
+                    mma_f16(dcol, a_hi, b_lo, idesc, 1u);
+                    mma_f16(dcol, a_lo, b_hi, idesc, 1u);
+                }
+                mma_commit(a_empty + 8u * sa);
+                mma_commit(acc_full + 8u * ai);
+                if (++sa == S) { sa = 0; pa ^= 1u; }
+                if (++ai == n_acc) ai = 0;
+            }
+            mma_commit(b_empty + 8u * sb);
+            if (++sb == 2) { sb = 0; pb ^= 1u; }
+        }
+        // every MMA issued (also after an abort) completes before the TMEM is freed
+        mma_commit(mma_done);
+        if (!mbar_wait_final(mma_done, 0u, kTcWait)) *abort_flag = 1;
+    } else if (warp >= 2) {
+        // ---- epilogue: each stage's accumulator is added into FP32 registers (lane
+        // quadrant warp % 4, column groups of parity h), then released to the MMAs
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const int cc = c0 + 32 * q + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        float acc[kTcGroups][16];
+#pragma unroll
+        for (int g = 0; g < kTcGroups; ++g)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[g][j] = 0.f;
+        int ai = 0;
+        uint32_t pf = 0;
+        bool ok = true;
+        for (int kb = 0; kb < sh.n_kb && ok; ++kb) {
+            for (int d = d_lo; d < d_hi; ++d) {
+                ok = __all_sync(0xffffffffu, mbar_wait(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag));
+                if (!ok) break;
+                pf ^= 1u << ai;
+                tc_fence_after();
+                const int t_first = d > 0 ? d : 0;
+                const int t_end = d < 0 ? sh.NT + d : sh.NT;
+                const int g_lo = t_first >> 4, g_hi = (t_end + 15) >> 4;
+                const uint32_t src = lane_base + (uint32_t)ai * acc_cols;
+#pragma unroll
+                for (int gi = 0; gi < kTcGroups; ++gi) {
+                    const int g = 2 * gi + h;
+                    if (g >= g_lo && g < g_hi) {
+                        float v[16];
+                        tmem_ld16(src + 16u * (uint32_t)g, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[gi][j] += v[j];
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + 8u * ai);
+                if (++ai == n_acc) ai = 0;
+            }
+        }
+        if (ok && !*abort_flag && cc < sh.C) {
+            float* out = part + (size_t)chunk * sh.N + cc;
+#pragma unroll
+            for (int gi = 0; gi < kTcGroups; ++gi) {
+                const int t0 = 16 * (2 * gi + h);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (t0 + j < sh.NT) out[(size_t)(t0 + j) * sh.C] = acc[gi][j];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicExch(&c.sc->status, (int)ST_KERNEL);
+        atomicExch(&c.sc->done, 1);
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, (uint32_t)sh.ncols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Input split, reduction, table
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float block_max_f(float v) {
+    __shared__ float sm[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < (int)(blockDim.x >> 5) ? sm[l] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (l == 0) sm[0] = v;
+    }
+    __syncthreads();
+    return sm[0];
+}
+
+// Power-of-two exponent that brings a maximum m below 2^14 (0 if m is zero,
+// not finite or not a number).
+__host__ __device__ inline int tc_exponent(double m) {
+    if (!(m > 0.0) || !(m < 1.0e300)) return 0;
+    int e = 0;
+    frexp(m, &e);                  // m < 2^e
+    int x = 14 - e;
+    return x > 120 ? 120 : (x < -120 ? -120 : x);
+}
+
+// Block maxima of |p| (p = the FP32 operator input pf).
+__global__ void k_tc_pmax(const CoilDev* __restrict__ cd, float* __restrict__ pmax) {
+    const CoilDev& c = *cd;
+    if (c.sc->done) return;
+    float m = 0.f;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c.N; e += gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(c.pf[e]));
+    m = block_max_f(m);
+    if (threadIdx.x == 0) pmax[blockIdx.x] = m;
+}
+
+__device__ __forceinline__ int input_exponent(const float* pmax, int n) {
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, pmax[i]);
+    return tc_exponent((double)block_max_f(m));
+}
+
+// p -> FP16 hi/lo in [half][c'/8][t][c' % 8] order, scaled by 2^exP.
+__global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ pmax,
+                           __half* __restrict__ p16) {
+    const CoilDev& c = *cd;
+    if (c.sc->done) return;
+    const float s = ldexpf(1.f, input_exponent(pmax, sh.n_pmax));
+    const int total = sh.Cp * sh.NT;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int j = idx & 7, rest = idx >> 3;
+        const int t = rest % sh.NT, ch = rest / sh.NT;
+        const int cc = 8 * ch + j;
+        const float v = cc < sh.C ? c.pf[(size_t)t * sh.C + cc] * s : 0.f;
+        const __half hi = __float2half_rn(v);
+        p16[idx] = hi;
+        p16[total + idx] = __float2half_rn(v - __half2float(hi));
+    }
+}
+
+// q[e] = sum over the offset chunks (fixed order, FP64), unscaled.
+__global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ pmax,
+                            const float* __restrict__ part, int exT) {
+    const CoilDev& c = *cd;
+    if (c.sc->done) return;
+    const double inv = ldexp(1.0, -(exT + input_exponent(pmax, sh.n_pmax)));
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sh.N; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < sh.n_chunks; ++k) s += (double)part[(size_t)k * sh.N + e];
+        c.qv[e] = s * inv;
+    }
+}
+
+__global__ void k_tc_absmax(const double* __restrict__ tab, long long n, double* __restrict__ out) {
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(tab[i]));
+    m = warp_max(m);
+    __shared__ double sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sm[w]);
+        out[blockIdx.x] = m;
+    }
+}
+
+// FP64 table [offset][c][c'] -> FP16 hi/lo [half][offset][c][c' < Cp] scaled
+// by 2^exT; intra-wire entries of offset 0 are zero (applied from the FP64
+// near blocks), padding columns c' >= C are zero.
+__global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int wire_div, int exT,
+                           __half* __restrict__ t16) {
+    const long long total = (long long)(2 * sh.NT - 1) * sh.C * sh.Cp;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int cj = (int)(idx % sh.Cp);
+        const long long rest = idx / sh.Cp;
+        const int ci = (int)(rest % sh.C);
+        const int dd = (int)(rest / sh.C);
+        double v = cj < sh.C ? tab[((long long)dd * sh.C + ci) * sh.C + cj] : 0.0;
+        if (dd == sh.NT - 1 && ci / wire_div == cj / wire_div) v = 0.0;
+        v = ldexp(v, exT);
+        const __half hi = __double2half(v);
+        t16[idx] = hi;
+        t16[total + idx] = __double2half(v - (double)__half2float(hi));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+size_t tc_smem_bytes(const TcShape& sh) {
+    size_t b_pitch = ((size_t)256 * sh.NR + 1023) & ~(size_t)1023;
+    return 1024 + 2 * b_pitch + (size_t)sh.stages * kTcAStage + 8 * (size_t)kTcBars(sh.stages) + 16;
+}
+
+bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
+    if (C < 1 || NT < 1 || NT > kTcMaxTurns) return false;
+    TcShape s{};
+    s.C = C;
+    s.Cp = (C + 7) & ~7;
+    s.NT = NT;
+    s.NR = NT + 2 * kTcPad;
+    s.N = C * NT;
+    s.n_ct = (C + kTcM - 1) / kTcM;
+    int ndist = 2 * NT - 1;
+    int ch = n_sm / s.n_ct;
+    s.n_chunks = ch < 1 ? 1 : (ch > ndist ? ndist : ch);
+    s.n_kb = (s.Cp + kTcK - 1) / kTcK;
+    int used = (NT + 15) & ~15;
+    s.acc_cols = 32;
+    while (s.acc_cols < used) s.acc_cols *= 2;
+    s.n_acc = 512 / s.acc_cols > 4 ? 4 : 512 / s.acc_cols;   // 2..4 accumulators in 512 columns
+    s.ncols = s.n_acc * s.acc_cols;
+    s.n_pmax = (s.N + 1023) / 1024;
+    if (s.n_pmax > n_sm) s.n_pmax = n_sm;
+    const size_t limit = kTcSmemLimit;
+    s.stages = 6;
+    while (s.stages > 2 && tc_smem_bytes(s) > limit) --s.stages;
+    if (tc_smem_bytes(s) > limit) return false;
+    *sh = s;
+    return true;
+}
+
+size_t tc_table_halves(const TcShape& sh) { return 2 * (size_t)(2 * sh.NT - 1) * sh.C * sh.Cp; }
+
+cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* scratch, cudaStream_t s) {
+    const TcShape& sh = P->sh;
+    long long n = (long long)(2 * sh.NT - 1) * sh.C * sh.C;
+    const int nb = 512;
+    k_tc_absmax<<<nb, 256, 0, s>>>(tab, n, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double hm[nb];
+    e = cudaMemcpyAsync(hm, scratch, sizeof(hm), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    double m = 0.0;
+    for (int i = 0; i < nb; ++i) m = hm[i] > m ? hm[i] : m;
+    P->exT = tc_exponent(m);
+    long long total = (long long)(2 * sh.NT - 1) * sh.C * sh.Cp;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 148LL * 64) blocks = 148LL * 64;
+    k_tc_table<<<(unsigned)blocks, 256, 0, s>>>(tab, sh, wire_div, P->exT, P->t16);
+    return cudaGetLastError();
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+}  // namespace
+
+cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
+    EncodeTiled enc = encoder();
+    if (!enc) {
+        *why = "cuTensorMapEncodeTiled is not available from the driver";
+        return cudaErrorNotSupported;
+    }
+    const TcShape& sh = P->sh;
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)sh.Cp, (cuuint64_t)sh.C, (cuuint64_t)(2 * sh.NT - 1), 2};
+        const cuuint64_t strides[3] = {(cuuint64_t)sh.Cp * 2, (cuuint64_t)sh.C * sh.Cp * 2,
+                                       (cuuint64_t)(2 * sh.NT - 1) * sh.C * sh.Cp * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM, 1, 2};
+        CUresult r = enc(&P->tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->t16, dims, strides, box, ones,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "encoding the table tensor map failed";
+            return cudaErrorInvalidValue;
+        }
+    }
+    {
+        const cuuint64_t dims[4] = {8, (cuuint64_t)sh.NT, (cuuint64_t)(sh.Cp / 8), 2};
+        const cuuint64_t strides[3] = {16, (cuuint64_t)sh.NT * 16, (cuuint64_t)(sh.Cp / 8) * sh.NT * 16};
+        const cuuint32_t box[4] = {8, (cuuint32_t)sh.NR, (cuuint32_t)(kTcK / 8), 2};
+        CUresult r = enc(&P->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->p16, dims, strides, box, ones,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "encoding the input tensor map failed";
+            return cudaErrorInvalidValue;
+        }
+    }
+    // the attribute belongs to the kernel, not to the coil: set the largest size
+    // any coil may take, so that every coil's launch fits
+    cudaError_t e = cudaFuncSetAttribute(k_toeplitz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLimit);
+    if (e != cudaSuccess) *why = "setting the shared-memory size of the tensor-core apply failed";
+    return e;
+}
+
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s) {
+    const TcShape& sh = P.sh;
+    k_tc_pmax<<<sh.n_pmax, 1024, 0, s>>>(P.d, P.pmax);
+    int total = sh.Cp * sh.NT;
+    int sb = (total + 255) / 256;
+    k_tc_split<<<sb, 256, 0, s>>>(P.d, sh, P.pmax, P.p16);
+    k_toeplitz_tc<<<sh.n_ct * sh.n_chunks, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.d, sh, P.part);
+    int rb = (sh.N + 255) / 256;
+    if (rb > 148 * 8) rb = 148 * 8;
+    k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.pmax, P.part, P.exT);
+    return cudaGetLastError();
+}
+
+}  // namespace cq

@@ -1,0 +1,52 @@
+// Host-side plan of the tensor-core block-Toeplitz apply (one per coil).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace cq {
+
+// Sizes of one coil's tensor-core apply (all fixed at setup).
+struct TcShape {
+    int C, Cp, NT, NR;          // channels per turn row, C rounded up to 8, turn rows, staged p rows
+    int N;                      // elements (NT C)
+    int n_ct, n_chunks, n_kb;   // 128-channel tiles, turn-offset chunks, 64-channel k blocks
+    int stages;                 // table tiles in flight per CTA
+    int acc_cols, n_acc;        // TMEM columns per accumulator, accumulators (stages alternate)
+    int ncols;                  // TMEM columns allocated per CTA (n_acc acc_cols)
+    int n_pmax;                 // blocks of the max |p| pass
+};
+
+struct TcPlan {
+    CUtensorMap tmA;            // split table: [half][offset][c][c'] FP16, 128-byte swizzle
+    CUtensorMap tmB;            // split input: [half][c'/8][t][c' % 8] FP16, no swizzle
+    TcShape sh;
+    const CoilDev* d = nullptr; // device descriptor of the coil
+    __half* t16 = nullptr;      // 2 (2 NT - 1) C Cp
+    __half* p16 = nullptr;      // 2 Cp NT
+    float* part = nullptr;      // n_chunks N partial sums
+    float* pmax = nullptr;      // n_pmax block maxima of |p|
+    int exT = 0;                // table scale 2^exT
+    size_t smem = 0;            // dynamic shared memory per CTA
+};
+
+constexpr int kTcMaxTurns = 224;   // staged p rows NT + 32 fit one TMA box (<= 256)
+
+// Fill the shape for C channels, NT turns on n_sm SMs; false if unsupported.
+bool tc_shape(int C, int NT, int n_sm, TcShape* sh);
+size_t tc_table_halves(const TcShape& sh);
+size_t tc_smem_bytes(const TcShape& sh);
+
+// Split the FP64 table (with intra-wire entries of offset 0 zeroed) into the
+// FP16 hi/lo table; `scratch` holds at least 1024 doubles.  Synchronizes s.
+cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* scratch, cudaStream_t s);
+// Encode the two tensor maps (after t16 and p16 are allocated).
+cudaError_t tc_encode_maps(TcPlan* P, const char** why);
+// q = M_far p for the coil of P (pf -> qv of its descriptor).
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s);
+
+}  // namespace cq

@@ -1,9 +1,9 @@
 """Parity at the benchmark's full size: the 96,000-element real-size coil in
-the configuration bench.py times (dense operator, PCG rtol 1e-9).  The oracle
-cannot solve this coil directly, so it checks outputs it can compute one at a
-time: operator columns, the field at sampled elements, the stationarity of
-the step's constrained solve on sampled wires, the whole heat step and the
-step's diagnostics."""
+the configurations bench.py times (tensor-core Toeplitz and dense operators,
+PCG rtol 1e-9).  The oracle cannot solve this coil directly, so it checks
+outputs it can compute one at a time: operator columns, the field at sampled
+elements, the stationarity of the step's constrained solve on sampled wires,
+the whole heat step and the step's diagnostics."""
 import numpy as np
 import pytest
 
@@ -47,9 +47,12 @@ def _stencil_B(geo, I, e):
 # FP32 storage rounds every operator entry by up to 2^-24; the flux carries that
 # rounding and the 3-point stencil differentiates it across one element, which
 # amplifies it about 10^3-fold in B (measured 1.7e-4 after 5 steps).
-@pytest.mark.parametrize("precision,tol_op,tol,tol_B", [("fp32", 2e-7, 2e-5, 5e-4),
-                                                         ("fp64", 1e-11, 1e-6, 1e-6)])
-def test_real_coil_sampled_parity(precision, tol_op, tol, tol_B):
+# The tensor-core Toeplitz form stores each entry as an FP16 hi + lo pair
+# (about 2^-22 relative) and is the operator format bench.py times.
+@pytest.mark.parametrize("precision,fmt,tol_op,tol,tol_B", [("fp32", "dense", 2e-7, 2e-5, 5e-4),
+                                                             ("fp32", "toeplitz_tc", 3e-7, 2e-5, 5e-4),
+                                                             ("fp64", "dense", 1e-11, 1e-6, 1e-6)])
+def test_real_coil_sampled_parity(precision, fmt, tol_op, tol, tol_B):
     from paper_2403_07666_b300.coil import Coil
     w = wl.real_coil()
     g = w.geometry
@@ -59,7 +62,7 @@ def test_real_coil_sampled_parity(precision, tol_op, tol, tol_B):
     assert N == 96000
     drive = dict(w.drive, ramp_rate=1e4)                 # non-trivial currents within a few steps
     p = w.material
-    with Coil.from_workload(w, precision=precision, rtol=1e-9) as c:
+    with Coil.from_workload(w, precision=precision, format=fmt, rtol=1e-9) as c:
         # operator columns (M symmetric: column j = row j)
         for j in (0, 12345, 48017, N - 1):
             e = np.zeros(N)

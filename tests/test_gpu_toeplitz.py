@@ -1,5 +1,7 @@
 """Block-Toeplitz storage of the far operator (regular solenoids): the same
-FP32 entries as the dense form, applied as a Toeplitz-structured product."""
+FP32 entries as the dense form applied as a Toeplitz-structured CUDA-core
+product ("toeplitz"), and the FP16 hi/lo split of the entries applied on the
+tensor cores ("toeplitz_tc")."""
 import numpy as np
 import pytest
 
@@ -23,6 +25,7 @@ def _coil(w, **kw):
 # C = 80, 108, 128, 16 channels per turn row: ragged channel tiles and k chunks;
 # 7, 5, 3, 40 turns: one or more row tiles with shifted rows falling outside.
 SHAPES = [(5, 7, 4), (3, 5, 6), (2, 3, 8), (1, 40, 4)]
+FORMATS = ["toeplitz", "toeplitz_tc"]
 
 
 @pytest.mark.parametrize("L,T,n", SHAPES)
@@ -34,20 +37,68 @@ def test_toeplitz_entries_equal_dense_fp32(L, T, n):
 
 
 @pytest.mark.parametrize("L,T,n", SHAPES)
-def test_toeplitz_apply_matches_oracle(L, T, n):
+def test_tc_entries_match_oracle(L, T, n):
+    """hi + lo of the FP16 split carries ~22 bits: entries within FP32 rounding."""
+    w = wl.random_coil(91, L, T, n)
+    M = oracle_of(w).M
+    with _coil(w, precision="fp32", format="toeplitz_tc") as t:
+        Mt = t.operator()
+        assert t.info().operator_bytes == 4 * (2 * T - 1) * (L * n * n) * (((L * n * n) + 7) // 8 * 8)
+    err = np.abs(Mt - M)
+    assert np.max(err / np.abs(M).max()) < 2.0 ** -22
+    assert rel(Mt, M) < 2e-7
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("L,T,n", SHAPES)
+def test_toeplitz_apply_matches_oracle(L, T, n, fmt):
     w = wl.random_coil(92, L, T, n)
     rng = np.random.default_rng(4)
     p = rng.standard_normal(w.n_elem)
-    with _coil(w, precision="fp32", format="toeplitz") as t:
+    with _coil(w, precision="fp32", format=fmt) as t:
         y = t.apply_operator(p)
+        y2 = t.apply_operator(p)
     assert rel(y, oracle_of(w).M @ p) < 2e-6
+    assert np.array_equal(y, y2)                          # fixed-order sums: deterministic
 
 
-def test_toeplitz_steps_match_oracle_and_dense():
+# tensor-core edge shapes: C = 147 (two channel tiles, the second ragged, C not a
+# multiple of 8), one turn (only offset 0), 224 turns (the largest staged copy of p),
+# a single-element wire, inputs spanning 30 decades and an input of zeros
+@pytest.mark.parametrize("L,T,n", [(3, 4, 7), (4, 1, 4), (1, 224, 2), (9, 6, 1)])
+def test_tc_edge_shapes(L, T, n):
+    w = wl.random_coil(98, L, T, n)
+    rng = np.random.default_rng(6)
+    M = oracle_of(w).M
+    with _coil(w, precision="fp32", format="toeplitz_tc") as t:
+        for p in (rng.standard_normal(w.n_elem),
+                  rng.standard_normal(w.n_elem) * 10.0 ** rng.uniform(-15, 15, w.n_elem),
+                  np.zeros(w.n_elem)):
+            y = t.apply_operator(p)
+            ref = M @ p
+            if not p.any():
+                assert not y.any()
+                continue
+            # per element: error within FP32-class rounding of the largest term
+            bound = 4e-6 * (np.abs(M) @ np.abs(p)) + 1e-300
+            assert np.all(np.abs(y - ref) <= bound)
+
+
+def test_tc_rejects_unsupported():
+    from paper_2403_07666_b300.coil import CoilError, ERR_INVALID
+    for w, prec in ((wl.random_coil(97, 1, 225, 2), "fp32"), (wl.random_coil(97, 2, 3, 4), "fp64"),
+                    (wl.random_coil(97, 2, 3, 4), "bf16")):
+        with pytest.raises(CoilError) as ei:
+            _coil(w, precision=prec, format="toeplitz_tc")
+        assert ei.value.status == ERR_INVALID
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_toeplitz_steps_match_oracle_and_dense(fmt):
     mtl = dict(wl.MATERIAL, Jc0=2e8)
     w = wl.random_coil(93, 5, 7, 4, ramp_rate=5e4, material=mtl)
     orc = oracle_of(w)
-    with _coil(w, precision="fp32", format="toeplitz", rtol=1e-9) as t, \
+    with _coil(w, precision="fp32", format=fmt, rtol=1e-9) as t, \
             _coil(w, precision="fp32", rtol=1e-9) as d:
         for k in range(6):
             t.step(20, w.drive)
@@ -58,14 +109,15 @@ def test_toeplitz_steps_match_oracle_and_dense():
         assert rel(t.currents(), d.currents()) < 1e-5        # both within 1e-5 of the oracle
 
 
-def test_toeplitz_batch_equals_single():
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_toeplitz_batch_equals_single(fmt):
     from paper_2403_07666_b300.coil import batch_step
     mtl = dict(wl.MATERIAL, Jc0=2e8)
     ws = [wl.random_coil(94, 3, 4, 4, ramp_rate=4e4, material=mtl),
           wl.random_coil(95, 5, 9, 6, ramp_rate=1e4, material=mtl),
           wl.random_coil(96, 2, 40, 4, ramp_rate=2e4, material=mtl)]
-    batch = [_coil(w, precision="fp32", format="toeplitz", rtol=1e-10) for w in ws]
-    alone = [_coil(w, precision="fp32", format="toeplitz", rtol=1e-10) for w in ws]
+    batch = [_coil(w, precision="fp32", format=fmt, rtol=1e-10) for w in ws]
+    alone = [_coil(w, precision="fp32", format=fmt, rtol=1e-10) for w in ws]
     try:
         batch_step(batch, 30, [w.drive for w in ws])
         for c, w in zip(alone, ws):
