@@ -239,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     hbm, peak_kind = peaks()
     t0 = time.perf_counter()
-    toep = args.format == "toeplitz"
+    toep = args.format != "dense"
     coil = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
                               stream=stream.cuda_stream, profile=True, format=args.format)
     setup_s = time.perf_counter() - t0
@@ -262,23 +262,7 @@ def run_ours(args, rank, world, local_rank):
     op_bytes = int(info.operator_bytes)
     applies = op_launches / args.steps
     launches = int(inf.kernel_launches)
-    if toep:
-        flops = 2.0 * N * N
-        achieved = flops / (gemv_ms / 1e3) / 1e12
-        prof = PROFILED_TRAFFIC.get("toeplitz")
-        traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic,
-                    "kernel": "k_toeplitz_f32 (+transpose, reduce)",
-                    "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz",
-                    "avg_launch_ms": gemv_ms, "flops_per_launch": flops, "table_bytes": op_bytes}
-    else:
-        achieved = op_bytes / (gemv_ms / 1e3) / 1e9
-        prof = PROFILED_TRAFFIC.get(args.precision)
-        traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": traffic, "kernel": f"k_gemv_{args.precision}",
-                    "peak_kind": peak_kind, "avg_launch_ms": gemv_ms, "bytes_per_launch": op_bytes}
+    roofline = roofline_of(args.format, args.precision, N, op_bytes, gemv_ms, hbm, peak_kind)
 
     # end to end through the public API: host buffers, copies inside the region
     import torch as _t
@@ -322,9 +306,11 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16": "bf16-stored operator, fp32 products, fp64 solve/accumulation",
-                  "fp32": "fp32-stored operator, fp32 products, fp64 solve/accumulation",
-                  "fp64": "f64"}[args.precision],
+        "dtype": ("fp16 hi+lo split operator and input (fp32-class), tensor-core products with fp32 "
+                  "accumulation, fp64 solve/accumulation" if args.format == "toeplitz_tc" else
+                  {"bf16": "bf16-stored operator, fp32 products, fp64 solve/accumulation",
+                   "fp32": "fp32-stored operator, fp32 products, fp64 solve/accumulation",
+                   "fp64": "f64"}[args.precision]),
         "data": "synthetic (seeded coil geometry, lognormal Jc factor, uniform strain)",
         "config": {"workload": w.name, "n_elem": N, "n_layers": w.geometry["n_layers"],
                    "n_turns": w.geometry["n_turns"], "n_sub": w.geometry["n_sub"],
@@ -343,11 +329,9 @@ def run_ours(args, rank, world, local_rank):
     if fp64 is not None:
         line["fp64"] = fp64
         line["mixed_over_fp64"] = value / fp64["value"]
-    if args.other_format:
-        if toep:
-            line["dense"] = dense_leg(args, local_rank, stream, torch)
-        else:
-            line["toeplitz"] = toeplitz_leg(args, local_rank, stream, torch)
+    if args.other_format and args.precision == "fp32":
+        line["other_formats"] = {f: format_leg(args, local_rank, stream, torch, f)
+                                 for f in ("toeplitz_tc", "toeplitz", "dense") if f != args.format}
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
     if args.batch_steps > 0:
@@ -362,38 +346,48 @@ def run_ours(args, rank, world, local_rank):
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
-def toeplitz_leg(args, local_rank, stream, torch):
-    """The same coil with the far operator in block-Toeplitz FP32 storage."""
-    from paper_2403_07666_b300.coil import Coil
-    w = pick_workload(args.workload)
-    c = Coil.from_workload(w, precision="fp32", rtol=args.rtol, device=local_rank,
-                           stream=stream.cuda_stream, profile=True, format="toeplitz")
-    c.step(args.warmup, w.drive)
-    c.reset_counters()
-    secs = timed_steps(c, w.drive, args.steps, stream, torch)
-    inf = c.info()
-    N = c.N
-    c.close()
-    op_ms = inf.operator_ms / max(int(inf.operator_launches), 1)
-    flops = 2.0 * N * N
-    achieved = flops / (op_ms / 1e3) / 1e12
-    return {"value": N * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
-            "applies_per_step": int(inf.operator_launches) / args.steps,
-            "operator_bytes": int(inf.operator_bytes),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_ALU_TFLOPS, "traffic": None,
-                         "kernel": "k_toeplitz_f32 (+transpose, reduce)", "avg_launch_ms": op_ms,
-                         "flops_per_launch": flops,
-                         "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz"}}
+def roofline_of(fmt, precision, N, op_bytes, op_ms, hbm, peak_kind):
+    """Roofline of the operator apply (all its launches) of one storage format.
+
+    dense: HBM-bound GEMV, algorithmic bytes = the stored operator.
+    toeplitz (CUDA cores, FP32): bound by the FP32 pipe, 2 N^2 flops.
+    toeplitz_tc (tensor cores): HBM-bound, algorithmic bytes = the split table
+    (read once) + the FP32 input read + the FP64 result written (12 N); its
+    tensor work, 3 x 2 N^2 FP16 flops, is reported beside it."""
+    if fmt == "toeplitz":
+        flops = 2.0 * N * N
+        achieved = flops / (op_ms / 1e3) / 1e12
+        prof = PROFILED_TRAFFIC.get("toeplitz")
+        traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic,
+                "kernel": "k_toeplitz_f32 (+transpose, reduce)",
+                "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                "avg_launch_ms": op_ms, "flops_per_launch": flops, "table_bytes": op_bytes}
+    if fmt == "toeplitz_tc":
+        nbytes = op_bytes + 12.0 * N
+        achieved = nbytes / (op_ms / 1e3) / 1e9
+        prof = PROFILED_TRAFFIC.get("toeplitz_tc")
+        traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": "k_toeplitz_tc (+pmax, split, reduce)", "peak_kind": peak_kind,
+                "avg_launch_ms": op_ms, "bytes_per_launch": nbytes, "table_bytes": op_bytes,
+                "tensor_tflops_fp16": 6.0 * N * N / (op_ms / 1e3) / 1e12}
+    achieved = op_bytes / (op_ms / 1e3) / 1e9
+    prof = PROFILED_TRAFFIC.get(precision)
+    traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": f"k_gemv_{precision}", "peak_kind": peak_kind,
+            "avg_launch_ms": op_ms, "bytes_per_launch": op_bytes}
 
 
-def dense_leg(args, local_rank, stream, torch):
-    """The same coil with the far operator stored dense (FP32, HBM-bound apply)."""
+def format_leg(args, local_rank, stream, torch, fmt):
+    """The same coil and steps with the far operator in another FP32 storage format."""
     from paper_2403_07666_b300.coil import Coil
     w = pick_workload(args.workload)
     hbm, peak_kind = peaks()
     c = Coil.from_workload(w, precision="fp32", rtol=args.rtol, device=local_rank,
-                           stream=stream.cuda_stream, profile=True, format="dense")
+                           stream=stream.cuda_stream, profile=True, format=fmt)
     c.step(args.warmup, w.drive)
     c.reset_counters()
     secs = timed_steps(c, w.drive, args.steps, stream, torch)
@@ -402,15 +396,9 @@ def dense_leg(args, local_rank, stream, torch):
     c.close()
     op_ms = inf.operator_ms / max(int(inf.operator_launches), 1)
     op_bytes = int(inf.operator_bytes)
-    achieved = op_bytes / (op_ms / 1e3) / 1e9
-    prof = PROFILED_TRAFFIC.get("fp32")
     return {"value": N * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
             "applies_per_step": int(inf.operator_launches) / args.steps, "operator_bytes": op_bytes,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
-                         "traffic": prof["dram_bytes"] * op_bytes / prof["operator_bytes"],
-                         "kernel": "k_gemv_fp32", "avg_launch_ms": op_ms, "bytes_per_launch": op_bytes,
-                         "peak_kind": peak_kind}}
+            "roofline": roofline_of(fmt, "fp32", N, op_bytes, op_ms, hbm, peak_kind)}
 
 
 def adjoint_leg(args, local_rank, stream, torch):
@@ -441,8 +429,9 @@ def batch_leg(args, local_rank, stream, torch):
     """64 coils of uneven size (2k-41k elements) stepped together."""
     from paper_2403_07666_b300.coil import Coil, batch_step
     ws = wl.batch_coils()
+    fmt = args.batch_format if args.precision == "fp32" else "dense"
     coils = [Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
-                                stream=stream.cuda_stream) for w in ws]
+                                stream=stream.cuda_stream, format=fmt) for w in ws]
     drives = [w.drive for w in ws]
     batch_step(coils, args.warmup, drives)
     for c in coils:
@@ -463,7 +452,7 @@ def batch_leg(args, local_rank, stream, torch):
     return {"workload": f"batch of {len(ws)} coils", "n_elem_total": total_elem,
             "n_elem_min": min(w.n_elem for w in ws), "n_elem_max": max(w.n_elem for w in ws),
             "steps": args.batch_steps, "value": total_elem * args.batch_steps / secs, "unit": UNIT,
-            "ms_per_step": 1e3 * secs / args.batch_steps, "operator_bytes": op_bytes,
+            "ms_per_step": 1e3 * secs / args.batch_steps, "operator_format": fmt, "operator_bytes": op_bytes,
             "gpu_launches": launches}
 
 
@@ -499,11 +488,12 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-9)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--format", default="toeplitz", choices=["toeplitz", "dense"],
+    ap.add_argument("--format", default="toeplitz_tc", choices=["toeplitz_tc", "toeplitz", "dense"],
                     help="storage of the far operator in the main leg")
-    ap.add_argument("--other-format", type=int, default=1, help="also time the other operator format")
+    ap.add_argument("--other-format", type=int, default=1, help="also time the other operator formats")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--batch-format", default="toeplitz_tc", choices=["toeplitz_tc", "toeplitz", "dense"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
