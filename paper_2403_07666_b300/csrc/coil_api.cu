@@ -456,8 +456,13 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         P.smem = tc_smem_bytes(tsh);
         P.t16 = static_cast<__half*>(M);
         TRY(dalloc(c, &P.p16, 2 * (size_t)tsh.Cp * NT, "split operator input"));
-        TRY(dalloc(c, &P.part, (size_t)tsh.n_chunks * N, "tensor-core partial sums"));
-        TRY(dalloc(c, &P.pmax, (size_t)tsh.n_pmax, "input maxima"));
+        TRY(dalloc(c, &P.part, (size_t)tsh.n_cta * NT * 128, "tensor-core partial tiles"));
+        std::vector<int4> work;
+        std::vector<int2> range;
+        tc_schedule(tsh, c->n_sm, &work, &range);
+        TRY(upload(c, &P.work, work, "tensor-core schedule"));
+        TRY(upload(c, &P.range, range, "tensor-core schedule"));
+        TRY(dalloc(c, &P.pexp, (size_t)NT, "input scale exponents"));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
@@ -1049,9 +1054,9 @@ coil_status coil_read_operator(coil_t* c, double* M) {
             }
     }
     if (h.op_format == 2) {
-        // (hi + lo) 2^-exT of the split FP16 table [half][offset][c][c' < Cp]
+        // (hi + lo) 2^-exT of the split FP16 table [half][offset][k block][c][64]
         const TcShape& sh = c->tc->sh;
-        size_t C = sh.C, Cp = sh.Cp, NT = sh.NT;
+        size_t C = sh.C, NT = sh.NT, nkb = sh.n_kb;
         size_t half_n = tc_table_halves(sh) / 2;
         std::vector<__half> t16(2 * half_n);
         CK(cudaMemcpy(t16.data(), c->tc->t16, t16.size() * sizeof(__half), cudaMemcpyDeviceToHost),
@@ -1060,7 +1065,8 @@ coil_status coil_read_operator(coil_t* c, double* M) {
         for (size_t i = 0; i < N; ++i)
             for (size_t j = 0; j < N; ++j) {
                 long long d = (long long)(i / C) - (long long)(j / C);
-                size_t k = ((size_t)(d + (long long)NT - 1) * C + (i % C)) * Cp + (j % C);
+                size_t cj = j % C;
+                size_t k = (((size_t)(d + (long long)NT - 1) * nkb + cj / 64) * C + (i % C)) * 64 + cj % 64;
                 M[i * N + j] = ((double)__half2float(t16[k]) + (double)__half2float(t16[half_n + k])) * inv;
             }
     }

@@ -7,7 +7,7 @@
 //
 // element e = t C + c.  For one turn offset d this is a (C x C) by
 // (C x valid turns) product, so a CTA that owns a tile of 128 channels c and a
-// chunk of offsets runs, on the tensor cores,
+// run of (64-channel k block, offset) stages runs, on the tensor cores,
 //
 //     D[c][t] += A_d[c][k] B_d[t][k],   A_d = T_d tile,  B_d[t][.] = p[t - d][.],
 //
@@ -19,17 +19,26 @@
 // Toeplitz shift costs no copy and no padded work, and every table entry is
 // read from HBM once per apply.
 //
-// Precision: entries and inputs are scaled by powers of two (max |T| and
-// max |p| below 2^14) and split v = hi + lo into two FP16 numbers; the three
-// products hi*hi + hi*lo + lo*hi keep about 22 significant bits, the FP32
-// class.  The tensor cores' FP32 accumulation does not round to nearest, so
-// its error grows with the number of MMAs added into one accumulator; here an
-// accumulator takes only one stage (one offset, one 64-channel k block: 12
+// Precision: entries and inputs are scaled by powers of two (2^exT brings
+// max |T| over the table below 2^14, 2^x[t] the largest |p| of turn row t)
+// and split v = hi + lo into two FP16 numbers; the three products
+// hi*hi + hi*lo + lo*hi keep about 22 significant bits, the FP32 class.  The
+// tensor cores' FP32 accumulation does not round to nearest, so its error
+// grows with the number of MMAs added into one accumulator; here an
+// accumulator takes only one stage (one offset d, one 64-channel k block: 12
 // MMAs), after which the epilogue warps add it into FP32 registers (round to
-// nearest) and hand it back.  Up to four TMEM accumulators rotate so the MMAs
-// of the next stages run while one is drained.  The offset chunks are summed
-// in FP64 in a fixed order, so the result is deterministic.  The table takes
-// 2 x 2 bytes per entry, as many as FP32.
+// nearest), column t times 2^(xmin - x[t - d]): the scale of its source row
+// relative to the largest-scale row, an exact power of two of at most 1, so
+// the FP32 sums stay in the range of a single global scale.  The reduction
+// removes 2^(xmin + exT) in FP64.  Up to four TMEM accumulators rotate, so
+// the MMAs of the next stages run while one is drained.  The CTAs' partial
+// tiles are summed in FP64 in a fixed order: the result is deterministic.
+//
+// Work split: the CTAs (one per SM) are dealt evenly to the 128-channel
+// tiles, and each takes a contiguous run of its tile's stages in (k block,
+// offset) order, so it meets only one or two k blocks and loads the staged
+// copy of p once per k block.  The
+// table takes 2 x 2 bytes per entry, as many as FP32.
 //
 // CTA roles (320 threads): warp 0 issues the TMA loads, warp 1 owns the TMEM
 // accumulators and issues the MMAs, warps 2-9 drain the accumulators (lane
@@ -43,6 +52,9 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 namespace cq {
 
 constexpr int kTcM = 128;                        // channels per tile (MMA M)
@@ -54,7 +66,8 @@ constexpr int kTcGroups = 7;                     // 16-column groups per epilogu
 constexpr uint32_t kTcAStage = 2u * kTcM * kTcK * 2u;   // hi + lo table tiles, 32 KB
 constexpr int kTcSmemLimit = 227 * 1024;         // dynamic shared memory per CTA (opt-in maximum)
 constexpr long long kTcWait = 1LL << 31;         // cycles before a wait gives up (~1 s)
-__host__ __device__ constexpr int kTcBars(int stages) { return 2 * stages + 13; }
+constexpr int kTcBStages = 1;                    // staged copies of p (a CTA meets few k blocks)
+__host__ __device__ constexpr int kTcBars(int stages) { return 2 * stages + 2 * kTcBStages + 9; }
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -110,6 +123,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w, int v,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(v), "r"(bar)
         : "memory");
 }
 
@@ -177,7 +199,8 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const CoilDev* __restrict__ cd, const TcShape sh, float* __restrict__ part) {
+              const CoilDev* __restrict__ cd, const TcShape sh, const int4* __restrict__ work,
+              const int* __restrict__ pexp, float* __restrict__ part) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
     extern __shared__ uint8_t tc_smem[];
@@ -185,26 +208,34 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = tc_smem + (base - raw);
     const uint32_t b_stage = 256u * (uint32_t)sh.NR;             // hi + lo staged p, bytes
-    const uint32_t b_pitch = (b_stage + 1023u) & ~1023u;
-    const uint32_t sB = base;                                     // 2 stages
-    const uint32_t sA = base + 2u * b_pitch;                      // sh.stages x 32 KB
-    const uint32_t bar_off = 2u * b_pitch + (uint32_t)sh.stages * kTcAStage;
+    const uint32_t b_pitch = (b_stage + 127u) & ~127u;
+    const uint32_t sA = base;                                     // sh.stages x 32 KB (1024-aligned)
+    const uint32_t sB = base + (uint32_t)sh.stages * kTcAStage;   // kTcBStages staged copies of p
+    const uint32_t bar_off = (uint32_t)sh.stages * kTcAStage + kTcBStages * b_pitch;
     const uint32_t sBar = base + bar_off;
     const int S = sh.stages;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + bar_off + 8 * kTcBars(S));
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + bar_off + 8 * kTcBars(S) + 4);
-    // barriers: a_full[S], a_empty[S], b_full[2], b_empty[2], acc_full[4], acc_empty[4], mma_done
+    int* xmin_s = reinterpret_cast<int*>(gbase + bar_off + 8 * kTcBars(S) + 8);
+    // relative inverse input scale of staged row r (p row r - 16; zero outside the winding)
+    float* inv_s = reinterpret_cast<float*>(gbase + bar_off + 8 * kTcBars(S) + 16);
+    // barriers: a_full[S], a_empty[S], b_full[kTcBStages], b_empty[kTcBStages], acc_full[4],
+    // acc_empty[4], mma_done
     const uint32_t a_full = sBar, a_empty = sBar + 8u * S;
-    const uint32_t b_full = sBar + 16u * S, b_empty = b_full + 16u;
-    const uint32_t acc_full = b_empty + 16u, acc_empty = acc_full + 32u;
+    const uint32_t b_full = sBar + 16u * S, b_empty = b_full + 8u * kTcBStages;
+    const uint32_t acc_full = b_empty + 8u * kTcBStages, acc_empty = acc_full + 32u;
     const uint32_t mma_done = acc_empty + 32u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ct = blockIdx.x % sh.n_ct, chunk = blockIdx.x / sh.n_ct;
-    const int c0 = ct * kTcM;
+    // this CTA's work: channel tile ct, stages s0 <= s < s1 of that tile in the
+    // order (k block kb = s / ndist, offset d = s % ndist - (NT - 1))
+    const int4 wk = work[blockIdx.x];
+    const int c0 = wk.x * kTcM;
     const int ndist = 2 * sh.NT - 1;
-    const int d_lo = -(sh.NT - 1) + (int)((long long)chunk * ndist / sh.n_chunks);
-    const int d_hi = -(sh.NT - 1) + (int)((long long)(chunk + 1) * ndist / sh.n_chunks);
+    const int kb_first = wk.y / ndist, kb_last = (wk.z - 1) / ndist;
+    // offsets of k block kb inside the range: [d_begin(kb), d_end(kb))
+    auto d_begin = [&](int kb) { return (kb == kb_first ? wk.y - kb * ndist : 0) - (sh.NT - 1); };
+    auto d_end = [&](int kb) { return (kb == kb_last ? wk.z - kb * ndist : ndist) - (sh.NT - 1); };
     const int n_acc = sh.n_acc;
     const uint32_t acc_cols = (uint32_t)sh.acc_cols;
 
@@ -215,8 +246,11 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             mbar_init(bar, (bar >= acc_empty && bar < acc_empty + 32u) ? (uint32_t)kTcEpiWarps : 1u);
         }
         *abort_flag = 0;
+        *xmin_s = 1 << 30;
         mbar_fence_init();
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < sh.NT; t += blockDim.x) atomicMin(xmin_s, pexp[t]);
     if (warp == 1) {
         __syncwarp();
         tmem_alloc(su32(tslot), (uint32_t)sh.ncols);
@@ -225,6 +259,11 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    for (int r = threadIdx.x; r < sh.NR; r += blockDim.x) {
+        const int t = r - kTcPad;
+        inv_s[r] = (t >= 0 && t < sh.NT) ? ldexpf(1.f, *xmin_s - pexp[t]) : 0.f;
+    }
+    __syncthreads();
 
     if (warp == 0 && lane == 0) {
         // ---- producer: per k block one staged p copy, then the table tiles of every offset
@@ -232,19 +271,19 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         uint32_t pa = 0, pb = 0;
         uint32_t a_used = 0, a_par = 0, b_used = 0, b_par = 0;   // bit s: stage s loaded / its parity
         bool ok = true;
-        for (int kb = 0; kb < sh.n_kb && ok; ++kb) {
+        for (int kb = kb_first; kb <= kb_last && ok; ++kb) {
             ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
             if (!ok) break;
             mbar_expect_tx(b_full + 8u * sb, b_stage);
             tma_load_4d(sB + (uint32_t)sb * b_pitch, &tmB, 0, -kTcPad, kb * (kTcK / 8), 0, b_full + 8u * sb);
             b_used |= 1u << sb;
             b_par = (b_par & ~(1u << sb)) | (pb << sb);
-            if (++sb == 2) { sb = 0; pb ^= 1u; }
-            for (int d = d_lo; d < d_hi; ++d) {
+            if (++sb == kTcBStages) { sb = 0; pb ^= 1u; }
+            for (int d = d_begin(kb), de = d_end(kb); d < de; ++d) {
                 ok = mbar_wait(a_empty + 8u * sa, pa ^ 1u, abort_flag);
                 if (!ok) break;
                 mbar_expect_tx(a_full + 8u * sa, kTcAStage);
-                tma_load_4d(sA + (uint32_t)sa * kTcAStage, &tmA, kb * kTcK, c0, d + sh.NT - 1, 0, a_full + 8u * sa);
+                tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmA, 0, c0, kb, d + sh.NT - 1, 0, a_full + 8u * sa);
                 a_used |= 1u << sa;
                 a_par = (a_par & ~(1u << sa)) | (pa << sa);
                 if (++sa == S) { sa = 0; pa ^= 1u; }
@@ -253,7 +292,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // retire the copies in flight (only the latest load of a stage can be)
         for (int s = 0; s < S; ++s)
             if (a_used >> s & 1u) mbar_wait_final(a_full + 8u * s, a_par >> s & 1u, kTcWait);
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < kTcBStages; ++s)
             if (b_used >> s & 1u) mbar_wait_final(b_full + 8u * s, b_par >> s & 1u, kTcWait);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer: stage (kb, d) accumulates into TMEM accumulator i (round robin),
@@ -261,13 +300,13 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         int sa = 0, sb = 0, ai = 0;
         uint32_t pa = 0, pb = 0, pe = 0;   // pe bit i: phase of acc_empty[i]
         bool ok = true;
-        for (int kb = 0; kb < sh.n_kb && ok; ++kb) {
+        for (int kb = kb_first; kb <= kb_last && ok; ++kb) {
             ok = mbar_wait(b_full + 8u * sb, pb, abort_flag);
             if (!ok) break;
             tc_fence_after();
             const uint32_t bh = sB + (uint32_t)sb * b_pitch;
             const uint32_t bl = bh + 128u * (uint32_t)sh.NR;
-            for (int d = d_lo; d < d_hi; ++d) {
+            for (int d = d_begin(kb), de = d_end(kb); d < de; ++d) {
                 ok = mbar_wait(a_full + 8u * sa, pa, abort_flag);
                 if (ok) ok = mbar_wait(acc_empty + 8u * ai, ((pe >> ai) & 1u) ^ 1u, abort_flag);
                 if (!ok) break;
@@ -299,7 +338,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 if (++ai == n_acc) ai = 0;
             }
             mma_commit(b_empty + 8u * sb);
-            if (++sb == 2) { sb = 0; pb ^= 1u; }
+            if (++sb == kTcBStages) { sb = 0; pb ^= 1u; }
         }
         // every MMA issued (also after an abort) completes before the TMEM is freed
         mma_commit(mma_done);
@@ -319,8 +358,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         int ai = 0;
         uint32_t pf = 0;
         bool ok = true;
-        for (int kb = 0; kb < sh.n_kb && ok; ++kb) {
-            for (int d = d_lo; d < d_hi; ++d) {
+        for (int kb = kb_first; kb <= kb_last && ok; ++kb) {
+            for (int d = d_begin(kb), de = d_end(kb); d < de; ++d) {
                 ok = __all_sync(0xffffffffu, mbar_wait(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag));
                 if (!ok) break;
                 pf ^= 1u << ai;
@@ -329,6 +368,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const int t_end = d < 0 ? sh.NT + d : sh.NT;
                 const int g_lo = t_first >> 4, g_hi = (t_end + 15) >> 4;
                 const uint32_t src = lane_base + (uint32_t)ai * acc_cols;
+                const float* sc = inv_s + (kTcPad - d);        // sc[t]: scale of source row t - d
 #pragma unroll
                 for (int gi = 0; gi < kTcGroups; ++gi) {
                     const int g = 2 * gi + h;
@@ -336,7 +376,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         float v[16];
                         tmem_ld16(src + 16u * (uint32_t)g, v);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[gi][j] += v[j];
+                        for (int j = 0; j < 16; ++j) acc[gi][j] = fmaf(v[j], sc[16 * g + j], acc[gi][j]);
                     }
                 }
                 tc_fence_before();
@@ -346,13 +386,14 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
         }
         if (ok && !*abort_flag && cc < sh.C) {
-            float* out = part + (size_t)chunk * sh.N + cc;
+            // partial tile of this CTA: part[cta][t][c - c0]
+            float* out = part + (size_t)blockIdx.x * sh.NT * kTcM + 32 * q + lane;
 #pragma unroll
             for (int gi = 0; gi < kTcGroups; ++gi) {
                 const int t0 = 16 * (2 * gi + h);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    if (t0 + j < sh.NT) out[(size_t)(t0 + j) * sh.C] = acc[gi][j];
+                    if (t0 + j < sh.NT) out[(size_t)(t0 + j) * kTcM] = acc[gi][j];
             }
         }
     }
@@ -400,50 +441,57 @@ __host__ __device__ inline int tc_exponent(double m) {
     return x > 120 ? 120 : (x < -120 ? -120 : x);
 }
 
-// Block maxima of |p| (p = the FP32 operator input pf).
-__global__ void k_tc_pmax(const CoilDev* __restrict__ cd, float* __restrict__ pmax) {
+// p -> FP16 hi/lo in [half][c'/8][t][c' % 8] order; one block per turn row t,
+// scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.
+__global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
+                           int* __restrict__ pexp) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
+    const int t = blockIdx.x;
+    const float* row = c.pf + (size_t)t * sh.C;
     float m = 0.f;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c.N; e += gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(c.pf[e]));
-    m = block_max_f(m);
-    if (threadIdx.x == 0) pmax[blockIdx.x] = m;
-}
-
-__device__ __forceinline__ int input_exponent(const float* pmax, int n) {
-    float m = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, pmax[i]);
-    return tc_exponent((double)block_max_f(m));
-}
-
-// p -> FP16 hi/lo in [half][c'/8][t][c' % 8] order, scaled by 2^exP.
-__global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ pmax,
-                           __half* __restrict__ p16) {
-    const CoilDev& c = *cd;
-    if (c.sc->done) return;
-    const float s = ldexpf(1.f, input_exponent(pmax, sh.n_pmax));
+    for (int cc = threadIdx.x; cc < sh.C; cc += blockDim.x) m = fmaxf(m, fabsf(row[cc]));
+    const int x = tc_exponent((double)block_max_f(m));
+    if (threadIdx.x == 0) pexp[t] = x;
+    const float s = ldexpf(1.f, x);
     const int total = sh.Cp * sh.NT;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int j = idx & 7, rest = idx >> 3;
-        const int t = rest % sh.NT, ch = rest / sh.NT;
-        const int cc = 8 * ch + j;
-        const float v = cc < sh.C ? c.pf[(size_t)t * sh.C + cc] * s : 0.f;
+    for (int cc = threadIdx.x; cc < sh.Cp; cc += blockDim.x) {
+        const float v = cc < sh.C ? row[cc] * s : 0.f;
         const __half hi = __float2half_rn(v);
+        const int idx = ((cc >> 3) * sh.NT + t) * 8 + (cc & 7);
         p16[idx] = hi;
         p16[total + idx] = __float2half_rn(v - __half2float(hi));
     }
 }
 
-// q[e] = sum over the offset chunks (fixed order, FP64), unscaled.
-__global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ pmax,
-                            const float* __restrict__ part, int exT) {
+// q[e] = 2^-(exT + xmin) x the sum of the partial tiles of the CTAs that
+// worked on e's channel tile (fixed order, FP64; the loads of eight tiles are
+// issued before their sums).  range[ct] = (first CTA, number of CTAs).
+__global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ part,
+                            const int2* __restrict__ range, const int* __restrict__ pexp, int exT) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
-    const double inv = ldexp(1.0, -(exT + input_exponent(pmax, sh.n_pmax)));
+    __shared__ int xmin;
+    if (threadIdx.x == 0) xmin = 1 << 30;
+    __syncthreads();
+    for (int t = threadIdx.x; t < sh.NT; t += blockDim.x) atomicMin(&xmin, pexp[t]);
+    __syncthreads();
+    const double inv = ldexp(1.0, -(exT + xmin));
+    const size_t tile = (size_t)sh.NT * kTcM;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sh.N; e += gridDim.x * blockDim.x) {
+        const int t = e / sh.C, cc = e - t * sh.C;
+        const int2 rg = range[cc / kTcM];
+        const float* p = part + (size_t)rg.x * tile + (size_t)t * kTcM + (cc % kTcM);
         double s = 0.0;
-        for (int k = 0; k < sh.n_chunks; ++k) s += (double)part[(size_t)k * sh.N + e];
+        int k = 0;
+        for (; k + 8 <= rg.y; k += 8) {
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = p[(size_t)(k + i) * tile];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s += (double)v[i];
+        }
+        for (; k < rg.y; ++k) s += (double)p[(size_t)k * tile];
         c.qv[e] = s * inv;
     }
 }
@@ -462,18 +510,21 @@ __global__ void k_tc_absmax(const double* __restrict__ tab, long long n, double*
     }
 }
 
-// FP64 table [offset][c][c'] -> FP16 hi/lo [half][offset][c][c' < Cp] scaled
-// by 2^exT; intra-wire entries of offset 0 are zero (applied from the FP64
-// near blocks), padding columns c' >= C are zero.
+// FP64 table [offset][c][c'] -> FP16 hi/lo [half][offset][k block][c][64]
+// (c' = 64 k block + column), scaled by 2^exT, so that the 128 x 64 tile of
+// one stage is a contiguous 16 KB per half; intra-wire entries of offset 0
+// are zero (applied from the FP64 near blocks), padding columns c' >= C zero.
 __global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int wire_div, int exT,
                            __half* __restrict__ t16) {
-    const long long total = (long long)(2 * sh.NT - 1) * sh.C * sh.Cp;
+    const long long total = (long long)(2 * sh.NT - 1) * sh.n_kb * sh.C * kTcK;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int cj = (int)(idx % sh.Cp);
-        const long long rest = idx / sh.Cp;
+        const int kk = (int)(idx % kTcK);
+        const long long rest = idx / kTcK;
         const int ci = (int)(rest % sh.C);
-        const int dd = (int)(rest / sh.C);
+        const long long rest2 = rest / sh.C;
+        const int cj = (int)(rest2 % sh.n_kb) * kTcK + kk;
+        const int dd = (int)(rest2 / sh.n_kb);
         double v = cj < sh.C ? tab[((long long)dd * sh.C + ci) * sh.C + cj] : 0.0;
         if (dd == sh.NT - 1 && ci / wire_div == cj / wire_div) v = 0.0;
         v = ldexp(v, exT);
@@ -487,8 +538,9 @@ __global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int
 // Host side
 // ---------------------------------------------------------------------------
 size_t tc_smem_bytes(const TcShape& sh) {
-    size_t b_pitch = ((size_t)256 * sh.NR + 1023) & ~(size_t)1023;
-    return 1024 + 2 * b_pitch + (size_t)sh.stages * kTcAStage + 8 * (size_t)kTcBars(sh.stages) + 16;
+    size_t b_pitch = ((size_t)256 * sh.NR + 127) & ~(size_t)127;
+    return 1024 + kTcBStages * b_pitch + (size_t)sh.stages * kTcAStage + 8 * (size_t)kTcBars(sh.stages) + 16 +
+           4 * (size_t)sh.NR;
 }
 
 bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
@@ -500,26 +552,58 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
     s.NR = NT + 2 * kTcPad;
     s.N = C * NT;
     s.n_ct = (C + kTcM - 1) / kTcM;
-    int ndist = 2 * NT - 1;
-    int ch = n_sm / s.n_ct;
-    s.n_chunks = ch < 1 ? 1 : (ch > ndist ? ndist : ch);
     s.n_kb = (s.Cp + kTcK - 1) / kTcK;
+    s.n_cta = (int)tc_schedule(s, n_sm, nullptr, nullptr);
     int used = (NT + 15) & ~15;
     s.acc_cols = 32;
     while (s.acc_cols < used) s.acc_cols *= 2;
     s.n_acc = 512 / s.acc_cols > 4 ? 4 : 512 / s.acc_cols;   // 2..4 accumulators in 512 columns
     s.ncols = s.n_acc * s.acc_cols;
-    s.n_pmax = (s.N + 1023) / 1024;
-    if (s.n_pmax > n_sm) s.n_pmax = n_sm;
     const size_t limit = kTcSmemLimit;
-    s.stages = 6;
+    s.stages = 6;                      // 192 KB of table copies in flight per SM
     while (s.stages > 2 && tc_smem_bytes(s) > limit) --s.stages;
     if (tc_smem_bytes(s) > limit) return false;
     *sh = s;
     return true;
 }
 
-size_t tc_table_halves(const TcShape& sh) { return 2 * (size_t)(2 * sh.NT - 1) * sh.C * sh.Cp; }
+// CTAs per channel tile: start from one each and keep adding a CTA to the
+// tile whose CTAs carry the most stages, while CTAs are left (n_sm in all, or
+// one per tile when there are more tiles than SMs) and no tile has more CTAs
+// than stages.  Stages, not bytes, are balanced: a stage's time is set by the
+// latency of its copy (a few in flight per SM), which the ragged last tile's
+// half-height stages take as well.
+// A tile's stages (n_kb x (2 NT - 1)) are split into contiguous near-equal
+// ranges.  work[cta] = (tile, first stage, end stage, 0); range[tile] =
+// (first CTA, CTAs).  Returns the number of CTAs.
+size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::vector<int2>* range) {
+    const long long stages = (long long)sh.n_kb * (2 * sh.NT - 1);
+    std::vector<int> cnt(sh.n_ct, 1);
+    long long total = sh.n_ct;
+    while (total < n_sm) {
+        int best = -1;
+        double load = -1.0;
+        for (int ct = 0; ct < sh.n_ct; ++ct) {
+            double l = (double)stages / cnt[ct];
+            if (cnt[ct] < stages && l > load) { load = l; best = ct; }
+        }
+        if (best < 0) break;
+        cnt[best] += 1;
+        total += 1;
+    }
+    if (work && range) {
+        work->clear();
+        range->clear();
+        for (int ct = 0; ct < sh.n_ct; ++ct) {
+            range->push_back(make_int2((int)work->size(), cnt[ct]));
+            for (int i = 0; i < cnt[ct]; ++i)
+                work->push_back(make_int4(ct, (int)(stages * i / cnt[ct]), (int)(stages * (i + 1) / cnt[ct]), 0));
+        }
+    }
+    return (size_t)total;
+}
+
+size_t tc_table_halves(const TcShape& sh) { return 2 * (size_t)(2 * sh.NT - 1) * sh.n_kb * sh.C * kTcK; }
 
 cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* scratch, cudaStream_t s) {
     const TcShape& sh = P->sh;
@@ -535,7 +619,7 @@ cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* s
     double m = 0.0;
     for (int i = 0; i < nb; ++i) m = hm[i] > m ? hm[i] : m;
     P->exT = tc_exponent(m);
-    long long total = (long long)(2 * sh.NT - 1) * sh.C * sh.Cp;
+    long long total = (long long)(2 * sh.NT - 1) * sh.n_kb * sh.C * kTcK;
     long long blocks = (total + 255) / 256;
     if (blocks > 148LL * 64) blocks = 148LL * 64;
     k_tc_table<<<(unsigned)blocks, 256, 0, s>>>(tab, sh, wire_div, P->exT, P->t16);
@@ -568,13 +652,15 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
         return cudaErrorNotSupported;
     }
     const TcShape& sh = P->sh;
-    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     {
-        const cuuint64_t dims[4] = {(cuuint64_t)sh.Cp, (cuuint64_t)sh.C, (cuuint64_t)(2 * sh.NT - 1), 2};
-        const cuuint64_t strides[3] = {(cuuint64_t)sh.Cp * 2, (cuuint64_t)sh.C * sh.Cp * 2,
-                                       (cuuint64_t)(2 * sh.NT - 1) * sh.C * sh.Cp * 2};
-        const cuuint32_t box[4] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM, 1, 2};
-        CUresult r = enc(&P->tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->t16, dims, strides, box, ones,
+        // [half][offset][k block][c][64]: box = one stage's 128 x 64 tile of both halves
+        const cuuint64_t row = (cuuint64_t)kTcK * 2;
+        const cuuint64_t dims[5] = {(cuuint64_t)kTcK, (cuuint64_t)sh.C, (cuuint64_t)sh.n_kb,
+                                    (cuuint64_t)(2 * sh.NT - 1), 2};
+        const cuuint64_t strides[4] = {row, row * sh.C, row * sh.C * sh.n_kb, row * sh.C * sh.n_kb * (2 * sh.NT - 1)};
+        const cuuint32_t box[5] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM, 1, 1, 2};
+        CUresult r = enc(&P->tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, P->t16, dims, strides, box, ones,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -603,14 +689,11 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
 
 cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s) {
     const TcShape& sh = P.sh;
-    k_tc_pmax<<<sh.n_pmax, 1024, 0, s>>>(P.d, P.pmax);
-    int total = sh.Cp * sh.NT;
-    int sb = (total + 255) / 256;
-    k_tc_split<<<sb, 256, 0, s>>>(P.d, sh, P.pmax, P.p16);
-    k_toeplitz_tc<<<sh.n_ct * sh.n_chunks, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.d, sh, P.part);
+    k_tc_split<<<sh.NT, 256, 0, s>>>(P.d, sh, P.p16, P.pexp);
+    k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.d, sh, P.work, P.pexp, P.part);
     int rb = (sh.N + 255) / 256;
     if (rb > 148 * 8) rb = 148 * 8;
-    k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.pmax, P.part, P.exT);
+    k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.range, P.pexp, P.exT);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace cq {
@@ -14,22 +16,24 @@ namespace cq {
 struct TcShape {
     int C, Cp, NT, NR;          // channels per turn row, C rounded up to 8, turn rows, staged p rows
     int N;                      // elements (NT C)
-    int n_ct, n_chunks, n_kb;   // 128-channel tiles, turn-offset chunks, 64-channel k blocks
+    int n_ct, n_kb;             // 128-channel tiles, 64-channel k blocks
+    int n_cta;                  // CTAs of the apply (see tc_schedule)
     int stages;                 // table tiles in flight per CTA
     int acc_cols, n_acc;        // TMEM columns per accumulator, accumulators (stages alternate)
     int ncols;                  // TMEM columns allocated per CTA (n_acc acc_cols)
-    int n_pmax;                 // blocks of the max |p| pass
 };
 
 struct TcPlan {
-    CUtensorMap tmA;            // split table: [half][offset][c][c'] FP16, 128-byte swizzle
+    CUtensorMap tmA;            // split table: [half][offset][c'/64][c][c' % 64] FP16, 128-byte swizzle
     CUtensorMap tmB;            // split input: [half][c'/8][t][c' % 8] FP16, no swizzle
     TcShape sh;
     const CoilDev* d = nullptr; // device descriptor of the coil
-    __half* t16 = nullptr;      // 2 (2 NT - 1) C Cp
+    __half* t16 = nullptr;      // 2 (2 NT - 1) n_kb C 64
     __half* p16 = nullptr;      // 2 Cp NT
-    float* part = nullptr;      // n_chunks N partial sums
-    float* pmax = nullptr;      // n_pmax block maxima of |p|
+    float* part = nullptr;      // n_cta x NT x 128 partial tiles
+    int4* work = nullptr;       // n_cta (tile, first stage, end stage, 0)
+    int2* range = nullptr;      // n_ct (first CTA, CTAs)
+    int* pexp = nullptr;        // NT input scale exponents (one per turn row)
     int exT = 0;                // table scale 2^exT
     size_t smem = 0;            // dynamic shared memory per CTA
 };
@@ -39,6 +43,8 @@ constexpr int kTcMaxTurns = 224;   // staged p rows NT + 32 fit one TMA box (<= 
 // Fill the shape for C channels, NT turns on n_sm SMs; false if unsupported.
 bool tc_shape(int C, int NT, int n_sm, TcShape* sh);
 size_t tc_table_halves(const TcShape& sh);
+// CTA schedule of the apply; fills work/range when both are non-null.
+size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::vector<int2>* range);
 size_t tc_smem_bytes(const TcShape& sh);
 
 // Split the FP64 table (with intra-wire entries of offset 0 zeroed) into the

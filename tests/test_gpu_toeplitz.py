@@ -43,7 +43,8 @@ def test_tc_entries_match_oracle(L, T, n):
     M = oracle_of(w).M
     with _coil(w, precision="fp32", format="toeplitz_tc") as t:
         Mt = t.operator()
-        assert t.info().operator_bytes == 4 * (2 * T - 1) * (L * n * n) * (((L * n * n) + 7) // 8 * 8)
+        C = L * n * n
+        assert t.info().operator_bytes == 4 * (2 * T - 1) * C * ((C + 63) // 64 * 64)
     err = np.abs(Mt - M)
     assert np.max(err / np.abs(M).max()) < 2.0 ** -22
     assert rel(Mt, M) < 2e-7
