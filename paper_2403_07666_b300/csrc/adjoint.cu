@@ -124,7 +124,7 @@ __global__ void k_adj_mult(const CoilDev* __restrict__ cds) {
     double yr = 0.0;
     for (int k = lane; k < c.B; k += 32) yr += c.y1[w * c.B + k] * c.res[w * c.B + k];
     yr = warp_sum(yr);
-    if (lane == 0) c.uw[w] = c.constrained[w] ? c.uw[w] + yr / c.sigma[w] : 0.0;
+    if (lane == 0) c.uw[w] = c.constrained[w] ? c.uw[w] + yr * c.isigma[w] : 0.0;
 }
 
 // Jc and its partial derivatives (zero outside the superconducting region).

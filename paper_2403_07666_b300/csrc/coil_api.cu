@@ -33,6 +33,9 @@ __global__ void k_factor(const CoilDev* __restrict__ cds);
 __global__ void k_near(const CoilDev* __restrict__ cds, int which);
 __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
+__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which);
+__global__ void k_init_seg(const CoilDev* __restrict__ cds);
+__global__ void k_update_seg(const CoilDev* __restrict__ cds);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode);
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
@@ -408,6 +411,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.L, (size_t)W * B * B, "L"));
     TRY(dalloc(c, &h.y1, (size_t)W * B, "y1"));
     TRY(dalloc(c, &h.sigma, W, "sigma"));
+    TRY(dalloc(c, &h.isigma, W, "1 / sigma"));
     TRY(dalloc(c, &h.cw, W, "cw"));
     TRY(dalloc(c, &h.uw, W, "uw"));
     TRY(dalloc(c, &h.parts, 8 * (size_t)W, "parts"));
@@ -588,6 +592,7 @@ struct Launch {
     int n_sm = 148;
     int format = 0;
     int maxC = 0, maxNT = 0;
+    bool seg = false, big = false;   // coils with blocks of <= kSegMax / more elements present
 };
 
 Launch single_launch(coil_t* c) {
@@ -607,6 +612,8 @@ Launch single_launch(coil_t* c) {
     L.format = h.op_format;
     L.maxC = h.C;
     L.maxNT = h.NT;
+    L.seg = h.B <= kSegMax;
+    L.big = !L.seg;
     if (c->tc) L.tc.push_back(c->tc);
     return L;
 }
@@ -657,16 +664,36 @@ void harvest_events(coil_t* c) {
 
 dim3 warp_grid(const Launch& L) { return dim3((unsigned)((L.maxW + 7) / 8), L.n); }
 
+// Near-block product, initial residual and PCG update: one warp per wire for
+// blocks of more than kSegMax elements, shared warps (at least two wires per
+// warp) for smaller ones; a batch with both kinds launches both kernels, each
+// skipping the other kind's coils.  Return the number of launches.
+int launch_near(const Launch& L, int which) {
+    if (L.big) k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, which);
+    if (L.seg) k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which);
+    return (int)L.big + (int)L.seg;
+}
+int launch_init(const Launch& L) {
+    if (L.big) k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.seg) k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
+    return (int)L.big + (int)L.seg;
+}
+int launch_update(const Launch& L) {
+    if (L.big) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.seg) k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
+    return (int)L.big + (int)L.seg;
+}
+
 // Pointwise, factorisation, right-hand-side norm, initial residual.
 coil_status step_prologue(coil_t* c, const Launch& L) {
     k_pointwise<<<warp_grid(L), 256, 0, L.s>>>(L.d);
     k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
     k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 0);
     TRY(gemv(c, L, 0));
-    k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, 0);
-    k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    c->launches += launch_near(L, 0);
+    c->launches += launch_init(L);
     k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 1);
-    c->launches += 6;
+    c->launches += 4;
     CK(cudaGetLastError(), "step launch");
     return COIL_OK;
 }
@@ -674,14 +701,14 @@ coil_status step_prologue(coil_t* c, const Launch& L) {
 // One projected-PCG iteration (kernels of converged coils return at once).
 coil_status step_iteration(coil_t* c, const Launch& L) {
     TRY(gemv(c, L, 1));
-    k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, 1);
+    c->launches += launch_near(L, 1);
     k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 2);
-    k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    c->launches += launch_update(L);
     k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 3);
     unsigned eb = (unsigned)((L.maxN + 255) / 256);
     if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
     k_direction<<<dim3(eb, L.n), 256, 0, L.s>>>(L.d);
-    c->launches += 5;
+    c->launches += 3;
     CK(cudaGetLastError(), "iteration launch");
     return COIL_OK;
 }
@@ -742,7 +769,7 @@ coil_status apply_plain(coil_t* c, const double* dev_p) {
     CK(cudaMemsetAsync(&h.sc->done, 0, sizeof(int), s), "apply");
     k_to_float<<<(h.N + 255) / 256, 256, 0, s>>>(h.x, h.pf, h.N);
     CK(launch_far(single_launch(c), 0), "operator apply");
-    k_near<<<(unsigned)((h.W + 7) / 8), 256, 0, s>>>(c->d, 0);
+    launch_near(single_launch(c), 0);
     CK(cudaGetLastError(), "apply");
     h.dt = dt_save;
     TRY(sync_descriptor(c));
@@ -872,6 +899,8 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.smem = std::max(L.smem, block_smem(ci->h));
         L.maxC = std::max(L.maxC, ci->h.C);
         L.maxNT = std::max(L.maxNT, ci->h.NT);
+        L.seg = L.seg || ci->h.B <= kSegMax;
+        L.big = L.big || ci->h.B > kSegMax;
         if (ci->tc) L.tc.push_back(ci->tc);
     }
     // descriptors and the gathered status live in one device block per call
@@ -1310,10 +1339,10 @@ coil_status adjoint_solve(coil_t* c) {
     k_factor<<<dim3(L.maxW, 1), 32, L.smem, L.s>>>(L.d);
     k_reduce<<<1, 256, 0, L.s>>>(L.d, 0);
     TRY(gemv(c, L, 0));
-    k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, 0);
-    k_init<<<dim3(L.maxW, 1), 32, L.smem, L.s>>>(L.d);
+    c->launches += launch_near(L, 0);
+    c->launches += launch_init(L);
     k_reduce<<<1, 256, 0, L.s>>>(L.d, 1);
-    c->launches += 5;
+    c->launches += 3;
     CK(cudaGetLastError(), "adjoint solve");
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;

@@ -14,6 +14,8 @@ namespace cq {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kMu0 = 4.0e-7 * kPi;
 constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one warp
+constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B rounded up to a power of 2)
+constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
 
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_BF16 = 2 };
 
@@ -76,6 +78,7 @@ struct CoilDev {
     float *pf;                    // FP32 copy of the operator input (ld long)
     double *uT, *ustar, *src, *qgrid;   // grid order [Gz][Gr]
     double *L, *y1, *sigma, *cw, *uw;   // per block
+    double *isigma;                     // 1 / sigma per block
     double *parts;                // 8 x W per-block partials (see step.cu)
     double *partT;                // per grid column partial of T_max
     long long *first_jump, *first_quench;
@@ -94,6 +97,20 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// 1 / sqrt(a) for a > 0 in FP64 without the FP64 divide and square-root
+// sequences (B300's FP64 pipe is narrow): the FP32 reciprocal square root as
+// the seed, then two Newton-Raphson steps y <- y (3 - a y^2) / 2, each of
+// which doubles the number of correct bits (24 -> 48 -> full precision).
+// Inputs outside the FP32 exponent range take the plain expression.
+__device__ __forceinline__ double rsqrt_nr(double a) {
+    if (!(a > 1.0e-30 && a < 1.0e30)) return 1.0 / sqrt(a);
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    y = y * (1.5 - h * y * y);
+    y = y * (1.5 - h * y * y);
+    return y;
 }
 
 // Transport current and applied field of the drive at time t.

@@ -131,7 +131,7 @@ __device__ void project_precond(const CoilDev& c, int w, const double* L, const 
     chol_solve_warp(L, v, B, lane);
     if (c.constrained[w]) {
         double s = warp_block_sum(v, B, lane);
-        double f = s / c.sigma[w];
+        double f = s * c.isigma[w];
         for (int k = lane; k < B; k += 32) v[k] -= y[k] * f;
         __syncwarp();
     }
@@ -157,7 +157,7 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
     for (int k = 0; k < B; ++k) {
         double piv = A[k * B + k];
         if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
-        double rkk = 1.0 / sqrt(piv);                  // the factor keeps 1 / L_kk on its diagonal
+        double rkk = rsqrt_nr(piv);                    // the factor keeps 1 / L_kk on its diagonal
         __syncwarp();
         if (lane == 0) A[k * B + k] = rkk;
         for (int i = k + 1 + lane; i < B; i += 32) A[i * B + k] *= rkk;
@@ -177,7 +177,10 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
     chol_solve_warp(A, y, B, lane);
     double sig = warp_block_sum(y, B, lane);
     for (int k = lane; k < B; k += 32) c.y1[w * B + k] = y[k];
-    if (lane == 0) c.sigma[w] = sig;
+    if (lane == 0) {
+        c.sigma[w] = sig;
+        c.isigma[w] = 1.0 / sig;
+    }
     __syncwarp();
     // preconditioned norm^2 of the right-hand side: R^T Pproj(R) + c_w^2 / sigma
     for (int k = lane; k < B; k += 32) v[k] = c.R[w * B + k];
@@ -212,7 +215,7 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
 __global__ void k_near(const CoilDev* __restrict__ cds, int which) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
-    if (c.sc->done) return;
+    if (c.sc->done || c.B <= kSegMax) return;
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (w >= c.W) return;
@@ -246,7 +249,7 @@ __device__ void project_residual(const CoilDev& c, int w, const double* y, doubl
     double s = 0.0;
     for (int k = lane; k < B; k += 32) s += y[k] * v[k];
     s = warp_sum(s);
-    double u = s / c.sigma[w];
+    double u = s * c.isigma[w];
     for (int k = lane; k < B; k += 32) v[k] -= u;
     __syncwarp();
     if (lane == 0) c.uw[w] = first ? u : c.uw[w] + u;
@@ -256,7 +259,7 @@ __device__ void project_residual(const CoilDev& c, int w, const double* y, doubl
 __global__ void k_init(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
-    if (c.sc->done) return;
+    if (c.sc->done || c.B <= kSegMax) return;
     int w = blockIdx.x;
     if (w >= c.W) return;
     extern __shared__ double sm[];
@@ -293,7 +296,7 @@ __global__ void k_init(const CoilDev* __restrict__ cds) {
 __global__ void k_update(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
-    if (c.sc->done) return;
+    if (c.sc->done || c.B <= kSegMax) return;
     int w = blockIdx.x;
     if (w >= c.W) return;
     extern __shared__ double sm[];
@@ -323,6 +326,162 @@ __global__ void k_update(const CoilDev* __restrict__ cds) {
     }
     rz = warp_sum(rz);
     if (lane == 0) parts[4 * (size_t)c.W + w] = rz;
+}
+
+// ------------------------------------------ blocks of at most 16 elements
+//
+// The same three kernels with 32 / Bp wires per warp (Bp = B rounded up to a
+// power of two): lane kk of a Bp-lane segment holds element kk of the
+// segment's wire, the triangular solves broadcast inside the segment, and
+// sums are xor-butterflies over the segment.  Every FP64 operation on an
+// element is the one of the one-wire-per-warp kernels in the same order (the
+// butterflies there only added the idle lanes' zeros), but each FP64 warp
+// instruction now serves 32 / Bp wires: B300's FP64 pipe is narrow.
+
+__device__ __forceinline__ int seg_width(int B) {
+    int p = 1;
+    while (p < B) p <<= 1;
+    return p;
+}
+
+__device__ __forceinline__ double seg_sum(double v, int Bp) {
+    for (int o = Bp >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// L L^T x = v for the segment's wire (L as chol_solve_warp: reciprocal
+// diagonal); lane kk holds v_kk on entry and x_kk on return.
+__device__ double seg_chol_solve(const double* L, double x, int B, int kk, int base) {
+    for (int k = 0; k < B; ++k) {
+        double xk = __shfl_sync(0xffffffffu, x, base + k) * L[k * B + k];
+        if (kk == k) x = xk;
+        else if (kk > k && kk < B) x -= L[kk * B + k] * xk;
+    }
+    for (int k = B - 1; k >= 0; --k) {
+        double xk = __shfl_sync(0xffffffffu, x, base + k) * L[k * B + k];
+        if (kk == k) x = xk;
+        else if (kk < k) x -= L[k * B + kk] * xk;
+    }
+    return x;
+}
+
+struct Seg {
+    int B, Bp, kk, base, w, e;
+    bool wv, ev;        // wire exists, element exists
+};
+
+__device__ __forceinline__ Seg seg_of(const CoilDev& c, int warp_global) {
+    Seg s;
+    s.B = c.B;
+    s.Bp = seg_width(c.B);
+    const int lane = threadIdx.x & 31;
+    s.kk = lane & (s.Bp - 1);
+    s.base = lane - s.kk;
+    s.w = warp_global * (32 / s.Bp) + lane / s.Bp;
+    s.wv = s.w < c.W;
+    s.ev = s.wv && s.kk < s.B;
+    s.e = s.w * s.B + s.kk;
+    return s;
+}
+
+// The warp's wires' factors into shared memory (zero for wires past the end).
+__device__ __forceinline__ void seg_load_L(const CoilDev& c, int warp_global, double* Ls) {
+    const int B = c.B, G = 32 / seg_width(B), w0 = warp_global * G;
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < G * B * B; i += 32)
+        Ls[i] = (w0 + i / (B * B) < c.W) ? c.L[(size_t)w0 * B * B + i] : 0.0;
+    __syncwarp();
+}
+
+// q_w += (M_ww + dt G_w) p_w; optional partial p^T q (as k_near).
+__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->done || c.B > kSegMax) return;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;
+    const Seg s = seg_of(c, wg);
+    const double* p = which == 0 ? c.x : c.dv;
+    const double pv = s.ev ? p[s.e] : 0.0;
+    const double* nb = c.near + (size_t)c.block_type[s.wv ? s.w : 0] * s.B * s.B;
+    const int row = s.kk < s.B ? s.kk : 0;
+    double acc = 0.0;
+    for (int j = 0; j < s.B; ++j) acc += nb[row * s.B + j] * __shfl_sync(0xffffffffu, pv, s.base + j);
+    double dot = 0.0;
+    if (s.ev) {
+        acc += c.dt * c.G[s.e] * pv;
+        double qe = c.qv[s.e] + acc;
+        c.qv[s.e] = qe;
+        dot = pv * qe;
+    }
+    dot = seg_sum(dot, s.Bp);
+    if (which == 1 && s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = dot;
+}
+
+// Projected residual update and preconditioner of the segment's wire: v is
+// the raw residual on entry; writes res, z and returns z (partial r^T z in rz).
+__device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const Seg& s, const double* L, double v,
+                                                        double y, bool first, double* rz) {
+    const int con = s.wv ? c.constrained[s.w] : 0;
+    const double isg = s.wv ? c.isigma[s.w] : 0.0;
+    // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
+    const double u = seg_sum(y * v, s.Bp) * isg;
+    if (con && s.ev) v -= u;
+    if (s.kk == 0 && s.wv) {
+        if (first) c.uw[s.w] = con ? u : 0.0;
+        else if (con) c.uw[s.w] += u;
+    }
+    if (s.ev) c.res[s.e] = v;
+    // z = A_w^-1 r, then remove the component that changes the wire's total current
+    double z = seg_chol_solve(L, s.kk < s.B ? v : 0.0, s.B, s.kk, s.base);
+    const double f = seg_sum(s.ev ? z : 0.0, s.Bp) * isg;
+    if (con && s.ev) z -= y * f;
+    *rz = seg_sum(s.ev ? v * z : 0.0, s.Bp);
+    return z;
+}
+
+__global__ void __launch_bounds__(32 * kSegWarps)
+k_init_seg(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->done || c.B > kSegMax) return;
+    __shared__ double Ls[kSegWarps][kSegMax * kSegMax * 2];
+    const int warp = threadIdx.x >> 5;
+    const int wg = blockIdx.x * kSegWarps + warp;
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;
+    const Seg s = seg_of(c, wg);
+    seg_load_L(c, wg, Ls[warp]);
+    const double v = s.ev ? c.qv[s.e] + c.R[s.e] : 0.0;
+    const double y = s.ev ? c.y1[s.e] : 0.0;
+    double rz;
+    const double z = seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, true, &rz);
+    if (s.ev) {
+        c.zv[s.e] = z;
+        c.dv[s.e] = -z;
+        c.pf[s.e] = (float)(-z);
+    }
+    if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
+}
+
+__global__ void __launch_bounds__(32 * kSegWarps)
+k_update_seg(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->done || c.B > kSegMax) return;
+    __shared__ double Ls[kSegWarps][kSegMax * kSegMax * 2];
+    const int warp = threadIdx.x >> 5;
+    const int wg = blockIdx.x * kSegWarps + warp;
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;
+    const Seg s = seg_of(c, wg);
+    seg_load_L(c, wg, Ls[warp]);
+    const double alpha = c.sc->alpha;
+    double v = 0.0, y = 0.0;
+    if (s.ev) {
+        c.x[s.e] += alpha * c.dv[s.e];
+        v = c.res[s.e] + alpha * c.qv[s.e];
+        y = c.y1[s.e];
+    }
+    double rz;
+    const double z = seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, false, &rz);
+    if (s.ev) c.zv[s.e] = z;
+    if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
@@ -444,7 +603,7 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     yr = warp_sum(yr);
     mom = warp_sum(mom);
     if (lane == 0) {
-        double u = con ? U + yr / c.sigma[w] : 0.0;
+        double u = con ? U + yr * c.isigma[w] : 0.0;
         c.uw[w] = u;
         parts[5 * (size_t)c.W + w] = u;
         parts[6 * (size_t)c.W + w] = mom;
