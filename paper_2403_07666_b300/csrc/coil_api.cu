@@ -33,11 +33,11 @@ __global__ void k_factor(const CoilDev* __restrict__ cds);
 __global__ void k_near(const CoilDev* __restrict__ cds, int which);
 __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
-__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which);
+__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha);
 __global__ void k_init_seg(const CoilDev* __restrict__ cds);
-__global__ void k_update_seg(const CoilDev* __restrict__ cds);
+__global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
-__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode);
+__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg);
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
 __global__ void k_adi_r(const CoilDev* __restrict__ cds);
 __global__ void k_adi_z(const CoilDev* __restrict__ cds);
@@ -421,6 +421,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     CK(cudaMemsetAsync(h.first_quench, 0xff, W * sizeof(long long), c->stream), "memset");
     TRY(dalloc(c, &h.diag, (size_t)h.diag_cap * COIL_DIAG_WIDTH, "diag"));
     TRY(dalloc(c, &h.sc, 1, "scalars"));
+    TRY(dalloc(c, &h.ticket, 2, "arrival counters"));
     TRY(dalloc(c, &c->readbuf, 5 * (size_t)N, "read buffer"));
 
     // operator: table of distinct entries, dense far part, FP64 near blocks
@@ -466,7 +467,11 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         tc_schedule(tsh, c->n_sm, &work, &range);
         TRY(upload(c, &P.work, work, "tensor-core schedule"));
         TRY(upload(c, &P.range, range, "tensor-core schedule"));
+        h.tc_range = P.range;
         TRY(dalloc(c, &P.pexp, (size_t)NT, "input scale exponents"));
+        P.fused = B <= kSegMax;
+        h.tc_part = P.part;
+        h.tc_pexp = P.pexp;
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
@@ -496,6 +501,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         double* scratch;
         TRY(dalloc(c, &scratch, 1024, "scratch"));
         CK(tc_build_table(c->tc, tab, B, scratch, c->stream), "tensor-core Toeplitz table");
+        h.tc_exT = c->tc->exT;
     } else {
         h.Mfar = M;
         CK(launch_expand(tab, C, NT, B, N, h.ld, o->precision, M, c->stream), "expand");
@@ -593,6 +599,7 @@ struct Launch {
     int format = 0;
     int maxC = 0, maxNT = 0;
     bool seg = false, big = false;   // coils with blocks of <= kSegMax / more elements present
+    bool need_q = false;             // the far apply must leave its result in q (no fused consumer)
 };
 
 Launch single_launch(coil_t* c) {
@@ -623,7 +630,7 @@ cudaError_t launch_far(const Launch& L, int which) {
     if (L.format == 1) return launch_toeplitz(L.d, L.n, L.maxC, L.maxNT, L.maxN, L.n_sm, L.s);
     if (L.format == 2) {
         for (const TcPlan* P : L.tc) {
-            cudaError_t e = launch_toeplitz_tc(*P, L.s);
+            cudaError_t e = launch_toeplitz_tc(*P, L.s, L.need_q || !P->fused);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -670,7 +677,10 @@ dim3 warp_grid(const Launch& L) { return dim3((unsigned)((L.maxW + 7) / 8), L.n)
 // skipping the other kind's coils.  Return the number of launches.
 int launch_near(const Launch& L, int which) {
     if (L.big) k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, which);
-    if (L.seg) k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which);
+    // tensor-core format: small-block coils take the far part from the partial tiles
+    const int far_tiles = L.format == 2 && !L.need_q;
+    if (L.seg)
+        k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1);
     return (int)L.big + (int)L.seg;
 }
 int launch_init(const Launch& L) {
@@ -680,7 +690,7 @@ int launch_init(const Launch& L) {
 }
 int launch_update(const Launch& L) {
     if (L.big) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.seg) k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
+    if (L.seg) k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d, 1);
     return (int)L.big + (int)L.seg;
 }
 
@@ -688,11 +698,11 @@ int launch_update(const Launch& L) {
 coil_status step_prologue(coil_t* c, const Launch& L) {
     k_pointwise<<<warp_grid(L), 256, 0, L.s>>>(L.d);
     k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 0);
+    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
     c->launches += launch_init(L);
-    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 1);
+    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 1, 0);
     c->launches += 4;
     CK(cudaGetLastError(), "step launch");
     return COIL_OK;
@@ -701,14 +711,15 @@ coil_status step_prologue(coil_t* c, const Launch& L) {
 // One projected-PCG iteration (kernels of converged coils return at once).
 coil_status step_iteration(coil_t* c, const Launch& L) {
     TRY(gemv(c, L, 1));
+    // small-block coils reduce alpha and beta in the last CTA of their kernels
     c->launches += launch_near(L, 1);
-    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 2);
+    if (L.big) k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 2, 1);
     c->launches += launch_update(L);
-    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 3);
+    if (L.big) k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 3, 1);
     unsigned eb = (unsigned)((L.maxN + 255) / 256);
     if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
     k_direction<<<dim3(eb, L.n), 256, 0, L.s>>>(L.d);
-    c->launches += 3;
+    c->launches += 1 + 2 * (int)L.big;
     CK(cudaGetLastError(), "iteration launch");
     return COIL_OK;
 }
@@ -1337,11 +1348,11 @@ coil_status adjoint_solve(coil_t* c) {
     const CoilDev& h = c->h;
     Launch L = single_launch(c);
     k_factor<<<dim3(L.maxW, 1), 32, L.smem, L.s>>>(L.d);
-    k_reduce<<<1, 256, 0, L.s>>>(L.d, 0);
+    k_reduce<<<1, 256, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
     c->launches += launch_init(L);
-    k_reduce<<<1, 256, 0, L.s>>>(L.d, 1);
+    k_reduce<<<1, 256, 0, L.s>>>(L.d, 1, 0);
     c->launches += 3;
     CK(cudaGetLastError(), "adjoint solve");
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
@@ -1486,6 +1497,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
             if (grid) {
                 launch_adj_stencil_t(c->d, h, ab, s);
                 Launch L = single_launch(c);
+                L.need_q = true;                     // k_adj_near reads q
                 TRY(gemv(c, L, 1));
                 launch_adj_near(c->d, h, s);
             }

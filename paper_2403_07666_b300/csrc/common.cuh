@@ -16,6 +16,7 @@ constexpr double kMu0 = 4.0e-7 * kPi;
 constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one warp
 constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B rounded up to a power of 2)
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
+constexpr int kTcTileRows = 128;     // channels per tile of the tensor-core Toeplitz apply
 
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_BF16 = 2 };
 
@@ -57,6 +58,13 @@ struct CoilDev {
     const float *tab32;
     float *tpart;
     float *pT;                    // operator input transposed to [c][t] (FP32)
+    // tensor-core Toeplitz apply (format 2): per-CTA partial tiles
+    // [cta][t][kTcTileRows], (first CTA, CTAs) per channel tile, input scale
+    // exponent per turn row, table scale exponent
+    const float *tc_part;
+    const int2 *tc_range;
+    const int *tc_pexp;
+    int tc_exT;
     // stencil: per grid column (resp. row) the first node and three weights
     const int *sr_j0, *sz_j0;
     const double *sr_w, *sz_w;
@@ -85,6 +93,7 @@ struct CoilDev {
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;
+    unsigned *ticket;             // 2 arrival counters of the fused last-CTA reductions
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

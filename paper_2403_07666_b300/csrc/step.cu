@@ -328,6 +328,110 @@ __global__ void k_update(const CoilDev* __restrict__ cds) {
     if (lane == 0) parts[4 * (size_t)c.W + w] = rz;
 }
 
+enum ReduceMode { RED_SCALE = 0, RED_INIT = 1, RED_ALPHA = 2, RED_BETA = 3 };
+
+__device__ double block_reduce_sum(double v, double* sh) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+__device__ double block_reduce_max(double v, double* sh) {
+    v = warp_max(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : -1.0e308;
+    if (wid == 0) v = warp_max(v);
+    __syncthreads();
+    return v;
+}
+
+// Deterministic sum of a per-block partial array by one CTA (any size) and
+// the scalar update that follows it.
+__device__ void reduce_and_update(const CoilDev& c, int mode) {
+    Scalars* sc = c.sc;
+    if ((mode == RED_ALPHA || mode == RED_BETA || mode == RED_INIT) && sc->done) return;
+    __shared__ double sh[32];
+    const double* parts = c.parts;
+    const double* a = parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four loads in flight per thread
+    const int W = c.W, st = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 3 * st < W; i += 4 * st) {
+        s0 += a[i];
+        s1 += a[i + st];
+        s2 += a[i + 2 * st];
+        s3 += a[i + 3 * st];
+    }
+    for (; i < W; i += st) s0 += a[i];
+    double s = block_reduce_sum((s0 + s1) + (s2 + s3), sh);
+    if (threadIdx.x != 0) return;
+    if (mode == RED_SCALE) {
+        sc->scale2 = s;
+        sc->done = 0;
+        sc->iter = 0;
+        sc->status = ST_OK;
+        if (sc->nonpd) { sc->status = ST_NONFINITE; sc->done = 1; }
+        if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
+    } else if (mode == RED_INIT) {
+        sc->rz = s;
+        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(s, 0.0) / sc->scale2) : 0.0;
+        if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
+        else if (s <= c.rtol2 * sc->scale2) sc->done = 1;
+    } else if (mode == RED_ALPHA) {
+        sc->dq = s;
+        if (!(s > 0.0)) {                      // A is SPD on the feasible subspace
+            sc->status = (s == s) ? ST_NONFINITE : ST_NONFINITE;
+            sc->done = 1;
+            return;
+        }
+        sc->alpha = sc->rz / s;
+    } else {
+        double rz_new = s;
+        sc->iter += 1;
+        sc->beta = rz_new / sc->rz;
+        sc->rz = rz_new;
+        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(rz_new, 0.0) / sc->scale2) : 0.0;
+        if (!(rz_new == rz_new)) { sc->status = ST_NONFINITE; sc->done = 1; }
+        else if (rz_new <= c.rtol2 * sc->scale2) sc->done = 1;
+        else if (sc->iter >= c.maxit) { sc->status = ST_NOT_CONVERGED; sc->done = 1; }
+    }
+}
+
+// One CTA per coil; skip_seg: coils whose shared-warp kernels reduce their
+// partials themselves (last CTA) are left alone.
+__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg) {
+    const CoilDev& c = cds[blockIdx.x];
+    if (skip_seg && c.B <= kSegMax) return;
+    reduce_and_update(c, mode);
+}
+
+// Every thread of every CTA of the coil's grid row calls this after its
+// partials are stored; true in the CTA that arrives last (it resets the
+// counter for the next launch).  The fences order the partial stores of all
+// CTAs before the last CTA's loads.
+__device__ bool last_cta(unsigned* ticket) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        is_last = t == gridDim.x - 1;
+        if (is_last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
 // ------------------------------------------ blocks of at most 16 elements
 //
 // The same three kernels with 32 / Bp wires per warp (Bp = B rounded up to a
@@ -393,28 +497,63 @@ __device__ __forceinline__ void seg_load_L(const CoilDev& c, int warp_global, do
     __syncwarp();
 }
 
+// Far-operator value at element e of the tensor-core Toeplitz apply: the sum
+// of the partial tiles of the CTAs that worked on e's channel tile (fixed
+// order, FP64, eight loads in flight), times 2^-(exT + xmin).
+__device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv) {
+    const int t = e / c.C, cc = e - t * c.C;
+    const int2 rg = c.tc_range[cc / kTcTileRows];
+    const size_t tile = (size_t)c.NT * kTcTileRows;
+    const float* p = c.tc_part + (size_t)rg.x * tile + (size_t)t * kTcTileRows + (cc % kTcTileRows);
+    double s = 0.0;
+    int k = 0;
+    for (; k + 8 <= rg.y; k += 8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = p[(size_t)(k + i) * tile];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += (double)v[i];
+    }
+    for (; k < rg.y; ++k) s += (double)p[(size_t)k * tile];
+    return s * inv;
+}
+
 // q_w += (M_ww + dt G_w) p_w; optional partial p^T q (as k_near).
-__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which) {
+// far_tiles: the far part comes from the tensor-core apply's partial tiles
+// (its separate reduction was skipped) instead of q.  fuse_alpha: the last
+// CTA sums the p^T q partials and sets alpha (the k_reduce ALPHA step).
+__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->done || c.B > kSegMax) return;
-    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (wg * (32 / seg_width(c.B)) >= c.W) return;
-    const Seg s = seg_of(c, wg);
-    const double* p = which == 0 ? c.x : c.dv;
-    const double pv = s.ev ? p[s.e] : 0.0;
-    const double* nb = c.near + (size_t)c.block_type[s.wv ? s.w : 0] * s.B * s.B;
-    const int row = s.kk < s.B ? s.kk : 0;
-    double acc = 0.0;
-    for (int j = 0; j < s.B; ++j) acc += nb[row * s.B + j] * __shfl_sync(0xffffffffu, pv, s.base + j);
-    double dot = 0.0;
-    if (s.ev) {
-        acc += c.dt * c.G[s.e] * pv;
-        double qe = c.qv[s.e] + acc;
-        c.qv[s.e] = qe;
-        dot = pv * qe;
+    double inv = 0.0;
+    if (far_tiles) {
+        __shared__ int xmin;
+        if (threadIdx.x == 0) xmin = 1 << 30;
+        __syncthreads();
+        for (int t = threadIdx.x; t < c.NT; t += blockDim.x) atomicMin(&xmin, c.tc_pexp[t]);
+        __syncthreads();
+        inv = ldexp(1.0, -(c.tc_exT + xmin));
     }
-    dot = seg_sum(dot, s.Bp);
-    if (which == 1 && s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = dot;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
+        const Seg s = seg_of(c, wg);
+        const double* p = which == 0 ? c.x : c.dv;
+        const double pv = s.ev ? p[s.e] : 0.0;
+        const double* nb = c.near + (size_t)c.block_type[s.wv ? s.w : 0] * s.B * s.B;
+        const int row = s.kk < s.B ? s.kk : 0;
+        double acc = 0.0;
+        for (int j = 0; j < s.B; ++j) acc += nb[row * s.B + j] * __shfl_sync(0xffffffffu, pv, s.base + j);
+        double dot = 0.0;
+        if (s.ev) {
+            acc += c.dt * c.G[s.e] * pv;
+            double qe = (far_tiles ? tc_far_sum(c, s.e, inv) : c.qv[s.e]) + acc;
+            c.qv[s.e] = qe;
+            dot = pv * qe;
+        }
+        dot = seg_sum(dot, s.Bp);
+        if (which == 1 && s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = dot;
+    }
+    if (fuse_alpha && last_cta(c.ticket)) reduce_and_update(c, RED_ALPHA);
 }
 
 // Projected residual update and preconditioner of the segment's wire: v is
@@ -461,27 +600,32 @@ k_init_seg(const CoilDev* __restrict__ cds) {
     if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
 }
 
+// fuse_beta: the last CTA sums the r^T z partials and sets beta and the
+// convergence flags (the k_reduce BETA step).
 __global__ void __launch_bounds__(32 * kSegWarps)
-k_update_seg(const CoilDev* __restrict__ cds) {
+k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->done || c.B > kSegMax) return;
     __shared__ double Ls[kSegWarps][kSegMax * kSegMax * 2];
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
-    if (wg * (32 / seg_width(c.B)) >= c.W) return;
-    const Seg s = seg_of(c, wg);
-    seg_load_L(c, wg, Ls[warp]);
-    const double alpha = c.sc->alpha;
-    double v = 0.0, y = 0.0;
-    if (s.ev) {
-        c.x[s.e] += alpha * c.dv[s.e];
-        v = c.res[s.e] + alpha * c.qv[s.e];
-        y = c.y1[s.e];
+    if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
+        const Seg s = seg_of(c, wg);
+        seg_load_L(c, wg, Ls[warp]);
+        const double alpha = c.sc->alpha;
+        double v = 0.0, y = 0.0;
+        if (s.ev) {
+            c.x[s.e] += alpha * c.dv[s.e];
+            v = c.res[s.e] + alpha * c.qv[s.e];
+            y = c.y1[s.e];
+        }
+        double rz;
+        const double z =
+            seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, false, &rz);
+        if (s.ev) c.zv[s.e] = z;
+        if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
     }
-    double rz;
-    const double z = seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, false, &rz);
-    if (s.ev) c.zv[s.e] = z;
-    if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
+    if (fuse_beta && last_cta(c.ticket + 1)) reduce_and_update(c, RED_BETA);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
@@ -493,85 +637,6 @@ __global__ void k_direction(const CoilDev* __restrict__ cds) {
         double d = -c.zv[e] + beta * c.dv[e];
         c.dv[e] = d;
         c.pf[e] = (float)d;
-    }
-}
-
-enum ReduceMode { RED_SCALE = 0, RED_INIT = 1, RED_ALPHA = 2, RED_BETA = 3 };
-
-__device__ double block_reduce_sum(double v, double* sh) {
-    v = warp_sum(v);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    int nw = blockDim.x >> 5;
-    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
-    if (wid == 0) v = warp_sum(v);
-    __syncthreads();
-    return v;
-}
-
-__device__ double block_reduce_max(double v, double* sh) {
-    v = warp_max(v);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    int nw = blockDim.x >> 5;
-    v = threadIdx.x < nw ? sh[threadIdx.x] : -1.0e308;
-    if (wid == 0) v = warp_max(v);
-    __syncthreads();
-    return v;
-}
-
-// One CTA per coil: deterministic sum of a per-block partial array and the
-// scalar update that follows it.
-__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode) {
-    const CoilDev& c = cds[blockIdx.x];
-    Scalars* sc = c.sc;
-    if ((mode == RED_ALPHA || mode == RED_BETA || mode == RED_INIT) && sc->done) return;
-    __shared__ double sh[32];
-    const double* parts = c.parts;
-    const double* a = parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four loads in flight per thread
-    const int W = c.W, st = blockDim.x;
-    int i = threadIdx.x;
-    for (; i + 3 * st < W; i += 4 * st) {
-        s0 += a[i];
-        s1 += a[i + st];
-        s2 += a[i + 2 * st];
-        s3 += a[i + 3 * st];
-    }
-    for (; i < W; i += st) s0 += a[i];
-    double s = block_reduce_sum((s0 + s1) + (s2 + s3), sh);
-    if (threadIdx.x != 0) return;
-    if (mode == RED_SCALE) {
-        sc->scale2 = s;
-        sc->done = 0;
-        sc->iter = 0;
-        sc->status = ST_OK;
-        if (sc->nonpd) { sc->status = ST_NONFINITE; sc->done = 1; }
-        if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
-    } else if (mode == RED_INIT) {
-        sc->rz = s;
-        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(s, 0.0) / sc->scale2) : 0.0;
-        if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
-        else if (s <= c.rtol2 * sc->scale2) sc->done = 1;
-    } else if (mode == RED_ALPHA) {
-        sc->dq = s;
-        if (!(s > 0.0)) {                      // A is SPD on the feasible subspace
-            sc->status = (s == s) ? ST_NONFINITE : ST_NONFINITE;
-            sc->done = 1;
-            return;
-        }
-        sc->alpha = sc->rz / s;
-    } else {
-        double rz_new = s;
-        sc->iter += 1;
-        sc->beta = rz_new / sc->rz;
-        sc->rz = rz_new;
-        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(rz_new, 0.0) / sc->scale2) : 0.0;
-        if (!(rz_new == rz_new)) { sc->status = ST_NONFINITE; sc->done = 1; }
-        else if (rz_new <= c.rtol2 * sc->scale2) sc->done = 1;
-        else if (sc->iter >= c.maxit) { sc->status = ST_NOT_CONVERGED; sc->done = 1; }
     }
 }
 

@@ -57,7 +57,7 @@
 
 namespace cq {
 
-constexpr int kTcM = 128;                        // channels per tile (MMA M)
+constexpr int kTcM = kTcTileRows;                // channels per tile (MMA M)
 constexpr int kTcK = 64;                         // channels per k block (one 128-byte FP16 row)
 constexpr int kTcPad = 16;                       // zero rows staged above and below the winding
 constexpr int kTcEpiWarps = 8;                   // epilogue warps: 4 lane quadrants x 2 column parities
@@ -687,13 +687,15 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
     return e;
 }
 
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s) {
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q) {
     const TcShape& sh = P.sh;
     k_tc_split<<<sh.NT, 256, 0, s>>>(P.d, sh, P.p16, P.pexp);
     k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.d, sh, P.work, P.pexp, P.part);
-    int rb = (sh.N + 255) / 256;
-    if (rb > 148 * 8) rb = 148 * 8;
-    k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.range, P.pexp, P.exT);
+    if (write_q) {
+        int rb = (sh.N + 255) / 256;
+        if (rb > 148 * 8) rb = 148 * 8;
+        k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.range, P.pexp, P.exT);
+    }
     return cudaGetLastError();
 }
 

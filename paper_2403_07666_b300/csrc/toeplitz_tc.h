@@ -36,6 +36,7 @@ struct TcPlan {
     int* pexp = nullptr;        // NT input scale exponents (one per turn row)
     int exT = 0;                // table scale 2^exT
     size_t smem = 0;            // dynamic shared memory per CTA
+    bool fused = false;         // the coil's near kernel sums the partial tiles itself
 };
 
 constexpr int kTcMaxTurns = 224;   // staged p rows NT + 32 fit one TMA box (<= 256)
@@ -52,7 +53,9 @@ size_t tc_smem_bytes(const TcShape& sh);
 cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* scratch, cudaStream_t s);
 // Encode the two tensor maps (after t16 and p16 are allocated).
 cudaError_t tc_encode_maps(TcPlan* P, const char** why);
-// q = M_far p for the coil of P (pf -> qv of its descriptor).
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s);
+// M_far p for the coil of P (from pf): the split, the apply into the partial
+// tiles and, with write_q, their reduction into qv (otherwise the coil's
+// shared-warp near kernel sums the tiles).
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q);
 
 }  // namespace cq
