@@ -73,9 +73,52 @@ def pick_workload(name):
 
 # ------------------------------------------------------------------ clocks
 
-class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml): SM
+    clock, its maximum and the clock-event reason bits of the CUDA device."""
 
+    def __init__(self, gpu):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib, self.ct = lib, ctypes
+        self.h = ctypes.c_void_p()
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(gpu)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        except Exception:
+            pass
+        if bus is None or lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu), ctypes.byref(self.h)) != 0:
+                raise RuntimeError("no NVML handle")
+        v = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(v)) != 0:      # NVML_CLOCK_SM = 1
+            raise RuntimeError("max clock query failed")
+        self.maxsm = float(v.value)
+        self.sample()
+
+    def sample(self):
+        ct, lib = self.ct, self.lib
+        v, bits = ct.c_uint(), ct.c_ulonglong()
+        if lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(v)) != 0:
+            raise RuntimeError("clock query failed")
+        if lib.nvmlDeviceGetCurrentClocksThrottleReasons(self.h, ct.byref(bits)) != 0:
+            raise RuntimeError("reason query failed")
+        return (float(v.value), self.maxsm, int(bits.value))
+
+
+class ClockSampler:
+    """SM clock and clock-event reasons during the timed region.
+
+    In-process NVML polling every 5 ms (plus one sample on entry and one on
+    exit), so that even a timed region of a few tens of milliseconds is
+    covered; nvidia-smi -lms 200 is the fallback when libnvidia-ml is not
+    loadable."""
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -84,8 +127,33 @@ class ClockSampler:
         self.gpu = gpu
         self.proc = None
         self.lines = []
+        self.samples = []            # (sm MHz, max sm MHz, reason bits)
+        self.nv = None
+        self.stop = threading.Event()
+        try:
+            self.nv = _Nvml(gpu)
+        except Exception:
+            self.nv = None
+
+    def _sample(self):
+        self.samples.append(self.nv.sample())
+
+    def _poll(self):
+        while not self.stop.wait(0.005):
+            try:
+                self._sample()
+            except Exception:
+                return
 
     def __enter__(self):
+        if self.nv is not None:
+            try:
+                self._sample()
+                self.t = threading.Thread(target=self._poll, daemon=True)
+                self.t.start()
+                return self
+            except Exception:
+                self.nv = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -102,6 +170,13 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        if self.nv is not None:
+            self.stop.set()
+            self.t.join(timeout=1)
+            try:
+                self._sample()
+            except Exception:
+                pass
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -111,7 +186,13 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for f, m, bits in self.samples:
+            sm.append(f)
+            mx.append(m)
+            for nm, b in self.REASONS:
+                if bits & b:
+                    reasons.add(nm)
+        names = [nm for nm, _ in self.REASONS]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
@@ -126,7 +207,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvml 5 ms" if self.samples else "nvidia-smi 200 ms"}
 
 
 # ------------------------------------------------------------- oracle (CPU)
@@ -370,7 +452,7 @@ def roofline_of(fmt, precision, N, op_bytes, op_ms, hbm, peak_kind):
         prof = PROFILED_TRAFFIC.get("toeplitz_tc")
         traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": "k_toeplitz_tc (+pmax, split, reduce)", "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": "k_toeplitz_tc (+split)", "peak_kind": peak_kind,
                 "avg_launch_ms": op_ms, "bytes_per_launch": nbytes, "table_bytes": op_bytes,
                 "tensor_tflops_fp16": 6.0 * N * N / (op_ms / 1e3) / 1e12}
     achieved = op_bytes / (op_ms / 1e3) / 1e9

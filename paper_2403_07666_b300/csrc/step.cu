@@ -354,16 +354,14 @@ __device__ double block_reduce_max(double v, double* sh) {
     return v;
 }
 
-// Deterministic sum of a per-block partial array by one CTA (any size) and
-// the scalar update that follows it.
-__device__ void reduce_and_update(const CoilDev& c, int mode) {
+// Deterministic sum of a partial array a[0..W) by one CTA (any size) and the
+// scalar update that follows it.
+__device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, int W) {
     Scalars* sc = c.sc;
     if ((mode == RED_ALPHA || mode == RED_BETA || mode == RED_INIT) && sc->done) return;
     __shared__ double sh[32];
-    const double* parts = c.parts;
-    const double* a = parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four loads in flight per thread
-    const int W = c.W, st = blockDim.x;
+    const int st = blockDim.x;
     int i = threadIdx.x;
     for (; i + 3 * st < W; i += 4 * st) {
         s0 += a[i];
@@ -411,25 +409,35 @@ __device__ void reduce_and_update(const CoilDev& c, int mode) {
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg) {
     const CoilDev& c = cds[blockIdx.x];
     if (skip_seg && c.B <= kSegMax) return;
-    reduce_and_update(c, mode);
+    reduce_and_update(c, mode, c.parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W, c.W);
 }
 
-// Every thread of every CTA of the coil's grid row calls this after its
-// partials are stored; true in the CTA that arrives last (it resets the
-// counter for the next launch).  The fences order the partial stores of all
-// CTAs before the last CTA's loads.
-__device__ bool last_cta(unsigned* ticket) {
+// Fused reduction of a per-wire value held by the head lane of each wire's
+// segment: every thread of the coil's first n_cta CTAs calls this.  Each CTA
+// sums its wires in a fixed order (butterfly per warp, then warps in order)
+// into parts row 7 at its index; the CTA that arrives last on the counter
+// (which it resets for the next launch) sums those n_cta values and does the
+// scalar update of `mode`.  The fences order every CTA's partial store before
+// the last CTA's loads.
+__device__ void fused_reduce(const CoilDev& c, double head_value, unsigned* ticket, int n_cta, int mode) {
+    __shared__ double wsum[32];
     __shared__ int is_last;
-    __threadfence();
+    const double v = warp_sum(head_value);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
+    double* ctap = c.parts + 7 * (size_t)c.W;
     if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(ticket, 1u);
-        is_last = t == gridDim.x - 1;
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        ctap[blockIdx.x] = t;
+        __threadfence();
+        is_last = atomicAdd(ticket, 1u) == (unsigned)n_cta - 1u;
         if (is_last) *ticket = 0u;
     }
     __syncthreads();
-    if (is_last) __threadfence();
-    return is_last != 0;
+    if (!is_last) return;
+    __threadfence();
+    reduce_and_update(c, mode, ctap, n_cta);
 }
 
 // ------------------------------------------ blocks of at most 16 elements
@@ -498,24 +506,33 @@ __device__ __forceinline__ void seg_load_L(const CoilDev& c, int warp_global, do
 }
 
 // Far-operator value at element e of the tensor-core Toeplitz apply: the sum
-// of the partial tiles of the CTAs that worked on e's channel tile (fixed
-// order, FP64, eight loads in flight), times 2^-(exT + xmin).
+// of the partial tiles of the CTAs that worked on e's channel tile, in a fixed
+// order with eight loads in flight, times 2^-(exT + xmin).  The sum runs on
+// the FP32 pipe with Kahan's compensated summation and returns s - comp in
+// FP64: about twice FP32's precision for these few terms, at a fraction of
+// the cost of FP64 additions on B300.
+__device__ __forceinline__ void kahan_add(float v, float& s, float& comp) {
+    const float y = v - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+}
 __device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv) {
     const int t = e / c.C, cc = e - t * c.C;
     const int2 rg = c.tc_range[cc / kTcTileRows];
     const size_t tile = (size_t)c.NT * kTcTileRows;
     const float* p = c.tc_part + (size_t)rg.x * tile + (size_t)t * kTcTileRows + (cc % kTcTileRows);
-    double s = 0.0;
+    float s = 0.f, comp = 0.f;
     int k = 0;
     for (; k + 8 <= rg.y; k += 8) {
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = p[(size_t)(k + i) * tile];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) s += (double)v[i];
+        for (int i = 0; i < 8; ++i) kahan_add(v[i], s, comp);
     }
-    for (; k < rg.y; ++k) s += (double)p[(size_t)k * tile];
-    return s * inv;
+    for (; k < rg.y; ++k) kahan_add(p[(size_t)k * tile], s, comp);
+    return ((double)s - (double)comp) * inv;
 }
 
 // q_w += (M_ww + dt G_w) p_w; optional partial p^T q (as k_near).
@@ -524,7 +541,9 @@ __device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv
 // CTA sums the p^T q partials and sets alpha (the k_reduce ALPHA step).
 __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha) {
     const CoilDev& c = cds[blockIdx.y];
-    if (c.sc->done || c.B > kSegMax) return;
+    const int per_cta = (int)(blockDim.x >> 5) * (32 / seg_width(c.B));   // wires per CTA
+    const int n_cta = (c.W + per_cta - 1) / per_cta;
+    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
     double inv = 0.0;
     if (far_tiles) {
         __shared__ int xmin;
@@ -535,6 +554,7 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
         inv = ldexp(1.0, -(c.tc_exT + xmin));
     }
     const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    double head = 0.0;                                  // p^T q of the lane's wire on segment heads
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
         const double* p = which == 0 ? c.x : c.dv;
@@ -551,9 +571,12 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
             dot = pv * qe;
         }
         dot = seg_sum(dot, s.Bp);
-        if (which == 1 && s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = dot;
+        if (which == 1 && s.kk == 0 && s.wv) {
+            if (fuse_alpha) head = dot;
+            else c.parts[4 * (size_t)c.W + s.w] = dot;
+        }
     }
-    if (fuse_alpha && last_cta(c.ticket)) reduce_and_update(c, RED_ALPHA);
+    if (fuse_alpha) fused_reduce(c, head, c.ticket, n_cta, RED_ALPHA);
 }
 
 // Projected residual update and preconditioner of the segment's wire: v is
@@ -605,10 +628,13 @@ k_init_seg(const CoilDev* __restrict__ cds) {
 __global__ void __launch_bounds__(32 * kSegWarps)
 k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
     const CoilDev& c = cds[blockIdx.y];
-    if (c.sc->done || c.B > kSegMax) return;
+    const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
+    const int n_cta = (c.W + per_cta - 1) / per_cta;
+    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
     __shared__ double Ls[kSegWarps][kSegMax * kSegMax * 2];
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
+    double head = 0.0;                                  // r^T z of the lane's wire on segment heads
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
         seg_load_L(c, wg, Ls[warp]);
@@ -623,9 +649,12 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
         const double z =
             seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, false, &rz);
         if (s.ev) c.zv[s.e] = z;
-        if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
+        if (s.kk == 0 && s.wv) {
+            if (fuse_beta) head = rz;
+            else c.parts[4 * (size_t)c.W + s.w] = rz;
+        }
     }
-    if (fuse_beta && last_cta(c.ticket + 1)) reduce_and_update(c, RED_BETA);
+    if (fuse_beta) fused_reduce(c, head, c.ticket + 1, n_cta, RED_BETA);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
