@@ -130,7 +130,8 @@ __global__ void k_adj_mult(const CoilDev* __restrict__ cds) {
 // Jc and its partial derivatives (zero outside the superconducting region).
 struct JcD { double Jc, dBm, dT, df, dCe; };
 
-__device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double eps, double f) {
+// ep = |eps|^p_eps of the element (tabulated at coil creation).
+__device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double ep, double f) {
     JcD d = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (c.jc_model == 1) {
         d.Jc = f * c.Jc0;
@@ -140,11 +141,11 @@ __device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double
     double tr = T / c.Tc;
     double Bc2 = c.Bc2_0 * (1.0 - tr * tr);
     if (!(T < c.Tc && Bm < Bc2)) return d;
-    double ep = pow(fabs(eps), c.p_eps);
     double S = 1.0 - c.C_eps * ep;
     if (!(S > 0.0)) return d;
     double bfac = 1.0 - Bm / Bc2;
-    double core = c.Jc0 * pow(1.0 - tr, 1.5) * (bfac * bfac) / sqrt(Bm + c.B_reg);
+    double omt = 1.0 - tr;
+    double core = c.Jc0 * (omt * sqrt(omt)) * (bfac * bfac) / sqrt(Bm + c.B_reg);
     d.Jc = f * core * S;
     d.df = core * S;
     d.dCe = -f * core * ep;
@@ -206,7 +207,7 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab) {
         double Bm = sqrt(Br * Br + Bz * Bz);
         int fil = c.mat[e];
         JcD jd = {0.0, 0.0, 0.0, 0.0, 0.0};
-        if (fil) jd = jc_with_derivatives(c, Bm, T, c.strain[e], c.jc_factor[e]);
+        if (fil) jd = jc_with_derivatives(c, Bm, T, c.strain_pow[e], c.jc_factor[e]);
         double I = c.I[e];
         double J = I / a;
         EJD ej = ej_with_derivatives(c, fil, J, jd.Jc);

@@ -36,6 +36,8 @@ __global__ void k_update(const CoilDev* __restrict__ cds);
 __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha);
 __global__ void k_init_seg(const CoilDev* __restrict__ cds);
 __global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta);
+__global__ void k_pointwise_seg(const CoilDev* __restrict__ cds);
+__global__ void k_factor_seg(const CoilDev* __restrict__ cds);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg);
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
@@ -350,6 +352,9 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(upload(c, &dp, area, "area")); h.area = dp;
     TRY(upload(c, &dp, jf, "jc_factor")); h.jc_factor = dp;
     TRY(upload(c, &dp, st, "strain")); h.strain = dp;
+    std::vector<double> stp(N);
+    for (int e = 0; e < N; ++e) stp[e] = pow(fabs(st[e]), m->p_eps);
+    TRY(upload(c, &dp, stp, "strain power")); h.strain_pow = dp;
     TRY(upload(c, &ip, mt, "mat")); h.mat = ip;
     TRY(upload(c, &ip, constrained, "constrained")); h.constrained = ip;
     TRY(upload(c, &ip, block_type, "block_type")); h.block_type = ip;
@@ -688,6 +693,16 @@ int launch_init(const Launch& L) {
     if (L.seg) k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
     return (int)L.big + (int)L.seg;
 }
+int launch_pointwise(const Launch& L) {
+    if (L.big) k_pointwise<<<warp_grid(L), 256, 0, L.s>>>(L.d);
+    if (L.seg) k_pointwise_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d);
+    return (int)L.big + (int)L.seg;
+}
+int launch_factor(const Launch& L) {
+    if (L.big) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.seg) k_factor_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
+    return (int)L.big + (int)L.seg;
+}
 int launch_update(const Launch& L) {
     if (L.big) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
     if (L.seg) k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d, 1);
@@ -696,14 +711,14 @@ int launch_update(const Launch& L) {
 
 // Pointwise, factorisation, right-hand-side norm, initial residual.
 coil_status step_prologue(coil_t* c, const Launch& L) {
-    k_pointwise<<<warp_grid(L), 256, 0, L.s>>>(L.d);
-    k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    c->launches += launch_pointwise(L);
+    c->launches += launch_factor(L);
     k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
     c->launches += launch_init(L);
     k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 1, 0);
-    c->launches += 4;
+    c->launches += 2;
     CK(cudaGetLastError(), "step launch");
     return COIL_OK;
 }
@@ -1347,13 +1362,13 @@ coil_status set_device_time(coil_t* c, double t, long long step) {
 coil_status adjoint_solve(coil_t* c) {
     const CoilDev& h = c->h;
     Launch L = single_launch(c);
-    k_factor<<<dim3(L.maxW, 1), 32, L.smem, L.s>>>(L.d);
+    c->launches += launch_factor(L);
     k_reduce<<<1, 256, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
     c->launches += launch_init(L);
     k_reduce<<<1, 256, 0, L.s>>>(L.d, 1, 0);
-    c->launches += 3;
+    c->launches += 2;
     CK(cudaGetLastError(), "adjoint solve");
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
@@ -1487,8 +1502,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
             TRY(state_copy(c, slot, false, false));
             TRY(set_device_time(c, t_k[k - k0], st_ck[sg] + (k - k0)));
             AdjBufs ab{lamI, lamI_next, lamU, lamU_next, abuf, bbuf, lamQ, lamBr, lamBz, slot + xoff, gf, gparts};
-            unsigned wb = (unsigned)((h.W + 7) / 8);
-            k_pointwise<<<dim3(wb, 1), 256, 0, s>>>(c->d);
+            c->launches += launch_pointwise(single_launch(c));
             if (thermal) launch_adj_thermal(c->d, h, ab, s);
             launch_adj_setup(c->d, h, ab, s);
             CK(cudaGetLastError(), "adjoint launch");
@@ -1502,7 +1516,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
                 launch_adj_near(c->d, h, s);
             }
             launch_adj_accum(c->d, h, ab, k >= 1 ? dL_dm[k - 1] : 0.0, grid ? 1 : 0, s);
-            c->launches += 6;
+            c->launches += 5;
             CK(cudaGetLastError(), "adjoint launch");
             std::swap(lamI, lamI_next);
             std::swap(lamU, lamU_next);

@@ -43,6 +43,7 @@ struct CoilDev {
     long long ld;                 // leading dimension (elements) of the far operator
     // element data (element order)
     const double *r, *area, *jc_factor, *strain;
+    const double *strain_pow;     // |strain|^p_eps per element
     const int *mat;               // 1 filament, 0 Cu
     const int *elem_grid;         // i_z * Gr + i_r
     const int *grid_elem;         // inverse map

@@ -34,14 +34,16 @@ __device__ __forceinline__ void field_at(const CoilDev& c, int e, double Ba, dou
     *Br = -dz / (2.0 * kPi * r);
 }
 
-__device__ __forceinline__ double critical_current(const CoilDev& c, double Bm, double T, double eps, double f) {
+// pe = |eps|^p_eps of the element (constant, tabulated at coil creation).
+__device__ __forceinline__ double critical_current(const CoilDev& c, double Bm, double T, double pe, double f) {
     if (c.jc_model == 1) return f * c.Jc0;
     double tr = T / c.Tc;
     double Bc2 = c.Bc2_0 * (1.0 - tr * tr);
     if (!(T < c.Tc && Bm < Bc2)) return 0.0;
-    double strain = fmax(0.0, 1.0 - c.C_eps * pow(fabs(eps), c.p_eps));
+    double strain = fmax(0.0, 1.0 - c.C_eps * pe);
     double bfac = 1.0 - Bm / Bc2;
-    return f * c.Jc0 * pow(1.0 - tr, 1.5) * (bfac * bfac) / sqrt(Bm + c.B_reg) * strain;
+    double omt = 1.0 - tr;
+    return f * c.Jc0 * (omt * sqrt(omt)) * (bfac * bfac) / sqrt(Bm + c.B_reg) * strain;
 }
 
 // rho/rho_n, (dE/dJ)/rho_n and |J|/Jc of the parallel power-law / normal law.

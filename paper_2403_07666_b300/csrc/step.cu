@@ -24,7 +24,7 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
     double* parts = c.parts;
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
-    if (w >= c.W) return;
+    if (w >= c.W || c.B <= kSegMax) return;
     Scalars* sc = c.sc;
     double t0 = sc->t, dt = c.dt, t1 = t0 + dt;
     double It1 = drive_current(c, t1);
@@ -45,7 +45,7 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
         }
         double Bm = sqrt(Br * Br + Bz * Bz);
         int fil = c.mat[e];
-        double Jc = fil ? critical_current(c, Bm, T, c.strain[e], c.jc_factor[e]) : 0.0;
+        double Jc = fil ? critical_current(c, Bm, T, c.strain_pow[e], c.jc_factor[e]) : 0.0;
         double I = c.I[e];
         double J = I / a;
         double frac, dfac, jrat;
@@ -142,7 +142,7 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
     int w = blockIdx.x;
-    if (w >= c.W) return;
+    if (w >= c.W || c.B <= kSegMax) return;
     extern __shared__ double sm[];
     int B = c.B, lane = threadIdx.x;
     double* A = sm;
@@ -655,6 +655,140 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
         }
     }
     if (fuse_beta) fused_reduce(c, head, c.ticket + 1, n_cta, RED_BETA);
+}
+
+__device__ __forceinline__ double seg_max(double v, int Bp) {
+    for (int o = Bp >> 1; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// k_pointwise for blocks of at most 16 elements (32 / Bp wires per warp).
+__global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.B > kSegMax) return;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
+    const Seg s = seg_of(c, wg);
+    Scalars* sc = c.sc;
+    const double t0 = sc->t, dt = c.dt, t1 = t0 + dt;
+    const double It1 = drive_current(c, t1);
+    const double Ba0 = drive_field(c, t0), Ba1 = drive_field(c, t1);
+    const double dBa = (Ba1 - Ba0) / dt;
+    if (s.w == 0 && s.kk == 0) {
+        sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
+        sc->nonpd = 0;                         // k_factor of this step sets it again if needed
+    }
+    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0;
+    if (s.ev) {
+        const int e = s.e;
+        double r = c.r[e], a = c.area[e];
+        double Br = 0.0, Bz = 0.0, T = c.T_bath;
+        if (c.has_grid) {
+            field_at(c, e, Ba0, &Br, &Bz);
+            T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
+        }
+        double Bm = sqrt(Br * Br + Bz * Bz);
+        int fil = c.mat[e];
+        double Jc = fil ? critical_current(c, Bm, T, c.strain_pow[e], c.jc_factor[e]) : 0.0;
+        double I = c.I[e];
+        double J = I / a;
+        double frac, dfac, jrat;
+        ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
+        double rho = c.rho_n * frac;
+        double E = rho * J;
+        double q = E * J;
+        c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
+        c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
+        if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
+        sumI = I;
+        pj = q * 2.0 * kPi * r * a;
+        if (fil) { jr = jrat; rhof = frac; nfil = 1.0; }
+    }
+    sumI = seg_sum(sumI, s.Bp);
+    pj = seg_sum(pj, s.Bp);
+    jr = seg_max(jr, s.Bp);
+    rhof = seg_sum(rhof, s.Bp);
+    nfil = seg_sum(nfil, s.Bp);
+    if (s.kk == 0 && s.wv) {
+        const int w = s.w;
+        double* parts = c.parts;
+        c.cw[w] = c.constrained[w] ? (It1 - sumI) / dt : 0.0;
+        double mean_rho = nfil > 0.0 ? rhof / nfil : 0.0;
+        parts[0 * (size_t)c.W + w] = pj;
+        parts[1 * (size_t)c.W + w] = jr;
+        parts[2 * (size_t)c.W + w] = mean_rho;
+        long long st = sc->step;
+        if (c.first_jump[w] < 0 && jr > 1.0) c.first_jump[w] = st;
+        if (c.first_quench[w] < 0 && mean_rho > 0.95) c.first_quench[w] = st;
+    }
+}
+
+// k_factor for blocks of at most 16 elements: the same Cholesky (lane kk owns
+// row kk of its wire's block in shared memory), y = A^-1 1, sigma, the
+// right-hand-side norm and the projected warm start.
+__global__ void __launch_bounds__(32 * kSegWarps)
+k_factor_seg(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.B > kSegMax) return;
+    __shared__ double As[kSegWarps][kSegMax * kSegMax * 2];
+    const int warp = threadIdx.x >> 5;
+    const int wg = blockIdx.x * kSegWarps + warp;
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
+    const Seg s = seg_of(c, wg);
+    const int B = s.B, kk = s.kk, w = s.w, e = s.e;
+    double* A = As[warp] + ((threadIdx.x & 31) / s.Bp) * B * B;
+    if (s.wv) {
+        const double* nb = c.near + (size_t)c.block_type[w] * B * B;
+        for (int i = kk; i < B * B; i += s.Bp) A[i] = nb[i];
+    } else {
+        for (int i = kk; i < B * B; i += s.Bp) A[i] = (i % (B + 1) == 0) ? 1.0 : 0.0;   // identity
+    }
+    __syncwarp();
+    if (s.ev) A[kk * B + kk] += c.dt * c.G[e];
+    __syncwarp();
+    int bad = 0;
+    for (int k = 0; k < B; ++k) {
+        double piv = A[k * B + k];
+        if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
+        double rkk = rsqrt_nr(piv);                    // the factor keeps 1 / L_kk on its diagonal
+        __syncwarp();
+        if (kk == k) A[k * B + k] = rkk;
+        if (kk > k && kk < B) A[kk * B + k] *= rkk;
+        __syncwarp();
+        if (kk > k && kk < B) {
+            double lik = A[kk * B + k];
+            for (int j = k + 1; j <= kk; ++j) A[kk * B + j] -= lik * A[j * B + k];
+        }
+        __syncwarp();
+    }
+    if (bad && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
+    if (s.wv)
+        for (int i = kk; i < B * B; i += s.Bp) c.L[(size_t)w * B * B + i] = A[i];
+    // y = A_w^-1 1, sigma = 1^T y
+    const double y = seg_chol_solve(A, kk < B ? 1.0 : 0.0, B, kk, s.base);
+    const double sig = seg_sum(s.ev ? y : 0.0, s.Bp);
+    if (s.ev) c.y1[e] = y;
+    if (kk == 0 && s.wv) {
+        c.sigma[w] = sig;
+        c.isigma[w] = 1.0 / sig;
+    }
+    // preconditioned norm^2 of the right-hand side: R^T Pproj(R) + c_w^2 / sigma
+    const double R = s.ev ? c.R[e] : 0.0;
+    double v = seg_chol_solve(A, R, B, kk, s.base);
+    const double cw = s.wv ? c.cw[w] : 0.0;
+    const int con = s.wv ? c.constrained[w] : 0;
+    const double sv = seg_sum(s.ev ? v : 0.0, s.Bp);
+    if (con && s.ev) v -= y * (sv / sig);
+    const double rn = seg_sum(s.ev ? R * v : 0.0, s.Bp);
+    // warm start from the previous step's Idot, moved onto this step's constraint
+    const double sx = seg_sum(s.ev ? c.x[e] : 0.0, s.Bp);
+    const double corr = con ? (cw - sx) / sig : 0.0;
+    if (s.ev) {
+        double xe = c.x[e] + corr * y;
+        c.x[e] = xe;
+        c.pf[e] = (float)xe;
+    }
+    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw / sig : 0.0);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
