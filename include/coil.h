@@ -127,14 +127,15 @@ typedef struct {
  * distinct blocks are stored (C^2 (2 n_turns - 1) entries instead of N^2, the
  * same FP32 values as the dense form) and applied as a Toeplitz-structured
  * FP32 matrix product.
- * TOEPLITZ_TC (regular solenoids with n_turns <= 224, FP32 precision only):
- * the same blocks, each entry stored as two FP16 numbers hi + lo after a
- * power-of-two scaling (about 22 significant bits, 4 bytes per entry), applied
- * on the tensor cores as hi*hi + hi*lo + lo*hi products of an equally split
- * input with FP32 accumulation; chunk sums are added in FP64.  Unsupported
- * shapes get COIL_ERR_INVALID.  A bounded wait inside the apply kernel that
- * runs out makes the step return COIL_ERR_CUDA ("tensor-core apply timed
- * out"). */
+ * TOEPLITZ_TC (regular solenoids with n_turns <= 112, FP32 precision only):
+ * the blocks of offsets >= 0 (the others are their transposes), each entry
+ * stored as two FP16 numbers hi + lo after a power-of-two scaling (about 22
+ * significant bits, 4 bytes per entry: half the bytes of the FP32 Toeplitz
+ * table), applied on the tensor cores to an equally split input (all four
+ * products hi*hi, hi*lo, lo*hi, lo*lo) with FP32 accumulation per stage and
+ * compensated sums across stages.  Unsupported shapes get COIL_ERR_INVALID.
+ * A bounded wait inside the apply kernel that runs out makes the step return
+ * COIL_ERR_CUDA ("tensor-core apply timed out"). */
 enum { COIL_FORMAT_DENSE = 0, COIL_FORMAT_TOEPLITZ = 1, COIL_FORMAT_TOEPLITZ_TC = 2 };
 
 /*

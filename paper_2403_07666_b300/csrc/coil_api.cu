@@ -213,7 +213,7 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
     if (o->format != COIL_FORMAT_DENSE && (g->kind != COIL_GEOM_SOLENOID || o->precision != PREC_FP32))
         return fail(c, COIL_ERR_INVALID, "the Toeplitz formats need a solenoid and FP32 precision");
     if (o->format == COIL_FORMAT_TOEPLITZ_TC && g->n_turns > kTcMaxTurns)
-        return fail(c, COIL_ERR_INVALID, "the tensor-core Toeplitz format takes at most 224 turns");
+        return fail(c, COIL_ERR_INVALID, "the tensor-core Toeplitz format takes at most 112 turns");
     if (g->kind == COIL_GEOM_SOLENOID) {
         if (g->n_layers < 1 || g->n_turns < 1 || g->n_sub < 1)
             return fail(c, COIL_ERR_INVALID, "solenoid needs n_layers, n_turns, n_sub >= 1");
@@ -1109,9 +1109,10 @@ coil_status coil_read_operator(coil_t* c, double* M) {
             }
     }
     if (h.op_format == 2) {
-        // (hi + lo) 2^-exT of the split FP16 table [half][offset][k block][c][64]
+        // (hi + lo) 2^-exT of the split FP16 table [half][offset >= 0][k block][c][64];
+        // offset d < 0 reads T_{-d} transposed
         const TcShape& sh = c->tc->sh;
-        size_t C = sh.C, NT = sh.NT, nkb = sh.n_kb;
+        size_t C = sh.C, nkb = sh.n_kb;
         size_t half_n = tc_table_halves(sh) / 2;
         std::vector<__half> t16(2 * half_n);
         CK(cudaMemcpy(t16.data(), c->tc->t16, t16.size() * sizeof(__half), cudaMemcpyDeviceToHost),
@@ -1120,8 +1121,8 @@ coil_status coil_read_operator(coil_t* c, double* M) {
         for (size_t i = 0; i < N; ++i)
             for (size_t j = 0; j < N; ++j) {
                 long long d = (long long)(i / C) - (long long)(j / C);
-                size_t cj = j % C;
-                size_t k = (((size_t)(d + (long long)NT - 1) * nkb + cj / 64) * C + (i % C)) * 64 + cj % 64;
+                size_t ci = d >= 0 ? i % C : j % C, cj = d >= 0 ? j % C : i % C;
+                size_t k = (((size_t)(d >= 0 ? d : -d) * nkb + cj / 64) * C + ci) * 64 + cj % 64;
                 M[i * N + j] = ((double)__half2float(t16[k]) + (double)__half2float(t16[half_n + k])) * inv;
             }
     }

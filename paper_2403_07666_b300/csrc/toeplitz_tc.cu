@@ -40,9 +40,9 @@
 // copy of p once per k block.  The
 // table takes 2 x 2 bytes per entry, as many as FP32.
 //
-// CTA roles (320 threads): warp 0 issues the TMA loads, warp 1 owns the TMEM
-// accumulators and issues the MMAs, warps 2-9 drain the accumulators (lane
-// quadrant warp % 4, even or odd 16-column groups).  Every wait on an
+// CTA roles (352 threads): warp 0 issues the TMA loads, warps 1 and 2 issue
+// the MMAs of alternate stages (warp 1 owns the TMEM), warps 3-10 drain the
+// accumulators (lane quadrant warp % 4, even or odd 8-turn groups).  Every wait on an
 // mbarrier is bounded: on a timeout the CTA raises an abort flag, the others
 // stop issuing, the copies and MMAs already in flight are waited for (again
 // bounded), the TMEM is freed, and the coil's status word reports the failure
@@ -59,11 +59,15 @@ namespace cq {
 
 constexpr int kTcM = kTcTileRows;                // channels per tile (MMA M)
 constexpr int kTcK = 64;                         // channels per k block (one 128-byte FP16 row)
-constexpr int kTcPad = 16;                       // zero rows staged above and below the winding
+constexpr int kTcPad = 8;                        // zero turn rows staged above and below the winding
 constexpr int kTcEpiWarps = 8;                   // epilogue warps: 4 lane quadrants x 2 column parities
-constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
-constexpr int kTcGroups = 7;                     // 16-column groups per epilogue warp (NT <= 224)
+constexpr int kTcThreads = 96 + 32 * kTcEpiWarps;      // producer, two MMA issuers, epilogue
+constexpr int kTcGroups = 7;                     // 8-turn groups per epilogue warp (NT <= 112)
 constexpr uint32_t kTcAStage = 2u * kTcM * kTcK * 2u;   // hi + lo table tiles, 32 KB
+// MN-major A (128-byte swizzle): byte offsets between the two 64-channel
+// blocks along M (8 KB) and between 8-row groups along K (1 KB)
+constexpr uint32_t kTcMnLbo = 8192u;
+constexpr uint32_t kTcMnSbo = 1024u;
 constexpr int kTcSmemLimit = 227 * 1024;         // dynamic shared memory per CTA (opt-in maximum)
 constexpr long long kTcWait = 1LL << 31;         // cycles before a wait gives up (~1 s)
 constexpr int kTcBStages = 1;                    // staged copies of p (a CTA meets few k blocks)
@@ -108,6 +112,10 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
         }
     }
 }
+// Inline fast path for a phase that has already completed.
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    return mbar_try(bar, parity) || mbar_wait(bar, parity, abort_flag);
+}
 // The same, ignoring the abort flag (used to retire work already in flight).
 __device__ __noinline__ bool mbar_wait_final(uint32_t bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
@@ -123,6 +131,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 
@@ -153,10 +170,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
 }
-// Instruction descriptor of kind::f16: FP16 A and B (both K-major), FP32 D,
-// M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_f16(int n) {
-    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+// Instruction descriptor of kind::f16: FP16 A and B, FP32 D, M = 128, N = n;
+// B K-major, A K-major or (a_mn) MN-major.
+__device__ __forceinline__ uint32_t idesc_f16(int n, bool a_mn) {
+    return (1u << 4) | ((a_mn ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -198,7 +215,8 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // The apply
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAT,
+              const __grid_constant__ CUtensorMap tmB,
               const CoilDev* __restrict__ cd, const TcShape sh, const int4* __restrict__ work,
               const int* __restrict__ pexp, float* __restrict__ part) {
     const CoilDev& c = *cd;
@@ -207,7 +225,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const uint32_t raw = su32(tc_smem);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = tc_smem + (base - raw);
-    const uint32_t b_stage = 256u * (uint32_t)sh.NR;             // hi + lo staged p, bytes
+    const uint32_t b_stage = 512u * (uint32_t)sh.NR;             // hi + lo staged p of 128 channels, bytes
     const uint32_t b_pitch = (b_stage + 127u) & ~127u;
     const uint32_t sA = base;                                     // sh.stages x 32 KB (1024-aligned)
     const uint32_t sB = base + (uint32_t)sh.stages * kTcAStage;   // kTcBStages staged copies of p
@@ -217,8 +235,11 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + bar_off + 8 * kTcBars(S));
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + bar_off + 8 * kTcBars(S) + 4);
     int* xmin_s = reinterpret_cast<int*>(gbase + bar_off + 8 * kTcBars(S) + 8);
-    // relative inverse input scale of staged row r (p row r - 16; zero outside the winding)
-    float* inv_s = reinterpret_cast<float*>(gbase + bar_off + 8 * kTcBars(S) + 16);
+    // relative inverse input scale of staged row r (p row r - 16; zero outside the
+    // winding), in four copies shifted by 0..3 entries (copy k holds entry r + k at
+    // r), so that any 16 consecutive entries are four aligned 16-byte loads
+    const int scp = (sh.NR + 7) & ~3;                             // floats per copy
+    float* inv_s = reinterpret_cast<float*>(gbase + ((bar_off + 8 * kTcBars(S) + 16 + 15) & ~15u));
     // barriers: a_full[S], a_empty[S], b_full[kTcBStages], b_empty[kTcBStages], acc_full[4],
     // acc_empty[4], mma_done
     const uint32_t a_full = sBar, a_empty = sBar + 8u * S;
@@ -227,23 +248,25 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const uint32_t mma_done = acc_empty + 32u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // this CTA's work: channel tile ct, stages s0 <= s < s1 of that tile in the
-    // order (k block kb = s / ndist, offset d = s % ndist - (NT - 1))
+    // This CTA's work: channel tile ct, steps wk.y <= sg < wk.z.  Step sg = (k, D),
+    // k = sg / NT, D = sg % NT, pairs the tile with column tile cb = (k - ct) mod
+    // n_ct and runs the stages (kb, +D) and, for D > 0, (kb, -D), kb = 2 cb, 2 cb + 1.
+    // Column tile cb's CTA with the same step range is at step k with cb and ct
+    // exchanged: it reads the same 128 x 128 region of the stored T_D, transposed,
+    // at the same time, so that region comes from DRAM once and from L2 once.
     const int4 wk = work[blockIdx.x];
-    const int c0 = wk.x * kTcM;
-    const int ndist = 2 * sh.NT - 1;
-    const int kb_first = wk.y / ndist, kb_last = (wk.z - 1) / ndist;
-    // offsets of k block kb inside the range: [d_begin(kb), d_end(kb))
-    auto d_begin = [&](int kb) { return (kb == kb_first ? wk.y - kb * ndist : 0) - (sh.NT - 1); };
-    auto d_end = [&](int kb) { return (kb == kb_last ? wk.z - kb * ndist : ndist) - (sh.NT - 1); };
+    const int ct = wk.x, c0 = ct * kTcM;
+    auto col_tile = [&](int sg) { return (sg / sh.NT - ct + sh.n_ct) % sh.n_ct; };
     const int n_acc = sh.n_acc;
     const uint32_t acc_cols = (uint32_t)sh.acc_cols;
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < kTcBars(S); ++b) {
             const uint32_t bar = sBar + 8u * b;
-            // acc_empty: one arrival per epilogue warp; the others: one arrival (+ bytes)
-            mbar_init(bar, (bar >= acc_empty && bar < acc_empty + 32u) ? (uint32_t)kTcEpiWarps : 1u);
+            // acc_empty: one arrival per epilogue warp; b_empty and mma_done: one per MMA
+            // issuer; the others: one arrival (+ bytes)
+            const bool two = bar == b_empty || bar == mma_done;
+            mbar_init(bar, (bar >= acc_empty && bar < acc_empty + 32u) ? (uint32_t)kTcEpiWarps : (two ? 2u : 1u));
         }
         *abort_flag = 0;
         *xmin_s = 1 << 30;
@@ -259,9 +282,9 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
-    for (int r = threadIdx.x; r < sh.NR; r += blockDim.x) {
-        const int t = r - kTcPad;
-        inv_s[r] = (t >= 0 && t < sh.NT) ? ldexpf(1.f, *xmin_s - pexp[t]) : 0.f;
+    for (int i = threadIdx.x; i < 4 * scp; i += blockDim.x) {
+        const int k = i / scp, r = i - k * scp + k, t = r - kTcPad;
+        inv_s[i] = (t >= 0 && t < sh.NT) ? ldexpf(1.f, *xmin_s - pexp[t]) : 0.f;
     }
     __syncthreads();
 
@@ -271,112 +294,154 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         uint32_t pa = 0, pb = 0;
         uint32_t a_used = 0, a_par = 0, b_used = 0, b_par = 0;   // bit s: stage s loaded / its parity
         bool ok = true;
-        for (int kb = kb_first; kb <= kb_last && ok; ++kb) {
-            ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
-            if (!ok) break;
-            mbar_expect_tx(b_full + 8u * sb, b_stage);
-            tma_load_4d(sB + (uint32_t)sb * b_pitch, &tmB, 0, -kTcPad, kb * (kTcK / 8), 0, b_full + 8u * sb);
-            b_used |= 1u << sb;
-            b_par = (b_par & ~(1u << sb)) | (pb << sb);
-            if (++sb == kTcBStages) { sb = 0; pb ^= 1u; }
-            for (int d = d_begin(kb), de = d_end(kb); d < de; ++d) {
-                ok = mbar_wait(a_empty + 8u * sa, pa ^ 1u, abort_flag);
+        for (int sg = wk.y; sg < wk.z && ok; ++sg) {
+            const int D = sg % sh.NT, cb = col_tile(sg), nk = min(2, sh.n_kb - 2 * cb);
+            if (sg == wk.y || D == 0) {                 // a new column tile: its staged copy of p
+                ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
                 if (!ok) break;
-                mbar_expect_tx(a_full + 8u * sa, kTcAStage);
-                tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmA, 0, c0, kb, d + sh.NT - 1, 0, a_full + 8u * sa);
-                a_used |= 1u << sa;
-                a_par = (a_par & ~(1u << sa)) | (pa << sa);
-                if (++sa == S) { sa = 0; pa ^= 1u; }
+                mbar_expect_tx(b_full + 8u * sb, b_stage);
+                // rows -2 kTcPad .. 2 NT + 2 kTcPad - 1 (turn rows -kTcPad .., hi and lo) of 16 chunks
+                tma_load_3d(sB + (uint32_t)sb * b_pitch, &tmB, 0, -2 * kTcPad, cb * (kTcM / 8), b_full + 8u * sb);
+                b_used |= 1u << sb;
+                b_par = (b_par & ~(1u << sb)) | (pb << sb);
+                if (++sb == kTcBStages) { sb = 0; pb ^= 1u; }
             }
+            for (int sgn = 0; sgn < (D > 0 ? 2 : 1) && ok; ++sgn)
+                for (int j = 0; j < nk && ok; ++j) {
+                    const int kb = 2 * cb + j, d = sgn ? -D : D;
+                    ok = mbar_wait_fast(a_empty + 8u * sa, pa ^ 1u, abort_flag);
+                    if (!ok) break;
+                    mbar_expect_tx(a_full + 8u * sa, kTcAStage);
+                    // offset d >= 0: T_d tile, K-major; d < 0: T_d = T_{-d}^T, the stored tile
+                    // of T_{-d} (rows c' of this k block, columns c of the channel tile)
+                    if (d >= 0)
+                        tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmA, 0, c0, kb, d, 0, a_full + 8u * sa);
+                    else
+                        tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmAT, 0, kb * kTcK, c0 / kTcK, -d, 0,
+                                    a_full + 8u * sa);
+                    a_used |= 1u << sa;
+                    a_par = (a_par & ~(1u << sa)) | (pa << sa);
+                    if (++sa == S) { sa = 0; pa ^= 1u; }
+                }
         }
         // retire the copies in flight (only the latest load of a stage can be)
         for (int s = 0; s < S; ++s)
             if (a_used >> s & 1u) mbar_wait_final(a_full + 8u * s, a_par >> s & 1u, kTcWait);
         for (int s = 0; s < kTcBStages; ++s)
             if (b_used >> s & 1u) mbar_wait_final(b_full + 8u * s, b_par >> s & 1u, kTcWait);
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer: stage (kb, d) accumulates into TMEM accumulator i (round robin),
-        // its first MMA overwriting the columns it covers
-        int sa = 0, sb = 0, ai = 0;
-        uint32_t pa = 0, pb = 0, pe = 0;   // pe bit i: phase of acc_empty[i]
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+        // ---- MMA issuers: stage i of this CTA (table slot i % S, TMEM accumulator
+        // i % n_acc, the latter's first MMA overwriting the columns it covers) is
+        // issued by warp 1 + i % 2, so that two threads' issue overheads overlap;
+        // each issuer frees a staged copy of p (two arrivals) once it has no more
+        // stages on it
+        const int me = warp - 1;
+        int i = 0, grp = 0;
         bool ok = true;
-        for (int kb = kb_first; kb <= kb_last && ok; ++kb) {
-            ok = mbar_wait(b_full + 8u * sb, pb, abort_flag);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t bh = sB + (uint32_t)sb * b_pitch;
-            const uint32_t bl = bh + 128u * (uint32_t)sh.NR;
-            for (int d = d_begin(kb), de = d_end(kb); d < de; ++d) {
-                ok = mbar_wait(a_full + 8u * sa, pa, abort_flag);
-                if (ok) ok = mbar_wait(acc_empty + 8u * ai, ((pe >> ai) & 1u) ^ 1u, abort_flag);
+        const uint32_t bbase = sB;                      // one staged copy (kTcBStages == 1)
+        for (int sg = wk.y; sg < wk.z && ok; ++sg) {
+            const int D = sg % sh.NT, cb = col_tile(sg), nk = min(2, sh.n_kb - 2 * cb);
+            if (sg == wk.y || D == 0) {
+                if (sg != wk.y) mma_commit(b_empty);    // free once this issuer's MMAs on it finish
+                ok = mbar_wait(b_full, (uint32_t)grp & 1u, abort_flag);
                 if (!ok) break;
-                pe ^= 1u << ai;
+                ++grp;
+                tc_fence_after();
+            }
+            for (int sgn = 0; sgn < (D > 0 ? 2 : 1) && ok; ++sgn)
+              for (int j = 0; j < nk && ok; ++j, ++i) {
+                if ((i & 1) != me) continue;
+                const int d = sgn ? -D : D;
+                const int sa = i % S, ai = i % n_acc;
+                // staged copy: [16 chunks of 8 channels][2 NR rows: hi, lo of each turn row][8];
+                // k block j of the column tile = chunks 8 j .. 8 j + 7
+                const uint32_t bj = bbase + (uint32_t)j * 256u * (uint32_t)sh.NR;
+                ok = mbar_wait_fast(a_full + 8u * sa, (uint32_t)(i / S) & 1u, abort_flag);
+                if (ok) ok = mbar_wait_fast(acc_empty + 8u * ai, ((uint32_t)(i / n_acc) & 1u) ^ 1u, abort_flag);
+                if (!ok) break;
                 tc_fence_after();
                 const int t_first = d > 0 ? d : 0;
                 const int t_end = d < 0 ? sh.NT + d : sh.NT;
-                const int ts = t_first & ~15;
-                const int n = (t_end - ts + 15) & ~15;
-                const uint32_t idesc = idesc_f16(n);
-                const uint32_t dcol = tmem + (uint32_t)ai * acc_cols + (uint32_t)ts;
-                const uint32_t row0 = (uint32_t)(ts - d + kTcPad);
+                const int ts = t_first & ~7;
+                const int n = (t_end - ts + 7) & ~7;            // turns covered (2 n accumulator columns)
+                const bool amn = d < 0;
                 const uint32_t ah = sA + (uint32_t)sa * kTcAStage;
-                const uint32_t al = ah + (uint32_t)kTcM * 128u;
+                // K-major A: rows of 64 channels c', 8-row groups 1 KB apart, K step = 32 B.
+                // MN-major A: rows of 64 channels c (two 8 KB blocks along M), one row per
+                // c', 8-row groups 1 KB apart, K step = 16 rows = 2 KB.  B: K step = two
+                // 8-channel chunks.  The descriptors are built once per stage and advanced
+                // by adding to their address field (addr >> 4, below 2^14 for any shared
+                // memory address, so the additions never carry out of it).
+                const uint64_t a_hi = amn ? sdesc(ah, kTcMnLbo, kTcMnSbo, 2u) : sdesc(ah, 16u, 1024u, 2u);
+                const uint64_t a_lo = a_hi + (((uint64_t)kTcM * 128u) >> 4);
+                const uint64_t a_step = amn ? (2048u >> 4) : (32u >> 4);
+                // B: the 2 n rows of turns ts .. ts + n - 1 (source rows ts - d ..), hi and lo
+                // interleaved, so A_hi x B gives hi*hi | hi*lo and A_lo x B gives lo*hi | lo*lo
+                // in column pairs 2 t, 2 t + 1; at most 128 turns (N = 256) per MMA
+                const uint64_t b_step = (2u * 32u * (uint32_t)sh.NR) >> 4;
+                for (int part0 = 0; part0 < n; part0 += 128) {
+                    const int np = min(128, n - part0);
+                    const uint32_t idesc = idesc_f16(2 * np, amn);
+                    const uint32_t dcol = tmem + (uint32_t)ai * acc_cols + 2u * (uint32_t)(ts + part0);
+                    const uint32_t row0 = (uint32_t)(ts + part0 - d + kTcPad);
+                    const uint64_t b0 = sdesc(bj + 32u * row0, 32u * (uint32_t)sh.NR, 128u, 0u);
 #pragma unroll
-                for (int s = 0; s < kTcK / 16; ++s) {
-                    const uint64_t a_hi = sdesc(ah + 32u * s, 16u, 1024u, 2u);
-                    const uint64_t a_lo = sdesc(al + 32u * s, 16u, 1024u, 2u);
-                    const uint32_t boff = (uint32_t)(2 * s) * 16u * (uint32_t)sh.NR + 16u * row0;
-                    const uint64_t b_hi = sdesc(bh + boff, 16u * (uint32_t)sh.NR, 128u, 0u);
-                    const uint64_t b_lo = sdesc(bl + boff, 16u * (uint32_t)sh.NR, 128u, 0u);
-                    mma_f16(dcol, a_hi, b_hi, idesc, s > 0 ? 1u : 0u);
-                    mma_f16(dcol, a_hi, b_lo, idesc, 1u);
-                    mma_f16(dcol, a_lo, b_hi, idesc, 1u);
+                    for (int s = 0; s < kTcK / 16; ++s) {
+                        mma_f16(dcol, a_hi + s * a_step, b0 + s * b_step, idesc, s > 0 ? 1u : 0u);
+                        mma_f16(dcol, a_lo + s * a_step, b0 + s * b_step, idesc, 1u);
+                    }
                 }
                 mma_commit(a_empty + 8u * sa);
                 mma_commit(acc_full + 8u * ai);
-                if (++sa == S) { sa = 0; pa ^= 1u; }
-                if (++ai == n_acc) ai = 0;
-            }
-            mma_commit(b_empty + 8u * sb);
-            if (++sb == kTcBStages) { sb = 0; pb ^= 1u; }
+              }
         }
         // every MMA issued (also after an abort) completes before the TMEM is freed
         mma_commit(mma_done);
         if (!mbar_wait_final(mma_done, 0u, kTcWait)) *abort_flag = 1;
-    } else if (warp >= 2) {
+    } else if (warp >= 3) {
         // ---- epilogue: each stage's accumulator is added into FP32 registers (lane
-        // quadrant warp % 4, column groups of parity h), then released to the MMAs
+        // quadrant warp % 4, turn groups of parity h), then released to the MMAs
         const int q = warp & 3;
-        const int h = (warp - 2) >> 2;
+        const int h = (warp - 3) >> 2;
         const int cc = c0 + 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        float acc[kTcGroups][16];
+        float acc[kTcGroups][8];                       // turn group g = 2 gi + h: turns 8 g .. 8 g + 7
 #pragma unroll
         for (int g = 0; g < kTcGroups; ++g)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[g][j] = 0.f;
+            for (int j = 0; j < 8; ++j) acc[g][j] = 0.f;
         int ai = 0;
         uint32_t pf = 0;
         bool ok = true;
-        for (int kb = kb_first; kb <= kb_last && ok; ++kb) {
-            for (int d = d_begin(kb), de = d_end(kb); d < de; ++d) {
-                ok = __all_sync(0xffffffffu, mbar_wait(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag));
+        for (int sg = wk.y; sg < wk.z && ok; ++sg) {
+            const int D = sg % sh.NT, nk = min(2, sh.n_kb - 2 * col_tile(sg));
+            for (int st = 0; st < (D > 0 ? 2 : 1) * nk; ++st) {
+                const int d = st >= nk ? -D : D;
+                ok = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag));
                 if (!ok) break;
                 pf ^= 1u << ai;
                 tc_fence_after();
                 const int t_first = d > 0 ? d : 0;
                 const int t_end = d < 0 ? sh.NT + d : sh.NT;
-                const int g_lo = t_first >> 4, g_hi = (t_end + 15) >> 4;
+                const int g_lo = t_first >> 3, g_hi = (t_end + 7) >> 3;
                 const uint32_t src = lane_base + (uint32_t)ai * acc_cols;
-                const float* sc = inv_s + (kTcPad - d);        // sc[t]: scale of source row t - d
 #pragma unroll
                 for (int gi = 0; gi < kTcGroups; ++gi) {
                     const int g = 2 * gi + h;
                     if (g >= g_lo && g < g_hi) {
-                        float v[16];
+                        float v[16];                            // column pairs of turns 8 g .. 8 g + 7
                         tmem_ld16(src + 16u * (uint32_t)g, v);
+                        // scales of source rows 8 g + i - d (staged rows + kTcPad): copy a % 4
+                        const int a = 8 * g + kTcPad - d;
+                        const float4* sc4 = reinterpret_cast<const float4*>(inv_s + (a & 3) * scp + (a & ~3));
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[gi][j] = fmaf(v[j], sc[16 * g + j], acc[gi][j]);
+                        for (int q4 = 0; q4 < 2; ++q4) {
+                            const float4 f = sc4[q4];
+                            acc[gi][4 * q4 + 0] = fmaf(v[8 * q4 + 0] + v[8 * q4 + 1], f.x, acc[gi][4 * q4 + 0]);
+                            acc[gi][4 * q4 + 1] = fmaf(v[8 * q4 + 2] + v[8 * q4 + 3], f.y, acc[gi][4 * q4 + 1]);
+                            acc[gi][4 * q4 + 2] = fmaf(v[8 * q4 + 4] + v[8 * q4 + 5], f.z, acc[gi][4 * q4 + 2]);
+                            acc[gi][4 * q4 + 3] = fmaf(v[8 * q4 + 6] + v[8 * q4 + 7], f.w, acc[gi][4 * q4 + 3]);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -390,9 +455,9 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             float* out = part + (size_t)blockIdx.x * sh.NT * kTcM + 32 * q + lane;
 #pragma unroll
             for (int gi = 0; gi < kTcGroups; ++gi) {
-                const int t0 = 16 * (2 * gi + h);
+                const int t0 = 8 * (2 * gi + h);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
+                for (int j = 0; j < 8; ++j)
                     if (t0 + j < sh.NT) out[(size_t)(t0 + j) * kTcM] = acc[gi][j];
             }
         }
@@ -441,8 +506,8 @@ __host__ __device__ inline int tc_exponent(double m) {
     return x > 120 ? 120 : (x < -120 ? -120 : x);
 }
 
-// p -> FP16 hi/lo in [half][c'/8][t][c' % 8] order; one block per turn row t,
-// scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.
+// p -> FP16 hi/lo in [c'/8][t][hi, lo][c' % 8] order (row 2 t + h); one block per
+// turn row t, scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.
 __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
                            int* __restrict__ pexp) {
     const CoilDev& c = *cd;
@@ -454,13 +519,12 @@ __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __h
     const int x = tc_exponent((double)block_max_f(m));
     if (threadIdx.x == 0) pexp[t] = x;
     const float s = ldexpf(1.f, x);
-    const int total = sh.Cp * sh.NT;
     for (int cc = threadIdx.x; cc < sh.Cp; cc += blockDim.x) {
         const float v = cc < sh.C ? row[cc] * s : 0.f;
         const __half hi = __float2half_rn(v);
-        const int idx = ((cc >> 3) * sh.NT + t) * 8 + (cc & 7);
+        const int idx = (((cc >> 3) * sh.NT + t) * 2) * 8 + (cc & 7);
         p16[idx] = hi;
-        p16[total + idx] = __float2half_rn(v - __half2float(hi));
+        p16[idx + 8] = __float2half_rn(v - __half2float(hi));
     }
 }
 
@@ -510,13 +574,14 @@ __global__ void k_tc_absmax(const double* __restrict__ tab, long long n, double*
     }
 }
 
-// FP64 table [offset][c][c'] -> FP16 hi/lo [half][offset][k block][c][64]
-// (c' = 64 k block + column), scaled by 2^exT, so that the 128 x 64 tile of
-// one stage is a contiguous 16 KB per half; intra-wire entries of offset 0
-// are zero (applied from the FP64 near blocks), padding columns c' >= C zero.
+// FP64 table [offset + NT - 1][c][c'] -> FP16 hi/lo [half][offset][k block][c][64]
+// for offsets 0 .. NT - 1 only (T_{-d} = T_d^T is read transposed), c' = 64 k
+// block + column, scaled by 2^exT, so that the 128 x 64 tile of one stage is a
+// contiguous 16 KB per half; intra-wire entries of offset 0 are zero (applied
+// from the FP64 near blocks), padding columns c' >= C zero.
 __global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int wire_div, int exT,
                            __half* __restrict__ t16) {
-    const long long total = (long long)(2 * sh.NT - 1) * sh.n_kb * sh.C * kTcK;
+    const long long total = (long long)sh.NT * sh.n_kb * sh.C * kTcK;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int kk = (int)(idx % kTcK);
@@ -525,8 +590,8 @@ __global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int
         const long long rest2 = rest / sh.C;
         const int cj = (int)(rest2 % sh.n_kb) * kTcK + kk;
         const int dd = (int)(rest2 / sh.n_kb);
-        double v = cj < sh.C ? tab[((long long)dd * sh.C + ci) * sh.C + cj] : 0.0;
-        if (dd == sh.NT - 1 && ci / wire_div == cj / wire_div) v = 0.0;
+        double v = cj < sh.C ? tab[((long long)(dd + sh.NT - 1) * sh.C + ci) * sh.C + cj] : 0.0;
+        if (dd == 0 && ci / wire_div == cj / wire_div) v = 0.0;
         v = ldexp(v, exT);
         const __half hi = __double2half(v);
         t16[idx] = hi;
@@ -538,9 +603,9 @@ __global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int
 // Host side
 // ---------------------------------------------------------------------------
 size_t tc_smem_bytes(const TcShape& sh) {
-    size_t b_pitch = ((size_t)256 * sh.NR + 127) & ~(size_t)127;
-    return 1024 + kTcBStages * b_pitch + (size_t)sh.stages * kTcAStage + 8 * (size_t)kTcBars(sh.stages) + 16 +
-           4 * (size_t)sh.NR;
+    size_t b_pitch = ((size_t)512 * sh.NR + 127) & ~(size_t)127;
+    return 1024 + kTcBStages * b_pitch + (size_t)sh.stages * kTcAStage + 8 * (size_t)kTcBars(sh.stages) + 32 +
+           16 * (size_t)((sh.NR + 7) & ~3);
 }
 
 bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
@@ -554,56 +619,44 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
     s.n_ct = (C + kTcM - 1) / kTcM;
     s.n_kb = (s.Cp + kTcK - 1) / kTcK;
     s.n_cta = (int)tc_schedule(s, n_sm, nullptr, nullptr);
-    int used = (NT + 15) & ~15;
+    int used = 2 * ((NT + 7) & ~7);   // two accumulator columns per turn
     s.acc_cols = 32;
     while (s.acc_cols < used) s.acc_cols *= 2;
     s.n_acc = 512 / s.acc_cols > 4 ? 4 : 512 / s.acc_cols;   // 2..4 accumulators in 512 columns
     s.ncols = s.n_acc * s.acc_cols;
     const size_t limit = kTcSmemLimit;
-    s.stages = 6;                      // 192 KB of table copies in flight per SM
+    s.stages = 6;                      // up to 192 KB of table copies in flight per SM
     while (s.stages > 2 && tc_smem_bytes(s) > limit) --s.stages;
     if (tc_smem_bytes(s) > limit) return false;
     *sh = s;
     return true;
 }
 
-// CTAs per channel tile: start from one each and keep adding a CTA to the
-// tile whose CTAs carry the most stages, while CTAs are left (n_sm in all, or
-// one per tile when there are more tiles than SMs) and no tile has more CTAs
-// than stages.  Stages, not bytes, are balanced: a stage's time is set by the
-// latency of its copy (a few in flight per SM), which the ragged last tile's
-// half-height stages take as well.
-// A tile's stages (n_kb x (2 NT - 1)) are split into contiguous near-equal
-// ranges.  work[cta] = (tile, first stage, end stage, 0); range[tile] =
-// (first CTA, CTAs).  Returns the number of CTAs.
+// The same number of CTAs for every channel tile (n_sm / n_ct, at least one,
+// at most one per step) and the same step ranges for all tiles: tile ct's
+// j-th CTA and tile cb's j-th CTA meet the 128 x 128 region (ct, cb) of every
+// stored offset block at the same step, one of them reading it transposed.
+// A tile's n_ct NT steps are split into contiguous near-equal ranges.
+// work[cta] = (tile, first step, end step, 0); range[tile] = (first CTA, CTAs).
+// Returns the number of CTAs.
 size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::vector<int2>* range) {
-    const long long stages = (long long)sh.n_kb * (2 * sh.NT - 1);
-    std::vector<int> cnt(sh.n_ct, 1);
-    long long total = sh.n_ct;
-    while (total < n_sm) {
-        int best = -1;
-        double load = -1.0;
-        for (int ct = 0; ct < sh.n_ct; ++ct) {
-            double l = (double)stages / cnt[ct];
-            if (cnt[ct] < stages && l > load) { load = l; best = ct; }
-        }
-        if (best < 0) break;
-        cnt[best] += 1;
-        total += 1;
-    }
+    const long long steps = (long long)sh.n_ct * sh.NT;
+    long long per = n_sm / sh.n_ct;
+    if (per < 1) per = 1;
+    if (per > steps) per = steps;
     if (work && range) {
         work->clear();
         range->clear();
         for (int ct = 0; ct < sh.n_ct; ++ct) {
-            range->push_back(make_int2((int)work->size(), cnt[ct]));
-            for (int i = 0; i < cnt[ct]; ++i)
-                work->push_back(make_int4(ct, (int)(stages * i / cnt[ct]), (int)(stages * (i + 1) / cnt[ct]), 0));
+            range->push_back(make_int2((int)work->size(), (int)per));
+            for (long long i = 0; i < per; ++i)
+                work->push_back(make_int4(ct, (int)(steps * i / per), (int)(steps * (i + 1) / per), 0));
         }
     }
-    return (size_t)total;
+    return (size_t)(per * sh.n_ct);
 }
 
-size_t tc_table_halves(const TcShape& sh) { return 2 * (size_t)(2 * sh.NT - 1) * sh.n_kb * sh.C * kTcK; }
+size_t tc_table_halves(const TcShape& sh) { return 2 * (size_t)sh.NT * sh.n_kb * sh.C * kTcK; }
 
 cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* scratch, cudaStream_t s) {
     const TcShape& sh = P->sh;
@@ -619,7 +672,7 @@ cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* s
     double m = 0.0;
     for (int i = 0; i < nb; ++i) m = hm[i] > m ? hm[i] : m;
     P->exT = tc_exponent(m);
-    long long total = (long long)(2 * sh.NT - 1) * sh.n_kb * sh.C * kTcK;
+    long long total = (long long)sh.NT * sh.n_kb * sh.C * kTcK;
     long long blocks = (total + 255) / 256;
     if (blocks > 148LL * 64) blocks = 148LL * 64;
     k_tc_table<<<(unsigned)blocks, 256, 0, s>>>(tab, sh, wire_div, P->exT, P->t16);
@@ -654,25 +707,32 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
     const TcShape& sh = P->sh;
     const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     {
-        // [half][offset][k block][c][64]: box = one stage's 128 x 64 tile of both halves
+        // [half][offset >= 0][k block][c][64]: tmA's box is one stage's 128 x 64 tile
+        // (rows c, columns c') of both halves; tmAT's box is the 64 x 128 tile of
+        // the transposed block (rows c' of one k block, columns c of two k blocks)
         const cuuint64_t row = (cuuint64_t)kTcK * 2;
-        const cuuint64_t dims[5] = {(cuuint64_t)kTcK, (cuuint64_t)sh.C, (cuuint64_t)sh.n_kb,
-                                    (cuuint64_t)(2 * sh.NT - 1), 2};
-        const cuuint64_t strides[4] = {row, row * sh.C, row * sh.C * sh.n_kb, row * sh.C * sh.n_kb * (2 * sh.NT - 1)};
+        const cuuint64_t dims[5] = {(cuuint64_t)kTcK, (cuuint64_t)sh.C, (cuuint64_t)sh.n_kb, (cuuint64_t)sh.NT, 2};
+        const cuuint64_t strides[4] = {row, row * sh.C, row * sh.C * sh.n_kb, row * sh.C * sh.n_kb * sh.NT};
         const cuuint32_t box[5] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM, 1, 1, 2};
+        const cuuint32_t boxT[5] = {(cuuint32_t)kTcK, (cuuint32_t)kTcK, (cuuint32_t)(kTcM / kTcK), 1, 2};
         CUresult r = enc(&P->tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, P->t16, dims, strides, box, ones,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = enc(&P->tmAT, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, P->t16, dims, strides, boxT, ones,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             *why = "encoding the table tensor map failed";
             return cudaErrorInvalidValue;
         }
     }
     {
-        const cuuint64_t dims[4] = {8, (cuuint64_t)sh.NT, (cuuint64_t)(sh.Cp / 8), 2};
-        const cuuint64_t strides[3] = {16, (cuuint64_t)sh.NT * 16, (cuuint64_t)(sh.Cp / 8) * sh.NT * 16};
-        const cuuint32_t box[4] = {8, (cuuint32_t)sh.NR, (cuuint32_t)(kTcK / 8), 2};
-        CUresult r = enc(&P->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->p16, dims, strides, box, ones,
+        // [c'/8][2 NT rows (hi, lo of each turn row)][8]: box = the staged copy of a column tile
+        const cuuint64_t dims[3] = {8, 2 * (cuuint64_t)sh.NT, (cuuint64_t)(sh.Cp / 8)};
+        const cuuint64_t strides[2] = {16, 2 * (cuuint64_t)sh.NT * 16};
+        const cuuint32_t box[3] = {8, 2 * (cuuint32_t)sh.NR, (cuuint32_t)(kTcM / 8)};
+        CUresult r = enc(&P->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->p16, dims, strides, box, ones,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -690,7 +750,7 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
 cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q) {
     const TcShape& sh = P.sh;
     k_tc_split<<<sh.NT, 256, 0, s>>>(P.d, sh, P.p16, P.pexp);
-    k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.d, sh, P.work, P.pexp, P.part);
+    k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmAT, P.tmB, P.d, sh, P.work, P.pexp, P.part);
     if (write_q) {
         int rb = (sh.N + 255) / 256;
         if (rb > 148 * 8) rb = 148 * 8;

@@ -24,11 +24,12 @@ struct TcShape {
 };
 
 struct TcPlan {
-    CUtensorMap tmA;            // split table: [half][offset][c'/64][c][c' % 64] FP16, 128-byte swizzle
-    CUtensorMap tmB;            // split input: [half][c'/8][t][c' % 8] FP16, no swizzle
+    CUtensorMap tmA;            // split table: [half][offset >= 0][c'/64][c][c' % 64] FP16, 128-byte swizzle
+    CUtensorMap tmAT;           // the same table, transposed-tile boxes (offsets < 0)
+    CUtensorMap tmB;            // split input: [c'/8][t][hi, lo][c' % 8] FP16, no swizzle
     TcShape sh;
     const CoilDev* d = nullptr; // device descriptor of the coil
-    __half* t16 = nullptr;      // 2 (2 NT - 1) n_kb C 64
+    __half* t16 = nullptr;      // 2 NT n_kb C 64
     __half* p16 = nullptr;      // 2 Cp NT
     float* part = nullptr;      // n_cta x NT x 128 partial tiles
     int4* work = nullptr;       // n_cta (tile, first stage, end stage, 0)
@@ -39,7 +40,7 @@ struct TcPlan {
     bool fused = false;         // the coil's near kernel sums the partial tiles itself
 };
 
-constexpr int kTcMaxTurns = 224;   // staged p rows NT + 32 fit one TMA box (<= 256)
+constexpr int kTcMaxTurns = 112;   // the staged copy's 2 (NT + 16) rows fit one TMA box (<= 256)
 
 // Fill the shape for C channels, NT turns on n_sm SMs; false if unsupported.
 bool tc_shape(int C, int NT, int n_sm, TcShape* sh);
