@@ -294,8 +294,10 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         uint32_t pa = 0, pb = 0;
         uint32_t a_used = 0, a_par = 0, b_used = 0, b_par = 0;   // bit s: stage s loaded / its parity
         bool ok = true;
-        for (int sg = wk.y; sg < wk.z && ok; ++sg) {
-            const int D = sg % sh.NT, cb = col_tile(sg), nk = min(2, sh.n_kb - 2 * cb);
+        int D = wk.y % sh.NT, cb = col_tile(wk.y);
+        for (int sg = wk.y; sg < wk.z && ok; ++sg, D = (D + 1 == sh.NT ? 0 : D + 1)) {
+            if (sg != wk.y && D == 0) cb = (cb + 1 == sh.n_ct ? 0 : cb + 1);
+            const int nk = min(2, sh.n_kb - 2 * cb);
             if (sg == wk.y || D == 0) {                 // a new column tile: its staged copy of p
                 ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
                 if (!ok) break;
@@ -337,10 +339,14 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // stages on it
         const int me = warp - 1;
         int i = 0, grp = 0;
+        int sa = 0, ai = 0;                             // slot and accumulator of stage i
+        uint32_t pa = 0, pacc = 0;                      // their phases: (i / S) & 1, (i / n_acc) & 1
         bool ok = true;
         const uint32_t bbase = sB;                      // one staged copy (kTcBStages == 1)
-        for (int sg = wk.y; sg < wk.z && ok; ++sg) {
-            const int D = sg % sh.NT, cb = col_tile(sg), nk = min(2, sh.n_kb - 2 * cb);
+        int D = wk.y % sh.NT, cb = col_tile(wk.y);
+        for (int sg = wk.y; sg < wk.z && ok; ++sg, D = (D + 1 == sh.NT ? 0 : D + 1)) {
+            if (sg != wk.y && D == 0) cb = (cb + 1 == sh.n_ct ? 0 : cb + 1);
+            const int nk = min(2, sh.n_kb - 2 * cb);
             if (sg == wk.y || D == 0) {
                 if (sg != wk.y) mma_commit(b_empty);    // free once this issuer's MMAs on it finish
                 ok = mbar_wait(b_full, (uint32_t)grp & 1u, abort_flag);
@@ -350,14 +356,17 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             for (int sgn = 0; sgn < (D > 0 ? 2 : 1) && ok; ++sgn)
               for (int j = 0; j < nk && ok; ++j, ++i) {
+                const int sa_i = sa, ai_i = ai;
+                const uint32_t pa_i = pa, pacc_i = pacc;
+                if (++sa == S) { sa = 0; pa ^= 1u; }
+                if (++ai == n_acc) { ai = 0; pacc ^= 1u; }
                 if ((i & 1) != me) continue;
                 const int d = sgn ? -D : D;
-                const int sa = i % S, ai = i % n_acc;
                 // staged copy: [16 chunks of 8 channels][2 NR rows: hi, lo of each turn row][8];
                 // k block j of the column tile = chunks 8 j .. 8 j + 7
                 const uint32_t bj = bbase + (uint32_t)j * 256u * (uint32_t)sh.NR;
-                ok = mbar_wait_fast(a_full + 8u * sa, (uint32_t)(i / S) & 1u, abort_flag);
-                if (ok) ok = mbar_wait_fast(acc_empty + 8u * ai, ((uint32_t)(i / n_acc) & 1u) ^ 1u, abort_flag);
+                ok = mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag);
+                if (ok) ok = mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 const int t_first = d > 0 ? d : 0;
@@ -365,7 +374,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const int ts = t_first & ~7;
                 const int n = (t_end - ts + 7) & ~7;            // turns covered (2 n accumulator columns)
                 const bool amn = d < 0;
-                const uint32_t ah = sA + (uint32_t)sa * kTcAStage;
+                const uint32_t ah = sA + (uint32_t)sa_i * kTcAStage;
                 // K-major A: rows of 64 channels c', 8-row groups 1 KB apart, K step = 32 B.
                 // MN-major A: rows of 64 channels c (two 8 KB blocks along M), one row per
                 // c', 8-row groups 1 KB apart, K step = 16 rows = 2 KB.  B: K step = two
@@ -382,7 +391,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 for (int part0 = 0; part0 < n; part0 += 128) {
                     const int np = min(128, n - part0);
                     const uint32_t idesc = idesc_f16(2 * np, amn);
-                    const uint32_t dcol = tmem + (uint32_t)ai * acc_cols + 2u * (uint32_t)(ts + part0);
+                    const uint32_t dcol = tmem + (uint32_t)ai_i * acc_cols + 2u * (uint32_t)(ts + part0);
                     const uint32_t row0 = (uint32_t)(ts + part0 - d + kTcPad);
                     const uint64_t b0 = sdesc(bj + 32u * row0, 32u * (uint32_t)sh.NR, 128u, 0u);
 #pragma unroll
@@ -391,8 +400,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         mma_f16(dcol, a_lo + s * a_step, b0 + s * b_step, idesc, 1u);
                     }
                 }
-                mma_commit(a_empty + 8u * sa);
-                mma_commit(acc_full + 8u * ai);
+                mma_commit(a_empty + 8u * sa_i);
+                mma_commit(acc_full + 8u * ai_i);
               }
         }
         // every MMA issued (also after an abort) completes before the TMEM is freed
@@ -413,8 +422,10 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         int ai = 0;
         uint32_t pf = 0;
         bool ok = true;
-        for (int sg = wk.y; sg < wk.z && ok; ++sg) {
-            const int D = sg % sh.NT, nk = min(2, sh.n_kb - 2 * col_tile(sg));
+        int D = wk.y % sh.NT, cb = col_tile(wk.y);
+        for (int sg = wk.y; sg < wk.z && ok; ++sg, D = (D + 1 == sh.NT ? 0 : D + 1)) {
+            if (sg != wk.y && D == 0) cb = (cb + 1 == sh.n_ct ? 0 : cb + 1);
+            const int nk = min(2, sh.n_kb - 2 * cb);
             for (int st = 0; st < (D > 0 ? 2 : 1) * nk; ++st) {
                 const int d = st >= nk ? -D : D;
                 ok = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag));
