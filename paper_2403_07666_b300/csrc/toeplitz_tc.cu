@@ -644,12 +644,15 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
 }
 
 // The same number of CTAs for every channel tile (n_sm / n_ct, at least one,
-// at most one per step) and the same step ranges for all tiles: tile ct's
-// j-th CTA and tile cb's j-th CTA meet the 128 x 128 region (ct, cb) of every
-// stored offset block at the same step, one of them reading it transposed.
-// A tile's n_ct NT steps are split into contiguous near-equal ranges.
-// work[cta] = (tile, first step, end step, 0); range[tile] = (first CTA, CTAs).
-// Returns the number of CTAs.
+// at most one per step).  Tile ct's j-th CTA and tile cb's j-th CTA meet the
+// 128 x 128 region (ct, cb) of every stored offset block at about the same
+// time, one of them reading it transposed, so the region comes from DRAM
+// once.  A tile's n_ct NT steps are split into contiguous ranges of about
+// equal stage counts (a step has 2 stages per k block of its column tile, 1
+// for D = 0; the half-height last column tile has one k block); every tile has
+// the same total, so partner CTAs stay within a fraction of a range of each
+// other.  work[cta] = (tile, first step, end step, 0); range[tile] = (first
+// CTA, CTAs).  Returns the number of CTAs.
 size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::vector<int2>* range) {
     const long long steps = (long long)sh.n_ct * sh.NT;
     long long per = n_sm / sh.n_ct;
@@ -660,8 +663,22 @@ size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::ve
         range->clear();
         for (int ct = 0; ct < sh.n_ct; ++ct) {
             range->push_back(make_int2((int)work->size(), (int)per));
-            for (long long i = 0; i < per; ++i)
-                work->push_back(make_int4(ct, (int)(steps * i / per), (int)(steps * (i + 1) / per), 0));
+            std::vector<long long> cum(steps + 1, 0);
+            for (long long sg = 0; sg < steps; ++sg) {
+                const int D = (int)(sg % sh.NT), cb = (int)((sg / sh.NT - ct + sh.n_ct) % sh.n_ct);
+                const int nk = std::min(2, sh.n_kb - 2 * cb);
+                cum[sg + 1] = cum[sg] + nk * (D > 0 ? 2 : 1);
+            }
+            long long s0 = 0;
+            for (long long i = 0; i < per; ++i) {
+                long long s1 = s0;
+                const long long target = cum[steps] * (i + 1) / per;
+                const long long s_max = steps - (per - 1 - i);      // leave a step for every later CTA
+                while (s1 < s_max && (cum[s1 + 1] <= target || s1 == s0)) ++s1;
+                if (i == per - 1) s1 = steps;
+                work->push_back(make_int4(ct, (int)s0, (int)s1, 0));
+                s0 = s1;
+            }
         }
     }
     return (size_t)(per * sh.n_ct);
