@@ -123,6 +123,19 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
     return y;
 }
 
+// 1 / a in FP64 without the FP64 divide sequence: the FP32 reciprocal as the
+// seed, then two Newton-Raphson steps y <- y (2 - a y) (24 -> 48 -> full
+// precision bits).  Inputs outside the FP32 exponent range take the plain
+// expression.
+__device__ __forceinline__ double rcp_nr(double a) {
+    const double m = fabs(a);
+    if (!(m > 1.0e-30 && m < 1.0e30)) return 1.0 / a;
+    double y = (double)__frcp_rn((float)a);
+    y = y * (2.0 - a * y);
+    y = y * (2.0 - a * y);
+    return y;
+}
+
 // Transport current and applied field of the drive at time t.
 __device__ __forceinline__ double drive_current(const CoilDev& c, double t) {
     return fmin(c.ramp * t, c.Imax);

@@ -461,22 +461,6 @@ __device__ __forceinline__ double seg_sum(double v, int Bp) {
     return v;
 }
 
-// L L^T x = v for the segment's wire (L as chol_solve_warp: reciprocal
-// diagonal); lane kk holds v_kk on entry and x_kk on return.
-__device__ double seg_chol_solve(const double* L, double x, int B, int kk, int base) {
-    for (int k = 0; k < B; ++k) {
-        double xk = __shfl_sync(0xffffffffu, x, base + k) * L[k * B + k];
-        if (kk == k) x = xk;
-        else if (kk > k && kk < B) x -= L[kk * B + k] * xk;
-    }
-    for (int k = B - 1; k >= 0; --k) {
-        double xk = __shfl_sync(0xffffffffu, x, base + k) * L[k * B + k];
-        if (kk == k) x = xk;
-        else if (kk < k) x -= L[k * B + kk] * xk;
-    }
-    return x;
-}
-
 struct Seg {
     int B, Bp, kk, base, w, e;
     bool wv, ev;        // wire exists, element exists
@@ -494,15 +478,6 @@ __device__ __forceinline__ Seg seg_of(const CoilDev& c, int warp_global) {
     s.ev = s.wv && s.kk < s.B;
     s.e = s.w * s.B + s.kk;
     return s;
-}
-
-// The warp's wires' factors into shared memory (zero for wires past the end).
-__device__ __forceinline__ void seg_load_L(const CoilDev& c, int warp_global, double* Ls) {
-    const int B = c.B, G = 32 / seg_width(B), w0 = warp_global * G;
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < G * B * B; i += 32)
-        Ls[i] = (w0 + i / (B * B) < c.W) ? c.L[(size_t)w0 * B * B + i] : 0.0;
-    __syncwarp();
 }
 
 // Far-operator value at element e of the tensor-core Toeplitz apply: the sum
@@ -581,8 +556,8 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
 
 // Projected residual update and preconditioner of the segment's wire: v is
 // the raw residual on entry; writes res, z and returns z (partial r^T z in rz).
-__device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const Seg& s, const double* L, double v,
-                                                        double y, bool first, double* rz) {
+__device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const Seg& s, double v, double y,
+                                                        bool first, double* rz) {
     const int con = s.wv ? c.constrained[s.w] : 0;
     const double isg = s.wv ? c.isigma[s.w] : 0.0;
     // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
@@ -593,10 +568,17 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
         else if (con) c.uw[s.w] += u;
     }
     if (s.ev) c.res[s.e] = v;
-    // z = A_w^-1 r, then remove the component that changes the wire's total current
-    double z = seg_chol_solve(L, s.kk < s.B ? v : 0.0, s.B, s.kk, s.base);
-    const double f = seg_sum(s.ev ? z : 0.0, s.Bp) * isg;
-    if (con && s.ev) z -= y * f;
+    // z = P_w r (P_w = A_w^-1 minus, on constrained wires, the component that
+    // changes the wire's total current; stored by k_factor_seg): B independent
+    // products per lane, two partial sums
+    const double* P = c.L + ((size_t)(s.wv ? s.w : 0) * s.B + (s.kk < s.B ? s.kk : 0)) * s.B;
+    double z0 = 0.0, z1 = 0.0;
+    for (int j = 0; j + 1 < s.B; j += 2) {
+        z0 += P[j] * __shfl_sync(0xffffffffu, v, s.base + j);
+        z1 += P[j + 1] * __shfl_sync(0xffffffffu, v, s.base + j + 1);
+    }
+    if (s.B & 1) z0 += P[s.B - 1] * __shfl_sync(0xffffffffu, v, s.base + s.B - 1);
+    const double z = s.ev ? z0 + z1 : 0.0;
     *rz = seg_sum(s.ev ? v * z : 0.0, s.Bp);
     return z;
 }
@@ -605,16 +587,14 @@ __global__ void __launch_bounds__(32 * kSegWarps)
 k_init_seg(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->done || c.B > kSegMax) return;
-    __shared__ double Ls[kSegWarps][kSegMax * kSegMax * 2];
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
     if (wg * (32 / seg_width(c.B)) >= c.W) return;
     const Seg s = seg_of(c, wg);
-    seg_load_L(c, wg, Ls[warp]);
     const double v = s.ev ? c.qv[s.e] + c.R[s.e] : 0.0;
     const double y = s.ev ? c.y1[s.e] : 0.0;
     double rz;
-    const double z = seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, true, &rz);
+    const double z = seg_residual_precond(c, s, v, y, true, &rz);
     if (s.ev) {
         c.zv[s.e] = z;
         c.dv[s.e] = -z;
@@ -631,13 +611,11 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
     const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
     if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
-    __shared__ double Ls[kSegWarps][kSegMax * kSegMax * 2];
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
     double head = 0.0;                                  // r^T z of the lane's wire on segment heads
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
-        seg_load_L(c, wg, Ls[warp]);
         const double alpha = c.sc->alpha;
         double v = 0.0, y = 0.0;
         if (s.ev) {
@@ -646,8 +624,7 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
             y = c.y1[s.e];
         }
         double rz;
-        const double z =
-            seg_residual_precond(c, s, Ls[warp] + ((threadIdx.x & 31) / s.Bp) * s.B * s.B, v, y, false, &rz);
+        const double z = seg_residual_precond(c, s, v, y, false, &rz);
         if (s.ev) c.zv[s.e] = z;
         if (s.kk == 0 && s.wv) {
             if (fuse_beta) head = rz;
@@ -723,72 +700,96 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
     }
 }
 
-// k_factor for blocks of at most 16 elements: the same Cholesky (lane kk owns
-// row kk of its wire's block in shared memory), y = A^-1 1, sigma, the
-// right-hand-side norm and the projected warm start.
+// k_factor for blocks of at most 16 elements.  Lane kk holds row kk of
+// A_w = M_ww + dt G_w in registers and the segment inverts it in place by
+// Gauss-Jordan elimination without pivoting (A_w is SPD, so every pivot is a
+// positive Schur complement; a non-positive one flags the step as the
+// Cholesky does), broadcasting each scaled pivot row by shuffles.  From A_w^-1:
+// y = A_w^-1 1, sigma = 1^T y, and the projected preconditioner
+// P_w = A_w^-1 - y y^T / sigma (constrained wires; A_w^-1 otherwise), which
+// is stored (in the factor array) so that every PCG application is one
+// B x B product.  Also the right-hand-side norm R^T P_w R + c_w^2 / sigma and
+// the projected warm start.
 __global__ void __launch_bounds__(32 * kSegWarps)
 k_factor_seg(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.B > kSegMax) return;
-    __shared__ double As[kSegWarps][kSegMax * kSegMax * 2];
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
     if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
     const Seg s = seg_of(c, wg);
     const int B = s.B, kk = s.kk, w = s.w, e = s.e;
-    double* A = As[warp] + ((threadIdx.x & 31) / s.Bp) * B * B;
-    if (s.wv) {
-        const double* nb = c.near + (size_t)c.block_type[w] * B * B;
-        for (int i = kk; i < B * B; i += s.Bp) A[i] = nb[i];
-    } else {
-        for (int i = kk; i < B * B; i += s.Bp) A[i] = (i % (B + 1) == 0) ? 1.0 : 0.0;   // identity
+    double a[kSegMax];
+    const double* nb = c.near + (size_t)c.block_type[s.wv ? w : 0] * B * B;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j)
+        a[j] = (s.wv && kk < B && j < B) ? nb[kk * B + j] : (j == kk ? 1.0 : 0.0);
+    if (s.ev) {
+        const double g = c.dt * c.G[e];
+#pragma unroll
+        for (int j = 0; j < kSegMax; ++j)
+            if (j == kk) a[j] += g;
     }
-    __syncwarp();
-    if (s.ev) A[kk * B + kk] += c.dt * c.G[e];
-    __syncwarp();
     int bad = 0;
-    for (int k = 0; k < B; ++k) {
-        double piv = A[k * B + k];
-        if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
-        double rkk = rsqrt_nr(piv);                    // the factor keeps 1 / L_kk on its diagonal
-        __syncwarp();
-        if (kk == k) A[k * B + k] = rkk;
-        if (kk > k && kk < B) A[kk * B + k] *= rkk;
-        __syncwarp();
-        if (kk > k && kk < B) {
-            double lik = A[kk * B + k];
-            for (int j = k + 1; j <= kk; ++j) A[kk * B + j] -= lik * A[j * B + k];
+#pragma unroll
+    for (int k = 0; k < kSegMax; ++k) {
+        if (k < B) {
+            double piv = __shfl_sync(0xffffffffu, a[k], s.base + k);
+            if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
+            const double ip = rcp_nr(piv);
+            if (kk == k) {
+#pragma unroll
+                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
+            }
+            double rk[kSegMax];                         // scaled pivot row
+#pragma unroll
+            for (int j = 0; j < kSegMax; ++j) rk[j] = __shfl_sync(0xffffffffu, a[j], s.base + k);
+            if (kk != k) {
+                const double f = a[k];
+#pragma unroll
+                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * rk[j];
+            }
         }
-        __syncwarp();
     }
     if (bad && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
-    if (s.wv)
-        for (int i = kk; i < B * B; i += s.Bp) c.L[(size_t)w * B * B + i] = A[i];
-    // y = A_w^-1 1, sigma = 1^T y
-    const double y = seg_chol_solve(A, kk < B ? 1.0 : 0.0, B, kk, s.base);
-    const double sig = seg_sum(s.ev ? y : 0.0, s.Bp);
+    // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
+    double y = 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j)
+        if (j < B) y += a[j];
+    y = s.ev ? y : 0.0;
+    const double sig = seg_sum(y, s.Bp);
+    const int con = s.wv ? c.constrained[w] : 0;
+    const double isg = 1.0 / sig;
     if (s.ev) c.y1[e] = y;
     if (kk == 0 && s.wv) {
         c.sigma[w] = sig;
-        c.isigma[w] = 1.0 / sig;
+        c.isigma[w] = isg;
     }
-    // preconditioned norm^2 of the right-hand side: R^T Pproj(R) + c_w^2 / sigma
+    // P_w row kk, stored; R^T P_w R
     const double R = s.ev ? c.R[e] : 0.0;
-    double v = seg_chol_solve(A, R, B, kk, s.base);
+    double pr = 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j) {
+        if (j < B) {
+            const double yj = __shfl_sync(0xffffffffu, y, s.base + j);
+            const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
+            const double pj = con ? a[j] - y * yj * isg : a[j];
+            if (s.ev) c.L[((size_t)w * B + kk) * B + j] = pj;
+            pr += pj * Rj;
+        }
+    }
+    const double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
     const double cw = s.wv ? c.cw[w] : 0.0;
-    const int con = s.wv ? c.constrained[w] : 0;
-    const double sv = seg_sum(s.ev ? v : 0.0, s.Bp);
-    if (con && s.ev) v -= y * (sv / sig);
-    const double rn = seg_sum(s.ev ? R * v : 0.0, s.Bp);
     // warm start from the previous step's Idot, moved onto this step's constraint
     const double sx = seg_sum(s.ev ? c.x[e] : 0.0, s.Bp);
-    const double corr = con ? (cw - sx) / sig : 0.0;
+    const double corr = con ? (cw - sx) * isg : 0.0;
     if (s.ev) {
         double xe = c.x[e] + corr * y;
         c.x[e] = xe;
         c.pf[e] = (float)xe;
     }
-    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw / sig : 0.0);
+    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
