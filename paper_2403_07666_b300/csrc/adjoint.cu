@@ -17,6 +17,7 @@
 //   the operator transpose (M symmetric: one more apply).
 #include "common.cuh"
 #include "pointwise.cuh"
+#include "tridiag.cuh"
 
 namespace cq {
 
@@ -35,12 +36,6 @@ struct AdjBufs {
     double* gparts;     // 2 x W per-block partial sums of dL/dn and dL/dC_eps
 };
 
-__device__ void adj_thomas(double* v, int G, const double* lo, const double* inv, const double* cp) {
-    v[0] = v[0] * inv[0];
-    for (int i = 1; i < G; ++i) v[i] = (v[i] - lo[i] * v[i - 1]) * inv[i];
-    for (int i = G - 2; i >= 0; --i) v[i] -= cp[i] * v[i + 1];
-}
-
 // a = (I - dt/2 A_z)^-1 lam_u'   (z-lines; the matrix is symmetric)
 __global__ void k_adj_adi_z(const CoilDev* __restrict__ cds, AdjBufs ab) {
     const CoilDev& c = cds[0];
@@ -50,8 +45,7 @@ __global__ void k_adj_adi_z(const CoilDev* __restrict__ cds, AdjBufs ab) {
     int Gr = c.Gr, Gz = c.Gz, lane = threadIdx.x;
     for (int j = lane; j < Gz; j += 32) sm[j] = ab.lamU_next[j * Gr + i];
     __syncwarp();
-    if (lane == 0) adj_thomas(sm, Gz, c.thz_lo, c.thz_inv, c.thz_cp);
-    __syncwarp();
+    warp_tridiag(sm, Gz, c.thz_lo, c.thz_inv, c.thz_cp);
     for (int j = lane; j < Gz; j += 32) ab.a[j * Gr + i] = sm[j];
 }
 
@@ -72,8 +66,7 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
         sm[i] = ai + hd * (ar * invC);
     }
     __syncwarp();
-    if (lane == 0) adj_thomas(sm, Gr, c.thr_lo, c.thr_inv, c.thr_cp);
-    __syncwarp();
+    warp_tridiag(sm, Gr, c.thr_lo, c.thr_inv, c.thr_cp);
     for (int i = lane; i < Gr; i += 32) ab.b[j * Gr + i] = sm[i];
 }
 
