@@ -376,8 +376,19 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([s64], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             s64 = float(t.item())
+        # the mixed form over the same steps from the same start: moment and current error
+        n64 = 1 + args.fp64_steps
+        cm = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                                stream=stream.cuda_stream, format=args.format)
+        cm.step(n64, drive)
+        m64, mm = c64.diag(0, n64)[:, 3], cm.diag(0, n64)[:, 3]
+        I64, Im = c64.currents(), cm.currents()
+        cm.close()
         fp64 = {"value": world * N * args.fp64_steps / s64, "ms_per_step": 1e3 * s64 / args.fp64_steps,
-                "steps": args.fp64_steps}
+                "steps": args.fp64_steps,
+                "mixed_moment_rel_err": float(np.max(np.abs(mm - m64)) / max(np.max(np.abs(m64)), 1e-300)),
+                "mixed_current_rel_err": float(np.linalg.norm(Im - I64) / max(np.linalg.norm(I64), 1e-300)),
+                "compared_steps": n64}
         c64.close()
     else:
         coil.close()

@@ -27,6 +27,24 @@ Pins (tests/test_oracle_step.py): constraint and KKT residual of the direct
 solve, closed-form two-loop recurrence, a 4-loop KKT solved by plain
 numpy.linalg.solve, Bean's critical-state moment -Jc a / 3, and the energy
 balance of the stepped circuit.
+
+Per-wire statistics (Flux Jumps Propagation and Quenches Propagation
+sections: the maximum temperature and the maximum Joule power density of
+each wire, the Joule heat Q_FJ of a wire from the occurrence of a flux jump to
+its peak, and the Joule heat Q_q from the onset of the rapid increase of rho
+to the quench), all from the start-of-step state of every step:
+
+    Q_total[w]  += dt * P_w,  P_w = sum_{e in w} q_e 2 pi r_e a_e   (rectangle rule)
+    T_max[w]     = max over steps and elements of T_e
+    P_max[w]     = max over steps and elements of q_e
+    Q_at_jump[w], Q_at_rise[w], Q_at_quench[w] = Q_total before the step on which
+        the wire first meets |J/Jc| > 1, mean rho/rho_n > 0.05 (the onset of the
+        rapid rise of rho; the threshold is this build's reading), mean
+        rho/rho_n > 0.95 (-1 until then)
+
+so Q_FJ = Q_total(t_peak) - Q_at_jump and Q_q = Q_at_quench - Q_at_rise.
+Pins: Q_total of an ohmic loop is I^2 R t; the per-wire Q_total sum to the
+time integral of the diagnostic Joule power.
 """
 
 import numpy as np
@@ -116,6 +134,13 @@ class OracleCoil:
         self.thermal = ThermalGrid(geo, self.p) if (geo["grid"] and self.p["thermal"]) else None
         self.first_jump = np.full(W, -1, dtype=np.int64)
         self.first_quench = np.full(W, -1, dtype=np.int64)
+        self.first_rise = np.full(W, -1, dtype=np.int64)
+        self.Q_total = np.zeros(W)
+        self.T_max_w = np.zeros(W)
+        self.P_max_w = np.zeros(W)
+        self.Q_at_jump = np.full(W, -1.0)
+        self.Q_at_rise = np.full(W, -1.0)
+        self.Q_at_quench = np.full(W, -1.0)
         self.last = None
 
     # -- the state's fields ----------------------------------------------------
@@ -166,8 +191,20 @@ class OracleCoil:
         nfil = fil.sum(axis=1)
         mean_rho = np.where(nfil > 0, rho_frac.sum(axis=1) / np.maximum(nfil, 1), 0.0)
         wire_jr = jr.max(axis=1)
-        self.first_jump = np.where((self.first_jump < 0) & (wire_jr > 1.0), self.steps, self.first_jump)
-        self.first_quench = np.where((self.first_quench < 0) & (mean_rho > 0.95), self.steps, self.first_quench)
+        new_jump = (self.first_jump < 0) & (wire_jr > 1.0)
+        new_rise = (self.first_rise < 0) & (mean_rho > 0.05)
+        new_quench = (self.first_quench < 0) & (mean_rho > 0.95)
+        self.first_jump = np.where(new_jump, self.steps, self.first_jump)
+        self.first_rise = np.where(new_rise, self.steps, self.first_rise)
+        self.first_quench = np.where(new_quench, self.steps, self.first_quench)
+        # per-wire statistics: onsets take the heat accumulated before this step
+        self.Q_at_jump = np.where(new_jump, self.Q_total, self.Q_at_jump)
+        self.Q_at_rise = np.where(new_rise, self.Q_total, self.Q_at_rise)
+        self.Q_at_quench = np.where(new_quench, self.Q_total, self.Q_at_quench)
+        P_w = (pw["q"] * 2.0 * np.pi * r * area).reshape(W, B).sum(axis=1)
+        self.Q_total = self.Q_total + dt * P_w
+        self.T_max_w = np.maximum(self.T_max_w, pw["T"].reshape(W, B).max(axis=1))
+        self.P_max_w = np.maximum(self.P_max_w, pw["q"].reshape(W, B).max(axis=1))
         # advance
         self.I = self.I + dt * Idot
         if self.thermal is not None:
@@ -183,6 +220,11 @@ class OracleCoil:
                float(wire_jr.max()), float(mean_rho.max()))
         self.diag.append(rec)
         return rec
+
+    def wire_stats(self):
+        """Rows Q_total, T_max, P_max, Q_at_jump, Q_at_rise, Q_at_quench, first_rise."""
+        return np.stack([self.Q_total, self.T_max_w, self.P_max_w, self.Q_at_jump, self.Q_at_rise,
+                         self.Q_at_quench, self.first_rise.astype(np.float64)])
 
     def read(self, drive=None):
         """J, B_r, B_z, T and moment of the current state."""
