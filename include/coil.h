@@ -241,6 +241,25 @@ coil_status coil_read_diag(coil_t *c, long first, long count, double *out);
  * never.  Host arrays of n_blocks longs. */
 coil_status coil_read_onsets(coil_t *c, long *first_jump, long *first_quench);
 
+/* Per-wire statistics of the forward steps taken so far (Flux Jumps
+ * Propagation and Quenches Propagation sections), into the host array
+ * out[7][n_blocks] (row-major, a row per quantity):
+ *   0  Q_total: Joule heat per unit of time integrated by the rectangle rule,
+ *      sum over steps of dt * P_w, P_w = sum_e q_e 2 pi r_e a_e [J]
+ *   1  T_max: maximum element temperature over the start-of-step states [K]
+ *   2  P_max: maximum Joule power density q = rho J^2 over them [W/m^3]
+ *   3  Q_at_jump, 4 Q_at_rise, 5 Q_at_quench: Q_total before the step whose
+ *      start state first met max |J|/Jc > 1, mean rho/rho_n > 0.05 and mean
+ *      rho/rho_n > 0.95 respectively; -1 while not met
+ *   6  first_rise: index of that step for the resistivity rise, -1 if never.
+ * The adjoint's recomputations do not count; coil_save_state/coil_load_state
+ * carry these statistics. */
+coil_status coil_read_wire_stats(coil_t *c, double *out);
+
+/* Start a new observation window: the statistics above back to 0 / -1 and the
+ * onsets of coil_read_onsets back to -1. */
+coil_status coil_reset_wire_stats(coil_t *c);
+
 /* Element currents I [A] (host, N doubles) and set them (state injection for
  * tests; also resets the accumulated flux to M I). */
 coil_status coil_get_currents(coil_t *c, double *I);
@@ -276,7 +295,8 @@ coil_status coil_apply_operator_static(coil_t *c, const double *d_p, double *d_y
  * (far part converted from its storage precision, near blocks added). */
 coil_status coil_read_operator(coil_t *c, double *M);
 
-/* Serialise / restore the FP64 state (I, flux, T^4, t, step, warm start).
+/* Serialise / restore the FP64 state (I, flux, T^4, t, step, warm start,
+ * onsets and per-wire statistics).
  * With buf == NULL, *bytes receives the required size. */
 coil_status coil_save_state(coil_t *c, void *buf, size_t *bytes);
 coil_status coil_load_state(coil_t *c, const void *buf, size_t bytes);

@@ -76,6 +76,8 @@ def load_library(path=LIB_PATH):
         "coil_read_device": ([P, C.POINTER(Drive), P, P, P, P], C.c_int),
         "coil_read_diag": ([P, C.c_long, C.c_long, _dp], C.c_int),
         "coil_read_onsets": ([P, C.POINTER(C.c_long), C.POINTER(C.c_long)], C.c_int),
+        "coil_read_wire_stats": ([P, C.POINTER(C.c_double)], C.c_int),
+        "coil_reset_wire_stats": ([P], C.c_int),
         "coil_get_currents": ([P, _dp], C.c_int),
         "coil_set_currents": ([P, _dp], C.c_int),
         "coil_apply_operator": ([P, _dp, _dp], C.c_int),
@@ -239,6 +241,16 @@ class Coil:
         b = np.empty(self.W, dtype=np.int64)
         self._check(self._lib.coil_read_onsets(self._h, _ptr(a, C.c_long), _ptr(b, C.c_long)))
         return a, b
+
+    def wire_stats(self):
+        """Rows Q_total, T_max, P_max, Q_at_jump, Q_at_rise, Q_at_quench,
+        first_rise (as float) of each wire: an array of shape (7, W)."""
+        out = np.empty((7, self.W))
+        self._check(self._lib.coil_read_wire_stats(self._h, _ptr(out)))
+        return out
+
+    def reset_wire_stats(self):
+        self._check(self._lib.coil_reset_wire_stats(self._h))
 
     def currents(self):
         I = np.empty(self.N)

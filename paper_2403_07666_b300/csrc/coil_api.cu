@@ -94,6 +94,9 @@ coil_status fail(coil_t* c, coil_status st, const std::string& msg) {
     return st;
 }
 
+coil_status reset_wire_stats(coil_t* c, bool onsets);
+coil_status sync_descriptor(coil_t* c);
+
 coil_status cuda_fail(coil_t* c, cudaError_t e, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     if (e == cudaErrorMemoryAllocation) return fail(c, COIL_ERR_OOM, m);
@@ -424,6 +427,10 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.first_quench, W, "first_quench"));
     CK(cudaMemsetAsync(h.first_jump, 0xff, W * sizeof(long long), c->stream), "memset");
     CK(cudaMemsetAsync(h.first_quench, 0xff, W * sizeof(long long), c->stream), "memset");
+    TRY(dalloc(c, &h.wstat, 6 * (size_t)W, "wire statistics"));
+    TRY(dalloc(c, &h.first_rise, W, "first_rise"));
+    TRY(reset_wire_stats(c, false));
+    h.acc_on = 1;
     TRY(dalloc(c, &h.diag, (size_t)h.diag_cap * COIL_DIAG_WIDTH, "diag"));
     TRY(dalloc(c, &h.sc, 1, "scalars"));
     TRY(dalloc(c, &h.ticket, 2, "arrival counters"));
@@ -543,6 +550,24 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         }
     }
     CK(cudaStreamSynchronize(c->stream), "create");
+    return COIL_OK;
+}
+
+// Per-wire statistics back to their empty values (heat and maxima 0, onset
+// heat -1, first_rise -1); with onsets also first_jump and first_quench.
+coil_status reset_wire_stats(coil_t* c, bool onsets) {
+    const CoilDev& h = c->h;
+    const size_t W = h.W;
+    std::vector<double> init(6 * W, 0.0);
+    std::fill(init.begin() + 3 * W, init.end(), -1.0);
+    CK(cudaMemcpyAsync(h.wstat, init.data(), init.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "wire statistics");
+    CK(cudaMemsetAsync(h.first_rise, 0xff, W * sizeof(long long), c->stream), "memset");
+    if (onsets) {
+        CK(cudaMemsetAsync(h.first_jump, 0xff, W * sizeof(long long), c->stream), "memset");
+        CK(cudaMemsetAsync(h.first_quench, 0xff, W * sizeof(long long), c->stream), "memset");
+    }
+    CK(cudaStreamSynchronize(c->stream), "wire statistics");
     return COIL_OK;
 }
 
@@ -1055,6 +1080,24 @@ coil_status coil_read_onsets(coil_t* c, long* first_jump, long* first_quench) {
     return COIL_OK;
 }
 
+coil_status coil_read_wire_stats(coil_t* c, double* out) {
+    if (!c || !out) return c ? fail(c, COIL_ERR_INVALID, "null buffer") : COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    const size_t W = c->h.W;
+    std::vector<long long> fr(W);
+    CK(cudaMemcpyAsync(out, c->h.wstat, 6 * W * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "wire statistics");
+    CK(cudaMemcpyAsync(fr.data(), c->h.first_rise, W * 8, cudaMemcpyDeviceToHost, c->stream), "wire statistics");
+    CK(cudaStreamSynchronize(c->stream), "wire statistics");
+    for (size_t w = 0; w < W; ++w) out[6 * W + w] = (double)fr[w];
+    return COIL_OK;
+}
+
+coil_status coil_reset_wire_stats(coil_t* c) {
+    if (!c) return COIL_ERR_INVALID;
+    cudaSetDevice(c->device);
+    return reset_wire_stats(c, true);
+}
+
 coil_status coil_get_currents(coil_t* c, double* I) {
     if (!c || !I) return c ? fail(c, COIL_ERR_INVALID, "null buffer") : COIL_ERR_INVALID;
     cudaSetDevice(c->device);
@@ -1159,6 +1202,9 @@ coil_status coil_read_operator(coil_t* c, double* M) {
     return COIL_OK;
 }
 
+// "COILST02": state of I, Phi, x, u_T, onsets and per-wire statistics
+constexpr unsigned long long kStateMagic = 0x434f494c53543032ULL;
+
 struct StateHeader {
     unsigned long long magic;
     long long N, W, G, steps;
@@ -1169,11 +1215,11 @@ coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
     if (!c || !bytes) return c ? fail(c, COIL_ERR_INVALID, "null size pointer") : COIL_ERR_INVALID;
     const CoilDev& h = c->h;
     size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
-    size_t need = sizeof(StateHeader) + (3 * N + G) * sizeof(double) + 2 * W * sizeof(long long);
+    size_t need = sizeof(StateHeader) + (3 * N + G + 6 * W) * sizeof(double) + 3 * W * sizeof(long long);
     if (!buf) { *bytes = need; return COIL_OK; }
     if (*bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
     cudaSetDevice(c->device);
-    StateHeader hd{0x434f494c53543031ULL, (long long)N, (long long)W, (long long)G, c->steps, c->t};
+    StateHeader hd{kStateMagic, (long long)N, (long long)W, (long long)G, c->steps, c->t};
     unsigned char* p = (unsigned char*)buf;
     memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
@@ -1182,7 +1228,9 @@ coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
     CK(cudaMemcpy(p, h.x, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
     if (G) { CK(cudaMemcpy(p, h.uT, G * 8, cudaMemcpyDeviceToHost), "save"); p += G * 8; }
     CK(cudaMemcpy(p, h.first_jump, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
-    CK(cudaMemcpy(p, h.first_quench, W * 8, cudaMemcpyDeviceToHost), "save");
+    CK(cudaMemcpy(p, h.first_quench, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
+    CK(cudaMemcpy(p, h.first_rise, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
+    CK(cudaMemcpy(p, h.wstat, 6 * W * 8, cudaMemcpyDeviceToHost), "save");
     *bytes = need;
     return COIL_OK;
 }
@@ -1191,11 +1239,11 @@ coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
     if (!c || !buf) return c ? fail(c, COIL_ERR_INVALID, "null state buffer") : COIL_ERR_INVALID;
     const CoilDev& h = c->h;
     size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
-    size_t need = sizeof(StateHeader) + (3 * N + G) * sizeof(double) + 2 * W * sizeof(long long);
+    size_t need = sizeof(StateHeader) + (3 * N + G + 6 * W) * sizeof(double) + 3 * W * sizeof(long long);
     StateHeader hd;
     if (bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
     memcpy(&hd, buf, sizeof(hd));
-    if (hd.magic != 0x434f494c53543031ULL || hd.N != (long long)N || hd.W != (long long)W || hd.G != (long long)G)
+    if (hd.magic != kStateMagic || hd.N != (long long)N || hd.W != (long long)W || hd.G != (long long)G)
         return fail(c, COIL_ERR_INVALID, "state does not belong to a coil of this shape");
     cudaSetDevice(c->device);
     const unsigned char* p = (const unsigned char*)buf + sizeof(hd);
@@ -1204,7 +1252,9 @@ coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
     CK(cudaMemcpy(h.x, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
     if (G) { CK(cudaMemcpy(h.uT, p, G * 8, cudaMemcpyHostToDevice), "load"); p += G * 8; }
     CK(cudaMemcpy(h.first_jump, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
-    CK(cudaMemcpy(h.first_quench, p, W * 8, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(h.first_quench, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
+    CK(cudaMemcpy(h.first_rise, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
+    CK(cudaMemcpy(h.wstat, p, 6 * W * 8, cudaMemcpyHostToDevice), "load");
     Scalars sc;
     CK(cudaMemcpy(&sc, h.sc, sizeof(sc), cudaMemcpyDeviceToHost), "load");
     sc.t = hd.t;
@@ -1471,7 +1521,14 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     const long long st_fin = c->steps;
     const int last_iters_fin = c->last_iters;
 
-    // reverse sweep
+    // reverse sweep: its pointwise launches recompute steps already counted,
+    // so the per-wire statistics stay as the forward pass left them
+    struct AccGuard {
+        coil_t* c;
+        ~AccGuard() { c->h.acc_on = 1; sync_descriptor(c); }
+    } acc_guard{c};
+    h.acc_on = 0;
+    TRY(sync_descriptor(c));
     double* lamI_next = lamA;
     double* lamI = lamB;
     double* lamU_next = lamUA;

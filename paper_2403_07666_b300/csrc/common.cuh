@@ -91,6 +91,12 @@ struct CoilDev {
     double *parts;                // 8 x W per-block partials (see step.cu)
     double *partT;                // per grid column partial of T_max
     long long *first_jump, *first_quench;
+    // per-wire statistics (rows of W): Q_total, T_max, P_max, Q_at_jump,
+    // Q_at_rise, Q_at_quench; first_rise; updated by the pointwise kernels of
+    // forward steps while acc_on (the adjoint's recomputations turn it off)
+    double *wstat;
+    long long *first_rise;
+    int acc_on;
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;

@@ -18,6 +18,27 @@
 
 namespace cq {
 
+// Detectors and per-wire statistics of wire w from its start-of-step state
+// (Flux Jumps Propagation and Quenches Propagation sections): onsets of the
+// flux-jump criterion max |J|/Jc > 1, of the rise of the resistivity (mean
+// rho/rho_n > 0.05) and of the quench criterion (mean rho/rho_n > 0.95); the
+// heat accumulated before the onset step is kept with each onset; then the
+// running heat Q_total += dt P_w and the running maxima of T and q.  Forward
+// steps only (acc_on); onsets are only ever set once.
+__device__ __forceinline__ void wire_detectors(const CoilDev& c, int w, long long st, double dt, double pj,
+                                               double jr, double mean_rho, double tmx, double qmx) {
+    if (!c.acc_on) return;
+    const size_t W = c.W;
+    double* ws = c.wstat;
+    const double Q = ws[w];
+    if (c.first_jump[w] < 0 && jr > 1.0) { c.first_jump[w] = st; ws[3 * W + w] = Q; }
+    if (c.first_rise[w] < 0 && mean_rho > 0.05) { c.first_rise[w] = st; ws[4 * W + w] = Q; }
+    if (c.first_quench[w] < 0 && mean_rho > 0.95) { c.first_quench[w] = st; ws[5 * W + w] = Q; }
+    ws[w] = Q + dt * pj;
+    ws[W + w] = fmax(ws[W + w], tmx);
+    ws[2 * W + w] = fmax(ws[2 * W + w], qmx);
+}
+
 // One warp per block (wire).  Partials: P[0] Joule power, P[1] max |J|/Jc,
 // P[2] mean rho/rho_n of filament elements.
 __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
@@ -35,7 +56,7 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
         sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
         sc->nonpd = 0;                         // k_factor of this step sets it again if needed
     }
-    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0;
+    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
     for (int k = lane; k < c.B; k += 32) {
         int e = w * c.B + k;
         double r = c.r[e], a = c.area[e];
@@ -59,6 +80,8 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
         if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
         sumI += I;
         pj += q * 2.0 * kPi * r * a;
+        tmx = fmax(tmx, T);
+        qmx = fmax(qmx, q);
         if (fil) { jr = fmax(jr, jrat); rhof += frac; nfil += 1.0; }
     }
     sumI = warp_sum(sumI);
@@ -66,15 +89,15 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
     jr = warp_max(jr);
     rhof = warp_sum(rhof);
     nfil = warp_sum(nfil);
+    tmx = warp_max(tmx);
+    qmx = warp_max(qmx);
     if (lane == 0) {
         c.cw[w] = c.constrained[w] ? (It1 - sumI) / dt : 0.0;
         double mean_rho = nfil > 0.0 ? rhof / nfil : 0.0;
         parts[0 * (size_t)c.W + w] = pj;
         parts[1 * (size_t)c.W + w] = jr;
         parts[2 * (size_t)c.W + w] = mean_rho;
-        long long st = sc->step;
-        if (c.first_jump[w] < 0 && jr > 1.0) c.first_jump[w] = st;
-        if (c.first_quench[w] < 0 && mean_rho > 0.95) c.first_quench[w] = st;
+        wire_detectors(c, w, sc->step, dt, pj, jr, mean_rho, tmx, qmx);
     }
 }
 
@@ -656,7 +679,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
         sc->nonpd = 0;                         // k_factor of this step sets it again if needed
     }
-    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0;
+    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
     if (s.ev) {
         const int e = s.e;
         double r = c.r[e], a = c.area[e];
@@ -680,6 +703,8 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
         sumI = I;
         pj = q * 2.0 * kPi * r * a;
+        tmx = T;
+        qmx = q;
         if (fil) { jr = jrat; rhof = frac; nfil = 1.0; }
     }
     sumI = seg_sum(sumI, s.Bp);
@@ -687,6 +712,8 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
     jr = seg_max(jr, s.Bp);
     rhof = seg_sum(rhof, s.Bp);
     nfil = seg_sum(nfil, s.Bp);
+    tmx = seg_max(tmx, s.Bp);
+    qmx = seg_max(qmx, s.Bp);
     if (s.kk == 0 && s.wv) {
         const int w = s.w;
         double* parts = c.parts;
@@ -695,9 +722,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         parts[0 * (size_t)c.W + w] = pj;
         parts[1 * (size_t)c.W + w] = jr;
         parts[2 * (size_t)c.W + w] = mean_rho;
-        long long st = sc->step;
-        if (c.first_jump[w] < 0 && jr > 1.0) c.first_jump[w] = st;
-        if (c.first_quench[w] < 0 && mean_rho > 0.95) c.first_quench[w] = st;
+        wire_detectors(c, w, sc->step, dt, pj, jr, mean_rho, tmx, qmx);
     }
 }
 
