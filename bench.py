@@ -425,6 +425,9 @@ def run_ours(args, rank, world, local_rank):
     if args.other_format and args.precision == "fp32":
         line["other_formats"] = {f: format_leg(args, local_rank, stream, torch, f)
                                  for f in ("toeplitz_tc", "toeplitz", "dense") if f != args.format}
+    if args.lorentz:
+        line["lorentz_strain"] = lorentz_leg(args, local_rank, stream, torch)
+        line["lorentz_strain"]["over_static"] = line["lorentz_strain"]["value"] / value
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
     if args.batch_steps > 0:
@@ -492,6 +495,26 @@ def format_leg(args, local_rank, stream, torch, fmt):
     return {"value": N * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
             "applies_per_step": int(inf.operator_launches) / args.steps, "operator_bytes": op_bytes,
             "roofline": roofline_of(fmt, "fp32", N, op_bytes, op_ms, hbm, peak_kind)}
+
+
+# Effective Young's modulus of an epoxy-impregnated Nb3Sn winding [Pa] for the
+# Lorentz hoop-strain leg.
+Y_WINDING = 5e10
+
+
+def lorentz_leg(args, local_rank, stream, torch):
+    """The same coil and steps with the Lorentz hoop strain feeding Jc."""
+    from paper_2403_07666_b300.coil import Coil
+    w = pick_workload(args.workload)
+    w.material["Y_eff"] = Y_WINDING
+    c = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                           stream=stream.cuda_stream, format=args.format)
+    c.step(args.warmup, w.drive)
+    secs = timed_steps(c, w.drive, args.steps, stream, torch)
+    N = c.N
+    c.close()
+    return {"Y_eff_Pa": Y_WINDING, "value": N * args.steps / secs, "unit": UNIT,
+            "ms_per_step": 1e3 * secs / args.steps}
 
 
 def adjoint_leg(args, local_rank, stream, torch):
@@ -585,6 +608,7 @@ def main():
                     help="storage of the far operator in the main leg")
     ap.add_argument("--other-format", type=int, default=1, help="also time the other operator formats")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--lorentz", type=int, default=1, help="also time the step with the Lorentz hoop strain")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--batch-format", default="toeplitz_tc", choices=["toeplitz_tc", "toeplitz", "dense"])
     args = ap.parse_args()

@@ -89,6 +89,13 @@ typedef struct {
  *   bath coefficient h0 (T/T_ref)^3, bath temperature T_bath.
  * jc_factor (f), strain (eps) and mat (1 = filament, 0 = Cu) are per-element
  * host arrays of length N, copied at coil_create.
+ * Y_eff [Pa] > 0 adds the Lorentz-force hoop strain of the winding (Flux
+ * Jumps Propagation section: the electromagnetic strain produced by the
+ * Lorentz force, to which Jc of Nb3Sn is sensitive): the strain of element e is
+ *   eps_e = strain_e + r_e J_e B_z,e / Y_eff
+ * from the start-of-step current density and axial field (hoop stress r J B_z
+ * of a loop carrying J in the axial field B_z, over an effective Young's
+ * modulus of the winding).  Y_eff = 0: the static strain only.
  */
 typedef struct {
     double E0, n, Jc0, Tc, Bc2_0, B_reg, C_eps, p_eps;
@@ -98,6 +105,7 @@ typedef struct {
     const double *jc_factor;
     const double *strain;
     const int *mat;
+    double Y_eff;       /* > 0: Lorentz hoop strain on; 0: off */
 } coil_material;
 
 /*

@@ -45,6 +45,16 @@ to the quench), all from the start-of-step state of every step:
 so Q_FJ = Q_total(t_peak) - Q_at_jump and Q_q = Q_at_quench - Q_at_rise.
 Pins: Q_total of an ohmic loop is I^2 R t; the per-wire Q_total sum to the
 time integral of the diagnostic Joule power.
+
+Lorentz hoop strain (Flux Jumps Propagation section: thermal, pre-strain and
+the electromagnetic strain of the Lorentz force set Jc(eps); Quenches
+Propagation section, cases 3-5 with electromagnetic strain fields): with
+Y_eff > 0 the strain entering Jc is eps = eps0 + r J B_z / Y_eff from the
+start-of-step state, the hoop stress r J B_z over an effective Young's modulus
+of the winding (this build's reading; the paper's mechanics model is in its
+supplement).  Pins (tests/test_oracle_lorentz.py): the magnetic-pressure
+closed form of a long thin solenoid, sign and evenness under current reversal,
+and the static-strain limit Y_eff -> infinity.
 """
 
 import numpy as np
@@ -158,13 +168,25 @@ class OracleCoil:
         phi_tot = self.flux() + np.pi * geo["r"] ** 2 * Ba
         return field_from_flux(geo, phi_tot)
 
+    def strain_now(self, Bz):
+        """Element strain: the static strain, plus with Y_eff > 0 the Lorentz
+        hoop strain r J B_z / Y_eff of the current state (Flux Jumps Propagation
+        section: the electromagnetic strain produced by the Lorentz force; the
+        hoop stress of a loop carrying J in the axial field B_z is r J B_z)."""
+        Y = self.p.get("Y_eff", 0.0)
+        if not Y:
+            return self.strain
+        J = self.I / self.geo["area"]
+        return self.strain + self.geo["r"] * J * Bz / Y
+
     def pointwise(self, Ba):
         Br, Bz = self.field(Ba)
         Bmag = np.sqrt(Br * Br + Bz * Bz)
         T = self.temperature()
-        Jc = critical_current(Bmag, T, self.strain, self.jc_factor, self.mat, self.p)
+        eps = self.strain_now(Bz)
+        Jc = critical_current(Bmag, T, eps, self.jc_factor, self.mat, self.p)
         terms = ej_terms(self.I, Jc, self.mat, self.geo["r"], self.geo["area"], self.p)
-        terms.update(Br=Br, Bz=Bz, Bmag=Bmag, T=T, Jc=Jc)
+        terms.update(Br=Br, Bz=Bz, Bmag=Bmag, T=T, Jc=Jc, eps=eps)
         return terms
 
     # -- one step ------------------------------------------------------------

@@ -40,7 +40,7 @@ class Material(C.Structure):
                                           "rho_n", "rho_m", "c0", "kappa_cu", "kappa_ep", "h0",
                                           "T_ref", "T_bath")] + \
               [("jc_model", C.c_int), ("thermal", C.c_int), ("jc_factor", _dp), ("strain", _dp),
-               ("mat", _ip)]
+               ("mat", _ip), ("Y_eff", C.c_double)]
 
 
 class Options(C.Structure):
@@ -156,6 +156,7 @@ class Coil:
                   "kappa_cu", "kappa_ep", "h0", "T_ref", "T_bath"):
             setattr(m, k, float(material[k]))
         m.jc_model = int(material["jc_model"])
+        m.Y_eff = float(material.get("Y_eff", 0.0))
         m.thermal = int(material["thermal"])
         jf = np.ascontiguousarray(jc_factor, dtype=np.float64)
         st = np.ascontiguousarray(strain, dtype=np.float64)

@@ -121,11 +121,11 @@ __global__ void k_adj_mult(const CoilDev* __restrict__ cds) {
 }
 
 // Jc and its partial derivatives (zero outside the superconducting region).
-struct JcD { double Jc, dBm, dT, df, dCe; };
+struct JcD { double Jc, dBm, dT, df, dCe, dep; };
 
-// ep = |eps|^p_eps of the element (tabulated at coil creation).
+// ep = |eps|^p_eps of the element; dep = dJc/d(ep).
 __device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double ep, double f) {
-    JcD d = {0.0, 0.0, 0.0, 0.0, 0.0};
+    JcD d = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (c.jc_model == 1) {
         d.Jc = f * c.Jc0;
         d.df = c.Jc0;
@@ -142,6 +142,7 @@ __device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double
     d.Jc = f * core * S;
     d.df = core * S;
     d.dCe = -f * core * ep;
+    d.dep = -f * core * c.C_eps;
     d.dBm = d.Jc * (-2.0 / (bfac * Bc2) - 0.5 / (Bm + c.B_reg));
     double db_dT = Bm * (2.0 * c.Bc2_0 * tr / c.Tc) / (Bc2 * Bc2);
     d.dT = d.Jc * (-1.5 / (c.Tc * (1.0 - tr)) - 2.0 / bfac * db_dT);
@@ -199,10 +200,10 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab) {
         }
         double Bm = sqrt(Br * Br + Bz * Bz);
         int fil = c.mat[e];
-        JcD jd = {0.0, 0.0, 0.0, 0.0, 0.0};
-        if (fil) jd = jc_with_derivatives(c, Bm, T, c.strain_pow[e], c.jc_factor[e]);
+        JcD jd = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         double I = c.I[e];
         double J = I / a;
+        if (fil) jd = jc_with_derivatives(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]);
         EJD ej = ej_with_derivatives(c, fil, J, jd.Jc);
         double E = rho_n * ej.frac * J;
         double Kg = 2.0 * kPi * r * rho_n / a;
@@ -226,6 +227,13 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab) {
             if (c.has_grid && c.thermal) ab.lamU[g] += lamT * T / (4.0 * u);
             ab.lamBr[e] = Bm > 0.0 ? lamBm * Br / Bm : 0.0;
             ab.lamBz[e] = Bm > 0.0 ? lamBm * Bz / Bm : 0.0;
+            // Lorentz hoop strain eps = eps0 + r J B_z / Y: d|eps|^p/d eps = p |eps|^p / eps
+            const double eps = element_strain(c, e, r, J, Bz);
+            if (c.inv_Y != 0.0 && eps != 0.0) {
+                const double lamEps = lamJc * jd.dep * c.p_eps * pow(fabs(eps), c.p_eps) / eps;
+                lamI += lamEps * r * Bz * c.inv_Y / a;
+                ab.lamBz[e] += lamEps * r * J * c.inv_Y;
+            }
         } else {
             ab.lamBr[e] = 0.0;
             ab.lamBz[e] = 0.0;

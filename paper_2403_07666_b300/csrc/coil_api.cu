@@ -255,6 +255,7 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
         return fail(c, COIL_ERR_INVALID, "material constant out of range");
     if (!m->jc_factor || !m->strain || !m->mat)
         return fail(c, COIL_ERR_INVALID, "jc_factor, strain and mat arrays are required");
+    if (!is_fin(m->Y_eff) || m->Y_eff < 0.0) return fail(c, COIL_ERR_INVALID, "Y_eff must be finite and >= 0");
     return COIL_OK;
 }
 
@@ -339,6 +340,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.precision = o->precision;
     h.ld = ((long long)N + 63) / 64 * 64;
     h.E0 = m->E0; h.nexp = m->n; h.Jc0 = m->Jc0; h.Tc = m->Tc; h.Bc2_0 = m->Bc2_0; h.B_reg = m->B_reg;
+    h.inv_Y = m->Y_eff > 0.0 ? 1.0 / m->Y_eff : 0.0;
     h.C_eps = m->C_eps; h.p_eps = m->p_eps; h.rho_n = m->rho_n; h.rho_m = m->rho_m; h.c0 = m->c0;
     h.h0 = m->h0; h.T_ref = m->T_ref; h.T_bath = m->T_bath;
     h.maxit = o->maxit;

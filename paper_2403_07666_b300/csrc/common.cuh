@@ -77,6 +77,7 @@ struct CoilDev {
     const double *thz_lo, *thz_inv, *thz_cp;
     // material scalars
     double E0, nexp, Jc0, Tc, Bc2_0, B_reg, C_eps, p_eps, rho_n, rho_m, c0, h0, T_ref, T_bath;
+    double inv_Y;                 // 1 / Y_eff of the Lorentz hoop strain; 0 = static strain
     // drive of the current coil_step call
     double dt, ramp, Imax, Ba_rate, Ba_max;
     int Ba_wf;

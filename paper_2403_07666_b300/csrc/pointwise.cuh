@@ -34,7 +34,21 @@ __device__ __forceinline__ void field_at(const CoilDev& c, int e, double Ba, dou
     *Br = -dz / (2.0 * kPi * r);
 }
 
-// pe = |eps|^p_eps of the element (constant, tabulated at coil creation).
+// Strain of element e: the static strain, plus with the Lorentz hoop strain
+// (inv_Y > 0) r J B_z / Y_eff from the start-of-step J and B_z (Flux Jumps
+// Propagation section: the electromagnetic strain from the Lorentz force).
+__device__ __forceinline__ double element_strain(const CoilDev& c, int e, double r, double J, double Bz) {
+    return c.strain[e] + r * J * Bz * c.inv_Y;
+}
+
+// pe = |eps|^p_eps of element e: tabulated at coil creation for the static
+// strain, evaluated per step with the Lorentz term.
+__device__ __forceinline__ double strain_power(const CoilDev& c, int e, double r, double J, double Bz) {
+    if (c.inv_Y == 0.0) return c.strain_pow[e];
+    return pow(fabs(element_strain(c, e, r, J, Bz)), c.p_eps);
+}
+
+// pe = |eps|^p_eps of the element.
 __device__ __forceinline__ double critical_current(const CoilDev& c, double Bm, double T, double pe, double f) {
     if (c.jc_model == 1) return f * c.Jc0;
     double tr = T / c.Tc;

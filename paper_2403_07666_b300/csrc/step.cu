@@ -67,9 +67,9 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
         }
         double Bm = sqrt(Br * Br + Bz * Bz);
         int fil = c.mat[e];
-        double Jc = fil ? critical_current(c, Bm, T, c.strain_pow[e], c.jc_factor[e]) : 0.0;
         double I = c.I[e];
         double J = I / a;
+        double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
         double frac, dfac, jrat;
         ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
         double rho = c.rho_n * frac;
@@ -690,9 +690,9 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         }
         double Bm = sqrt(Br * Br + Bz * Bz);
         int fil = c.mat[e];
-        double Jc = fil ? critical_current(c, Bm, T, c.strain_pow[e], c.jc_factor[e]) : 0.0;
         double I = c.I[e];
         double J = I / a;
+        double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
         double frac, dfac, jrat;
         ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
         double rho = c.rho_n * frac;

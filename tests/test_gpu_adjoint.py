@@ -1,6 +1,7 @@
 """GPU adjoint (coil_adjoint) against central finite differences of the FP64
 oracle: gradients of a magnetization-loop loss with respect to the creep
-exponent n, the strain coefficient C_eps and the per-element Jc factor."""
+exponent n, the strain coefficient C_eps and the per-element Jc factor, also
+with the Lorentz hoop strain coupling J and B_z into Jc."""
 import numpy as np
 import pytest
 
@@ -18,10 +19,10 @@ def _built():
     B.build()
 
 
-def _loop_coil(thermal=1, transport=0):
+def _loop_coil(thermal=1, transport=0, Y_eff=0.0):
     """Free loops (or a transport ramp) under a triangular applied field, past
     penetration, with heating: the field-loop calibration case."""
-    mtl = dict(wl.MATERIAL, Jc0=2e8, thermal=thermal)
+    mtl = dict(wl.MATERIAL, Jc0=2e8, thermal=thermal, Y_eff=Y_eff)
     w = wl.random_coil(81, 3, 4, 4, ramp_rate=2e4 if transport else 0.0, I_max=1e9, dt=1e-4,
                        Ba_rate=4.0, Ba_max=0.02, Ba_waveform=2, material=mtl)
     w.geometry["transport"] = transport
@@ -37,10 +38,10 @@ def _oracle_moments(w, f=None, n=None, ce=None):
     return np.array([o.step(w.drive)[3] for _ in range(K)])
 
 
-@pytest.mark.parametrize("thermal,transport", [(1, 0), (0, 1)])
-def test_adjoint_matches_oracle_finite_differences(thermal, transport):
+@pytest.mark.parametrize("thermal,transport,Y_eff", [(1, 0, 0.0), (0, 1, 0.0), (1, 0, 5e7), (0, 1, 5e7)])
+def test_adjoint_matches_oracle_finite_differences(thermal, transport, Y_eff):
     from paper_2403_07666_b300.coil import Coil
-    w = _loop_coil(thermal, transport)
+    w = _loop_coil(thermal, transport, Y_eff)
     target = _oracle_moments(w, f=w.jc_factor * 1.05, n=27.0)
 
     def loss(m):
