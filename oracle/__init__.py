@@ -38,4 +38,5 @@ from .geometry import solenoid_elements, list_elements  # noqa: F401
 from .field import field_from_flux  # noqa: F401
 from .constitutive import critical_current, ej_terms  # noqa: F401
 from .thermal import ThermalGrid  # noqa: F401
-from .step import OracleCoil, kkt_solve, drive_values, build, DIAG_FIELDS  # noqa: F401
+from .step import (OracleCoil, kkt_solve, transport_shares, subelement_kkt_solve, drive_values,  # noqa: F401
+                   build, DIAG_FIELDS)

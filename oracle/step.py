@@ -46,6 +46,21 @@ so Q_FJ = Q_total(t_peak) - Q_at_jump and Q_q = Q_at_quench - Q_at_rise.
 Pins: Q_total of an ohmic loop is I^2 R t; the per-wire Q_total sum to the
 time integral of the diagnostic Joule power.
 
+Subelements (Numerical Algorithm section: J = J_H + J_I; the field-driven
+part J_H circulates in each subelement with zero net current, the transport
+part J_I spreads over the whole wire with its subelements coupled, by the A-V
+formulation; both with the resistivity of the total J).  With a group id per
+element position of a turn (``groups``), every transport turn tracks J_I as
+state; a step first solves J_I on the turn alone (its self block of
+M + dt G, the resistive voltage 2 pi r rho J_I, the transport constraint;
+``transport_shares``), then the coupled system with one constraint per
+subelement fixing its net rate to the J_I share (``subelement_kkt_solve``):
+the fields of the other turns and of the background move current only inside
+subelements.  Pins (tests/test_oracle_subelement.py): one group per turn
+equals the turn-constrained solve, a dense bordered solve, the parallel
+inductor division (L2 - M) : (L1 - M), the zero-net invariant under a field
+ramp, the resistive division 1/r_k of a held current, outer subelements first.
+
 Lorentz hoop strain (Flux Jumps Propagation section: thermal, pre-strain and
 the electromagnetic strain of the Lorentz force set Jc(eps); Quenches
 Propagation section, cases 3-5 with electromagnetic strain fields): with
@@ -121,6 +136,73 @@ def kkt_solve(A, R, c, block, constrained):
     return x, u
 
 
+def transport_shares(A, R_I, c, block, constrained, groups):
+    """Rate x_I of the transport part J_I and its per-subelement nets d[w, s].
+
+    Numerical Algorithm section: J = J_H + J_I; the transport part J_I is
+    distributed over the whole wire, its subelements coupled, by the A-V
+    formulation; the field-driven part J_H, driven by the field of the other
+    wires and the background, circulates inside each subelement with zero
+    net; both use the resistivity of the total J at the start of the step.
+    Reading: J_I of turn w solves the turn's own circuit, its self block
+    A_w = M_ww + dt G_w, with the resistive voltage of the transport part
+    R_I = 2 pi r rho J_I, under the turn's transport constraint:
+        A_w x_I - 1 u = -R_I,w,   1^T x_I = c_w,
+    and d[w, s] = sum of x_I over the elements of subelement s.
+    """
+    N = A.shape[0]
+    W = N // block
+    S = int(np.max(groups)) + 1
+    d = np.zeros((W, S))
+    xI = np.zeros(N)
+    ones = np.ones(block)
+    for w in np.nonzero(constrained)[0]:
+        sl = slice(w * block, (w + 1) * block)
+        Aw = A[sl, sl]
+        y = np.linalg.solve(Aw, ones)
+        t = np.linalg.solve(Aw, R_I[sl])
+        u = (c[w] + t.sum()) / y.sum()
+        xI[sl] = y * u - t
+        for g in range(S):
+            d[w, g] = xI[sl][groups == g].sum()
+    return xI, d
+
+
+def subelement_kkt_solve(A, R, d, block, constrained, groups):
+    """Exact solution of  A x - Q v = -R,  Q^T x = d  with one constraint per
+    subelement of every constrained turn (Q = element-to-subelement incidence
+    of those turns; free loops stay unconstrained).  The field-driven part of
+    the step cannot change a subelement's net current: only the transport
+    shares d do.  Returns (x, u, v): v[w, s] the subelement loop voltages,
+    u[w] their mean weighted by the subelement's element count (the turn
+    voltage reported in the diagnostics; 0 on free loops)."""
+    N = A.shape[0]
+    W = N // block
+    S = int(np.max(groups)) + 1
+    wires = np.nonzero(constrained)[0]
+    cho = sla.cho_factor(A, lower=True)
+    xR = sla.cho_solve(cho, R)
+    v = np.zeros((W, S))
+    u = np.zeros(W)
+    if wires.size == 0:
+        return -xR, u, v
+    Q = np.zeros((N, wires.size * S))
+    rhs = np.zeros(wires.size * S)
+    for k, w in enumerate(wires):
+        for g in range(S):
+            Q[w * block + np.nonzero(groups == g)[0], k * S + g] = 1.0
+            rhs[k * S + g] = d[w, g]
+    Y = sla.cho_solve(cho, Q)
+    Sc = Q.T @ Y
+    vc = np.linalg.solve(Sc, rhs + Q.T @ xR)
+    x = Y @ vc - xR
+    size = np.bincount(groups, minlength=S) / block
+    for k, w in enumerate(wires):
+        v[w] = vc[k * S:(k + 1) * S]
+        u[w] = np.dot(size, v[w])
+    return x, u, v
+
+
 class OracleCoil:
     """State and step of one coil, every quantity in FP64."""
 
@@ -136,6 +218,10 @@ class OracleCoil:
             constrained = np.ones(W, dtype=bool)
         self.constrained = np.asarray(constrained, dtype=bool)
         self.M = assemble_M(geo["r"], geo["z"], geo["h"]) if M is None else M
+        # subelements: group id of every element position of a turn (None: one group)
+        g = geo.get("groups")
+        self.groups = None if g is None or int(np.max(g)) == 0 else np.asarray(g, dtype=np.int64)
+        self.I_tr = np.zeros(N)      # transport part J_I a of the element currents (with subelements)
         self.I = np.zeros(N)
         self.u_T = np.full(N, self.p["T_bath"] ** 4)
         self.t = 0.0
@@ -204,7 +290,13 @@ class OracleCoil:
         R = 2.0 * np.pi * r * pw["E"] + np.pi * r * r * dBa
         c = (It1 - self.I.reshape(W, B).sum(axis=1)) / dt
         A = self.M + np.diag(dt * pw["G"])
-        Idot, u = kkt_solve(A, R, c, B, self.constrained)
+        if self.groups is None:
+            Idot, u = kkt_solve(A, R, c, B, self.constrained)
+        else:
+            R_I = 2.0 * np.pi * r * pw["rho"] * self.I_tr / area
+            xI, d = transport_shares(A, R_I, c, B, self.constrained, self.groups)
+            Idot, u, _ = subelement_kkt_solve(A, R, d, B, self.constrained, self.groups)
+            self.I_tr = self.I_tr + dt * xI
         self.last = dict(pw, Idot=Idot, u=u, R=R, c=c, A=A)
         # detectors on the start-of-step state (flux-jump |J/Jc| > 1, quench rho > 0.95 rho_n)
         fil = (self.mat == FILAMENT).reshape(W, B)
@@ -262,8 +354,12 @@ def build(geometry, material, jc_factor, strain, mat, constrained=None):
     if geometry["kind"] == "solenoid":
         geo = solenoid_elements(geometry["n_layers"], geometry["n_turns"], geometry["n_sub"],
                                 geometry["r_in"], geometry["pitch"], geometry["wire_d"])
+        if geometry.get("groups") is not None:
+            geo["groups"] = np.asarray(geometry["groups"])
         if constrained is None:
             constrained = np.full(geo["W"], bool(geometry.get("transport", 1)))
     else:
         geo = list_elements(geometry["r"], geometry["z"], geometry["h"], geometry["block"])
+        if geometry.get("groups") is not None:
+            geo["groups"] = np.asarray(geometry["groups"])
     return OracleCoil(geo, material, jc_factor, strain, mat, constrained)
