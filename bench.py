@@ -428,6 +428,9 @@ def run_ours(args, rank, world, local_rank):
     if args.lorentz:
         line["lorentz_strain"] = lorentz_leg(args, local_rank, stream, torch)
         line["lorentz_strain"]["over_static"] = line["lorentz_strain"]["value"] / value
+    if args.subelements:
+        line["subelements"] = subelement_leg(args, local_rank, stream, torch)
+        line["subelements"]["over_one_group"] = line["subelements"]["value"] / value
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
     if args.batch_steps > 0:
@@ -515,6 +518,27 @@ def lorentz_leg(args, local_rank, stream, torch):
     c.close()
     return {"Y_eff_Pa": Y_WINDING, "value": N * args.steps / secs, "unit": UNIT,
             "ms_per_step": 1e3 * secs / args.steps}
+
+
+def subelement_leg(args, local_rank, stream, torch):
+    """The same coil and steps with every turn split into subelements (the Cu
+    ring and the four filament quadrants): the transport part solved per turn,
+    one net-current constraint per subelement in the coupled solve."""
+    from paper_2403_07666_b300.coil import Coil
+    w = pick_workload(args.workload)
+    grp = wl.subelement_groups(w.geometry["n_sub"])
+    w.geometry["groups"] = grp
+    c = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                           stream=stream.cuda_stream, format=args.format, profile=True)
+    c.step(args.warmup, w.drive)
+    c.reset_counters()
+    secs = timed_steps(c, w.drive, args.steps, stream, torch)
+    inf = c.info()
+    N = c.N
+    c.close()
+    return {"groups_per_turn": int(grp.max()) + 1, "value": N * args.steps / secs, "unit": UNIT,
+            "ms_per_step": 1e3 * secs / args.steps,
+            "applies_per_step": int(inf.operator_launches) / args.steps}
 
 
 def adjoint_leg(args, local_rank, stream, torch):
@@ -609,6 +633,7 @@ def main():
     ap.add_argument("--other-format", type=int, default=1, help="also time the other operator formats")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--lorentz", type=int, default=1, help="also time the step with the Lorentz hoop strain")
+    ap.add_argument("--subelements", type=int, default=1, help="also time the step with subelement decoupling")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--batch-format", default="toeplitz_tc", choices=["toeplitz_tc", "toeplitz", "dense"])
     args = ap.parse_args()

@@ -68,7 +68,22 @@ enum { COIL_PREC_FP64 = 0, COIL_PREC_FP32 = 1, COIL_PREC_BF16 = 2 };
  *   no element grid: the stencil field (B = 0) and the thermal update are
  *   unavailable, so the material must use jc_model = 1 and thermal = 0.
  * Blocks (wires) hold at most 64 elements (n_sub <= 8).
+ *
+ * Subelements (Numerical Algorithm section: J = J_H + J_I, the field-driven
+ * part J_H with zero net current in every subelement, the transport part J_I
+ * spread over the whole wire with coupled subelements by the A-V
+ * formulation).  n_groups > 1 with group[k] in [0, n_groups) for each of the
+ * `block` element positions k of a turn (the same layout in every turn)
+ * splits every transport turn into subelements: each step first solves J_I
+ * on the turn alone (its own block of M + dt G, the resistive voltage
+ * 2 pi r rho J_I of the transport part, the transport constraint), then the
+ * coupled step with the net current rate of every subelement fixed to its
+ * J_I share; J_I is kept as state.  Free loops are unaffected.  Limits: at
+ * most COIL_MAX_GROUPS subelements, every group non-empty, blocks of at most
+ * 16 elements; coil_adjoint is unavailable with subelements.
+ * n_groups <= 1 (group may be NULL): one group, the plain turn constraint.
  */
+#define COIL_MAX_GROUPS 6
 typedef struct {
     int kind;
     int n_layers, n_turns, n_sub;
@@ -77,6 +92,8 @@ typedef struct {
     int n_elem, block;
     const double *r, *z, *h;
     const int *block_transport;
+    int n_groups;
+    const int *group;
 } coil_geometry;
 
 /*

@@ -32,7 +32,8 @@ class Geometry(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_layers", C.c_int), ("n_turns", C.c_int), ("n_sub", C.c_int),
                 ("r_in", C.c_double), ("pitch", C.c_double), ("wire_d", C.c_double),
                 ("transport", C.c_int), ("n_elem", C.c_int), ("block", C.c_int),
-                ("r", _dp), ("z", _dp), ("h", _dp), ("block_transport", _ip)]
+                ("r", _dp), ("z", _dp), ("h", _dp), ("block_transport", _ip),
+                ("n_groups", C.c_int), ("group", _ip)]
 
 
 class Material(C.Structure):
@@ -151,6 +152,11 @@ class Coil:
             self._keep += [r, z, h, bt]
             g.r, g.z, g.h = _ptr(r), _ptr(z), _ptr(h)
             g.block_transport = _ptr(bt, C.c_int)
+        if geometry.get("groups") is not None:
+            gr = np.ascontiguousarray(geometry["groups"], dtype=np.int32)
+            self._keep.append(gr)
+            g.n_groups = int(gr.max()) + 1 if gr.size else 0
+            g.group = _ptr(gr, C.c_int)
         m = Material()
         for k in ("E0", "n", "Jc0", "Tc", "Bc2_0", "B_reg", "C_eps", "p_eps", "rho_n", "rho_m", "c0",
                   "kappa_cu", "kappa_ep", "h0", "T_ref", "T_bath"):

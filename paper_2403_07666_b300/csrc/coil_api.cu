@@ -245,6 +245,20 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
     } else {
         return fail(c, COIL_ERR_INVALID, "unknown geometry kind");
     }
+    if (g->n_groups > 1) {
+        static_assert(COIL_MAX_GROUPS == kGroupMax, "subelement limit of the ABI and the kernels");
+        const int B = g->kind == COIL_GEOM_SOLENOID ? g->n_sub * g->n_sub : g->block;
+        if (!g->group || g->n_groups > COIL_MAX_GROUPS || B > kSegMax)
+            return fail(c, COIL_ERR_INVALID, "subelements need a group array, at most 6 groups and blocks of at most 16 elements");
+        std::vector<int> cnt(g->n_groups, 0);
+        for (int k = 0; k < B; ++k) {
+            if (g->group[k] < 0 || g->group[k] >= g->n_groups)
+                return fail(c, COIL_ERR_INVALID, "subelement group id outside [0, n_groups)");
+            ++cnt[g->group[k]];
+        }
+        for (int v : cnt)
+            if (!v) return fail(c, COIL_ERR_INVALID, "empty subelement group");
+    }
     const double vals[] = {m->E0, m->n, m->Jc0, m->Tc, m->Bc2_0, m->B_reg, m->C_eps, m->p_eps,
                            m->rho_n, m->rho_m, m->c0, m->kappa_cu, m->kappa_ep, m->h0, m->T_ref, m->T_bath};
     for (double v : vals)
@@ -364,6 +378,19 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(upload(c, &dp, stp, "strain power")); h.strain_pow = dp;
     TRY(upload(c, &ip, mt, "mat")); h.mat = ip;
     TRY(upload(c, &ip, constrained, "constrained")); h.constrained = ip;
+    h.n_groups = g->n_groups > 1 ? g->n_groups : 0;
+    if (h.n_groups) {
+        const int S = h.n_groups;
+        std::vector<int> grp(g->group, g->group + B);
+        TRY(upload(c, &ip, grp, "subelement groups")); h.group = ip;
+        for (int k = 0; k < kGroupMax; ++k) h.gwt[k] = 0.0;
+        for (int k = 0; k < B; ++k) h.gwt[grp[k]] += 1.0 / B;
+        TRY(dalloc(c, &h.Itr, N, "transport part"));
+        CK(cudaMemsetAsync(h.Itr, 0, N * sizeof(double), c->stream), "memset");
+        TRY(dalloc(c, &h.xI, N, "transport rate"));
+        TRY(dalloc(c, &h.zgrp, (size_t)N * S, "subelement projections"));
+        TRY(dalloc(c, &h.ugrp, (size_t)W * S, "subelement voltages"));
+    }
     TRY(upload(c, &ip, block_type, "block_type")); h.block_type = ip;
 
     // thermal / stencil tables
@@ -1131,6 +1158,8 @@ coil_status coil_set_currents(coil_t* c, const double* I) {
     CK(cudaMemcpyAsync(h.I, I, h.N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "set");
     TRY(apply_plain(c, h.I));
     CK(cudaMemcpyAsync(h.Phi, h.qv, h.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "set");
+    if (h.n_groups)    // injected currents carry no transport history: J_I restarts from 0
+        CK(cudaMemsetAsync(h.Itr, 0, h.N * sizeof(double), c->stream), "set");
     CK(cudaMemsetAsync(h.x, 0, h.ld * sizeof(double), c->stream), "set");
     CK(cudaStreamSynchronize(c->stream), "set");
     return COIL_OK;
@@ -1231,7 +1260,8 @@ coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
     if (!c || !bytes) return c ? fail(c, COIL_ERR_INVALID, "null size pointer") : COIL_ERR_INVALID;
     const CoilDev& h = c->h;
     size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
-    size_t need = sizeof(StateHeader) + (3 * N + G + 6 * W) * sizeof(double) + 3 * W * sizeof(long long);
+    const size_t NI = h.n_groups ? N : 0;   // transport part J_I with subelements
+    size_t need = sizeof(StateHeader) + (3 * N + G + 6 * W + NI) * sizeof(double) + 3 * W * sizeof(long long);
     if (!buf) { *bytes = need; return COIL_OK; }
     if (*bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
     cudaSetDevice(c->device);
@@ -1246,7 +1276,8 @@ coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
     CK(cudaMemcpy(p, h.first_jump, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
     CK(cudaMemcpy(p, h.first_quench, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
     CK(cudaMemcpy(p, h.first_rise, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
-    CK(cudaMemcpy(p, h.wstat, 6 * W * 8, cudaMemcpyDeviceToHost), "save");
+    CK(cudaMemcpy(p, h.wstat, 6 * W * 8, cudaMemcpyDeviceToHost), "save"); p += 6 * W * 8;
+    if (NI) CK(cudaMemcpy(p, h.Itr, NI * 8, cudaMemcpyDeviceToHost), "save");
     *bytes = need;
     return COIL_OK;
 }
@@ -1255,7 +1286,8 @@ coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
     if (!c || !buf) return c ? fail(c, COIL_ERR_INVALID, "null state buffer") : COIL_ERR_INVALID;
     const CoilDev& h = c->h;
     size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
-    size_t need = sizeof(StateHeader) + (3 * N + G + 6 * W) * sizeof(double) + 3 * W * sizeof(long long);
+    const size_t NI = h.n_groups ? N : 0;   // transport part J_I with subelements
+    size_t need = sizeof(StateHeader) + (3 * N + G + 6 * W + NI) * sizeof(double) + 3 * W * sizeof(long long);
     StateHeader hd;
     if (bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
     memcpy(&hd, buf, sizeof(hd));
@@ -1270,7 +1302,8 @@ coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
     CK(cudaMemcpy(h.first_jump, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
     CK(cudaMemcpy(h.first_quench, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
     CK(cudaMemcpy(h.first_rise, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
-    CK(cudaMemcpy(h.wstat, p, 6 * W * 8, cudaMemcpyHostToDevice), "load");
+    CK(cudaMemcpy(h.wstat, p, 6 * W * 8, cudaMemcpyHostToDevice), "load"); p += 6 * W * 8;
+    if (NI) CK(cudaMemcpy(h.Itr, p, NI * 8, cudaMemcpyHostToDevice), "load");
     Scalars sc;
     CK(cudaMemcpy(&sc, h.sc, sizeof(sc), cudaMemcpyDeviceToHost), "load");
     sc.t = hd.t;
@@ -1481,6 +1514,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
                                     const double* dL_dm, double* g_jc_factor, double* g_n, double* g_C_eps) {
     if (!c) return COIL_ERR_INVALID;
     if (n_steps < 1 || ckpt_every < 1 || !dL_dm) return fail(c, COIL_ERR_INVALID, "adjoint needs n_steps >= 1, ckpt_every >= 1, dL_dm");
+    if (c->h.n_groups) return fail(c, COIL_ERR_INVALID, "the adjoint does not differentiate the subelement decoupling");
     for (long k = 0; k < n_steps; ++k)
         if (!is_fin(dL_dm[k])) return fail(c, COIL_ERR_NONFINITE, "non-finite dL/dm");
     cudaSetDevice(c->device);

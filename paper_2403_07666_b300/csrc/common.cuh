@@ -15,6 +15,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kMu0 = 4.0e-7 * kPi;
 constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one warp
 constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B rounded up to a power of 2)
+constexpr int kGroupMax = 6;         // subelements per turn (blocks of at most kSegMax elements)
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
 constexpr int kTcTileRows = 128;     // channels per tile of the tensor-core Toeplitz apply
 
@@ -98,6 +99,16 @@ struct CoilDev {
     double *wstat;
     long long *first_rise;
     int acc_on;
+    // subelements (J = J_H + J_I): n_groups > 1 groups the B element
+    // positions of every turn (group[k]); Itr is the transport part J_I a of
+    // the element currents (state), xI its resistive voltage 2 pi r rho J_I
+    // after k_pointwise and its rate after k_factor; zgrp = Y S^-1 rows
+    // (element x n_groups), ugrp the subelement loop voltages (W x n_groups),
+    // gwt the subelements' element fractions (turn voltage = sum gwt v)
+    int n_groups;
+    const int *group;
+    double *Itr, *xI, *zgrp, *ugrp;
+    double gwt[kGroupMax];
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;

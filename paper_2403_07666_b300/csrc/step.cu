@@ -583,13 +583,35 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
 __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const Seg& s, double v, double y,
                                                         bool first, double* rz) {
     const int con = s.wv ? c.constrained[s.w] : 0;
-    const double isg = s.wv ? c.isigma[s.w] : 0.0;
-    // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
-    const double u = seg_sum(y * v, s.Bp) * isg;
-    if (con && s.ev) v -= u;
-    if (s.kk == 0 && s.wv) {
-        if (first) c.uw[s.w] = con ? u : 0.0;
-        else if (con) c.uw[s.w] += u;
+    if (c.n_groups) {
+        // subelements: remove Q v, v = (Y S^-1)^T r the subelement voltage
+        // estimates, accumulated in ugrp
+        const int S = c.n_groups;
+        const int gk = s.ev ? c.group[s.kk] : -1;
+        const double* Z = c.zgrp + (size_t)(s.ev ? s.e : 0) * S;
+        double mine = 0.0;
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) {
+            if (g < S) {
+                const double vg = seg_sum(s.ev ? Z[g] * v : 0.0, s.Bp);
+                if (g == gk) mine = vg;
+                if (s.kk == 0 && s.wv) {
+                    double* U = c.ugrp + (size_t)s.w * S + g;
+                    if (first) *U = con ? vg : 0.0;
+                    else if (con) *U += vg;
+                }
+            }
+        }
+        if (con && s.ev) v -= mine;
+    } else {
+        const double isg = s.wv ? c.isigma[s.w] : 0.0;
+        // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
+        const double u = seg_sum(y * v, s.Bp) * isg;
+        if (con && s.ev) v -= u;
+        if (s.kk == 0 && s.wv) {
+            if (first) c.uw[s.w] = con ? u : 0.0;
+            else if (con) c.uw[s.w] += u;
+        }
     }
     if (s.ev) c.res[s.e] = v;
     // z = P_w r (P_w = A_w^-1 minus, on constrained wires, the component that
@@ -700,6 +722,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         double q = E * J;
         c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
         c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
+        if (c.n_groups) c.xI[e] = 2.0 * kPi * r * rho * c.Itr[e] / a;   // resistive voltage of J_I
         if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
         sumI = I;
         pj = q * 2.0 * kPi * r * a;
@@ -724,6 +747,132 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         parts[2 * (size_t)c.W + w] = mean_rho;
         wire_detectors(c, w, sc->step, dt, pj, jr, mean_rho, tmx, qmx);
     }
+}
+
+// Subelement part of k_factor_seg (J = J_H + J_I), from row kk of A_w^-1 in
+// a, y = A_w^-1 1 and 1 / sigma:
+//  * the transport part on the turn alone, x_I = y u - A_w^-1 R_I with
+//    u = (c_w + 1^T A_w^-1 R_I) / sigma (R_I, the resistive voltage of J_I,
+//    is in xI on entry; x_I replaces it) and its subelement nets d = Q^T x_I;
+//  * Y = A_w^-1 Q, S_m = Q^T Y (Q: element-to-subelement incidence), S_m^-1
+//    by Gauss-Jordan in every lane (at most kGroupMax^2 registers), the rows
+//    Z = Y S_m^-1 (stored) and P_w = A_w^-1 - Z Y^T (stored, constrained turns);
+//  * R^T P_w R + d^T S_m^-1 d, and the warm start moved onto Q^T x = d.
+__device__ __noinline__ void factor_groups(const CoilDev& c, const Seg& s, const double (&a)[kSegMax], double y,
+                                           double isg, int con) {
+    const int B = s.B, kk = s.kk, w = s.w, e = s.e, S = c.n_groups;
+    const int gk = s.ev ? c.group[kk] : -1;
+    const double RI = s.ev ? c.xI[e] : 0.0;
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j)
+        if (j < B) t += a[j] * __shfl_sync(0xffffffffu, RI, s.base + j);
+    const double cw = s.wv ? c.cw[w] : 0.0;
+    const double uI = (cw + seg_sum(s.ev ? t : 0.0, s.Bp)) * isg;
+    const double xI = (con && s.ev) ? y * uI - t : 0.0;
+    if (s.ev) c.xI[e] = xI;
+    double Yv[kGroupMax];
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) Yv[g] = 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j) {
+        if (j < B) {
+            const int gj = c.group[j];
+#pragma unroll
+            for (int g = 0; g < kGroupMax; ++g)
+                if (g == gj) Yv[g] += a[j];
+        }
+    }
+    if (!s.ev) {
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) Yv[g] = 0.0;
+    }
+    double Sm[kGroupMax][kGroupMax];
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) {
+#pragma unroll
+        for (int h = 0; h < kGroupMax; ++h) {
+            if (h < g) continue;
+            double v = (g == h) ? 1.0 : 0.0;             // identity on the padding
+            if (g < S && h < S) v = seg_sum(gk == g ? Yv[h] : 0.0, s.Bp);
+            Sm[g][h] = v;
+            Sm[h][g] = v;
+        }
+    }
+    int bad = 0;
+#pragma unroll
+    for (int k = 0; k < kGroupMax; ++k) {
+        double piv = Sm[k][k];
+        if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
+        const double ip = 1.0 / piv;
+        Sm[k][k] = 1.0;
+#pragma unroll
+        for (int j = 0; j < kGroupMax; ++j) Sm[k][j] *= ip;
+#pragma unroll
+        for (int i = 0; i < kGroupMax; ++i) {
+            if (i == k) continue;
+            const double f = Sm[i][k];
+            Sm[i][k] = 0.0;
+#pragma unroll
+            for (int j = 0; j < kGroupMax; ++j) Sm[i][j] -= f * Sm[k][j];
+        }
+    }
+    if (bad && con && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
+    double Zv[kGroupMax];
+#pragma unroll
+    for (int h = 0; h < kGroupMax; ++h) {
+        double z = 0.0;
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) z += Yv[g] * Sm[g][h];
+        Zv[h] = z;
+    }
+    if (s.ev) {
+        double* Zo = c.zgrp + (size_t)e * S;
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g)
+            if (g < S) Zo[g] = Zv[g];
+    }
+    // P_w row kk, stored; R^T P_w R
+    const double R = s.ev ? c.R[e] : 0.0;
+    double pr = 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j) {
+        if (j < B) {
+            double pj = a[j];
+#pragma unroll
+            for (int g = 0; g < kGroupMax; ++g) {
+                const double Yjg = __shfl_sync(0xffffffffu, Yv[g], s.base + j);
+                if (con) pj -= Zv[g] * Yjg;
+            }
+            const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
+            if (s.ev) c.L[((size_t)w * B + kk) * B + j] = pj;
+            pr += pj * Rj;
+        }
+    }
+    double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
+    // subelement shares of J_I and the warm start moved onto them
+    double d[kGroupMax], gap[kGroupMax];
+    const double xe0 = s.ev ? c.x[e] : 0.0;
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) {
+        d[g] = g < S ? seg_sum(gk == g ? xI : 0.0, s.Bp) : 0.0;
+        gap[g] = g < S ? d[g] - seg_sum(gk == g ? xe0 : 0.0, s.Bp) : 0.0;
+    }
+    double dSd = 0.0, corr = 0.0;
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) {
+        double sd = 0.0;
+#pragma unroll
+        for (int h = 0; h < kGroupMax; ++h) sd += Sm[g][h] * d[h];
+        dSd += d[g] * sd;
+        corr += Zv[g] * gap[g];
+    }
+    if (s.ev) {
+        const double xe = con ? xe0 + corr : xe0;
+        c.x[e] = xe;
+        c.pf[e] = (float)xe;
+    }
+    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? dSd : 0.0);
 }
 
 // k_factor for blocks of at most 16 elements.  Lane kk holds row kk of
@@ -792,6 +941,10 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
         c.sigma[w] = sig;
         c.isigma[w] = isg;
     }
+    if (c.n_groups) {
+        factor_groups(c, s, a, y, isg, con);
+        return;
+    }
     // P_w row kk, stored; R^T P_w R
     const double R = s.ev ? c.R[e] : 0.0;
     double pr = 0.0;
@@ -843,6 +996,51 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     int B = c.B;
     double dt = c.dt;
     int con = c.constrained[w];
+    if (c.n_groups) {
+        // subelements: M x = (r + Q v) - R - dt G x; v += (Y S^-1)^T r; the
+        // transport part advances with its rate x_I
+        const int S = c.n_groups;
+        double V[kGroupMax], inc[kGroupMax];
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) {
+            V[g] = (con && g < S) ? c.ugrp[(size_t)w * S + g] : 0.0;
+            inc[g] = 0.0;
+        }
+        double mom = 0.0;
+        for (int k = lane; k < B; k += 32) {
+            int e = w * B + k;
+            const int gk = c.group[k];
+            double Vk = 0.0;
+#pragma unroll
+            for (int g = 0; g < kGroupMax; ++g)
+                if (g == gk) Vk = V[g];
+            double xe = c.x[e], re = c.res[e];
+#pragma unroll
+            for (int g = 0; g < kGroupMax; ++g)
+                if (g < S) inc[g] += c.zgrp[(size_t)e * S + g] * re;
+            double In = c.I[e] + dt * xe;
+            c.I[e] = In;
+            c.Itr[e] += dt * c.xI[e];
+            c.Phi[e] += dt * ((re + Vk) - c.R[e] - dt * c.G[e] * xe);
+            double r = c.r[e];
+            mom += kPi * r * r * In;
+        }
+        double u = 0.0;
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) {
+            const double vg = V[g] + warp_sum(inc[g]);
+            u += c.gwt[g] * vg;
+            if (lane == 0 && con && g < S) c.ugrp[(size_t)w * S + g] = vg;
+        }
+        mom = warp_sum(mom);
+        if (lane == 0) {
+            u = con ? u : 0.0;
+            c.uw[w] = u;
+            parts[5 * (size_t)c.W + w] = u;
+            parts[6 * (size_t)c.W + w] = mom;
+        }
+        return;
+    }
     double U = con ? c.uw[w] : 0.0;
     double yr = 0.0, mom = 0.0;
     for (int k = lane; k < B; k += 32) {

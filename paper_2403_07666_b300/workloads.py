@@ -65,6 +65,22 @@ def filament_mask(n_layers, n_turns, n_sub):
     return ((np.abs(xa) < half) & (np.abs(xb) < half)).astype(np.int32)
 
 
+def subelement_groups(n_sub):
+    """Subelement id of every element position of a wire (position b n + a):
+    the Cu elements (outside the filament zone) form one group, the filament
+    zone splits into its four quadrants about the wire centre; ids renumbered
+    from 0 in order of first appearance of (Cu, quadrant 0..3)."""
+    n = n_sub
+    fil = filament_mask(1, 1, n)
+    raw = []
+    for b in range(n):
+        for a in range(n):
+            k = b * n + a
+            raw.append(0 if not fil[k] else 1 + int(2 * a >= n) + 2 * int(2 * b >= n))
+    ids = {v: i for i, v in enumerate(sorted(set(raw)))}
+    return np.array([ids[v] for v in raw], dtype=np.int32)
+
+
 def solenoid(name, n_layers, n_turns, n_sub, seed, ramp_rate=10.0, I_max=400.0, dt=1e-5,
              steps=2000, r_in=0.020, pitch=0.9e-3, wire_d=0.8e-3, material=None,
              Ba_rate=0.0, Ba_max=0.0, Ba_waveform=0):
