@@ -63,6 +63,8 @@ PROFILED_TRAFFIC = {
     "fp32": {"dram_bytes": 1.595007e9 + 3.258624e6, "operator_bytes": 1594884096},
     # profiles/k_toeplitz_f32_real96k.md: the bench workload itself (table 0.73 GB)
     "toeplitz": {"dram_bytes": 1.556434e9 + 14.971904e6, "operator_bytes": 733593600},
+    # profiles/k_toeplitz_tc_real96k.md: the bench workload itself (split table 0.37 GB)
+    "toeplitz_tc": {"dram_bytes": 453.019136e6 + 3.197952e6, "operator_bytes": 368640000},
 }
 
 
@@ -452,7 +454,8 @@ def roofline_of(fmt, precision, N, op_bytes, op_ms, hbm, peak_kind):
     toeplitz (CUDA cores, FP32): bound by the FP32 pipe, 2 N^2 flops.
     toeplitz_tc (tensor cores): HBM-bound, algorithmic bytes = the split table
     (read once) + the FP32 input read + the FP64 result written (12 N); its
-    tensor work, 3 x 2 N^2 FP16 flops, is reported beside it."""
+    tensor work, 4 x 2 N^2 FP16 flops (hi.hi, hi.lo, lo.hi, lo.lo), is
+    reported beside it."""
     if fmt == "toeplitz":
         flops = 2.0 * N * N
         achieved = flops / (op_ms / 1e3) / 1e12
@@ -471,7 +474,7 @@ def roofline_of(fmt, precision, N, op_bytes, op_ms, hbm, peak_kind):
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": "k_toeplitz_tc (+split)", "peak_kind": peak_kind,
                 "avg_launch_ms": op_ms, "bytes_per_launch": nbytes, "table_bytes": op_bytes,
-                "tensor_tflops_fp16": 6.0 * N * N / (op_ms / 1e3) / 1e12}
+                "tensor_tflops_fp16": 8.0 * N * N / (op_ms / 1e3) / 1e12}
     achieved = op_bytes / (op_ms / 1e3) / 1e9
     prof = PROFILED_TRAFFIC.get(precision)
     traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None

@@ -13,32 +13,42 @@
 //
 // with the turn index t as the MMA's N dimension.  For offset d only turns
 // max(0, d) <= t < min(NT, NT + d) have a source row; each MMA covers exactly
-// those turns (rounded out to 16 columns), writes its accumulator at TMEM
-// column t, and reads its B operand as a window, starting at row t - d, of one
-// staged copy of p (rows -16 .. NT + 15, zero outside the winding).  So the
-// Toeplitz shift costs no copy and no padded work, and every table entry is
-// read from HBM once per apply.
+// those turns (rounded out to groups of 8), writes its accumulator at TMEM
+// columns 2 t, 2 t + 1, and reads its B operand as a window, starting at row
+// t - d, of one staged copy of p (rows -8 .. NT + 7, zero outside the
+// winding).  So the Toeplitz shift costs no copy and no padded work.
+//
+// Only the offsets d >= 0 are stored: T_{-d} = T_d^T (M is symmetric), so the
+// tile of T_d that serves y += T_d p, read K-major, serves y += T_d^T p read
+// MN-major from the same shared memory: every table byte feeds two products.
 //
 // Precision: entries and inputs are scaled by powers of two (2^exT brings
 // max |T| over the table below 2^14, 2^x[t] the largest |p| of turn row t)
-// and split v = hi + lo into two FP16 numbers; the three products
-// hi*hi + hi*lo + lo*hi keep about 22 significant bits, the FP32 class.  The
-// tensor cores' FP32 accumulation does not round to nearest, so its error
-// grows with the number of MMAs added into one accumulator; here an
-// accumulator takes only one stage (one offset d, one 64-channel k block: 12
-// MMAs), after which the epilogue warps add it into FP32 registers (round to
-// nearest), column t times 2^(xmin - x[t - d]): the scale of its source row
-// relative to the largest-scale row, an exact power of two of at most 1, so
-// the FP32 sums stay in the range of a single global scale.  The reduction
-// removes 2^(xmin + exT) in FP64.  Up to four TMEM accumulators rotate, so
-// the MMAs of the next stages run while one is drained.  The CTAs' partial
-// tiles are summed in FP64 in a fixed order: the result is deterministic.
+// and split v = hi + lo into two FP16 numbers.  The staged input interleaves
+// hi and lo of each turn row (rows 2 t, 2 t + 1), so one MMA A_hi x B gives
+// hi*hi and hi*lo in the column pair (2 t, 2 t + 1) and A_lo x B gives lo*hi
+// and lo*lo: two MMAs per K step, all four products, about 22 significant
+// bits, the FP32 class.  The tensor cores' FP32 accumulation does not round
+// to nearest, so its error grows with the number of MMAs added into one
+// accumulator; here an accumulator takes only one stage (one offset, one
+// 64-channel k block: 8 MMAs), after which the epilogue warps add its column
+// pairs into FP32 registers (round to nearest), column t times
+// 2^(xmin - x[t - d]): the scale of its source row relative to the
+// largest-scale row, an exact power of two of at most 1, so the FP32 sums
+// stay in the range of a single global scale.  The reduction removes
+// 2^(xmin + exT) in FP64.  Up to four TMEM accumulators rotate, so the MMAs
+// of the next stages run while one is drained.  The CTAs' partial tiles are
+// summed in a fixed order: the result is deterministic.
 //
-// Work split: the CTAs (one per SM) are dealt evenly to the 128-channel
-// tiles, and each takes a contiguous run of its tile's stages in (k block,
-// offset) order, so it meets only one or two k blocks and loads the staged
-// copy of p once per k block.  The
-// table takes 2 x 2 bytes per entry, as many as FP32.
+// Work split: every 128-channel tile gets the same number of CTAs (one per
+// SM: 144 for 960 channels).  A tile's steps (k, D), k = 0 .. n_ct - 1,
+// D = 0 .. NT - 1, pair it with column tile cb = (k - tile) mod n_ct and run
+// the stages (k block, +D) and, for D > 0, (k block, -D) for both k blocks of
+// cb; each CTA takes a contiguous range of steps, the ranges balanced by
+// stage count.  The CTA of tile cb with the same range reads the same
+// 128 x 128 region of T_D (transposed) at about the same time, so the region
+// comes from DRAM once and from L2 once.  One staged copy of p (the column
+// tile's 128 channels) is loaded per change of cb.
 //
 // CTA roles (352 threads): warp 0 issues the TMA loads, warps 1 and 2 issue
 // the MMAs of alternate stages (warp 1 owns the TMEM), warps 3-10 drain the
