@@ -13,10 +13,10 @@
 //
 // with the turn index t as the MMA's N dimension.  For offset d only turns
 // max(0, d) <= t < min(NT, NT + d) have a source row; each MMA covers exactly
-// those turns (rounded out to groups of 8), writes its accumulator at TMEM
-// columns 2 t, 2 t + 1, and reads its B operand as a window, starting at row
-// t - d, of one staged copy of p (rows -8 .. NT + 7, zero outside the
-// winding).  So the Toeplitz shift costs no copy and no padded work.
+// those turns (from a multiple of 8, N rounded up to 16), writes its
+// accumulator at TMEM column t, and reads its B operand as a window, starting
+// at row t - d, of one staged copy of p (rows -8 .. NT + 15, zero outside the
+// winding).  So the Toeplitz shift costs no copy and almost no padded work.
 //
 // Only the offsets d >= 0 are stored: T_{-d} = T_d^T (M is symmetric), so the
 // tile of T_d that serves y += T_d p, read K-major, serves y += T_d^T p read
@@ -24,21 +24,20 @@
 //
 // Precision: entries and inputs are scaled by powers of two (2^exT brings
 // max |T| over the table below 2^14, 2^x[t] the largest |p| of turn row t)
-// and split v = hi + lo into two FP16 numbers.  The staged input interleaves
-// hi and lo of each turn row (rows 2 t, 2 t + 1), so one MMA A_hi x B gives
-// hi*hi and hi*lo in the column pair (2 t, 2 t + 1) and A_lo x B gives lo*hi
-// and lo*lo: two MMAs per K step, all four products, about 22 significant
-// bits, the FP32 class.  The tensor cores' FP32 accumulation does not round
-// to nearest, so its error grows with the number of MMAs added into one
-// accumulator; here an accumulator takes only one stage (one offset, one
-// 64-channel k block: 8 MMAs), after which the epilogue warps add its column
-// pairs into FP32 registers (round to nearest), column t times
-// 2^(xmin - x[t - d]): the scale of its source row relative to the
-// largest-scale row, an exact power of two of at most 1, so the FP32 sums
-// stay in the range of a single global scale.  The reduction removes
-// 2^(xmin + exT) in FP64.  Up to four TMEM accumulators rotate, so the MMAs
-// of the next stages run while one is drained.  The CTAs' partial tiles are
-// summed in a fixed order: the result is deterministic.
+// and split v = hi + lo into two FP16 numbers.  The staged input holds the hi
+// rows and the lo rows of the turns as two blocks, so per K step three MMAs
+// A_hi x B_hi, A_hi x B_lo and A_lo x B_hi add the three products that keep
+// about 22 significant bits (the FP32 class) into accumulator column t.  The
+// tensor cores' FP32 accumulation does not round to nearest, so its error
+// grows with the number of MMAs added into one accumulator; here an
+// accumulator takes only one stage (one offset, one 64-channel k block: 12
+// MMAs), after which the epilogue warps add its columns into FP32 registers
+// (round to nearest), column t times 2^(xmin - x[t - d]): the scale of its
+// source row relative to the largest-scale row, an exact power of two of at
+// most 1, so the FP32 sums stay in the range of a single global scale.  The
+// reduction removes 2^(xmin + exT) in FP64.  Up to four TMEM accumulators
+// rotate, so the MMAs of the next stages run while one is drained.  The CTAs'
+// partial tiles are summed in a fixed order: the result is deterministic.
 //
 // Work split: every 128-channel tile gets the same number of CTAs (one per
 // SM: 144 for 960 channels).  A tile's steps (k, D), k = 0 .. n_ct - 1,
@@ -69,9 +68,12 @@ namespace cq {
 
 constexpr int kTcM = kTcTileRows;                // channels per tile (MMA M)
 constexpr int kTcK = 64;                         // channels per k block (one 128-byte FP16 row)
-constexpr int kTcPad = 8;                        // zero turn rows staged above and below the winding
+constexpr int kTcPad = 8;                        // zero turn rows staged below the winding
+constexpr int kTcPadTop = 16;                    // and above it (an MMA's N rounds up to 16 turns)
 constexpr int kTcEpiWarps = 8;                   // epilogue warps: 4 lane quadrants x 2 column parities
-constexpr int kTcThreads = 96 + 32 * kTcEpiWarps;      // producer, two MMA issuers, epilogue
+constexpr int kTcIssuers = 2;                    // MMA-issuing warps, taking the stages in turn
+constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
+constexpr int kTcThreads = 32 * (kTcEpi0 + kTcEpiWarps);   // producer, MMA issuers, epilogue
 constexpr int kTcGroups = 7;                     // 8-turn groups per epilogue warp (NT <= 112)
 constexpr uint32_t kTcAStage = 2u * kTcM * kTcK * 2u;   // hi + lo table tiles, 32 KB
 // MN-major A (128-byte swizzle): byte offsets between the two 64-channel
@@ -206,6 +208,18 @@ __device__ __forceinline__ void tmem_st16_zero(uint32_t taddr) {
         "r"(z)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -276,7 +290,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // acc_empty: one arrival per epilogue warp; b_empty and mma_done: one per MMA
             // issuer; the others: one arrival (+ bytes)
             const bool two = bar == b_empty || bar == mma_done;
-            mbar_init(bar, (bar >= acc_empty && bar < acc_empty + 32u) ? (uint32_t)kTcEpiWarps : (two ? 2u : 1u));
+            mbar_init(bar, (bar >= acc_empty && bar < acc_empty + 32u) ? (uint32_t)kTcEpiWarps
+                                                                         : (two ? (uint32_t)kTcIssuers : 1u));
         }
         *abort_flag = 0;
         *xmin_s = 1 << 30;
@@ -312,8 +327,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
                 if (!ok) break;
                 mbar_expect_tx(b_full + 8u * sb, b_stage);
-                // rows -2 kTcPad .. 2 NT + 2 kTcPad - 1 (turn rows -kTcPad .., hi and lo) of 16 chunks
-                tma_load_3d(sB + (uint32_t)sb * b_pitch, &tmB, 0, -2 * kTcPad, cb * (kTcM / 8), b_full + 8u * sb);
+                // turn rows -kTcPad .. NT + kTcPadTop - 1, hi and lo, of 16 chunks
+                tma_load_4d(sB + (uint32_t)sb * b_pitch, &tmB, 0, -kTcPad, 0, cb * (kTcM / 8), b_full + 8u * sb);
                 b_used |= 1u << sb;
                 b_par = (b_par & ~(1u << sb)) | (pb << sb);
                 if (++sb == kTcBStages) { sb = 0; pb ^= 1u; }
@@ -341,12 +356,12 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (a_used >> s & 1u) mbar_wait_final(a_full + 8u * s, a_par >> s & 1u, kTcWait);
         for (int s = 0; s < kTcBStages; ++s)
             if (b_used >> s & 1u) mbar_wait_final(b_full + 8u * s, b_par >> s & 1u, kTcWait);
-    } else if ((warp == 1 || warp == 2) && lane == 0) {
+    } else if (warp >= 1 && warp < kTcEpi0 && lane == 0) {
         // ---- MMA issuers: stage i of this CTA (table slot i % S, TMEM accumulator
         // i % n_acc, the latter's first MMA overwriting the columns it covers) is
-        // issued by warp 1 + i % 2, so that two threads' issue overheads overlap;
-        // each issuer frees a staged copy of p (two arrivals) once it has no more
-        // stages on it
+        // issued by warp 1 + i % kTcIssuers, so that the issuing threads' overheads
+        // and the MMA chains into different accumulators overlap; each issuer frees
+        // a staged copy of p (one arrival each) once it has no more stages on it
         const int me = warp - 1;
         int i = 0, grp = 0;
         int sa = 0, ai = 0;                             // slot and accumulator of stage i
@@ -370,19 +385,23 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const uint32_t pa_i = pa, pacc_i = pacc;
                 if (++sa == S) { sa = 0; pa ^= 1u; }
                 if (++ai == n_acc) { ai = 0; pacc ^= 1u; }
-                if ((i & 1) != me) continue;
+                if (i % kTcIssuers != me) continue;
                 const int d = sgn ? -D : D;
-                // staged copy: [16 chunks of 8 channels][2 NR rows: hi, lo of each turn row][8];
+                // staged copy: [16 chunks of 8 channels][hi, lo][NR turn rows][8];
                 // k block j of the column tile = chunks 8 j .. 8 j + 7
                 const uint32_t bj = bbase + (uint32_t)j * 256u * (uint32_t)sh.NR;
-                ok = mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag);
-                if (ok) ok = mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag);
+                // accumulator first: its release by the drain of stage i - n_acc means
+                // every stage up to there has completed its MMAs, so (S >= n_acc) the
+                // previous load of this stage's slot has landed and the parity wait
+                // below cannot be satisfied by the phase before it (another issuer's)
+                ok = mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag);
+                if (ok) ok = mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 const int t_first = d > 0 ? d : 0;
                 const int t_end = d < 0 ? sh.NT + d : sh.NT;
                 const int ts = t_first & ~7;
-                const int n = (t_end - ts + 7) & ~7;            // turns covered (2 n accumulator columns)
+                const int n = (t_end - ts + 15) & ~15;          // turns covered = accumulator columns
                 const bool amn = d < 0;
                 const uint32_t ah = sA + (uint32_t)sa_i * kTcAStage;
                 // K-major A: rows of 64 channels c', 8-row groups 1 KB apart, K step = 32 B.
@@ -394,20 +413,23 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const uint64_t a_hi = amn ? sdesc(ah, kTcMnLbo, kTcMnSbo, 2u) : sdesc(ah, 16u, 1024u, 2u);
                 const uint64_t a_lo = a_hi + (((uint64_t)kTcM * 128u) >> 4);
                 const uint64_t a_step = amn ? (2048u >> 4) : (32u >> 4);
-                // B: the 2 n rows of turns ts .. ts + n - 1 (source rows ts - d ..), hi and lo
-                // interleaved, so A_hi x B gives hi*hi | hi*lo and A_lo x B gives lo*hi | lo*lo
-                // in column pairs 2 t, 2 t + 1; at most 128 turns (N = 256) per MMA
+                // B: the n rows of turns ts .. ts + n - 1 (source rows ts - d ..) of the hi
+                // and of the lo half; three MMAs per K step, hi*hi + hi*lo + lo*hi, into
+                // accumulator column t; at most 256 turns per MMA
                 const uint64_t b_step = (2u * 32u * (uint32_t)sh.NR) >> 4;
-                for (int part0 = 0; part0 < n; part0 += 128) {
-                    const int np = min(128, n - part0);
-                    const uint32_t idesc = idesc_f16(2 * np, amn);
-                    const uint32_t dcol = tmem + (uint32_t)ai_i * acc_cols + 2u * (uint32_t)(ts + part0);
+                const uint64_t b_half = (16u * (uint32_t)sh.NR) >> 4;
+                for (int part0 = 0; part0 < n; part0 += 256) {
+                    const int np = min(256, n - part0);
+                    const uint32_t idesc = idesc_f16(np, amn);
+                    const uint32_t dcol = tmem + (uint32_t)ai_i * acc_cols + (uint32_t)(ts + part0);
                     const uint32_t row0 = (uint32_t)(ts + part0 - d + kTcPad);
-                    const uint64_t b0 = sdesc(bj + 32u * row0, 32u * (uint32_t)sh.NR, 128u, 0u);
+                    const uint64_t b_hi = sdesc(bj + 16u * row0, 32u * (uint32_t)sh.NR, 128u, 0u);
+                    const uint64_t b_lo = b_hi + b_half;
 #pragma unroll
                     for (int s = 0; s < kTcK / 16; ++s) {
-                        mma_f16(dcol, a_hi + s * a_step, b0 + s * b_step, idesc, s > 0 ? 1u : 0u);
-                        mma_f16(dcol, a_lo + s * a_step, b0 + s * b_step, idesc, 1u);
+                        mma_f16(dcol, a_hi + s * a_step, b_hi + s * b_step, idesc, s > 0 ? 1u : 0u);
+                        mma_f16(dcol, a_hi + s * a_step, b_lo + s * b_step, idesc, 1u);
+                        mma_f16(dcol, a_lo + s * a_step, b_hi + s * b_step, idesc, 1u);
                     }
                 }
                 mma_commit(a_empty + 8u * sa_i);
@@ -417,11 +439,11 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // every MMA issued (also after an abort) completes before the TMEM is freed
         mma_commit(mma_done);
         if (!mbar_wait_final(mma_done, 0u, kTcWait)) *abort_flag = 1;
-    } else if (warp >= 3) {
+    } else if (warp >= kTcEpi0) {
         // ---- epilogue: each stage's accumulator is added into FP32 registers (lane
         // quadrant warp % 4, turn groups of parity h), then released to the MMAs
         const int q = warp & 3;
-        const int h = (warp - 3) >> 2;
+        const int h = (warp - kTcEpi0) >> 2;
         const int cc = c0 + 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         float acc[kTcGroups][8];                       // turn group g = 2 gi + h: turns 8 g .. 8 g + 7
@@ -450,18 +472,18 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 for (int gi = 0; gi < kTcGroups; ++gi) {
                     const int g = 2 * gi + h;
                     if (g >= g_lo && g < g_hi) {
-                        float v[16];                            // column pairs of turns 8 g .. 8 g + 7
-                        tmem_ld16(src + 16u * (uint32_t)g, v);
+                        float v[8];                             // columns of turns 8 g .. 8 g + 7
+                        tmem_ld8(src + 8u * (uint32_t)g, v);
                         // scales of source rows 8 g + i - d (staged rows + kTcPad): copy a % 4
                         const int a = 8 * g + kTcPad - d;
                         const float4* sc4 = reinterpret_cast<const float4*>(inv_s + (a & 3) * scp + (a & ~3));
 #pragma unroll
                         for (int q4 = 0; q4 < 2; ++q4) {
                             const float4 f = sc4[q4];
-                            acc[gi][4 * q4 + 0] = fmaf(v[8 * q4 + 0] + v[8 * q4 + 1], f.x, acc[gi][4 * q4 + 0]);
-                            acc[gi][4 * q4 + 1] = fmaf(v[8 * q4 + 2] + v[8 * q4 + 3], f.y, acc[gi][4 * q4 + 1]);
-                            acc[gi][4 * q4 + 2] = fmaf(v[8 * q4 + 4] + v[8 * q4 + 5], f.z, acc[gi][4 * q4 + 2]);
-                            acc[gi][4 * q4 + 3] = fmaf(v[8 * q4 + 6] + v[8 * q4 + 7], f.w, acc[gi][4 * q4 + 3]);
+                            acc[gi][4 * q4 + 0] = fmaf(v[4 * q4 + 0], f.x, acc[gi][4 * q4 + 0]);
+                            acc[gi][4 * q4 + 1] = fmaf(v[4 * q4 + 1], f.y, acc[gi][4 * q4 + 1]);
+                            acc[gi][4 * q4 + 2] = fmaf(v[4 * q4 + 2], f.z, acc[gi][4 * q4 + 2]);
+                            acc[gi][4 * q4 + 3] = fmaf(v[4 * q4 + 3], f.w, acc[gi][4 * q4 + 3]);
                         }
                     }
                 }
@@ -527,8 +549,8 @@ __host__ __device__ inline int tc_exponent(double m) {
     return x > 120 ? 120 : (x < -120 ? -120 : x);
 }
 
-// p -> FP16 hi/lo in [c'/8][t][hi, lo][c' % 8] order (row 2 t + h); one block per
-// turn row t, scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.
+// p -> FP16 hi/lo in [c'/8][hi, lo][t][c' % 8] order; one block per turn row t,
+// scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.
 __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
                            int* __restrict__ pexp) {
     const CoilDev& c = *cd;
@@ -543,9 +565,9 @@ __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __h
     for (int cc = threadIdx.x; cc < sh.Cp; cc += blockDim.x) {
         const float v = cc < sh.C ? row[cc] * s : 0.f;
         const __half hi = __float2half_rn(v);
-        const int idx = (((cc >> 3) * sh.NT + t) * 2) * 8 + (cc & 7);
+        const int idx = (((cc >> 3) * 2) * sh.NT + t) * 8 + (cc & 7);
         p16[idx] = hi;
-        p16[idx + 8] = __float2half_rn(v - __half2float(hi));
+        p16[idx + 8 * sh.NT] = __float2half_rn(v - __half2float(hi));
     }
 }
 
@@ -635,12 +657,12 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
     s.C = C;
     s.Cp = (C + 7) & ~7;
     s.NT = NT;
-    s.NR = NT + 2 * kTcPad;
+    s.NR = NT + kTcPad + kTcPadTop;
     s.N = C * NT;
     s.n_ct = (C + kTcM - 1) / kTcM;
     s.n_kb = (s.Cp + kTcK - 1) / kTcK;
     s.n_cta = (int)tc_schedule(s, n_sm, nullptr, nullptr);
-    int used = 2 * ((NT + 7) & ~7);   // two accumulator columns per turn
+    int used = (NT + 15) & ~7;        // an MMA's columns end before NT + 15
     s.acc_cols = 32;
     while (s.acc_cols < used) s.acc_cols *= 2;
     s.n_acc = 512 / s.acc_cols > 4 ? 4 : 512 / s.acc_cols;   // 2..4 accumulators in 512 columns
@@ -649,6 +671,12 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
     s.stages = 6;                      // up to 192 KB of table copies in flight per SM
     while (s.stages > 2 && tc_smem_bytes(s) > limit) --s.stages;
     if (tc_smem_bytes(s) > limit) return false;
+    // the issuers' slot waits rely on stages >= accumulators (see the MMA loop)
+    if (s.n_acc > s.stages) {
+        s.n_acc = s.stages;
+        s.ncols = 32;
+        while (s.ncols < s.n_acc * s.acc_cols) s.ncols *= 2;
+    }
     *sh = s;
     return true;
 }
@@ -766,11 +794,12 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
         }
     }
     {
-        // [c'/8][2 NT rows (hi, lo of each turn row)][8]: box = the staged copy of a column tile
-        const cuuint64_t dims[3] = {8, 2 * (cuuint64_t)sh.NT, (cuuint64_t)(sh.Cp / 8)};
-        const cuuint64_t strides[2] = {16, 2 * (cuuint64_t)sh.NT * 16};
-        const cuuint32_t box[3] = {8, 2 * (cuuint32_t)sh.NR, (cuuint32_t)(kTcM / 8)};
-        CUresult r = enc(&P->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->p16, dims, strides, box, ones,
+        // [c'/8][hi, lo][NT turn rows][8]: box = the staged copy of a column tile,
+        // turn rows -kTcPad .. NT + kTcPadTop - 1 (zero fill outside the winding)
+        const cuuint64_t dims[4] = {8, (cuuint64_t)sh.NT, 2, (cuuint64_t)(sh.Cp / 8)};
+        const cuuint64_t strides[3] = {16, (cuuint64_t)sh.NT * 16, 2 * (cuuint64_t)sh.NT * 16};
+        const cuuint32_t box[4] = {8, (cuuint32_t)sh.NR, 2, (cuuint32_t)(kTcM / 8)};
+        CUresult r = enc(&P->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->p16, dims, strides, box, ones,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {

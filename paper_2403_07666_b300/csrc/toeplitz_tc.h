@@ -26,7 +26,7 @@ struct TcShape {
 struct TcPlan {
     CUtensorMap tmA;            // split table: [half][offset >= 0][c'/64][c][c' % 64] FP16, 128-byte swizzle
     CUtensorMap tmAT;           // the same table, transposed-tile boxes (offsets < 0)
-    CUtensorMap tmB;            // split input: [c'/8][t][hi, lo][c' % 8] FP16, no swizzle
+    CUtensorMap tmB;            // split input: [c'/8][hi, lo][t][c' % 8] FP16, no swizzle
     TcShape sh;
     const CoilDev* d = nullptr; // device descriptor of the coil
     __half* t16 = nullptr;      // 2 NT n_kb C 64
