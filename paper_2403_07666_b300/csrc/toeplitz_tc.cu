@@ -49,8 +49,9 @@
 // comes from DRAM once and from L2 once.  One staged copy of p (the column
 // tile's 128 channels) is loaded per change of cb.
 //
-// CTA roles (352 threads): warp 0 issues the TMA loads, warps 1 and 2 issue
-// the MMAs of alternate stages (warp 1 owns the TMEM), warps 3-10 drain the
+// CTA roles (416 threads): warp 0 issues the TMA loads, warps 1-4 issue the
+// MMAs of every fourth stage each (warp 1 owns the TMEM; one thread issues a
+// small-N MMA far slower than the tensor cores run it), warps 5-12 drain the
 // accumulators (lane quadrant warp % 4, even or odd 8-turn groups).  Every wait on an
 // mbarrier is bounded: on a timeout the CTA raises an abort flag, the others
 // stop issuing, the copies and MMAs already in flight are waited for (again
@@ -71,7 +72,7 @@ constexpr int kTcK = 64;                         // channels per k block (one 12
 constexpr int kTcPad = 8;                        // zero turn rows staged below the winding
 constexpr int kTcPadTop = 16;                    // and above it (an MMA's N rounds up to 16 turns)
 constexpr int kTcEpiWarps = 8;                   // epilogue warps: 4 lane quadrants x 2 column parities
-constexpr int kTcIssuers = 2;                    // MMA-issuing warps, taking the stages in turn
+constexpr int kTcIssuers = 4;                    // MMA-issuing warps, taking the stages in turn
 constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
 constexpr int kTcThreads = 32 * (kTcEpi0 + kTcEpiWarps);   // producer, MMA issuers, epilogue
 constexpr int kTcGroups = 7;                     // 8-turn groups per epilogue warp (NT <= 112)
