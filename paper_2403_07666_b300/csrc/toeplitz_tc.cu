@@ -71,11 +71,12 @@ constexpr int kTcM = kTcTileRows;                // channels per tile (MMA M)
 constexpr int kTcK = 64;                         // channels per k block (one 128-byte FP16 row)
 constexpr int kTcPad = 8;                        // zero turn rows staged below the winding
 constexpr int kTcPadTop = 16;                    // and above it (an MMA's N rounds up to 16 turns)
-constexpr int kTcEpiWarps = 8;                   // epilogue warps: 4 lane quadrants x 2 column parities
+constexpr int kTcParities = 3;                   // epilogue warps per lane quadrant (turn groups g % 3)
+constexpr int kTcEpiWarps = 4 * kTcParities;     // epilogue warps: 4 lane quadrants x kTcParities
 constexpr int kTcIssuers = 4;                    // MMA-issuing warps, taking the stages in turn
 constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
 constexpr int kTcThreads = 32 * (kTcEpi0 + kTcEpiWarps);   // producer, MMA issuers, epilogue
-constexpr int kTcGroups = 7;                     // 8-turn groups per epilogue warp (NT <= 112)
+constexpr int kTcGroups = (14 + kTcParities - 1) / kTcParities;   // 8-turn groups per epilogue warp (NT <= 112)
 constexpr uint32_t kTcAStage = 2u * kTcM * kTcK * 2u;   // hi + lo table tiles, 32 KB
 // MN-major A (128-byte swizzle): byte offsets between the two 64-channel
 // blocks along M (8 KB) and between 8-row groups along K (1 KB)
@@ -447,7 +448,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int h = (warp - kTcEpi0) >> 2;
         const int cc = c0 + 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        float acc[kTcGroups][8];                       // turn group g = 2 gi + h: turns 8 g .. 8 g + 7
+        float acc[kTcGroups][8];                       // turn group g = kTcParities gi + h: turns 8 g .. 8 g + 7
 #pragma unroll
         for (int g = 0; g < kTcGroups; ++g)
 #pragma unroll
@@ -471,7 +472,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const uint32_t src = lane_base + (uint32_t)ai * acc_cols;
 #pragma unroll
                 for (int gi = 0; gi < kTcGroups; ++gi) {
-                    const int g = 2 * gi + h;
+                    const int g = kTcParities * gi + h;
                     if (g >= g_lo && g < g_hi) {
                         float v[8];                             // columns of turns 8 g .. 8 g + 7
                         tmem_ld8(src + 8u * (uint32_t)g, v);
@@ -499,7 +500,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             float* out = part + (size_t)blockIdx.x * sh.NT * kTcM + 32 * q + lane;
 #pragma unroll
             for (int gi = 0; gi < kTcGroups; ++gi) {
-                const int t0 = 8 * (2 * gi + h);
+                const int t0 = 8 * (kTcParities * gi + h);
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (t0 + j < sh.NT) out[(size_t)(t0 + j) * kTcM] = acc[gi][j];
