@@ -365,12 +365,11 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // and the MMA chains into different accumulators overlap; each issuer frees
         // a staged copy of p (one arrival each) once it has no more stages on it
         const int me = warp - 1;
-        int i = 0, grp = 0;
-        int sa = 0, ai = 0;                             // slot and accumulator of stage i
-        uint32_t pa = 0, pacc = 0;                      // their phases: (i / S) & 1, (i / n_acc) & 1
+        int grp = 0;
         bool ok = true;
         const uint32_t bbase = sB;                      // one staged copy (kTcBStages == 1)
         int D = wk.y % sh.NT, cb = col_tile(wk.y);
+        int i0 = 0;                                     // the step's first stage
         for (int sg = wk.y; sg < wk.z && ok; ++sg, D = (D + 1 == sh.NT ? 0 : D + 1)) {
             if (sg != wk.y && D == 0) cb = (cb + 1 == sh.n_ct ? 0 : cb + 1);
             const int nk = min(2, sh.n_kb - 2 * cb);
@@ -381,13 +380,15 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 ++grp;
                 tc_fence_after();
             }
-            for (int sgn = 0; sgn < (D > 0 ? 2 : 1) && ok; ++sgn)
-              for (int j = 0; j < nk && ok; ++j, ++i) {
-                const int sa_i = sa, ai_i = ai;
-                const uint32_t pa_i = pa, pacc_i = pacc;
-                if (++sa == S) { sa = 0; pa ^= 1u; }
-                if (++ai == n_acc) { ai = 0; pacc ^= 1u; }
-                if (i % kTcIssuers != me) continue;
+            // this issuer's stages of the step: positions pos = sgn nk + j with
+            // (i0 + pos) % kTcIssuers == me (one per step in the common case)
+            const int ns = (D > 0 ? 2 : 1) * nk;
+            for (int pos = ((me - i0) % kTcIssuers + kTcIssuers) % kTcIssuers; pos < ns && ok;
+                 pos += kTcIssuers) {
+                const int i = i0 + pos;
+                const int sgn = pos >= nk ? 1 : 0, j = pos - sgn * nk;
+                const int sa_i = i % S, ai_i = i % n_acc;
+                const uint32_t pa_i = (uint32_t)(i / S) & 1u, pacc_i = (uint32_t)(i / n_acc) & 1u;
                 const int d = sgn ? -D : D;
                 // staged copy: [16 chunks of 8 channels][hi, lo][NR turn rows][8];
                 // k block j of the column tile = chunks 8 j .. 8 j + 7
@@ -436,7 +437,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
                 mma_commit(a_empty + 8u * sa_i);
                 mma_commit(acc_full + 8u * ai_i);
-              }
+            }
+            i0 += ns;
         }
         // every MMA issued (also after an abort) completes before the TMEM is freed
         mma_commit(mma_done);
@@ -689,8 +691,9 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
 // time, one of them reading it transposed, so the region comes from DRAM
 // once.  A tile's n_ct NT steps are split into contiguous ranges of about
 // equal stage counts (a step has 2 stages per k block of its column tile, 1
-// for D = 0; the half-height last column tile has one k block); every tile has
-// the same total, so partner CTAs stay within a fraction of a range of each
+// for D = 0; the half-height last column tile has one k block; a stage's cost
+// is mostly its issue, nearly independent of its turns); every tile has the
+// same total, so partner CTAs stay within a fraction of a range of each
 // other.  work[cta] = (tile, first step, end step, 0); range[tile] = (first
 // CTA, CTAs).  Returns the number of CTAs.
 size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::vector<int2>* range) {
