@@ -71,7 +71,7 @@ constexpr int kTcM = kTcTileRows;                // channels per tile (MMA M)
 constexpr int kTcK = 64;                         // channels per k block (one 128-byte FP16 row)
 constexpr int kTcPad = 8;                        // zero turn rows staged below the winding
 constexpr int kTcPadTop = 16;                    // and above it (an MMA's N rounds up to 16 turns)
-constexpr int kTcParities = 3;                   // epilogue warps per lane quadrant (turn groups g % 3)
+constexpr int kTcParities = 4;                   // epilogue warps per lane quadrant (turn groups g mod kTcParities)
 constexpr int kTcEpiWarps = 4 * kTcParities;     // epilogue warps: 4 lane quadrants x kTcParities
 constexpr int kTcIssuers = 4;                    // MMA-issuing warps, taking the stages in turn
 constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
