@@ -758,7 +758,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
 //    by Gauss-Jordan in every lane (at most kGroupMax^2 registers), the rows
 //    Z = Y S_m^-1 (stored) and P_w = A_w^-1 - Z Y^T (stored, constrained turns);
 //  * R^T P_w R + d^T S_m^-1 d, and the warm start moved onto Q^T x = d.
-__device__ __noinline__ void factor_groups(const CoilDev& c, const Seg& s, const double (&a)[kSegMax], double y,
+__device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, const double (&a)[kSegMax], double y,
                                            double isg, int con) {
     const int B = s.B, kk = s.kk, w = s.w, e = s.e, S = c.n_groups;
     const int gk = s.ev ? c.group[kk] : -1;
