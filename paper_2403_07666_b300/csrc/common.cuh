@@ -109,6 +109,11 @@ struct CoilDev {
     const int *group;
     double *Itr, *xI, *zgrp, *ugrp;
     double gwt[kGroupMax];
+    // warm start of a forward step: extrap = 1 starts the PCG from the linear
+    // extrapolation 2 Idot_{n-1} - Idot_{n-2} (xprev holds Idot_{n-2}) once two
+    // steps have been taken; the adjoint's transposed solves turn it off
+    double *xprev;
+    int extrap;
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;

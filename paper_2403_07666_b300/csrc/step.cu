@@ -6,7 +6,8 @@
 //                 E-J law, Joule source, right-hand side R, diagonal G,
 //                 per-wire constraint right-hand side c_w, detectors
 //   k_factor      per wire: Cholesky of A_w = M_ww + dt G_w, y_w = A_w^-1 1,
-//                 warm start made feasible, norm of the right-hand side
+//                 warm start (extrapolated from the last two steps' Idot)
+//                 made feasible, norm of the right-hand side
 //   projected PCG (operator apply = dense far GEMV + k_near; k_init,
 //                 k_update, k_direction, k_reduce)
 //   k_finalize    loop voltages u_w, I += dt Idot, flux += dt M Idot
@@ -17,6 +18,20 @@
 #include "tridiag.cuh"
 
 namespace cq {
+
+// Warm start of element e for this step's PCG: the last step's Idot, or (a
+// forward step of a coil with extrap set, from its third step on) the linear
+// extrapolation 2 Idot_{n-1} - Idot_{n-2}; xprev takes Idot_{n-1} on every
+// forward step.  ext is uniform over the launch.
+__device__ __forceinline__ double warm_start(const CoilDev& c, int e, bool ext) {
+    const double x = c.x[e];
+    if (!c.extrap) return x;
+    const double xp = c.xprev[e];
+    c.xprev[e] = x;
+    return ext ? 2.0 * x - xp : x;
+}
+
+__device__ __forceinline__ bool extrapolate(const CoilDev& c) { return c.extrap && c.sc->step >= 2; }
 
 // Detectors and per-wire statistics of wire w from its start-of-step state
 // (Flux Jumps Propagation and Quenches Propagation sections): onsets of the
@@ -221,9 +236,14 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
     double rn = 0.0;
     for (int k = lane; k < B; k += 32) rn += c.R[w * B + k] * v[k];
     rn = warp_sum(rn);
-    // warm start from the previous step's Idot, moved onto this step's constraint
+    // warm start from the previous steps' Idot, moved onto this step's constraint
+    const bool ext = extrapolate(c);
     double sx = 0.0;
-    for (int k = lane; k < B; k += 32) sx += c.x[w * B + k];
+    for (int k = lane; k < B; k += 32) {
+        const double x0 = warm_start(c, w * B + k, ext);
+        c.x[w * B + k] = x0;
+        sx += x0;
+    }
     sx = warp_sum(sx);
     double corr = con ? (cw - sx) / sig : 0.0;
     for (int k = lane; k < B; k += 32) {
@@ -759,7 +779,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
 //    Z = Y S_m^-1 (stored) and P_w = A_w^-1 - Z Y^T (stored, constrained turns);
 //  * R^T P_w R + d^T S_m^-1 d, and the warm start moved onto Q^T x = d.
 __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, const double (&a)[kSegMax], double y,
-                                           double isg, int con) {
+                                           double isg, int con, double xe0) {
     const int B = s.B, kk = s.kk, w = s.w, e = s.e, S = c.n_groups;
     const int gk = s.ev ? c.group[kk] : -1;
     const double RI = s.ev ? c.xI[e] : 0.0;
@@ -852,7 +872,6 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
     double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
     // subelement shares of J_I and the warm start moved onto them
     double d[kGroupMax], gap[kGroupMax];
-    const double xe0 = s.ev ? c.x[e] : 0.0;
 #pragma unroll
     for (int g = 0; g < kGroupMax; ++g) {
         d[g] = g < S ? seg_sum(gk == g ? xI : 0.0, s.Bp) : 0.0;
@@ -941,8 +960,9 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
         c.sigma[w] = sig;
         c.isigma[w] = isg;
     }
+    const double x0 = s.ev ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
     if (c.n_groups) {
-        factor_groups(c, s, a, y, isg, con);
+        factor_groups(c, s, a, y, isg, con, x0);
         return;
     }
     // P_w row kk, stored; R^T P_w R
@@ -960,11 +980,11 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
     }
     const double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
     const double cw = s.wv ? c.cw[w] : 0.0;
-    // warm start from the previous step's Idot, moved onto this step's constraint
-    const double sx = seg_sum(s.ev ? c.x[e] : 0.0, s.Bp);
+    // warm start moved onto this step's constraint
+    const double sx = seg_sum(x0, s.Bp);
     const double corr = con ? (cw - sx) * isg : 0.0;
     if (s.ev) {
-        double xe = c.x[e] + corr * y;
+        double xe = x0 + corr * y;
         c.x[e] = xe;
         c.pf[e] = (float)xe;
     }
