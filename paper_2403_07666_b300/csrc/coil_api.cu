@@ -1549,6 +1549,8 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     TRY(mem.get(&gparts, 2 * W, "partials"));
     TRY(mem.get(&musave, N, "mu"));
     TRY(mem.get(&out2, 2, "outputs"));
+    double* muprev;
+    TRY(mem.get(&muprev, N, "previous adjoint solution"));
 
     // forward pass, checkpoint every ckpt_every steps; the states of the last
     // segment are kept as they are made, so that segment needs no recomputation
@@ -1577,15 +1579,19 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     const int last_iters_fin = c->last_iters;
 
     // reverse sweep: its pointwise launches recompute steps already counted,
-    // so the per-wire statistics stay as the forward pass left them
-    // and its transposed solves start from the adjoint's own last solution (no
-    // extrapolation; the recomputed forward steps extrapolate as the forward pass did)
+    // so the per-wire statistics stay as the forward pass left them.  Its
+    // transposed solves extrapolate from their own last two solutions (history
+    // in muprev); the recomputed forward steps use the forward history, as the
+    // forward pass did.
+    double* const xprev_fwd = h.xprev;
     struct AccGuard {
         coil_t* c;
-        ~AccGuard() { c->h.acc_on = 1; c->h.extrap = 1; sync_descriptor(c); }
-    } acc_guard{c};
+        double* xp;
+        ~AccGuard() { c->h.acc_on = 1; c->h.extrap = 1; c->h.xprev = xp; sync_descriptor(c); }
+    } acc_guard{c, xprev_fwd};
     h.acc_on = 0;
     TRY(sync_descriptor(c));
+    long solved = 0;                                 // transposed solves done
     double* lamI_next = lamA;
     double* lamI = lamB;
     double* lamU_next = lamUA;
@@ -1600,6 +1606,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
         } else {
             CK(cudaMemcpyAsync(musave, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
             h.extrap = 1;
+            h.xprev = xprev_fwd;
             TRY(sync_descriptor(c));
             TRY(state_copy(c, ck + sg * S, false, true));
             c->t = t_ck[sg];
@@ -1614,8 +1621,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
             }
             CK(cudaMemcpyAsync(h.x, musave, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
         }
-        h.extrap = 0;
-        TRY(sync_descriptor(c));
+        h.xprev = muprev;
         for (long k = k1 - 1; k >= k0; --k) {
             double* slot = seg + (k - k0) * S;
             TRY(state_copy(c, slot, false, false));
@@ -1625,7 +1631,13 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
             if (thermal) launch_adj_thermal(c->d, h, ab, s);
             launch_adj_setup(c->d, h, ab, s);
             CK(cudaGetLastError(), "adjoint launch");
+            const int mode = solved >= 2 ? 3 : 2;
+            if (h.extrap != mode) {
+                h.extrap = mode;
+                TRY(sync_descriptor(c));
+            }
             TRY(adjoint_solve(c));
+            ++solved;
             launch_adj_mult_pointwise(c->d, h, ab, s);
             if (grid) {
                 launch_adj_stencil_t(c->d, h, ab, s);
@@ -1649,6 +1661,9 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     if (g_n) *g_n = g2[0];
     if (g_C_eps) *g_C_eps = g2[1];
     // back to the state after the forward steps
+    h.extrap = 1;
+    h.xprev = xprev_fwd;
+    TRY(sync_descriptor(c));
     TRY(state_copy(c, fin, false, true));
     c->t = t_fin;
     c->steps = st_fin;

@@ -109,9 +109,11 @@ struct CoilDev {
     const int *group;
     double *Itr, *xI, *zgrp, *ugrp;
     double gwt[kGroupMax];
-    // warm start of a forward step: extrap = 1 starts the PCG from the linear
-    // extrapolation 2 Idot_{n-1} - Idot_{n-2} (xprev holds Idot_{n-2}) once two
-    // steps have been taken; the adjoint's transposed solves turn it off
+    // warm start of a solve: the PCG starts from the linear extrapolation
+    // 2 x_{n-1} - x_{n-2} of the last two solutions (xprev holds x_{n-2}).
+    // extrap: 0 plain warm start; 1 forward steps (extrapolate from the third
+    // step on); 2 record x only; 3 extrapolate always (the adjoint's transposed
+    // solves, with xprev pointing at their own history)
     double *xprev;
     int extrap;
     double *diag;                 // ring [cap][10]

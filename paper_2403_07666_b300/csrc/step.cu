@@ -19,10 +19,9 @@
 
 namespace cq {
 
-// Warm start of element e for this step's PCG: the last step's Idot, or (a
-// forward step of a coil with extrap set, from its third step on) the linear
-// extrapolation 2 Idot_{n-1} - Idot_{n-2}; xprev takes Idot_{n-1} on every
-// forward step.  ext is uniform over the launch.
+// Warm start of element e for this solve's PCG: the last solution, or the
+// linear extrapolation 2 x_{n-1} - x_{n-2} (see CoilDev::extrap); xprev takes
+// x_{n-1} whenever extrap is set.  ext is uniform over the launch.
 __device__ __forceinline__ double warm_start(const CoilDev& c, int e, bool ext) {
     const double x = c.x[e];
     if (!c.extrap) return x;
@@ -31,7 +30,9 @@ __device__ __forceinline__ double warm_start(const CoilDev& c, int e, bool ext) 
     return ext ? 2.0 * x - xp : x;
 }
 
-__device__ __forceinline__ bool extrapolate(const CoilDev& c) { return c.extrap && c.sc->step >= 2; }
+__device__ __forceinline__ bool extrapolate(const CoilDev& c) {
+    return (c.extrap == 1 && c.sc->step >= 2) || c.extrap == 3;
+}
 
 // Detectors and per-wire statistics of wire w from its start-of-step state
 // (Flux Jumps Propagation and Quenches Propagation sections): onsets of the
