@@ -320,7 +320,7 @@ coil_status coil_apply_operator_static(coil_t *c, const double *d_p, double *d_y
  * (far part converted from its storage precision, near blocks added). */
 coil_status coil_read_operator(coil_t *c, double *M);
 
-/* Serialise / restore the FP64 state (I, flux, T^4, t, step, the last two
+/* Serialise / restore the FP64 state (I, flux, T^4, t, step, the last three
  * steps' Idot that start the next PCG,
  * onsets and per-wire statistics).
  * With buf == NULL, *bytes receives the required size. */

@@ -441,6 +441,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.Phi, N, "Phi"));
     TRY(dalloc(c, &h.x, ld, "x"));
     TRY(dalloc(c, &h.xprev, N, "previous Idot"));
+    TRY(dalloc(c, &h.xprev2, N, "Idot before the previous"));
     h.extrap = 1;
     TRY(dalloc(c, &h.res, N, "res"));
     TRY(dalloc(c, &h.zv, N, "z"));
@@ -1164,6 +1165,7 @@ coil_status coil_set_currents(coil_t* c, const double* I) {
         CK(cudaMemsetAsync(h.Itr, 0, h.N * sizeof(double), c->stream), "set");
     CK(cudaMemsetAsync(h.x, 0, h.ld * sizeof(double), c->stream), "set");
     CK(cudaMemsetAsync(h.xprev, 0, h.N * sizeof(double), c->stream), "set");
+    CK(cudaMemsetAsync(h.xprev2, 0, h.N * sizeof(double), c->stream), "set");
     CK(cudaStreamSynchronize(c->stream), "set");
     return COIL_OK;
 }
@@ -1250,8 +1252,8 @@ coil_status coil_read_operator(coil_t* c, double* M) {
     return COIL_OK;
 }
 
-// "COILST03": state of I, Phi, x, xprev, u_T, onsets and per-wire statistics
-constexpr unsigned long long kStateMagic = 0x434f494c53543033ULL;
+// "COILST04": state of I, Phi, x, xprev, xprev2, u_T, onsets and per-wire statistics
+constexpr unsigned long long kStateMagic = 0x434f494c53543034ULL;
 
 struct StateHeader {
     unsigned long long magic;
@@ -1264,7 +1266,7 @@ coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
     const CoilDev& h = c->h;
     size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
     const size_t NI = h.n_groups ? N : 0;   // transport part J_I with subelements
-    size_t need = sizeof(StateHeader) + (4 * N + G + 6 * W + NI) * sizeof(double) + 3 * W * sizeof(long long);
+    size_t need = sizeof(StateHeader) + (5 * N + G + 6 * W + NI) * sizeof(double) + 3 * W * sizeof(long long);
     if (!buf) { *bytes = need; return COIL_OK; }
     if (*bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
     cudaSetDevice(c->device);
@@ -1276,6 +1278,7 @@ coil_status coil_save_state(coil_t* c, void* buf, size_t* bytes) {
     CK(cudaMemcpy(p, h.Phi, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
     CK(cudaMemcpy(p, h.x, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
     CK(cudaMemcpy(p, h.xprev, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
+    CK(cudaMemcpy(p, h.xprev2, N * 8, cudaMemcpyDeviceToHost), "save"); p += N * 8;
     if (G) { CK(cudaMemcpy(p, h.uT, G * 8, cudaMemcpyDeviceToHost), "save"); p += G * 8; }
     CK(cudaMemcpy(p, h.first_jump, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
     CK(cudaMemcpy(p, h.first_quench, W * 8, cudaMemcpyDeviceToHost), "save"); p += W * 8;
@@ -1291,7 +1294,7 @@ coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
     const CoilDev& h = c->h;
     size_t N = h.N, W = h.W, G = (size_t)h.Gr * h.Gz;
     const size_t NI = h.n_groups ? N : 0;   // transport part J_I with subelements
-    size_t need = sizeof(StateHeader) + (4 * N + G + 6 * W + NI) * sizeof(double) + 3 * W * sizeof(long long);
+    size_t need = sizeof(StateHeader) + (5 * N + G + 6 * W + NI) * sizeof(double) + 3 * W * sizeof(long long);
     StateHeader hd;
     if (bytes < need) return fail(c, COIL_ERR_INVALID, "state buffer too small");
     memcpy(&hd, buf, sizeof(hd));
@@ -1303,6 +1306,7 @@ coil_status coil_load_state(coil_t* c, const void* buf, size_t bytes) {
     CK(cudaMemcpy(h.Phi, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
     CK(cudaMemcpy(h.x, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
     CK(cudaMemcpy(h.xprev, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
+    CK(cudaMemcpy(h.xprev2, p, N * 8, cudaMemcpyHostToDevice), "load"); p += N * 8;
     if (G) { CK(cudaMemcpy(h.uT, p, G * 8, cudaMemcpyHostToDevice), "load"); p += G * 8; }
     CK(cudaMemcpy(h.first_jump, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
     CK(cudaMemcpy(h.first_quench, p, W * 8, cudaMemcpyHostToDevice), "load"); p += W * 8;
@@ -1442,11 +1446,11 @@ coil_status state_copy(coil_t* c, double* slot, bool save, bool with_x) {
     const CoilDev& h = c->h;
     size_t N = h.N, G = (size_t)h.Gr * h.Gz;
     cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-    double* parts[5] = {h.I, h.Phi, h.x, h.xprev, h.uT};
-    size_t sizes[5] = {N, N, N, N, G};
+    double* parts[6] = {h.I, h.Phi, h.x, h.xprev, h.xprev2, h.uT};
+    size_t sizes[6] = {N, N, N, N, N, G};
     size_t off = 0;
-    for (int i = 0; i < 5; ++i) {
-        if (sizes[i] && ((i != 2 && i != 3) || with_x)) {
+    for (int i = 0; i < 6; ++i) {
+        if (sizes[i] && ((i < 2 || i > 4) || with_x)) {
             if (save) CK(cudaMemcpyAsync(slot + off, parts[i], sizes[i] * 8, k, c->stream), "state copy");
             else CK(cudaMemcpyAsync(parts[i], slot + off, sizes[i] * 8, k, c->stream), "state copy");
         }
@@ -1526,7 +1530,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     TRY(set_drive(c, drive));
     CoilDev& h = c->h;
     const size_t N = h.N, G = (size_t)h.Gr * h.Gz, W = h.W;
-    const size_t S = 4 * N + G;                       // one stored state: I, Phi, x, xprev, u_T
+    const size_t S = 5 * N + G;                       // one stored state: I, Phi, x, xprev, xprev2, u_T
     const long nseg = (n_steps + ckpt_every - 1) / ckpt_every;
     const bool grid = h.has_grid != 0, thermal = h.thermal != 0;
     cudaStream_t s = c->stream;

@@ -109,12 +109,13 @@ struct CoilDev {
     const int *group;
     double *Itr, *xI, *zgrp, *ugrp;
     double gwt[kGroupMax];
-    // warm start of a solve: the PCG starts from the linear extrapolation
-    // 2 x_{n-1} - x_{n-2} of the last two solutions (xprev holds x_{n-2}).
-    // extrap: 0 plain warm start; 1 forward steps (extrapolate from the third
-    // step on); 2 record x only; 3 extrapolate always (the adjoint's transposed
-    // solves, with xprev pointing at their own history)
-    double *xprev;
+    // warm start of a solve: the PCG starts from an extrapolation of the last
+    // solutions (xprev holds x_{n-2}, xprev2 x_{n-3}).  extrap: 0 plain warm
+    // start; 1 forward steps (2 x_{n-1} - x_{n-2} on the third step,
+    // 3 x_{n-1} - 3 x_{n-2} + x_{n-3} from the fourth on); 2 record x only;
+    // 3 linear extrapolation always (the adjoint's transposed solves, with
+    // xprev pointing at their own history)
+    double *xprev, *xprev2;
     int extrap;
     double *diag;                 // ring [cap][10]
     long long diag_cap;

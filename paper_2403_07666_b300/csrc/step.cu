@@ -19,14 +19,20 @@
 
 namespace cq {
 
-// Warm start of element e for this solve's PCG: the last solution, or the
-// linear extrapolation 2 x_{n-1} - x_{n-2} (see CoilDev::extrap); xprev takes
-// x_{n-1} whenever extrap is set.  ext is uniform over the launch.
+// Warm start of element e for this solve's PCG: the last solution, or its
+// linear or (forward steps from the fourth on) quadratic extrapolation from
+// the solutions before it (see CoilDev::extrap); the history shifts whenever
+// extrap is set.  ext is uniform over the launch.
 __device__ __forceinline__ double warm_start(const CoilDev& c, int e, bool ext) {
     const double x = c.x[e];
     if (!c.extrap) return x;
     const double xp = c.xprev[e];
     c.xprev[e] = x;
+    if (c.extrap == 1) {
+        const double xp2 = c.xprev2[e];
+        c.xprev2[e] = xp;
+        if (c.sc->step >= 3) return 3.0 * x - 3.0 * xp + xp2;
+    }
     return ext ? 2.0 * x - xp : x;
 }
 

@@ -139,11 +139,11 @@ def test_thermal_relaxation_single_element():
     with Coil(geom, p, np.ones(1), np.zeros(1), np.zeros(1, np.int32)) as c:
         st = c.save_state()
         # raise T to 6 K through the state buffer (T^4 sits after I, flux, Idot
-        # and the previous step's Idot)
+        # and the two steps' Idot before it)
         hdr = 8 + 8 * 4 + 8
-        u = np.frombuffer(st[hdr + 32:hdr + 40].tobytes(), dtype=np.float64)
+        u = np.frombuffer(st[hdr + 40:hdr + 48].tobytes(), dtype=np.float64)
         assert abs(u[0] - 4.2 ** 4) < 1e-9
-        st[hdr + 32:hdr + 40] = np.frombuffer(np.array([6.0 ** 4]).tobytes(), dtype=np.uint8)
+        st[hdr + 40:hdr + 48] = np.frombuffer(np.array([6.0 ** 4]).tobytes(), dtype=np.uint8)
         c.load_state(st)
         c.step(2000, drive)
         T = c.read(drive)["T"][0]
