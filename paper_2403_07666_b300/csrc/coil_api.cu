@@ -451,6 +451,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.G, N, "G"));
     TRY(dalloc(c, &h.pf, ld, "pf"));
     TRY(dalloc(c, &h.L, (size_t)W * B * B, "L"));
+    if (B <= kSegMax) TRY(dalloc(c, &h.Lf, (size_t)W * B * B, "preconditioner"));
     TRY(dalloc(c, &h.y1, (size_t)W * B, "y1"));
     TRY(dalloc(c, &h.sigma, W, "sigma"));
     TRY(dalloc(c, &h.isigma, W, "1 / sigma"));

@@ -642,16 +642,36 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
     }
     if (s.ev) c.res[s.e] = v;
     // z = P_w r (P_w = A_w^-1 minus, on constrained wires, the component that
-    // changes the wire's total current; stored by k_factor_seg): B independent
-    // products per lane, two partial sums
-    const double* P = c.L + ((size_t)(s.wv ? s.w : 0) * s.B + (s.kk < s.B ? s.kk : 0)) * s.B;
-    double z0 = 0.0, z1 = 0.0;
+    // changes the wire's total current; stored by k_factor_seg in FP32): B
+    // independent FP32 products per lane, two partial sums.  The preconditioner
+    // needs no more (the residual stays FP64, so the solution does not depend on
+    // it), but the iterates must stay feasible: the FP32 rounding's component
+    // along the constrained directions is removed in FP64.
+    const float* P = c.Lf + ((size_t)(s.wv ? s.w : 0) * s.B + (s.kk < s.B ? s.kk : 0)) * s.B;
+    const float vf = (float)v;
+    float z0 = 0.f, z1 = 0.f;
     for (int j = 0; j + 1 < s.B; j += 2) {
-        z0 += P[j] * __shfl_sync(0xffffffffu, v, s.base + j);
-        z1 += P[j + 1] * __shfl_sync(0xffffffffu, v, s.base + j + 1);
+        z0 = fmaf(P[j], __shfl_sync(0xffffffffu, vf, s.base + j), z0);
+        z1 = fmaf(P[j + 1], __shfl_sync(0xffffffffu, vf, s.base + j + 1), z1);
     }
-    if (s.B & 1) z0 += P[s.B - 1] * __shfl_sync(0xffffffffu, v, s.base + s.B - 1);
-    const double z = s.ev ? z0 + z1 : 0.0;
+    if (s.B & 1) z0 = fmaf(P[s.B - 1], __shfl_sync(0xffffffffu, vf, s.base + s.B - 1), z0);
+    double z = s.ev ? (double)(z0 + z1) : 0.0;
+    if (c.n_groups) {
+        const int S = c.n_groups;
+        const int gk = s.ev ? c.group[s.kk] : -1;
+        const double* Z = c.zgrp + (size_t)(s.ev ? s.e : 0) * S;
+        double corr = 0.0;
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g)
+            if (g < S) {
+                const double ng = seg_sum(gk == g ? z : 0.0, s.Bp);
+                if (s.ev) corr += Z[g] * ng;
+            }
+        if (con) z -= corr;
+    } else {
+        const double sz = seg_sum(z, s.Bp);            // all lanes: the shuffles span the warp
+        if (con) z -= y * sz * c.isigma[s.w];
+    }
     *rz = seg_sum(s.ev ? v * z : 0.0, s.Bp);
     return z;
 }
@@ -872,7 +892,7 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
                 if (con) pj -= Zv[g] * Yjg;
             }
             const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
-            if (s.ev) c.L[((size_t)w * B + kk) * B + j] = pj;
+            if (s.ev) c.Lf[((size_t)w * B + kk) * B + j] = (float)pj;
             pr += pj * Rj;
         }
     }
@@ -981,7 +1001,7 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
             const double yj = __shfl_sync(0xffffffffu, y, s.base + j);
             const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
             const double pj = con ? a[j] - y * yj * isg : a[j];
-            if (s.ev) c.L[((size_t)w * B + kk) * B + j] = pj;
+            if (s.ev) c.Lf[((size_t)w * B + kk) * B + j] = (float)pj;
             pr += pj * Rj;
         }
     }
