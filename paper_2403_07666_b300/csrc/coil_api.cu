@@ -665,6 +665,7 @@ struct Launch {
     int maxC = 0, maxNT = 0;
     bool seg = false, big = false;   // coils with blocks of <= kSegMax / more elements present
     bool need_q = false;             // the far apply must leave its result in q (no fused consumer)
+    bool dir = false;                // format 2: the apply forms the PCG direction first
 };
 
 Launch single_launch(coil_t* c) {
@@ -695,7 +696,7 @@ cudaError_t launch_far(const Launch& L, int which) {
     if (L.format == 1) return launch_toeplitz(L.d, L.n, L.maxC, L.maxNT, L.maxN, L.n_sm, L.s);
     if (L.format == 2) {
         for (const TcPlan* P : L.tc) {
-            cudaError_t e = launch_toeplitz_tc(*P, L.s, L.need_q || !P->fused);
+            cudaError_t e = launch_toeplitz_tc(*P, L.s, L.need_q || !P->fused, L.dir);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -784,17 +785,29 @@ coil_status step_prologue(coil_t* c, const Launch& L) {
 }
 
 // One projected-PCG iteration (kernels of converged coils return at once).
-coil_status step_iteration(coil_t* c, const Launch& L) {
-    TRY(gemv(c, L, 1));
+// One PCG iteration.  The tensor-core format forms the direction d = -z + beta d
+// inside the next iteration's input split (first: the direction k_init set).
+coil_status step_iteration(coil_t* c, const Launch& L, bool first) {
+    const bool fuse_dir = L.format == 2;
+    if (fuse_dir && !first) {
+        Launch Ld = L;
+        Ld.dir = true;
+        TRY(gemv(c, Ld, 1));
+    } else {
+        TRY(gemv(c, L, 1));
+    }
     // small-block coils reduce alpha and beta in the last CTA of their kernels
     c->launches += launch_near(L, 1);
     if (L.big) k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 2, 1);
     c->launches += launch_update(L);
     if (L.big) k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 3, 1);
-    unsigned eb = (unsigned)((L.maxN + 255) / 256);
-    if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
-    k_direction<<<dim3(eb, L.n), 256, 0, L.s>>>(L.d);
-    c->launches += 1 + 2 * (int)L.big;
+    if (!fuse_dir) {
+        unsigned eb = (unsigned)((L.maxN + 255) / 256);
+        if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
+        k_direction<<<dim3(eb, L.n), 256, 0, L.s>>>(L.d);
+        c->launches += 1;
+    }
+    c->launches += 2 * (int)L.big;
     CK(cudaGetLastError(), "iteration launch");
     return COIL_OK;
 }
@@ -821,7 +834,7 @@ coil_status run_step(coil_t* c) {
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
-        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
+        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L, total + i == 0));
         total += chunk;
         TRY(read_scalars(c));
         if (c->pinned->done) break;
@@ -1017,7 +1030,7 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         int total = 0;
         bool all_done = false;
         while (result == COIL_OK) {
-            for (int i = 0; i < chunk && result == COIL_OK; ++i) result = step_iteration(c, L);
+            for (int i = 0; i < chunk && result == COIL_OK; ++i) result = step_iteration(c, L, total + i == 0);
             total += chunk;
             k_gather_status<<<(n + 127) / 128, 128, 0, L.s>>>(dd, n, dstat);
             e = cudaMemcpyAsync(hstat.data(), dstat, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, L.s);
@@ -1483,7 +1496,7 @@ coil_status adjoint_solve(coil_t* c) {
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
-        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
+        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L, total + i == 0));
         total += chunk;
         TRY(read_scalars(c));
         if (c->pinned->done) break;

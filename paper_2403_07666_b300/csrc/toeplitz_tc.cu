@@ -554,13 +554,25 @@ __host__ __device__ inline int tc_exponent(double m) {
 }
 
 // p -> FP16 hi/lo in [c'/8][hi, lo][t][c' % 8] order; one block per turn row t,
-// scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.
+// scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.  dir: p is
+// the PCG's next search direction, formed here first, d = -z + beta d (FP64
+// into d, FP32 into the input copy), in place of a separate pass.
 __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
-                           int* __restrict__ pexp) {
+                           int* __restrict__ pexp, int dir) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
     const int t = blockIdx.x;
-    const float* row = c.pf + (size_t)t * sh.C;
+    float* row = c.pf + (size_t)t * sh.C;
+    if (dir) {
+        const double beta = c.sc->beta;
+        const size_t e0 = (size_t)t * sh.C;
+        for (int cc = threadIdx.x; cc < sh.C; cc += blockDim.x) {
+            const double d = -c.zv[e0 + cc] + beta * c.dv[e0 + cc];
+            c.dv[e0 + cc] = d;
+            row[cc] = (float)d;
+        }
+        __syncthreads();
+    }
     float m = 0.f;
     for (int cc = threadIdx.x; cc < sh.C; cc += blockDim.x) m = fmaxf(m, fabsf(row[cc]));
     const int x = tc_exponent((double)block_max_f(m));
@@ -819,9 +831,9 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
     return e;
 }
 
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q) {
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir) {
     const TcShape& sh = P.sh;
-    k_tc_split<<<sh.NT, 256, 0, s>>>(P.d, sh, P.p16, P.pexp);
+    k_tc_split<<<sh.NT, 256, 0, s>>>(P.d, sh, P.p16, P.pexp, dir ? 1 : 0);
     k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmAT, P.tmB, P.d, sh, P.work, P.pexp, P.part);
     if (write_q) {
         int rb = (sh.N + 255) / 256;

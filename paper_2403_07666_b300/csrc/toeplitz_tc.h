@@ -57,6 +57,7 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why);
 // M_far p for the coil of P (from pf): the split, the apply into the partial
 // tiles and, with write_q, their reduction into qv (otherwise the coil's
 // shared-warp near kernel sums the tiles).
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q);
+// dir: form the PCG direction d = -z + beta d in the input split first.
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir = false);
 
 }  // namespace cq
