@@ -588,7 +588,19 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
         const double* nb = c.near + (size_t)c.block_type[s.wv ? s.w : 0] * s.B * s.B;
         const int row = s.kk < s.B ? s.kk : 0;
         double acc = 0.0;
-        for (int j = 0; j < s.B; ++j) acc += nb[row * s.B + j] * __shfl_sync(0xffffffffu, pv, s.base + j);
+        if (s.B == kSegMax) {
+            // 16-element wires: the row as eight 16-byte loads, all in flight at once
+            double2 nr[kSegMax / 2];
+#pragma unroll
+            for (int q = 0; q < kSegMax / 2; ++q) nr[q] = reinterpret_cast<const double2*>(nb + row * kSegMax)[q];
+#pragma unroll
+            for (int q = 0; q < kSegMax / 2; ++q) {
+                acc += nr[q].x * __shfl_sync(0xffffffffu, pv, s.base + 2 * q);
+                acc += nr[q].y * __shfl_sync(0xffffffffu, pv, s.base + 2 * q + 1);
+            }
+        } else {
+            for (int j = 0; j < s.B; ++j) acc += nb[row * s.B + j] * __shfl_sync(0xffffffffu, pv, s.base + j);
+        }
         double dot = 0.0;
         if (s.ev) {
             acc += c.dt * c.G[s.e] * pv;
@@ -650,11 +662,25 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
     const float* P = c.Lf + ((size_t)(s.wv ? s.w : 0) * s.B + (s.kk < s.B ? s.kk : 0)) * s.B;
     const float vf = (float)v;
     float z0 = 0.f, z1 = 0.f;
-    for (int j = 0; j + 1 < s.B; j += 2) {
-        z0 = fmaf(P[j], __shfl_sync(0xffffffffu, vf, s.base + j), z0);
-        z1 = fmaf(P[j + 1], __shfl_sync(0xffffffffu, vf, s.base + j + 1), z1);
+    if (s.B == kSegMax) {
+        // 16-element wires: the row as four 16-byte loads, all in flight at once
+        float4 pr[kSegMax / 4];
+#pragma unroll
+        for (int q = 0; q < kSegMax / 4; ++q) pr[q] = reinterpret_cast<const float4*>(P)[q];
+#pragma unroll
+        for (int q = 0; q < kSegMax / 4; ++q) {
+            z0 = fmaf(pr[q].x, __shfl_sync(0xffffffffu, vf, s.base + 4 * q), z0);
+            z1 = fmaf(pr[q].y, __shfl_sync(0xffffffffu, vf, s.base + 4 * q + 1), z1);
+            z0 = fmaf(pr[q].z, __shfl_sync(0xffffffffu, vf, s.base + 4 * q + 2), z0);
+            z1 = fmaf(pr[q].w, __shfl_sync(0xffffffffu, vf, s.base + 4 * q + 3), z1);
+        }
+    } else {
+        for (int j = 0; j + 1 < s.B; j += 2) {
+            z0 = fmaf(P[j], __shfl_sync(0xffffffffu, vf, s.base + j), z0);
+            z1 = fmaf(P[j + 1], __shfl_sync(0xffffffffu, vf, s.base + j + 1), z1);
+        }
+        if (s.B & 1) z0 = fmaf(P[s.B - 1], __shfl_sync(0xffffffffu, vf, s.base + s.B - 1), z0);
     }
-    if (s.B & 1) z0 = fmaf(P[s.B - 1], __shfl_sync(0xffffffffu, vf, s.base + s.B - 1), z0);
     double z = s.ev ? (double)(z0 + z1) : 0.0;
     if (c.n_groups) {
         const int S = c.n_groups;
