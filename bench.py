@@ -351,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API: host buffers, copies inside the region
     import torch as _t
     bufs = [_t.empty(N, dtype=_t.float64, pin_memory=True).numpy() for _ in range(4)]
-    Ke = max(1, min(args.steps, 5))
+    Ke = max(1, min(args.steps, 20))
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(Ke):
@@ -623,7 +623,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 50 for the GPU arm, 10 oracle samples for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="real", choices=["real", "mid", "small", "prof"])
@@ -643,6 +644,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else 50
     if args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
