@@ -40,6 +40,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2403_07666_b300 import workloads as wl  # noqa: E402
+from paper_2403_07666_b300.replicas import job_throughput, shard_coils  # noqa: E402
 
 METRIC = "element-steps/s (EM+thermal)"
 UNIT = "element-steps/s"
@@ -336,11 +337,8 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         secs = timed_steps(coil, drive, args.steps, stream, torch)
     inf = coil.info()
-    if dist:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
-    value = world * N * args.steps / secs
+    # replicas: the units of all ranks over the slowest rank's time
+    value, secs = job_throughput(secs, N * args.steps, dist, "cuda")
     op_launches = int(inf.operator_launches)
     gemv_ms = inf.operator_ms / max(op_launches, 1)
     op_bytes = int(info.operator_bytes)
@@ -359,11 +357,8 @@ def run_ours(args, rank, world, local_rank):
         coil.read_into(drive, *bufs)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * N * Ke / e2e_s, "unit": UNIT,
+    e2e_value, _ = job_throughput(e2e_s, N * Ke, dist, "cuda")
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(inf.descriptor_bytes) + 48,
            "d2h_bytes_per_step": 4 * N * 8 + 8}
 
@@ -374,10 +369,7 @@ def run_ours(args, rank, world, local_rank):
                                  stream=stream.cuda_stream)
         c64.step(1, drive)
         s64 = timed_steps(c64, drive, args.fp64_steps, stream, torch)
-        if dist:
-            t = torch.tensor([s64], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            s64 = float(t.item())
+        v64, s64 = job_throughput(s64, N * args.fp64_steps, dist, "cuda")
         # the mixed form over the same steps from the same start: moment and current error
         n64 = 1 + args.fp64_steps
         cm = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
@@ -386,7 +378,7 @@ def run_ours(args, rank, world, local_rank):
         m64, mm = c64.diag(0, n64)[:, 3], cm.diag(0, n64)[:, 3]
         I64, Im = c64.currents(), cm.currents()
         cm.close()
-        fp64 = {"value": world * N * args.fp64_steps / s64, "ms_per_step": 1e3 * s64 / args.fp64_steps,
+        fp64 = {"value": v64, "ms_per_step": 1e3 * s64 / args.fp64_steps,
                 "steps": args.fp64_steps,
                 "mixed_moment_rel_err": float(np.max(np.abs(mm - m64)) / max(np.max(np.abs(m64)), 1e-300)),
                 "mixed_current_rel_err": float(np.linalg.norm(Im - I64) / max(np.linalg.norm(I64), 1e-300)),
@@ -395,6 +387,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         coil.close()
 
+    batched = batch_leg(args, local_rank, stream, torch, rank, world, dist) if args.batch_steps > 0 else None
     if rank != 0:
         return None
     line = {
@@ -435,8 +428,8 @@ def run_ours(args, rank, world, local_rank):
         line["subelements"]["over_one_group"] = line["subelements"]["value"] / value
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, local_rank, stream, torch)
-    if args.batch_steps > 0:
-        line["batched"] = batch_leg(args, local_rank, stream, torch)
+    if batched is not None:
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     return line
@@ -568,10 +561,12 @@ def adjoint_leg(args, local_rank, stream, torch):
             "note": "adjoint_s includes the checkpointed forward pass and the segment recomputation"}
 
 
-def batch_leg(args, local_rank, stream, torch):
-    """64 coils of uneven size (2k-41k elements) stepped together."""
+def batch_leg(args, local_rank, stream, torch, rank=0, world=1, dist=None):
+    """64 coils of uneven size (2k-41k elements) stepped together; with several
+    ranks each steps its share of the coils (dealt by element count)."""
     from paper_2403_07666_b300.coil import Coil, batch_step
-    ws = wl.batch_coils()
+    ws_all = wl.batch_coils()
+    ws = [ws_all[i] for i in shard_coils([w.n_elem for w in ws_all], world, rank)]
     fmt = args.batch_format if args.precision == "fp32" else "dense"
     coils = [Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
                                 stream=stream.cuda_stream, format=fmt) for w in ws]
@@ -587,14 +582,16 @@ def batch_leg(args, local_rank, stream, torch):
     end.record(stream)
     torch.cuda.synchronize()
     secs = start.elapsed_time(end) / 1e3
-    total_elem = sum(c.N for c in coils)
+    local_elem = sum(c.N for c in coils)
     launches = int(coils[0].info().kernel_launches)
     op_bytes = sum(int(c.info().operator_bytes) for c in coils)
     for c in coils:
         c.close()
-    return {"workload": f"batch of {len(ws)} coils", "n_elem_total": total_elem,
-            "n_elem_min": min(w.n_elem for w in ws), "n_elem_max": max(w.n_elem for w in ws),
-            "steps": args.batch_steps, "value": total_elem * args.batch_steps / secs, "unit": UNIT,
+    value, secs = job_throughput(secs, local_elem * args.batch_steps, dist, "cuda")
+    total_elem = sum(w.n_elem for w in ws_all)
+    return {"workload": f"batch of {len(ws_all)} coils", "n_elem_total": total_elem,
+            "n_elem_min": min(w.n_elem for w in ws_all), "n_elem_max": max(w.n_elem for w in ws_all),
+            "ranks": world, "steps": args.batch_steps, "value": value, "unit": UNIT,
             "ms_per_step": 1e3 * secs / args.batch_steps, "operator_format": fmt, "operator_bytes": op_bytes,
             "gpu_launches": launches}
 
