@@ -78,12 +78,13 @@ enum { COIL_PREC_FP64 = 0, COIL_PREC_FP32 = 1, COIL_PREC_BF16 = 2 };
  * on the turn alone (its own block of M + dt G, the resistive voltage
  * 2 pi r rho J_I of the transport part, the transport constraint), then the
  * coupled step with the net current rate of every subelement fixed to its
- * J_I share; J_I is kept as state.  Free loops are unaffected.  Limits: at
- * most COIL_MAX_GROUPS subelements, every group non-empty, blocks of at most
- * 16 elements; coil_adjoint is unavailable with subelements.
+ * J_I share; J_I is kept as state.  Free loops are unaffected.  Limits:
+ * every group non-empty, at most 6 subelements for blocks of up to 16
+ * elements and COIL_MAX_GROUPS for larger blocks; coil_adjoint is unavailable
+ * with subelements.
  * n_groups <= 1 (group may be NULL): one group, the plain turn constraint.
  */
-#define COIL_MAX_GROUPS 6
+#define COIL_MAX_GROUPS 16
 typedef struct {
     int kind;
     int n_layers, n_turns, n_sub;

@@ -248,8 +248,9 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
     if (g->n_groups > 1) {
         static_assert(COIL_MAX_GROUPS == kGroupMax, "subelement limit of the ABI and the kernels");
         const int B = g->kind == COIL_GEOM_SOLENOID ? g->n_sub * g->n_sub : g->block;
-        if (!g->group || g->n_groups > COIL_MAX_GROUPS || B > kSegMax)
-            return fail(c, COIL_ERR_INVALID, "subelements need a group array, at most 6 groups and blocks of at most 16 elements");
+        if (!g->group || g->n_groups > (B <= kSegMax ? kGroupMaxSeg : COIL_MAX_GROUPS))
+            return fail(c, COIL_ERR_INVALID,
+                        "subelements need a group array and at most 6 groups (blocks of up to 16 elements) or 16");
         std::vector<int> cnt(g->n_groups, 0);
         for (int k = 0; k < B; ++k) {
             if (g->group[k] < 0 || g->group[k] >= g->n_groups)
@@ -648,7 +649,10 @@ coil_status read_scalars(coil_t* c) {
     return COIL_OK;
 }
 
-size_t block_smem(const CoilDev& h) { return ((size_t)h.B * h.B + 2 * (size_t)h.B) * sizeof(double); }
+size_t block_smem(const CoilDev& h) {
+    const size_t S = h.n_groups;     // subelement scratch of the factor kernel
+    return ((size_t)h.B * h.B + 2 * (size_t)h.B + (size_t)h.B * S + S * S) * sizeof(double);
+}
 
 // Launch geometry of one step for one coil or a batch (grid row y = coil).
 struct Launch {

@@ -15,7 +15,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kMu0 = 4.0e-7 * kPi;
 constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one warp
 constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B rounded up to a power of 2)
-constexpr int kGroupMax = 6;         // subelements per turn (blocks of at most kSegMax elements)
+constexpr int kGroupMax = 16;        // subelements per turn
+constexpr int kGroupMaxSeg = 6;      // subelements per turn of blocks of at most kSegMax elements
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
 constexpr int kTcTileRows = 128;     // channels per tile of the tensor-core Toeplitz apply
 

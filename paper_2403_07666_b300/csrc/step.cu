@@ -99,6 +99,7 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
         double q = E * J;
         c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
         c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
+        if (c.n_groups) c.xI[e] = 2.0 * kPi * r * rho * c.Itr[e] / a;   // resistive voltage of J_I
         if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
         sumI += I;
         pj += q * 2.0 * kPi * r * a;
@@ -175,15 +176,151 @@ __device__ void project_precond(const CoilDev& c, int w, const double* L, const 
                                 int lane) {
     int B = c.B;
     chol_solve_warp(L, v, B, lane);
-    if (c.constrained[w]) {
-        double s = warp_block_sum(v, B, lane);
-        double f = s * c.isigma[w];
-        for (int k = lane; k < B; k += 32) v[k] -= y[k] * f;
+    if (!c.constrained[w]) return;
+    if (c.n_groups) {
+        // subelements: remove Y S^-1 Q^T A_w^-1 r (the part that changes a
+        // subelement's net current), with the stored rows Z = Y S^-1
+        const int S = c.n_groups;
+        double n[kGroupMax];
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) {
+            double a = 0.0;
+            if (g < S)
+                for (int k = lane; k < B; k += 32) a += c.group[k] == g ? v[k] : 0.0;
+            n[g] = g < S ? warp_sum(a) : 0.0;
+        }
+        for (int k = lane; k < B; k += 32) {
+            const double* Z = c.zgrp + ((size_t)w * B + k) * S;
+            double corr = 0.0;
+            for (int g = 0; g < S; ++g) corr += Z[g] * n[g];
+            v[k] -= corr;
+        }
         __syncwarp();
+        return;
     }
+    double s = warp_block_sum(v, B, lane);
+    double f = s * c.isigma[w];
+    for (int k = lane; k < B; k += 32) v[k] -= y[k] * f;
+    __syncwarp();
 }
 
-// One warp per CTA, one CTA per block.  Shared: A (B*B), v (B), y (B).
+// Subelement part of k_factor (blocks of more than kSegMax elements), from the
+// Cholesky factor L of A_w in shared memory, y = A_w^-1 1 and sigma:
+//  * the transport part on the turn alone, x_I = y u - A_w^-1 R_I,
+//    u = (c_w + 1^T A_w^-1 R_I) / sigma (R_I in xI on entry, x_I replaces it),
+//    and its subelement nets d = Q^T x_I;
+//  * Y = A_w^-1 Q (one solve per subelement), S_m = Q^T Y, S_m^-1 by
+//    Gauss-Jordan with a row per lane, and the stored rows Z = Y S_m^-1;
+//  * R^T P_w R + d^T S_m^-1 d (P_w = A_w^-1 - Z Y^T on constrained turns), and
+//    the warm start moved onto Q^T x = d.
+// ws: shared scratch of B S + S S doubles after v and y.
+__device__ void factor_groups_big(const CoilDev& c, int w, const double* L, const double* y, double* v, double* ws,
+                                  double sig, int lane) {
+    const int B = c.B, S = c.n_groups;
+    const int con = c.constrained[w];
+    double* Ysm = ws;                 // [B][S]
+    double* Sm = ws + B * S;          // [S][S], inverted in place
+    // transport part
+    for (int k = lane; k < B; k += 32) v[k] = c.xI[w * B + k];
+    __syncwarp();
+    chol_solve_warp(L, v, B, lane);
+    const double uI = (c.cw[w] + warp_block_sum(v, B, lane)) / sig;
+    double d[kGroupMax];
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) d[g] = 0.0;
+    for (int k = lane; k < B; k += 32) {
+        const double xI = con ? y[k] * uI - v[k] : 0.0;
+        c.xI[w * B + k] = xI;
+        const int gk = c.group[k];
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g)
+            if (g == gk) d[g] += xI;
+    }
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) d[g] = g < S ? warp_sum(d[g]) : 0.0;
+    __syncwarp();
+    // Y = A_w^-1 Q
+    for (int g = 0; g < S; ++g) {
+        for (int k = lane; k < B; k += 32) v[k] = c.group[k] == g ? 1.0 : 0.0;
+        __syncwarp();
+        chol_solve_warp(L, v, B, lane);
+        for (int k = lane; k < B; k += 32) Ysm[k * S + g] = v[k];
+        __syncwarp();
+    }
+    // S_m = Q^T Y and its inverse
+    for (int p = lane; p < S * S; p += 32) {
+        const int g = p / S, h = p - g * S;
+        double a = 0.0;
+        for (int k = 0; k < B; ++k)
+            if (c.group[k] == g) a += Ysm[k * S + h];
+        Sm[p] = a;
+    }
+    __syncwarp();
+    int bad = 0;
+    for (int kp = 0; kp < S; ++kp) {
+        double piv = Sm[kp * S + kp];
+        if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
+        const double ip = 1.0 / piv;
+        const double f = lane < S ? Sm[lane * S + kp] : 0.0;
+        __syncwarp();
+        if (lane == kp)
+            for (int j = 0; j < S; ++j) Sm[kp * S + j] = j == kp ? ip : Sm[kp * S + j] * ip;
+        __syncwarp();
+        if (lane < S && lane != kp)
+            for (int j = 0; j < S; ++j) Sm[lane * S + j] = j == kp ? -f * ip : Sm[lane * S + j] - f * Sm[kp * S + j];
+        __syncwarp();
+    }
+    if (bad && con && lane == 0) atomicExch(&c.sc->nonpd, 1);
+    // Z = Y S_m^-1
+    for (int k = lane; k < B; k += 32) {
+        double* Z = c.zgrp + ((size_t)w * B + k) * S;
+        for (int h = 0; h < S; ++h) {
+            double a = 0.0;
+            for (int g = 0; g < S; ++g) a += Ysm[k * S + g] * Sm[g * S + h];
+            Z[h] = a;
+        }
+    }
+    __syncwarp();
+    // R^T P_w R: v = R, A_w^-1 v, then the subelement projection
+    for (int k = lane; k < B; k += 32) v[k] = c.R[w * B + k];
+    __syncwarp();
+    project_precond(c, w, L, y, v, lane);
+    double rn = 0.0;
+    for (int k = lane; k < B; k += 32) rn += c.R[w * B + k] * v[k];
+    rn = warp_sum(rn);
+    double dSd = 0.0;
+    for (int g = 0; g < S; ++g)
+        for (int h = 0; h < S; ++h) dSd += d[g] * Sm[g * S + h] * d[h];
+    // warm start, then moved onto Q^T x = d
+    const bool ext = extrapolate(c);
+    double gap[kGroupMax];
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) gap[g] = 0.0;
+    for (int k = lane; k < B; k += 32) {
+        const double x0 = warm_start(c, w * B + k, ext);
+        c.x[w * B + k] = x0;
+        const int gk = c.group[k];
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g)
+            if (g == gk) gap[g] += x0;
+    }
+#pragma unroll
+    for (int g = 0; g < kGroupMax; ++g) gap[g] = g < S ? d[g] - warp_sum(gap[g]) : 0.0;
+    for (int k = lane; k < B; k += 32) {
+        const int e = w * B + k;
+        double xe = c.x[e];
+        if (con) {
+            const double* Z = c.zgrp + (size_t)e * S;
+            for (int g = 0; g < S; ++g) xe += Z[g] * gap[g];
+        }
+        c.x[e] = xe;
+        c.pf[e] = (float)xe;
+    }
+    if (lane == 0) c.parts[3 * (size_t)c.W + w] = rn + (con ? dSd : 0.0);
+}
+
+// One warp per CTA, one CTA per block.  Shared: A (B*B), v (B), y (B), and
+// with subelements the scratch of factor_groups_big.
 __global__ void k_factor(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
@@ -228,6 +365,10 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
         c.isigma[w] = 1.0 / sig;
     }
     __syncwarp();
+    if (c.n_groups) {
+        factor_groups_big(c, w, A, y, v, y + B, sig, lane);
+        return;
+    }
     // preconditioned norm^2 of the right-hand side: R^T Pproj(R) + c_w^2 / sigma
     for (int k = lane; k < B; k += 32) v[k] = c.R[w * B + k];
     __syncwarp();
@@ -295,8 +436,41 @@ __global__ void k_near(const CoilDev* __restrict__ cds, int which) {
 // does not drown in the rounding of the large loop-voltage term
 // (Gould, Hribar and Nocedal's residual update for constraint preconditioners).
 __device__ void project_residual(const CoilDev& c, int w, const double* y, double* v, int lane, bool first) {
-    if (!c.constrained[w]) return;
     int B = c.B;
+    if (c.n_groups) {
+        // subelements: remove Q u, u = Z^T r the subelement voltage estimates,
+        // accumulated in ugrp
+        const int S = c.n_groups;
+        const int con = c.constrained[w];
+        double u[kGroupMax];
+#pragma unroll
+        for (int g = 0; g < kGroupMax; ++g) {
+            double a = 0.0;
+            if (g < S)
+                for (int k = lane; k < B; k += 32) a += c.zgrp[((size_t)w * B + k) * S + g] * v[k];
+            u[g] = g < S ? warp_sum(a) : 0.0;
+        }
+        if (con) {
+            for (int k = lane; k < B; k += 32) {
+                const int gk = c.group[k];
+                double ug = 0.0;
+#pragma unroll
+                for (int g = 0; g < kGroupMax; ++g)
+                    if (g == gk) ug = u[g];
+                v[k] -= ug;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            for (int g = 0; g < S; ++g) {
+                double* U = c.ugrp + (size_t)w * S + g;
+                if (first) *U = con ? u[g] : 0.0;
+                else if (con) *U += u[g];
+            }
+        }
+        return;
+    }
+    if (!c.constrained[w]) return;
     double s = 0.0;
     for (int k = lane; k < B; k += 32) s += y[k] * v[k];
     s = warp_sum(s);
@@ -630,7 +804,7 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
         const double* Z = c.zgrp + (size_t)(s.ev ? s.e : 0) * S;
         double mine = 0.0;
 #pragma unroll
-        for (int g = 0; g < kGroupMax; ++g) {
+        for (int g = 0; g < kGroupMaxSeg; ++g) {
             if (g < S) {
                 const double vg = seg_sum(s.ev ? Z[g] * v : 0.0, s.Bp);
                 if (g == gk) mine = vg;
@@ -688,7 +862,7 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
         const double* Z = c.zgrp + (size_t)(s.ev ? s.e : 0) * S;
         double corr = 0.0;
 #pragma unroll
-        for (int g = 0; g < kGroupMax; ++g)
+        for (int g = 0; g < kGroupMaxSeg; ++g)
             if (g < S) {
                 const double ng = seg_sum(gk == g ? z : 0.0, s.Bp);
                 if (s.ev) corr += Z[g] * ng;
@@ -828,7 +1002,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
 //    u = (c_w + 1^T A_w^-1 R_I) / sigma (R_I, the resistive voltage of J_I,
 //    is in xI on entry; x_I replaces it) and its subelement nets d = Q^T x_I;
 //  * Y = A_w^-1 Q, S_m = Q^T Y (Q: element-to-subelement incidence), S_m^-1
-//    by Gauss-Jordan in every lane (at most kGroupMax^2 registers), the rows
+//    by Gauss-Jordan in every lane (at most kGroupMaxSeg^2 registers), the rows
 //    Z = Y S_m^-1 (stored) and P_w = A_w^-1 - Z Y^T (stored, constrained turns);
 //  * R^T P_w R + d^T S_m^-1 d, and the warm start moved onto Q^T x = d.
 __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, const double (&a)[kSegMax], double y,
@@ -844,27 +1018,27 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
     const double uI = (cw + seg_sum(s.ev ? t : 0.0, s.Bp)) * isg;
     const double xI = (con && s.ev) ? y * uI - t : 0.0;
     if (s.ev) c.xI[e] = xI;
-    double Yv[kGroupMax];
+    double Yv[kGroupMaxSeg];
 #pragma unroll
-    for (int g = 0; g < kGroupMax; ++g) Yv[g] = 0.0;
+    for (int g = 0; g < kGroupMaxSeg; ++g) Yv[g] = 0.0;
 #pragma unroll
     for (int j = 0; j < kSegMax; ++j) {
         if (j < B) {
             const int gj = c.group[j];
 #pragma unroll
-            for (int g = 0; g < kGroupMax; ++g)
+            for (int g = 0; g < kGroupMaxSeg; ++g)
                 if (g == gj) Yv[g] += a[j];
         }
     }
     if (!s.ev) {
 #pragma unroll
-        for (int g = 0; g < kGroupMax; ++g) Yv[g] = 0.0;
+        for (int g = 0; g < kGroupMaxSeg; ++g) Yv[g] = 0.0;
     }
-    double Sm[kGroupMax][kGroupMax];
+    double Sm[kGroupMaxSeg][kGroupMaxSeg];
 #pragma unroll
-    for (int g = 0; g < kGroupMax; ++g) {
+    for (int g = 0; g < kGroupMaxSeg; ++g) {
 #pragma unroll
-        for (int h = 0; h < kGroupMax; ++h) {
+        for (int h = 0; h < kGroupMaxSeg; ++h) {
             if (h < g) continue;
             double v = (g == h) ? 1.0 : 0.0;             // identity on the padding
             if (g < S && h < S) v = seg_sum(gk == g ? Yv[h] : 0.0, s.Bp);
@@ -874,35 +1048,35 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
     }
     int bad = 0;
 #pragma unroll
-    for (int k = 0; k < kGroupMax; ++k) {
+    for (int k = 0; k < kGroupMaxSeg; ++k) {
         double piv = Sm[k][k];
         if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
         const double ip = 1.0 / piv;
         Sm[k][k] = 1.0;
 #pragma unroll
-        for (int j = 0; j < kGroupMax; ++j) Sm[k][j] *= ip;
+        for (int j = 0; j < kGroupMaxSeg; ++j) Sm[k][j] *= ip;
 #pragma unroll
-        for (int i = 0; i < kGroupMax; ++i) {
+        for (int i = 0; i < kGroupMaxSeg; ++i) {
             if (i == k) continue;
             const double f = Sm[i][k];
             Sm[i][k] = 0.0;
 #pragma unroll
-            for (int j = 0; j < kGroupMax; ++j) Sm[i][j] -= f * Sm[k][j];
+            for (int j = 0; j < kGroupMaxSeg; ++j) Sm[i][j] -= f * Sm[k][j];
         }
     }
     if (bad && con && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
-    double Zv[kGroupMax];
+    double Zv[kGroupMaxSeg];
 #pragma unroll
-    for (int h = 0; h < kGroupMax; ++h) {
+    for (int h = 0; h < kGroupMaxSeg; ++h) {
         double z = 0.0;
 #pragma unroll
-        for (int g = 0; g < kGroupMax; ++g) z += Yv[g] * Sm[g][h];
+        for (int g = 0; g < kGroupMaxSeg; ++g) z += Yv[g] * Sm[g][h];
         Zv[h] = z;
     }
     if (s.ev) {
         double* Zo = c.zgrp + (size_t)e * S;
 #pragma unroll
-        for (int g = 0; g < kGroupMax; ++g)
+        for (int g = 0; g < kGroupMaxSeg; ++g)
             if (g < S) Zo[g] = Zv[g];
     }
     // P_w row kk, stored; R^T P_w R
@@ -913,7 +1087,7 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
         if (j < B) {
             double pj = a[j];
 #pragma unroll
-            for (int g = 0; g < kGroupMax; ++g) {
+            for (int g = 0; g < kGroupMaxSeg; ++g) {
                 const double Yjg = __shfl_sync(0xffffffffu, Yv[g], s.base + j);
                 if (con) pj -= Zv[g] * Yjg;
             }
@@ -924,18 +1098,18 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
     }
     double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
     // subelement shares of J_I and the warm start moved onto them
-    double d[kGroupMax], gap[kGroupMax];
+    double d[kGroupMaxSeg], gap[kGroupMaxSeg];
 #pragma unroll
-    for (int g = 0; g < kGroupMax; ++g) {
+    for (int g = 0; g < kGroupMaxSeg; ++g) {
         d[g] = g < S ? seg_sum(gk == g ? xI : 0.0, s.Bp) : 0.0;
         gap[g] = g < S ? d[g] - seg_sum(gk == g ? xe0 : 0.0, s.Bp) : 0.0;
     }
     double dSd = 0.0, corr = 0.0;
 #pragma unroll
-    for (int g = 0; g < kGroupMax; ++g) {
+    for (int g = 0; g < kGroupMaxSeg; ++g) {
         double sd = 0.0;
 #pragma unroll
-        for (int h = 0; h < kGroupMax; ++h) sd += Sm[g][h] * d[h];
+        for (int h = 0; h < kGroupMaxSeg; ++h) sd += Sm[g][h] * d[h];
         dSd += d[g] * sd;
         corr += Zv[g] * gap[g];
     }

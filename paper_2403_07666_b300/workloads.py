@@ -65,18 +65,27 @@ def filament_mask(n_layers, n_turns, n_sub):
     return ((np.abs(xa) < half) & (np.abs(xb) < half)).astype(np.int32)
 
 
-def subelement_groups(n_sub):
+def subelement_groups(n_sub, tile=None):
     """Subelement id of every element position of a wire (position b n + a):
-    the Cu elements (outside the filament zone) form one group, the filament
-    zone splits into its four quadrants about the wire centre; ids renumbered
-    from 0 in order of first appearance of (Cu, quadrant 0..3)."""
+    the Cu elements (outside the filament zone) form one group; the filament
+    zone splits into its four quadrants about the wire centre, or with `tile`
+    into tile x tile squares of filament elements counted from the zone's
+    corner; ids renumbered from 0 in order of (Cu, subelement index)."""
     n = n_sub
     fil = filament_mask(1, 1, n)
+    ks = [k for k in range(n * n) if fil[k]]
+    a0 = min(k % n for k in ks) if ks else 0
+    b0 = min(k // n for k in ks) if ks else 0
     raw = []
     for b in range(n):
         for a in range(n):
             k = b * n + a
-            raw.append(0 if not fil[k] else 1 + int(2 * a >= n) + 2 * int(2 * b >= n))
+            if not fil[k]:
+                raw.append(0)
+            elif tile is None:
+                raw.append(1 + int(2 * a >= n) + 2 * int(2 * b >= n))
+            else:
+                raw.append(1 + (a - a0) // tile + n * ((b - b0) // tile))
     ids = {v: i for i, v in enumerate(sorted(set(raw)))}
     return np.array([ids[v] for v in raw], dtype=np.int32)
 

@@ -27,19 +27,22 @@ def _coil(w, **kw):
     return _C.from_workload(w, **kw)
 
 
-def _grouped(seed, L, T, n, **kw):
+def _grouped(seed, L, T, n, tile=None, **kw):
     kw.setdefault("material", dict(wl.MATERIAL, Jc0=2e7))
     kw.setdefault("ramp_rate", 5e5)
     w = wl.random_coil(seed, L, T, n, **kw)
-    w.geometry["groups"] = wl.subelement_groups(n)
+    w.geometry["groups"] = wl.subelement_groups(n, tile)
     return w
 
 
-@pytest.mark.parametrize("seed,L,T,n", [(71, 2, 3, 4), (72, 3, 4, 3), (73, 3, 3, 2)])
-def test_subelement_steps_match_oracle(seed, L, T, n):
+@pytest.mark.parametrize("seed,L,T,n,tile", [(71, 2, 3, 4, None), (72, 3, 4, 3, None), (73, 3, 3, 2, None),
+                                             (74, 2, 3, 5, None), (75, 2, 3, 8, 2)])
+def test_subelement_steps_match_oracle(seed, L, T, n, tile):
     """Cu ring + filament quadrants (n = 4: 5 groups of a 16-element turn;
-    n = 3: 4 groups of 9, a padded segment; n = 2: single-element groups)."""
-    w = _grouped(seed, L, T, n)
+    n = 3: 4 groups of 9, a padded segment; n = 2: single-element groups;
+    n = 5: one warp per turn) and Cu ring + nine 2 x 2 subelements of a
+    64-element turn (n = 8)."""
+    w = _grouped(seed, L, T, n, tile)
     orc = oracle_of(w)
     with _coil(w, rtol=1e-11) as c:
         for k in range(50):
@@ -62,18 +65,19 @@ def test_subelement_steps_match_oracle(seed, L, T, n):
     assert np.max(np.abs(I.reshape(-1, n * n).sum(axis=1) - It)) <= 1e-9 * It
 
 
-@pytest.mark.parametrize("fmt,prec", [("dense", "fp64"), ("toeplitz_tc", "fp32")])
-def test_field_ramp_keeps_every_subelement_net_zero(fmt, prec):
+@pytest.mark.parametrize("fmt,prec,n,tile", [("dense", "fp64", 4, None), ("toeplitz_tc", "fp32", 4, None),
+                                             ("dense", "fp64", 8, 2)])
+def test_field_ramp_keeps_every_subelement_net_zero(fmt, prec, n, tile):
     """No transport current, a ramping applied field: the nets of all
     subelements stay zero (up to rounding) in any operator precision."""
-    w = _grouped(74, 3, 4, 4, ramp_rate=0.0, I_max=0.0, dt=1e-4, Ba_rate=40.0, Ba_max=0.05,
+    w = _grouped(74, 3, 4, n, tile, ramp_rate=0.0, I_max=0.0, dt=1e-4, Ba_rate=40.0, Ba_max=0.05,
                  Ba_waveform=1, material=dict(wl.MATERIAL, Jc0=2e8))
     grp = w.geometry["groups"]
     peak = net = 0.0
     with _coil(w, precision=prec, format=fmt) as c:
         for _ in range(15):
             c.step(1, w.drive)
-            I = c.currents().reshape(-1, 16)
+            I = c.currents().reshape(-1, n * n)
             peak = max(peak, np.max(np.abs(I)))
             net = max(net, max(np.max(np.abs(I[:, grp == g].sum(axis=1))) for g in range(grp.max() + 1)))
     assert peak > 0
@@ -99,11 +103,11 @@ def test_subelement_refusals():
             c.adjoint(3, w.drive, np.ones(3))
         assert ei.value.status == ERR_INVALID
     w5 = wl.random_coil(77, 2, 3, 5)
-    w5.geometry["groups"] = np.arange(25) % 2          # 25-element turns: not supported
+    w5.geometry["groups"] = np.arange(25) % 17         # more than 16 subelements
     with pytest.raises(CoilError):
         _coil(w5)
     w7 = wl.random_coil(78, 2, 3, 4)
-    w7.geometry["groups"] = np.arange(16) % 7          # more than 6 subelements
+    w7.geometry["groups"] = np.arange(16) % 7          # more than 6 subelements of a 16-element turn
     with pytest.raises(CoilError):
         _coil(w7)
     we = wl.random_coil(79, 2, 3, 4)
