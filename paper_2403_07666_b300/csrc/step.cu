@@ -1121,6 +1121,97 @@ __device__ __forceinline__ void factor_groups(const CoilDev& c, const Seg& s, co
     if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? dSd : 0.0);
 }
 
+__device__ __forceinline__ float inv_pivot(float p) { return 1.0f / p; }
+__device__ __forceinline__ double inv_pivot(double p) { return rcp_nr(p); }
+
+// Body of k_factor_seg in the precision T of the inverse.  T = float: the
+// inverse only serves the preconditioner P_w (stored in FP32 anyway) and y for
+// the constraint projections, which stay exact for any y because sigma is
+// summed in FP64 from the y that are stored; the PCG's residual stays FP64,
+// so the solution does not depend on it.  T = double: the subelement path.
+template <typename T>
+__device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
+    const int B = s.B, kk = s.kk, w = s.w, e = s.e;
+    T a[kSegMax];
+    const double* nb = c.near + (size_t)c.block_type[s.wv ? w : 0] * B * B;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j)
+        a[j] = (s.wv && kk < B && j < B) ? (T)nb[kk * B + j] : (T)(j == kk ? 1 : 0);
+    if (s.ev) {
+        const T g = (T)(c.dt * c.G[e]);
+#pragma unroll
+        for (int j = 0; j < kSegMax; ++j)
+            if (j == kk) a[j] += g;
+    }
+    int bad = 0;
+#pragma unroll
+    for (int k = 0; k < kSegMax; ++k) {
+        if (k < B) {
+            T piv = __shfl_sync(0xffffffffu, a[k], s.base + k);
+            if (!(piv > (T)0)) { bad = 1; piv = (T)1; }
+            const T ip = inv_pivot(piv);
+            if (kk == k) {
+#pragma unroll
+                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
+            }
+            T rk[kSegMax];                              // scaled pivot row
+#pragma unroll
+            for (int j = 0; j < kSegMax; ++j) rk[j] = __shfl_sync(0xffffffffu, a[j], s.base + k);
+            if (kk != k) {
+                const T f = a[k];
+#pragma unroll
+                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * rk[j];
+            }
+        }
+    }
+    if (bad && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
+    // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
+    T yt = 0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j)
+        if (j < B) yt += a[j];
+    const double y = s.ev ? (double)yt : 0.0;
+    const double sig = seg_sum(y, s.Bp);
+    const int con = s.wv ? c.constrained[w] : 0;
+    const double isg = 1.0 / sig;
+    if (s.ev) c.y1[e] = y;
+    if (kk == 0 && s.wv) {
+        c.sigma[w] = sig;
+        c.isigma[w] = isg;
+    }
+    const double x0 = s.ev ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if (c.n_groups) {
+            factor_groups(c, s, a, y, isg, con, x0);
+            return;
+        }
+    }
+    // P_w row kk, stored; R^T P_w R
+    const double R = s.ev ? c.R[e] : 0.0;
+    double pr = 0.0;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j) {
+        if (j < B) {
+            const T yj = __shfl_sync(0xffffffffu, (T)y, s.base + j);
+            const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
+            const double pj = con ? (double)(a[j] - (T)(y * isg) * yj) : (double)a[j];
+            if (s.ev) c.Lf[((size_t)w * B + kk) * B + j] = (float)pj;
+            pr += pj * Rj;
+        }
+    }
+    const double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
+    const double cw = s.wv ? c.cw[w] : 0.0;
+    // warm start moved onto this step's constraint
+    const double sx = seg_sum(x0, s.Bp);
+    const double corr = con ? (cw - sx) * isg : 0.0;
+    if (s.ev) {
+        double xe = x0 + corr * y;
+        c.x[e] = xe;
+        c.pf[e] = (float)xe;
+    }
+    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+}
+
 // k_factor for blocks of at most 16 elements.  Lane kk holds row kk of
 // A_w = M_ww + dt G_w in registers and the segment inverts it in place by
 // Gauss-Jordan elimination without pivoting (A_w is SPD, so every pivot is a
@@ -1139,83 +1230,10 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
     const int wg = blockIdx.x * kSegWarps + warp;
     if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
     const Seg s = seg_of(c, wg);
-    const int B = s.B, kk = s.kk, w = s.w, e = s.e;
-    double a[kSegMax];
-    const double* nb = c.near + (size_t)c.block_type[s.wv ? w : 0] * B * B;
-#pragma unroll
-    for (int j = 0; j < kSegMax; ++j)
-        a[j] = (s.wv && kk < B && j < B) ? nb[kk * B + j] : (j == kk ? 1.0 : 0.0);
-    if (s.ev) {
-        const double g = c.dt * c.G[e];
-#pragma unroll
-        for (int j = 0; j < kSegMax; ++j)
-            if (j == kk) a[j] += g;
-    }
-    int bad = 0;
-#pragma unroll
-    for (int k = 0; k < kSegMax; ++k) {
-        if (k < B) {
-            double piv = __shfl_sync(0xffffffffu, a[k], s.base + k);
-            if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
-            const double ip = rcp_nr(piv);
-            if (kk == k) {
-#pragma unroll
-                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
-            }
-            double rk[kSegMax];                         // scaled pivot row
-#pragma unroll
-            for (int j = 0; j < kSegMax; ++j) rk[j] = __shfl_sync(0xffffffffu, a[j], s.base + k);
-            if (kk != k) {
-                const double f = a[k];
-#pragma unroll
-                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * rk[j];
-            }
-        }
-    }
-    if (bad && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
-    // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
-    double y = 0.0;
-#pragma unroll
-    for (int j = 0; j < kSegMax; ++j)
-        if (j < B) y += a[j];
-    y = s.ev ? y : 0.0;
-    const double sig = seg_sum(y, s.Bp);
-    const int con = s.wv ? c.constrained[w] : 0;
-    const double isg = 1.0 / sig;
-    if (s.ev) c.y1[e] = y;
-    if (kk == 0 && s.wv) {
-        c.sigma[w] = sig;
-        c.isigma[w] = isg;
-    }
-    const double x0 = s.ev ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
-    if (c.n_groups) {
-        factor_groups(c, s, a, y, isg, con, x0);
-        return;
-    }
-    // P_w row kk, stored; R^T P_w R
-    const double R = s.ev ? c.R[e] : 0.0;
-    double pr = 0.0;
-#pragma unroll
-    for (int j = 0; j < kSegMax; ++j) {
-        if (j < B) {
-            const double yj = __shfl_sync(0xffffffffu, y, s.base + j);
-            const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
-            const double pj = con ? a[j] - y * yj * isg : a[j];
-            if (s.ev) c.Lf[((size_t)w * B + kk) * B + j] = (float)pj;
-            pr += pj * Rj;
-        }
-    }
-    const double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
-    const double cw = s.wv ? c.cw[w] : 0.0;
-    // warm start moved onto this step's constraint
-    const double sx = seg_sum(x0, s.Bp);
-    const double corr = con ? (cw - sx) * isg : 0.0;
-    if (s.ev) {
-        double xe = x0 + corr * y;
-        c.x[e] = xe;
-        c.pf[e] = (float)xe;
-    }
-    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+    // the subelement path needs A_w^-1 itself (the transport part); otherwise the
+    // inverse only builds the preconditioner, which FP32 serves (see factor_seg)
+    if (c.n_groups) factor_seg<double>(c, s);
+    else factor_seg<float>(c, s);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
