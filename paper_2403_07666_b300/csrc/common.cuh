@@ -125,6 +125,15 @@ struct CoilDev {
     unsigned *ticket;             // 2 arrival counters of the fused last-CTA reductions
 };
 
+// Smallest of the n exponents e[0..n) over a warp (every lane gets it).
+__device__ __forceinline__ int warp_min_exponent(const int* e, int n, int lane) {
+    int m = 1 << 30;
+    for (int t = lane; t < n; t += 32) m = min(m, e[t]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

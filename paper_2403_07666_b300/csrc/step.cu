@@ -744,21 +744,15 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
     const int per_cta = (int)(blockDim.x >> 5) * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
     if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
-    double inv = 0.0;
-    if (far_tiles) {
-        __shared__ int xmin;
-        if (threadIdx.x == 0) xmin = 1 << 30;
-        __syncthreads();
-        for (int t = threadIdx.x; t < c.NT; t += blockDim.x) atomicMin(&xmin, c.tc_pexp[t]);
-        __syncthreads();
-        inv = ldexp(1.0, -(c.tc_exT + xmin));
-    }
     const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     double head = 0.0;                                  // p^T q of the lane's wire on segment heads
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
         const double* p = which == 0 ? c.x : c.dv;
         const double pv = s.ev ? p[s.e] : 0.0;
+        const double ge = s.ev ? c.G[s.e] : 0.0;
+        const double inv = far_tiles ? ldexp(1.0, -(c.tc_exT + warp_min_exponent(c.tc_pexp, c.NT, threadIdx.x & 31)))
+                                     : 0.0;
         const double* nb = c.near + (size_t)c.block_type[s.wv ? s.w : 0] * s.B * s.B;
         const int row = s.kk < s.B ? s.kk : 0;
         double acc = 0.0;
@@ -777,7 +771,7 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
         }
         double dot = 0.0;
         if (s.ev) {
-            acc += c.dt * c.G[s.e] * pv;
+            acc += c.dt * ge * pv;
             double qe = (far_tiles ? tc_far_sum(c, s.e, inv) : c.qv[s.e]) + acc;
             c.qv[s.e] = qe;
             dot = pv * qe;

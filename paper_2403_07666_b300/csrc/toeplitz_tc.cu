@@ -300,7 +300,10 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         mbar_fence_init();
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < sh.NT; t += blockDim.x) atomicMin(xmin_s, pexp[t]);
+    if (warp == 0) {
+        const int m = warp_min_exponent(pexp, sh.NT, lane);
+        if (lane == 0) *xmin_s = m;
+    }
     if (warp == 1) {
         __syncwarp();
         tmem_alloc(su32(tslot), (uint32_t)sh.ncols);
@@ -594,12 +597,7 @@ __global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, co
                             const int2* __restrict__ range, const int* __restrict__ pexp, int exT) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
-    __shared__ int xmin;
-    if (threadIdx.x == 0) xmin = 1 << 30;
-    __syncthreads();
-    for (int t = threadIdx.x; t < sh.NT; t += blockDim.x) atomicMin(&xmin, pexp[t]);
-    __syncthreads();
-    const double inv = ldexp(1.0, -(exT + xmin));
+    const double inv = ldexp(1.0, -(exT + warp_min_exponent(pexp, sh.NT, threadIdx.x & 31)));
     const size_t tile = (size_t)sh.NT * kTcM;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sh.N; e += gridDim.x * blockDim.x) {
         const int t = e / sh.C, cc = e - t * sh.C;
