@@ -40,7 +40,8 @@ def _material(N):
     return m, arrs
 
 
-@pytest.mark.parametrize("bad", ["n_sub", "pitch", "kind", "precision", "rtol", "nan"])
+@pytest.mark.parametrize("bad", ["n_sub", "pitch", "kind", "precision", "rtol", "nan", "young", "groups_many",
+                                 "groups_empty", "groups_range"])
 def test_invalid_input_rejected_on_host(lib, bad):
     g = K.Geometry()
     g.kind = K.GEOM_SOLENOID
@@ -62,6 +63,17 @@ def test_invalid_input_rejected_on_host(lib, bad):
     elif bad == "nan":
         m.T_bath = float("nan")
         expect = K.ERR_NONFINITE
+    elif bad == "young":
+        m.Y_eff = -1.0                   # Lorentz strain needs Y_eff >= 0
+    elif bad.startswith("groups"):
+        # subelements of the 4-element turns: more than 6 groups, an empty group,
+        # an id outside [0, n_groups)
+        grp, n_groups = {"groups_many": (np.arange(4, dtype=np.int32), 7),
+                         "groups_empty": (np.array([0, 0, 2, 2], dtype=np.int32), 3),
+                         "groups_range": (np.array([0, 1, 5, 1], dtype=np.int32), 3)}[bad]
+        keep.append(grp)
+        g.group = K._ptr(grp, C.c_int)
+        g.n_groups = n_groups
     h = C.c_void_p()
     st = lib.coil_create(C.byref(g), C.byref(m), C.byref(o), C.byref(h))
     assert st == expect and not h.value
