@@ -82,6 +82,9 @@ struct coil {
     long long launches = 0, op_launches = 0, pcg_iters = 0;
     double op_ms = 0.0;
     std::vector<cudaEvent_t> ev_pool;
+    // side streams and their events for the batched tensor-core applies
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_ev;
     size_t ev_used = 0;          // event pairs recorded since the last harvest
     cq::TcPlan* tc = nullptr;    // tensor-core Toeplitz apply (format 2)
 };
@@ -89,6 +92,7 @@ struct coil {
 namespace {
 
 const char* kNoHandle = "null coil handle";
+constexpr int kAuxStreams = 8;          // side streams of a batch's tensor-core applies
 constexpr size_t kMomentBlocks = 148;   // partial sums of the moment in coil_read
 
 coil_status fail(coil_t* c, coil_status st, const std::string& msg) {
@@ -670,6 +674,11 @@ struct Launch {
     bool seg = false, big = false;   // coils with blocks of <= kSegMax / more elements present
     bool need_q = false;             // the far apply must leave its result in q (no fused consumer)
     bool dir = false;                // format 2: the apply forms the PCG direction first
+    // format 2 batches: side streams the coils' applies are spread over (fork
+    // and join events: aux_ev[0..n_aux) per stream, aux_ev[n_aux] the fork)
+    const cudaStream_t* aux = nullptr;
+    const cudaEvent_t* aux_ev = nullptr;
+    int n_aux = 0;
 };
 
 Launch single_launch(coil_t* c) {
@@ -699,6 +708,20 @@ Launch single_launch(coil_t* c) {
 cudaError_t launch_far(const Launch& L, int which) {
     if (L.format == 1) return launch_toeplitz(L.d, L.n, L.maxC, L.maxNT, L.maxN, L.n_sm, L.s);
     if (L.format == 2) {
+        if (L.n_aux > 0 && L.tc.size() > 1) {
+            // a batch: the coils' applies are independent, so they run side by
+            // side on the side streams (one SM per CTA each: a small coil's
+            // apply alone leaves most of the GPU idle)
+            cudaError_t e = cudaEventRecord(L.aux_ev[L.n_aux], L.s);
+            for (int a = 0; a < L.n_aux && e == cudaSuccess; ++a) e = cudaStreamWaitEvent(L.aux[a], L.aux_ev[L.n_aux], 0);
+            for (size_t i = 0; i < L.tc.size() && e == cudaSuccess; ++i)
+                e = launch_toeplitz_tc(*L.tc[i], L.aux[i % L.n_aux], L.need_q || !L.tc[i]->fused, L.dir);
+            for (int a = 0; a < L.n_aux && e == cudaSuccess; ++a) {
+                e = cudaEventRecord(L.aux_ev[a], L.aux[a]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(L.s, L.aux_ev[a], 0);
+            }
+            return e;
+        }
         for (const TcPlan* P : L.tc) {
             cudaError_t e = launch_toeplitz_tc(*P, L.s, L.need_q || !P->fused, L.dir);
             if (e != cudaSuccess) return e;
@@ -1015,6 +1038,23 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.seg = L.seg || ci->h.B <= kSegMax;
         L.big = L.big || ci->h.B > kSegMax;
         if (ci->tc) L.tc.push_back(ci->tc);
+    }
+    if (L.format == 2 && n > 1) {
+        if (c->aux.empty()) {
+            for (int a = 0; a < kAuxStreams; ++a) {
+                cudaStream_t st;
+                CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch streams");
+                c->aux.push_back(st);
+            }
+            for (int a = 0; a <= kAuxStreams; ++a) {
+                cudaEvent_t ev;
+                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch events");
+                c->aux_ev.push_back(ev);
+            }
+        }
+        L.aux = c->aux.data();
+        L.aux_ev = c->aux_ev.data();
+        L.n_aux = (int)c->aux.size();
     }
     // descriptors and the gathered status live in one device block per call
     CoilDev* dd = nullptr;
@@ -1380,6 +1420,8 @@ void coil_destroy(coil_t* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (void* p : c->allocs) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaStream_t st : c->aux) cudaStreamDestroy(st);
+    for (cudaEvent_t e : c->aux_ev) cudaEventDestroy(e);
     if (c->d) cudaFree(c->d);
     delete c->tc;
     if (c->pinned) cudaFreeHost(c->pinned);
