@@ -326,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     toep = args.format != "dense"
     coil = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
-                              stream=stream.cuda_stream, profile=True, format=args.format)
+                              stream=stream.cuda_stream, format=args.format)
     setup_s = time.perf_counter() - t0
     info = coil.info()
     N = coil.N
@@ -339,12 +339,24 @@ def run_ours(args, rank, world, local_rank):
     inf = coil.info()
     # replicas: the units of all ranks over the slowest rank's time
     value, secs = job_throughput(secs, N * args.steps, dist, "cuda")
-    op_launches = int(inf.operator_launches)
-    gemv_ms = inf.operator_ms / max(op_launches, 1)
     op_bytes = int(info.operator_bytes)
-    applies = op_launches / args.steps
+    applies = int(inf.operator_launches) / args.steps
     launches = int(inf.kernel_launches)
+    step_graph = bool(inf.step_graph)
+    # the operator apply's own duration: the same warm-up and timed steps on a
+    # second coil whose every apply is bracketed by CUDA events on its stream
+    # (event records cannot sit inside the step graph's loop, so this coil
+    # launches its kernels one by one)
+    cp = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
+                            stream=stream.cuda_stream, profile=True, format=args.format)
+    cp.step(args.warmup, drive)
+    cp.reset_counters()
+    timed_steps(cp, drive, args.steps, stream, torch)
+    ip = cp.info()
+    cp.close()
+    gemv_ms = ip.operator_ms / max(int(ip.operator_launches), 1)
     roofline = roofline_of(args.format, args.precision, N, op_bytes, gemv_ms, hbm, peak_kind)
+    roofline["timed"] = "every apply of the same steps, CUDA events on the coil's stream, kernels launched one by one"
 
     # end to end through the public API: host buffers, copies inside the region
     import torch as _t
@@ -403,7 +415,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w.name, "n_elem": N, "n_layers": w.geometry["n_layers"],
                    "n_turns": w.geometry["n_turns"], "n_sub": w.geometry["n_sub"],
                    "precision": args.precision, "dt": drive["dt"], "ramp_A_per_s": drive["ramp_rate"],
-                   "rtol": args.rtol, "parallelism": f"replicas x{world}",
+                   "rtol": args.rtol, "parallelism": f"replicas x{world}", "step_graph": step_graph,
                    "operator_format": args.format,
                    "l2": (f"operator table {op_bytes / 1e9:.2f} GB > 126 MB L2 (no flush needed)" if toep else
                           f"operator {op_bytes / 1e9:.1f} GB > 126 MB L2 (no flush needed)")},
@@ -481,14 +493,18 @@ def format_leg(args, local_rank, stream, torch, fmt):
     from paper_2403_07666_b300.coil import Coil
     w = pick_workload(args.workload)
     hbm, peak_kind = peaks()
-    c = Coil.from_workload(w, precision="fp32", rtol=args.rtol, device=local_rank,
-                           stream=stream.cuda_stream, profile=True, format=fmt)
-    c.step(args.warmup, w.drive)
-    c.reset_counters()
-    secs = timed_steps(c, w.drive, args.steps, stream, torch)
-    inf = c.info()
-    N = c.N
-    c.close()
+    secs, inf, N = None, None, 0
+    for profile in (False, True):           # the step's time, then every apply's (as the main line)
+        c = Coil.from_workload(w, precision="fp32", rtol=args.rtol, device=local_rank,
+                               stream=stream.cuda_stream, profile=profile, format=fmt)
+        c.step(args.warmup, w.drive)
+        c.reset_counters()
+        t = timed_steps(c, w.drive, args.steps, stream, torch)
+        if not profile:
+            secs, N = t, c.N
+        else:
+            inf = c.info()
+        c.close()
     op_ms = inf.operator_ms / max(int(inf.operator_launches), 1)
     op_bytes = int(inf.operator_bytes)
     return {"value": N * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
@@ -525,7 +541,7 @@ def subelement_leg(args, local_rank, stream, torch):
     grp = wl.subelement_groups(w.geometry["n_sub"])
     w.geometry["groups"] = grp
     c = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
-                           stream=stream.cuda_stream, format=args.format, profile=True)
+                           stream=stream.cuda_stream, format=args.format)
     c.step(args.warmup, w.drive)
     c.reset_counters()
     secs = timed_steps(c, w.drive, args.steps, stream, torch)

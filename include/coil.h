@@ -133,7 +133,8 @@ typedef struct {
  * stream: a cudaStream_t to launch on (NULL: the library creates one).
  * diag_capacity: per-step diagnostic records kept on the device (ring).
  * profile: record a CUDA event pair around every dense-operator launch on the
- * coil's stream (coil_info reports their summed duration).
+ * coil's stream (coil_info reports their summed duration); the step's kernels
+ * are then launched one by one.  Without it a step runs as one CUDA graph.
  */
 typedef struct {
     int precision;
@@ -197,6 +198,9 @@ typedef struct {
     double operator_ms;           /* their summed duration (profile = 1) */
     long long pcg_iterations;     /* summed over all steps */
     size_t descriptor_bytes;      /* host-to-device bytes uploaded per coil_step call */
+    int step_graph;               /* 1: each step runs as one CUDA graph (its PCG loop a
+                                     device-controlled while node); profile = 1 launches
+                                     the kernels one by one to time every operator apply */
 } coil_info_t;
 
 /* Zero the launch / timing counters of coil_info. */

@@ -61,7 +61,7 @@ class Info(C.Structure):
                 ("device_bytes", C.c_size_t), ("steps", C.c_long), ("t", C.c_double),
                 ("setup_ms", C.c_double), ("kernel_launches", C.c_longlong),
                 ("operator_launches", C.c_longlong), ("operator_ms", C.c_double),
-                ("pcg_iterations", C.c_longlong), ("descriptor_bytes", C.c_size_t)]
+                ("pcg_iterations", C.c_longlong), ("descriptor_bytes", C.c_size_t), ("step_graph", C.c_int)]
 
 
 def load_library(path=LIB_PATH):

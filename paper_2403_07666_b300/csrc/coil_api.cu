@@ -50,6 +50,7 @@ __global__ void k_moment(const CoilDev* __restrict__ cds, double* part);
 __global__ void k_moment_sum(const double* part, int n, double* out);
 __global__ void k_to_float(const double* x, float* f, int n);
 __global__ void k_gather_status(const CoilDev* __restrict__ cds, int n, int* out);
+__global__ void k_loop_cond(const CoilDev* __restrict__ cds, cudaGraphConditionalHandle h);
 }  // namespace cq
 
 using namespace cq;
@@ -85,6 +86,12 @@ struct coil {
     // side streams and their events for the batched tensor-core applies
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> aux_ev;
+    // the step as one graph (prologue, PCG while loop, epilogue, scalars read
+    // back), when operator applies are not being timed one by one
+    cudaGraphExec_t step_exec = nullptr;
+    cudaStream_t body_stream = nullptr;
+    bool graph_failed = false;
+    int graph_fixed = 0, graph_per_pass = 0;   // kernels outside and inside the loop
     size_t ev_used = 0;          // event pairs recorded since the last harvest
     cq::TcPlan* tc = nullptr;    // tensor-core Toeplitz apply (format 2)
 };
@@ -812,11 +819,11 @@ coil_status step_prologue(coil_t* c, const Launch& L) {
 }
 
 // One projected-PCG iteration (kernels of converged coils return at once).
-// One PCG iteration.  The tensor-core format forms the direction d = -z + beta d
-// inside the next iteration's input split (first: the direction k_init set).
-coil_status step_iteration(coil_t* c, const Launch& L, bool first) {
+// The tensor-core format forms the direction d = -z + beta d inside the input
+// split of the iteration that uses it (from the second iteration on).
+coil_status step_iteration(coil_t* c, const Launch& L) {
     const bool fuse_dir = L.format == 2;
-    if (fuse_dir && !first) {
+    if (fuse_dir) {
         Launch Ld = L;
         Ld.dir = true;
         TRY(gemv(c, Ld, 1));
@@ -853,15 +860,108 @@ coil_status step_epilogue(coil_t* c, const Launch& L) {
     return COIL_OK;
 }
 
+// Capture one step as a graph: the prologue, a while node whose body is one
+// PCG iteration plus k_loop_cond (the device decides when to stop), the
+// epilogue (its kernels skip a failed step) and the copy of the scalars to the
+// pinned mirror.  One launch and one synchronization per step instead of
+// ~5 launches per iteration and a host check per chunk of iterations.
+coil_status build_step_graph(coil_t* c) {
+    cudaStream_t s = c->stream;
+    Launch L = single_launch(c);
+    if (!c->body_stream) CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking), "graph stream");
+    const long long l0 = c->launches, op0 = c->op_launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step capture");
+    coil_status st = step_prologue(c, L);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle hnd = 0;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t cnode = nullptr;
+    if (st == COIL_OK) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd);
+    if (st == COIL_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, cg, 1, cudaGraphCondAssignDefault);
+    if (st == COIL_OK && e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hnd;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &np);
+    }
+    if (st == COIL_OK && e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    const long long l1 = c->launches;
+    if (st == COIL_OK && e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(c->body_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            Launch Lb = L;
+            Lb.s = c->body_stream;
+            st = step_iteration(c, Lb);
+            k_loop_cond<<<1, 1, 0, c->body_stream>>>(c->d, hnd);
+            c->launches += 1;
+            cudaGraph_t body = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &body);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    const long long l2 = c->launches;
+    if (st == COIL_OK && e == cudaSuccess) st = step_epilogue(c, L);
+    const long long l3 = c->launches;
+    if (st == COIL_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pinned, c->h.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
+    cudaError_t e3 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = e3;
+    c->launches = l0;                                // counted per launch of the graph instead
+    c->op_launches = op0;
+    if (st == COIL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->step_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != COIL_OK) return st;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->step_exec = nullptr;
+        return cuda_fail(c, e, "step graph");
+    }
+    c->graph_fixed = (int)((l1 - l0) + (l3 - l2));
+    c->graph_per_pass = (int)(l2 - l1);
+    return COIL_OK;
+}
+
 coil_status run_step(coil_t* c) {
     const CoilDev& h = c->h;
+    if (!c->profile && !c->graph_failed) {
+        if (!c->step_exec && build_step_graph(c) != COIL_OK) {
+            c->graph_failed = true;                      // the same kernels, launched one by one
+            c->err.clear();
+        }
+        if (c->step_exec) {
+            CK(cudaGraphLaunch(c->step_exec, c->stream), "step graph launch");
+            CK(cudaStreamSynchronize(c->stream), "step");
+            const int passes = c->pinned->passes > 0 ? c->pinned->passes : 1;
+            c->launches += c->graph_fixed + (long long)c->graph_per_pass * passes;
+            c->op_launches += 1 + passes;
+            int st = c->pinned->status;
+            if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+            if (!c->pinned->done || st == ST_NOT_CONVERGED)
+                return fail(c, COIL_ERR_NOT_CONVERGED, "per-step solve did not converge within maxit iterations");
+            if (st == ST_NONFINITE)
+                return fail(c, COIL_ERR_NONFINITE, "non-finite value or non-positive pivot in the step solve");
+            c->last_iters = c->pinned->iter > 0 ? c->pinned->iter : 1;
+            c->pcg_iters += c->pinned->iter;
+            c->steps += 1;
+            c->t += h.dt;
+            return COIL_OK;
+        }
+    }
     Launch L = single_launch(c);
     TRY(step_prologue(c, L));
     // PCG: enqueue the expected number of iterations, then one at a time
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
-        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L, total + i == 0));
+        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
         total += chunk;
         TRY(read_scalars(c));
         if (c->pinned->done) break;
@@ -1074,7 +1174,7 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         int total = 0;
         bool all_done = false;
         while (result == COIL_OK) {
-            for (int i = 0; i < chunk && result == COIL_OK; ++i) result = step_iteration(c, L, total + i == 0);
+            for (int i = 0; i < chunk && result == COIL_OK; ++i) result = step_iteration(c, L);
             total += chunk;
             k_gather_status<<<(n + 127) / 128, 128, 0, L.s>>>(dd, n, dstat);
             e = cudaMemcpyAsync(hstat.data(), dstat, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, L.s);
@@ -1399,6 +1499,7 @@ coil_status coil_info(const coil_t* c, coil_info_t* info) {
     info->operator_ms = c->op_ms;
     info->pcg_iterations = c->pcg_iters;
     info->descriptor_bytes = sizeof(CoilDev);
+    info->step_graph = c->step_exec ? 1 : 0;
     return COIL_OK;
 }
 
@@ -1421,6 +1522,8 @@ void coil_destroy(coil_t* c) {
     for (void* p : c->allocs) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaStream_t st : c->aux) cudaStreamDestroy(st);
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    if (c->body_stream) cudaStreamDestroy(c->body_stream);
     for (cudaEvent_t e : c->aux_ev) cudaEventDestroy(e);
     if (c->d) cudaFree(c->d);
     delete c->tc;
@@ -1542,7 +1645,7 @@ coil_status adjoint_solve(coil_t* c) {
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
-        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L, total + i == 0));
+        for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
         total += chunk;
         TRY(read_scalars(c));
         if (c->pinned->done) break;

@@ -35,6 +35,7 @@ struct Scalars {
     double rz, dq, alpha, beta;
     int iter, done, status, nonpd;
     double last_resid;
+    int passes;          // loop passes of a graph-launched step (a guard on its while loop)
 };
 
 struct CoilDev {

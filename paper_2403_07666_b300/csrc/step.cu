@@ -601,6 +601,7 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
         sc->scale2 = s;
         sc->done = 0;
         sc->iter = 0;
+        sc->passes = 0;
         sc->status = ST_OK;
         if (sc->nonpd) { sc->status = ST_NONFINITE; sc->done = 1; }
         if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
@@ -1228,6 +1229,20 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
     // inverse only builds the preconditioner, which FP32 serves (see factor_seg)
     if (c.n_groups) factor_seg<double>(c, s);
     else factor_seg<float>(c, s);
+}
+
+// Condition of a graph-launched step's PCG while loop: go on while the solve
+// is not done; a pass count past maxit + 2 (which the scalar updates never
+// let happen) ends it as not converged, so the loop always terminates.
+__global__ void k_loop_cond(const CoilDev* __restrict__ cds, cudaGraphConditionalHandle h) {
+    const CoilDev& c = *cds;
+    Scalars* sc = c.sc;
+    const int p = ++sc->passes;
+    if (!sc->done && p > c.maxit + 2) {
+        sc->status = ST_NOT_CONVERGED;
+        sc->done = 1;
+    }
+    cudaGraphSetConditional(h, sc->done ? 0u : 1u);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).

@@ -558,15 +558,16 @@ __host__ __device__ inline int tc_exponent(double m) {
 
 // p -> FP16 hi/lo in [c'/8][hi, lo][t][c' % 8] order; one block per turn row t,
 // scaled by 2^pexp[t] so that the row's largest |p| lies below 2^14.  dir: p is
-// the PCG's next search direction, formed here first, d = -z + beta d (FP64
-// into d, FP32 into the input copy), in place of a separate pass.
+// the PCG's next search direction, formed here first (from the second
+// iteration on), d = -z + beta d (FP64 into d, FP32 into the input copy), in
+// place of a separate pass.
 __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
                            int* __restrict__ pexp, int dir) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
     const int t = blockIdx.x;
     float* row = c.pf + (size_t)t * sh.C;
-    if (dir) {
+    if (dir && c.sc->iter > 0) {                 // the first iteration's direction is k_init's
         const double beta = c.sc->beta;
         const size_t e0 = (size_t)t * sh.C;
         for (int cc = threadIdx.x; cc < sh.C; cc += blockDim.x) {
