@@ -458,9 +458,10 @@ def roofline_of(fmt, precision, N, op_bytes, op_ms, hbm, peak_kind):
     dense: HBM-bound GEMV, algorithmic bytes = the stored operator.
     toeplitz (CUDA cores, FP32): bound by the FP32 pipe, 2 N^2 flops.
     toeplitz_tc (tensor cores): HBM-bound, algorithmic bytes = the split table
-    (read once) + the FP32 input read + the FP64 result written (12 N); its
-    tensor work, 3 x 2 N^2 FP16 flops (hi.hi, hi.lo, lo.hi), is reported
-    beside it."""
+    (read once) + the operator's input and result (4 + 8 bytes per element);
+    the duration is the product kernel's (k_toeplitz_tc) alone, the input
+    split being a kernel of its own; its tensor work, 3 x 2 N^2 FP16 flops
+    (hi.hi, hi.lo, lo.hi), is reported beside it."""
     if fmt == "toeplitz":
         flops = 2.0 * N * N
         achieved = flops / (op_ms / 1e3) / 1e12
@@ -477,7 +478,7 @@ def roofline_of(fmt, precision, N, op_bytes, op_ms, hbm, peak_kind):
         prof = PROFILED_TRAFFIC.get("toeplitz_tc")
         traffic = prof["dram_bytes"] * op_bytes / prof["operator_bytes"] if prof else None
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": "k_toeplitz_tc (+split)", "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": "k_toeplitz_tc", "peak_kind": peak_kind,
                 "avg_launch_ms": op_ms, "bytes_per_launch": nbytes, "table_bytes": op_bytes,
                 "tensor_tflops_fp16": 6.0 * N * N / (op_ms / 1e3) / 1e12}
     achieved = op_bytes / (op_ms / 1e3) / 1e9

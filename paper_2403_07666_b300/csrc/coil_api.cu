@@ -740,6 +740,26 @@ cudaError_t launch_far(const Launch& L, int which) {
 
 // Dense-operator launch, bracketed by an event pair when profiling.
 coil_status gemv(coil_t* c, const Launch& L, int which) {
+    if (c->profile && L.format == 2 && L.tc.size() == 1 && L.n_aux == 0) {
+        // the tensor-core form: the events bracket its product kernel alone
+        // (the input split is a kernel of its own)
+        if (c->ev_used * 2 + 2 > c->ev_pool.size()) {
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e), "event");
+                c->ev_pool.push_back(e);
+            }
+        }
+        const TcPlan& P = *L.tc[0];
+        CK(launch_tc_split(P, L.s, L.dir), "operator apply");
+        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used], L.s), "event");
+        CK(launch_tc_apply(P, L.s, L.need_q || !P.fused), "operator apply");
+        CK(cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], L.s), "event");
+        c->ev_used += 1;
+        c->op_launches += 1;
+        c->launches += 1;
+        return COIL_OK;
+    }
     if (c->profile) {
         if (c->ev_used * 2 + 2 > c->ev_pool.size()) {
             for (int k = 0; k < 2; ++k) {

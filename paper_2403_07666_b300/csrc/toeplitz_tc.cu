@@ -830,9 +830,13 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
     return e;
 }
 
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir) {
+cudaError_t launch_tc_split(const TcPlan& P, cudaStream_t s, bool dir) {
+    k_tc_split<<<P.sh.NT, 256, 0, s>>>(P.d, P.sh, P.p16, P.pexp, dir ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q) {
     const TcShape& sh = P.sh;
-    k_tc_split<<<sh.NT, 256, 0, s>>>(P.d, sh, P.p16, P.pexp, dir ? 1 : 0);
     k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmAT, P.tmB, P.d, sh, P.work, P.pexp, P.part);
     if (write_q) {
         int rb = (sh.N + 255) / 256;
@@ -840,6 +844,11 @@ cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bo
         k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.range, P.pexp, P.exT);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir) {
+    cudaError_t e = launch_tc_split(P, s, dir);
+    return e == cudaSuccess ? launch_tc_apply(P, s, write_q) : e;
 }
 
 }  // namespace cq

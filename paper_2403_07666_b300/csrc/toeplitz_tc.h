@@ -59,5 +59,9 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why);
 // shared-warp near kernel sums the tiles).
 // dir: form the PCG direction d = -z + beta d in the input split first.
 cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir = false);
+// Its two halves: the input split (k_tc_split) and the tensor-core product
+// (k_toeplitz_tc, plus the FP64 reduction into q when write_q).
+cudaError_t launch_tc_split(const TcPlan& P, cudaStream_t s, bool dir);
+cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q);
 
 }  // namespace cq
