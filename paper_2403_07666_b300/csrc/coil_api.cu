@@ -35,7 +35,8 @@ __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
 __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha);
 __global__ void k_init_seg(const CoilDev* __restrict__ cds);
-__global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta);
+__global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond,
+                             int use_cond);
 __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds);
 __global__ void k_factor_seg(const CoilDev* __restrict__ cds);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
@@ -686,6 +687,10 @@ struct Launch {
     const cudaStream_t* aux = nullptr;
     const cudaEvent_t* aux_ev = nullptr;
     int n_aux = 0;
+    // a graph-launched step's PCG iteration: (fuse_cond) the update kernel
+    // sets the loop's condition
+    bool fuse_cond = false;
+    cudaGraphConditionalHandle cond = 0;
 };
 
 Launch single_launch(coil_t* c) {
@@ -820,7 +825,9 @@ int launch_factor(const Launch& L) {
 }
 int launch_update(const Launch& L) {
     if (L.big) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.seg) k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d, 1);
+    if (L.seg)
+        k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(
+            L.d, 1, L.cond, (int)L.fuse_cond);
     return (int)L.big + (int)L.seg;
 }
 
@@ -881,7 +888,9 @@ coil_status step_epilogue(coil_t* c, const Launch& L) {
 }
 
 // Capture one step as a graph: the prologue, a while node whose body is one
-// PCG iteration plus k_loop_cond (the device decides when to stop), the
+// PCG iteration whose update kernel's last CTA (or, for coils with blocks of
+// more than 16 elements, k_loop_cond) sets the loop's condition (the device
+// decides when to stop), the
 // epilogue (its kernels skip a failed step) and the copy of the scalars to the
 // pinned mirror.  One launch and one synchronization per step instead of
 // ~5 launches per iteration and a host check per chunk of iterations.
@@ -919,9 +928,13 @@ coil_status build_step_graph(coil_t* c) {
         if (e == cudaSuccess) {
             Launch Lb = L;
             Lb.s = c->body_stream;
+            Lb.cond = hnd;
+            Lb.fuse_cond = L.seg && !L.big;          // the shared-warp update kernel's last CTA
             st = step_iteration(c, Lb);
-            k_loop_cond<<<1, 1, 0, c->body_stream>>>(c->d, hnd);
-            c->launches += 1;
+            if (!Lb.fuse_cond) {
+                k_loop_cond<<<1, 1, 0, c->body_stream>>>(c->d, hnd);
+                c->launches += 1;
+            }
             cudaGraph_t body = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(c->body_stream, &body);
             if (e == cudaSuccess) e = e2;

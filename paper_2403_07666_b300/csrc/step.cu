@@ -638,14 +638,28 @@ __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg
     reduce_and_update(c, mode, c.parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W, c.W);
 }
 
+// Condition of a graph-launched step's PCG while loop: go on while the solve
+// is not done; a pass count past maxit + 2 (which the scalar updates never
+// let happen) ends it as not converged, so the loop always terminates.  One
+// thread, once per pass.
+__device__ void loop_condition(const CoilDev& c, cudaGraphConditionalHandle h) {
+    Scalars* sc = c.sc;
+    const int p = ++sc->passes;
+    if (!sc->done && p > c.maxit + 2) {
+        sc->status = ST_NOT_CONVERGED;
+        sc->done = 1;
+    }
+    cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+}
+
 // Fused reduction of a per-wire value held by the head lane of each wire's
 // segment: every thread of the coil's first n_cta CTAs calls this.  Each CTA
 // sums its wires in a fixed order (butterfly per warp, then warps in order)
 // into parts row 7 at its index; the CTA that arrives last on the counter
 // (which it resets for the next launch) sums those n_cta values and does the
-// scalar update of `mode`.  The fences order every CTA's partial store before
-// the last CTA's loads.
-__device__ void fused_reduce(const CoilDev& c, double head_value, unsigned* ticket, int n_cta, int mode) {
+// scalar update of `mode`; true in that CTA.  The fences order every CTA's
+// partial store before the last CTA's loads.
+__device__ bool fused_reduce(const CoilDev& c, double head_value, unsigned* ticket, int n_cta, int mode) {
     __shared__ double wsum[32];
     __shared__ int is_last;
     const double v = warp_sum(head_value);
@@ -661,9 +675,10 @@ __device__ void fused_reduce(const CoilDev& c, double head_value, unsigned* tick
         if (is_last) *ticket = 0u;
     }
     __syncthreads();
-    if (!is_last) return;
+    if (!is_last) return false;
     __threadfence();
     reduce_and_update(c, mode, ctap, n_cta);
+    return true;
 }
 
 // ------------------------------------------ blocks of at most 16 elements
@@ -892,13 +907,18 @@ k_init_seg(const CoilDev* __restrict__ cds) {
 }
 
 // fuse_beta: the last CTA sums the r^T z partials and sets beta and the
-// convergence flags (the k_reduce BETA step).
+// convergence flags (the k_reduce BETA step).  use_cond (one coil, a
+// graph-launched step): that CTA (CTA 0 when the solve was already done) also
+// sets the PCG loop's condition, in place of k_loop_cond.
 __global__ void __launch_bounds__(32 * kSegWarps)
-k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
+k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond, int use_cond) {
     const CoilDev& c = cds[blockIdx.y];
     const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
-    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
+    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) loop_condition(c, cond);
+        return;
+    }
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
     double head = 0.0;                                  // r^T z of the lane's wire on segment heads
@@ -919,7 +939,8 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta) {
             else c.parts[4 * (size_t)c.W + s.w] = rz;
         }
     }
-    if (fuse_beta) fused_reduce(c, head, c.ticket + 1, n_cta, RED_BETA);
+    if (fuse_beta && fused_reduce(c, head, c.ticket + 1, n_cta, RED_BETA) && use_cond && threadIdx.x == 0)
+        loop_condition(c, cond);
 }
 
 __device__ __forceinline__ double seg_max(double v, int Bp) {
@@ -1231,18 +1252,10 @@ k_factor_seg(const CoilDev* __restrict__ cds) {
     else factor_seg<float>(c, s);
 }
 
-// Condition of a graph-launched step's PCG while loop: go on while the solve
-// is not done; a pass count past maxit + 2 (which the scalar updates never
-// let happen) ends it as not converged, so the loop always terminates.
+// The PCG loop's condition as a kernel of its own (coils whose update kernel
+// does not set it).
 __global__ void k_loop_cond(const CoilDev* __restrict__ cds, cudaGraphConditionalHandle h) {
-    const CoilDev& c = *cds;
-    Scalars* sc = c.sc;
-    const int p = ++sc->passes;
-    if (!sc->done && p > c.maxit + 2) {
-        sc->status = ST_NOT_CONVERGED;
-        sc->done = 1;
-    }
-    cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+    loop_condition(*cds, h);
 }
 
 // d = -z + beta d (and its FP32 copy for the mixed-precision operator).
