@@ -93,6 +93,9 @@ struct coil {
     cudaStream_t body_stream = nullptr;
     bool graph_failed = false;
     int graph_fixed = 0, graph_per_pass = 0;   // kernels outside and inside the loop
+    // the adjoint's transposed solve as one graph (its prologue and PCG loop)
+    cudaGraphExec_t adj_exec = nullptr;
+    int adj_fixed = 0, adj_per_pass = 0;
     size_t ev_used = 0;          // event pairs recorded since the last harvest
     cq::TcPlan* tc = nullptr;    // tensor-core Toeplitz apply (format 2)
 };
@@ -890,11 +893,16 @@ coil_status step_epilogue(coil_t* c, const Launch& L) {
 // Capture one step as a graph: the prologue, a while node whose body is one
 // PCG iteration whose update kernel's last CTA (or, for coils with blocks of
 // more than 16 elements, k_loop_cond) sets the loop's condition (the device
-// decides when to stop), the
-// epilogue (its kernels skip a failed step) and the copy of the scalars to the
-// pinned mirror.  One launch and one synchronization per step instead of
+// decides when to stop), the epilogue (its kernels skip a failed step) and the
+// copy of the scalars to the pinned mirror; the adjoint's transposed solve the
+// same way with its own prologue and no epilogue.  One launch and one
+// synchronization per step instead of
 // ~5 launches per iteration and a host check per chunk of iterations.
-coil_status build_step_graph(coil_t* c) {
+coil_status adjoint_prologue(coil_t* c, const Launch& L);
+
+// kind 0: the forward step (step_prologue, loop, step_epilogue, scalars); kind
+// 1: the adjoint's transposed solve (adjoint_prologue, loop, scalars).
+coil_status build_step_graph(coil_t* c, int kind = 0) {
     cudaStream_t s = c->stream;
     Launch L = single_launch(c);
     if (!c->body_stream) CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking), "graph stream");
@@ -902,7 +910,7 @@ coil_status build_step_graph(coil_t* c) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "step capture");
-    coil_status st = step_prologue(c, L);
+    coil_status st = kind == 0 ? step_prologue(c, L) : adjoint_prologue(c, L);
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -941,7 +949,7 @@ coil_status build_step_graph(coil_t* c) {
         }
     }
     const long long l2 = c->launches;
-    if (st == COIL_OK && e == cudaSuccess) st = step_epilogue(c, L);
+    if (st == COIL_OK && e == cudaSuccess && kind == 0) st = step_epilogue(c, L);
     const long long l3 = c->launches;
     if (st == COIL_OK && e == cudaSuccess)
         e = cudaMemcpyAsync(c->pinned, c->h.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
@@ -949,16 +957,17 @@ coil_status build_step_graph(coil_t* c) {
     if (e == cudaSuccess) e = e3;
     c->launches = l0;                                // counted per launch of the graph instead
     c->op_launches = op0;
-    if (st == COIL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->step_exec, g, 0);
+    cudaGraphExec_t* exec = kind == 0 ? &c->step_exec : &c->adj_exec;
+    if (st == COIL_OK && e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (st != COIL_OK) return st;
     if (e != cudaSuccess) {
         cudaGetLastError();
-        c->step_exec = nullptr;
+        *exec = nullptr;
         return cuda_fail(c, e, "step graph");
     }
-    c->graph_fixed = (int)((l1 - l0) + (l3 - l2));
-    c->graph_per_pass = (int)(l2 - l1);
+    (kind == 0 ? c->graph_fixed : c->adj_fixed) = (int)((l1 - l0) + (l3 - l2));
+    (kind == 0 ? c->graph_per_pass : c->adj_per_pass) = (int)(l2 - l1);
     return COIL_OK;
 }
 
@@ -1556,6 +1565,7 @@ void coil_destroy(coil_t* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaStream_t st : c->aux) cudaStreamDestroy(st);
     if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    if (c->adj_exec) cudaGraphExecDestroy(c->adj_exec);
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
     for (cudaEvent_t e : c->aux_ev) cudaEventDestroy(e);
     if (c->d) cudaFree(c->d);
@@ -1664,9 +1674,7 @@ coil_status set_device_time(coil_t* c, double t, long long step) {
 
 // The transposed KKT solve of one reverse step: the same projected PCG with
 // the right-hand side prepared by k_adj_setup (k_pointwise already ran).
-coil_status adjoint_solve(coil_t* c) {
-    const CoilDev& h = c->h;
-    Launch L = single_launch(c);
+coil_status adjoint_prologue(coil_t* c, const Launch& L) {
     c->launches += launch_factor(L);
     k_reduce<<<1, 256, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
@@ -1675,6 +1683,38 @@ coil_status adjoint_solve(coil_t* c) {
     k_reduce<<<1, 256, 0, L.s>>>(L.d, 1, 0);
     c->launches += 2;
     CK(cudaGetLastError(), "adjoint solve");
+    return COIL_OK;
+}
+
+coil_status adjoint_status(coil_t* c) {
+    int st = c->pinned->status;
+    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+    if (!c->pinned->done || st == ST_NOT_CONVERGED)
+        return fail(c, COIL_ERR_NOT_CONVERGED, "adjoint solve did not converge within maxit iterations");
+    if (st == ST_NONFINITE) return fail(c, COIL_ERR_NONFINITE, "non-finite value in the adjoint solve");
+    c->pcg_iters += c->pinned->iter;
+    return COIL_OK;
+}
+
+coil_status adjoint_solve(coil_t* c) {
+    const CoilDev& h = c->h;
+    if (!c->profile && !c->graph_failed) {
+        // one graph: the prologue, then the PCG loop the device ends
+        if (!c->adj_exec && build_step_graph(c, 1) != COIL_OK) {
+            c->graph_failed = true;                      // the same kernels, launched one by one
+            c->err.clear();
+        }
+        if (c->adj_exec) {
+            CK(cudaGraphLaunch(c->adj_exec, c->stream), "adjoint graph launch");
+            CK(cudaStreamSynchronize(c->stream), "adjoint solve");
+            const int passes = c->pinned->passes > 0 ? c->pinned->passes : 1;
+            c->launches += c->adj_fixed + (long long)c->adj_per_pass * passes;
+            c->op_launches += 1 + passes;
+            return adjoint_status(c);
+        }
+    }
+    Launch L = single_launch(c);
+    TRY(adjoint_prologue(c, L));
     int chunk = c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
@@ -1685,14 +1725,8 @@ coil_status adjoint_solve(coil_t* c) {
         if (total > h.maxit + 2) break;
         chunk = 1;
     }
-    int st = c->pinned->status;
-    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
-    if (!c->pinned->done || st == ST_NOT_CONVERGED)
-        return fail(c, COIL_ERR_NOT_CONVERGED, "adjoint solve did not converge within maxit iterations");
-    if (st == ST_NONFINITE) return fail(c, COIL_ERR_NONFINITE, "non-finite value in the adjoint solve");
-    c->pcg_iters += c->pinned->iter;
     harvest_events(c);
-    return COIL_OK;
+    return adjoint_status(c);
 }
 
 }  // namespace
