@@ -585,17 +585,26 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
     Scalars* sc = c.sc;
     if ((mode == RED_ALPHA || mode == RED_BETA || mode == RED_INIT) && sc->done) return;
     __shared__ double sh[32];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;     // four loads in flight per thread
-    const int st = blockDim.x;
-    int i = threadIdx.x;
-    for (; i + 3 * st < W; i += 4 * st) {
-        s0 += a[i];
-        s1 += a[i + st];
-        s2 += a[i + 2 * st];
-        s3 += a[i + 3 * st];
+    // the scalars the update needs, loaded while the partials are (it runs
+    // on the tail of a kernel, one CTA, every round trip in sequence)
+    double rz_old = 0.0, scale2 = 0.0;
+    int iter = 0;
+    if (threadIdx.x == 0) {
+        rz_old = sc->rz;
+        scale2 = sc->scale2;
+        iter = sc->iter;
     }
-    for (; i < W; i += st) s0 += a[i];
-    double s = block_reduce_sum((s0 + s1) + (s2 + s3), sh);
+    // eight loads in flight per thread, summed in a fixed order
+    double s0 = 0.0, s1 = 0.0;
+    const int st = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < W; i0 += 8 * st) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = i0 + k * st < W ? a[i0 + k * st] : 0.0;
+        s0 += ((v[0] + v[1]) + (v[2] + v[3]));
+        s1 += ((v[4] + v[5]) + (v[6] + v[7]));
+    }
+    double s = block_reduce_sum(s0 + s1, sh);
     if (threadIdx.x != 0) return;
     if (mode == RED_SCALE) {
         sc->scale2 = s;
@@ -606,27 +615,26 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
         if (sc->nonpd) { sc->status = ST_NONFINITE; sc->done = 1; }
         if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
     } else if (mode == RED_INIT) {
+        // (the relative residual sqrt(rz / scale2) is formed once per step, by k_step_end)
         sc->rz = s;
-        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(s, 0.0) / sc->scale2) : 0.0;
         if (!(s == s)) { sc->status = ST_NONFINITE; sc->done = 1; }
-        else if (s <= c.rtol2 * sc->scale2) sc->done = 1;
+        else if (s <= c.rtol2 * scale2) sc->done = 1;
     } else if (mode == RED_ALPHA) {
         sc->dq = s;
         if (!(s > 0.0)) {                      // A is SPD on the feasible subspace
-            sc->status = (s == s) ? ST_NONFINITE : ST_NONFINITE;
+            sc->status = ST_NONFINITE;
             sc->done = 1;
             return;
         }
-        sc->alpha = sc->rz / s;
+        sc->alpha = rz_old / s;
     } else {
         double rz_new = s;
-        sc->iter += 1;
-        sc->beta = rz_new / sc->rz;
+        sc->iter = iter + 1;
+        sc->beta = rz_new / rz_old;
         sc->rz = rz_new;
-        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(rz_new, 0.0) / sc->scale2) : 0.0;
         if (!(rz_new == rz_new)) { sc->status = ST_NONFINITE; sc->done = 1; }
-        else if (rz_new <= c.rtol2 * sc->scale2) sc->done = 1;
-        else if (sc->iter >= c.maxit) { sc->status = ST_NOT_CONVERGED; sc->done = 1; }
+        else if (rz_new <= c.rtol2 * scale2) sc->done = 1;
+        else if (iter + 1 >= c.maxit) { sc->status = ST_NOT_CONVERGED; sc->done = 1; }
     }
 }
 
@@ -1457,6 +1465,7 @@ __global__ void k_step_end(const CoilDev* __restrict__ cds) {
     rec[6] = jr;
     rec[7] = rh;
     rec[8] = (double)sc->iter;
+    sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(sc->rz, 0.0) / sc->scale2) : 0.0;
     rec[9] = sc->last_resid;
     sc->t = t1;
     sc->step += 1;

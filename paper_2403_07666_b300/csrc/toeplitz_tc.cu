@@ -49,14 +49,14 @@
 // comes from DRAM once and from L2 once.  One staged copy of p (the column
 // tile's 128 channels) is loaded per change of cb.
 //
-// CTA roles (416 threads): warp 0 issues the TMA loads, warps 1-4 issue the
+// CTA roles (672 threads): warp 0 issues the TMA loads, warps 1-4 issue the
 // MMAs of every fourth stage each (warp 1 owns the TMEM; one thread issues a
-// small-N MMA far slower than the tensor cores run it), warps 5-12 drain the
-// accumulators (lane quadrant warp % 4, even or odd 8-turn groups).  Every wait on an
-// mbarrier is bounded: on a timeout the CTA raises an abort flag, the others
-// stop issuing, the copies and MMAs already in flight are waited for (again
-// bounded), the TMEM is freed, and the coil's status word reports the failure
-// to the host.
+// small-N MMA far slower than the tensor cores run it), warps 5-20 drain the
+// accumulators (lane quadrant warp % 4, 8-turn groups g of one residue g mod 4).
+// Every wait on an mbarrier is bounded: on a timeout the CTA raises an abort
+// flag, the others stop issuing, the copies and MMAs already in flight are
+// waited for (again bounded), the TMEM is freed, and the coil's status word
+// reports the failure to the host.
 #include "toeplitz_tc.h"
 
 #include <cuda_fp16.h>
