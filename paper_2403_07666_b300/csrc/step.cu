@@ -665,8 +665,8 @@ __device__ void loop_condition(const CoilDev& c, cudaGraphConditionalHandle h) {
 // sums its wires in a fixed order (butterfly per warp, then warps in order)
 // into parts row 7 at its index; the CTA that arrives last on the counter
 // (which it resets for the next launch) sums those n_cta values and does the
-// scalar update of `mode`; true in that CTA.  The fences order every CTA's
-// partial store before the last CTA's loads.
+// scalar update of `mode`; true in that CTA.  The counter's release/acquire
+// orders every CTA's partial store before the last CTA's loads.
 __device__ bool fused_reduce(const CoilDev& c, double head_value, unsigned* ticket, int n_cta, int mode) {
     __shared__ double wsum[32];
     __shared__ int is_last;
@@ -678,13 +678,16 @@ __device__ bool fused_reduce(const CoilDev& c, double head_value, unsigned* tick
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
         ctap[blockIdx.x] = t;
-        __threadfence();
-        is_last = atomicAdd(ticket, 1u) == (unsigned)n_cta - 1u;
+        // release: the partial is visible before the count moves; acquire (in
+        // the CTA that arrives last): every other CTA's partial is visible to
+        // this thread, and through the barrier below to the rest of its CTA
+        unsigned prev;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(prev) : "l"(ticket) : "memory");
+        is_last = prev == (unsigned)n_cta - 1u;
         if (is_last) *ticket = 0u;
     }
     __syncthreads();
     if (!is_last) return false;
-    __threadfence();
     reduce_and_update(c, mode, ctap, n_cta);
     return true;
 }
