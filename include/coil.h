@@ -132,9 +132,11 @@ typedef struct {
  * right-hand side.  maxit: iteration cap (then COIL_ERR_NOT_CONVERGED).
  * stream: a cudaStream_t to launch on (NULL: the library creates one).
  * diag_capacity: per-step diagnostic records kept on the device (ring).
- * profile: record a CUDA event pair around every dense-operator launch on the
- * coil's stream (coil_info reports their summed duration); the step's kernels
- * are then launched one by one.  Without it a step runs as one CUDA graph.
+ * profile: record a CUDA event pair around every operator launch on the coil's
+ * stream (coil_info reports their summed duration; in the tensor-core format
+ * the pair brackets the tensor-core product kernel, not the input split); the
+ * step's kernels are then launched one by one, the convergence test read
+ * after every PCG iteration.  Without it a step runs as one CUDA graph.
  */
 typedef struct {
     int precision;

@@ -1000,7 +1000,9 @@ coil_status run_step(coil_t* c) {
     Launch L = single_launch(c);
     TRY(step_prologue(c, L));
     // PCG: enqueue the expected number of iterations, then one at a time
-    int chunk = c->last_iters > 1 ? c->last_iters : 1;
+    // (profiling: one at a time throughout, so that no timed apply is one
+    // enqueued after convergence, which returns at once)
+    int chunk = !c->profile && c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
         for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
@@ -1715,7 +1717,7 @@ coil_status adjoint_solve(coil_t* c) {
     }
     Launch L = single_launch(c);
     TRY(adjoint_prologue(c, L));
-    int chunk = c->last_iters > 1 ? c->last_iters : 1;
+    int chunk = !c->profile && c->last_iters > 1 ? c->last_iters : 1;
     int total = 0;
     for (;;) {
         for (int i = 0; i < chunk; ++i) TRY(step_iteration(c, L));
