@@ -104,6 +104,7 @@ namespace {
 
 const char* kNoHandle = "null coil handle";
 constexpr int kAuxStreams = 8;          // side streams of a batch's tensor-core applies
+constexpr int kRedThreads = 1024;       // threads of the one-CTA-per-coil reductions (k_reduce, k_step_end)
 constexpr size_t kMomentBlocks = 148;   // partial sums of the moment in coil_read
 
 coil_status fail(coil_t* c, coil_status st, const std::string& msg) {
@@ -838,11 +839,11 @@ int launch_update(const Launch& L) {
 coil_status step_prologue(coil_t* c, const Launch& L) {
     c->launches += launch_pointwise(L);
     c->launches += launch_factor(L);
-    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 0, 0);
+    k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
     c->launches += launch_init(L);
-    k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 1, 0);
+    k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 1, 0);
     c->launches += 2;
     CK(cudaGetLastError(), "step launch");
     return COIL_OK;
@@ -862,9 +863,9 @@ coil_status step_iteration(coil_t* c, const Launch& L) {
     }
     // small-block coils reduce alpha and beta in the last CTA of their kernels
     c->launches += launch_near(L, 1);
-    if (L.big) k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 2, 1);
+    if (L.big) k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 2, 1);
     c->launches += launch_update(L);
-    if (L.big) k_reduce<<<L.n, 256, 0, L.s>>>(L.d, 3, 1);
+    if (L.big) k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 3, 1);
     if (!fuse_dir) {
         unsigned eb = (unsigned)((L.maxN + 255) / 256);
         if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
@@ -884,7 +885,7 @@ coil_status step_epilogue(coil_t* c, const Launch& L) {
         k_adi_z<<<dim3(L.maxGr, L.n), 32, L.maxGz * sizeof(double), L.s>>>(L.d);
         c->launches += 2;
     }
-    k_step_end<<<L.n, 256, 0, L.s>>>(L.d);
+    k_step_end<<<L.n, kRedThreads, 0, L.s>>>(L.d);
     c->launches += 2;
     CK(cudaGetLastError(), "step end launch");
     return COIL_OK;
@@ -1678,11 +1679,11 @@ coil_status set_device_time(coil_t* c, double t, long long step) {
 // the right-hand side prepared by k_adj_setup (k_pointwise already ran).
 coil_status adjoint_prologue(coil_t* c, const Launch& L) {
     c->launches += launch_factor(L);
-    k_reduce<<<1, 256, 0, L.s>>>(L.d, 0, 0);
+    k_reduce<<<1, kRedThreads, 0, L.s>>>(L.d, 0, 0);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
     c->launches += launch_init(L);
-    k_reduce<<<1, 256, 0, L.s>>>(L.d, 1, 0);
+    k_reduce<<<1, kRedThreads, 0, L.s>>>(L.d, 1, 0);
     c->launches += 2;
     CK(cudaGetLastError(), "adjoint solve");
     return COIL_OK;

@@ -640,7 +640,7 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
 
 // One CTA per coil; skip_seg: coils whose shared-warp kernels reduce their
 // partials themselves (last CTA) are left alone.
-__global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg) {
+__global__ void __launch_bounds__(1024) k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg) {
     const CoilDev& c = cds[blockIdx.x];
     if (skip_seg && c.B <= kSegMax) return;
     reduce_and_update(c, mode, c.parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W, c.W);
@@ -1427,13 +1427,14 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
 }
 
 // One CTA per coil: the step's diagnostic record, then t += dt.
-__global__ void k_step_end(const CoilDev* __restrict__ cds) {
+__global__ void __launch_bounds__(1024) k_step_end(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.x];
     if (c.sc->status != ST_OK) return;
     __shared__ double sh[32];
     const double* parts = c.parts;
     size_t W = c.W;
     double pj = 0.0, V = 0.0, m = 0.0, jr = 0.0, rh = 0.0;
+#pragma unroll 4
     for (int w = threadIdx.x; w < c.W; w += blockDim.x) {
         pj += parts[0 * W + w];
         jr = fmax(jr, parts[1 * W + w]);
