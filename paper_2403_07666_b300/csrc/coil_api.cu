@@ -7,6 +7,7 @@
 
 #include <string>
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "../../include/coil.h"
@@ -52,7 +53,19 @@ __global__ void k_moment_sum(const double* part, int n, double* out);
 __global__ void k_to_float(const double* x, float* f, int n);
 __global__ void k_gather_status(const CoilDev* __restrict__ cds, int n, int* out);
 __global__ void k_loop_cond(const CoilDev* __restrict__ cds, cudaGraphConditionalHandle h);
+__global__ void k_batch_cond(const CoilDev* __restrict__ cds, int n, int* passes, int maxit,
+                             cudaGraphConditionalHandle h);
 }  // namespace cq
+
+// A batched step captured as one graph, kept by the batch's first coil for the
+// next call with the same coils (matched by their creation ids).
+struct BatchGraph {
+    std::vector<long long> ids;
+    cq::CoilDev* dd = nullptr;    // n descriptors, then 3 n + 1 ints: done, status, iter per coil; passes
+    int* hstat = nullptr;         // pinned copy of the 3 n + 1 ints
+    cudaGraphExec_t exec = nullptr;
+    int fixed = 0, per_pass = 0;
+};
 
 using namespace cq;
 
@@ -96,6 +109,8 @@ struct coil {
     // the adjoint's transposed solve as one graph (its prologue and PCG loop)
     cudaGraphExec_t adj_exec = nullptr;
     int adj_fixed = 0, adj_per_pass = 0;
+    long long uid = 0;           // creation id (batched-step graphs match coils by it)
+    BatchGraph* batch = nullptr;
     size_t ev_used = 0;          // event pairs recorded since the last harvest
     cq::TcPlan* tc = nullptr;    // tensor-core Toeplitz apply (format 2)
 };
@@ -902,16 +917,29 @@ coil_status step_epilogue(coil_t* c, const Launch& L) {
 coil_status adjoint_prologue(coil_t* c, const Launch& L);
 
 // kind 0: the forward step (step_prologue, loop, step_epilogue, scalars); kind
-// 1: the adjoint's transposed solve (adjoint_prologue, loop, scalars).
-coil_status build_step_graph(coil_t* c, int kind = 0) {
+// 1: the adjoint's transposed solve (adjoint_prologue, loop, scalars); kind 2:
+// a batched step (L over the batch's coils, bg its descriptors and status:
+// pass counter reset, step_prologue, loop with k_batch_cond, step_epilogue,
+// status gathered and copied to bg->hstat).
+coil_status build_step_graph(coil_t* c, int kind = 0, const Launch* Lbatch = nullptr, BatchGraph* bg = nullptr,
+                             int maxit = 0) {
     cudaStream_t s = c->stream;
-    Launch L = single_launch(c);
+    Launch L = kind == 2 ? *Lbatch : single_launch(c);
+    const int n = L.n;
+    // the side streams of a batch's tensor-core applies join the loop body's
+    // capture only: the prologue's apply runs its coils one after another
+    Launch Lp = L;
+    Lp.aux = nullptr;
+    Lp.aux_ev = nullptr;
+    Lp.n_aux = 0;
+    int* dstat = kind == 2 ? reinterpret_cast<int*>(bg->dd + n) : nullptr;
     if (!c->body_stream) CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking), "graph stream");
     const long long l0 = c->launches, op0 = c->op_launches;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "step capture");
-    coil_status st = kind == 0 ? step_prologue(c, L) : adjoint_prologue(c, L);
+    if (kind == 2) e = cudaMemsetAsync(dstat + 3 * n, 0, sizeof(int), s);   // the batch's pass counter
+    coil_status st = kind == 1 ? adjoint_prologue(c, Lp) : step_prologue(c, Lp);
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -938,9 +966,12 @@ coil_status build_step_graph(coil_t* c, int kind = 0) {
             Launch Lb = L;
             Lb.s = c->body_stream;
             Lb.cond = hnd;
-            Lb.fuse_cond = L.seg && !L.big;          // the shared-warp update kernel's last CTA
+            Lb.fuse_cond = kind != 2 && L.seg && !L.big;   // the shared-warp update kernel's last CTA
             st = step_iteration(c, Lb);
-            if (!Lb.fuse_cond) {
+            if (kind == 2) {
+                k_batch_cond<<<1, 128, 0, c->body_stream>>>(L.d, n, dstat + 3 * n, maxit, hnd);
+                c->launches += 1;
+            } else if (!Lb.fuse_cond) {
                 k_loop_cond<<<1, 1, 0, c->body_stream>>>(c->d, hnd);
                 c->launches += 1;
             }
@@ -950,15 +981,23 @@ coil_status build_step_graph(coil_t* c, int kind = 0) {
         }
     }
     const long long l2 = c->launches;
-    if (st == COIL_OK && e == cudaSuccess && kind == 0) st = step_epilogue(c, L);
+    if (st == COIL_OK && e == cudaSuccess && kind != 1) st = step_epilogue(c, Lp);
+    if (st == COIL_OK && e == cudaSuccess && kind == 2) {
+        k_gather_status<<<(n + 127) / 128, 128, 0, s>>>(L.d, n, dstat);
+        c->launches += 1;
+    }
     const long long l3 = c->launches;
-    if (st == COIL_OK && e == cudaSuccess)
-        e = cudaMemcpyAsync(c->pinned, c->h.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
+    if (st == COIL_OK && e == cudaSuccess) {
+        if (kind == 2)
+            e = cudaMemcpyAsync(bg->hstat, dstat, (3 * n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s);
+        else
+            e = cudaMemcpyAsync(c->pinned, c->h.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
+    }
     cudaError_t e3 = cudaStreamEndCapture(s, &g);
     if (e == cudaSuccess) e = e3;
     c->launches = l0;                                // counted per launch of the graph instead
     c->op_launches = op0;
-    cudaGraphExec_t* exec = kind == 0 ? &c->step_exec : &c->adj_exec;
+    cudaGraphExec_t* exec = kind == 0 ? &c->step_exec : (kind == 1 ? &c->adj_exec : &bg->exec);
     if (st == COIL_OK && e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (st != COIL_OK) return st;
@@ -967,8 +1006,10 @@ coil_status build_step_graph(coil_t* c, int kind = 0) {
         *exec = nullptr;
         return cuda_fail(c, e, "step graph");
     }
-    (kind == 0 ? c->graph_fixed : c->adj_fixed) = (int)((l1 - l0) + (l3 - l2));
-    (kind == 0 ? c->graph_per_pass : c->adj_per_pass) = (int)(l2 - l1);
+    const int fixed = (int)((l1 - l0) + (l3 - l2)), per_pass = (int)(l2 - l1);
+    if (kind == 0) { c->graph_fixed = fixed; c->graph_per_pass = per_pass; }
+    else if (kind == 1) { c->adj_fixed = fixed; c->adj_per_pass = per_pass; }
+    else { bg->fixed = fixed; bg->per_pass = per_pass; }
     return COIL_OK;
 }
 
@@ -1070,6 +1111,30 @@ __global__ void k_gather_status(const CoilDev* __restrict__ cds, int n, int* out
     }
 }
 
+// Condition of a graph-launched batched step's PCG while loop: go on while
+// any coil's solve is not done; past maxit + 2 passes the unfinished coils end
+// as not converged, so the loop always terminates.  One CTA.
+__global__ void k_batch_cond(const CoilDev* __restrict__ cds, int n, int* passes, int maxit,
+                             cudaGraphConditionalHandle h) {
+    __shared__ int p;
+    if (threadIdx.x == 0) p = ++*passes;
+    __syncthreads();
+    int open = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        Scalars* sc = cds[i].sc;
+        if (!sc->done) {
+            if (p > maxit + 2) {
+                sc->status = ST_NOT_CONVERGED;
+                sc->done = 1;
+            } else {
+                open = 1;
+            }
+        }
+    }
+    open = __syncthreads_or(open);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, open ? 1u : 0u);
+}
+
 // Moment sum(pi r^2 I) in two fixed-order passes: a grid-strided partial per
 // block (the FP64 pipe of one SM alone takes ~0.2 ms at 96,000 elements), then
 // one warp sums the partials.
@@ -1110,6 +1175,8 @@ coil_status coil_create(const coil_geometry* geom, const coil_material* mat, con
     *out = nullptr;
     coil_t* c = new (std::nothrow) coil();
     if (!c) return COIL_ERR_OOM;
+    static std::atomic<long long> next_uid{1};
+    c->uid = next_uid++;
     coil_status st = validate(geom, mat, opt, c);
     if (st == COIL_OK) {
         cudaError_t e = cudaSetDevice(opt->device);
@@ -1201,6 +1268,84 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.aux_ev = c->aux_ev.data();
         L.n_aux = (int)c->aux.size();
     }
+    int maxit = 0;
+    for (int i = 0; i < n; ++i) maxit = std::max(maxit, coils[i]->h.maxit);
+    // per coil after a step: counters on success, the first failure reported
+    auto finish_step = [&](const int* hs) {
+        coil_status first_err = COIL_OK;
+        for (int i = 0; i < n; ++i) {
+            coil_t* ci = coils[i];
+            int done = hs[3 * i], st = hs[3 * i + 1], it = hs[3 * i + 2];
+            if (done && st == ST_OK) {
+                ci->steps += 1;
+                ci->t += ci->h.dt;
+                ci->last_iters = it > 0 ? it : 1;
+                ci->pcg_iters += it;
+            } else if (first_err == COIL_OK) {
+                first_err = st == ST_KERNEL ? COIL_ERR_CUDA
+                            : (!done || st == ST_NOT_CONVERGED) ? COIL_ERR_NOT_CONVERGED : COIL_ERR_NONFINITE;
+                fail(ci, first_err, "batched step: this coil's solve failed; its state was kept");
+            }
+        }
+        if (first_err != COIL_OK) fail(c, first_err, "batched step: at least one coil's solve failed");
+        return first_err;
+    };
+    // graph-launched steps: the batch's step captured once (prologue, the PCG
+    // loop over every coil until all are done, epilogue, status copy) and kept
+    // by the first coil for later calls with the same coils
+    if (!c->profile && !c->graph_failed) {
+        std::vector<long long> ids(n);
+        for (int i = 0; i < n; ++i) ids[i] = coils[i]->uid;
+        if (c->batch && c->batch->ids != ids) {
+            CK(cudaStreamSynchronize(L.s), "batch graph");
+            if (c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
+            cudaFree(c->batch->dd);
+            cudaFreeHost(c->batch->hstat);
+            delete c->batch;
+            c->batch = nullptr;
+        }
+        bool fresh = false;
+        if (!c->batch) {
+            BatchGraph* bg = new BatchGraph;
+            bg->ids = ids;
+            cudaError_t ea = cudaMalloc(&bg->dd, n * sizeof(CoilDev) + (3 * (size_t)n + 1) * sizeof(int));
+            if (ea == cudaSuccess) ea = cudaMallocHost(&bg->hstat, (3 * (size_t)n + 1) * sizeof(int));
+            if (ea == cudaSuccess)
+                ea = cudaMemcpyAsync(bg->dd, hd.data(), n * sizeof(CoilDev), cudaMemcpyHostToDevice, L.s);
+            coil_status sb = ea == cudaSuccess ? COIL_OK : COIL_ERR_CUDA;
+            Launch Lg = L;
+            Lg.d = bg->dd;
+            if (sb == COIL_OK) sb = build_step_graph(c, 2, &Lg, bg, maxit);
+            if (sb == COIL_OK && bg->exec) {
+                c->batch = bg;
+                fresh = true;
+            } else {
+                cudaGetLastError();
+                if (bg->dd) cudaFree(bg->dd);
+                if (bg->hstat) cudaFreeHost(bg->hstat);
+                delete bg;
+                c->graph_failed = true;                  // the same kernels, launched one by one
+                c->err.clear();
+            }
+        }
+        if (c->batch) {
+            BatchGraph* bg = c->batch;
+            cudaError_t e = fresh ? cudaSuccess
+                                  : cudaMemcpyAsync(bg->dd, hd.data(), n * sizeof(CoilDev), cudaMemcpyHostToDevice, L.s);
+            coil_status result = COIL_OK;
+            for (long k = 0; k < n_steps && e == cudaSuccess && result == COIL_OK; ++k) {
+                e = cudaGraphLaunch(bg->exec, L.s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(L.s);
+                if (e != cudaSuccess) break;
+                const int passes = bg->hstat[3 * n] > 0 ? bg->hstat[3 * n] : 1;
+                c->launches += bg->fixed + (long long)bg->per_pass * passes;
+                c->op_launches += 1 + passes;
+                result = finish_step(bg->hstat);
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "batch step");
+            return result;
+        }
+    }
     // descriptors and the gathered status live in one device block per call
     CoilDev* dd = nullptr;
     int* dstat = nullptr;
@@ -1210,8 +1355,6 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
     coil_status result = COIL_OK;
     cudaError_t e = cudaMemcpyAsync(dd, hd.data(), n * sizeof(CoilDev), cudaMemcpyHostToDevice, L.s);
     L.d = dd;
-    int maxit = 0;
-    for (int i = 0; i < n; ++i) maxit = std::max(maxit, coils[i]->h.maxit);
     for (long k = 0; k < n_steps && e == cudaSuccess && result == COIL_OK; ++k) {
         result = step_prologue(c, L);
         int chunk = 1;
@@ -1233,25 +1376,7 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         if (e != cudaSuccess || result != COIL_OK) break;
         harvest_events(c);
         result = step_epilogue(c, L);
-        coil_status first_err = COIL_OK;
-        for (int i = 0; i < n; ++i) {
-            coil_t* ci = coils[i];
-            int done = hstat[3 * i], st = hstat[3 * i + 1], it = hstat[3 * i + 2];
-            if (done && st == ST_OK) {
-                ci->steps += 1;
-                ci->t += ci->h.dt;
-                ci->last_iters = it > 0 ? it : 1;
-                ci->pcg_iters += it;
-            } else if (first_err == COIL_OK) {
-                first_err = st == ST_KERNEL ? COIL_ERR_CUDA
-                            : (!done || st == ST_NOT_CONVERGED) ? COIL_ERR_NOT_CONVERGED : COIL_ERR_NONFINITE;
-                fail(ci, first_err, "batched step: this coil's solve failed; its state was kept");
-            }
-        }
-        if (result == COIL_OK && first_err != COIL_OK) {
-            fail(c, first_err, "batched step: at least one coil's solve failed");
-            result = first_err;
-        }
+        if (result == COIL_OK) result = finish_step(hstat.data());
     }
     cudaError_t e2 = cudaStreamSynchronize(L.s);
     cudaFree(dd);
@@ -1569,6 +1694,12 @@ void coil_destroy(coil_t* c) {
     for (cudaStream_t st : c->aux) cudaStreamDestroy(st);
     if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
     if (c->adj_exec) cudaGraphExecDestroy(c->adj_exec);
+    if (c->batch) {
+        if (c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
+        cudaFree(c->batch->dd);
+        cudaFreeHost(c->batch->hstat);
+        delete c->batch;
+    }
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
     for (cudaEvent_t e : c->aux_ev) cudaEventDestroy(e);
     if (c->d) cudaFree(c->d);
