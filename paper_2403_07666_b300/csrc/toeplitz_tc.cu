@@ -85,6 +85,8 @@ constexpr uint32_t kTcMnSbo = 1024u;
 constexpr int kTcSmemLimit = 227 * 1024;         // dynamic shared memory per CTA (opt-in maximum)
 constexpr long long kTcWait = 1LL << 31;         // cycles before a wait gives up (~1 s)
 constexpr int kTcBStages = 1;                    // staged copies of p (a CTA meets few k blocks)
+constexpr long long kTcMinSteps = 8;             // schedule steps per CTA, at least (see tc_schedule)
+constexpr long long kTcMinCtas = 4;              // CTAs per channel tile the step floor keeps
 __host__ __device__ constexpr int kTcBars(int stages) { return 2 * stages + 2 * kTcBStages + 9; }
 
 // ---------------------------------------------------------------------------
@@ -697,7 +699,7 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
 }
 
 // The same number of CTAs for every channel tile (n_sm / n_ct, at least one,
-// at most one per step).  Tile ct's j-th CTA and tile cb's j-th CTA meet the
+// at most one per step, and beyond four at most one per eight steps).  Tile ct's j-th CTA and tile cb's j-th CTA meet the
 // 128 x 128 region (ct, cb) of every stored offset block at about the same
 // time, one of them reading it transposed, so the region comes from DRAM
 // once.  A tile's n_ct NT steps are split into contiguous ranges of about
@@ -712,6 +714,12 @@ size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::ve
     long long per = n_sm / sh.n_ct;
     if (per < 1) per = 1;
     if (per > steps) per = steps;
+    // at least kTcMinSteps steps per CTA beyond kTcMinCtas CTAs per tile: a
+    // small coil's apply then takes a few SMs, not one CTA per SM with a step
+    // or two each, so a batch's applies on the side streams run side by side;
+    // the kTcMinCtas floor keeps each CTA's FP32 register sums short
+    const long long cap = std::max(std::min(per, kTcMinCtas), steps / kTcMinSteps);
+    if (per > cap) per = cap;
     if (work && range) {
         work->clear();
         range->clear();
