@@ -118,7 +118,7 @@ struct coil {
 namespace {
 
 const char* kNoHandle = "null coil handle";
-constexpr int kAuxStreams = 8;          // side streams of a batch's tensor-core applies
+constexpr int kAuxStreams = 16;         // side streams of a batch's tensor-core applies
 constexpr int kRedThreads = 1024;       // threads of the one-CTA-per-coil reductions (k_reduce, k_step_end)
 constexpr size_t kMomentBlocks = 148;   // partial sums of the moment in coil_read
 
