@@ -80,3 +80,35 @@ def test_batch_rejects_mixed_precision():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("fmt,prec", [("dense", "fp64"), ("toeplitz_tc", "fp32")])
+def test_batch_graph_follows_the_coil_set(fmt, prec):
+    """A batched step runs as a graph kept by the batch's first coil: a call
+    with another set of coils behind the same first coil, or with a coil
+    replaced by a new one, must rebuild it; every coil still gets exactly what
+    stepping it alone gives."""
+    from paper_2403_07666_b300.coil import Coil, batch_step
+    ws = _coils()[:3]
+    kw = dict(precision=prec, format=fmt, rtol=1e-11)
+    a, b, c = (Coil.from_workload(w, **kw) for w in ws)
+    alone = [Coil.from_workload(w, **kw) for w in ws]
+    d = None
+    try:
+        batch_step([a, b], 4, [ws[0].drive, ws[1].drive])
+        batch_step([a, c], 4, [ws[0].drive, ws[2].drive])
+        batch_step([a, b, c], 4, [w.drive for w in ws])
+        b.close()
+        d = Coil.from_workload(ws[1], **kw)             # a new coil, possibly at the old one's address
+        batch_step([a, d], 4, [ws[0].drive, ws[1].drive])
+        alone[0].step(16, ws[0].drive)
+        alone[1].step(4, ws[1].drive)
+        alone[2].step(8, ws[2].drive)
+        assert np.array_equal(a.currents(), alone[0].currents())
+        assert np.array_equal(c.currents(), alone[2].currents())
+        assert np.array_equal(d.currents(), alone[1].currents())
+        assert a.info().steps == 16 and c.info().steps == 8 and d.info().steps == 4
+    finally:
+        for x in (a, c, d, *alone):
+            if x is not None:
+                x.close()
