@@ -173,3 +173,29 @@ def test_energy_balance_first_order():
         imb.append((Ein - Ejoule - Emag) / Ein)
     assert abs(imb[1]) < 2e-2
     assert 1.6 < imb[0] / imb[1] < 2.4
+
+
+def test_triangle_field_drive_values():
+    """Waveform 2 of the applied field (Numerical Algorithm section: ramping
+    external field): a triangle 0 -> +Ba_max -> -Ba_max -> 0 of slope Ba_rate,
+    period P = 4 Ba_max / Ba_rate, repeated.  Values at the corners, at the
+    quarter points of each leg, across a period boundary, and the sign of the
+    slope on each leg."""
+    amp, rate = 0.1, 4.0
+    d = {"dt": 1e-4, "ramp_rate": 0.0, "I_max": 0.0, "Ba_rate": rate, "Ba_max": amp, "Ba_waveform": 2}
+    per = 4 * amp / rate
+    expect = {0.0: 0.0, per / 8: amp / 2, per / 4: amp, 3 * per / 8: amp / 2, per / 2: 0.0,
+              5 * per / 8: -amp / 2, 3 * per / 4: -amp, 7 * per / 8: -amp / 2,
+              per: 0.0, per + per / 8: amp / 2, 2 * per + 3 * per / 4: -amp}
+    for t, want in expect.items():
+        It, Ba = oracle.drive_values(t, d)
+        assert It == 0.0
+        assert abs(Ba - want) < 1e-12 * amp, (t, Ba, want)
+    eps = 1e-6 * per
+    for t0, slope in ((per / 8, rate), (per / 2, -rate), (7 * per / 8, rate), (per + per / 16, rate)):
+        s = (oracle.drive_values(t0 + eps, d)[1] - oracle.drive_values(t0 - eps, d)[1]) / (2 * eps)
+        assert abs(s - slope) < 1e-6 * rate, (t0, s, slope)
+    # the ramp waveform caps at Ba_max and the transport ramp at I_max
+    d1 = dict(d, Ba_waveform=1, ramp_rate=10.0, I_max=3.0)
+    assert oracle.drive_values(0.01, d1) == (0.1, 0.04)
+    assert oracle.drive_values(1.0, d1) == (3.0, amp)

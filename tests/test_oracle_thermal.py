@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 from oracle.thermal import ThermalGrid
@@ -90,3 +91,74 @@ def test_adi_step_against_dense_half_step_solves():
     unew = np.linalg.solve(I - dt / 2 * Az, ustar + dt / 2 * Ar @ ustar + dt / 2 * s)
     out = th.adi_step(u.reshape(Gz, Gr), q.reshape(Gz, Gr), dt).ravel()
     assert np.max(np.abs(out - unew)) < 1e-13 * np.max(np.abs(unew))
+
+
+def _fine_grid_conductance(segments, face_height, slices=4000):
+    """Brute-force 1-D steady conduction between two cell centres.
+
+    ``segments`` lists (length, conductivity) of the materials in series; each
+    is cut into equal slices, node temperatures solved with u = 1 at one end
+    and u = 0 at the other by a dense linear solve of the nodal balance (not
+    a series-resistance formula).  Returns the heat flow per unit depth
+    through a face of height ``face_height`` per unit of u difference."""
+    k_links, dx_links = [], []
+    for length, kappa in segments:
+        n = max(1, int(round(slices * length / sum(s[0] for s in segments))))
+        k_links += [kappa] * n
+        dx_links += [length / n] * n
+    cond = np.array(k_links) / np.array(dx_links)          # per link
+    m = cond.size + 1                                        # nodes
+    A = np.zeros((m, m))
+    b = np.zeros(m)
+    for i, g in enumerate(cond):
+        A[i, i] += g
+        A[i + 1, i + 1] += g
+        A[i, i + 1] -= g
+        A[i + 1, i] -= g
+    A[0, :] = 0.0
+    A[0, 0] = 1.0
+    b[0] = 1.0
+    A[-1, :] = 0.0
+    A[-1, -1] = 1.0
+    u = np.linalg.solve(A, b)
+    return cond[0] * (u[0] - u[1]) * face_height
+
+
+@pytest.mark.parametrize("layers,turns,axis", [(2, 1, 1), (1, 2, 0)])
+def test_epoxy_gap_conductance_against_fine_grid_conduction(layers, turns, axis):
+    """Two one-element wires side by side (radially, then axially), no bath,
+    no source.  In u = T^4 the heat flux is -(kappa_ref / (4 T_ref^3)) du/dx
+    in both Cu and epoxy (both follow the T^3 law), so the conductance between
+    the two cell centres is that of half a Cu cell, the epoxy gap and half a
+    Cu cell in series.  One Peaceman-Rachford step multiplies the difference
+    mode u1 - u2 by (1 - dt K / C) / (1 + dt K / C); K read off the oracle's
+    step must equal the brute-force fine-grid conduction across Cu | epoxy |
+    Cu (Methods, heat-diffusion paragraph: the composite section)."""
+    d, pitch = 0.8e-3, 0.9e-3
+    geo = oracle.solenoid_elements(layers, turns, 1, 0.02, pitch, d)
+    p = dict(P, h0=0.0)
+    th = ThermalGrid(geo, p)
+    T3 = 4.0 * p["T_ref"] ** 3
+    gap = pitch - d
+    K_fine = _fine_grid_conductance(
+        [(d / 2, p["kappa_cu"] / T3), (gap, p["kappa_ep"] / T3), (d / 2, p["kappa_cu"] / T3)], d)
+    C = p["rho_m"] * p["c0"] * d * d / 4.0                 # cell capacity per unit depth
+    dt = 1e-5
+    base, amp = 5.0 ** 4, 40.0
+    u = np.full((geo["Gz"], geo["Gr"]), base)
+    if axis == 1:
+        u[0, 0] += amp
+        u[0, 1] -= amp
+    else:
+        u[0, 0] += amp
+        u[1, 0] -= amp
+    out = th.adi_step(u, np.zeros_like(u), dt)
+    diff = (out.ravel()[0] - out.ravel()[1]) / (2 * amp)
+    K_step = C * (1.0 - diff) / (dt * (1.0 + diff))
+    assert abs(K_step - K_fine) < 1e-9 * K_fine
+    # the epoxy dominates: swapping the two conductivities or dropping the gap
+    # would move K by orders of magnitude
+    K_swapped = _fine_grid_conductance(
+        [(d / 2, p["kappa_ep"] / T3), (gap, p["kappa_cu"] / T3), (d / 2, p["kappa_ep"] / T3)], d)
+    assert abs(K_step - K_swapped) > 0.5 * K_fine
+    assert abs(K_step - p["kappa_cu"] / T3) > 0.5 * K_fine
