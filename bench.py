@@ -10,15 +10,19 @@ and current update, ADI heat step, diagnostics.  Metric: element-steps/s.
 
 Default workload: the 96,000-element real-size coil (60 x 100 turns, 4 x 4
 elements per wire), transport ramp 2 A/s, dt = 1e-5 s, synthetic seeded
-inputs, far operator in FP32.  Main leg: the operator in block-Toeplitz
-storage (the same FP32 entries as the dense 96,000^2 matrix, 0.73 GB, larger
-than the 126 MB L2, so no flush is needed between steps; the apply is bound
-by the FP32 pipe).  Beside it: the dense FP32 storage (36.9 GB, HBM-bound),
-the plain FP64 dense form (mixed/FP64 ratio), the adjoint/forward cost on the
-4,608-element field-loop coil and the 64-coil batch.  BF16 storage (--precision bf16)
+inputs.  Main leg: the far operator in the tensor-core block-Toeplitz form
+(offsets >= 0 of the C x C turn-offset blocks, each FP32-class entry stored
+as an FP16 hi + lo pair: 0.37 GB, larger than the 126 MB L2, so no flush is
+needed between steps), applied with tcgen05 MMAs fed by TMA; its roofline is
+HBM (the table streamed once per apply).  Beside it: the FP32 block-Toeplitz
+form on CUDA cores (bound by the FP32 pipe), the dense FP32 storage (36.9 GB,
+HBM-bound), the plain FP64 dense form (the mixed/FP64 ratio: storage format
+and precision change together), the adjoint/forward cost on the 4,608-element
+field-loop coil and the 64-coil batch.  BF16 storage (--precision bf16)
 rounds the operator by 2^-9 per entry, which at this size is more than its
 smallest eigenvalue: the stored operator is no longer positive definite and
-the conjugate-gradient solve breaks down, so FP32 is the mixed form here.
+the conjugate-gradient solve breaks down, so FP32-class storage is the mixed
+form here.
 
 Multi-GPU: the coil does not shard across GPUs in this build ("replicas
 only"): under torchrun each rank steps its own replica; value = all ranks'

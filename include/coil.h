@@ -160,9 +160,9 @@ typedef struct {
  * the blocks of offsets >= 0 (the others are their transposes), each entry
  * stored as two FP16 numbers hi + lo after a power-of-two scaling (about 22
  * significant bits, 4 bytes per entry: half the bytes of the FP32 Toeplitz
- * table), applied on the tensor cores to an equally split input (all four
- * products hi*hi, hi*lo, lo*hi, lo*lo) with FP32 accumulation per stage and
- * compensated sums across stages.  Unsupported shapes get COIL_ERR_INVALID.
+ * table), applied on the tensor cores to an equally split input with three
+ * products hi*hi, hi*lo and lo*hi (lo*lo, below 2^-22 of the result, is
+ * left out), FP32 accumulation per stage and compensated sums across stages.  Unsupported shapes get COIL_ERR_INVALID.
  * A bounded wait inside the apply kernel that runs out makes the step return
  * COIL_ERR_CUDA ("tensor-core apply timed out"). */
 enum { COIL_FORMAT_DENSE = 0, COIL_FORMAT_TOEPLITZ = 1, COIL_FORMAT_TOEPLITZ_TC = 2 };
@@ -312,14 +312,19 @@ coil_status coil_apply_operator(coil_t *c, const double *p, double *y);
  * the operator kernels read lives in one file-scope device array of
  * 1,048,576 doubles (8 MiB), which every device that loads the library holds
  * until the process exits.  Coils whose operator pitch (n_elem rounded up to
- * 64) exceeds 1,048,576 get COIL_ERR_INVALID.  The first call on a device
+ * 64) exceeds 1,048,576 get COIL_ERR_INVALID, and so do coils whose far
+ * operator is not in the dense format (COIL_FORMAT_TOEPLITZ and
+ * COIL_FORMAT_TOEPLITZ_TC are not accepted here).  The first call on a device
  * looks up that array's device address (one cudaGetSymbolAddress); make that
  * first call before any stream capture.  Launches go to `stream` (a
  * cudaStream_t, NULL = default stream) and the call returns without waiting;
  * d_y is ready when the stream reaches that point.  Every call shares the
  * array and it keeps the last call's contents: two calls that overlap on the
  * GPU (different streams or threads at the same time) race on it and give
- * wrong results. */
+ * wrong results.  The looked-up address is kept for the life of the process:
+ * after a cudaDeviceReset (or anything else that destroys the device's
+ * primary context) it is stale, and this entry point must not be called
+ * again in that process. */
 coil_status coil_apply_operator_static(coil_t *c, const double *d_p, double *d_y,
                                        void *stream);
 
@@ -333,6 +338,21 @@ coil_status coil_read_operator(coil_t *c, double *M);
  * With buf == NULL, *bytes receives the required size. */
 coil_status coil_save_state(coil_t *c, void *buf, size_t *bytes);
 coil_status coil_load_state(coil_t *c, const void *buf, size_t bytes);
+
+/* Test hook of the failure path of the tensor-core apply (COIL_FORMAT_
+ * TOEPLITZ_TC): the bounded waits inside its kernel that raise the kernel's
+ * abort flag give up after `cycles` SM clock cycles instead of their default
+ * (cycles = 0 restores it: 2^31 cycles, about a second).  A limit of a few
+ * cycles makes the next apply stop early on purpose: the CTA that gave up
+ * raises the flag, the others stop issuing, the copies and products already
+ * in flight are waited for (with the default limit), the tensor memory is
+ * freed and the step returns COIL_ERR_CUDA ("tensor-core apply timed out")
+ * with I, flux, T and t of the last completed step (the warm start of the
+ * next solve and the per-wire statistics may include the stopped attempt).
+ * The GPU context stays usable, and the coil steps normally once the limit
+ * is back at 0.  Other formats ignore the limit.  COIL_ERR_INVALID for
+ * cycles < 0. */
+coil_status coil_set_wait_limit(coil_t *c, long long cycles);
 
 coil_status coil_info(const coil_t *c, coil_info_t *info);
 const char *coil_last_error(const coil_t *c);

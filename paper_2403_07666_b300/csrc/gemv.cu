@@ -8,9 +8,10 @@
 // its lanes walk the row with 16-byte streaming loads (L2 evict-first, the
 // operator is read once per apply), the input vector comes through the
 // read-only path and stays L1/L2 resident.  Mixed precision stores the
-// operator in FP32 or BF16 and multiplies it with the FP32 copy of p in FP32,
-// flushing the FP32 lane partials into FP64 every 32 vectors; the row sums are
-// FP64.
+// operator in FP32 or BF16 and multiplies it with the FP32 copy of p in a
+// pure FP32 inner loop: two FP32 lane partials are folded into a second FP32
+// level every 16 unrolled iterations, and FP64 is reached only in the per-row
+// warp reduction.
 #include "common.cuh"
 
 namespace cq {
