@@ -90,6 +90,7 @@ def load_library(path=LIB_PATH):
         "coil_adjoint": ([P, C.c_long, C.POINTER(Drive), C.c_int, _dp, _dp, _dp, _dp], C.c_int),
         "coil_info": ([P, C.POINTER(Info)], C.c_int),
         "coil_reset_counters": ([P], C.c_int),
+        "coil_set_wait_limit": ([P, C.c_longlong], C.c_int),
         "coil_last_error": ([P], C.c_char_p),
         "coil_destroy": ([P], None),
     }
@@ -311,6 +312,11 @@ class Coil:
         self._check(self._lib.coil_adjoint(self._h, int(n_steps), C.byref(make_drive(drive)),
                                            int(ckpt_every), _ptr(dm), _ptr(gf), C.byref(gn), C.byref(gc)))
         return gf, gn.value, gc.value
+
+    def set_wait_limit(self, cycles):
+        """coil_set_wait_limit: test hook of the tensor-core apply's bounded
+        waits (0 = the default limit)."""
+        self._check(self._lib.coil_set_wait_limit(self._h, int(cycles)))
 
     def reset_counters(self):
         self._check(self._lib.coil_reset_counters(self._h))

@@ -1673,6 +1673,16 @@ coil_status coil_info(const coil_t* c, coil_info_t* info) {
     return COIL_OK;
 }
 
+coil_status coil_set_wait_limit(coil_t* c, long long cycles) {
+    if (!c) return COIL_ERR_INVALID;
+    if (cycles < 0) return fail(c, COIL_ERR_INVALID, "wait limit must be >= 0");
+    cudaSetDevice(c->device);
+    const long long v = cycles;
+    CK(cudaMemcpyAsync(&c->h.sc->tc_wait, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream), "wait limit");
+    CK(cudaStreamSynchronize(c->stream), "wait limit");
+    return COIL_OK;
+}
+
 coil_status coil_reset_counters(coil_t* c) {
     if (!c) return COIL_ERR_INVALID;
     c->launches = c->op_launches = c->pcg_iters = 0;

@@ -36,6 +36,7 @@ struct Scalars {
     int iter, done, status, nonpd;
     double last_resid;
     int passes;          // loop passes of a graph-launched step (a guard on its while loop)
+    long long tc_wait;   // cycles before a wait of the tensor-core apply gives up (0: its default)
 };
 
 struct CoilDev {

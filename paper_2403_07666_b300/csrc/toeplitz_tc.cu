@@ -115,22 +115,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the phase of the given parity; false on abort or after kTcWait
+// Wait for the phase of the given parity; false on abort or after `limit`
 // cycles (then the abort flag is raised).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kTcWait) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
     }
 }
 // Inline fast path for a phase that has already completed.
-__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    return mbar_try(bar, parity) || mbar_wait(bar, parity, abort_flag);
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                               long long limit) {
+    return mbar_try(bar, parity) || mbar_wait(bar, parity, abort_flag, limit);
 }
 // The same, ignoring the abort flag (used to retire work already in flight).
 __device__ __noinline__ bool mbar_wait_final(uint32_t bar, uint32_t parity, long long limit) {
@@ -217,6 +218,9 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               const int* __restrict__ pexp, float* __restrict__ part) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
+    // the limit of the waits that raise the abort flag (a test hook can shorten
+    // it; the waits that retire work already in flight keep kTcWait)
+    const long long wlim = c.sc->tc_wait > 0 ? c.sc->tc_wait : kTcWait;
     extern __shared__ uint8_t tc_smem[];
     const uint32_t raw = su32(tc_smem);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -299,7 +303,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (sg != wk.y && D == 0) cb = (cb + 1 == sh.n_ct ? 0 : cb + 1);
             const int nk = min(2, sh.n_kb - 2 * cb);
             if (sg == wk.y || D == 0) {                 // a new column tile: its staged copy of p
-                ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag);
+                ok = mbar_wait(b_empty + 8u * sb, pb ^ 1u, abort_flag, wlim);
                 if (!ok) break;
                 mbar_expect_tx(b_full + 8u * sb, b_stage);
                 // turn rows -kTcPad .. NT + kTcPadTop - 1, hi and lo, of 16 chunks
@@ -311,7 +315,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             for (int sgn = 0; sgn < (D > 0 ? 2 : 1) && ok; ++sgn)
                 for (int j = 0; j < nk && ok; ++j) {
                     const int kb = 2 * cb + j, d = sgn ? -D : D;
-                    ok = mbar_wait_fast(a_empty + 8u * sa, pa ^ 1u, abort_flag);
+                    ok = mbar_wait_fast(a_empty + 8u * sa, pa ^ 1u, abort_flag, wlim);
                     if (!ok) break;
                     mbar_expect_tx(a_full + 8u * sa, kTcAStage);
                     // offset d >= 0: T_d tile, K-major; d < 0: T_d = T_{-d}^T, the stored tile
@@ -348,7 +352,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const int nk = min(2, sh.n_kb - 2 * cb);
             if (sg == wk.y || D == 0) {
                 if (sg != wk.y) mma_commit(b_empty);    // free once this issuer's MMAs on it finish
-                ok = mbar_wait(b_full, (uint32_t)grp & 1u, abort_flag);
+                ok = mbar_wait(b_full, (uint32_t)grp & 1u, abort_flag, wlim);
                 if (!ok) break;
                 ++grp;
                 tc_fence_after();
@@ -370,8 +374,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 // every stage up to there has completed its MMAs, so (S >= n_acc) the
                 // previous load of this stage's slot has landed and the parity wait
                 // below cannot be satisfied by the phase before it (another issuer's)
-                ok = mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag);
-                if (ok) ok = mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag);
+                ok = mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag, wlim);
+                if (ok) ok = mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag, wlim);
                 if (!ok) break;
                 tc_fence_after();
                 const int t_first = d > 0 ? d : 0;
@@ -437,7 +441,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const int nk = min(2, sh.n_kb - 2 * cb);
             for (int st = 0; st < (D > 0 ? 2 : 1) * nk; ++st) {
                 const int d = st >= nk ? -D : D;
-                ok = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag));
+                ok = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag, wlim));
                 if (!ok) break;
                 pf ^= 1u << ai;
                 tc_fence_after();
