@@ -6,7 +6,7 @@
 // it in one file-scope device array instead, so a call needs no allocation at
 // all: the caller passes its own N-long device input and output.
 //
-// The array is COIL_STATIC_MAX_LD doubles (8 MiB) in every device that loads
+// The array is kStaticMaxLd = 2^20 doubles (8 MiB) in every device that loads
 // the library, held until the process exits.  All calls share it and it keeps
 // the last call's contents; the padding past N is cleared on every call.
 // Two calls that overlap on the GPU (different streams, or different handles
@@ -57,8 +57,14 @@ __global__ void k_static_pad(const double* __restrict__ p, int N, long long ld, 
 
 __device__ __forceinline__ float static_bf16(unsigned short v) { return __uint_as_float((unsigned)v << 16); }
 
+// Entries a lane adds into its inner FP32 partial before folding it into the
+// outer one (two FP32 levels, as the regular FP32/BF16 apply keeps them, so
+// that the rounding does not grow with the row length).
+constexpr int kStaticFold = 16;
+
 // y = M_far p (one warp per row; FP64 storage multiplies in FP64, FP32/BF16
-// storage in FP32 with FP32 lane partials and an FP64 warp reduction).
+// storage in FP32 with two levels of FP32 lane partials and an FP64 warp
+// reduction).
 __global__ void k_static_far(const CoilDev* __restrict__ cds, const void* __restrict__ pin,
                              double* __restrict__ y) {
     const CoilDev& c = cds[0];
@@ -72,15 +78,21 @@ __global__ void k_static_far(const CoilDev* __restrict__ cds, const void* __rest
         for (long long j = lane; j < c.ld; j += 32) s = fma(M[j], p[j], s);
     } else {
         const float* p = static_cast<const float*>(pin);
-        float f = 0.f;
-        if (c.precision == PREC_FP32) {
-            const float* M = static_cast<const float*>(c.Mfar) + (size_t)row * c.ld;
-            for (long long j = lane; j < c.ld; j += 32) f = fmaf(M[j], p[j], f);
-        } else {
-            const unsigned short* M = static_cast<const unsigned short*>(c.Mfar) + (size_t)row * c.ld;
-            for (long long j = lane; j < c.ld; j += 32) f = fmaf(static_bf16(M[j]), p[j], f);
+        const bool f32 = c.precision == PREC_FP32;
+        const float* M32 = static_cast<const float*>(c.Mfar) + (size_t)row * c.ld;
+        const unsigned short* M16 = static_cast<const unsigned short*>(c.Mfar) + (size_t)row * c.ld;
+        float f = 0.f, outer = 0.f;
+        int k = 0;
+        for (long long j = lane; j < c.ld; j += 32) {
+            float m = f32 ? M32[j] : static_bf16(M16[j]);
+            f = fmaf(m, p[j], f);
+            if (++k == kStaticFold) {
+                outer += f;
+                f = 0.f;
+                k = 0;
+            }
         }
-        s = (double)f;
+        s = (double)outer + (double)f;
     }
     s = warp_sum(s);
     if (lane == 0) y[row] = s;
