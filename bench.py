@@ -378,30 +378,17 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": int(inf.descriptor_bytes) + 48,
            "d2h_bytes_per_step": 4 * N * 8 + 8}
 
-    fp64 = None
-    if args.fp64_steps > 0 and args.precision != "fp64":
-        coil.close()
-        c64 = Coil.from_workload(w, precision="fp64", rtol=args.rtol, device=local_rank,
-                                 stream=stream.cuda_stream)
-        c64.step(1, drive)
-        s64 = timed_steps(c64, drive, args.fp64_steps, stream, torch)
-        v64, s64 = job_throughput(s64, N * args.fp64_steps, dist, "cuda")
-        # the mixed form over the same steps from the same start: moment and current error
-        n64 = 1 + args.fp64_steps
-        cm = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
-                                stream=stream.cuda_stream, format=args.format)
-        cm.step(n64, drive)
-        m64, mm = c64.diag(0, n64)[:, 3], cm.diag(0, n64)[:, 3]
-        I64, Im = c64.currents(), cm.currents()
-        cm.close()
-        fp64 = {"value": v64, "ms_per_step": 1e3 * s64 / args.fp64_steps,
-                "steps": args.fp64_steps,
-                "mixed_moment_rel_err": float(np.max(np.abs(mm - m64)) / max(np.max(np.abs(m64)), 1e-300)),
-                "mixed_current_rel_err": float(np.linalg.norm(Im - I64) / max(np.linalg.norm(I64), 1e-300)),
-                "compared_steps": n64}
-        c64.close()
-    else:
-        coil.close()
+    coil.close()
+    # the same coil from a state well into a scaled ramp (flux flow under way):
+    # the mixed form timed over a window there, then the plain FP64 form and
+    # the mixed form stepped side by side from that state
+    traj_real = mid_window = None
+    if args.traj_steps > 0 and args.precision != "fp64":
+        mid_window, traj_real = real_trajectory_leg(args, local_rank, stream, torch, w)
+    traj_mid = None
+    if args.traj_mid_steps > 0 and args.precision != "fp64":
+        traj_mid = trajectory_leg(args, local_rank, stream, torch, wl.mid_coil(), MID_RAMP, 0,
+                                  args.traj_mid_steps)
 
     batched = batch_leg(args, local_rank, stream, torch, rank, world, dist) if args.batch_steps > 0 else None
     if rank != 0:
@@ -430,9 +417,19 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-    if fp64 is not None:
-        line["fp64"] = fp64
-        line["mixed_over_fp64"] = value / fp64["value"]
+    if mid_window is not None:
+        line["windows"] = {"start": {"start_step": args.warmup, "ramp_A_per_s": drive["ramp_rate"],
+                                     "value": value, "ms_per_step": 1e3 * secs / args.steps,
+                                     "applies_per_step": applies},
+                           "mid_ramp": mid_window}
+    if traj_real is not None:
+        line["fp64"] = traj_real
+        line["mixed_over_fp64"] = traj_real["mixed_value"] / traj_real["value"]
+        line["mixed_over_fp64_note"] = ("tensor-core block-Toeplitz operator (FP16 hi/lo, FP32-class) with the FP32 "
+                                        "pointwise chain against the dense FP64 operator with the FP64 chain, on the "
+                                        "same steps from the same state: storage format and precision change together")
+    if traj_mid is not None:
+        line["fp64_mid"] = traj_mid
     if args.other_format and args.precision == "fp32":
         line["other_formats"] = {f: format_leg(args, local_rank, stream, torch, f)
                                  for f in ("toeplitz_tc", "toeplitz", "dense") if f != args.format}
@@ -559,27 +556,153 @@ def subelement_leg(args, local_rank, stream, torch):
 
 
 def adjoint_leg(args, local_rank, stream, torch):
-    """Adjoint / forward cost on the 4,608-element field-loop coil."""
+    """Adjoint / forward cost on the 4,608-element field-loop coil (one full
+    triangle loop of the applied field in 1000 steps of 1e-4 s, checkpoints
+    every 50 steps), in the headline operator form and in the plain FP64
+    form.  The loss is a magnetization-loop term on the moment series plus a
+    soft maximum of the Joule-power series (the quench-onset term)."""
     from paper_2403_07666_b300.coil import Coil
     w = wl.adjoint_coil()
     K = args.adjoint_steps
+    out = {"workload": w.name, "n_elem": w.n_elem, "steps": K, "checkpoint_every": 50,
+           "loss": "sum (m_k - m_target)^2 + soft maximum of the Joule power P_k",
+           "note": "adjoint_s includes the checkpointed forward pass and the segment recomputation"}
+    forms = [(args.format, {"precision": args.precision, "format": args.format})]
+    if args.format != "dense" or args.precision != "fp64":
+        forms.append(("fp64", {"precision": "fp64"}))
+    for name, kw in forms:
+        c = Coil.from_workload(w, rtol=args.rtol, device=local_rank, stream=stream.cuda_stream, **kw)
+        s0 = c.save_state()
+        c.step(3, w.drive)
+        c.load_state(s0)
+        fwd = timed_steps(c, w.drive, K, stream, torch)
+        d = c.diag(0, K)
+        m, P = d[:, 3], d[:, 4]
+        target = 0.95 * m
+        scale = 0.05 * max(float(np.max(P)), 1e-300)
+        z = P / scale
+        wts = np.exp(z - np.max(z))
+        dLdP = wts / np.sum(wts)
+        c.load_state(s0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.adjoint_losses(K, w.drive, 2.0 * (m - target), dLdP, ckpt_every=50)
+        torch.cuda.synchronize()
+        adj = time.perf_counter() - t0
+        c.close()
+        out[name] = {"forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd}
+    out["adjoint_over_forward"] = out[args.format]["adjoint_over_forward"]
+    return out
+
+
+# Scaled transport ramps of the trajectory legs (the configurations' ramps
+# reach only a few amperes in their step windows; x1000 brings the coils into
+# flux flow and past their first flux jump within a few thousand steps: the
+# 96,000-element coil's first jump at 2000 A/s comes near step 1990, the
+# 51,200-element coil's at 5000 A/s near step 970).
+REAL_RAMP = 2000.0
+MID_RAMP = 5000.0
+
+
+def c13_errors(got, ref, T_bath, m_scale):
+    """Per-step errors of the mixed form against the FP64 form: J, B and the
+    heating T - T_bath relative to the step's maximum (the heating with a
+    floor of 1e-6 T_bath), the moment relative to the largest |m| so far."""
+    def rel(a, b):
+        sc = np.max(np.abs(b))
+        return float(np.max(np.abs(a - b)) / sc) if sc > 0 else float(np.max(np.abs(a - b)))
+    eJ = rel(got["J"], ref["J"])
+    eB = max(rel(got["Br"], ref["Br"]), rel(got["Bz"], ref["Bz"]))
+    eT = float(np.max(np.abs(got["T"] - ref["T"])) / max(np.max(np.abs(ref["T"] - T_bath)), 1e-6 * T_bath))
+    em = abs(got["moment"] - ref["moment"]) / max(m_scale, 1e-300)
+    return eJ, eB, eT, em
+
+
+C13_BOUNDS = {"J": 1e-3, "B": 1e-4, "T": 1e-3, "m": 1e-4}
+
+
+def trajectory_leg(args, local_rank, stream, torch, w, ramp, pre_steps, steps, state=None):
+    """The mixed form (tensor-core operator) and the plain FP64 form (dense
+    FP64 operator) stepped side by side on a scaled ramp, from t = 0 or from
+    a saved state; every step's J, B, T and moment compared (C-13 bounds)."""
+    from paper_2403_07666_b300.coil import Coil
+    d = dict(w.drive, ramp_rate=ramp)
+    T_bath = w.material["T_bath"]
+    cm = Coil.from_workload(w, precision="fp32", format="toeplitz_tc", rtol=args.rtol, device=local_rank,
+                            stream=stream.cuda_stream)
+    c64 = Coil.from_workload(w, precision="fp64", rtol=args.rtol, device=local_rank, stream=stream.cuda_stream)
+    if state is not None:
+        cm.load_state(state)
+        c64.load_state(state)
+    elif pre_steps > 0:
+        cm.step(pre_steps, d)
+        st = cm.save_state()
+        c64.load_state(st)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t64 = tm = 0.0
+    worst = {"J": 0.0, "B": 0.0, "T": 0.0, "m": 0.0}
+    m_scale = 0.0
+    max_jr = 0.0
+    c64.reset_counters()
+    cm.reset_counters()
+    for _ in range(steps):
+        ev[0].record(stream)
+        c64.step(1, d)
+        ev[1].record(stream)
+        cm.step(1, d)
+        ev[2].record(stream)
+        ref, got = c64.read(d), cm.read(d)
+        torch.cuda.synchronize()
+        t64 += ev[0].elapsed_time(ev[1]) / 1e3
+        tm += ev[1].elapsed_time(ev[2]) / 1e3
+        m_scale = max(m_scale, abs(ref["moment"]))
+        for k, e in zip(("J", "B", "T", "m"), c13_errors(got, ref, T_bath, m_scale)):
+            worst[k] = max(worst[k], e)
+    dg = c64.diag()
+    max_jr = float(np.max(dg[-steps:, 6]))
+    fj, _ = c64.onsets()
+    fjm, _ = cm.onsets()
+    i64, im = c64.info(), cm.info()
+    N = cm.N
+    out = {"workload": w.name, "n_elem": N, "ramp_A_per_s": ramp,
+           "start_step": int(i64.steps) - steps, "compared_steps": steps,
+           "value": N * steps / t64, "ms_per_step": 1e3 * t64 / steps,
+           "applies_per_step": int(i64.operator_launches) / steps,
+           "mixed_value": N * steps / tm, "mixed_ms_per_step": 1e3 * tm / steps,
+           "mixed_applies_per_step": int(im.operator_launches) / steps,
+           "max_rel_err": worst, "bounds": C13_BOUNDS,
+           "within_bounds": all(worst[k] <= C13_BOUNDS[k] for k in C13_BOUNDS),
+           "max_J_over_Jc": max_jr,
+           "wires_jumped": {"fp64": int((fj >= 0).sum()), "mixed": int((fjm >= 0).sum())},
+           "first_jump_step": {"fp64": int(fj[fj >= 0].min()) if (fj >= 0).any() else -1,
+                               "mixed": int(fjm[fjm >= 0].min()) if (fjm >= 0).any() else -1},
+           "timed": "CUDA events around every step of each form (state read back between steps, not timed)"}
+    cm.close()
+    c64.close()
+    return out
+
+
+def real_trajectory_leg(args, local_rank, stream, torch, w):
+    """The bench coil from a state well into the scaled ramp: a timed window
+    of the mixed form there, then the FP64 comparison from the same state."""
+    from paper_2403_07666_b300.coil import Coil
+    d = dict(w.drive, ramp_rate=REAL_RAMP)
     c = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
-                           stream=stream.cuda_stream)
-    s0 = c.save_state()
-    c.step(3, w.drive)
-    c.load_state(s0)
-    fwd = timed_steps(c, w.drive, K, stream, torch)
-    m = c.diag(0, K)[:, 3]
-    c.load_state(s0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    c.adjoint(K, w.drive, 2.0 * m, ckpt_every=50)
-    torch.cuda.synchronize()
-    adj = time.perf_counter() - t0
+                           stream=stream.cuda_stream, format=args.format)
+    c.step(args.traj_pre, d)
+    state = c.save_state()
+    c.step(args.warmup, d)
+    c.reset_counters()
+    secs = timed_steps(c, d, args.steps, stream, torch)
+    inf = c.info()
+    N = c.N
+    window = {"start_step": args.traj_pre + args.warmup, "ramp_A_per_s": REAL_RAMP, "steps": args.steps,
+              "value": N * args.steps / secs, "ms_per_step": 1e3 * secs / args.steps,
+              "applies_per_step": int(inf.operator_launches) / args.steps,
+              "max_J_over_Jc": float(np.max(c.diag()[-args.steps:, 6]))}
     c.close()
-    return {"workload": w.name, "n_elem": w.n_elem, "steps": K, "checkpoint_every": 50,
-            "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd,
-            "note": "adjoint_s includes the checkpointed forward pass and the segment recomputation"}
+    traj = trajectory_leg(args, local_rank, stream, torch, w, REAL_RAMP, 0, args.traj_steps, state=state)
+    return window, traj
 
 
 def batch_leg(args, local_rank, stream, torch, rank=0, world=1, dist=None):
@@ -648,12 +771,17 @@ def main():
     ap.add_argument("--workload", default="real", choices=["real", "mid", "small", "prof"])
     ap.add_argument("--precision", default="fp32", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--rtol", type=float, default=1e-9)
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--traj-pre", type=int, default=1900,
+                    help="steps of the mixed form on the scaled ramp before the mid-ramp window and the FP64 comparison")
+    ap.add_argument("--traj-steps", type=int, default=200,
+                    help="steps of the plain FP64 form beside the mixed form from the mid-ramp state (0: skip)")
+    ap.add_argument("--traj-mid-steps", type=int, default=1100,
+                    help="steps of the FP64 / mixed comparison on the 51,200-element coil from t = 0 (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--format", default="toeplitz_tc", choices=["toeplitz_tc", "toeplitz", "dense"],
                     help="storage of the far operator in the main leg")
     ap.add_argument("--other-format", type=int, default=1, help="also time the other operator formats")
-    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-steps", type=int, default=1000)
     ap.add_argument("--lorentz", type=int, default=1, help="also time the step with the Lorentz hoop strain")
     ap.add_argument("--subelements", type=int, default=1, help="also time the step with subelement decoupling")
     ap.add_argument("--batch-steps", type=int, default=5)

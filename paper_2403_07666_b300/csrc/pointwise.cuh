@@ -83,4 +83,76 @@ __device__ __forceinline__ void ej_law(const CoilDev& c, int fil, double J, doub
     }
 }
 
+// ------------------------------------------------- FP32 forms (mixed mode)
+//
+// The mixed form (far operator stored in FP32 or as FP16 hi/lo pairs) takes
+// the field and the constitutive chain in FP32, as its precision plan says:
+// the stencil's flux differences are summed in FP64 (they cancel across one
+// element) and only then rounded, T, Jc, the E-J law's logarithm and
+// exponential, rho/rho_n and its derivative are FP32; the currents, the
+// products that form G, R and q, and every accumulation stay FP64.  B300's
+// FP64 pipe issues two thread-operations per SM per clock, so the FP64
+// logarithms, exponentials, divisions and square roots of this chain bound
+// the FP64 kernel; in FP32 they run on the 128-lane pipe.  The E-J law
+// amplifies a relative error of Jc by n in E, but the current that the solve
+// returns moves by about the error of Jc itself (J ~ Jc (E/E0)^(1/n)).
+
+// B_r, B_z at element e in FP32 from FP64 stencil sums.
+__device__ __forceinline__ void field_at_f(const CoilDev& c, int e, double Ba, float* Br, float* Bz) {
+    int g = c.elem_grid[e];
+    int iz = g / c.Gr, ir = g - iz * c.Gr;
+    double dr = 0.0, dz = 0.0;
+    int j0 = c.sr_j0[ir];
+    for (int k = 0; k < 3; ++k) {
+        double wk = c.sr_w[3 * ir + k];
+        if (wk != 0.0) dr += wk * phi_total(c, iz * c.Gr + j0 + k, Ba);
+    }
+    j0 = c.sz_j0[iz];
+    for (int k = 0; k < 3; ++k) {
+        double wk = c.sz_w[3 * iz + k];
+        if (wk != 0.0) dz += wk * phi_total(c, (j0 + k) * c.Gr + ir, Ba);
+    }
+    const float inv = 1.0f / (float)(2.0 * kPi * c.r[e]);
+    *Bz = (float)dr * inv;
+    *Br = -(float)dz * inv;
+}
+
+__device__ __forceinline__ float strain_power_f(const CoilDev& c, int e, double r, double J, float Bz) {
+    if (c.inv_Y == 0.0) return (float)c.strain_pow[e];
+    const float eps = (float)c.strain[e] + (float)(r * J * c.inv_Y) * Bz;
+    return powf(fabsf(eps), (float)c.p_eps);
+}
+
+__device__ __forceinline__ float critical_current_f(const CoilDev& c, float Bm, float T, float pe, float f) {
+    if (c.jc_model == 1) return f * (float)c.Jc0;
+    const float tr = T / (float)c.Tc;
+    const float Bc2 = (float)c.Bc2_0 * (1.0f - tr * tr);
+    if (!(T < (float)c.Tc && Bm < Bc2)) return 0.0f;
+    const float strain = fmaxf(0.0f, 1.0f - (float)c.C_eps * pe);
+    const float bfac = 1.0f - Bm / Bc2;
+    const float omt = 1.0f - tr;
+    return f * (float)c.Jc0 * (omt * sqrtf(omt)) * (bfac * bfac) / sqrtf(Bm + (float)c.B_reg) * strain;
+}
+
+__device__ __forceinline__ void ej_law_f(const CoilDev& c, int fil, float aJ, float Jc, float* frac, float* dfac,
+                                         float* jrat) {
+    if (!fil) { *frac = 1.0f; *dfac = 1.0f; *jrat = 0.0f; return; }
+    if (Jc <= 0.0f) { *frac = 1.0f; *dfac = 1.0f; *jrat = aJ > 0.0f ? __int_as_float(0x7f800000) : 0.0f; return; }
+    *jrat = aJ / Jc;
+    if (aJ == 0.0f) { *frac = 0.0f; *dfac = 0.0f; return; }
+    const float n = (float)c.nexp;
+    const float ell = logf((float)c.E0 / (Jc * (float)c.rho_n)) + (n - 1.0f) * logf(aJ / Jc);
+    if (ell > 0.0f) {
+        const float t = expf(-ell);
+        const float opt = 1.0f + t;
+        *frac = 1.0f / opt;
+        *dfac = (1.0f + n * t) / (opt * opt);
+    } else {
+        const float s = expf(ell);
+        const float ops = 1.0f + s;
+        *frac = s / ops;
+        *dfac = s * (s + n) / (ops * ops);
+    }
+}
+
 }  // namespace cq

@@ -61,6 +61,80 @@ __device__ __forceinline__ void wire_detectors(const CoilDev& c, int w, long lon
     ws[2 * W + w] = fmax(ws[2 * W + w], qmx);
 }
 
+// Rows a2 and a5 for element e from the start-of-step state: the field from
+// the loop-flux stencil, T, Jc(B, T, eps), the E-J law; writes G, R, the
+// Joule source on the thermal grid and (subelements) the resistive voltage
+// of J_I, and returns what the per-wire reductions need.  F32: the mixed
+// form's FP32 chain (see pointwise.cuh); the element's u = T^4 is returned
+// in place of T, so that the wire's maximum takes one FP64 fourth root.
+struct ElemOut {
+    double I, pj, tq, q, jrat, frac;   // tq: T (FP64 chain) or u = T^4 (F32)
+    int fil;
+};
+
+template <bool F32>
+__device__ __forceinline__ ElemOut pointwise_element(const CoilDev& c, int e, double Ba0, double dBa) {
+    ElemOut o;
+    const double r = c.r[e], a = c.area[e];
+    const int fil = c.mat[e];
+    const double I = c.I[e];
+    double J, frac, dfac, jrat, inv_a;
+    if (!F32) {
+        double Br = 0.0, Bz = 0.0, T = c.T_bath;
+        if (c.has_grid) {
+            field_at(c, e, Ba0, &Br, &Bz);
+            T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
+        }
+        const double Bm = sqrt(Br * Br + Bz * Bz);
+        J = I / a;
+        const double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
+        ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
+        o.tq = T;
+        inv_a = 0.0;
+    } else {
+        float Br = 0.0f, Bz = 0.0f, T = (float)c.T_bath;
+        double u = c.T_bath * c.T_bath * c.T_bath * c.T_bath;
+        if (c.has_grid) {
+            field_at_f(c, e, Ba0, &Br, &Bz);
+            u = c.uT[c.elem_grid[e]];
+            T = sqrtf(sqrtf((float)u));
+        }
+        const float Bm = sqrtf(Br * Br + Bz * Bz);
+        inv_a = rcp_nr(a);
+        J = I * inv_a;
+        const float Jc = fil ? critical_current_f(c, Bm, T, strain_power_f(c, e, r, J, Bz), (float)c.jc_factor[e])
+                             : 0.0f;
+        float ff, df, jf;
+        ej_law_f(c, fil, fabsf((float)J), Jc, &ff, &df, &jf);
+        frac = ff;
+        dfac = df;
+        jrat = jf;
+        o.tq = u;
+    }
+    const double rho = c.rho_n * frac;
+    const double E = rho * J;
+    const double q = E * J;
+    c.G[e] = F32 ? 2.0 * kPi * r * (c.rho_n * dfac) * inv_a : 2.0 * kPi * r * (c.rho_n * dfac) / a;
+    c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
+    if (c.n_groups)                                   // resistive voltage of J_I
+        c.xI[e] = F32 ? 2.0 * kPi * r * rho * c.Itr[e] * inv_a : 2.0 * kPi * r * rho * c.Itr[e] / a;
+    if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
+    o.I = I;
+    o.pj = q * 2.0 * kPi * r * a;
+    o.q = q;
+    o.jrat = jrat;
+    o.frac = frac;
+    o.fil = fil;
+    return o;
+}
+
+// The wire's maximum temperature from the maximum of tq (the fourth root of
+// a maximum of u is the maximum of the fourth roots).
+template <bool F32>
+__device__ __forceinline__ double wire_tmax(double tq) {
+    return F32 ? sqrt(sqrt(tq)) : tq;
+}
+
 // One warp per block (wire).  Partials: P[0] Joule power, P[1] max |J|/Jc,
 // P[2] mean rho/rho_n of filament elements.
 __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
@@ -69,6 +143,7 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (w >= c.W || c.B <= kSegMax) return;
+    const bool F32 = c.precision != PREC_FP64;      // the mixed form's FP32 chain
     Scalars* sc = c.sc;
     double t0 = sc->t, dt = c.dt, t1 = t0 + dt;
     double It1 = drive_current(c, t1);
@@ -80,39 +155,20 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
     }
     double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
     for (int k = lane; k < c.B; k += 32) {
-        int e = w * c.B + k;
-        double r = c.r[e], a = c.area[e];
-        double Br = 0.0, Bz = 0.0, T = c.T_bath;
-        if (c.has_grid) {
-            field_at(c, e, Ba0, &Br, &Bz);
-            T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
-        }
-        double Bm = sqrt(Br * Br + Bz * Bz);
-        int fil = c.mat[e];
-        double I = c.I[e];
-        double J = I / a;
-        double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
-        double frac, dfac, jrat;
-        ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
-        double rho = c.rho_n * frac;
-        double E = rho * J;
-        double q = E * J;
-        c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
-        c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
-        if (c.n_groups) c.xI[e] = 2.0 * kPi * r * rho * c.Itr[e] / a;   // resistive voltage of J_I
-        if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
-        sumI += I;
-        pj += q * 2.0 * kPi * r * a;
-        tmx = fmax(tmx, T);
-        qmx = fmax(qmx, q);
-        if (fil) { jr = fmax(jr, jrat); rhof += frac; nfil += 1.0; }
+        const ElemOut o = F32 ? pointwise_element<true>(c, w * c.B + k, Ba0, dBa)
+                              : pointwise_element<false>(c, w * c.B + k, Ba0, dBa);
+        sumI += o.I;
+        pj += o.pj;
+        tmx = fmax(tmx, o.tq);
+        qmx = fmax(qmx, o.q);
+        if (o.fil) { jr = fmax(jr, o.jrat); rhof += o.frac; nfil += 1.0; }
     }
     sumI = warp_sum(sumI);
     pj = warp_sum(pj);
     jr = warp_max(jr);
     rhof = warp_sum(rhof);
     nfil = warp_sum(nfil);
-    tmx = warp_max(tmx);
+    tmx = F32 ? wire_tmax<true>(warp_max(tmx)) : warp_max(tmx);
     qmx = warp_max(qmx);
     if (lane == 0) {
         c.cw[w] = c.constrained[w] ? (It1 - sumI) / dt : 0.0;
@@ -976,33 +1032,14 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         sc->nonpd = 0;                         // k_factor of this step sets it again if needed
     }
     double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
+    const bool F32 = c.precision != PREC_FP64;      // the mixed form's FP32 chain
     if (s.ev) {
-        const int e = s.e;
-        double r = c.r[e], a = c.area[e];
-        double Br = 0.0, Bz = 0.0, T = c.T_bath;
-        if (c.has_grid) {
-            field_at(c, e, Ba0, &Br, &Bz);
-            T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
-        }
-        double Bm = sqrt(Br * Br + Bz * Bz);
-        int fil = c.mat[e];
-        double I = c.I[e];
-        double J = I / a;
-        double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
-        double frac, dfac, jrat;
-        ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
-        double rho = c.rho_n * frac;
-        double E = rho * J;
-        double q = E * J;
-        c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
-        c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
-        if (c.n_groups) c.xI[e] = 2.0 * kPi * r * rho * c.Itr[e] / a;   // resistive voltage of J_I
-        if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
-        sumI = I;
-        pj = q * 2.0 * kPi * r * a;
-        tmx = T;
-        qmx = q;
-        if (fil) { jr = jrat; rhof = frac; nfil = 1.0; }
+        const ElemOut o = F32 ? pointwise_element<true>(c, s.e, Ba0, dBa) : pointwise_element<false>(c, s.e, Ba0, dBa);
+        sumI = o.I;
+        pj = o.pj;
+        tmx = o.tq;
+        qmx = o.q;
+        if (o.fil) { jr = o.jrat; rhof = o.frac; nfil = 1.0; }
     }
     sumI = seg_sum(sumI, s.Bp);
     pj = seg_sum(pj, s.Bp);
@@ -1010,6 +1047,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
     rhof = seg_sum(rhof, s.Bp);
     nfil = seg_sum(nfil, s.Bp);
     tmx = seg_max(tmx, s.Bp);
+    if (F32) tmx = wire_tmax<true>(tmx);
     qmx = seg_max(qmx, s.Bp);
     if (s.kk == 0 && s.wv) {
         const int w = s.w;
