@@ -253,6 +253,18 @@ coil_status coil_adjoint(coil_t *c, long n_steps, const coil_drive *drive, int c
                          const double *dL_dm, double *g_jc_factor, double *g_n,
                          double *g_C_eps);
 
+/* The adjoint of coil_adjoint for a loss on two per-step series: dL_dm[k]
+ * as above (the moment after step k+1) and dL_dP[k], the derivative of the
+ * loss with respect to the Joule power P_k = sum q 2 pi r a of the start
+ * state of step k (column 4 of the diagnostic records; it rises steeply when
+ * filaments go normal, so a soft maximum of P over the steps is a smooth
+ * quench-onset loss: Quenches Propagation section, the Joule heat released
+ * from the onset of the rise of rho to the quench).  Either array may be
+ * NULL (not both); everything else as coil_adjoint. */
+coil_status coil_adjoint_losses(coil_t *c, long n_steps, const coil_drive *drive, int ckpt_every,
+                                const double *dL_dm, const double *dL_dP, double *g_jc_factor,
+                                double *g_n, double *g_C_eps);
+
 /* Copy the current state to host buffers of N doubles (NULL = skip): current
  * density J [A/m^2], B_r, B_z [T] from the stencil of the loop flux, T [K];
  * and the moment sum(pi r^2 I) [A m^2].  `Ba` is the applied field at the

@@ -24,6 +24,9 @@ real-size multifilamentary superconducting coil"):
 * ``step``         the per-step constrained solve (A-V transport constraint)
                    solved exactly by Cholesky + Schur complement, and the
                    linearly-implicit Euler time step
+* ``tangent``      forward-mode derivatives of the step series (moment and
+                   Joule power) with respect to the calibration parameters,
+                   by the complex step (the adjoint's reference)
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
 against closed forms, library special functions, brute force or invariants.

@@ -88,6 +88,7 @@ def load_library(path=LIB_PATH):
         "coil_load_state": ([P, P, C.c_size_t], C.c_int),
         "coil_set_params": ([P, _dp, C.c_double, C.c_double], C.c_int),
         "coil_adjoint": ([P, C.c_long, C.POINTER(Drive), C.c_int, _dp, _dp, _dp, _dp], C.c_int),
+        "coil_adjoint_losses": ([P, C.c_long, C.POINTER(Drive), C.c_int, _dp, _dp, _dp, _dp, _dp], C.c_int),
         "coil_info": ([P, C.POINTER(Info)], C.c_int),
         "coil_reset_counters": ([P], C.c_int),
         "coil_set_wait_limit": ([P, C.c_longlong], C.c_int),
@@ -311,6 +312,20 @@ class Coil:
         gc = C.c_double()
         self._check(self._lib.coil_adjoint(self._h, int(n_steps), C.byref(make_drive(drive)),
                                            int(ckpt_every), _ptr(dm), _ptr(gf), C.byref(gn), C.byref(gc)))
+        return gf, gn.value, gc.value
+
+    def adjoint_losses(self, n_steps, drive, dL_dm=None, dL_dP=None, ckpt_every=50):
+        """coil_adjoint_losses: gradients of a loss on the moment series
+        (dL_dm) and the Joule-power series (dL_dP, per step's start state)."""
+        dm = None if dL_dm is None else np.ascontiguousarray(dL_dm, dtype=np.float64)
+        dp = None if dL_dP is None else np.ascontiguousarray(dL_dP, dtype=np.float64)
+        gf = np.empty(self.N)
+        gn = C.c_double()
+        gc = C.c_double()
+        self._check(self._lib.coil_adjoint_losses(self._h, int(n_steps), C.byref(make_drive(drive)),
+                                                  int(ckpt_every), None if dm is None else _ptr(dm),
+                                                  None if dp is None else _ptr(dp), _ptr(gf), C.byref(gn),
+                                                  C.byref(gc)))
         return gf, gn.value, gc.value
 
     def set_wait_limit(self, cycles):

@@ -1,5 +1,6 @@
 // Reverse (adjoint) kernels of the coupled step, for gradients of a loss on
-// the moment series with respect to the calibration parameters: per-element
+// the moment series and the Joule-power series with respect to the
+// calibration parameters: per-element
 // Jc factor f, the creep exponent n and the strain coefficient C_eps (the
 // paper calibrates its E-J and Jc laws against a measured magnetization loop,
 // Methods).
@@ -178,7 +179,9 @@ __device__ EJD ej_with_derivatives(const CoilDev& c, int fil, double J, double J
 }
 
 // Per wire (one warp): reverse of the pointwise kernel and of the constraint.
-__global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab) {
+// wP = dL/dP of the step's Joule power P = sum q 2 pi r a (its diagnostic
+// record), which adds wP 2 pi r a to lam_q of every element.
+__global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, double wP) {
     const CoilDev& c = cds[0];
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -210,7 +213,7 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab) {
         double mu = c.x[e];
         double lamG = -dt * mu * ab.xk[e];
         double lamR = -mu;
-        double lamq = (c.has_grid && c.thermal) ? ab.lamQ[g] : 0.0;
+        double lamq = ((c.has_grid && c.thermal) ? ab.lamQ[g] : 0.0) + wP * 2.0 * kPi * r * a;
         double lamE = 2.0 * kPi * r * lamR + lamq * J;
         double dGdJ = (fil && jd.Jc > 0.0 && J != 0.0) ? Kg * ej.A2 * (n - 1.0) / J : 0.0;
         double lamJ = lamq * E + lamE * rho_n * ej.dfac + lamG * dGdJ;
@@ -353,9 +356,9 @@ void launch_adj_setup(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cud
     k_adj_setup<<<(h.W + 7) / 8, 256, 0, s>>>(d, ab);
 }
 
-void launch_adj_mult_pointwise(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s) {
+void launch_adj_mult_pointwise(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, double wP, cudaStream_t s) {
     k_adj_mult<<<(h.W + 7) / 8, 256, 0, s>>>(d);
-    k_adj_pointwise<<<(h.W + 7) / 8, 256, 0, s>>>(d, ab);
+    k_adj_pointwise<<<(h.W + 7) / 8, 256, 0, s>>>(d, ab, wP);
 }
 
 void launch_adj_stencil_t(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s) {

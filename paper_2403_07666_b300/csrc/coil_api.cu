@@ -1758,7 +1758,7 @@ struct AdjBufs {
 };
 void launch_adj_thermal(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
 void launch_adj_setup(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
-void launch_adj_mult_pointwise(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
+void launch_adj_mult_pointwise(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, double wP, cudaStream_t s);
 void launch_adj_stencil_t(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s);
 void launch_adj_near(const CoilDev* d, const CoilDev& h, cudaStream_t s);
 void launch_adj_accum(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, double wk, int with_field,
@@ -1895,11 +1895,21 @@ extern "C" coil_status coil_set_params(coil_t* c, const double* jc_factor, doubl
 
 extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* drive, int ckpt_every,
                                     const double* dL_dm, double* g_jc_factor, double* g_n, double* g_C_eps) {
+    if (c && !dL_dm) return fail(c, COIL_ERR_INVALID, "adjoint needs dL_dm");
+    return coil_adjoint_losses(c, n_steps, drive, ckpt_every, dL_dm, nullptr, g_jc_factor, g_n, g_C_eps);
+}
+
+extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_drive* drive, int ckpt_every,
+                                           const double* dL_dm, const double* dL_dP, double* g_jc_factor,
+                                           double* g_n, double* g_C_eps) {
     if (!c) return COIL_ERR_INVALID;
-    if (n_steps < 1 || ckpt_every < 1 || !dL_dm) return fail(c, COIL_ERR_INVALID, "adjoint needs n_steps >= 1, ckpt_every >= 1, dL_dm");
+    if (n_steps < 1 || ckpt_every < 1 || (!dL_dm && !dL_dP))
+        return fail(c, COIL_ERR_INVALID, "adjoint needs n_steps >= 1, ckpt_every >= 1 and dL_dm or dL_dP");
     if (c->h.n_groups) return fail(c, COIL_ERR_INVALID, "the adjoint does not differentiate the subelement decoupling");
     for (long k = 0; k < n_steps; ++k)
-        if (!is_fin(dL_dm[k])) return fail(c, COIL_ERR_NONFINITE, "non-finite dL/dm");
+        if ((dL_dm && !is_fin(dL_dm[k])) || (dL_dP && !is_fin(dL_dP[k])))
+            return fail(c, COIL_ERR_NONFINITE, "non-finite dL/dm or dL/dP");
+    auto wm = [&](long k) { return dL_dm ? dL_dm[k] : 0.0; };
     cudaSetDevice(c->device);
     TRY(set_drive(c, drive));
     CoilDev& h = c->h;
@@ -1974,7 +1984,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
     double* lamI = lamB;
     double* lamU_next = lamUA;
     double* lamU = lamUB;
-    launch_adj_seed(c->d, h, lamI_next, dL_dm[n_steps - 1], s);
+    launch_adj_seed(c->d, h, lamI_next, wm(n_steps - 1), s);
     CK(cudaMemsetAsync(h.x, 0, h.ld * sizeof(double), s), "adjoint");
     for (long sg = nseg - 1; sg >= 0; --sg) {
         long k0 = sg * ckpt_every, k1 = std::min<long>(n_steps, k0 + ckpt_every);
@@ -2016,7 +2026,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
             }
             TRY(adjoint_solve(c));
             ++solved;
-            launch_adj_mult_pointwise(c->d, h, ab, s);
+            launch_adj_mult_pointwise(c->d, h, ab, dL_dP ? dL_dP[k] : 0.0, s);
             if (grid) {
                 launch_adj_stencil_t(c->d, h, ab, s);
                 Launch L = single_launch(c);
@@ -2024,7 +2034,7 @@ extern "C" coil_status coil_adjoint(coil_t* c, long n_steps, const coil_drive* d
                 TRY(gemv(c, L, 1));
                 launch_adj_near(c->d, h, s);
             }
-            launch_adj_accum(c->d, h, ab, k >= 1 ? dL_dm[k - 1] : 0.0, grid ? 1 : 0, s);
+            launch_adj_accum(c->d, h, ab, k >= 1 ? wm(k - 1) : 0.0, grid ? 1 : 0, s);
             c->launches += 5;
             CK(cudaGetLastError(), "adjoint launch");
             std::swap(lamI, lamI_next);
