@@ -334,6 +334,7 @@ def run_ours(args, rank, world, local_rank):
     setup_s = time.perf_counter() - t0
     info = coil.info()
     N = coil.N
+    schedule = coil.tc_schedule() if args.format == "toeplitz_tc" else None
     coil.step(args.warmup, drive)
     coil.reset_counters()
     if dist:
@@ -423,6 +424,7 @@ def run_ours(args, rank, world, local_rank):
                       "FP64 form"),
         "setup_s": setup_s,
         "roofline": roofline,
+        "autotune": schedule,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -587,7 +589,9 @@ def adjoint_leg(args, local_rank, stream, torch):
         s0 = c.save_state()
         c.step(3, w.drive)
         c.load_state(s0)
+        c.reset_counters()
         fwd = timed_steps(c, w.drive, K, stream, torch)
+        it_fwd = int(c.info().pcg_iterations)
         d = c.diag(0, K)
         m, P = d[:, 3], d[:, 4]
         target = 0.95 * m
@@ -598,11 +602,14 @@ def adjoint_leg(args, local_rank, stream, torch):
         c.load_state(s0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        c.reset_counters()
         c.adjoint_losses(K, w.drive, 2.0 * (m - target), dLdP, ckpt_every=50)
         torch.cuda.synchronize()
         adj = time.perf_counter() - t0
+        it_adj = int(c.info().pcg_iterations)
         c.close()
-        out[name] = {"rtol": rt, "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd}
+        out[name] = {"rtol": rt, "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd,
+                     "pcg_iterations_forward": it_fwd, "pcg_iterations_adjoint_call": it_adj}
     out["adjoint_over_forward"] = out[args.format]["adjoint_over_forward"]
     return out
 
@@ -792,6 +799,29 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def apply_once(args):
+    """One operator apply on the workload (for profiler captures of the apply
+    kernel): the coil built as in the main leg, the tensor-core schedule
+    optionally pinned (--tc-mode), one apply of a seeded input; prints the
+    schedule and the apply's wall time."""
+    import torch
+    from paper_2403_07666_b300.coil import Coil
+    w = pick_workload(args.workload)
+    c = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=0, format=args.format)
+    if args.tc_mode >= 0:
+        c.set_tc_schedule(args.tc_mode)
+    p = np.random.default_rng(0).standard_normal(c.N)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c.apply_operator(p)
+    torch.cuda.synchronize()
+    out = {"workload": w.name, "apply_s": time.perf_counter() - t0}
+    if args.format == "toeplitz_tc":
+        out["schedule"] = c.tc_schedule()
+    c.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -822,6 +852,10 @@ def main():
     ap.add_argument("--subelements", type=int, default=1, help="also time the step with subelement decoupling")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--batch-format", default="toeplitz_tc", choices=["toeplitz_tc", "toeplitz", "dense"])
+    ap.add_argument("--apply-once", action="store_true",
+                    help="build the coil, run one operator apply and exit (profiler captures of the apply)")
+    ap.add_argument("--tc-mode", type=int, default=-1,
+                    help="with --apply-once: pin the tensor-core schedule (0 two-fill, 1 one-fill)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -830,6 +864,9 @@ def main():
         args.steps = 10 if args.impl == "reference" else 50
     if args.rtol is None:
         args.rtol = 1e-9 if args.precision == "fp64" else 1e-6
+    if args.apply_once:
+        print(json.dumps(apply_once(args)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
     else:

@@ -226,6 +226,12 @@ coil_status coil_step(coil_t *c, long n_steps, const coil_drive *drive);
  * on the same device and use the same operator precision; the launches go to
  * the first coil's stream.  A coil whose solve fails stops advancing; the
  * call returns the first failure after the others completed the step. */
+/* With the tensor-core format the coils' applies run side by side on side
+ * streams, each with the two-fill schedule and its floor of schedule steps
+ * per CTA (a small coil's apply on a few SMs) in place of its autotuned one;
+ * a coil stepped alone afterwards returns to its autotuned schedule, and a
+ * coil stepped alone with that batch schedule (coil_set_tc_schedule(c, 0, 0,
+ * 0)) gets bit for bit what the batch gives it. */
 coil_status coil_batch_step(coil_t *const *coils, int n_coils, long n_steps,
                             const coil_drive *drives);
 
@@ -365,6 +371,29 @@ coil_status coil_load_state(coil_t *c, const void *buf, size_t bytes);
  * is back at 0.  Other formats ignore the limit.  COIL_ERR_INVALID for
  * cycles < 0. */
 coil_status coil_set_wait_limit(coil_t *c, long long cycles);
+
+/* Schedule of the tensor-core apply (COIL_FORMAT_TOEPLITZ_TC).  coil_create
+ * picks it with an autotuner: a few candidate schedules are timed on the
+ * coil's own table (CUDA events around four applies each) and the fastest is
+ * kept; the choice is remembered for later coils of the same shape (channels,
+ * turns, SM count, device) in the process.  mode 0: every stored tile is
+ * loaded by the CTAs of both of its products (the tile and its transpose);
+ * mode 1: one load serves both products (a 128-row and a 64-row MMA per
+ * tile).  n_cta: CTAs of the apply; stages: table tiles in flight per CTA;
+ * us: measured duration of one apply [microseconds].  COIL_ERR_INVALID for
+ * other formats. */
+coil_status coil_tc_schedule(const coil_t *c, int *mode, int *n_cta, int *stages, double *us);
+
+/* The autotuner's candidates of the last tuning run: on entry *count is the
+ * capacity of out (rows), on return the number of candidates; out[i][4] =
+ * (mode, n_cta, stages, us).  out may be NULL to query the count. */
+coil_status coil_tc_candidates(const coil_t *c, int *count, double *out);
+
+/* Pin the schedule: mode 0 or 1 with n_cta <= 0 and stages <= 0 for that
+ * mode's defaults (mode 0 takes no CTA count), or mode -1 to run the
+ * autotuner again.  The new schedule is timed; COIL_ERR_INVALID when the
+ * coil's shape does not admit it. */
+coil_status coil_set_tc_schedule(coil_t *c, int mode, int n_cta, int stages);
 
 coil_status coil_info(const coil_t *c, coil_info_t *info);
 const char *coil_last_error(const coil_t *c);

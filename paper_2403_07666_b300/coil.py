@@ -89,6 +89,9 @@ def load_library(path=LIB_PATH):
         "coil_set_params": ([P, _dp, C.c_double, C.c_double], C.c_int),
         "coil_adjoint": ([P, C.c_long, C.POINTER(Drive), C.c_int, _dp, _dp, _dp, _dp], C.c_int),
         "coil_adjoint_losses": ([P, C.c_long, C.POINTER(Drive), C.c_int, _dp, _dp, _dp, _dp, _dp], C.c_int),
+        "coil_tc_schedule": ([P, _ip, _ip, _ip, _dp], C.c_int),
+        "coil_tc_candidates": ([P, _ip, _dp], C.c_int),
+        "coil_set_tc_schedule": ([P, C.c_int, C.c_int, C.c_int], C.c_int),
         "coil_info": ([P, C.POINTER(Info)], C.c_int),
         "coil_reset_counters": ([P], C.c_int),
         "coil_set_wait_limit": ([P, C.c_longlong], C.c_int),
@@ -327,6 +330,23 @@ class Coil:
                                                   None if dp is None else _ptr(dp), _ptr(gf), C.byref(gn),
                                                   C.byref(gc)))
         return gf, gn.value, gc.value
+
+    def tc_schedule(self):
+        """The tensor-core apply's schedule: dict(mode, n_cta, stages, us) and the
+        autotuner's candidates as rows (mode, n_cta, stages, us)."""
+        m, n, st = C.c_int(), C.c_int(), C.c_int()
+        us = C.c_double()
+        self._check(self._lib.coil_tc_schedule(self._h, C.byref(m), C.byref(n), C.byref(st), C.byref(us)))
+        cnt = C.c_int(0)
+        self._check(self._lib.coil_tc_candidates(self._h, C.byref(cnt), None))
+        rows = np.empty((cnt.value, 4))
+        if cnt.value:
+            self._check(self._lib.coil_tc_candidates(self._h, C.byref(cnt), _ptr(rows)))
+        return {"mode": m.value, "n_cta": n.value, "stages": st.value, "us": us.value,
+                "candidates": rows.tolist()}
+
+    def set_tc_schedule(self, mode, n_cta=0, stages=0):
+        self._check(self._lib.coil_set_tc_schedule(self._h, int(mode), int(n_cta), int(stages)))
 
     def set_wait_limit(self, cycles):
         """coil_set_wait_limit: test hook of the tensor-core apply's bounded

@@ -5,7 +5,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <algorithm>
 #include <atomic>
 #include <vector>
@@ -122,12 +125,35 @@ constexpr int kAuxStreams = 16;         // side streams of a batch's tensor-core
 constexpr int kRedThreads = 1024;       // threads of the one-CTA-per-coil reductions (k_reduce, k_step_end)
 constexpr size_t kMomentBlocks = 148;   // partial sums of the moment in coil_read
 
+std::string tc_timeout_text(const coil_t* c);
+
 coil_status fail(coil_t* c, coil_status st, const std::string& msg) {
     if (c) c->err = msg;
     return st;
 }
 
 coil_status reset_wire_stats(coil_t* c, bool onsets);
+coil_status read_scalars(coil_t* c);
+
+// "tensor-core apply timed out", with the first wait that ran out when the
+// apply recorded one (site, CTA, stage, index, parity, thread)
+std::string tc_timeout_text(const coil_t* c) {
+    std::string s = "tensor-core apply timed out";
+    const int* w = c->pinned ? c->pinned->tc_where : nullptr;
+    if (w && w[0] != 0) {
+        s += " (wait site " + std::to_string(w[0]) + ", CTA " + std::to_string(w[1]) + ", stage " +
+             std::to_string(w[2]) + ", index " + std::to_string(w[3]) + ", parity " + std::to_string(w[4]) +
+             ", thread " + std::to_string(w[5]) + ")";
+        if (c->tc && c->tc->prog && w[1] >= 0 && w[1] < c->tc->sh.n_cta) {
+            int pr[32];
+            if (cudaMemcpy(pr, c->tc->prog + 32 * w[1], sizeof(pr), cudaMemcpyDeviceToHost) == cudaSuccess) {
+                s += " progress:";
+                for (int k = 0; k < 24; ++k) s += " " + std::to_string(pr[k]);
+            }
+        }
+    }
+    return s;
+}
 coil_status sync_descriptor(coil_t* c);
 
 coil_status cuda_fail(coil_t* c, cudaError_t e, const char* where) {
@@ -302,6 +328,191 @@ coil_status validate(const coil_geometry* g, const coil_material* m, const coil_
     if (!m->jc_factor || !m->strain || !m->mat)
         return fail(c, COIL_ERR_INVALID, "jc_factor, strain and mat arrays are required");
     if (!is_fin(m->Y_eff) || m->Y_eff < 0.0) return fail(c, COIL_ERR_INVALID, "Y_eff must be finite and >= 0");
+    return COIL_OK;
+}
+
+// ---- schedule of the tensor-core apply and its autotuner
+
+// Device buffers of the current schedule (work list, reduction lists, partial
+// tiles), freed when another schedule replaces it.
+void tc_free_schedule(coil_t* c) {
+    TcPlan& P = *c->tc;
+    for (void* p : P.sched_bufs) {
+        for (size_t i = 0; i < c->allocs.size(); ++i)
+            if (c->allocs[i] == p) { c->allocs.erase(c->allocs.begin() + i); break; }
+        cudaFree(p);
+    }
+    c->bytes -= P.sched_bytes;
+    P.sched_bufs.clear();
+    P.sched_bytes = 0;
+    P.part = P.part2 = nullptr;
+    P.work = nullptr;
+    P.range = P.l1 = P.l2 = nullptr;
+    P.segs1 = P.segs2 = P.prog = nullptr;
+}
+
+template <typename T>
+coil_status tc_sched_alloc(coil_t* c, T** p, size_t count, const std::vector<T>* host, const char* what) {
+    const size_t before = c->allocs.size(), b0 = c->bytes;
+    TRY(host ? upload(c, p, *host, what) : dalloc(c, p, count, what));
+    if (c->allocs.size() > before) {
+        c->tc->sched_bufs.push_back(c->allocs.back());
+        c->tc->sched_bytes += c->bytes - b0;
+    }
+    return COIL_OK;
+}
+
+// Make `sh` (mode 0: each table tile loaded by the CTAs of both its products;
+// mode 1: one-fill) the coil's schedule: work list, reduction lists, partial
+// tiles; the descriptor fields that point at them; graphs captured with the
+// previous schedule are dropped.
+coil_status tc_plan_schedule(coil_t* c, const TcShape& sh) {
+    TcPlan& P = *c->tc;
+    CoilDev& h = c->h;
+    if (c->stream) CK(cudaStreamSynchronize(c->stream), "schedule");
+    tc_free_schedule(c);
+    P.sh = sh;
+    P.smem = tc_smem_bytes(sh);
+    const size_t NT = sh.NT;
+    std::vector<int4> work;
+    if (sh.mode == 1) {
+        std::vector<int2> l1, l2;
+        std::vector<int> s1, s2;
+        tc2_schedule(&P.sh, &work, &l1, &s1, &l2, &s2);
+        TRY(tc_sched_alloc(c, &P.part, (size_t)P.sh.n_seg * NT * 128, (const std::vector<float>*)nullptr,
+                           "tensor-core partial tiles"));
+        TRY(tc_sched_alloc(c, &P.part2, (size_t)P.sh.n_seg * NT * 64, (const std::vector<float>*)nullptr,
+                           "tensor-core partial tiles"));
+        TRY(tc_sched_alloc(c, &P.work, 0, &work, "tensor-core schedule"));
+        TRY(tc_sched_alloc(c, &P.l1, 0, &l1, "tensor-core schedule"));
+        TRY(tc_sched_alloc(c, &P.l2, 0, &l2, "tensor-core schedule"));
+        TRY(tc_sched_alloc(c, &P.segs1, 0, &s1, "tensor-core schedule"));
+        TRY(tc_sched_alloc(c, &P.segs2, 0, &s2, "tensor-core schedule"));
+        TRY(tc_sched_alloc(c, &P.prog, (size_t)P.sh.n_cta * 32, (const std::vector<int>*)nullptr,
+                           "tensor-core progress"));
+    } else {
+        std::vector<int2> range;
+        tc_schedule(sh, c->n_sm, &work, &range);
+        P.sh.n_cta = (int)work.size();
+        TRY(tc_sched_alloc(c, &P.part, (size_t)P.sh.n_cta * NT * 128, (const std::vector<float>*)nullptr,
+                           "tensor-core partial tiles"));
+        TRY(tc_sched_alloc(c, &P.work, 0, &work, "tensor-core schedule"));
+        TRY(tc_sched_alloc(c, &P.range, 0, &range, "tensor-core schedule"));
+    }
+    h.tc_mode = sh.mode;
+    h.tc_part = P.part;
+    h.tc_part2 = P.part2;
+    h.tc_range = P.range;
+    h.tc_l1 = P.l1;
+    h.tc_l2 = P.l2;
+    h.tc_segs1 = P.segs1;
+    h.tc_segs2 = P.segs2;
+    if (c->d) TRY(sync_descriptor(c));
+    if (c->step_exec) { cudaGraphExecDestroy(c->step_exec); c->step_exec = nullptr; }
+    if (c->adj_exec) { cudaGraphExecDestroy(c->adj_exec); c->adj_exec = nullptr; }
+    if (c->batch) {
+        if (c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
+        cudaFree(c->batch->dd);
+        cudaFreeHost(c->batch->hstat);
+        delete c->batch;
+        c->batch = nullptr;
+    }
+    if (c->stream) CK(cudaStreamSynchronize(c->stream), "schedule");
+    return COIL_OK;
+}
+
+// Schedules the autotuner has chosen, per (device, C, NT, SM count).
+struct TcTuned {
+    TcShape sh;
+    double us;
+};
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, TcTuned> g_tuned;
+
+// Mean duration of the apply kernel (split excluded) over a few launches on
+// the coil's stream, after one untimed launch.
+coil_status tc_time_apply(coil_t* c, double* us) {
+    TcPlan& P = *c->tc;
+    const int kReps = 4;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "tune");
+    CK(cudaEventCreate(&e1), "tune");
+    CK(cudaMemsetAsync(&c->h.sc->done, 0, sizeof(int), c->stream), "tune");
+    CK(launch_tc_split(P, c->stream, false), "tune");
+    CK(launch_tc_apply(P, c->stream, false), "tune");
+    CK(cudaEventRecord(e0, c->stream), "tune");
+    for (int r = 0; r < kReps; ++r) CK(launch_tc_apply(P, c->stream, false), "tune");
+    CK(cudaEventRecord(e1, c->stream), "tune");
+    CK(cudaStreamSynchronize(c->stream), "tune");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    read_scalars(c);
+    if (c->pinned->status == ST_KERNEL) return fail(c, COIL_ERR_CUDA, tc_timeout_text(c));
+    *us = 1e3 * ms / kReps;
+    return COIL_OK;
+}
+
+// Autotuner of the tensor-core apply: time a small grid of schedules (the
+// two-fill apply with 6 to 4 table stages; the one-fill apply with its
+// largest stage count and with one fewer, on all SMs and on nine tenths of
+// them) on this coil's own table, keep the fastest, and remember it for later
+// coils of the same shape.  retune: ignore the remembered choice.
+coil_status tc_autotune(coil_t* c, bool retune) {
+    const TcShape base = c->tc->sh;
+    const auto key = std::make_tuple(c->device, base.C, base.NT, c->n_sm);
+    if (!retune) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            c->tc->tuned_us = it->second.us;
+            c->tc->tuned_sh = it->second.sh;
+            return tc_plan_schedule(c, it->second.sh);
+        }
+    }
+    std::vector<TcShape> cand;
+    TcShape s0;
+    if (tc_shape(base.C, base.NT, c->n_sm, &s0)) {
+        // the two-fill apply: its largest stage count and one fewer, with the
+        // step floor per CTA (small coils on few SMs) and without it
+        for (int ms : {0, 1})
+            for (int drop = 0; drop < 2; ++drop) {
+                TcShape s = s0;
+                s.min_steps = ms;
+                s.stages = s0.stages - drop;
+                if (s.stages < 2 || s.n_acc > s.stages) continue;
+                s.n_cta = (int)tc_schedule(s, c->n_sm, nullptr, nullptr);
+                if (ms == 1 && s.n_cta == s0.n_cta) continue;        // the floor changed nothing
+                cand.push_back(s);
+            }
+    }
+    // the one-fill apply: the default CTA count (a stage floor per CTA) and all
+    // SMs, its largest stage count and one fewer
+    for (int ctas : {0, c->n_sm}) {
+        TcShape s1;
+        if (!tc2_shape(base.C, base.NT, c->n_sm, ctas, 0, &s1)) continue;
+        if (ctas != 0 && !cand.empty() && cand.back().mode == 1 && cand.back().n_cta == s1.n_cta) continue;
+        cand.push_back(s1);
+        TcShape s2;
+        if (s1.stages > 2 && tc2_shape(base.C, base.NT, c->n_sm, ctas, s1.stages - 1, &s2)) cand.push_back(s2);
+    }
+    double best = 1e300;
+    TcShape best_sh = base;
+    c->tc->tuned.clear();
+    for (const TcShape& sh : cand) {
+        TRY(tc_plan_schedule(c, sh));
+        double us = 0.0;
+        TRY(tc_time_apply(c, &us));
+        c->tc->tuned.push_back({sh.mode, c->tc->sh.n_cta, sh.stages, us});
+        if (us < best) { best = us; best_sh = c->tc->sh; }
+    }
+    TRY(tc_plan_schedule(c, best_sh));
+    c->tc->tuned_us = best;
+    c->tc->tuned_sh = best_sh;
+    c->tc->in_batch = false;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = {best_sh, best};
     return COIL_OK;
 }
 
@@ -540,13 +751,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         P.smem = tc_smem_bytes(tsh);
         P.t16 = static_cast<__half*>(M);
         TRY(dalloc(c, &P.p16, 2 * (size_t)tsh.Cp * NT, "split operator input"));
-        TRY(dalloc(c, &P.part, (size_t)tsh.n_cta * NT * 128, "tensor-core partial tiles"));
-        std::vector<int4> work;
-        std::vector<int2> range;
-        tc_schedule(tsh, c->n_sm, &work, &range);
-        TRY(upload(c, &P.work, work, "tensor-core schedule"));
-        TRY(upload(c, &P.range, range, "tensor-core schedule"));
-        h.tc_range = P.range;
+        TRY(tc_plan_schedule(c, tsh));
         TRY(dalloc(c, &P.pexp, (size_t)NT, "input scale exponents"));
         P.fused = B <= kSegMax;
         h.tc_part = P.part;
@@ -615,6 +820,8 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
             cudaGetLastError();
             return fail(c, COIL_ERR_CUDA, why);
         }
+        CK(cudaStreamSynchronize(c->stream), "create");
+        TRY(tc_autotune(c, false));
     }
     CK(cudaStreamSynchronize(c->stream), "create");
     return COIL_OK;
@@ -1027,7 +1234,7 @@ coil_status run_step(coil_t* c) {
             c->launches += c->graph_fixed + (long long)c->graph_per_pass * passes;
             c->op_launches += 1 + passes;
             int st = c->pinned->status;
-            if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+            if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, tc_timeout_text(c));
             if (!c->pinned->done || st == ST_NOT_CONVERGED)
                 return fail(c, COIL_ERR_NOT_CONVERGED, "per-step solve did not converge within maxit iterations");
             if (st == ST_NONFINITE)
@@ -1055,7 +1262,7 @@ coil_status run_step(coil_t* c) {
         chunk = 1;
     }
     int st = c->pinned->status;
-    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, tc_timeout_text(c));
     if (!c->pinned->done || st == ST_NOT_CONVERGED)
         return fail(c, COIL_ERR_NOT_CONVERGED, "per-step solve did not converge within maxit iterations");
     if (st == ST_NONFINITE)
@@ -1087,7 +1294,7 @@ coil_status apply_plain(coil_t* c, const double* dev_p) {
     TRY(sync_descriptor(c));
     if (h.op_format == 2) {
         TRY(read_scalars(c));
-        if (c->pinned->status == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+        if (c->pinned->status == ST_KERNEL) return fail(c, COIL_ERR_CUDA, tc_timeout_text(c));
     }
     return COIL_OK;
 }
@@ -1210,6 +1417,11 @@ coil_status coil_step(coil_t* c, long n_steps, const coil_drive* drive) {
     if (n_steps < 0) return fail(c, COIL_ERR_INVALID, "n_steps must be >= 0");
     cudaSetDevice(c->device);
     TRY(set_drive(c, drive));
+    if (c->tc && c->tc->in_batch) {
+        // stepped alone again after batched steps: back to the autotuner's schedule
+        TRY(tc_plan_schedule(c, c->tc->tuned_sh));
+        c->tc->in_batch = false;
+    }
     for (long k = 0; k < n_steps; ++k) TRY(run_step(c));
     CK(cudaStreamSynchronize(c->stream), "coil_step");
     return COIL_OK;
@@ -1227,6 +1439,20 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
             if (coils[j] == coils[i]) return fail(c, COIL_ERR_INVALID, "a coil appears twice in the batch");
     }
     cudaSetDevice(c->device);
+    if (c->h.op_format == 2 && n > 1) {
+        // batched tensor-core applies run side by side on the side streams: each
+        // coil takes the two-fill schedule with its step floor per CTA (a small
+        // coil's apply on a few SMs), not the autotuner's choice for running alone
+        for (int i = 0; i < n; ++i) {
+            coil_t* ci = coils[i];
+            if (!ci->tc || ci->tc->in_batch) continue;
+            TcShape sb;
+            if (!tc_shape(ci->tc->sh.C, ci->tc->sh.NT, ci->n_sm, &sb))
+                return fail(c, COIL_ERR_INVALID, "coil shape not supported by the tensor-core Toeplitz format");
+            TRY(tc_plan_schedule(ci, sb));
+            ci->tc->in_batch = true;
+        }
+    }
     Launch L;
     L.n = n;
     L.prec = c->h.precision;
@@ -1673,6 +1899,63 @@ coil_status coil_info(const coil_t* c, coil_info_t* info) {
     return COIL_OK;
 }
 
+coil_status coil_tc_schedule(const coil_t* c, int* mode, int* n_cta, int* stages, double* us) {
+    if (!c) return COIL_ERR_INVALID;
+    if (!c->tc) return fail(const_cast<coil_t*>(c), COIL_ERR_INVALID, "not the tensor-core Toeplitz format");
+    if (mode) *mode = c->tc->sh.mode;
+    if (n_cta) *n_cta = c->tc->sh.n_cta;
+    if (stages) *stages = c->tc->sh.stages;
+    if (us) *us = c->tc->tuned_us;
+    return COIL_OK;
+}
+
+coil_status coil_tc_candidates(const coil_t* c, int* count, double* out) {
+    if (!c || !count) return COIL_ERR_INVALID;
+    if (!c->tc) return fail(const_cast<coil_t*>(c), COIL_ERR_INVALID, "not the tensor-core Toeplitz format");
+    const int n = (int)c->tc->tuned.size();
+    if (out) {
+        const int m = std::min(n, *count);
+        for (int i = 0; i < m; ++i) {
+            const TcPlan::Tuned& t = c->tc->tuned[i];
+            out[4 * i] = t.mode;
+            out[4 * i + 1] = t.n_cta;
+            out[4 * i + 2] = t.stages;
+            out[4 * i + 3] = t.us;
+        }
+    }
+    *count = n;
+    return COIL_OK;
+}
+
+coil_status coil_set_tc_schedule(coil_t* c, int mode, int n_cta, int stages) {
+    if (!c) return COIL_ERR_INVALID;
+    if (!c->tc) return fail(c, COIL_ERR_INVALID, "not the tensor-core Toeplitz format");
+    cudaSetDevice(c->device);
+    if (mode == -1) return tc_autotune(c, true);
+    const TcShape& cur = c->tc->sh;
+    TcShape sh;
+    bool ok = false;
+    if (mode == 0) {
+        ok = tc_shape(cur.C, cur.NT, c->n_sm, &sh);
+        if (ok && stages > 0) {
+            if (stages > sh.stages || stages < sh.n_acc) ok = false;
+            else sh.stages = stages;
+        }
+        if (ok && n_cta > 0) ok = false;          // the two-fill apply sizes its own grid
+    } else if (mode == 1) {
+        ok = tc2_shape(cur.C, cur.NT, c->n_sm, n_cta > 0 ? n_cta : 0, stages > 0 ? stages : 0, &sh) &&
+             (stages <= 0 || sh.stages == stages);
+    }
+    if (!ok) return fail(c, COIL_ERR_INVALID, "unsupported tensor-core schedule for this coil");
+    TRY(tc_plan_schedule(c, sh));
+    double us = 0.0;
+    TRY(tc_time_apply(c, &us));
+    c->tc->tuned_us = us;
+    c->tc->tuned_sh = c->tc->sh;      // kept when the coil steps alone after batched steps
+    c->tc->in_batch = false;
+    return COIL_OK;
+}
+
 coil_status coil_set_wait_limit(coil_t* c, long long cycles) {
     if (!c) return COIL_ERR_INVALID;
     if (cycles < 0) return fail(c, COIL_ERR_INVALID, "wait limit must be >= 0");
@@ -1832,7 +2115,7 @@ coil_status adjoint_prologue(coil_t* c, const Launch& L) {
 
 coil_status adjoint_status(coil_t* c) {
     int st = c->pinned->status;
-    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, "tensor-core apply timed out");
+    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, tc_timeout_text(c));
     if (!c->pinned->done || st == ST_NOT_CONVERGED)
         return fail(c, COIL_ERR_NOT_CONVERGED, "adjoint solve did not converge within maxit iterations");
     if (st == ST_NONFINITE) return fail(c, COIL_ERR_NONFINITE, "non-finite value in the adjoint solve");
@@ -1937,8 +2220,9 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
     TRY(mem.get(&gparts, 2 * W, "partials"));
     TRY(mem.get(&musave, N, "mu"));
     TRY(mem.get(&out2, 2, "outputs"));
-    double* muprev;
+    double *muprev, *muprev2;
     TRY(mem.get(&muprev, N, "previous adjoint solution"));
+    TRY(mem.get(&muprev2, N, "previous adjoint solution"));
 
     // forward pass, checkpoint every ckpt_every steps; the states of the last
     // segment are kept as they are made, so that segment needs no recomputation
@@ -1968,15 +2252,22 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
 
     // reverse sweep: its pointwise launches recompute steps already counted,
     // so the per-wire statistics stay as the forward pass left them.  Its
-    // transposed solves extrapolate from their own last two solutions (history
-    // in muprev); the recomputed forward steps use the forward history, as the
-    // forward pass did.
+    // transposed solves extrapolate quadratically from their own last three
+    // solutions (history in muprev, muprev2); the recomputed forward steps use
+    // the forward history, as the forward pass did.
     double* const xprev_fwd = h.xprev;
+    double* const xprev2_fwd = h.xprev2;
     struct AccGuard {
         coil_t* c;
-        double* xp;
-        ~AccGuard() { c->h.acc_on = 1; c->h.extrap = 1; c->h.xprev = xp; sync_descriptor(c); }
-    } acc_guard{c, xprev_fwd};
+        double *xp, *xp2;
+        ~AccGuard() {
+            c->h.acc_on = 1;
+            c->h.extrap = 1;
+            c->h.xprev = xp;
+            c->h.xprev2 = xp2;
+            sync_descriptor(c);
+        }
+    } acc_guard{c, xprev_fwd, xprev2_fwd};
     h.acc_on = 0;
     TRY(sync_descriptor(c));
     long solved = 0;                                 // transposed solves done
@@ -1995,6 +2286,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
             CK(cudaMemcpyAsync(musave, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
             h.extrap = 1;
             h.xprev = xprev_fwd;
+            h.xprev2 = xprev2_fwd;
             TRY(sync_descriptor(c));
             TRY(state_copy(c, ck + sg * S, false, true));
             c->t = t_ck[sg];
@@ -2010,6 +2302,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
             CK(cudaMemcpyAsync(h.x, musave, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
         }
         h.xprev = muprev;
+        h.xprev2 = muprev2;
         for (long k = k1 - 1; k >= k0; --k) {
             double* slot = seg + (k - k0) * S;
             TRY(state_copy(c, slot, false, false));
@@ -2019,7 +2312,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
             if (thermal) launch_adj_thermal(c->d, h, ab, s);
             launch_adj_setup(c->d, h, ab, s);
             CK(cudaGetLastError(), "adjoint launch");
-            const int mode = solved >= 2 ? 3 : 2;
+            const int mode = solved >= 3 ? 4 : (solved == 2 ? 6 : 5);
             if (h.extrap != mode) {
                 h.extrap = mode;
                 TRY(sync_descriptor(c));
@@ -2051,6 +2344,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
     // back to the state after the forward steps
     h.extrap = 1;
     h.xprev = xprev_fwd;
+    h.xprev2 = xprev2_fwd;
     TRY(sync_descriptor(c));
     TRY(state_copy(c, fin, false, true));
     c->t = t_fin;

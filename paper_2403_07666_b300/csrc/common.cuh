@@ -37,6 +37,7 @@ struct Scalars {
     double last_resid;
     int passes;          // loop passes of a graph-launched step (a guard on its while loop)
     long long tc_wait;   // cycles before a wait of the tensor-core apply gives up (0: its default)
+    int tc_where[6];     // the first wait of the apply that ran out: site, CTA, stage, index, parity, thread
 };
 
 struct CoilDev {
@@ -70,6 +71,13 @@ struct CoilDev {
     const int2 *tc_range;
     const int *tc_pexp;
     int tc_exT;
+    // one-fill apply (tc_mode 1): partial tiles part1 (tc_part, [segment][t][128])
+    // and part2 ([segment][t][64]); the segments of each channel tile (l1 into
+    // segs1) and of each 64-channel k block (l2 into segs2)
+    int tc_mode;
+    const float *tc_part2;
+    const int2 *tc_l1, *tc_l2;
+    const int *tc_segs1, *tc_segs2;
     // stencil: per grid column (resp. row) the first node and three weights
     const int *sr_j0, *sz_j0;
     const double *sr_w, *sz_w;
@@ -117,8 +125,9 @@ struct CoilDev {
     // solutions (xprev holds x_{n-2}, xprev2 x_{n-3}).  extrap: 0 plain warm
     // start; 1 forward steps (2 x_{n-1} - x_{n-2} on the third step,
     // 3 x_{n-1} - 3 x_{n-2} + x_{n-3} from the fourth on); 2 record x only;
-    // 3 linear extrapolation always (the adjoint's transposed solves, with
-    // xprev pointing at their own history)
+    // 3 linear extrapolation always; the adjoint's transposed solves, with
+    // xprev and xprev2 pointing at their own history: 5 record x (both
+    // histories shift), 6 linear (both shift), 4 quadratic
     double *xprev, *xprev2;
     int extrap;
     double *diag;                 // ring [cap][10]

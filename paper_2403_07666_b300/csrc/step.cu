@@ -28,16 +28,16 @@ __device__ __forceinline__ double warm_start(const CoilDev& c, int e, bool ext) 
     if (!c.extrap) return x;
     const double xp = c.xprev[e];
     c.xprev[e] = x;
-    if (c.extrap == 1) {
+    if (c.extrap == 1 || c.extrap >= 4) {
         const double xp2 = c.xprev2[e];
         c.xprev2[e] = xp;
-        if (c.sc->step >= 3) return 3.0 * x - 3.0 * xp + xp2;
+        if ((c.extrap == 1 && c.sc->step >= 3) || c.extrap == 4) return 3.0 * x - 3.0 * xp + xp2;
     }
     return ext ? 2.0 * x - xp : x;
 }
 
 __device__ __forceinline__ bool extrapolate(const CoilDev& c) {
-    return (c.extrap == 1 && c.sc->step >= 2) || c.extrap == 3;
+    return (c.extrap == 1 && c.sc->step >= 2) || c.extrap == 3 || c.extrap == 4 || c.extrap == 6;
 }
 
 // Detectors and per-wire statistics of wire w from its start-of-step state
@@ -802,6 +802,32 @@ __device__ __forceinline__ void kahan_add(float v, float& s, float& comp) {
 }
 __device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv) {
     const int t = e / c.C, cc = e - t * c.C;
+    if (c.tc_mode == 1) {
+        // one-fill apply: the segments of e's channel tile, then of its k block
+        const int2 r1 = c.tc_l1[cc / kTcTileRows], r2 = c.tc_l2[cc / 64];
+        const float* p1 = c.tc_part + (size_t)t * kTcTileRows + (cc % kTcTileRows);
+        const float* p2 = c.tc_part2 + (size_t)t * 64 + (cc % 64);
+        const size_t t1 = (size_t)c.NT * kTcTileRows, t2 = (size_t)c.NT * 64;
+        float s = 0.f, comp = 0.f;
+        int k = 0;
+        for (; k + 8 <= r1.y; k += 8) {
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = p1[(size_t)c.tc_segs1[r1.x + k + i] * t1];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) kahan_add(v[i], s, comp);
+        }
+        for (; k < r1.y; ++k) kahan_add(p1[(size_t)c.tc_segs1[r1.x + k] * t1], s, comp);
+        for (k = 0; k + 8 <= r2.y; k += 8) {
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = p2[(size_t)c.tc_segs2[r2.x + k + i] * t2];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) kahan_add(v[i], s, comp);
+        }
+        for (; k < r2.y; ++k) kahan_add(p2[(size_t)c.tc_segs2[r2.x + k] * t2], s, comp);
+        return ((double)s - (double)comp) * inv;
+    }
     const int2 rg = c.tc_range[cc / kTcTileRows];
     const size_t tile = (size_t)c.NT * kTcTileRows;
     const float* p = c.tc_part + (size_t)rg.x * tile + (size_t)t * kTcTileRows + (cc % kTcTileRows);

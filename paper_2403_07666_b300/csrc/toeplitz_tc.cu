@@ -500,6 +500,413 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------------------
+// One-fill apply: every table tile serves both of its products
+// ---------------------------------------------------------------------------
+//
+// The apply above loads each stored tile twice (once K-major by the CTA of its
+// row tile, once MN-major by the CTA of the transposed block), and what bounds
+// it is the rate at which TMA fills an SM's shared memory.  Here the unit of
+// work is a combination (channel tile a, 64-channel k block kb); its stage D
+// loads the tile A = T_D[a rows][kb columns] once and issues
+//
+//   (1)  y[t][a]  += A p[t - D][kb]      M = 128 (a), K = 64 (kb), K-major A
+//   (2)  y[t][kb] += A^T p[t + D][a]     M = 64 (kb), K = 128 (a), MN-major A
+//
+// (2) only for D > 0: T_{-D} = T_D^T (M is symmetric), so over every (a, kb)
+// and D the two products give all offsets -NT < d < NT, and at D = 0 the
+// stored T_0 is applied whole by (1).  The staged inputs are p[kb] (64
+// channels, B of (1)) and p[a] (128 channels, B of (2)), one copy each, in
+// the K-major split layout of the input; the kb copy changes with every
+// combination, the a copy every n_kb combinations (kb runs fastest).
+//
+// Accumulators: stage i takes the pair i % n_acc, (1) into 128 lanes of its
+// first acc_cols columns, (2) into the next acc_cols columns, where an M = 64
+// product leaves row r of D in lane 32 (r / 16) + r % 16 (lanes 0-15 of each
+// lane quadrant).  The drain warps add both into FP32 registers (as above),
+// (2) read with the 16x32bx2 shape so that the 16 rows of a quadrant serve
+// two 8-turn groups per load, and write a partial tile per combination the
+// CTA worked on: part1[segment][t][128] for y[a], part2[segment][t][64] for
+// y[kb].  The reduction sums, for every element, the segments of its channel
+// tile (part1) and of its k block (part2) in a fixed order.
+//
+// Work split: the n_ct n_kb NT stages in (a, kb, D) order are dealt to the
+// CTAs as equal contiguous ranges; a range crosses at most a few combination
+// boundaries, each a new segment.
+constexpr uint32_t kT2ABytes = 512u;             // bytes per staged turn row of p[a] (128 channels, hi + lo)
+constexpr uint32_t kT2KBytes = 256u;             // of p[kb] (64 channels)
+constexpr long long kT2MinStages = 8;            // stages per CTA, at least (small coils take few SMs)
+__host__ __device__ constexpr int kT2Bars(int stages, int n_acc) { return 2 * stages + 4 + 2 * n_acc + 1; }
+
+// Instruction descriptor of kind::f16 (FP16 A and B, FP32 D) for M = m.
+__device__ __forceinline__ uint32_t idesc_f16m(int n, bool a_mn, int m) {
+    return (1u << 4) | ((a_mn ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// 16 lanes x 8 columns twice: threads 0-15 read lanes 0-15 of the quadrant at
+// columns taddr .. +7, threads 16-31 the same lanes at columns taddr + 8 .. +15.
+__device__ __forceinline__ void tmem_ld16x2_8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], 8;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void scale_add8(const float* inv_s, int scp, int a, const float* v, float* acc) {
+    // scales of staged rows a .. a + 7 (copy a % 4 holds entry r + (a % 4) at r)
+    const float4* sc4 = reinterpret_cast<const float4*>(inv_s + (a & 3) * scp + (a & ~3));
+#pragma unroll
+    for (int q4 = 0; q4 < 2; ++q4) {
+        const float4 f = sc4[q4];
+        acc[4 * q4 + 0] = fmaf(v[4 * q4 + 0], f.x, acc[4 * q4 + 0]);
+        acc[4 * q4 + 1] = fmaf(v[4 * q4 + 1], f.y, acc[4 * q4 + 1]);
+        acc[4 * q4 + 2] = fmaf(v[4 * q4 + 2], f.z, acc[4 * q4 + 2]);
+        acc[4 * q4 + 3] = fmaf(v[4 * q4 + 3], f.w, acc[4 * q4 + 3]);
+    }
+}
+
+// A bounded wait of the one-fill apply that, when it runs out, records where
+// (site, CTA, stage, index, parity, thread) for the host's error message.
+__device__ __noinline__ bool wait2(const CoilDev& c, uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                   long long limit, int site, int s, int i) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > limit) {
+            *abort_flag = 1;
+            if (atomicCAS(&c.sc->tc_where[0], 0, site) == 0) {
+                c.sc->tc_where[1] = blockIdx.x;
+                c.sc->tc_where[2] = s;
+                c.sc->tc_where[3] = i;
+                c.sc->tc_where[4] = (int)parity;
+                c.sc->tc_where[5] = threadIdx.x;
+            }
+            return false;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmB64, const CoilDev* __restrict__ cd, const TcShape sh,
+               const int4* __restrict__ work, const int* __restrict__ pexp, float* __restrict__ part1,
+               float* __restrict__ part2, int* __restrict__ prog) {
+    const CoilDev& c = *cd;
+    if (c.sc->done) return;
+    const long long wlim = c.sc->tc_wait > 0 ? c.sc->tc_wait : kTcWait;
+    extern __shared__ uint8_t tc_smem[];
+    const uint32_t raw = su32(tc_smem);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = tc_smem + (base - raw);
+    const int S = sh.stages, NA = sh.n_acc, NT = sh.NT, NR = sh.NR;
+    const uint32_t pa_bytes = kT2ABytes * (uint32_t)NR, pk_bytes = kT2KBytes * (uint32_t)NR;
+    const uint32_t pa_pitch = (pa_bytes + 1023u) & ~1023u, pk_pitch = (pk_bytes + 1023u) & ~1023u;
+    const uint32_t sA = base;                                     // S x 32 KB table slots
+    const uint32_t sPA = base + (uint32_t)S * kTcAStage;          // staged p[a]
+    const uint32_t sPK = sPA + pa_pitch;                          // staged p[kb]
+    const uint32_t bar_off = (uint32_t)S * kTcAStage + pa_pitch + pk_pitch;
+    const uint32_t sBar = base + bar_off;
+    const int nbar = kT2Bars(S, NA);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + bar_off + 8 * nbar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + bar_off + 8 * nbar + 4);
+    int* xmin_s = reinterpret_cast<int*>(gbase + bar_off + 8 * nbar + 8);
+    // stages drained so far, times kTcEpiWarps (each drain warp adds one per stage)
+    volatile unsigned* drained = reinterpret_cast<volatile unsigned*>(gbase + bar_off + 8 * nbar + 12);
+    const int scp = (NR + 7) & ~3;
+    float* inv_s = reinterpret_cast<float*>(gbase + ((bar_off + 8 * nbar + 16 + 15) & ~15u));
+    // barriers: a_full[S], a_empty[S], pa_full, pa_empty, pk_full, pk_empty, acc_full[NA], acc_empty[NA]
+    // (not waited on: the issuers count drained stages instead, see below), mma_done
+    const uint32_t a_full = sBar, a_empty = sBar + 8u * S;
+    const uint32_t pa_full = sBar + 16u * S, pa_empty = pa_full + 8u, pk_full = pa_full + 16u, pk_empty = pa_full + 24u;
+    const uint32_t acc_full = pa_full + 32u, acc_empty = acc_full + 8u * NA;
+    const uint32_t mma_done = acc_empty + 8u * NA;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 wk = work[blockIdx.x];                 // stages [wk.x, wk.y), first segment wk.z
+    const uint32_t acc_cols = (uint32_t)sh.acc_cols;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nbar; ++b) {
+            const uint32_t bar = sBar + 8u * b;
+            uint32_t cnt = 1u;
+            if (bar >= acc_empty && bar < acc_empty + 8u * NA) cnt = (uint32_t)kTcEpiWarps;
+            else if (bar == pa_empty || bar == pk_empty || bar == mma_done) cnt = (uint32_t)kTcIssuers;
+            mbar_init(bar, cnt);
+        }
+        *abort_flag = 0;
+        *xmin_s = 1 << 30;
+        *drained = 0u;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int m = warp_min_exponent(pexp, NT, lane);
+        if (lane == 0) *xmin_s = m;
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(su32(tslot), (uint32_t)sh.ncols);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    for (int i = threadIdx.x; i < 4 * scp; i += blockDim.x) {
+        const int k = i / scp, r = i - k * scp + k, t = r - kTcPad;
+        inv_s[i] = (t >= 0 && t < NT) ? ldexpf(1.f, *xmin_s - pexp[t]) : 0.f;
+    }
+    __syncthreads();
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer: the staged copies when their combination changes, then the stage's tile
+        int sa = 0, cur_a = -1, cur_kb = -1, na = 0, nk = 0;
+        uint32_t pa = 0, a_used = 0, a_par = 0;
+        bool ok = true;
+        for (int s = wk.x; s < wk.y && ok; ++s) {
+            const int j = s / NT, D = s - j * NT, a = j / sh.n_kb, kb = j - a * sh.n_kb;
+            if (a != cur_a) {
+                ok = wait2(c, pa_empty, ((uint32_t)na & 1u) ^ 1u, abort_flag, wlim, 1, s, na);
+                if (!ok) break;
+                mbar_expect_tx(pa_full, pa_bytes);
+                tma_load_4d(sPA, &tmB, 0, -kTcPad, 0, a * (kTcM / 8), pa_full);
+                ++na;
+                cur_a = a;
+            }
+            if (kb != cur_kb) {
+                ok = wait2(c, pk_empty, ((uint32_t)nk & 1u) ^ 1u, abort_flag, wlim, 2, s, nk);
+                if (!ok) break;
+                mbar_expect_tx(pk_full, pk_bytes);
+                tma_load_4d(sPK, &tmB64, 0, -kTcPad, 0, kb * (kTcK / 8), pk_full);
+                ++nk;
+                cur_kb = kb;
+            }
+            ok = wait2(c, a_empty + 8u * sa, pa ^ 1u, abort_flag, wlim, 3, s, sa);
+            if (!ok) break;
+            mbar_expect_tx(a_full + 8u * sa, kTcAStage);
+            tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmA, 0, a * kTcM, kb, D, 0, a_full + 8u * sa);
+            a_used |= 1u << sa;
+            a_par = (a_par & ~(1u << sa)) | (pa << sa);
+            if (prog) prog[blockIdx.x * 32 + 0] = s - wk.x + 1;
+            if (++sa == S) { sa = 0; pa ^= 1u; }
+        }
+        // retire the copies in flight (only the latest load of a slot or a staged copy can be)
+        for (int q = 0; q < S; ++q)
+            if (a_used >> q & 1u) mbar_wait_final(a_full + 8u * q, a_par >> q & 1u, kTcWait);
+        if (na > 0) mbar_wait_final(pa_full, (uint32_t)(na - 1) & 1u, kTcWait);
+        if (nk > 0) mbar_wait_final(pk_full, (uint32_t)(nk - 1) & 1u, kTcWait);
+    } else if (warp >= 1 && warp < kTcEpi0 && lane == 0) {
+        // ---- MMA issuers: stage i (slot i % S, accumulator pair i % NA) by warp 1 + i % kTcIssuers;
+        // every issuer follows every copy change (waits for the new copy, frees the old one)
+        const int me = warp - 1;
+        int cur_a = -1, cur_kb = -1, na = 0, nk = 0;
+        bool ok = true;
+        for (int s = wk.x, i = 0; s < wk.y && ok; ++s, ++i) {
+            const int j = s / NT, D = s - j * NT, a = j / sh.n_kb, kb = j - a * sh.n_kb;
+            if (a != cur_a) {
+                if (cur_a >= 0) mma_commit(pa_empty);
+                ok = wait2(c, pa_full, (uint32_t)na & 1u, abort_flag, wlim, 4, s, na);
+                if (!ok) break;
+                ++na;
+                cur_a = a;
+                tc_fence_after();
+            }
+            if (kb != cur_kb) {
+                if (cur_kb >= 0) mma_commit(pk_empty);
+                ok = wait2(c, pk_full, (uint32_t)nk & 1u, abort_flag, wlim, 5, s, nk);
+                if (!ok) break;
+                ++nk;
+                cur_kb = kb;
+                tc_fence_after();
+            }
+            if (i % kTcIssuers != me) continue;
+            const int sa_i = i % S, ai = i % NA;
+            const uint32_t pa_i = (uint32_t)(i / S) & 1u, pacc_i = (uint32_t)(i / NA) & 1u;
+            // accumulator first: the drain of stage i - NA.  With fewer accumulator pairs
+            // than issuers, stages that share a pair belong to different issuers, which can
+            // run ahead of one another; a parity wait cannot tell a barrier two phases behind
+            // from one that is done, so the issuers wait on the exact count of drained stages.
+            // That count implies every stage up to i - NA has finished its MMAs, so (S >= NA)
+            // the previous load of this stage's slot has landed and its parity wait is exact.
+            if (i >= NA) {
+                const unsigned need = (unsigned)kTcEpiWarps * (unsigned)(i - NA + 1);
+                const long long t0 = clock64();
+                while (*drained < need) {
+                    if (*abort_flag) { ok = false; break; }
+                    if (clock64() - t0 > wlim) {
+                        *abort_flag = 1;
+                        if (atomicCAS(&c.sc->tc_where[0], 0, 6) == 0) {
+                            c.sc->tc_where[1] = blockIdx.x;
+                            c.sc->tc_where[2] = s;
+                            c.sc->tc_where[3] = i;
+                            c.sc->tc_where[5] = threadIdx.x;
+                        }
+                        ok = false;
+                        break;
+                    }
+                }
+                __threadfence_block();
+            }
+            (void)pacc_i;
+            if (ok) ok = wait2(c, a_full + 8u * sa_i, pa_i, abort_flag, wlim, 7, s, sa_i);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = sA + (uint32_t)sa_i * kTcAStage;
+            const uint32_t col0 = tmem + (uint32_t)ai * 2u * acc_cols;
+            {
+                // (1) y[a] += T_D[a][kb] p[kb](t - D), turns D <= t < NT, from a multiple of 8
+                const int ts = D & ~7;
+                const int n = (NT - ts + 15) & ~15;
+                const uint64_t a_hi = sdesc(ah, 16u, 1024u, 2u);
+                const uint64_t a_lo = a_hi + (((uint64_t)kTcM * 128u) >> 4);
+                const uint32_t row0 = (uint32_t)(ts - D + kTcPad);
+                const uint64_t b_hi = sdesc(sPK + 16u * row0, 32u * (uint32_t)NR, 128u, 0u);
+                const uint64_t b_lo = b_hi + ((16u * (uint32_t)NR) >> 4);
+                const uint64_t b_step = (2u * 32u * (uint32_t)NR) >> 4;
+                const uint32_t idesc = idesc_f16m(n, false, kTcM);
+                const uint32_t dcol = col0 + (uint32_t)ts;
+#pragma unroll
+                for (int k = 0; k < kTcK / 16; ++k) {
+                    mma_f16(dcol, a_hi + k * (32u >> 4), b_hi + k * b_step, idesc, k > 0 ? 1u : 0u);
+                    mma_f16(dcol, a_hi + k * (32u >> 4), b_lo + k * b_step, idesc, 1u);
+                    mma_f16(dcol, a_lo + k * (32u >> 4), b_hi + k * b_step, idesc, 1u);
+                }
+            }
+            if (D > 0) {
+                // (2) y[kb] += T_D[a][kb]^T p[a](t + D), turns 0 <= t < NT - D; the tile read
+                // MN-major (M = its 64 columns, K = its 128 rows, 8-row groups 1 KB apart)
+                const int n = (NT - D + 7) & ~7;
+                const uint64_t a_hi = sdesc(ah, kTcMnLbo, kTcMnSbo, 2u);
+                const uint64_t a_lo = a_hi + (((uint64_t)kTcM * 128u) >> 4);
+                const uint32_t row0 = (uint32_t)(D + kTcPad);
+                const uint64_t b_hi = sdesc(sPA + 16u * row0, 32u * (uint32_t)NR, 128u, 0u);
+                const uint64_t b_lo = b_hi + ((16u * (uint32_t)NR) >> 4);
+                const uint64_t b_step = (2u * 32u * (uint32_t)NR) >> 4;
+                const uint32_t idesc = idesc_f16m(n, true, kTcK);
+                const uint32_t dcol = col0 + acc_cols;
+#pragma unroll
+                for (int k = 0; k < kTcM / 16; ++k) {
+                    mma_f16(dcol, a_hi + k * (2048u >> 4), b_hi + k * b_step, idesc, k > 0 ? 1u : 0u);
+                    mma_f16(dcol, a_hi + k * (2048u >> 4), b_lo + k * b_step, idesc, 1u);
+                    mma_f16(dcol, a_lo + k * (2048u >> 4), b_hi + k * b_step, idesc, 1u);
+                }
+            }
+            mma_commit(a_empty + 8u * sa_i);
+            mma_commit(acc_full + 8u * ai);
+            if (prog) prog[blockIdx.x * 32 + 1 + me] = i + 1;
+        }
+        mma_commit(mma_done);
+        if (!mbar_wait_final(mma_done, 0u, kTcWait)) {
+            *abort_flag = 1;
+            if (atomicCAS(&c.sc->tc_where[0], 0, 9) == 0) c.sc->tc_where[1] = blockIdx.x;
+        }
+    } else if (warp >= kTcEpi0) {
+        // ---- drain: both accumulators of every stage into FP32 registers, a partial tile
+        // pair per combination
+        const int q = warp & 3;
+        const int h = (warp - kTcEpi0) >> 2;
+        const int hf = lane >> 4;                       // (2): the half of the warp (group 2m + hf)
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        float acc1[kTcGroups][8];                       // group g = kTcParities gi + h
+        float acc2[2][8];                               // group 2 (h + 4 k) + hf, kb channel 16 q + lane % 16
+#pragma unroll
+        for (int g = 0; g < kTcGroups; ++g)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc1[g][j] = 0.f;
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc2[g][j] = 0.f;
+        auto flush = [&](int seg) {
+            float* o1 = part1 + (size_t)seg * NT * kTcM + 32 * q + lane;
+#pragma unroll
+            for (int gi = 0; gi < kTcGroups; ++gi) {
+                const int t0 = 8 * (kTcParities * gi + h);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    if (t0 + jj < NT) o1[(size_t)(t0 + jj) * kTcM] = acc1[gi][jj];
+                    acc1[gi][jj] = 0.f;
+                }
+            }
+            float* o2 = part2 + (size_t)seg * NT * kTcK + 16 * q + (lane & 15);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int t0 = 8 * (2 * (h + 4 * k) + hf);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    if (t0 + jj < NT) o2[(size_t)(t0 + jj) * kTcK] = acc2[k][jj];
+                    acc2[k][jj] = 0.f;
+                }
+            }
+        };
+        int ai = 0, cur_j = -1, seg = wk.z - 1;
+        uint32_t pf = 0;
+        bool ok = true;
+        for (int s = wk.x; s < wk.y && ok; ++s) {
+            const int j = s / NT, D = s - j * NT;
+            if (j != cur_j) {
+                if (cur_j >= 0) flush(seg);
+                cur_j = j;
+                ++seg;
+            }
+            ok = __all_sync(0xffffffffu, wait2(c, acc_full + 8u * ai, (pf >> ai) & 1u, abort_flag, wlim, 8, s, ai));
+            if (!ok) break;
+            pf ^= 1u << ai;
+            tc_fence_after();
+            const uint32_t src1 = lane_base + (uint32_t)ai * 2u * acc_cols;
+            const int g_lo = D >> 3, g_hi = (NT + 7) >> 3;
+#pragma unroll
+            for (int gi = 0; gi < kTcGroups; ++gi) {
+                const int g = kTcParities * gi + h;
+                if (g >= g_lo && g < g_hi) {
+                    float v[8];
+                    tmem_ld8(src1 + 8u * (uint32_t)g, v);
+                    scale_add8(inv_s, scp, 8 * g + kTcPad - D, v, acc1[gi]);
+                }
+            }
+            if (D > 0) {
+                const uint32_t src2 = src1 + acc_cols;
+                const int g_hi2 = (NT - D + 7) >> 3;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int g0 = 2 * (h + 4 * k);             // this pair's first group (warp-uniform)
+                    if (g0 < g_hi2) {
+                        float v[8];
+                        tmem_ld16x2_8(src2 + 8u * (uint32_t)g0, v);
+                        const int g = g0 + hf;
+                        if (g < g_hi2) scale_add8(inv_s, scp, 8 * g + kTcPad + D, v, acc2[k]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicAdd(const_cast<unsigned*>(drained), 1u);
+            }
+            if (prog && lane == 0) prog[blockIdx.x * 32 + 8 + (warp - kTcEpi0)] = s - wk.x + 1;
+            if (++ai == NA) ai = 0;
+        }
+        if (ok && !*abort_flag && cur_j >= 0) flush(seg);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicExch(&c.sc->status, (int)ST_KERNEL);
+        atomicExch(&c.sc->done, 1);
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, (uint32_t)sh.ncols);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Input split, reduction, table
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float block_max_f(float v) {
@@ -592,6 +999,28 @@ __global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, co
     }
 }
 
+// Mode 1: q[e] = 2^-(exT + xmin) x (the part1 segments of e's channel tile +
+// the part2 segments of e's k block), fixed order, FP64.
+__global__ void k_tc2_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ part1,
+                             const float* __restrict__ part2, const int2* __restrict__ l1, const int* __restrict__ segs1,
+                             const int2* __restrict__ l2, const int* __restrict__ segs2, const int* __restrict__ pexp,
+                             int exT) {
+    const CoilDev& c = *cd;
+    if (c.sc->done) return;
+    const double inv = ldexp(1.0, -(exT + warp_min_exponent(pexp, sh.NT, threadIdx.x & 31)));
+    const size_t t1 = (size_t)sh.NT * kTcM, t2 = (size_t)sh.NT * kTcK;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sh.N; e += gridDim.x * blockDim.x) {
+        const int t = e / sh.C, cc = e - t * sh.C;
+        const int2 r1 = l1[cc / kTcM], r2 = l2[cc / kTcK];
+        const float* p1 = part1 + (size_t)t * kTcM + (cc % kTcM);
+        const float* p2 = part2 + (size_t)t * kTcK + (cc % kTcK);
+        double s = 0.0;
+        for (int k = 0; k < r1.y; ++k) s += (double)p1[(size_t)segs1[r1.x + k] * t1];
+        for (int k = 0; k < r2.y; ++k) s += (double)p2[(size_t)segs2[r2.x + k] * t2];
+        c.qv[e] = s * inv;
+    }
+}
+
 __global__ void k_tc_absmax(const double* __restrict__ tab, long long n, double* __restrict__ out) {
     double m = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -635,6 +1064,12 @@ __global__ void k_tc_table(const double* __restrict__ tab, const TcShape sh, int
 // Host side
 // ---------------------------------------------------------------------------
 size_t tc_smem_bytes(const TcShape& sh) {
+    if (sh.mode == 1) {
+        const size_t pa = ((size_t)kT2ABytes * sh.NR + 1023) & ~(size_t)1023;
+        const size_t pk = ((size_t)kT2KBytes * sh.NR + 1023) & ~(size_t)1023;
+        return 1024 + (size_t)sh.stages * kTcAStage + pa + pk + 8 * (size_t)kT2Bars(sh.stages, sh.n_acc) + 32 +
+               16 * (size_t)((sh.NR + 7) & ~3);
+    }
     size_t b_pitch = ((size_t)512 * sh.NR + 127) & ~(size_t)127;
     return 1024 + kTcBStages * b_pitch + (size_t)sh.stages * kTcAStage + 8 * (size_t)kTcBars(sh.stages) + 32 +
            16 * (size_t)((sh.NR + 7) & ~3);
@@ -670,6 +1105,78 @@ bool tc_shape(int C, int NT, int n_sm, TcShape* sh) {
     return true;
 }
 
+bool tc2_shape(int C, int NT, int n_sm, int n_cta, int stages, TcShape* sh) {
+    if (C < 1 || NT < 1 || NT > kTcMaxTurns) return false;
+    TcShape s{};
+    s.mode = 1;
+    s.C = C;
+    s.Cp = (C + 7) & ~7;
+    s.NT = NT;
+    s.NR = NT + kTcPad + kTcPadTop;
+    s.N = C * NT;
+    s.n_ct = (C + kTcM - 1) / kTcM;
+    s.n_kb = (s.Cp + kTcK - 1) / kTcK;
+    s.n_combo = s.n_ct * s.n_kb;
+    const long long total = (long long)s.n_combo * NT;
+    long long ctas = n_cta > 0 ? n_cta : std::min<long long>(n_sm, std::max<long long>(1, total / kT2MinStages));
+    s.n_cta = (int)std::max<long long>(1, std::min<long long>(ctas, total));
+    int used = (NT + 15) & ~7;        // an MMA's columns end before NT + 15
+    s.acc_cols = 32;
+    while (s.acc_cols < used) s.acc_cols *= 2;
+    s.n_acc = 512 / (2 * s.acc_cols) > 4 ? 4 : 512 / (2 * s.acc_cols);   // accumulator pairs
+    if (s.n_acc < 1) return false;
+    s.ncols = 32;
+    while (s.ncols < 2 * s.n_acc * s.acc_cols) s.ncols *= 2;
+    const size_t limit = kTcSmemLimit;
+    s.stages = stages > 0 ? stages : 6;
+    while (s.stages > 2 && tc_smem_bytes(s) > limit) --s.stages;
+    if (tc_smem_bytes(s) > limit) return false;
+    if (s.n_acc > s.stages) {          // the issuers' slot waits rely on stages >= accumulators
+        s.n_acc = s.stages;
+        s.ncols = 32;
+        while (s.ncols < 2 * s.n_acc * s.acc_cols) s.ncols *= 2;
+    }
+    *sh = s;
+    return true;
+}
+
+// Equal contiguous ranges of the (a, kb, D) stage order; a CTA's range gets a
+// segment per combination it touches (consecutive segment numbers), and every
+// segment is listed under its channel tile (l1/segs1, the products (1)) and
+// its k block (l2/segs2, the transposed products (2)), in segment order.
+size_t tc2_schedule(TcShape* sh, std::vector<int4>* work, std::vector<int2>* l1, std::vector<int>* segs1,
+                    std::vector<int2>* l2, std::vector<int>* segs2) {
+    const long long NT = sh->NT, total = (long long)sh->n_combo * NT;
+    const long long n = sh->n_cta;
+    std::vector<std::vector<int>> by_a(sh->n_ct), by_kb(sh->n_kb);
+    work->clear();
+    int seg = 0;
+    for (long long i = 0; i < n; ++i) {
+        const long long s0 = total * i / n, s1 = total * (i + 1) / n;
+        work->push_back(make_int4((int)s0, (int)s1, seg, 0));
+        if (s1 <= s0) continue;
+        for (long long j = s0 / NT; j <= (s1 - 1) / NT; ++j) {
+            by_a[j / sh->n_kb].push_back(seg);
+            by_kb[j % sh->n_kb].push_back(seg);
+            ++seg;
+        }
+    }
+    sh->n_seg = seg;
+    l1->clear();
+    l2->clear();
+    segs1->clear();
+    segs2->clear();
+    for (auto& v : by_a) {
+        l1->push_back(make_int2((int)segs1->size(), (int)v.size()));
+        segs1->insert(segs1->end(), v.begin(), v.end());
+    }
+    for (auto& v : by_kb) {
+        l2->push_back(make_int2((int)segs2->size(), (int)v.size()));
+        segs2->insert(segs2->end(), v.begin(), v.end());
+    }
+    return (size_t)n;
+}
+
 // The same number of CTAs for every channel tile (n_sm / n_ct, at least one,
 // at most one per step, and beyond four at most one per eight steps).  Tile ct's j-th CTA and tile cb's j-th CTA meet the
 // 128 x 128 region (ct, cb) of every stored offset block at about the same
@@ -690,7 +1197,8 @@ size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::ve
     // small coil's apply then takes a few SMs, not one CTA per SM with a step
     // or two each, so a batch's applies on the side streams run side by side;
     // the kTcMinCtas floor keeps each CTA's FP32 register sums short
-    const long long cap = std::max(std::min(per, kTcMinCtas), steps / kTcMinSteps);
+    const long long min_steps = sh.min_steps > 0 ? sh.min_steps : kTcMinSteps;
+    const long long cap = std::max(std::min(per, kTcMinCtas), steps / min_steps);
     if (per > cap) per = cap;
     if (work && range) {
         work->clear();
@@ -798,6 +1306,12 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
         CUresult r = enc(&P->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->p16, dims, strides, box, ones,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        // the one-fill apply's p[kb]: 64 channels (8 chunks) per box
+        const cuuint32_t box64[4] = {8, (cuuint32_t)sh.NR, 2, (cuuint32_t)(kTcK / 8)};
+        if (r == CUDA_SUCCESS)
+            r = enc(&P->tmB64, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, P->p16, dims, strides, box64, ones,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             *why = "encoding the input tensor map failed";
             return cudaErrorInvalidValue;
@@ -806,6 +1320,8 @@ cudaError_t tc_encode_maps(TcPlan* P, const char** why) {
     // the attribute belongs to the kernel, not to the coil: set the largest size
     // any coil may take, so that every coil's launch fits
     cudaError_t e = cudaFuncSetAttribute(k_toeplitz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_toeplitz_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLimit);
     if (e != cudaSuccess) *why = "setting the shared-memory size of the tensor-core apply failed";
     return e;
 }
@@ -817,6 +1333,16 @@ cudaError_t launch_tc_split(const TcPlan& P, cudaStream_t s, bool dir) {
 
 cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q) {
     const TcShape& sh = P.sh;
+    if (sh.mode == 1) {
+        k_toeplitz_tc2<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.tmB64, P.d, sh, P.work, P.pexp, P.part,
+                                                             P.part2, P.prog);
+        if (write_q) {
+            int rb = (sh.N + 255) / 256;
+            if (rb > 148 * 8) rb = 148 * 8;
+            k_tc2_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.part2, P.l1, P.segs1, P.l2, P.segs2, P.pexp, P.exT);
+        }
+        return cudaGetLastError();
+    }
     k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmAT, P.tmB, P.d, sh, P.work, P.pexp, P.part);
     if (write_q) {
         int rb = (sh.N + 255) / 256;

@@ -21,17 +21,38 @@ struct TcShape {
     int stages;                 // table tiles in flight per CTA
     int acc_cols, n_acc;        // TMEM columns per accumulator, accumulators (stages alternate)
     int ncols;                  // TMEM columns allocated per CTA (n_acc acc_cols)
+    // mode 1 (one-fill apply, k_toeplitz_tc2): work units (channel tile, k block),
+    // n_acc counts accumulator pairs, n_seg partial-tile segments in all
+    int mode;
+    int n_combo, n_seg;
+    int min_steps;              // mode 0: schedule steps per CTA at least beyond a few CTAs per tile
+                                // (0: the default; 1: one CTA per SM and channel tile share)
 };
 
 struct TcPlan {
     CUtensorMap tmA;            // split table: [half][offset >= 0][c'/64][c][c' % 64] FP16, 128-byte swizzle
     CUtensorMap tmAT;           // the same table, transposed-tile boxes (offsets < 0)
     CUtensorMap tmB;            // split input: [c'/8][hi, lo][t][c' % 8] FP16, no swizzle
+    CUtensorMap tmB64;          // the same input, 64-channel boxes (mode 1)
     TcShape sh;
     const CoilDev* d = nullptr; // device descriptor of the coil
     __half* t16 = nullptr;      // 2 NT n_kb C 64
     __half* p16 = nullptr;      // 2 Cp NT
-    float* part = nullptr;      // n_cta x NT x 128 partial tiles
+    float* part = nullptr;      // n_cta x NT x 128 partial tiles (mode 1: n_seg x NT x 128)
+    float* part2 = nullptr;     // mode 1: n_seg x NT x 64 partial tiles of the transposed products
+    int2* l1 = nullptr;         // mode 1: per channel tile (first, count) into segs1
+    int2* l2 = nullptr;         // mode 1: per k block (first, count) into segs2
+    int* segs1 = nullptr;
+    int* segs2 = nullptr;
+    int* prog = nullptr;        // mode 1: progress per CTA (32 ints: producer, issuers, drain warps),
+                                // read back when a bounded wait ran out
+    std::vector<void*> sched_bufs;   // device buffers of the current schedule
+    size_t sched_bytes = 0;
+    struct Tuned { int mode, n_cta, stages; double us; };
+    std::vector<Tuned> tuned;   // the autotuner's candidates and their measured apply time
+    double tuned_us = 0.0;      // the chosen schedule's apply time
+    TcShape tuned_sh{};         // the autotuner's choice for this coil alone
+    bool in_batch = false;      // the schedule is the batched steps' one (tuned_sh restored when stepped alone)
     int4* work = nullptr;       // n_cta (tile, first stage, end stage, 0)
     int2* range = nullptr;      // n_ct (first CTA, CTAs)
     int* pexp = nullptr;        // NT input scale exponents (one per turn row)
@@ -44,6 +65,12 @@ constexpr int kTcMaxTurns = 112;   // the staged copy's 2 (NT + 16) rows fit one
 
 // Fill the shape for C channels, NT turns on n_sm SMs; false if unsupported.
 bool tc_shape(int C, int NT, int n_sm, TcShape* sh);
+// The same for the one-fill apply (mode 1); n_cta = 0: the default CTA count.
+bool tc2_shape(int C, int NT, int n_sm, int n_cta, int stages, TcShape* sh);
+// Its schedule: work[cta] = (first stage, end stage, first segment, 0) and the
+// reduction lists; fills sh->n_seg.  Returns the number of CTAs.
+size_t tc2_schedule(TcShape* sh, std::vector<int4>* work, std::vector<int2>* l1, std::vector<int>* segs1,
+                    std::vector<int2>* l2, std::vector<int>* segs2);
 size_t tc_table_halves(const TcShape& sh);
 // CTA schedule of the apply; fills work/range when both are non-null.
 size_t tc_schedule(const TcShape& sh, int n_sm, std::vector<int4>* work, std::vector<int2>* range);
