@@ -116,6 +116,10 @@ struct coil {
     BatchGraph* batch = nullptr;
     size_t ev_used = 0;          // event pairs recorded since the last harvest
     cq::TcPlan* tc = nullptr;    // tensor-core Toeplitz apply (format 2)
+    // the first coil of a batch keeps the batch's one-launch tensor-core
+    // applies (the coils' arguments) for that set of coils
+    cq::TcBatch* tcb = nullptr;
+    std::vector<long long> tcb_ids;
 };
 
 namespace {
@@ -917,6 +921,8 @@ struct Launch {
     // sets the loop's condition
     bool fuse_cond = false;
     cudaGraphConditionalHandle cond = 0;
+    // format 2 batches: every coil's apply in one launch of each kernel
+    const TcBatch* tcb = nullptr;
 };
 
 Launch single_launch(coil_t* c) {
@@ -946,6 +952,7 @@ Launch single_launch(coil_t* c) {
 cudaError_t launch_far(const Launch& L, int which) {
     if (L.format == 1) return launch_toeplitz(L.d, L.n, L.maxC, L.maxNT, L.maxN, L.n_sm, L.s);
     if (L.format == 2) {
+        if (L.tcb && L.tc.size() > 1) return launch_tc_batch(*L.tcb, L.s, L.need_q, L.dir);
         if (L.n_aux > 0 && L.tc.size() > 1) {
             // a batch: the coils' applies are independent, so they run side by
             // side on the side streams (one SM per CTA each: a small coil's
@@ -1440,9 +1447,10 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
     }
     cudaSetDevice(c->device);
     if (c->h.op_format == 2 && n > 1) {
-        // batched tensor-core applies run side by side on the side streams: each
-        // coil takes the two-fill schedule with its step floor per CTA (a small
-        // coil's apply on a few SMs), not the autotuner's choice for running alone
+        // batched tensor-core applies: each coil takes the two-fill schedule with
+        // its step floor per CTA (not the autotuner's choice for running alone),
+        // and the CTAs of all coils run in one launch
+        bool replanned = false;
         for (int i = 0; i < n; ++i) {
             coil_t* ci = coils[i];
             if (!ci->tc || ci->tc->in_batch) continue;
@@ -1451,6 +1459,25 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
                 return fail(c, COIL_ERR_INVALID, "coil shape not supported by the tensor-core Toeplitz format");
             TRY(tc_plan_schedule(ci, sb));
             ci->tc->in_batch = true;
+            replanned = true;
+        }
+        std::vector<long long> ids(n);
+        for (int i = 0; i < n; ++i) ids[i] = coils[i]->uid;
+        if (replanned || !c->tcb || c->tcb_ids != ids) {
+            // the schedules' buffers or the coil set changed: new arguments, new graph
+            CK(cudaStreamSynchronize(c->stream), "batch applies");
+            if (c->batch) {
+                if (c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
+                cudaFree(c->batch->dd);
+                cudaFreeHost(c->batch->hstat);
+                delete c->batch;
+                c->batch = nullptr;
+            }
+            if (!c->tcb) c->tcb = new TcBatch();
+            std::vector<const TcPlan*> plans;
+            for (int i = 0; i < n; ++i) plans.push_back(coils[i]->tc);
+            CK(tc_batch_build(c->tcb, plans, c->stream), "batch applies");
+            c->tcb_ids = ids;
         }
     }
     Launch L;
@@ -1477,7 +1504,9 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.big = L.big || ci->h.B > kSegMax;
         if (ci->tc) L.tc.push_back(ci->tc);
     }
-    if (L.format == 2 && n > 1) {
+    if (L.format == 2 && n > 1 && c->tcb) {
+        L.tcb = c->tcb;
+    } else if (L.format == 2 && n > 1) {
         if (c->aux.empty()) {
             for (int a = 0; a < kAuxStreams; ++a) {
                 cudaStream_t st;
@@ -1992,6 +2021,10 @@ void coil_destroy(coil_t* c) {
         cudaFree(c->batch->dd);
         cudaFreeHost(c->batch->hstat);
         delete c->batch;
+    }
+    if (c->tcb) {
+        tc_batch_free(c->tcb);
+        delete c->tcb;
     }
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
     for (cudaEvent_t e : c->aux_ev) cudaEventDestroy(e);

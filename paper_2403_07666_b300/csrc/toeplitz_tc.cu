@@ -211,12 +211,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 // The apply
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTcThreads, 1)
-k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAT,
-              const __grid_constant__ CUtensorMap tmB,
-              const CoilDev* __restrict__ cd, const TcShape sh, const int4* __restrict__ work,
-              const int* __restrict__ pexp, float* __restrict__ part) {
-    const CoilDev& c = *cd;
+// The two-fill apply of one coil by one CTA: work entry wk = (channel tile,
+// first step, end step), partial tile `cta` of `part`.  The tensor maps may
+// live in the kernel's parameters or in global memory (a batch).
+__device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUtensorMap* mapAT,
+                                             const CUtensorMap* mapB, const CoilDev& c, const TcShape sh,
+                                             const int4 wk, const int cta, const int* __restrict__ pexp,
+                                             float* __restrict__ part) {
+    const CUtensorMap& tmA = *mapA;
+    const CUtensorMap& tmAT = *mapAT;
+    const CUtensorMap& tmB = *mapB;
     if (c.sc->done) return;
     // the limit of the waits that raise the abort flag (a test hook can shorten
     // it; the waits that retire work already in flight keep kTcWait)
@@ -254,7 +258,6 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // Column tile cb's CTA with the same step range is at step k with cb and ct
     // exchanged: it reads the same 128 x 128 region of the stored T_D, transposed,
     // at the same time, so that region comes from DRAM once and from L2 once.
-    const int4 wk = work[blockIdx.x];
     const int ct = wk.x, c0 = ct * kTcM;
     auto col_tile = [&](int sg) { return (sg / sh.NT - ct + sh.n_ct) % sh.n_ct; };
     const int n_acc = sh.n_acc;
@@ -476,7 +479,7 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         if (ok && !*abort_flag && cc < sh.C) {
             // partial tile of this CTA: part[cta][t][c - c0]
-            float* out = part + (size_t)blockIdx.x * sh.NT * kTcM + 32 * q + lane;
+            float* out = part + (size_t)cta * sh.NT * kTcM + 32 * q + lane;
 #pragma unroll
             for (int gi = 0; gi < kTcGroups; ++gi) {
                 const int t0 = 8 * (kTcParities * gi + h);
@@ -497,6 +500,28 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         __syncwarp();
         tmem_dealloc(tmem, (uint32_t)sh.ncols);
     }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAT,
+              const __grid_constant__ CUtensorMap tmB,
+              const CoilDev* __restrict__ cd, const TcShape sh, const int4* __restrict__ work,
+              const int* __restrict__ pexp, float* __restrict__ part) {
+    tc_apply_cta(&tmA, &tmAT, &tmB, *cd, sh, work[blockIdx.x], (int)blockIdx.x, pexp, part);
+}
+
+// A batch's applies in one launch: CTA b works for coil bwork[b].x as its
+// CTA bwork[b].y, with that coil's maps, schedule and partial tiles.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_toeplitz_tc_batch(const TcCoilArgs* __restrict__ args, const int2* __restrict__ bwork) {
+    const int2 bw = bwork[blockIdx.x];
+    const TcCoilArgs& A = args[bw.x];
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmAT)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmB)) : "memory");
+    }
+    tc_apply_cta(&A.tmA, &A.tmAT, &A.tmB, *A.d, A.sh, A.work[bw.y], bw.y, A.pexp, A.part);
 }
 
 // ---------------------------------------------------------------------------
@@ -942,11 +967,9 @@ __host__ __device__ inline int tc_exponent(double m) {
 // the PCG's next search direction, formed here first (from the second
 // iteration on), d = -z + beta d (FP64 into d, FP32 into the input copy), in
 // place of a separate pass.
-__global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
-                           int* __restrict__ pexp, int dir) {
-    const CoilDev& c = *cd;
+__device__ __forceinline__ void tc_split_row(const CoilDev& c, const TcShape& sh, __half* __restrict__ p16,
+                                             int* __restrict__ pexp, int dir, const int t) {
     if (c.sc->done) return;
-    const int t = blockIdx.x;
     float* row = c.pf + (size_t)t * sh.C;
     if (dir && c.sc->iter > 0) {                 // the first iteration's direction is k_init's
         const double beta = c.sc->beta;
@@ -972,12 +995,24 @@ __global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __h
     }
 }
 
+__global__ void k_tc_split(const CoilDev* __restrict__ cd, const TcShape sh, __half* __restrict__ p16,
+                           int* __restrict__ pexp, int dir) {
+    tc_split_row(*cd, sh, p16, pexp, dir, (int)blockIdx.x);
+}
+
+// A batch's input splits in one launch: block (t, coil).
+__global__ void k_tc_split_batch(const TcCoilArgs* __restrict__ args, int dir) {
+    const TcCoilArgs& A = args[blockIdx.y];
+    if ((int)blockIdx.x >= A.sh.NT) return;
+    tc_split_row(*A.d, A.sh, A.p16, A.pexp, dir, (int)blockIdx.x);
+}
+
 // q[e] = 2^-(exT + xmin) x the sum of the partial tiles of the CTAs that
 // worked on e's channel tile (fixed order, FP64; the loads of eight tiles are
 // issued before their sums).  range[ct] = (first CTA, number of CTAs).
-__global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ part,
-                            const int2* __restrict__ range, const int* __restrict__ pexp, int exT) {
-    const CoilDev& c = *cd;
+__device__ __forceinline__ void tc_reduce_body(const CoilDev& c, const TcShape& sh, const float* __restrict__ part,
+                                               const int2* __restrict__ range, const int* __restrict__ pexp,
+                                               int exT) {
     if (c.sc->done) return;
     const double inv = ldexp(1.0, -(exT + warp_min_exponent(pexp, sh.NT, threadIdx.x & 31)));
     const size_t tile = (size_t)sh.NT * kTcM;
@@ -997,6 +1032,19 @@ __global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, co
         for (; k < rg.y; ++k) s += (double)p[(size_t)k * tile];
         c.qv[e] = s * inv;
     }
+}
+
+__global__ void k_tc_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ part,
+                            const int2* __restrict__ range, const int* __restrict__ pexp, int exT) {
+    tc_reduce_body(*cd, sh, part, range, pexp, exT);
+}
+
+// A batch's reductions into q (coils whose near kernel does not sum the
+// partial tiles itself, or all of them with need_q): grid row = coil.
+__global__ void k_tc_reduce_batch(const TcCoilArgs* __restrict__ args, int need_q) {
+    const TcCoilArgs& A = args[blockIdx.y];
+    if (!need_q && !A.write_q) return;
+    tc_reduce_body(*A.d, A.sh, A.part, A.range, A.pexp, A.exT);
 }
 
 // Mode 1: q[e] = 2^-(exT + xmin) x (the part1 segments of e's channel tile +
@@ -1349,6 +1397,65 @@ cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q) {
         if (rb > 148 * 8) rb = 148 * 8;
         k_tc_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.range, P.pexp, P.exT);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t tc_batch_build(TcBatch* B, const std::vector<const TcPlan*>& plans, cudaStream_t s) {
+    tc_batch_free(B);
+    std::vector<TcCoilArgs> args(plans.size());
+    std::vector<int2> bwork;
+    B->n = (int)plans.size();
+    B->smem = 0;
+    B->maxNT = B->maxN = 0;
+    for (size_t i = 0; i < plans.size(); ++i) {
+        const TcPlan& P = *plans[i];
+        if (P.sh.mode != 0) return cudaErrorInvalidValue;     // batches run the two-fill apply
+        TcCoilArgs& A = args[i];
+        A.tmA = P.tmA;
+        A.tmAT = P.tmAT;
+        A.tmB = P.tmB;
+        A.sh = P.sh;
+        A.d = P.d;
+        A.work = P.work;
+        A.range = P.range;
+        A.pexp = P.pexp;
+        A.part = P.part;
+        A.p16 = P.p16;
+        A.exT = P.exT;
+        A.write_q = P.fused ? 0 : 1;
+        for (int k = 0; k < P.sh.n_cta; ++k) bwork.push_back(make_int2((int)i, k));
+        B->smem = std::max(B->smem, P.smem);
+        B->maxNT = std::max(B->maxNT, P.sh.NT);
+        B->maxN = std::max(B->maxN, P.sh.N);
+    }
+    B->n_cta = (int)bwork.size();
+    cudaError_t e = cudaMalloc(&B->args, args.size() * sizeof(TcCoilArgs));
+    if (e == cudaSuccess) e = cudaMalloc(&B->work, bwork.size() * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->args, args.data(), args.size() * sizeof(TcCoilArgs), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->work, bwork.data(), bwork.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_toeplitz_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLimit);
+    if (e != cudaSuccess) tc_batch_free(B);
+    return e;
+}
+
+void tc_batch_free(TcBatch* B) {
+    if (B->args) cudaFree(B->args);
+    if (B->work) cudaFree(B->work);
+    B->args = nullptr;
+    B->work = nullptr;
+    B->n = B->n_cta = 0;
+}
+
+cudaError_t launch_tc_batch(const TcBatch& B, cudaStream_t s, bool need_q, bool dir) {
+    k_tc_split_batch<<<dim3((unsigned)B.maxNT, (unsigned)B.n), 256, 0, s>>>(B.args, dir ? 1 : 0);
+    k_toeplitz_tc_batch<<<(unsigned)B.n_cta, kTcThreads, B.smem, s>>>(B.args, B.work);
+    int rb = (B.maxN + 255) / 256;
+    if (rb > 148 * 8) rb = 148 * 8;
+    k_tc_reduce_batch<<<dim3((unsigned)rb, (unsigned)B.n), 256, 0, s>>>(B.args, need_q ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,31 @@ struct TcPlan {
     bool fused = false;         // the coil's near kernel sums the partial tiles itself
 };
 
+// One coil's arguments of a batched apply (device memory; the tensor maps
+// must sit on 64-byte boundaries).
+struct alignas(64) TcCoilArgs {
+    CUtensorMap tmA, tmAT, tmB;
+    TcShape sh;
+    const CoilDev* d;
+    const int4* work;
+    const int2* range;
+    int* pexp;
+    float* part;
+    __half* p16;
+    int exT;
+    int write_q;                // the reduction into q is this coil's (its near kernel does not sum tiles)
+};
+
+// The applies of a batch of coils as one launch of each kernel (split, apply,
+// reduction): every coil with its own two-fill schedule, the CTAs of all
+// coils in one grid.
+struct TcBatch {
+    TcCoilArgs* args = nullptr;
+    int2* work = nullptr;       // per CTA: (coil, the coil's CTA index)
+    int n = 0, n_cta = 0, maxNT = 0, maxN = 0;
+    size_t smem = 0;
+};
+
 constexpr int kTcMaxTurns = 112;   // the staged copy's 2 (NT + 16) rows fit one TMA box (<= 256)
 
 // Fill the shape for C channels, NT turns on n_sm SMs; false if unsupported.
@@ -90,5 +115,11 @@ cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bo
 // (k_toeplitz_tc, plus the FP64 reduction into q when write_q).
 cudaError_t launch_tc_split(const TcPlan& P, cudaStream_t s, bool dir);
 cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q);
+// Batches: build (uploads the coils' arguments; every plan in the two-fill
+// mode), free, and launch split + apply + reductions (need_q: every coil's
+// result into q; dir: form the PCG direction first).
+cudaError_t tc_batch_build(TcBatch* B, const std::vector<const TcPlan*>& plans, cudaStream_t s);
+void tc_batch_free(TcBatch* B);
+cudaError_t launch_tc_batch(const TcBatch& B, cudaStream_t s, bool need_q, bool dir);
 
 }  // namespace cq
