@@ -43,6 +43,7 @@ __global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cud
                              int use_cond);
 __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds);
 __global__ void k_factor_seg(const CoilDev* __restrict__ cds);
+__global__ void k_factor_seg_groups(const CoilDev* __restrict__ cds);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg);
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
@@ -670,6 +671,9 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         TRY(upload(c, &ip, nb, "nborder")); h.nborder = ip;
         h.Ccell = m->rho_m * m->c0 * hel * hel / 4.0;
         h.helem = hel;
+        h.src_k = 4.0 / (m->rho_m * m->c0);
+        h.inv_Tref = 1.0 / m->T_ref;
+        h.inv_h2 = 1.0 / (hel * hel);
         double* t6;
         TRY(dalloc(c, &t6, 3 * (size_t)Gr + 3 * (size_t)Gz, "thomas"));
         h.thr_lo = t6; h.thr_inv = t6 + Gr; h.thr_cp = t6 + 2 * Gr;
@@ -704,7 +708,9 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.isigma, W, "1 / sigma"));
     TRY(dalloc(c, &h.cw, W, "cw"));
     TRY(dalloc(c, &h.uw, W, "uw"));
-    TRY(dalloc(c, &h.parts, 8 * (size_t)W, "parts"));
+    // 8 rows of W per-block partials; row 7 also takes the step end's 6
+    // partials per CTA, so it is at least 6 kStepEndCtas long
+    TRY(dalloc(c, &h.parts, 7 * (size_t)W + std::max<size_t>(W, 6 * kStepEndCtas), "parts"));
     TRY(dalloc(c, &h.first_jump, W, "first_jump"));
     TRY(dalloc(c, &h.first_quench, W, "first_quench"));
     CK(cudaMemsetAsync(h.first_jump, 0xff, W * sizeof(long long), c->stream), "memset");
@@ -715,7 +721,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.acc_on = 1;
     TRY(dalloc(c, &h.diag, (size_t)h.diag_cap * COIL_DIAG_WIDTH, "diag"));
     TRY(dalloc(c, &h.sc, 1, "scalars"));
-    TRY(dalloc(c, &h.ticket, 2, "arrival counters"));
+    TRY(dalloc(c, &h.ticket, 4, "arrival counters"));
     TRY(dalloc(c, &c->readbuf, 5 * (size_t)N + kMomentBlocks, "read buffer"));
 
     // operator: table of distinct entries, dense far part, FP64 near blocks
@@ -910,6 +916,7 @@ struct Launch {
     int format = 0;
     int maxC = 0, maxNT = 0;
     bool seg = false, big = false;   // coils with blocks of <= kSegMax / more elements present
+    bool groups = false;             // coils with subelements present
     bool need_q = false;             // the far apply must leave its result in q (no fused consumer)
     bool dir = false;                // format 2: the apply forms the PCG direction first
     // format 2 batches: side streams the coils' applies are spread over (fork
@@ -944,6 +951,7 @@ Launch single_launch(coil_t* c) {
     L.maxNT = h.NT;
     L.seg = h.B <= kSegMax;
     L.big = !L.seg;
+    L.groups = h.n_groups != 0;
     if (c->tc) L.tc.push_back(c->tc);
     return L;
 }
@@ -1053,7 +1061,12 @@ int launch_pointwise(const Launch& L) {
 }
 int launch_factor(const Launch& L) {
     if (L.big) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.seg) k_factor_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
+    if (L.seg) {
+        const dim3 grid((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n);
+        k_factor_seg<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);
+        if (L.groups) k_factor_seg_groups<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);
+        return (int)L.big + 1 + (int)L.groups;
+    }
     return (int)L.big + (int)L.seg;
 }
 int launch_update(const Launch& L) {
@@ -1114,7 +1127,7 @@ coil_status step_epilogue(coil_t* c, const Launch& L) {
         k_adi_z<<<dim3(L.maxGr, L.n), 32, L.maxGz * sizeof(double), L.s>>>(L.d);
         c->launches += 2;
     }
-    k_step_end<<<L.n, kRedThreads, 0, L.s>>>(L.d);
+    k_step_end<<<dim3(kStepEndCtas, L.n), kStepEndThreads, 0, L.s>>>(L.d);
     c->launches += 2;
     CK(cudaGetLastError(), "step end launch");
     return COIL_OK;
@@ -1502,6 +1515,7 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.maxNT = std::max(L.maxNT, ci->h.NT);
         L.seg = L.seg || ci->h.B <= kSegMax;
         L.big = L.big || ci->h.B > kSegMax;
+        L.groups = L.groups || ci->h.n_groups != 0;
         if (ci->tc) L.tc.push_back(ci->tc);
     }
     if (L.format == 2 && n > 1 && c->tcb) {

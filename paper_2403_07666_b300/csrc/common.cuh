@@ -19,6 +19,8 @@ constexpr int kGroupMax = 16;        // subelements per turn
 constexpr int kGroupMaxSeg = 6;      // subelements per turn of blocks of at most kSegMax elements
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
 constexpr int kTcTileRows = 128;     // channels per tile of the tensor-core Toeplitz apply
+constexpr int kStepEndCtas = 16;     // CTAs per coil of the step-end reductions
+constexpr int kStepEndThreads = 256;
 
 enum Prec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_BF16 = 2 };
 
@@ -85,6 +87,7 @@ struct CoilDev {
     const double *Kr, *Kz;
     const int *nborder;           // border faces per grid cell
     double Ccell, helem;
+    double src_k, inv_Tref, inv_h2;   // 4 / (rho_m c0), 1 / T_ref, 1 / helem^2 of the heat source
     const double *thr_lo, *thr_inv, *thr_cp;
     const double *thz_lo, *thz_inv, *thz_cp;
     // material scalars
@@ -133,7 +136,7 @@ struct CoilDev {
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;
-    unsigned *ticket;             // 2 arrival counters of the fused last-CTA reductions
+    unsigned *ticket;             // arrival counters of the last-CTA reductions (near, update, step end)
 };
 
 // Smallest of the n exponents e[0..n) over a warp (every lane gets it).

@@ -128,6 +128,88 @@ __device__ __forceinline__ ElemOut pointwise_element(const CoilDev& c, int e, do
     return o;
 }
 
+// The mixed form's element, FP64 kept to the flux stencil, the loop's
+// right-hand side R and the current sum: the stencil takes the loop flux alone
+// and adds the applied field afterwards (the 3-point derivative reproduces
+// pi r^2 B_a exactly: B_z gains B_a, B_r nothing), and E, q, G, the Joule
+// power and the reductions of the wire are FP32.  Returns q and the Joule
+// power in FP32, u = T^4 and I in FP64.
+struct ElemOutF {
+    double I, u;
+    float pj, q, jrat, frac;
+    int fil;
+};
+
+__device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e, float Ba0, double dBa) {
+    ElemOutF o;
+    const double r = c.r[e];
+    const float a = (float)c.area[e];
+    const int fil = c.mat[e];
+    const double I = c.I[e];
+    float Br = 0.0f, Bz = 0.0f, T = (float)c.T_bath;
+    double u = c.T_bath * c.T_bath * c.T_bath * c.T_bath;
+    const float inv2pir = 1.0f / (float)(2.0 * kPi * r);
+    if (c.has_grid) {
+        const int g = c.elem_grid[e];
+        const int iz = g / c.Gr, ir = g - iz * c.Gr;
+        double dr = 0.0, dz = 0.0;
+        int j0 = c.sr_j0[ir];
+        for (int k = 0; k < 3; ++k) {
+            const double wk = c.sr_w[3 * ir + k];
+            if (wk != 0.0) dr = fma(wk, c.Phi[c.grid_elem[iz * c.Gr + j0 + k]], dr);
+        }
+        j0 = c.sz_j0[iz];
+        for (int k = 0; k < 3; ++k) {
+            const double wk = c.sz_w[3 * iz + k];
+            if (wk != 0.0) dz = fma(wk, c.Phi[c.grid_elem[(j0 + k) * c.Gr + ir]], dz);
+        }
+        Bz = (float)dr * inv2pir + Ba0;
+        Br = -(float)dz * inv2pir;
+        u = c.uT[g];
+        T = sqrtf(sqrtf((float)u));
+    } else {
+        Bz = Ba0;
+    }
+    const float Bm = sqrtf(Br * Br + Bz * Bz);
+    const float ia = 1.0f / a;
+    const float J = (float)I * ia;
+    const float Jc = fil ? critical_current_f(c, Bm, T, strain_power_f(c, e, r, (double)J, Bz), (float)c.jc_factor[e])
+                         : 0.0f;
+    float frac, dfac, jrat;
+    ej_law_f(c, fil, fabsf(J), Jc, &frac, &dfac, &jrat);
+    const float rn = (float)c.rho_n, tpr = (float)(2.0 * kPi * r);
+    const float rho = rn * frac;
+    const float E = rho * J;
+    const float q = E * J;
+    c.G[e] = (double)(tpr * (rn * dfac) * ia);
+    c.R[e] = (double)(tpr * E) + kPi * r * r * dBa;
+    if (c.n_groups) c.xI[e] = (double)(tpr * rho * ia) * c.Itr[e];   // resistive voltage of J_I
+    if (c.has_grid) c.qgrid[c.elem_grid[e]] = (double)q;
+    o.I = I;
+    o.u = u;
+    o.pj = q * tpr * a;
+    o.q = q;
+    o.jrat = jrat;
+    o.frac = frac;
+    o.fil = fil;
+    return o;
+}
+
+__device__ __forceinline__ float seg_sumf(float v, int Bp) {
+    for (int o = Bp >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float seg_maxf(float v, int Bp) {
+    for (int o = Bp >> 1; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// Maximum of non-negative doubles through their bit patterns (ordered like
+// the values): no FP64 instruction.
+__device__ __forceinline__ long long seg_max_bits(long long v, int Bp) {
+    for (int o = Bp >> 1; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // The wire's maximum temperature from the maximum of tq (the fourth root of
 // a maximum of u is the maximum of the fourth roots).
 template <bool F32>
@@ -1050,31 +1132,60 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
     const Seg s = seg_of(c, wg);
     Scalars* sc = c.sc;
     const double t0 = sc->t, dt = c.dt, t1 = t0 + dt;
-    const double It1 = drive_current(c, t1);
-    const double Ba0 = drive_field(c, t0), Ba1 = drive_field(c, t1);
-    const double dBa = (Ba1 - Ba0) / dt;
+    // the drive once per warp (FP64 on one lane), broadcast
+    double It1 = 0.0, Ba0 = 0.0, Ba1 = 0.0, dBa = 0.0;
+    if ((threadIdx.x & 31) == 0) {
+        It1 = drive_current(c, t1);
+        Ba0 = drive_field(c, t0);
+        Ba1 = drive_field(c, t1);
+        dBa = (Ba1 - Ba0) / dt;
+    }
+    It1 = __shfl_sync(0xffffffffu, It1, 0);
+    Ba0 = __shfl_sync(0xffffffffu, Ba0, 0);
+    Ba1 = __shfl_sync(0xffffffffu, Ba1, 0);
+    dBa = __shfl_sync(0xffffffffu, dBa, 0);
     if (s.w == 0 && s.kk == 0) {
         sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
         sc->nonpd = 0;                         // k_factor of this step sets it again if needed
     }
     double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
-    const bool F32 = c.precision != PREC_FP64;      // the mixed form's FP32 chain
-    if (s.ev) {
-        const ElemOut o = F32 ? pointwise_element<true>(c, s.e, Ba0, dBa) : pointwise_element<false>(c, s.e, Ba0, dBa);
-        sumI = o.I;
-        pj = o.pj;
-        tmx = o.tq;
-        qmx = o.q;
-        if (o.fil) { jr = o.jrat; rhof = o.frac; nfil = 1.0; }
+    if (c.precision != PREC_FP64) {
+        // the mixed form's FP32 chain; the current sum stays FP64
+        float pjf = 0.f, jrf = 0.f, rhf = 0.f, nf = 0.f, qf = 0.f;
+        long long ub = 0;
+        if (s.ev) {
+            const ElemOutF o = pointwise_element_f(c, s.e, (float)Ba0, dBa);
+            sumI = o.I;
+            pjf = o.pj;
+            qf = o.q;
+            ub = __double_as_longlong(o.u);
+            if (o.fil) { jrf = o.jrat; rhf = o.frac; nf = 1.0f; }
+        }
+        sumI = seg_sum(sumI, s.Bp);
+        pj = (double)seg_sumf(pjf, s.Bp);
+        jr = (double)seg_maxf(jrf, s.Bp);
+        rhof = (double)seg_sumf(rhf, s.Bp);
+        nfil = (double)seg_sumf(nf, s.Bp);
+        const long long umax = seg_max_bits(ub, s.Bp);
+        if (s.kk == 0) tmx = sqrt(sqrt(__longlong_as_double(umax)));   // the head lane's
+        qmx = (double)seg_maxf(qf, s.Bp);
+    } else {
+        if (s.ev) {
+            const ElemOut o = pointwise_element<false>(c, s.e, Ba0, dBa);
+            sumI = o.I;
+            pj = o.pj;
+            tmx = o.tq;
+            qmx = o.q;
+            if (o.fil) { jr = o.jrat; rhof = o.frac; nfil = 1.0; }
+        }
+        sumI = seg_sum(sumI, s.Bp);
+        pj = seg_sum(pj, s.Bp);
+        jr = seg_max(jr, s.Bp);
+        rhof = seg_sum(rhof, s.Bp);
+        nfil = seg_sum(nfil, s.Bp);
+        tmx = seg_max(tmx, s.Bp);
+        qmx = seg_max(qmx, s.Bp);
     }
-    sumI = seg_sum(sumI, s.Bp);
-    pj = seg_sum(pj, s.Bp);
-    jr = seg_max(jr, s.Bp);
-    rhof = seg_sum(rhof, s.Bp);
-    nfil = seg_sum(nfil, s.Bp);
-    tmx = seg_max(tmx, s.Bp);
-    if (F32) tmx = wire_tmax<true>(tmx);
-    qmx = seg_max(qmx, s.Bp);
     if (s.kk == 0 && s.wv) {
         const int w = s.w;
         double* parts = c.parts;
@@ -1245,13 +1356,13 @@ __device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
 #pragma unroll
                 for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
             }
-            T rk[kSegMax];                              // scaled pivot row
+            // eliminate with the scaled pivot row, one broadcast entry at a time
+            // (no copy of the row held in registers)
+            const T f = a[k];
 #pragma unroll
-            for (int j = 0; j < kSegMax; ++j) rk[j] = __shfl_sync(0xffffffffu, a[j], s.base + k);
-            if (kk != k) {
-                const T f = a[k];
-#pragma unroll
-                for (int j = 0; j < kSegMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * rk[j];
+            for (int j = 0; j < kSegMax; ++j) {
+                const T rkj = __shfl_sync(0xffffffffu, a[j], s.base + k);
+                if (kk != k) a[j] = (j == k) ? -f * ip : a[j] - f * rkj;
             }
         }
     }
@@ -1313,18 +1424,26 @@ __device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
 // is stored (in the factor array) so that every PCG application is one
 // B x B product.  Also the right-hand-side norm R^T P_w R + c_w^2 / sigma and
 // the projected warm start.
-__global__ void __launch_bounds__(32 * kSegWarps)
-k_factor_seg(const CoilDev* __restrict__ cds) {
+// GROUPS: the coils with subelements (their path needs A_w^-1 itself, the
+// transport part, in FP64), launched as a kernel of its own so that its
+// registers do not weigh on the plain path (the inverse only builds the
+// preconditioner, which FP32 serves; see factor_seg).
+template <bool GROUPS>
+__device__ __forceinline__ void factor_seg_kernel(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
-    if (c.B > kSegMax) return;
+    if (c.B > kSegMax || (c.n_groups != 0) != GROUPS) return;
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
     if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
     const Seg s = seg_of(c, wg);
-    // the subelement path needs A_w^-1 itself (the transport part); otherwise the
-    // inverse only builds the preconditioner, which FP32 serves (see factor_seg)
-    if (c.n_groups) factor_seg<double>(c, s);
+    if (GROUPS) factor_seg<double>(c, s);
     else factor_seg<float>(c, s);
+}
+__global__ void __launch_bounds__(32 * kSegWarps) k_factor_seg(const CoilDev* __restrict__ cds) {
+    factor_seg_kernel<false>(cds);
+}
+__global__ void __launch_bounds__(32 * kSegWarps) k_factor_seg_groups(const CoilDev* __restrict__ cds) {
+    factor_seg_kernel<true>(cds);
 }
 
 // The PCG loop's condition as a kernel of its own (coils whose update kernel
@@ -1428,11 +1547,18 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
 // ------------------------------------------------------------------ thermal
 
 // Source s = 4/(rho_m c0) (q - border loss / h^2) of cell g with state u.
+// Only border cells lose heat to the bath: the others skip the temperature
+// (two FP64 square roots on B300's narrow FP64 pipe); the constant factors
+// are taken as precomputed reciprocals.
 __device__ __forceinline__ double thermal_source(const CoilDev& c, int g, double u) {
-    double T = sqrt(sqrt(u));
-    double tr = T / c.T_ref;
-    double loss = c.nborder[g] * c.helem * c.h0 * (tr * tr * tr) * (T - c.T_bath);
-    return 4.0 / (c.rho_m * c.c0) * (c.qgrid[g] - loss / (c.helem * c.helem));
+    const int nb = c.nborder[g];
+    double loss = 0.0;
+    if (nb) {
+        const double T = sqrt(sqrt(u));
+        const double tr = T * c.inv_Tref;
+        loss = nb * c.helem * c.h0 * (tr * tr * tr) * (T - c.T_bath);
+    }
+    return c.src_k * (c.qgrid[g] - loss * c.inv_h2);
 }
 
 // r-lines: u* = (I - dt/2 A_r)^-1 [(I + dt/2 A_z) u + dt/2 s].  One warp per grid row.
@@ -1490,16 +1616,23 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
     if (lane == 0) c.partT[i] = um;
 }
 
-// One CTA per coil: the step's diagnostic record, then t += dt.
-__global__ void __launch_bounds__(1024) k_step_end(const CoilDev* __restrict__ cds) {
-    const CoilDev& c = cds[blockIdx.x];
+// The step's diagnostic record, then t += dt.  kStepEndCtas CTAs per coil
+// (grid row = coil) each reduce a slice of the per-wire values and of the
+// thermal columns into partials (parts row 7, free once the solve is done);
+// the CTA that arrives last on the coil's third counter (which it resets)
+// combines them in a fixed order and writes the record.  On B300 one CTA's
+// FP64 pipe alone took ~28 us for the 96,000-element coil.
+__global__ void __launch_bounds__(kStepEndThreads) k_step_end(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
     if (c.sc->status != ST_OK) return;
     __shared__ double sh[32];
+    __shared__ int is_last;
     const double* parts = c.parts;
-    size_t W = c.W;
+    const size_t W = c.W;
+    const int nb = gridDim.x, tid = threadIdx.x;
+    const int stride = nb * blockDim.x;
     double pj = 0.0, V = 0.0, m = 0.0, jr = 0.0, rh = 0.0;
-#pragma unroll 4
-    for (int w = threadIdx.x; w < c.W; w += blockDim.x) {
+    for (int w = blockIdx.x * blockDim.x + tid; w < c.W; w += stride) {
         pj += parts[0 * W + w];
         jr = fmax(jr, parts[1 * W + w]);
         rh = fmax(rh, parts[2 * W + w]);
@@ -1509,9 +1642,9 @@ __global__ void __launch_bounds__(1024) k_step_end(const CoilDev* __restrict__ c
     double um = 0.0;
     if (c.has_grid) {
         if (c.thermal) {
-            for (int i = threadIdx.x; i < c.Gr; i += blockDim.x) um = fmax(um, c.partT[i]);
+            for (int i = blockIdx.x * blockDim.x + tid; i < c.Gr; i += stride) um = fmax(um, c.partT[i]);
         } else {
-            for (int g = threadIdx.x; g < c.Gr * c.Gz; g += blockDim.x) um = fmax(um, c.uT[g]);
+            for (int g = blockIdx.x * blockDim.x + tid; g < c.Gr * c.Gz; g += stride) um = fmax(um, c.uT[g]);
         }
     }
     pj = block_reduce_sum(pj, sh);
@@ -1520,7 +1653,30 @@ __global__ void __launch_bounds__(1024) k_step_end(const CoilDev* __restrict__ c
     jr = block_reduce_max(jr, sh);
     rh = block_reduce_max(rh, sh);
     um = block_reduce_max(um, sh);
-    if (threadIdx.x != 0) return;
+    double* cp = c.parts + 7 * W;                     // 6 partials per CTA
+    if (tid == 0) {
+        cp[6 * blockIdx.x + 0] = pj;
+        cp[6 * blockIdx.x + 1] = V;
+        cp[6 * blockIdx.x + 2] = m;
+        cp[6 * blockIdx.x + 3] = jr;
+        cp[6 * blockIdx.x + 4] = rh;
+        cp[6 * blockIdx.x + 5] = um;
+        unsigned prev;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(prev) : "l"(c.ticket + 2) : "memory");
+        is_last = prev == (unsigned)nb - 1u;
+        if (is_last) c.ticket[2] = 0u;
+    }
+    __syncthreads();
+    if (!is_last || tid != 0) return;
+    pj = V = m = jr = rh = um = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        pj += cp[6 * k + 0];
+        V += cp[6 * k + 1];
+        m += cp[6 * k + 2];
+        jr = fmax(jr, cp[6 * k + 3]);
+        rh = fmax(rh, cp[6 * k + 4]);
+        um = fmax(um, cp[6 * k + 5]);
+    }
     Scalars* sc = c.sc;
     double t1 = sc->t + c.dt;
     double* rec = c.diag + (size_t)(sc->step % c.diag_cap) * 10;
