@@ -104,19 +104,36 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// Non-blocking test of the phase of the given parity.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
 }
+// The same test, the thread suspended (issuing nothing) until the phase
+// completes or about `ns` nanoseconds have passed.
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint32_t kTcSleepNs = 2000;            // longest suspension between two limit checks
 // Wait for the phase of the given parity; false on abort or after `limit`
-// cycles (then the abort flag is raised).
+// cycles (then the abort flag is raised).  The limit is checked after every
+// failed non-blocking test, before the thread suspends again, so that a short
+// limit (the test hook) runs out at the first phase that is not complete.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
     const long long t0 = clock64();
     for (;;) {
@@ -126,6 +143,7 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
             *abort_flag = 1;
             return false;
         }
+        if (mbar_try_sleep(bar, parity, kTcSleepNs)) return true;
     }
 }
 // Inline fast path for a phase that has already completed.
@@ -139,6 +157,7 @@ __device__ __noinline__ bool mbar_wait_final(uint32_t bar, uint32_t parity, long
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (clock64() - t0 > limit) return false;
+        if (mbar_try_sleep(bar, parity, kTcSleepNs)) return true;
     }
 }
 
@@ -189,6 +208,54 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// One stage: 4 K steps x (A_hi B_hi, A_hi B_lo, A_lo B_hi) into accumulator d
+// as one block of 12 MMAs, issued by the warp's elected lane with the whole
+// warp executing it (converged), every descriptor formed before the first: a
+// single thread then issues them back to back at about the tensor cores' pace,
+// where one MMA per address computation costs it about twice as long.  The
+// first MMA overwrites the accumulator unless acc0.
+__device__ __forceinline__ void mma_stage_warp(uint32_t d, uint32_t idesc, uint32_t acc0, uint64_t a_hi,
+                                               uint64_t a_lo, uint64_t a_step, uint64_t b_hi, uint64_t b_lo,
+                                               uint64_t b_step) {
+    uint64_t ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ah[k] = a_hi + k * a_step;
+        al[k] = a_lo + k * a_step;
+        bh[k] = b_hi + k * b_step;
+        bl[k] = b_lo + k * b_step;
+    }
+    asm volatile(
+        "{\n\t.reg .pred p, e, t;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "setp.eq.b32 t, %1, %1;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %11, %2, p;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %15, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %11, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %12, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %16, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %8, %12, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %13, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %17, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %13, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %6, %14, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %6, %18, %2, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %10, %14, %2, t;\n\t}" ::"r"(d),
+        "r"(acc0), "r"(idesc), "l"(ah[0]), "l"(ah[1]), "l"(ah[2]), "l"(ah[3]), "l"(al[0]), "l"(al[1]), "l"(al[2]),
+        "l"(al[3]), "l"(bh[0]), "l"(bh[1]), "l"(bh[2]), "l"(bh[3]), "l"(bl[0]), "l"(bl[1]), "l"(bl[2]), "l"(bl[3])
+        : "memory");
+}
+// tcgen05.commit by the warp's elected lane (the same lane as in mma_stage_warp:
+// elect.sync picks the same lane for the same full mask, so the commit tracks
+// that lane's MMAs).
+__device__ __forceinline__ void mma_commit_warp(uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -338,24 +405,29 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
             if (a_used >> s & 1u) mbar_wait_final(a_full + 8u * s, a_par >> s & 1u, kTcWait);
         for (int s = 0; s < kTcBStages; ++s)
             if (b_used >> s & 1u) mbar_wait_final(b_full + 8u * s, b_par >> s & 1u, kTcWait);
-    } else if (warp >= 1 && warp < kTcEpi0 && lane == 0) {
-        // ---- MMA issuers: stage i of this CTA (table slot i % S, TMEM accumulator
-        // i % n_acc, the latter's first MMA overwriting the columns it covers) is
-        // issued by warp 1 + i % kTcIssuers, so that the issuing threads' overheads
-        // and the MMA chains into different accumulators overlap; each issuer frees
-        // a staged copy of p (one arrival each) once it has no more stages on it
+    } else if (warp >= 1 && warp < kTcEpi0) {
+        // ---- MMA issuers (whole warps, the elected lane issuing): stage i of this
+        // CTA (table slot i % S, TMEM accumulator i % n_acc, the latter's first MMA
+        // overwriting the columns it covers) is issued by warp 1 + i % kTcIssuers,
+        // so that the issuing threads' overheads and the MMA chains into different
+        // accumulators overlap; each issuer frees a staged copy of p (one arrival
+        // each) once it has no more stages on it.  The issuer's stages are
+        // i = me, me + 4, ...: their slot, accumulator and parities advance without
+        // divisions (a runtime division costs more than issuing a stage).
         const int me = warp - 1;
         int grp = 0;
         bool ok = true;
         const uint32_t bbase = sB;                      // one staged copy (kTcBStages == 1)
         int D = wk.y % sh.NT, cb = col_tile(wk.y);
         int i0 = 0;                                     // the step's first stage
+        int sa_i = me % S, ai_i = me % n_acc;           // this issuer's next stage i: i % S, i % n_acc
+        uint32_t pa_i = (uint32_t)(me / S) & 1u, pacc_i = (uint32_t)(me / n_acc) & 1u;
         for (int sg = wk.y; sg < wk.z && ok; ++sg, D = (D + 1 == sh.NT ? 0 : D + 1)) {
             if (sg != wk.y && D == 0) cb = (cb + 1 == sh.n_ct ? 0 : cb + 1);
             const int nk = min(2, sh.n_kb - 2 * cb);
             if (sg == wk.y || D == 0) {
-                if (sg != wk.y) mma_commit(b_empty);    // free once this issuer's MMAs on it finish
-                ok = mbar_wait(b_full, (uint32_t)grp & 1u, abort_flag, wlim);
+                if (sg != wk.y) mma_commit_warp(b_empty);    // free once this issuer's MMAs on it finish
+                ok = __all_sync(0xffffffffu, mbar_wait(b_full, (uint32_t)grp & 1u, abort_flag, wlim));
                 if (!ok) break;
                 ++grp;
                 tc_fence_after();
@@ -365,10 +437,7 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
             const int ns = (D > 0 ? 2 : 1) * nk;
             for (int pos = ((me - i0) % kTcIssuers + kTcIssuers) % kTcIssuers; pos < ns && ok;
                  pos += kTcIssuers) {
-                const int i = i0 + pos;
                 const int sgn = pos >= nk ? 1 : 0, j = pos - sgn * nk;
-                const int sa_i = i % S, ai_i = i % n_acc;
-                const uint32_t pa_i = (uint32_t)(i / S) & 1u, pacc_i = (uint32_t)(i / n_acc) & 1u;
                 const int d = sgn ? -D : D;
                 // staged copy: [16 chunks of 8 channels][hi, lo][NR turn rows][8];
                 // k block j of the column tile = chunks 8 j .. 8 j + 7
@@ -377,8 +446,8 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
                 // every stage up to there has completed its MMAs, so (S >= n_acc) the
                 // previous load of this stage's slot has landed and the parity wait
                 // below cannot be satisfied by the phase before it (another issuer's)
-                ok = mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag, wlim);
-                if (ok) ok = mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag, wlim);
+                ok = __all_sync(0xffffffffu, mbar_wait_fast(acc_empty + 8u * ai_i, pacc_i ^ 1u, abort_flag, wlim));
+                if (ok) ok = __all_sync(0xffffffffu, mbar_wait_fast(a_full + 8u * sa_i, pa_i, abort_flag, wlim));
                 if (!ok) break;
                 tc_fence_after();
                 const int t_first = d > 0 ? d : 0;
@@ -398,31 +467,29 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
                 const uint64_t a_step = amn ? (2048u >> 4) : (32u >> 4);
                 // B: the n rows of turns ts .. ts + n - 1 (source rows ts - d ..) of the hi
                 // and of the lo half; three MMAs per K step, hi*hi + hi*lo + lo*hi, into
-                // accumulator column t; at most 256 turns per MMA
+                // accumulator column t (n <= NT + 15 < 256: one MMA covers the turns)
                 const uint64_t b_step = (2u * 32u * (uint32_t)sh.NR) >> 4;
                 const uint64_t b_half = (16u * (uint32_t)sh.NR) >> 4;
-                for (int part0 = 0; part0 < n; part0 += 256) {
-                    const int np = min(256, n - part0);
-                    const uint32_t idesc = idesc_f16(np, amn);
-                    const uint32_t dcol = tmem + (uint32_t)ai_i * acc_cols + (uint32_t)(ts + part0);
-                    const uint32_t row0 = (uint32_t)(ts + part0 - d + kTcPad);
-                    const uint64_t b_hi = sdesc(bj + 16u * row0, 32u * (uint32_t)sh.NR, 128u, 0u);
-                    const uint64_t b_lo = b_hi + b_half;
-#pragma unroll
-                    for (int s = 0; s < kTcK / 16; ++s) {
-                        mma_f16(dcol, a_hi + s * a_step, b_hi + s * b_step, idesc, s > 0 ? 1u : 0u);
-                        mma_f16(dcol, a_hi + s * a_step, b_lo + s * b_step, idesc, 1u);
-                        mma_f16(dcol, a_lo + s * a_step, b_hi + s * b_step, idesc, 1u);
-                    }
-                }
-                mma_commit(a_empty + 8u * sa_i);
-                mma_commit(acc_full + 8u * ai_i);
+                const uint32_t idesc = idesc_f16(n, amn);
+                const uint32_t dcol = tmem + (uint32_t)ai_i * acc_cols + (uint32_t)ts;
+                const uint32_t row0 = (uint32_t)(ts - d + kTcPad);
+                const uint64_t b_hi = sdesc(bj + 16u * row0, 32u * (uint32_t)sh.NR, 128u, 0u);
+                static_assert(kTcK == 64, "one stage = 4 K steps of 16");
+                mma_stage_warp(dcol, idesc, 0u, a_hi, a_lo, a_step, b_hi, b_hi + b_half, b_step);
+                mma_commit_warp(a_empty + 8u * sa_i);
+                mma_commit_warp(acc_full + 8u * ai_i);
+                // this issuer's next stage: i + kTcIssuers
+                sa_i += kTcIssuers;
+                while (sa_i >= S) { sa_i -= S; pa_i ^= 1u; }
+                ai_i += kTcIssuers;
+                while (ai_i >= n_acc) { ai_i -= n_acc; pacc_i ^= 1u; }
             }
             i0 += ns;
         }
         // every MMA issued (also after an abort) completes before the TMEM is freed
-        mma_commit(mma_done);
-        if (!mbar_wait_final(mma_done, 0u, kTcWait)) *abort_flag = 1;
+        __syncwarp();
+        mma_commit_warp(mma_done);
+        if (!__all_sync(0xffffffffu, mbar_wait_final(mma_done, 0u, kTcWait)) && lane == 0) *abort_flag = 1;
     } else if (warp >= kTcEpi0) {
         // ---- epilogue: each stage's accumulator is added into FP32 registers (lane
         // quadrant warp % 4, turn groups of parity h), then released to the MMAs
@@ -614,6 +681,7 @@ __device__ __noinline__ bool wait2(const CoilDev& c, uint32_t bar, uint32_t pari
             }
             return false;
         }
+        if (mbar_try_sleep(bar, parity, kTcSleepNs)) return true;
     }
 }
 
@@ -761,6 +829,7 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const unsigned need = (unsigned)kTcEpiWarps * (unsigned)(i - NA + 1);
                 const long long t0 = clock64();
                 while (*drained < need) {
+                    __nanosleep(32);
                     if (*abort_flag) { ok = false; break; }
                     if (clock64() - t0 > wlim) {
                         *abort_flag = 1;
