@@ -69,7 +69,7 @@ PROFILED_TRAFFIC = {
     # profiles/k_toeplitz_f32_real96k.md: the bench workload itself (table 0.73 GB)
     "toeplitz": {"dram_bytes": 1.556434e9 + 14.971904e6, "operator_bytes": 733593600},
     # profiles/k_toeplitz_tc_real96k.md: the bench workload itself (split table 0.37 GB)
-    "toeplitz_tc": {"dram_bytes": 452.279040e6 + 3.208448e6, "operator_bytes": 368640000},
+    "toeplitz_tc": {"dram_bytes": 454.190336e6 + 3.817984e6, "operator_bytes": 368640000},
 }
 
 
@@ -332,6 +332,8 @@ def run_ours(args, rank, world, local_rank):
     coil = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
                               stream=stream.cuda_stream, format=args.format)
     setup_s = time.perf_counter() - t0
+    if args.tc_mode >= 0 and args.format == "toeplitz_tc":
+        coil.set_tc_schedule(args.tc_mode)
     info = coil.info()
     N = coil.N
     schedule = coil.tc_schedule() if args.format == "toeplitz_tc" else None
@@ -354,6 +356,8 @@ def run_ours(args, rank, world, local_rank):
     # launches its kernels one by one)
     cp = Coil.from_workload(w, precision=args.precision, rtol=args.rtol, device=local_rank,
                             stream=stream.cuda_stream, profile=True, format=args.format)
+    if args.tc_mode >= 0 and args.format == "toeplitz_tc":
+        cp.set_tc_schedule(args.tc_mode)
     cp.step(args.warmup, drive)
     cp.reset_counters()
     timed_steps(cp, drive, args.steps, stream, torch)
@@ -855,7 +859,9 @@ def main():
     ap.add_argument("--apply-once", action="store_true",
                     help="build the coil, run one operator apply and exit (profiler captures of the apply)")
     ap.add_argument("--tc-mode", type=int, default=-1,
-                    help="with --apply-once: pin the tensor-core schedule (0 two-fill, 1 one-fill)")
+                    help="pin the tensor-core schedule of the main leg and of --apply-once (0 two-fill, "
+                         "1 one-fill; default: the autotuner's choice), e.g. for profiler captures, under "
+                         "which the autotuner's timings differ")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
