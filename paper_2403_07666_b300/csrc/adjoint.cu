@@ -30,7 +30,7 @@ struct AdjBufs {
     double* a;          // reverse-ADI intermediates (grid)
     double* b;
     double* lamQ;       // lam_q (grid)
-    double* lamBr;      // per element
+    double* lamBr;      // per element, lam_B / (2 pi r)
     double* lamBz;
     const double* xk;   // Idot of the forward step being reversed
     double* g_f;        // dL/df accumulated (element order)
@@ -150,6 +150,36 @@ __device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double
     return d;
 }
 
+// The same in FP32: the mixed form's forward pointwise chain (Jc, E, G in
+// FP32), whose Jacobians these are.
+__device__ JcD jc_with_derivatives_f(const CoilDev& c, float Bm, float T, float ep, float f) {
+    JcD d = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const float Jc0 = (float)c.Jc0;
+    if (c.jc_model == 1) {
+        d.Jc = f * Jc0;
+        d.df = Jc0;
+        return d;
+    }
+    const float Tc = (float)c.Tc, Bc20 = (float)c.Bc2_0, Ce = (float)c.C_eps, Breg = (float)c.B_reg;
+    const float tr = T / Tc;
+    const float Bc2 = Bc20 * (1.0f - tr * tr);
+    if (!(T < Tc && Bm < Bc2)) return d;
+    const float S = 1.0f - Ce * ep;
+    if (!(S > 0.0f)) return d;
+    const float bfac = 1.0f - Bm / Bc2;
+    const float omt = 1.0f - tr;
+    const float core = Jc0 * (omt * sqrtf(omt)) * (bfac * bfac) / sqrtf(Bm + Breg);
+    const float Jc = f * core * S;
+    d.Jc = Jc;
+    d.df = core * S;
+    d.dCe = -f * core * ep;
+    d.dep = -f * core * Ce;
+    d.dBm = Jc * (-2.0f / (bfac * Bc2) - 0.5f / (Bm + Breg));
+    const float db_dT = Bm * (2.0f * Bc20 * tr / Tc) / (Bc2 * Bc2);
+    d.dT = Jc * (-1.5f / (Tc * omt) - 2.0f / bfac * db_dT);
+    return d;
+}
+
 // E-J law pieces: frac = rho/rho_n, dfac = (dE/dJ)/rho_n, A1 = s/(1+s)^2,
 // A2 = (n + s(2-n)) s/(1+s)^3, lnx = ln(|J|/Jc), evaluated without overflow.
 struct EJD { double frac, dfac, A1, A2, lnx; };
@@ -178,6 +208,31 @@ __device__ EJD ej_with_derivatives(const CoilDev& c, int fil, double J, double J
     return d;
 }
 
+// The same in FP32 (aJ = |J|).
+__device__ EJD ej_with_derivatives_f(const CoilDev& c, int fil, float aJ, float Jc) {
+    EJD d = {1.0, 1.0, 0.0, 0.0, 0.0};
+    if (!fil || Jc <= 0.0f) return d;
+    if (aJ == 0.0f) { d.frac = 0.0; d.dfac = 0.0; return d; }
+    const float n = (float)c.nexp;
+    const float lnx = logf(aJ / Jc);
+    d.lnx = lnx;
+    const float ell = logf((float)c.E0 / (Jc * (float)c.rho_n)) + (n - 1.0f) * lnx;
+    if (ell > 0.0f) {
+        const float t = expf(-ell), opt = 1.0f + t;
+        d.frac = 1.0f / opt;
+        d.dfac = (1.0f + n * t) / (opt * opt);
+        d.A1 = t / (opt * opt);
+        d.A2 = (n * t * t + (2.0f - n) * t) / (opt * opt * opt);
+    } else {
+        const float sv = expf(ell), ops = 1.0f + sv;
+        d.frac = sv / ops;
+        d.dfac = sv * (sv + n) / (ops * ops);
+        d.A1 = sv / (ops * ops);
+        d.A2 = (n + sv * (2.0f - n)) * sv / (ops * ops * ops);
+    }
+    return d;
+}
+
 // Per wire (one warp): reverse of the pointwise kernel and of the constraint.
 // wP = dL/dP of the step's Joule power P = sum q 2 pi r a (its diagnostic
 // record), which adds wP 2 pi r a to lam_q of every element.
@@ -190,24 +245,45 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, dou
     double Ba0 = c.sc->Ba0;
     double nu_term = c.constrained[w] ? c.uw[w] / dt : 0.0;   // -lam_c / dt with lam_c = nu = -u
     double gn = 0.0, gce = 0.0;
+    // the mixed form's forward chain is FP32 from the field on: its Jacobians too
+    const bool f32 = c.precision != PREC_FP64;
     for (int k = lane; k < c.B; k += 32) {
         int e = w * c.B + k;
         double r = c.r[e], a = c.area[e];
         double Br = 0.0, Bz = 0.0, T = c.T_bath, u = 0.0;
         int g = -1;
-        if (c.has_grid) {
-            field_at(c, e, Ba0, &Br, &Bz);
-            g = c.elem_grid[e];
-            u = c.uT[g];
-            T = sqrt(sqrt(u));
-        }
-        double Bm = sqrt(Br * Br + Bz * Bz);
         int fil = c.mat[e];
         JcD jd = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         double I = c.I[e];
         double J = I / a;
-        if (fil) jd = jc_with_derivatives(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]);
-        EJD ej = ej_with_derivatives(c, fil, J, jd.Jc);
+        double Bm;
+        EJD ej;
+        if (f32) {
+            float br = 0.0f, bz = 0.0f, tf = (float)c.T_bath;
+            if (c.has_grid) {
+                field_at_f(c, e, Ba0, &br, &bz);
+                g = c.elem_grid[e];
+                u = c.uT[g];
+                tf = sqrtf(sqrtf((float)u));
+            }
+            const float bm = sqrtf(br * br + bz * bz);
+            Br = br;
+            Bz = bz;
+            Bm = bm;
+            T = tf;
+            if (fil) jd = jc_with_derivatives_f(c, bm, tf, strain_power_f(c, e, r, J, bz), (float)c.jc_factor[e]);
+            ej = ej_with_derivatives_f(c, fil, (float)fabs(J), (float)jd.Jc);
+        } else {
+            if (c.has_grid) {
+                field_at(c, e, Ba0, &Br, &Bz);
+                g = c.elem_grid[e];
+                u = c.uT[g];
+                T = sqrt(sqrt(u));
+            }
+            Bm = sqrt(Br * Br + Bz * Bz);
+            if (fil) jd = jc_with_derivatives(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]);
+            ej = ej_with_derivatives(c, fil, J, jd.Jc);
+        }
         double E = rho_n * ej.frac * J;
         double Kg = 2.0 * kPi * r * rho_n / a;
         double mu = c.x[e];
@@ -228,15 +304,19 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, dou
             double lamBm = lamJc * jd.dBm;
             double lamT = lamJc * jd.dT;
             if (c.has_grid && c.thermal) ab.lamU[g] += lamT * T / (4.0 * u);
-            ab.lamBr[e] = Bm > 0.0 ? lamBm * Br / Bm : 0.0;
-            ab.lamBz[e] = Bm > 0.0 ? lamBm * Bz / Bm : 0.0;
+            // lam_B over 2 pi r, the scale of the stencil that k_adj_stencil_t transposes
+            const double s2pr = 1.0 / (2.0 * kPi * r);
+            const double sB = Bm > 0.0 ? lamBm * s2pr / Bm : 0.0;
+            double lbz = sB * Bz;
+            ab.lamBr[e] = sB * Br;
             // Lorentz hoop strain eps = eps0 + r J B_z / Y: d|eps|^p/d eps = p |eps|^p / eps
             const double eps = element_strain(c, e, r, J, Bz);
             if (c.inv_Y != 0.0 && eps != 0.0) {
                 const double lamEps = lamJc * jd.dep * c.p_eps * pow(fabs(eps), c.p_eps) / eps;
                 lamI += lamEps * r * Bz * c.inv_Y / a;
-                ab.lamBz[e] += lamEps * r * J * c.inv_Y;
+                lbz += lamEps * r * J * c.inv_Y * s2pr;
             }
+            ab.lamBz[e] = lbz;
         } else {
             ab.lamBr[e] = 0.0;
             ab.lamBz[e] = 0.0;
@@ -267,7 +347,7 @@ __global__ void k_adj_stencil_t(const CoilDev* __restrict__ cds, AdjBufs ab) {
             double wk = c.sr_w[3 * i + k];
             if (wk == 0.0) continue;
             int e = c.grid_elem[iz2 * Gr + i];
-            acc += wk * ab.lamBz[e] / (2.0 * kPi * c.r[e]);
+            acc += wk * ab.lamBz[e];                     // lam_B already over 2 pi r
         }
         for (int j = max(iz2 - 2, 0); j <= min(iz2 + 2, Gz - 1); ++j) {
             int k = iz2 - c.sz_j0[j];
@@ -275,7 +355,7 @@ __global__ void k_adj_stencil_t(const CoilDev* __restrict__ cds, AdjBufs ab) {
             double wk = c.sz_w[3 * j + k];
             if (wk == 0.0) continue;
             int e = c.grid_elem[j * Gr + ir2];
-            acc -= wk * ab.lamBr[e] / (2.0 * kPi * c.r[e]);
+            acc -= wk * ab.lamBr[e];
         }
         c.dv[e2] = acc;
         c.pf[e2] = (float)acc;
@@ -343,45 +423,47 @@ __global__ void k_adj_reduce(const CoilDev* __restrict__ cds, const double* gpar
 }
 
 // ---- host launchers ------------------------------------------------------
+// Small blocks (two warps): a coil of a few thousand elements then spreads its
+// wires and elements over most SMs instead of a few dozen (the reverse step's
+// kernels are FP64- and latency-bound, not occupancy-bound).
+constexpr int kAdjThreads = 64;
+
+inline unsigned adj_wire_blocks(const CoilDev& h) { return (unsigned)((h.W + kAdjThreads / 32 - 1) / (kAdjThreads / 32)); }
+inline unsigned adj_elem_blocks(long long n) {
+    long long b = (n + kAdjThreads - 1) / kAdjThreads;
+    return (unsigned)(b > 148LL * 32 ? 148LL * 32 : (b < 1 ? 1 : b));
+}
 
 void launch_adj_thermal(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s) {
     k_adj_adi_z<<<h.Gr, 32, h.Gz * sizeof(double), s>>>(d, ab);
     k_adj_adi_r<<<h.Gz, 32, h.Gr * sizeof(double), s>>>(d, ab);
-    unsigned gb = (unsigned)((h.Gr * h.Gz + 255) / 256);
-    if (gb > 2048u) gb = 2048u;
-    k_adj_adi_src<<<gb, 256, 0, s>>>(d, ab);
+    k_adj_adi_src<<<adj_elem_blocks((long long)h.Gr * h.Gz), kAdjThreads, 0, s>>>(d, ab);
 }
 
 void launch_adj_setup(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s) {
-    k_adj_setup<<<(h.W + 7) / 8, 256, 0, s>>>(d, ab);
+    k_adj_setup<<<adj_wire_blocks(h), kAdjThreads, 0, s>>>(d, ab);
 }
 
 void launch_adj_mult_pointwise(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, double wP, cudaStream_t s) {
-    k_adj_mult<<<(h.W + 7) / 8, 256, 0, s>>>(d);
-    k_adj_pointwise<<<(h.W + 7) / 8, 256, 0, s>>>(d, ab, wP);
+    k_adj_mult<<<adj_wire_blocks(h), kAdjThreads, 0, s>>>(d);
+    k_adj_pointwise<<<adj_wire_blocks(h), kAdjThreads, 0, s>>>(d, ab, wP);
 }
 
 void launch_adj_stencil_t(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s) {
-    unsigned eb = (unsigned)((h.N + 255) / 256);
-    if (eb > 2048u) eb = 2048u;
-    k_adj_stencil_t<<<eb, 256, 0, s>>>(d, ab);
+    k_adj_stencil_t<<<adj_elem_blocks(h.N), kAdjThreads, 0, s>>>(d, ab);
 }
 
 void launch_adj_near(const CoilDev* d, const CoilDev& h, cudaStream_t s) {
-    k_adj_near<<<(h.W + 7) / 8, 256, 0, s>>>(d);
+    k_adj_near<<<adj_wire_blocks(h), kAdjThreads, 0, s>>>(d);
 }
 
 void launch_adj_accum(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, double wk, int with_field,
                       cudaStream_t s) {
-    unsigned eb = (unsigned)((h.N + 255) / 256);
-    if (eb > 2048u) eb = 2048u;
-    k_adj_accum<<<eb, 256, 0, s>>>(d, ab, wk, with_field);
+    k_adj_accum<<<adj_elem_blocks(h.N), kAdjThreads, 0, s>>>(d, ab, wk, with_field);
 }
 
 void launch_adj_seed(const CoilDev* d, const CoilDev& h, double* lamI, double wk, cudaStream_t s) {
-    unsigned eb = (unsigned)((h.N + 255) / 256);
-    if (eb > 2048u) eb = 2048u;
-    k_adj_seed<<<eb, 256, 0, s>>>(d, lamI, wk);
+    k_adj_seed<<<adj_elem_blocks(h.N), kAdjThreads, 0, s>>>(d, lamI, wk);
 }
 
 void launch_adj_reduce(const CoilDev* d, const double* gparts, double* out, cudaStream_t s) {

@@ -47,6 +47,7 @@ __global__ void k_factor_seg_groups(const CoilDev* __restrict__ cds);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg);
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
+__global__ void k_replay_restore(const CoilDev* __restrict__ cds);
 __global__ void k_adi_r(const CoilDev* __restrict__ cds);
 __global__ void k_adi_z(const CoilDev* __restrict__ cds);
 __global__ void k_step_end(const CoilDev* __restrict__ cds);
@@ -113,6 +114,9 @@ struct coil {
     // the adjoint's transposed solve as one graph (its prologue and PCG loop)
     cudaGraphExec_t adj_exec = nullptr;
     int adj_fixed = 0, adj_per_pass = 0;
+    // the adjoint's replayed forward step as one graph (no solve)
+    cudaGraphExec_t replay_exec = nullptr;
+    int replay_fixed = 0;
     long long uid = 0;           // creation id (batched-step graphs match coils by it)
     BatchGraph* batch = nullptr;
     size_t ev_used = 0;          // event pairs recorded since the last harvest
@@ -415,6 +419,7 @@ coil_status tc_plan_schedule(coil_t* c, const TcShape& sh) {
     if (c->d) TRY(sync_descriptor(c));
     if (c->step_exec) { cudaGraphExecDestroy(c->step_exec); c->step_exec = nullptr; }
     if (c->adj_exec) { cudaGraphExecDestroy(c->adj_exec); c->adj_exec = nullptr; }
+    if (c->replay_exec) { cudaGraphExecDestroy(c->replay_exec); c->replay_exec = nullptr; }
     if (c->batch) {
         if (c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
         cudaFree(c->batch->dd);
@@ -694,6 +699,9 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.xprev, N, "previous Idot"));
     TRY(dalloc(c, &h.xprev2, N, "Idot before the previous"));
     h.extrap = 1;
+    h.rec_x = h.rec_res = h.rec_uw = nullptr;
+    h.rec_step0 = 0;
+    h.rec_mode = 0;
     TRY(dalloc(c, &h.res, N, "res"));
     TRY(dalloc(c, &h.zv, N, "z"));
     TRY(dalloc(c, &h.dv, ld, "d"));
@@ -1291,6 +1299,62 @@ coil_status run_step(coil_t* c) {
     c->pcg_iters += c->pinned->iter;
     harvest_events(c);
     TRY(step_epilogue(c, L));
+    c->steps += 1;
+    c->t += h.dt;
+    return COIL_OK;
+}
+
+// A replayed forward step of the adjoint's recomputation (rec_mode 2): the
+// pointwise update and the factor (y = A_w^-1 1 and 1/sigma, which the
+// finalisation reads) as in the step, then the recorded solution, residual
+// and loop voltages in place of the solve, then the step's epilogue.
+coil_status replay_kernels(coil_t* c, const Launch& L) {
+    c->launches += launch_pointwise(L);
+    c->launches += launch_factor(L);
+    const unsigned nb = (unsigned)std::min<long long>(((long long)c->h.N + 255) / 256, 148LL * 8);
+    k_replay_restore<<<dim3(nb, L.n), 256, 0, L.s>>>(L.d);
+    c->launches += 1;
+    CK(cudaGetLastError(), "replay launch");
+    return step_epilogue(c, L);
+}
+
+coil_status run_replay_step(coil_t* c) {
+    const CoilDev& h = c->h;
+    if (!c->profile && !c->graph_failed && !c->replay_exec) {
+        // one graph: the replay kernels and the scalars read back
+        const long long l0 = c->launches;
+        cudaGraph_t g = nullptr;
+        coil_status st = COIL_ERR_CUDA;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = replay_kernels(c, single_launch(c));
+            if (st == COIL_OK)
+                e = cudaMemcpyAsync(c->pinned, c->h.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream);
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);      // always ends the capture
+            if (e == cudaSuccess) e = e2;
+        }
+        c->replay_fixed = (int)(c->launches - l0);
+        c->launches = l0;
+        if (st == COIL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->replay_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st != COIL_OK || e != cudaSuccess) {
+            cudaGetLastError();
+            c->replay_exec = nullptr;
+            c->graph_failed = true;                  // the same kernels, launched one by one
+            c->err.clear();
+        }
+    }
+    if (c->replay_exec) {
+        CK(cudaGraphLaunch(c->replay_exec, c->stream), "replay graph launch");
+        CK(cudaStreamSynchronize(c->stream), "replay");
+        c->launches += c->replay_fixed;
+    } else {
+        TRY(replay_kernels(c, single_launch(c)));
+        TRY(read_scalars(c));
+    }
+    const int st = c->pinned->status;
+    if (st == ST_KERNEL) return fail(c, COIL_ERR_CUDA, tc_timeout_text(c));
+    if (st != ST_OK) return fail(c, COIL_ERR_NONFINITE, "replayed step of the adjoint failed");
     c->steps += 1;
     c->t += h.dt;
     return COIL_OK;
@@ -2030,6 +2094,7 @@ void coil_destroy(coil_t* c) {
     for (cudaStream_t st : c->aux) cudaStreamDestroy(st);
     if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
     if (c->adj_exec) cudaGraphExecDestroy(c->adj_exec);
+    if (c->replay_exec) cudaGraphExecDestroy(c->replay_exec);
     if (c->batch) {
         if (c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
         cudaFree(c->batch->dd);
@@ -2270,6 +2335,22 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
     double *muprev, *muprev2;
     TRY(mem.get(&muprev, N, "previous adjoint solution"));
     TRY(mem.get(&muprev2, N, "previous adjoint solution"));
+    // records of every forward step's solve outputs (x, residual, loop
+    // voltages), so that the recomputation of a segment replays its steps
+    // without solving them; left out (the recomputation then solves) when they
+    // would take more than a quarter of the free device memory or 4 GiB
+    bool replay = false;
+    double *rx = nullptr, *rres = nullptr, *ruw = nullptr;
+    if (nseg > 1) {
+        size_t free_b = 0, total_b = 0;
+        const size_t want = (size_t)n_steps * (2 * N + W) * sizeof(double);
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && want <= free_b / 4 && want <= (size_t(4) << 30)) {
+            replay = mem.get(&rx, (size_t)n_steps * N, "step records") == COIL_OK &&
+                     mem.get(&rres, (size_t)n_steps * N, "step records") == COIL_OK &&
+                     mem.get(&ruw, (size_t)n_steps * W, "step records") == COIL_OK;
+            if (!replay) c->err.clear();
+        }
+    }
 
     // forward pass, checkpoint every ckpt_every steps; the states of the last
     // segment are kept as they are made, so that segment needs no recomputation
@@ -2278,6 +2359,16 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
     const long k0_last = (nseg - 1) * ckpt_every;
     std::vector<double> t_last(n_steps - k0_last);
     const size_t xoff = 2 * N;                      // position of the warm start / Idot in a slot
+    if (replay) {
+        // the device's step index is the record index's origin
+        TRY(set_device_time(c, c->t, c->steps));
+        h.rec_x = rx;
+        h.rec_res = rres;
+        h.rec_uw = ruw;
+        h.rec_step0 = c->steps;
+        h.rec_mode = 1;
+        TRY(sync_descriptor(c));
+    }
     for (long k = 0; k < n_steps; ++k) {
         if (k % ckpt_every == 0) {
             TRY(state_copy(c, ck + (k / ckpt_every) * S, true, true));
@@ -2291,6 +2382,10 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
         }
         TRY(run_step(c));
         if (slot) CK(cudaMemcpyAsync(slot + xoff, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+    }
+    if (replay) {
+        h.rec_mode = 0;
+        TRY(sync_descriptor(c));
     }
     TRY(state_copy(c, fin, true, true));
     const double t_fin = c->t;
@@ -2312,6 +2407,8 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
             c->h.extrap = 1;
             c->h.xprev = xp;
             c->h.xprev2 = xp2;
+            c->h.rec_mode = 0;
+            c->h.rec_x = c->h.rec_res = c->h.rec_uw = nullptr;
             sync_descriptor(c);
         }
     } acc_guard{c, xprev_fwd, xprev2_fwd};
@@ -2334,6 +2431,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
             h.extrap = 1;
             h.xprev = xprev_fwd;
             h.xprev2 = xprev2_fwd;
+            h.rec_mode = replay ? 2 : 0;
             TRY(sync_descriptor(c));
             TRY(state_copy(c, ck + sg * S, false, true));
             c->t = t_ck[sg];
@@ -2343,8 +2441,12 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
                 double* slot = seg + (k - k0) * S;
                 TRY(state_copy(c, slot, true, false));
                 t_k[k - k0] = c->t;
-                TRY(run_step(c));
+                TRY(replay ? run_replay_step(c) : run_step(c));
                 CK(cudaMemcpyAsync(slot + xoff, h.x, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
+            }
+            if (replay) {
+                h.rec_mode = 0;
+                TRY(sync_descriptor(c));
             }
             CK(cudaMemcpyAsync(h.x, musave, N * 8, cudaMemcpyDeviceToDevice, s), "adjoint");
         }

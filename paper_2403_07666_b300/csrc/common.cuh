@@ -133,6 +133,16 @@ struct CoilDev {
     // histories shift), 6 linear (both shift), 4 quadratic
     double *xprev, *xprev2;
     int extrap;
+    // the adjoint's replayed forward steps: rec_mode 1 (its forward pass)
+    // records, in k_finalize, the solution x, the residual and the loop
+    // voltages each step's finalisation used, at record (device step index -
+    // rec_step0); rec_mode 2 (its recomputation of a segment) restores them in
+    // place of the solve (k_replay_restore), so the recomputed states equal
+    // the forward pass's bit for bit, and k_step_end keeps the forward pass's
+    // solver diagnostics
+    double *rec_x, *rec_res, *rec_uw;
+    long long rec_step0;
+    int rec_mode;
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;

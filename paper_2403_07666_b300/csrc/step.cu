@@ -1524,9 +1524,16 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     }
     double U = con ? c.uw[w] : 0.0;
     double yr = 0.0, mom = 0.0;
+    const bool rec = c.rec_mode == 1;
+    const size_t ri = rec ? (size_t)(c.sc->step - c.rec_step0) : 0;
+    if (rec && lane == 0) c.rec_uw[ri * c.W + w] = c.uw[w];
     for (int k = lane; k < B; k += 32) {
         int e = w * B + k;
         double xe = c.x[e];
+        if (rec) {
+            c.rec_x[ri * c.N + e] = xe;
+            c.rec_res[ri * c.N + e] = c.res[e];
+        }
         yr += c.y1[e] * c.res[e];
         double In = c.I[e] + dt * xe;
         c.I[e] = In;
@@ -1541,6 +1548,19 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
         c.uw[w] = u;
         parts[5 * (size_t)c.W + w] = u;
         parts[6 * (size_t)c.W + w] = mom;
+    }
+}
+
+// A replayed step (rec_mode 2): the solution, residual and loop voltages that
+// the forward pass's finalisation of this step used, in place of the solve.
+__global__ void k_replay_restore(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.rec_mode != 2 || c.sc->status != ST_OK) return;
+    const size_t ri = (size_t)(c.sc->step - c.rec_step0);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c.N; e += gridDim.x * blockDim.x) {
+        c.x[e] = c.rec_x[ri * c.N + e];
+        c.res[e] = c.rec_res[ri * c.N + e];
+        if (e < c.W) c.uw[e] = c.rec_uw[ri * c.W + e];
     }
 }
 
@@ -1688,9 +1708,11 @@ __global__ void __launch_bounds__(kStepEndThreads) k_step_end(const CoilDev* __r
     rec[5] = c.has_grid ? sqrt(sqrt(um)) : c.T_bath;
     rec[6] = jr;
     rec[7] = rh;
-    rec[8] = (double)sc->iter;
-    sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(sc->rz, 0.0) / sc->scale2) : 0.0;
-    rec[9] = sc->last_resid;
+    if (c.rec_mode != 2) {                        // a replayed step keeps the solve's diagnostics
+        rec[8] = (double)sc->iter;
+        sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(sc->rz, 0.0) / sc->scale2) : 0.0;
+        rec[9] = sc->last_resid;
+    }
     sc->t = t1;
     sc->step += 1;
 }

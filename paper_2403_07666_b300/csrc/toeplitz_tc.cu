@@ -1118,23 +1118,43 @@ __global__ void k_tc_reduce_batch(const TcCoilArgs* __restrict__ args, int need_
 
 // Mode 1: q[e] = 2^-(exT + xmin) x (the part1 segments of e's channel tile +
 // the part2 segments of e's k block), fixed order, FP64.
-__global__ void k_tc2_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ part1,
-                             const float* __restrict__ part2, const int2* __restrict__ l1, const int* __restrict__ segs1,
-                             const int2* __restrict__ l2, const int* __restrict__ segs2, const int* __restrict__ pexp,
-                             int exT) {
+// The one-fill apply's reduction into q: element e sums its channel tile's
+// segments of the T_d products and its k block's segments of the T_d^T
+// products.  A CTA takes 32 consecutive elements; its 8 warps take every 8th
+// segment of both lists (lanes = elements, so every load is coalesced), and
+// warp 0 adds the 8 sums in order: the result is deterministic, and an
+// element's chain of dependent loads is an eighth of its segment count.
+constexpr int kT2RedSplit = 8;
+__global__ void __launch_bounds__(32 * kT2RedSplit)
+k_tc2_reduce(const CoilDev* __restrict__ cd, const TcShape sh, const float* __restrict__ part1,
+             const float* __restrict__ part2, const int2* __restrict__ l1, const int* __restrict__ segs1,
+             const int2* __restrict__ l2, const int* __restrict__ segs2, const int* __restrict__ pexp, int exT) {
     const CoilDev& c = *cd;
     if (c.sc->done) return;
-    const double inv = ldexp(1.0, -(exT + warp_min_exponent(pexp, sh.NT, threadIdx.x & 31)));
+    __shared__ double sums[kT2RedSplit][32];
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const double inv = ldexp(1.0, -(exT + warp_min_exponent(pexp, sh.NT, lane)));
     const size_t t1 = (size_t)sh.NT * kTcM, t2 = (size_t)sh.NT * kTcK;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sh.N; e += gridDim.x * blockDim.x) {
-        const int t = e / sh.C, cc = e - t * sh.C;
-        const int2 r1 = l1[cc / kTcM], r2 = l2[cc / kTcK];
-        const float* p1 = part1 + (size_t)t * kTcM + (cc % kTcM);
-        const float* p2 = part2 + (size_t)t * kTcK + (cc % kTcK);
+    for (int e0 = blockIdx.x * 32; e0 < sh.N; e0 += gridDim.x * 32) {
+        const int e = e0 + lane;
         double s = 0.0;
-        for (int k = 0; k < r1.y; ++k) s += (double)p1[(size_t)segs1[r1.x + k] * t1];
-        for (int k = 0; k < r2.y; ++k) s += (double)p2[(size_t)segs2[r2.x + k] * t2];
-        c.qv[e] = s * inv;
+        if (e < sh.N) {
+            const int t = e / sh.C, cc = e - t * sh.C;
+            const int2 r1 = l1[cc / kTcM], r2 = l2[cc / kTcK];
+            const float* p1 = part1 + (size_t)t * kTcM + (cc % kTcM);
+            const float* p2 = part2 + (size_t)t * kTcK + (cc % kTcK);
+            for (int k = j; k < r1.y; k += kT2RedSplit) s += (double)p1[(size_t)segs1[r1.x + k] * t1];
+            for (int k = j; k < r2.y; k += kT2RedSplit) s += (double)p2[(size_t)segs2[r2.x + k] * t2];
+        }
+        sums[j][lane] = s;
+        __syncthreads();
+        if (j == 0 && e < sh.N) {
+            double q = 0.0;
+#pragma unroll
+            for (int i = 0; i < kT2RedSplit; ++i) q += sums[i][lane];
+            c.qv[e] = q * inv;
+        }
+        __syncthreads();
     }
 }
 
@@ -1454,9 +1474,10 @@ cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q) {
         k_toeplitz_tc2<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.tmB64, P.d, sh, P.work, P.pexp, P.part,
                                                              P.part2, P.prog);
         if (write_q) {
-            int rb = (sh.N + 255) / 256;
-            if (rb > 148 * 8) rb = 148 * 8;
-            k_tc2_reduce<<<rb, 256, 0, s>>>(P.d, sh, P.part, P.part2, P.l1, P.segs1, P.l2, P.segs2, P.pexp, P.exT);
+            int rb = (sh.N + 31) / 32;
+            if (rb > 148 * 16) rb = 148 * 16;
+            k_tc2_reduce<<<rb, 32 * kT2RedSplit, 0, s>>>(P.d, sh, P.part, P.part2, P.l1, P.segs1, P.l2, P.segs2,
+                                                       P.pexp, P.exT);
         }
         return cudaGetLastError();
     }
