@@ -610,6 +610,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.inv_Y = m->Y_eff > 0.0 ? 1.0 / m->Y_eff : 0.0;
     h.C_eps = m->C_eps; h.p_eps = m->p_eps; h.rho_n = m->rho_n; h.rho_m = m->rho_m; h.c0 = m->c0;
     h.h0 = m->h0; h.T_ref = m->T_ref; h.T_bath = m->T_bath;
+    h.u_bath = h.T_bath * h.T_bath * h.T_bath * h.T_bath;
     h.maxit = o->maxit;
     h.rtol2 = o->rtol * o->rtol;
     h.diag_cap = o->diag_capacity > 0 ? o->diag_capacity : 65536;
@@ -877,6 +878,7 @@ coil_status set_drive(coil_t* c, const coil_drive* dr) {
         return fail(c, COIL_ERR_INVALID, "triangle waveform needs Ba_max > 0");
     CoilDev& h = c->h;
     h.dt = dr->dt; h.ramp = dr->ramp_rate; h.Imax = dr->I_max;
+    h.inv_dt = dr->dt > 0.0 ? 1.0 / dr->dt : 0.0;
     h.Ba_rate = dr->Ba_rate; h.Ba_max = dr->Ba_max; h.Ba_wf = dr->Ba_waveform;
     if (h.has_grid && c->thomas_dt != dr->dt) {
         std::vector<double> lo, inv, cp, lz, iz, cz;

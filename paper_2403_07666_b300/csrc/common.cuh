@@ -88,6 +88,7 @@ struct CoilDev {
     const int *nborder;           // border faces per grid cell
     double Ccell, helem;
     double src_k, inv_Tref, inv_h2;   // 4 / (rho_m c0), 1 / T_ref, 1 / helem^2 of the heat source
+    double u_bath, inv_dt;            // T_bath^4, 1 / dt (0 for dt = 0)
     const double *thr_lo, *thr_inv, *thr_cp;
     const double *thz_lo, *thz_inv, *thz_cp;
     // material scalars

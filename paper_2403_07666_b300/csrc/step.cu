@@ -147,8 +147,9 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
     const int fil = c.mat[e];
     const double I = c.I[e];
     float Br = 0.0f, Bz = 0.0f, T = (float)c.T_bath;
-    double u = c.T_bath * c.T_bath * c.T_bath * c.T_bath;
-    const float inv2pir = 1.0f / (float)(2.0 * kPi * r);
+    double u = c.u_bath;
+    const float tpr = 2.0f * (float)kPi * (float)r;        // 2 pi r in FP32 (no FP64 product)
+    const float inv2pir = 1.0f / tpr;
     if (c.has_grid) {
         const int g = c.elem_grid[e];
         const int iz = g / c.Gr, ir = g - iz * c.Gr;
@@ -177,7 +178,7 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
                          : 0.0f;
     float frac, dfac, jrat;
     ej_law_f(c, fil, fabsf(J), Jc, &frac, &dfac, &jrat);
-    const float rn = (float)c.rho_n, tpr = (float)(2.0 * kPi * r);
+    const float rn = (float)c.rho_n;
     const float rho = rn * frac;
     const float E = rho * J;
     const float q = E * J;
@@ -253,8 +254,11 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
     tmx = F32 ? wire_tmax<true>(warp_max(tmx)) : warp_max(tmx);
     qmx = warp_max(qmx);
     if (lane == 0) {
-        c.cw[w] = c.constrained[w] ? (It1 - sumI) / dt : 0.0;
-        double mean_rho = nfil > 0.0 ? rhof / nfil : 0.0;
+        // the mixed form without FP64 divisions (B300's FP64 pipe): c_w through
+        // 1/dt, the wire-mean rho/rho_n (FP32 sums) in FP32
+        const bool f32 = c.precision != PREC_FP64;
+        c.cw[w] = c.constrained[w] ? (f32 ? (It1 - sumI) * c.inv_dt : (It1 - sumI) / dt) : 0.0;
+        double mean_rho = nfil > 0.0 ? (f32 ? (double)((float)rhof / (float)nfil) : rhof / nfil) : 0.0;
         parts[0 * (size_t)c.W + w] = pj;
         parts[1 * (size_t)c.W + w] = jr;
         parts[2 * (size_t)c.W + w] = mean_rho;
@@ -1167,7 +1171,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         rhof = (double)seg_sumf(rhf, s.Bp);
         nfil = (double)seg_sumf(nf, s.Bp);
         const long long umax = seg_max_bits(ub, s.Bp);
-        if (s.kk == 0) tmx = sqrt(sqrt(__longlong_as_double(umax)));   // the head lane's
+        if (s.kk == 0) tmx = (double)sqrtf(sqrtf((float)__longlong_as_double(umax)));   // the head lane's
         qmx = (double)seg_maxf(qf, s.Bp);
     } else {
         if (s.ev) {

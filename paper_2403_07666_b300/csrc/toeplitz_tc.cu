@@ -709,12 +709,14 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + bar_off + 8 * nbar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + bar_off + 8 * nbar + 4);
     int* xmin_s = reinterpret_cast<int*>(gbase + bar_off + 8 * nbar + 8);
-    // stages drained so far, times kTcEpiWarps (each drain warp adds one per stage)
-    volatile unsigned* drained = reinterpret_cast<volatile unsigned*>(gbase + bar_off + 8 * nbar + 12);
+    // stages each drain warp has finished (this CTA's count; one word per warp):
+    // an accumulator pair is free for stage i once the least of them reaches
+    // i - NA + 1 (a sum over the warps would let fast warps stand in for a slow one)
+    volatile unsigned* dprog = reinterpret_cast<volatile unsigned*>(gbase + bar_off + 8 * nbar + 16);
     const int scp = (NR + 7) & ~3;
-    float* inv_s = reinterpret_cast<float*>(gbase + ((bar_off + 8 * nbar + 16 + 15) & ~15u));
+    float* inv_s = reinterpret_cast<float*>(gbase + ((bar_off + 8 * nbar + 16 + 4 * kTcEpiWarps + 15) & ~15u));
     // barriers: a_full[S], a_empty[S], pa_full, pa_empty, pk_full, pk_empty, acc_full[NA], acc_empty[NA]
-    // (not waited on: the issuers count drained stages instead, see below), mma_done
+    // (not waited on: the issuers read the drain warps' progress words instead, see below), mma_done
     const uint32_t a_full = sBar, a_empty = sBar + 8u * S;
     const uint32_t pa_full = sBar + 16u * S, pa_empty = pa_full + 8u, pk_full = pa_full + 16u, pk_empty = pa_full + 24u;
     const uint32_t acc_full = pa_full + 32u, acc_empty = acc_full + 8u * NA;
@@ -733,7 +735,7 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         *abort_flag = 0;
         *xmin_s = 1 << 30;
-        *drained = 0u;
+        for (int q = 0; q < kTcEpiWarps; ++q) dprog[q] = 0u;
         mbar_fence_init();
     }
     __syncthreads();
@@ -822,13 +824,18 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // accumulator first: the drain of stage i - NA.  With fewer accumulator pairs
             // than issuers, stages that share a pair belong to different issuers, which can
             // run ahead of one another; a parity wait cannot tell a barrier two phases behind
-            // from one that is done, so the issuers wait on the exact count of drained stages.
-            // That count implies every stage up to i - NA has finished its MMAs, so (S >= NA)
-            // the previous load of this stage's slot has landed and its parity wait is exact.
+            // from one that is done, so the issuers wait until every drain warp has finished
+            // stage i - NA.  That implies every stage up to i - NA has finished its MMAs, so
+            // (S >= NA) the previous load of this stage's slot has landed and its parity wait
+            // is exact.
             if (i >= NA) {
-                const unsigned need = (unsigned)kTcEpiWarps * (unsigned)(i - NA + 1);
+                const unsigned need = (unsigned)(i - NA + 1);
                 const long long t0 = clock64();
-                while (*drained < need) {
+                for (;;) {
+                    unsigned m = dprog[0];
+#pragma unroll
+                    for (int q = 1; q < kTcEpiWarps; ++q) m = min(m, (unsigned)dprog[q]);
+                    if (m >= need) break;
                     __nanosleep(32);
                     if (*abort_flag) { ok = false; break; }
                     if (clock64() - t0 > wlim) {
@@ -980,7 +987,7 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
-                atomicAdd(const_cast<unsigned*>(drained), 1u);
+                dprog[warp - kTcEpi0] = (unsigned)(s - wk.x + 1);
             }
             if (prog && lane == 0) prog[blockIdx.x * 32 + 8 + (warp - kTcEpi0)] = s - wk.x + 1;
             if (++ai == NA) ai = 0;
@@ -1205,6 +1212,7 @@ size_t tc_smem_bytes(const TcShape& sh) {
         const size_t pa = ((size_t)kT2ABytes * sh.NR + 1023) & ~(size_t)1023;
         const size_t pk = ((size_t)kT2KBytes * sh.NR + 1023) & ~(size_t)1023;
         return 1024 + (size_t)sh.stages * kTcAStage + pa + pk + 8 * (size_t)kT2Bars(sh.stages, sh.n_acc) + 32 +
+               4 * kTcEpiWarps +
                16 * (size_t)((sh.NR + 7) & ~3);
     }
     size_t b_pitch = ((size_t)512 * sh.NR + 127) & ~(size_t)127;
