@@ -34,6 +34,10 @@ cudaError_t launch_toeplitz(const CoilDev* cds, int n_coils, int max_C, int max_
 
 __global__ void k_pointwise(const CoilDev* __restrict__ cds);
 __global__ void k_factor(const CoilDev* __restrict__ cds);
+__global__ void k_factor_med(const CoilDev* __restrict__ cds);
+__global__ void k_init_med(const CoilDev* __restrict__ cds);
+__global__ void k_update_med(const CoilDev* __restrict__ cds);
+__global__ void k_near_med(const CoilDev* __restrict__ cds, int which);
 __global__ void k_near(const CoilDev* __restrict__ cds, int which);
 __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
@@ -711,7 +715,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.G, N, "G"));
     TRY(dalloc(c, &h.pf, ld, "pf"));
     TRY(dalloc(c, &h.L, (size_t)W * B * B, "L"));
-    if (B <= kSegMax) TRY(dalloc(c, &h.Lf, (size_t)W * B * B, "preconditioner"));
+    if (B <= kMedMax) TRY(dalloc(c, &h.Lf, (size_t)W * B * B, "preconditioner"));
     TRY(dalloc(c, &h.y1, (size_t)W * B, "y1"));
     TRY(dalloc(c, &h.sigma, W, "sigma"));
     TRY(dalloc(c, &h.isigma, W, "1 / sigma"));
@@ -926,6 +930,8 @@ struct Launch {
     int format = 0;
     int maxC = 0, maxNT = 0;
     bool seg = false, big = false;   // coils with blocks of <= kSegMax / more elements present
+    bool med = false, chol = false;  // of the latter: the FP32-inverse kernels (<= kMedMax, no
+                                     // subelements) / the Cholesky ones
     bool groups = false;             // coils with subelements present
     bool need_q = false;             // the far apply must leave its result in q (no fused consumer)
     bool dir = false;                // format 2: the apply forms the PCG direction first
@@ -961,6 +967,8 @@ Launch single_launch(coil_t* c) {
     L.maxNT = h.NT;
     L.seg = h.B <= kSegMax;
     L.big = !L.seg;
+    L.med = L.big && h.B <= kMedMax && h.n_groups == 0;
+    L.chol = L.big && !L.med;
     L.groups = h.n_groups != 0;
     if (c->tc) L.tc.push_back(c->tc);
     return L;
@@ -1052,17 +1060,19 @@ dim3 warp_grid(const Launch& L) { return dim3((unsigned)((L.maxW + 7) / 8), L.n)
 // warp) for smaller ones; a batch with both kinds launches both kernels, each
 // skipping the other kind's coils.  Return the number of launches.
 int launch_near(const Launch& L, int which) {
-    if (L.big) k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, which);
+    if (L.chol) k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, which);
+    if (L.med) k_near_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, which);
     // tensor-core format: small-block coils take the far part from the partial tiles
     const int far_tiles = L.format == 2 && !L.need_q;
     if (L.seg)
         k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1);
-    return (int)L.big + (int)L.seg;
+    return (int)L.chol + (int)L.med + (int)L.seg;
 }
 int launch_init(const Launch& L) {
-    if (L.big) k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.chol) k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.med) k_init_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
     if (L.seg) k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
-    return (int)L.big + (int)L.seg;
+    return (int)L.chol + (int)L.med + (int)L.seg;
 }
 int launch_pointwise(const Launch& L) {
     if (L.big) k_pointwise<<<warp_grid(L), 256, 0, L.s>>>(L.d);
@@ -1070,21 +1080,23 @@ int launch_pointwise(const Launch& L) {
     return (int)L.big + (int)L.seg;
 }
 int launch_factor(const Launch& L) {
-    if (L.big) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.chol) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.med) k_factor_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
     if (L.seg) {
         const dim3 grid((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n);
         k_factor_seg<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);
         if (L.groups) k_factor_seg_groups<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);
-        return (int)L.big + 1 + (int)L.groups;
+        return (int)L.chol + (int)L.med + 1 + (int)L.groups;
     }
-    return (int)L.big + (int)L.seg;
+    return (int)L.chol + (int)L.med + (int)L.seg;
 }
 int launch_update(const Launch& L) {
-    if (L.big) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.chol) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
+    if (L.med) k_update_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
     if (L.seg)
         k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(
             L.d, 1, L.cond, (int)L.fuse_cond);
-    return (int)L.big + (int)L.seg;
+    return (int)L.chol + (int)L.med + (int)L.seg;
 }
 
 // Pointwise, factorisation, right-hand-side norm, initial residual.
@@ -1581,6 +1593,9 @@ coil_status coil_batch_step(coil_t* const* coils, int n, long n_steps, const coi
         L.maxNT = std::max(L.maxNT, ci->h.NT);
         L.seg = L.seg || ci->h.B <= kSegMax;
         L.big = L.big || ci->h.B > kSegMax;
+        const bool med_i = ci->h.B > kSegMax && ci->h.B <= kMedMax && ci->h.n_groups == 0;
+        L.med = L.med || med_i;
+        L.chol = L.chol || (ci->h.B > kSegMax && !med_i);
         L.groups = L.groups || ci->h.n_groups != 0;
         if (ci->tc) L.tc.push_back(ci->tc);
     }

@@ -15,6 +15,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kMu0 = 4.0e-7 * kPi;
 constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one warp
 constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B rounded up to a power of 2)
+constexpr int kMedMax = 64;          // blocks of kSegMax + 1 .. kMedMax elements (no subelements): one
+                                     // row per thread of a 64-thread CTA, FP32 inverse, stored P_w
 constexpr int kGroupMax = 16;        // subelements per turn
 constexpr int kGroupMaxSeg = 6;      // subelements per turn of blocks of at most kSegMax elements
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels

@@ -467,7 +467,7 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
     int w = blockIdx.x;
-    if (w >= c.W || c.B <= kSegMax) return;
+    if (w >= c.W || c.B <= kSegMax || (c.B <= kMedMax && c.n_groups == 0)) return;
     extern __shared__ double sm[];
     int B = c.B, lane = threadIdx.x;
     double* A = sm;
@@ -549,7 +549,7 @@ __global__ void k_factor(const CoilDev* __restrict__ cds) {
 __global__ void k_near(const CoilDev* __restrict__ cds, int which) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
-    if (c.sc->done || c.B <= kSegMax) return;
+    if (c.sc->done || c.B <= kSegMax || (c.B <= kMedMax && c.n_groups == 0)) return;
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (w >= c.W) return;
@@ -626,7 +626,7 @@ __device__ void project_residual(const CoilDev& c, int w, const double* y, doubl
 __global__ void k_init(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
-    if (c.sc->done || c.B <= kSegMax) return;
+    if (c.sc->done || c.B <= kSegMax || (c.B <= kMedMax && c.n_groups == 0)) return;
     int w = blockIdx.x;
     if (w >= c.W) return;
     extern __shared__ double sm[];
@@ -663,7 +663,7 @@ __global__ void k_init(const CoilDev* __restrict__ cds) {
 __global__ void k_update(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     double* parts = c.parts;
-    if (c.sc->done || c.B <= kSegMax) return;
+    if (c.sc->done || c.B <= kSegMax || (c.B <= kMedMax && c.n_groups == 0)) return;
     int w = blockIdx.x;
     if (w >= c.W) return;
     extern __shared__ double sm[];
@@ -693,6 +693,235 @@ __global__ void k_update(const CoilDev* __restrict__ cds) {
     }
     rz = warp_sum(rz);
     if (lane == 0) parts[4 * (size_t)c.W + w] = rz;
+}
+
+// ---- blocks of kSegMax + 1 .. kMedMax elements without subelements -------
+// One CTA of kMedMax threads per block, thread t holding element (row) t: the
+// per-wire algebra of the shared-warp kernels (FP32 Gauss-Jordan inverse of
+// A_w = M_ww + dt G_w, the projected preconditioner P_w stored in FP32, the
+// FP64 residual and projections) with every FP64 operation spread over the
+// block's rows instead of a warp's loops over them, and no Cholesky factor.
+__device__ __forceinline__ bool is_med(const CoilDev& c) {
+    return c.B > kSegMax && c.B <= kMedMax && c.n_groups == 0;
+}
+
+// Sum over the CTA's kMedMax threads in a fixed order, the result on every thread.
+__device__ __forceinline__ double med_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMedMax / 32; ++k) r += sh[k];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kMedMax) k_factor_med(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    const int w = blockIdx.x;
+    if (w >= c.W || !is_med(c)) return;
+    __shared__ float prow[kMedMax];
+    __shared__ double sv[kMedMax];
+    __shared__ double sh[kMedMax / 32];
+    __shared__ int bad_any;
+    const int B = c.B, t = threadIdx.x, e = w * B + t;
+    const bool ev = t < B;
+    if (t == 0) bad_any = 0;
+    const double* nb = c.near + (size_t)c.block_type[w] * B * B;
+    float a[kMedMax];                    // row t of A_w, then of its inverse (indices static: registers)
+#pragma unroll
+    for (int j = 0; j < kMedMax; ++j) a[j] = (ev && j < B) ? (float)nb[t * B + j] : 0.f;
+    if (ev) {
+        const float g = (float)(c.dt * c.G[e]);
+#pragma unroll
+        for (int j = 0; j < kMedMax; ++j)
+            if (j == t) a[j] += g;
+    }
+    // Gauss-Jordan without pivoting (A_w is SPD: every pivot a positive Schur
+    // complement; a non-positive one flags the step as the Cholesky does); the
+    // scaled pivot row goes through shared memory
+#pragma unroll
+    for (int k = 0; k < kMedMax; ++k) {
+        if (k < B) {                                   // block-uniform
+            __syncthreads();
+            if (t == k) {
+#pragma unroll
+                for (int j = 0; j < kMedMax; ++j) prow[j] = a[j];
+            }
+            __syncthreads();
+            float piv = prow[k];
+            if (!(piv > 0.f)) {
+                if (t == 0) bad_any = 1;
+                piv = 1.f;
+            }
+            const float ip = 1.f / piv;
+            if (t == k) {
+#pragma unroll
+                for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
+            } else if (ev) {
+                const float f = a[k];
+#pragma unroll
+                for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * (prow[j] * ip);
+            }
+        }
+    }
+    __syncthreads();
+    if (bad_any && t == 0) atomicExch(&c.sc->nonpd, 1);
+    // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
+    float yt = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMedMax; ++j) yt += a[j];
+    const double y = ev ? (double)yt : 0.0;
+    const double sig = med_sum(y, sh);
+    const double isg = 1.0 / sig;
+    const int con = c.constrained[w];
+    if (ev) c.y1[e] = y;
+    if (t == 0) {
+        c.sigma[w] = sig;
+        c.isigma[w] = isg;
+    }
+    const double x0 = ev ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
+    // P_w row t, stored; R^T P_w R (y and R of the block through shared memory)
+    const double R = ev ? c.R[e] : 0.0;
+    sv[t] = R;
+    prow[t] = (float)y;
+    __syncthreads();
+    const float yis = (float)(y * isg);
+    double pr = 0.0;
+    float* Pw = c.Lf + ((size_t)w * B + (ev ? t : 0)) * B;
+#pragma unroll
+    for (int j = 0; j < kMedMax; ++j) {
+        if (j < B) {
+            const float pj = con ? a[j] - yis * prow[j] : a[j];
+            if (ev) Pw[j] = pj;
+            pr += (double)pj * sv[j];
+        }
+    }
+    const double rn = med_sum(ev ? R * pr : 0.0, sh);
+    const double cw = c.cw[w];
+    // warm start moved onto this step's constraint
+    const double sx = med_sum(x0, sh);
+    const double corr = con ? (cw - sx) * isg : 0.0;
+    if (ev) {
+        const double xe = x0 + corr * y;
+        c.x[e] = xe;
+        c.pf[e] = (float)xe;
+    }
+    if (t == 0) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+}
+
+// Projected residual update and preconditioner of the block (thread t holds
+// element t; v the raw residual): writes res, returns z and the block's r^T z.
+__device__ __forceinline__ double med_residual_precond(const CoilDev& c, int w, double v, double y, bool first,
+                                                       double* rz, float* vf_s, double* sh) {
+    const int B = c.B, t = threadIdx.x, e = w * B + t;
+    const bool ev = t < B;
+    const int con = c.constrained[w];
+    const double isg = c.isigma[w];
+    // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
+    const double u = med_sum(ev ? y * v : 0.0, sh) * isg;
+    if (con && ev) v -= u;
+    if (t == 0) {
+        if (first) c.uw[w] = con ? u : 0.0;
+        else if (con) c.uw[w] += u;
+    }
+    if (ev) c.res[e] = v;
+    // z = P_w r: the row of the stored FP32 P_w against r in FP32, two partial sums
+    vf_s[t] = ev ? (float)v : 0.f;
+    __syncthreads();
+    float z0 = 0.f, z1 = 0.f;
+    if (ev) {
+        const float* P = c.Lf + ((size_t)w * B + t) * B;
+        int j = 0;
+        for (; j + 1 < B; j += 2) {
+            z0 = fmaf(P[j], vf_s[j], z0);
+            z1 = fmaf(P[j + 1], vf_s[j + 1], z1);
+        }
+        if (j < B) z0 = fmaf(P[j], vf_s[j], z0);
+    }
+    double z = ev ? (double)(z0 + z1) : 0.0;
+    // the FP32 rounding's component along the constrained direction, removed in FP64
+    const double sz = med_sum(z, sh);
+    if (con && ev) z -= y * sz * isg;
+    *rz = med_sum(ev ? v * z : 0.0, sh);
+    return z;
+}
+
+// After q = A x0: r = q + R (projected), z = P_w r, d = -z; partial r^T z.
+__global__ void __launch_bounds__(kMedMax) k_init_med(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    const int w = blockIdx.x;
+    if (c.sc->done || w >= c.W || !is_med(c)) return;
+    __shared__ float vf_s[kMedMax];
+    __shared__ double sh[kMedMax / 32];
+    const int t = threadIdx.x, e = w * c.B + t;
+    const bool ev = t < c.B;
+    const double v = ev ? c.qv[e] + c.R[e] : 0.0;
+    const double y = ev ? c.y1[e] : 0.0;
+    double rz;
+    const double z = med_residual_precond(c, w, v, y, true, &rz, vf_s, sh);
+    if (ev) {
+        c.zv[e] = z;
+        c.dv[e] = -z;
+        c.pf[e] = (float)(-z);
+    }
+    if (t == 0) c.parts[4 * (size_t)c.W + w] = rz;
+}
+
+// x += alpha d, r += alpha q (projected), z = P_w r; partial r^T z.
+__global__ void __launch_bounds__(kMedMax) k_update_med(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    const int w = blockIdx.x;
+    if (c.sc->done || w >= c.W || !is_med(c)) return;
+    __shared__ float vf_s[kMedMax];
+    __shared__ double sh[kMedMax / 32];
+    const int t = threadIdx.x, e = w * c.B + t;
+    const bool ev = t < c.B;
+    const double alpha = c.sc->alpha;
+    double v = 0.0, y = 0.0;
+    if (ev) {
+        c.x[e] += alpha * c.dv[e];
+        v = c.res[e] + alpha * c.qv[e];
+        y = c.y1[e];
+    }
+    double rz;
+    const double z = med_residual_precond(c, w, v, y, false, &rz, vf_s, sh);
+    if (ev) c.zv[e] = z;
+    if (t == 0) c.parts[4 * (size_t)c.W + w] = rz;
+}
+
+// q_w += (M_ww + dt G_w) p_w (FP64, row t on thread t); optional partial p^T q.
+__global__ void __launch_bounds__(kMedMax) k_near_med(const CoilDev* __restrict__ cds, int which) {
+    const CoilDev& c = cds[blockIdx.y];
+    const int w = blockIdx.x;
+    if (c.sc->done || w >= c.W || !is_med(c)) return;
+    __shared__ double ps[kMedMax];
+    __shared__ double sh[kMedMax / 32];
+    const int B = c.B, t = threadIdx.x, e = w * B + t;
+    const bool ev = t < B;
+    const double* p = which == 0 ? c.x : c.dv;
+    const double pv = ev ? p[e] : 0.0;
+    ps[t] = pv;
+    __syncthreads();
+    double dot = 0.0;
+    if (ev) {
+        const double* nb = c.near + (size_t)c.block_type[w] * B * B + (size_t)t * B;
+        double a0 = 0.0, a1 = 0.0;
+        int j = 0;
+        for (; j + 1 < B; j += 2) {
+            a0 = fma(nb[j], ps[j], a0);
+            a1 = fma(nb[j + 1], ps[j + 1], a1);
+        }
+        if (j < B) a0 = fma(nb[j], ps[j], a0);
+        const double acc = (a0 + a1) + c.dt * c.G[e] * pv;
+        const double qe = c.qv[e] + acc;
+        c.qv[e] = qe;
+        dot = pv * qe;
+    }
+    dot = med_sum(dot, sh);
+    if (which == 1 && t == 0) c.parts[4 * (size_t)c.W + w] = dot;
 }
 
 enum ReduceMode { RED_SCALE = 0, RED_INIT = 1, RED_ALPHA = 2, RED_BETA = 3 };
