@@ -106,7 +106,8 @@ struct CoilDev {
     float *pf;                    // FP32 copy of the operator input (ld long)
     double *uT, *ustar, *src, *qgrid;   // grid order [Gz][Gr]
     double *L, *y1, *sigma, *cw, *uw;   // per block
-    float *Lf;                          // P_w in FP32 (blocks of at most kSegMax elements)
+    float *Lf;                          // P_w in FP32, blocks of at most kMedMax elements:
+                                        // [w][row][col] up to kSegMax, [w][col][row] above
     double *isigma;                     // 1 / sigma per block
     double *parts;                // 8 x W per-block partials (see step.cu)
     double *partT;                // per grid column partial of T_max

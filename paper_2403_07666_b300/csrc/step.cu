@@ -741,30 +741,31 @@ __global__ void __launch_bounds__(kMedMax) k_factor_med(const CoilDev* __restric
     }
     // Gauss-Jordan without pivoting (A_w is SPD: every pivot a positive Schur
     // complement; a non-positive one flags the step as the Cholesky does); the
-    // scaled pivot row goes through shared memory
+    // pivot row goes through shared memory.  With the swept indices S and the
+    // others U the working matrix is [A_SS^-1, A_SS^-1 A_SU; -A_US A_SS^-1,
+    // A_UU - A_US A_SS^-1 A_SU]: symmetric but for the sign of its SU/US
+    // blocks, so row t's entry in the pivot column k is +-(pivot row)[t]
+    // (minus for a swept t < k) and the sweep needs no register indexed by k.
+    for (int k = 0; k < B; ++k) {
+        __syncthreads();
+        if (t == k) {
 #pragma unroll
-    for (int k = 0; k < kMedMax; ++k) {
-        if (k < B) {                                   // block-uniform
-            __syncthreads();
-            if (t == k) {
+            for (int j = 0; j < kMedMax; ++j) prow[j] = a[j];
+        }
+        __syncthreads();
+        float piv = prow[k];
+        if (!(piv > 0.f)) {
+            if (t == 0) bad_any = 1;
+            piv = 1.f;
+        }
+        const float ip = 1.f / piv;
+        if (t == k) {
 #pragma unroll
-                for (int j = 0; j < kMedMax; ++j) prow[j] = a[j];
-            }
-            __syncthreads();
-            float piv = prow[k];
-            if (!(piv > 0.f)) {
-                if (t == 0) bad_any = 1;
-                piv = 1.f;
-            }
-            const float ip = 1.f / piv;
-            if (t == k) {
+            for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
+        } else if (ev) {
+            const float f = t < k ? -prow[t] : prow[t];
 #pragma unroll
-                for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
-            } else if (ev) {
-                const float f = a[k];
-#pragma unroll
-                for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * (prow[j] * ip);
-            }
+            for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * (prow[j] * ip);
         }
     }
     __syncthreads();
@@ -790,12 +791,14 @@ __global__ void __launch_bounds__(kMedMax) k_factor_med(const CoilDev* __restric
     __syncthreads();
     const float yis = (float)(y * isg);
     double pr = 0.0;
-    float* Pw = c.Lf + ((size_t)w * B + (ev ? t : 0)) * B;
+    // stored column by column ([w][j][t]: row t of P_w at stride B), so that the
+    // block's threads write, and later read, consecutive words
+    float* Pw = c.Lf + (size_t)w * B * B + (ev ? t : 0);
 #pragma unroll
     for (int j = 0; j < kMedMax; ++j) {
         if (j < B) {
             const float pj = con ? a[j] - yis * prow[j] : a[j];
-            if (ev) Pw[j] = pj;
+            if (ev) Pw[(size_t)j * B] = pj;
             pr += (double)pj * sv[j];
         }
     }
@@ -833,13 +836,13 @@ __device__ __forceinline__ double med_residual_precond(const CoilDev& c, int w, 
     __syncthreads();
     float z0 = 0.f, z1 = 0.f;
     if (ev) {
-        const float* P = c.Lf + ((size_t)w * B + t) * B;
+        const float* P = c.Lf + (size_t)w * B * B + t;      // row t at stride B (see k_factor_med)
         int j = 0;
         for (; j + 1 < B; j += 2) {
-            z0 = fmaf(P[j], vf_s[j], z0);
-            z1 = fmaf(P[j + 1], vf_s[j + 1], z1);
+            z0 = fmaf(P[(size_t)j * B], vf_s[j], z0);
+            z1 = fmaf(P[(size_t)(j + 1) * B], vf_s[j + 1], z1);
         }
-        if (j < B) z0 = fmaf(P[j], vf_s[j], z0);
+        if (j < B) z0 = fmaf(P[(size_t)j * B], vf_s[j], z0);
     }
     double z = ev ? (double)(z0 + z1) : 0.0;
     // the FP32 rounding's component along the constrained direction, removed in FP64
