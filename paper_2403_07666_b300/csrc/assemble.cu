@@ -170,16 +170,19 @@ __global__ void k_expand(const double* __restrict__ tab, int C, int NT, int wire
     }
 }
 
-// FP64 intra-wire blocks: near[type][ka][kb] from the D = 0 slab.
+// FP64 intra-wire blocks: near[type][ka][kb] from the D = 0 slab (and, where
+// nearf is given, the same blocks rounded to FP32).
 __global__ void k_near_blocks(const double* __restrict__ tab, int C, int NT, int B, int n_types,
-                              double* __restrict__ near) {
+                              double* __restrict__ near, float* __restrict__ nearf) {
     long long CC = (long long)C * C;
     const double* slab = tab + (long long)(NT - 1) * CC;
     int total = n_types * B * B;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         int kb = idx % B, ka = (idx / B) % B, ty = idx / (B * B);
         int base = ty * B;
-        near[idx] = slab[(long long)(base + ka) * C + base + kb];
+        const double v = slab[(long long)(base + ka) * C + base + kb];
+        near[idx] = v;
+        if (nearf) nearf[idx] = __double2float_rn(v);
     }
 }
 
@@ -222,11 +225,11 @@ cudaError_t launch_expand(const double* tab, int C, int NT, int wire_div, long l
 }
 
 cudaError_t launch_near_blocks(const double* tab, int C, int NT, int B, int n_types, double* near,
-                               cudaStream_t s) {
+                               float* nearf, cudaStream_t s) {
     int total = n_types * B * B;
     int threads = 256;
     int blocks = (total + threads - 1) / threads;
-    k_near_blocks<<<blocks, threads, 0, s>>>(tab, C, NT, B, n_types, near);
+    k_near_blocks<<<blocks, threads, 0, s>>>(tab, C, NT, B, n_types, near, nearf);
     return cudaGetLastError();
 }
 

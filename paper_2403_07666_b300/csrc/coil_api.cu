@@ -24,7 +24,7 @@ cudaError_t launch_table(const double* rc, const double* zc, const double* hc, i
 cudaError_t launch_expand(const double* tab, int C, int NT, int wire_div, long long N, long long ld,
                           int prec, void* M, cudaStream_t s);
 cudaError_t launch_near_blocks(const double* tab, int C, int NT, int B, int n_types, double* near,
-                               cudaStream_t s);
+                               float* nearf, cudaStream_t s);
 cudaError_t launch_gemv(const CoilDev* cds, int n_coils, int prec, long long max_rows, int which,
                         int n_sm, cudaStream_t s);
 size_t toeplitz_part_floats(int C, int NT);
@@ -814,9 +814,12 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         CK(launch_expand(tab, C, NT, B, N, h.ld, o->precision, M, c->stream), "expand");
     }
     double* nearp;
+    float* nearfp = nullptr;
     TRY(dalloc(c, &nearp, (size_t)n_types * B * B, "near blocks"));
-    CK(launch_near_blocks(tab, C, NT, B, n_types, nearp, c->stream), "near blocks");
+    if (B > kSegMax && B <= kMedMax) TRY(dalloc(c, &nearfp, (size_t)n_types * B * B, "near blocks (FP32)"));
+    CK(launch_near_blocks(tab, C, NT, B, n_types, nearp, nearfp, c->stream), "near blocks");
     h.near = nearp;
+    h.nearf = nearfp;
     CK(cudaEventRecord(e1, c->stream), "event");
     CK(cudaStreamSynchronize(c->stream), "assembly");
     float ms = 0.f;
@@ -1081,7 +1084,7 @@ int launch_pointwise(const Launch& L) {
 }
 int launch_factor(const Launch& L) {
     if (L.chol) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.med) k_factor_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
+    if (L.med) k_factor_med<<<dim3(L.maxW, L.n), kMedFactorThreads, 0, L.s>>>(L.d);
     if (L.seg) {
         const dim3 grid((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n);
         k_factor_seg<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);

@@ -17,6 +17,7 @@ constexpr int kMaxBlock = 64;        // elements per wire (block) handled by one
 constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B rounded up to a power of 2)
 constexpr int kMedMax = 64;          // blocks of kSegMax + 1 .. kMedMax elements (no subelements): one
                                      // row per thread of a 64-thread CTA, FP32 inverse, stored P_w
+constexpr int kMedFactorThreads = 2 * kMedMax;   // the medium-wire factor: two threads per row
 constexpr int kGroupMax = 16;        // subelements per turn
 constexpr int kGroupMaxSeg = 6;      // subelements per turn of blocks of at most kSegMax elements
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
@@ -59,6 +60,7 @@ struct CoilDev {
     const int *block_type;        // near-block type per block
     const int *constrained;       // 1 if the block is a transport turn
     const double *near;           // n_types x B x B, FP64 intra-wire blocks of M
+    const float *nearf;           // the same in FP32 (wires of kSegMax < B <= kMedMax)
     const void *Mfar;             // N x ld far operator in `precision` (dense format)
     // block-Toeplitz format of a regular solenoid: far operator entries
     // tab32[(t_i - t_j + NT - 1)][c_i][c_j] (FP32, intra-wire entries zero),

@@ -705,7 +705,8 @@ __device__ __forceinline__ bool is_med(const CoilDev& c) {
     return c.B > kSegMax && c.B <= kMedMax && c.n_groups == 0;
 }
 
-// Sum over the CTA's kMedMax threads in a fixed order, the result on every thread.
+// Sum over the CTA's NT threads in a fixed order, the result on every thread.
+template <int NT = kMedMax>
 __device__ __forceinline__ double med_sum(double v, double* sh) {
     v = warp_sum(v);
     const int wid = threadIdx.x >> 5;
@@ -713,106 +714,185 @@ __device__ __forceinline__ double med_sum(double v, double* sh) {
     __syncthreads();
     double r = 0.0;
 #pragma unroll
-    for (int k = 0; k < kMedMax / 32; ++k) r += sh[k];
+    for (int k = 0; k < NT / 32; ++k) r += sh[k];
     __syncthreads();
     return r;
 }
 
-__global__ void __launch_bounds__(kMedMax) k_factor_med(const CoilDev* __restrict__ cds) {
-    const CoilDev& c = cds[blockIdx.y];
-    const int w = blockIdx.x;
-    if (w >= c.W || !is_med(c)) return;
-    __shared__ float prow[kMedMax];
-    __shared__ double sv[kMedMax];
-    __shared__ double sh[kMedMax / 32];
-    __shared__ int bad_any;
-    const int B = c.B, t = threadIdx.x, e = w * B + t;
+// Factor of one medium wire with rows padded to NP >= B slots, two threads per
+// row (thread 2t + h holds slots h NP/2 .. h NP/2 + NP/2 - 1 of row t).  The
+// FP32 Gauss-Jordan inverse runs rotated so that every register index is
+// static: at step k the pivot column sits in slot 0, each row moves one slot to
+// the left and the new entry of column k enters at slot NP - 1, so after the B
+// steps slot s holds column (s + B) mod NP; the columns from B on of a real row
+// start and stay exactly zero.  The row that pivots next publishes itself and
+// the reciprocal of its pivot through a double buffer in shared memory: one
+// barrier per step.
+template <int NP>
+__device__ __forceinline__ void factor_med_body(const CoilDev& c, int w, float (*prow)[kMedMax + 4], float* ip_s,
+                                                float* ys, float* rs, double* sh, int* bad_any) {
+    constexpr int H = NP / 2;
+    // the second half-row starts 16 bytes further on where NP/2 floats would put
+    // it in the first half's banks
+    constexpr int HO = H % 32 == 0 ? H + 4 : H;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int B = c.B, t = threadIdx.x >> 1, h = threadIdx.x & 1, e = w * B + t;
     const bool ev = t < B;
-    if (t == 0) bad_any = 0;
-    const double* nb = c.near + (size_t)c.block_type[w] * B * B;
-    float a[kMedMax];                    // row t of A_w, then of its inverse (indices static: registers)
+    // the self block is symmetric entry for entry, so row t is read as column t
+    const float* nb = c.nearf + (size_t)c.block_type[w] * B * B + (ev ? t : 0);
+    float a[H];
 #pragma unroll
-    for (int j = 0; j < kMedMax; ++j) a[j] = (ev && j < B) ? (float)nb[t * B + j] : 0.f;
+    for (int i = 0; i < H; ++i) {
+        const int j = h * H + i;
+        a[i] = (ev && j < B) ? nb[(size_t)j * B] : 0.f;
+    }
     if (ev) {
         const float g = (float)(c.dt * c.G[e]);
 #pragma unroll
-        for (int j = 0; j < kMedMax; ++j)
-            if (j == t) a[j] += g;
+        for (int i = 0; i < H; ++i)
+            if (h * H + i == t) a[i] += g;
     }
-    // Gauss-Jordan without pivoting (A_w is SPD: every pivot a positive Schur
-    // complement; a non-positive one flags the step as the Cholesky does); the
-    // pivot row goes through shared memory.  With the swept indices S and the
-    // others U the working matrix is [A_SS^-1, A_SS^-1 A_SU; -A_US A_SS^-1,
-    // A_UU - A_US A_SS^-1 A_SU]: symmetric but for the sign of its SU/US
-    // blocks, so row t's entry in the pivot column k is +-(pivot row)[t]
-    // (minus for a swept t < k) and the sweep needs no register indexed by k.
+    auto publish = [&](int b) {                 // this row as the next pivot row
+        float4* q = reinterpret_cast<float4*>(prow[b] + h * HO);
+#pragma unroll
+        for (int q4 = 0; q4 < H / 4; ++q4) q[q4] = make_float4(a[4 * q4], a[4 * q4 + 1], a[4 * q4 + 2], a[4 * q4 + 3]);
+        if (h == 0) {
+            // without pivoting: A_w is SPD, every pivot a positive Schur
+            // complement; a non-positive one flags the step as the Cholesky does
+            float piv = a[0];
+            if (!(piv > 0.f)) {
+                *bad_any = 1;
+                piv = 1.f;
+            }
+            ip_s[b] = 1.f / piv;
+        }
+    };
+    if (t == 0) publish(0);
     for (int k = 0; k < B; ++k) {
         __syncthreads();
+        const int b = k & 1;
+        const float ip = ip_s[b];
+        // the partner's first slot: slot NP/2 of the row for h = 0, slot 0 for h = 1
+        const float o = __shfl_xor_sync(kFull, a[0], 1);
+        const float tail = h ? 0.f : o;
         if (t == k) {
 #pragma unroll
-            for (int j = 0; j < kMedMax; ++j) prow[j] = a[j];
-        }
-        __syncthreads();
-        float piv = prow[k];
-        if (!(piv > 0.f)) {
-            if (t == 0) bad_any = 1;
-            piv = 1.f;
-        }
-        const float ip = 1.f / piv;
-        if (t == k) {
-#pragma unroll
-            for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? ip : a[j] * ip;
+            for (int i = 0; i + 1 < H; ++i) a[i] = a[i + 1] * ip;
+            a[H - 1] = h ? ip : tail * ip;
         } else if (ev) {
-            const float f = t < k ? -prow[t] : prow[t];
+            const float g = (h ? o : a[0]) * ip;
+            const float* pr = prow[b] + h * HO;
+            const float4* q = reinterpret_cast<const float4*>(pr);
+            const float pend = h ? 1.f : pr[HO];         // the slot after this half (1: column k's own entry)
+            float4 v = q[0];
 #pragma unroll
-            for (int j = 0; j < kMedMax; ++j) a[j] = (j == k) ? -f * ip : a[j] - f * (prow[j] * ip);
+            for (int q4 = 0; q4 < H / 4; ++q4) {
+                const float4 vn = q4 + 1 < H / 4 ? q[q4 + 1] : make_float4(pend, 0.f, 0.f, 0.f);
+                a[4 * q4] = fmaf(-g, v.y, a[4 * q4 + 1]);
+                a[4 * q4 + 1] = fmaf(-g, v.z, a[4 * q4 + 2]);
+                a[4 * q4 + 2] = fmaf(-g, v.w, a[4 * q4 + 3]);
+                a[4 * q4 + 3] = fmaf(-g, vn.x, 4 * q4 + 4 < H ? a[(4 * q4 + 4) % H] : tail);
+                v = vn;
+            }
         }
+        if (t == k + 1 && k + 1 < B) publish(b ^ 1);
     }
     __syncthreads();
-    if (bad_any && t == 0) atomicExch(&c.sc->nonpd, 1);
+    if (*bad_any && threadIdx.x == 0) atomicExch(&c.sc->nonpd, 1);
     // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
     float yt = 0.f;
 #pragma unroll
-    for (int j = 0; j < kMedMax; ++j) yt += a[j];
+    for (int i = 0; i < H; ++i) yt += a[i];
+    yt += __shfl_xor_sync(kFull, yt, 1);
+    const bool lead = ev && h == 0;
     const double y = ev ? (double)yt : 0.0;
-    const double sig = med_sum(y, sh);
+    const double sig = med_sum<kMedFactorThreads>(lead ? y : 0.0, sh);
     const double isg = 1.0 / sig;
     const int con = c.constrained[w];
-    if (ev) c.y1[e] = y;
-    if (t == 0) {
+    if (lead) c.y1[e] = y;
+    if (threadIdx.x == 0) {
         c.sigma[w] = sig;
         c.isigma[w] = isg;
     }
-    const double x0 = ev ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
-    // P_w row t, stored; R^T P_w R (y and R of the block through shared memory)
+    const double x0 = lead ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
+    // P_w row t, stored; R^T P_w R in FP32 (it only scales the stopping test)
     const double R = ev ? c.R[e] : 0.0;
-    sv[t] = R;
-    prow[t] = (float)y;
+    if (h == 0) {
+        rs[t] = (float)R;
+        ys[t] = (float)y;
+    }
     __syncthreads();
     const float yis = (float)(y * isg);
-    double pr = 0.0;
+    float pr0 = 0.f, pr1 = 0.f;
     // stored column by column ([w][j][t]: row t of P_w at stride B), so that the
     // block's threads write, and later read, consecutive words
     float* Pw = c.Lf + (size_t)w * B * B + (ev ? t : 0);
 #pragma unroll
-    for (int j = 0; j < kMedMax; ++j) {
+    for (int i = 0; i < H; ++i) {
+        const int sl = h * H + i;
+        const int j = sl + B - (sl + B >= NP ? NP : 0);      // the column in slot sl
         if (j < B) {
-            const float pj = con ? a[j] - yis * prow[j] : a[j];
+            const float pj = con ? a[i] - yis * ys[j] : a[i];
             if (ev) Pw[(size_t)j * B] = pj;
-            pr += (double)pj * sv[j];
+            if (i & 1) pr1 = fmaf(pj, rs[j], pr1);
+            else pr0 = fmaf(pj, rs[j], pr0);
         }
     }
-    const double rn = med_sum(ev ? R * pr : 0.0, sh);
+    float prt = pr0 + pr1;
+    prt += __shfl_xor_sync(kFull, prt, 1);
+    const double rn = med_sum<kMedFactorThreads>(lead ? R * (double)prt : 0.0, sh);
     const double cw = c.cw[w];
     // warm start moved onto this step's constraint
-    const double sx = med_sum(x0, sh);
+    const double sx = med_sum<kMedFactorThreads>(x0, sh);
     const double corr = con ? (cw - sx) * isg : 0.0;
-    if (ev) {
+    if (lead) {
         const double xe = x0 + corr * y;
         c.x[e] = xe;
         c.pf[e] = (float)xe;
     }
-    if (t == 0) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+    if (threadIdx.x == 0) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+}
+
+__global__ void __launch_bounds__(kMedFactorThreads, 6) k_factor_med(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    const int w = blockIdx.x;
+    if (w >= c.W || !is_med(c)) return;
+    __shared__ __align__(16) float prow[2][kMedMax + 4];
+    __shared__ float ip_s[2];
+    __shared__ float ys[kMedMax];
+    __shared__ float rs[kMedMax];
+    __shared__ double sh[kMedFactorThreads / 32];
+    __shared__ int bad_any;
+    if (threadIdx.x == 0) bad_any = 0;
+    if (c.B <= 32) factor_med_body<32>(c, w, prow, ip_s, ys, rs, sh, &bad_any);
+    else if (c.B <= 48) factor_med_body<48>(c, w, prow, ip_s, ys, rs, sh, &bad_any);
+    else factor_med_body<kMedMax>(c, w, prow, ip_s, ys, rs, sh, &bad_any);
+}
+
+// Row t of a B x B block stored column by column (entry (t, j) at col[j B])
+// against the vector v in shared memory (zero from B on), for B <= NP: the
+// loads unrolled over NP slots and issued ahead of their products, four
+// partial sums.
+template <int NP, typename T>
+__device__ __forceinline__ T med_row_dot_n(const T* col, const T* v, int B) {
+    constexpr int CH = sizeof(T) == 4 ? NP : 16;   // loads in flight: the FP32 row, or 16 FP64
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int j0 = 0; j0 < NP; j0 += CH) {
+        T m[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) m[u] = j0 + u < B ? __ldg(col + (size_t)(j0 + u) * B) : T(0);
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (j0 + u < NP) acc[u & 3] = fma(m[u], v[j0 + u], acc[u & 3]);
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+template <typename T>
+__device__ __forceinline__ T med_row_dot(const T* col, const T* v, int B) {
+    if (B <= 32) return med_row_dot_n<32>(col, v, B);
+    if (B <= 48) return med_row_dot_n<48>(col, v, B);
+    return med_row_dot_n<kMedMax>(col, v, B);
 }
 
 // Projected residual update and preconditioner of the block (thread t holds
@@ -831,20 +911,11 @@ __device__ __forceinline__ double med_residual_precond(const CoilDev& c, int w, 
         else if (con) c.uw[w] += u;
     }
     if (ev) c.res[e] = v;
-    // z = P_w r: the row of the stored FP32 P_w against r in FP32, two partial sums
+    // z = P_w r: the row of the stored FP32 P_w against r in FP32
     vf_s[t] = ev ? (float)v : 0.f;
     __syncthreads();
-    float z0 = 0.f, z1 = 0.f;
-    if (ev) {
-        const float* P = c.Lf + (size_t)w * B * B + t;      // row t at stride B (see k_factor_med)
-        int j = 0;
-        for (; j + 1 < B; j += 2) {
-            z0 = fmaf(P[(size_t)j * B], vf_s[j], z0);
-            z1 = fmaf(P[(size_t)(j + 1) * B], vf_s[j + 1], z1);
-        }
-        if (j < B) z0 = fmaf(P[(size_t)j * B], vf_s[j], z0);
-    }
-    double z = ev ? (double)(z0 + z1) : 0.0;
+    // (row t of P_w at stride B, see k_factor_med)
+    double z = ev ? (double)med_row_dot(c.Lf + (size_t)w * B * B + t, vf_s, B) : 0.0;
     // the FP32 rounding's component along the constrained direction, removed in FP64
     const double sz = med_sum(z, sh);
     if (con && ev) z -= y * sz * isg;
@@ -910,15 +981,9 @@ __global__ void __launch_bounds__(kMedMax) k_near_med(const CoilDev* __restrict_
     __syncthreads();
     double dot = 0.0;
     if (ev) {
-        const double* nb = c.near + (size_t)c.block_type[w] * B * B + (size_t)t * B;
-        double a0 = 0.0, a1 = 0.0;
-        int j = 0;
-        for (; j + 1 < B; j += 2) {
-            a0 = fma(nb[j], ps[j], a0);
-            a1 = fma(nb[j + 1], ps[j + 1], a1);
-        }
-        if (j < B) a0 = fma(nb[j], ps[j], a0);
-        const double acc = (a0 + a1) + c.dt * c.G[e] * pv;
+        // row t read as column t (the self block is symmetric entry for entry):
+        // consecutive threads, consecutive words
+        const double acc = med_row_dot(c.near + (size_t)c.block_type[w] * B * B + t, ps, B) + c.dt * c.G[e] * pv;
         const double qe = c.qv[e] + acc;
         c.qv[e] = qe;
         dot = pv * qe;
