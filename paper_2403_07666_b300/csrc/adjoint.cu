@@ -43,11 +43,10 @@ __global__ void k_adj_adi_z(const CoilDev* __restrict__ cds, AdjBufs ab) {
     int i = blockIdx.x;
     if (i >= c.Gr) return;
     extern __shared__ double sm[];
-    int Gr = c.Gr, Gz = c.Gz, lane = threadIdx.x;
-    for (int j = lane; j < Gz; j += 32) sm[j] = ab.lamU_next[j * Gr + i];
-    __syncwarp();
-    warp_tridiag(sm, Gz, c.thz_lo, c.thz_inv, c.thz_cp);
-    for (int j = lane; j < Gz; j += 32) ab.a[j * Gr + i] = sm[j];
+    int Gr = c.Gr, Gz = c.Gz;
+    for (int j = threadIdx.x; j < Gz; j += blockDim.x) sm[j] = ab.lamU_next[j * Gr + i];
+    line_tridiag(sm, sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
+    for (int j = threadIdx.x; j < Gz; j += blockDim.x) ab.a[j * Gr + i] = sm[j];
 }
 
 // b = (I - dt/2 A_r)^-1 (I + dt/2 A_r) a   (r-lines)
@@ -56,9 +55,9 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
     int j = blockIdx.x;
     if (j >= c.Gz) return;
     extern __shared__ double sm[];
-    int Gr = c.Gr, lane = threadIdx.x;
+    int Gr = c.Gr;
     double hd = 0.5 * c.dt, invC = 1.0 / c.Ccell;
-    for (int i = lane; i < Gr; i += 32) {
+    for (int i = threadIdx.x; i < Gr; i += blockDim.x) {
         int g = j * Gr + i;
         double ai = ab.a[g];
         double ar = 0.0;
@@ -66,9 +65,8 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
         if (i < Gr - 1) ar += c.Kr[i] * (ab.a[g + 1] - ai);
         sm[i] = ai + hd * (ar * invC);
     }
-    __syncwarp();
-    warp_tridiag(sm, Gr, c.thr_lo, c.thr_inv, c.thr_cp);
-    for (int i = lane; i < Gr; i += 32) ab.b[j * Gr + i] = sm[i];
+    line_tridiag(sm, sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
+    for (int i = threadIdx.x; i < Gr; i += blockDim.x) ab.b[j * Gr + i] = sm[i];
 }
 
 // lam_u = (I + dt/2 A_z) b + (ds/du) lam_s,  lam_s = dt/2 (a + b),
@@ -154,13 +152,13 @@ __device__ JcD jc_with_derivatives(const CoilDev& c, double Bm, double T, double
 // FP32), whose Jacobians these are.
 __device__ JcD jc_with_derivatives_f(const CoilDev& c, float Bm, float T, float ep, float f) {
     JcD d = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    const float Jc0 = (float)c.Jc0;
+    const float Jc0 = c.f_Jc0;
     if (c.jc_model == 1) {
         d.Jc = f * Jc0;
         d.df = Jc0;
         return d;
     }
-    const float Tc = (float)c.Tc, Bc20 = (float)c.Bc2_0, Ce = (float)c.C_eps, Breg = (float)c.B_reg;
+    const float Tc = c.f_Tc, Bc20 = c.f_Bc2_0, Ce = c.f_C_eps, Breg = c.f_B_reg;
     const float tr = T / Tc;
     const float Bc2 = Bc20 * (1.0f - tr * tr);
     if (!(T < Tc && Bm < Bc2)) return d;
@@ -213,10 +211,10 @@ __device__ EJD ej_with_derivatives_f(const CoilDev& c, int fil, float aJ, float 
     EJD d = {1.0, 1.0, 0.0, 0.0, 0.0};
     if (!fil || Jc <= 0.0f) return d;
     if (aJ == 0.0f) { d.frac = 0.0; d.dfac = 0.0; return d; }
-    const float n = (float)c.nexp;
+    const float n = c.f_nexp;
     const float lnx = logf(aJ / Jc);
     d.lnx = lnx;
-    const float ell = logf((float)c.E0 / (Jc * (float)c.rho_n)) + (n - 1.0f) * lnx;
+    const float ell = logf(c.f_E0 / (Jc * c.f_rho_n)) + (n - 1.0f) * lnx;
     if (ell > 0.0f) {
         const float t = expf(-ell), opt = 1.0f + t;
         d.frac = 1.0f / opt;
@@ -259,7 +257,7 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, dou
         double Bm;
         EJD ej;
         if (f32) {
-            float br = 0.0f, bz = 0.0f, tf = (float)c.T_bath;
+            float br = 0.0f, bz = 0.0f, tf = c.f_T_bath;
             if (c.has_grid) {
                 field_at_f(c, e, Ba0, &br, &bz);
                 g = c.elem_grid[e];
@@ -434,9 +432,17 @@ inline unsigned adj_elem_blocks(long long n) {
     return (unsigned)(b > 148LL * 32 ? 148LL * 32 : (b < 1 ? 1 : b));
 }
 
+// Dynamic shared memory the reverse ADI kernels may take (lines of more than
+// 1,536 cells need more than the default 48 KB).
+cudaError_t adj_adi_allow_smem(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_adi_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj_adi_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 void launch_adj_thermal(const CoilDev* d, const CoilDev& h, const AdjBufs& ab, cudaStream_t s) {
-    k_adj_adi_z<<<h.Gr, 32, h.Gz * sizeof(double), s>>>(d, ab);
-    k_adj_adi_r<<<h.Gz, 32, h.Gr * sizeof(double), s>>>(d, ab);
+    k_adj_adi_z<<<h.Gr, kAdiThreads, adi_smem_bytes(h.Gz), s>>>(d, ab);
+    k_adj_adi_r<<<h.Gz, kAdiThreads, adi_smem_bytes(h.Gr), s>>>(d, ab);
     k_adj_adi_src<<<adj_elem_blocks((long long)h.Gr * h.Gz), kAdjThreads, 0, s>>>(d, ab);
 }
 

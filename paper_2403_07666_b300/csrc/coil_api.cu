@@ -53,6 +53,8 @@ __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
 __global__ void k_replay_restore(const CoilDev* __restrict__ cds);
 __global__ void k_adi_r(const CoilDev* __restrict__ cds);
+cudaError_t adi_allow_smem(size_t bytes);
+cudaError_t adj_adi_allow_smem(size_t bytes);
 __global__ void k_adi_z(const CoilDev* __restrict__ cds);
 __global__ void k_step_end(const CoilDev* __restrict__ cds);
 __global__ void k_read(const CoilDev* __restrict__ cds, double Ba, double* J, double* Br, double* Bz,
@@ -217,6 +219,14 @@ coil_status upload(coil_t* c, T** p, const std::vector<T>& host, const char* wha
 
 bool is_fin(double v) { return isfinite(v) != 0; }
 
+// FP32 copies of the material constants (round to nearest, as a device
+// conversion would give).
+void round_constants(CoilDev& h) {
+    h.f_E0 = (float)h.E0; h.f_nexp = (float)h.nexp; h.f_Jc0 = (float)h.Jc0; h.f_Tc = (float)h.Tc;
+    h.f_Bc2_0 = (float)h.Bc2_0; h.f_B_reg = (float)h.B_reg; h.f_C_eps = (float)h.C_eps;
+    h.f_p_eps = (float)h.p_eps; h.f_rho_n = (float)h.rho_n; h.f_T_bath = (float)h.T_bath;
+}
+
 // 3-point Lagrange derivative weights at x for nodes x0 < x1 < x2.
 void lagrange_weights(double x0, double x1, double x2, double x, double* w) {
     w[0] = ((x - x1) + (x - x2)) / ((x0 - x1) * (x0 - x2));
@@ -244,6 +254,11 @@ void stencil_axis(const std::vector<double>& ax, std::vector<int>& j0, std::vect
 }
 
 // Thomas factors of (I - hd/C A) for face conductances K (G - 1 faces).
+// Thomas factors of (I - hd/C A) on one grid line (A the conductance
+// Laplacian with link conductances K), in the recurrence form of the line
+// solve: forward y_i = lo_i y_{i-1} + inv_i v_i, backward x_i = cp_i x_{i+1} +
+// y_i (on return lo holds the forward coefficients -l_i / d_i and cp the
+// backward ones -u_i / d_i; lo_0 = cp_{G-1} = 0).
 void thomas_factors(const std::vector<double>& K, double hd, double C, std::vector<double>& lo,
                     std::vector<double>& inv, std::vector<double>& cp) {
     int G = (int)K.size() + 1;
@@ -265,6 +280,10 @@ void thomas_factors(const std::vector<double>& K, double hd, double C, std::vect
         den = diag[i] - lo[i] * cp[i - 1];
         inv[i] = 1.0 / den;
         cp[i] = (i < G - 1) ? up[i] / den : 0.0;
+    }
+    for (int i = 0; i < G; ++i) {
+        lo[i] = i > 0 ? -lo[i] * inv[i] : 0.0;
+        cp[i] = i < G - 1 ? -cp[i] : 0.0;
     }
 }
 
@@ -606,6 +625,16 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.has_grid = sol ? 1 : 0;
     h.Gr = Gr;
     h.Gz = Gz;
+    if (sol) {
+        // each ADI line solve holds its line and three factor rows in shared memory
+        const size_t line_smem = adi_smem_bytes(std::max(Gr, Gz));
+        if (line_smem > (size_t)227 * 1024)
+            return fail(c, COIL_ERR_INVALID, "thermal grid line longer than 7,264 cells (layers or turns x n_sub)");
+        if (line_smem > (size_t)48 * 1024) {
+            CK(adi_allow_smem(line_smem), "ADI shared memory");
+            CK(adj_adi_allow_smem(line_smem), "ADI shared memory");
+        }
+    }
     h.thermal = (sol && m->thermal) ? 1 : 0;
     h.jc_model = m->jc_model;
     h.precision = o->precision;
@@ -615,6 +644,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.C_eps = m->C_eps; h.p_eps = m->p_eps; h.rho_n = m->rho_n; h.rho_m = m->rho_m; h.c0 = m->c0;
     h.h0 = m->h0; h.T_ref = m->T_ref; h.T_bath = m->T_bath;
     h.u_bath = h.T_bath * h.T_bath * h.T_bath * h.T_bath;
+    round_constants(h);
     h.maxit = o->maxit;
     h.rtol2 = o->rtol * o->rtol;
     h.diag_cap = o->diag_capacity > 0 ? o->diag_capacity : 65536;
@@ -686,8 +716,8 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         h.inv_h2 = 1.0 / (hel * hel);
         double* t6;
         TRY(dalloc(c, &t6, 3 * (size_t)Gr + 3 * (size_t)Gz, "thomas"));
-        h.thr_lo = t6; h.thr_inv = t6 + Gr; h.thr_cp = t6 + 2 * Gr;
-        h.thz_lo = t6 + 3 * Gr; h.thz_inv = t6 + 3 * Gr + Gz; h.thz_cp = t6 + 3 * Gr + 2 * Gz;
+        h.thr_a = t6; h.thr_inv = t6 + Gr; h.thr_c = t6 + 2 * Gr;
+        h.thz_a = t6 + 3 * Gr; h.thz_inv = t6 + 3 * Gr + Gz; h.thz_c = t6 + 3 * Gr + 2 * Gz;
         std::vector<double> u0((size_t)Gr * Gz, m->T_bath * m->T_bath * m->T_bath * m->T_bath);
         TRY(upload(c, &h.uT, u0, "uT"));
         TRY(dalloc(c, &h.ustar, (size_t)Gr * Gz, "ustar"));
@@ -898,7 +928,7 @@ coil_status set_drive(coil_t* c, const coil_drive* dr) {
         all.insert(all.end(), lz.begin(), lz.end());
         all.insert(all.end(), iz.begin(), iz.end());
         all.insert(all.end(), cz.begin(), cz.end());
-        CK(cudaMemcpyAsync((void*)h.thr_lo, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync((void*)h.thr_a, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice,
                            c->stream), "thomas");
         CK(cudaStreamSynchronize(c->stream), "thomas");
         c->thomas_dt = dr->dt;
@@ -1148,8 +1178,8 @@ coil_status step_iteration(coil_t* c, const Launch& L) {
 coil_status step_epilogue(coil_t* c, const Launch& L) {
     k_finalize<<<warp_grid(L), 256, 0, L.s>>>(L.d);
     if (L.thermal) {
-        k_adi_r<<<dim3(L.maxGz, L.n), 32, L.maxGr * sizeof(double), L.s>>>(L.d);
-        k_adi_z<<<dim3(L.maxGr, L.n), 32, L.maxGz * sizeof(double), L.s>>>(L.d);
+        k_adi_r<<<dim3(L.maxGz, L.n), kAdiThreads, adi_smem_bytes(L.maxGr), L.s>>>(L.d);
+        k_adi_z<<<dim3(L.maxGr, L.n), kAdiThreads, adi_smem_bytes(L.maxGz), L.s>>>(L.d);
         c->launches += 2;
     }
     k_step_end<<<dim3(kStepEndCtas, L.n), kStepEndThreads, 0, L.s>>>(L.d);
@@ -2303,6 +2333,7 @@ extern "C" coil_status coil_set_params(coil_t* c, const double* jc_factor, doubl
     }
     c->h.nexp = n;
     c->h.C_eps = C_eps;
+    round_constants(c->h);
     TRY(sync_descriptor(c));
     CK(cudaStreamSynchronize(c->stream), "set params");
     return COIL_OK;

@@ -18,6 +18,9 @@ constexpr int kSegMax = 16;          // blocks this small share a warp (32 / B r
 constexpr int kMedMax = 64;          // blocks of kSegMax + 1 .. kMedMax elements (no subelements): one
                                      // row per thread of a 64-thread CTA, FP32 inverse, stored P_w
 constexpr int kMedFactorThreads = 2 * kMedMax;   // the medium-wire factor: two threads per row
+constexpr int kAdiThreads = 128;     // threads per grid line of the ADI solves (tridiag.cuh)
+// shared memory of one ADI line solve: the line and its three factor rows
+__host__ __device__ constexpr size_t adi_smem_bytes(int G) { return 4 * (size_t)G * sizeof(double); }
 constexpr int kGroupMax = 16;        // subelements per turn
 constexpr int kGroupMaxSeg = 6;      // subelements per turn of blocks of at most kSegMax elements
 constexpr int kSegWarps = 4;         // warps per CTA of the shared-warp kernels
@@ -93,10 +96,13 @@ struct CoilDev {
     double Ccell, helem;
     double src_k, inv_Tref, inv_h2;   // 4 / (rho_m c0), 1 / T_ref, 1 / helem^2 of the heat source
     double u_bath, inv_dt;            // T_bath^4, 1 / dt (0 for dt = 0)
-    const double *thr_lo, *thr_inv, *thr_cp;
-    const double *thz_lo, *thz_inv, *thz_cp;
+    const double *thr_a, *thr_inv, *thr_c;    // line-solve factors (recurrence form, tridiag.cuh)
+    const double *thz_a, *thz_inv, *thz_c;
     // material scalars
     double E0, nexp, Jc0, Tc, Bc2_0, B_reg, C_eps, p_eps, rho_n, rho_m, c0, h0, T_ref, T_bath;
+    // the same rounded to FP32 once on the host (the FP32 pointwise chain of the
+    // mixed form would otherwise convert them per element on the FP64 pipe)
+    float f_E0, f_nexp, f_Jc0, f_Tc, f_Bc2_0, f_B_reg, f_C_eps, f_p_eps, f_rho_n, f_T_bath;
     double inv_Y;                 // 1 / Y_eff of the Lorentz hoop strain; 0 = static strain
     // drive of the current coil_step call
     double dt, ramp, Imax, Ba_rate, Ba_max;
@@ -106,7 +112,8 @@ struct CoilDev {
     // state and work vectors (element order unless noted)
     double *I, *Phi, *x, *res, *zv, *dv, *qv, *R, *G;
     float *pf;                    // FP32 copy of the operator input (ld long)
-    double *uT, *ustar, *src, *qgrid;   // grid order [Gz][Gr]
+    double *uT, *qgrid;           // grid order [Gz][Gr]
+    double *ustar, *src;          // column order [Gr][Gz] (the ADI z-lines read them)
     double *L, *y1, *sigma, *cw, *uw;   // per block
     float *Lf;                          // P_w in FP32, blocks of at most kMedMax elements:
                                         // [w][row][col] up to kSegMax, [w][col][row] above

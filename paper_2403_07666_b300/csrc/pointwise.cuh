@@ -120,18 +120,18 @@ __device__ __forceinline__ void field_at_f(const CoilDev& c, int e, double Ba, f
 __device__ __forceinline__ float strain_power_f(const CoilDev& c, int e, double r, double J, float Bz) {
     if (c.inv_Y == 0.0) return (float)c.strain_pow[e];
     const float eps = (float)c.strain[e] + (float)(r * J * c.inv_Y) * Bz;
-    return powf(fabsf(eps), (float)c.p_eps);
+    return powf(fabsf(eps), c.f_p_eps);
 }
 
 __device__ __forceinline__ float critical_current_f(const CoilDev& c, float Bm, float T, float pe, float f) {
-    if (c.jc_model == 1) return f * (float)c.Jc0;
-    const float tr = T / (float)c.Tc;
-    const float Bc2 = (float)c.Bc2_0 * (1.0f - tr * tr);
-    if (!(T < (float)c.Tc && Bm < Bc2)) return 0.0f;
-    const float strain = fmaxf(0.0f, 1.0f - (float)c.C_eps * pe);
+    if (c.jc_model == 1) return f * c.f_Jc0;
+    const float tr = T / c.f_Tc;
+    const float Bc2 = c.f_Bc2_0 * (1.0f - tr * tr);
+    if (!(T < c.f_Tc && Bm < Bc2)) return 0.0f;
+    const float strain = fmaxf(0.0f, 1.0f - c.f_C_eps * pe);
     const float bfac = 1.0f - Bm / Bc2;
     const float omt = 1.0f - tr;
-    return f * (float)c.Jc0 * (omt * sqrtf(omt)) * (bfac * bfac) / sqrtf(Bm + (float)c.B_reg) * strain;
+    return f * c.f_Jc0 * (omt * sqrtf(omt)) * (bfac * bfac) / sqrtf(Bm + c.f_B_reg) * strain;
 }
 
 __device__ __forceinline__ void ej_law_f(const CoilDev& c, int fil, float aJ, float Jc, float* frac, float* dfac,
@@ -140,8 +140,8 @@ __device__ __forceinline__ void ej_law_f(const CoilDev& c, int fil, float aJ, fl
     if (Jc <= 0.0f) { *frac = 1.0f; *dfac = 1.0f; *jrat = aJ > 0.0f ? __int_as_float(0x7f800000) : 0.0f; return; }
     *jrat = aJ / Jc;
     if (aJ == 0.0f) { *frac = 0.0f; *dfac = 0.0f; return; }
-    const float n = (float)c.nexp;
-    const float ell = logf((float)c.E0 / (Jc * (float)c.rho_n)) + (n - 1.0f) * logf(aJ / Jc);
+    const float n = c.f_nexp;
+    const float ell = logf(c.f_E0 / (Jc * c.f_rho_n)) + (n - 1.0f) * logf(aJ / Jc);
     if (ell > 0.0f) {
         const float t = expf(-ell);
         const float opt = 1.0f + t;

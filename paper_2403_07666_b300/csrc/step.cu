@@ -92,7 +92,7 @@ __device__ __forceinline__ ElemOut pointwise_element(const CoilDev& c, int e, do
         o.tq = T;
         inv_a = 0.0;
     } else {
-        float Br = 0.0f, Bz = 0.0f, T = (float)c.T_bath;
+        float Br = 0.0f, Bz = 0.0f, T = c.f_T_bath;
         double u = c.T_bath * c.T_bath * c.T_bath * c.T_bath;
         if (c.has_grid) {
             field_at_f(c, e, Ba0, &Br, &Bz);
@@ -146,7 +146,7 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
     const float a = (float)c.area[e];
     const int fil = c.mat[e];
     const double I = c.I[e];
-    float Br = 0.0f, Bz = 0.0f, T = (float)c.T_bath;
+    float Br = 0.0f, Bz = 0.0f, T = c.f_T_bath;
     double u = c.u_bath;
     const float tpr = 2.0f * (float)kPi * (float)r;        // 2 pi r in FP32 (no FP64 product)
     const float inv2pir = 1.0f / tpr;
@@ -178,7 +178,7 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
                          : 0.0f;
     float frac, dfac, jrat;
     ej_law_f(c, fil, fabsf(J), Jc, &frac, &dfac, &jrat);
-    const float rn = (float)c.rho_n;
+    const float rn = c.f_rho_n;
     const float rho = rn * frac;
     const float E = rho * J;
     const float q = E * J;
@@ -1882,59 +1882,58 @@ __device__ __forceinline__ double thermal_source(const CoilDev& c, int g, double
     return c.src_k * (c.qgrid[g] - loss * c.inv_h2);
 }
 
-// r-lines: u* = (I - dt/2 A_r)^-1 [(I + dt/2 A_z) u + dt/2 s].  One warp per grid row.
+// r-lines: u* = (I - dt/2 A_r)^-1 [(I + dt/2 A_z) u + dt/2 s].  One CTA per grid row.
 __global__ void k_adi_r(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->status != ST_OK) return;
     int j = blockIdx.x;
     if (j >= c.Gz) return;
     extern __shared__ double sm[];
-    int Gr = c.Gr, Gz = c.Gz, lane = threadIdx.x;
+    int Gr = c.Gr, Gz = c.Gz;
     double hd = 0.5 * c.dt;
     double invC = 1.0 / c.Ccell;
-    for (int i = lane; i < Gr; i += 32) {
+    for (int i = threadIdx.x; i < Gr; i += blockDim.x) {
         int g = j * Gr + i;
         double u = c.uT[g];
         double s = thermal_source(c, g, u);
-        c.src[g] = s;
+        c.src[(size_t)i * Gz + j] = s;
         double az = 0.0;
         if (j > 0) az += c.Kz[j - 1] * (c.uT[g - Gr] - u);
         if (j < Gz - 1) az += c.Kz[j] * (c.uT[g + Gr] - u);
         sm[i] = u + hd * (az * invC) + hd * s;
     }
-    __syncwarp();
-    warp_tridiag(sm, Gr, c.thr_lo, c.thr_inv, c.thr_cp);
-    for (int i = lane; i < Gr; i += 32) c.ustar[j * Gr + i] = sm[i];
+    line_tridiag(sm, sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
+    // stored column by column: the z-lines' loads are then contiguous
+    for (int i = threadIdx.x; i < Gr; i += blockDim.x) c.ustar[(size_t)i * Gz + j] = sm[i];
 }
 
-// z-lines: u' = (I - dt/2 A_z)^-1 [(I + dt/2 A_r) u* + dt/2 s].  One warp per column.
+// z-lines: u' = (I - dt/2 A_z)^-1 [(I + dt/2 A_r) u* + dt/2 s].  One CTA per column.
 __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->status != ST_OK) return;
     int i = blockIdx.x;
     if (i >= c.Gr) return;
     extern __shared__ double sm[];
-    int Gr = c.Gr, Gz = c.Gz, lane = threadIdx.x;
+    int Gr = c.Gr, Gz = c.Gz;
     double hd = 0.5 * c.dt;
     double invC = 1.0 / c.Ccell;
-    for (int j = lane; j < Gz; j += 32) {
-        int g = j * Gr + i;
-        double us = c.ustar[g];
+    const double* col = c.ustar + (size_t)i * Gz;       // column i (and i -/+ 1 at -/+ Gz)
+    for (int j = threadIdx.x; j < Gz; j += blockDim.x) {
+        double us = col[j];
         double ar = 0.0;
-        if (i > 0) ar += c.Kr[i - 1] * (c.ustar[g - 1] - us);
-        if (i < Gr - 1) ar += c.Kr[i] * (c.ustar[g + 1] - us);
-        sm[j] = us + hd * (ar * invC) + hd * c.src[g];
+        if (i > 0) ar += c.Kr[i - 1] * (col[j - Gz] - us);
+        if (i < Gr - 1) ar += c.Kr[i] * (col[j + Gz] - us);
+        sm[j] = us + hd * (ar * invC) + hd * c.src[(size_t)i * Gz + j];
     }
-    __syncwarp();
-    warp_tridiag(sm, Gz, c.thz_lo, c.thz_inv, c.thz_cp);
+    line_tridiag(sm, sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
     double um = 0.0;
-    for (int j = lane; j < Gz; j += 32) {
+    for (int j = threadIdx.x; j < Gz; j += blockDim.x) {
         double u = sm[j];
         c.uT[j * Gr + i] = u;
         um = fmax(um, u);
     }
-    um = warp_max(um);
-    if (lane == 0) c.partT[i] = um;
+    um = block_reduce_max(um, sm + Gz);     // the factor rows are free once line_tridiag returns
+    if (threadIdx.x == 0) c.partT[i] = um;
 }
 
 // The step's diagnostic record, then t += dt.  kStepEndCtas CTAs per coil
@@ -2030,6 +2029,14 @@ __global__ void k_read(const CoilDev* __restrict__ cds, double Ba, double* J, do
         if (Bz) Bz[e] = bz;
         if (T) T[e] = c.has_grid ? sqrt(sqrt(c.uT[c.elem_grid[e]])) : c.T_bath;
     }
+}
+
+// Dynamic shared memory the forward ADI kernels may take (lines of more than
+// 1,536 cells need more than the default 48 KB).
+cudaError_t adi_allow_smem(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_adi_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adi_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace cq
