@@ -269,7 +269,7 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, dou
             Bz = bz;
             Bm = bm;
             T = tf;
-            if (fil) jd = jc_with_derivatives_f(c, bm, tf, strain_power_f(c, e, r, J, bz), (float)c.jc_factor[e]);
+            if (fil) jd = jc_with_derivatives_f(c, bm, tf, strain_power_f(c, e, J, bz), (float)c.jc_factor[e]);
             ej = ej_with_derivatives_f(c, fil, (float)fabs(J), (float)jd.Jc);
         } else {
             if (c.has_grid) {

@@ -641,6 +641,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.ld = ((long long)N + 63) / 64 * 64;
     h.E0 = m->E0; h.nexp = m->n; h.Jc0 = m->Jc0; h.Tc = m->Tc; h.Bc2_0 = m->Bc2_0; h.B_reg = m->B_reg;
     h.inv_Y = m->Y_eff > 0.0 ? 1.0 / m->Y_eff : 0.0;
+    h.lorentz = h.inv_Y > 0.0 ? 1 : 0;
     h.C_eps = m->C_eps; h.p_eps = m->p_eps; h.rho_n = m->rho_n; h.rho_m = m->rho_m; h.c0 = m->c0;
     h.h0 = m->h0; h.T_ref = m->T_ref; h.T_bath = m->T_bath;
     h.u_bath = h.T_bath * h.T_bath * h.T_bath * h.T_bath;
@@ -664,6 +665,23 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     std::vector<double> stp(N);
     for (int e = 0; e < N; ++e) stp[e] = pow(fabs(st[e]), m->p_eps);
     TRY(upload(c, &dp, stp, "strain power")); h.strain_pow = dp;
+    {
+        std::vector<float4> geo(N);
+        std::vector<float> spf(N);
+        std::vector<double> pr2(N);
+        for (int e = 0; e < N; ++e) {
+            const float tpr = 2.0f * (float)kPi * (float)r[e];
+            const float a = (float)area[e];
+            geo[e] = make_float4(tpr, 1.0f / tpr, a, 1.0f / a);
+            spf[e] = (float)stp[e];
+            pr2[e] = kPi * r[e] * r[e];
+        }
+        float4* gp;
+        float* fp;
+        TRY(upload(c, &gp, geo, "geometry (FP32)")); h.geo_f = gp;
+        TRY(upload(c, &fp, spf, "strain power (FP32)")); h.strain_pow_f = fp;
+        TRY(upload(c, &dp, pr2, "pi r^2")); h.pir2 = dp;
+    }
     TRY(upload(c, &ip, mt, "mat")); h.mat = ip;
     TRY(upload(c, &ip, constrained, "constrained")); h.constrained = ip;
     h.n_groups = g->n_groups > 1 ? g->n_groups : 0;

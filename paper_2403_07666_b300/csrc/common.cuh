@@ -57,6 +57,13 @@ struct CoilDev {
     // element data (element order)
     const double *r, *area, *jc_factor, *strain;
     const double *strain_pow;     // |strain|^p_eps per element
+    // per element, rounded once at coil creation for the mixed form's FP32
+    // pointwise chain: (2 pi r, 1 / (2 pi r), area, 1 / area) and |strain|^p_eps;
+    // pi r^2 in FP64 (the flux-change term of R)
+    const float4 *geo_f;
+    const float *strain_pow_f;
+    const double *pir2;
+    int lorentz;                  // the hoop strain is on (inv_Y > 0)
     const int *mat;               // 1 filament, 0 Cu
     const int *elem_grid;         // i_z * Gr + i_r
     const int *grid_elem;         // inverse map

@@ -117,9 +117,10 @@ __device__ __forceinline__ void field_at_f(const CoilDev& c, int e, double Ba, f
     *Br = -(float)dz * inv;
 }
 
-__device__ __forceinline__ float strain_power_f(const CoilDev& c, int e, double r, double J, float Bz) {
-    if (c.inv_Y == 0.0) return (float)c.strain_pow[e];
-    const float eps = (float)c.strain[e] + (float)(r * J * c.inv_Y) * Bz;
+template <typename TJ>
+__device__ __forceinline__ float strain_power_f(const CoilDev& c, int e, TJ J, float Bz) {
+    if (!c.lorentz) return c.strain_pow_f[e];
+    const float eps = (float)c.strain[e] + (float)(c.r[e] * (double)J * c.inv_Y) * Bz;
     return powf(fabsf(eps), c.f_p_eps);
 }
 

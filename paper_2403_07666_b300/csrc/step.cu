@@ -64,61 +64,36 @@ __device__ __forceinline__ void wire_detectors(const CoilDev& c, int w, long lon
 // Rows a2 and a5 for element e from the start-of-step state: the field from
 // the loop-flux stencil, T, Jc(B, T, eps), the E-J law; writes G, R, the
 // Joule source on the thermal grid and (subelements) the resistive voltage
-// of J_I, and returns what the per-wire reductions need.  F32: the mixed
-// form's FP32 chain (see pointwise.cuh); the element's u = T^4 is returned
-// in place of T, so that the wire's maximum takes one FP64 fourth root.
+// of J_I, and returns what the per-wire reductions need.
 struct ElemOut {
-    double I, pj, tq, q, jrat, frac;   // tq: T (FP64 chain) or u = T^4 (F32)
+    double I, pj, tq, q, jrat, frac;   // tq: T
     int fil;
 };
 
-template <bool F32>
+// The FP64 form's element (every operation FP64).
 __device__ __forceinline__ ElemOut pointwise_element(const CoilDev& c, int e, double Ba0, double dBa) {
     ElemOut o;
     const double r = c.r[e], a = c.area[e];
     const int fil = c.mat[e];
     const double I = c.I[e];
-    double J, frac, dfac, jrat, inv_a;
-    if (!F32) {
-        double Br = 0.0, Bz = 0.0, T = c.T_bath;
-        if (c.has_grid) {
-            field_at(c, e, Ba0, &Br, &Bz);
-            T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
-        }
-        const double Bm = sqrt(Br * Br + Bz * Bz);
-        J = I / a;
-        const double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
-        ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
-        o.tq = T;
-        inv_a = 0.0;
-    } else {
-        float Br = 0.0f, Bz = 0.0f, T = c.f_T_bath;
-        double u = c.T_bath * c.T_bath * c.T_bath * c.T_bath;
-        if (c.has_grid) {
-            field_at_f(c, e, Ba0, &Br, &Bz);
-            u = c.uT[c.elem_grid[e]];
-            T = sqrtf(sqrtf((float)u));
-        }
-        const float Bm = sqrtf(Br * Br + Bz * Bz);
-        inv_a = rcp_nr(a);
-        J = I * inv_a;
-        const float Jc = fil ? critical_current_f(c, Bm, T, strain_power_f(c, e, r, J, Bz), (float)c.jc_factor[e])
-                             : 0.0f;
-        float ff, df, jf;
-        ej_law_f(c, fil, fabsf((float)J), Jc, &ff, &df, &jf);
-        frac = ff;
-        dfac = df;
-        jrat = jf;
-        o.tq = u;
+    double Br = 0.0, Bz = 0.0, T = c.T_bath;
+    if (c.has_grid) {
+        field_at(c, e, Ba0, &Br, &Bz);
+        T = sqrt(sqrt(c.uT[c.elem_grid[e]]));
     }
+    const double Bm = sqrt(Br * Br + Bz * Bz);
+    const double J = I / a;
+    const double Jc = fil ? critical_current(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]) : 0.0;
+    double frac, dfac, jrat;
+    ej_law(c, fil, J, Jc, &frac, &dfac, &jrat);
     const double rho = c.rho_n * frac;
     const double E = rho * J;
     const double q = E * J;
-    c.G[e] = F32 ? 2.0 * kPi * r * (c.rho_n * dfac) * inv_a : 2.0 * kPi * r * (c.rho_n * dfac) / a;
+    c.G[e] = 2.0 * kPi * r * (c.rho_n * dfac) / a;
     c.R[e] = 2.0 * kPi * r * E + kPi * r * r * dBa;
-    if (c.n_groups)                                   // resistive voltage of J_I
-        c.xI[e] = F32 ? 2.0 * kPi * r * rho * c.Itr[e] * inv_a : 2.0 * kPi * r * rho * c.Itr[e] / a;
+    if (c.n_groups) c.xI[e] = 2.0 * kPi * r * rho * c.Itr[e] / a;   // resistive voltage of J_I
     if (c.has_grid) c.qgrid[c.elem_grid[e]] = q;
+    o.tq = T;
     o.I = I;
     o.pj = q * 2.0 * kPi * r * a;
     o.q = q;
@@ -140,30 +115,37 @@ struct ElemOutF {
     int fil;
 };
 
+// Flux derivative of the 3-point stencil along one grid axis, in FP64 (the
+// loop fluxes cancel across one element).  With three cells or more every tap
+// is a cell of the axis and a zero weight adds an exact zero, so no FP64
+// compare is spent on the taps (each FP64 instruction takes a scheduler 64
+// cycles on B300); shorter axes skip their zero-weight taps.
+__device__ __forceinline__ double stencil_diff(const CoilDev& c, const double* w3, const int* cells, int stride,
+                                               bool all_taps) {
+    if (all_taps) {
+        double d = w3[0] * c.Phi[cells[0]];
+        d = fma(w3[1], c.Phi[cells[stride]], d);
+        return fma(w3[2], c.Phi[cells[2 * stride]], d);
+    }
+    double d = 0.0;
+    for (int k = 0; k < 3; ++k)
+        if (w3[k] != 0.0) d = fma(w3[k], c.Phi[cells[k * stride]], d);
+    return d;
+}
+
 __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e, float Ba0, double dBa) {
     ElemOutF o;
-    const double r = c.r[e];
-    const float a = (float)c.area[e];
+    const float4 gf = c.geo_f[e];                          // 2 pi r, 1 / (2 pi r), area, 1 / area
+    const float tpr = gf.x, inv2pir = gf.y, a = gf.z, ia = gf.w;
     const int fil = c.mat[e];
     const double I = c.I[e];
     float Br = 0.0f, Bz = 0.0f, T = c.f_T_bath;
     double u = c.u_bath;
-    const float tpr = 2.0f * (float)kPi * (float)r;        // 2 pi r in FP32 (no FP64 product)
-    const float inv2pir = 1.0f / tpr;
     if (c.has_grid) {
         const int g = c.elem_grid[e];
         const int iz = g / c.Gr, ir = g - iz * c.Gr;
-        double dr = 0.0, dz = 0.0;
-        int j0 = c.sr_j0[ir];
-        for (int k = 0; k < 3; ++k) {
-            const double wk = c.sr_w[3 * ir + k];
-            if (wk != 0.0) dr = fma(wk, c.Phi[c.grid_elem[iz * c.Gr + j0 + k]], dr);
-        }
-        j0 = c.sz_j0[iz];
-        for (int k = 0; k < 3; ++k) {
-            const double wk = c.sz_w[3 * iz + k];
-            if (wk != 0.0) dz = fma(wk, c.Phi[c.grid_elem[(j0 + k) * c.Gr + ir]], dz);
-        }
+        const double dr = stencil_diff(c, c.sr_w + 3 * ir, c.grid_elem + iz * c.Gr + c.sr_j0[ir], 1, c.Gr >= 3);
+        const double dz = stencil_diff(c, c.sz_w + 3 * iz, c.grid_elem + c.sz_j0[iz] * c.Gr + ir, c.Gr, c.Gz >= 3);
         Bz = (float)dr * inv2pir + Ba0;
         Br = -(float)dz * inv2pir;
         u = c.uT[g];
@@ -172,9 +154,8 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
         Bz = Ba0;
     }
     const float Bm = sqrtf(Br * Br + Bz * Bz);
-    const float ia = 1.0f / a;
     const float J = (float)I * ia;
-    const float Jc = fil ? critical_current_f(c, Bm, T, strain_power_f(c, e, r, (double)J, Bz), (float)c.jc_factor[e])
+    const float Jc = fil ? critical_current_f(c, Bm, T, strain_power_f(c, e, J, Bz), (float)c.jc_factor[e])
                          : 0.0f;
     float frac, dfac, jrat;
     ej_law_f(c, fil, fabsf(J), Jc, &frac, &dfac, &jrat);
@@ -183,7 +164,7 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
     const float E = rho * J;
     const float q = E * J;
     c.G[e] = (double)(tpr * (rn * dfac) * ia);
-    c.R[e] = (double)(tpr * E) + kPi * r * r * dBa;
+    c.R[e] = fma(c.pir2[e], dBa, (double)(tpr * E));
     if (c.n_groups) c.xI[e] = (double)(tpr * rho * ia) * c.Itr[e];   // resistive voltage of J_I
     if (c.has_grid) c.qgrid[c.elem_grid[e]] = (double)q;
     o.I = I;
@@ -213,11 +194,6 @@ __device__ __forceinline__ long long seg_max_bits(long long v, int Bp) {
 
 // The wire's maximum temperature from the maximum of tq (the fourth root of
 // a maximum of u is the maximum of the fourth roots).
-template <bool F32>
-__device__ __forceinline__ double wire_tmax(double tq) {
-    return F32 ? sqrt(sqrt(tq)) : tq;
-}
-
 // One warp per block (wire).  Partials: P[0] Joule power, P[1] max |J|/Jc,
 // P[2] mean rho/rho_n of filament elements.
 __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
@@ -231,28 +207,49 @@ __global__ void k_pointwise(const CoilDev* __restrict__ cds) {
     double t0 = sc->t, dt = c.dt, t1 = t0 + dt;
     double It1 = drive_current(c, t1);
     double Ba0 = drive_field(c, t0), Ba1 = drive_field(c, t1);
-    double dBa = (Ba1 - Ba0) / dt;
+    double dBa = F32 ? (Ba1 - Ba0) * c.inv_dt : (Ba1 - Ba0) / dt;
     if (w == 0 && lane == 0) {
         sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
         sc->nonpd = 0;                         // k_factor of this step sets it again if needed
     }
     double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
-    for (int k = lane; k < c.B; k += 32) {
-        const ElemOut o = F32 ? pointwise_element<true>(c, w * c.B + k, Ba0, dBa)
-                              : pointwise_element<false>(c, w * c.B + k, Ba0, dBa);
-        sumI += o.I;
-        pj += o.pj;
-        tmx = fmax(tmx, o.tq);
-        qmx = fmax(qmx, o.q);
-        if (o.fil) { jr = fmax(jr, o.jrat); rhof += o.frac; nfil += 1.0; }
+    if (F32) {
+        // the mixed form's FP32 element and reductions (as in k_pointwise_seg)
+        float pjf = 0.f, jrf = 0.f, rhf = 0.f, nf = 0.f, qf = 0.f;
+        long long ub = 0;
+        for (int k = lane; k < c.B; k += 32) {
+            const ElemOutF o = pointwise_element_f(c, w * c.B + k, (float)Ba0, dBa);
+            sumI += o.I;
+            pjf += o.pj;
+            qf = fmaxf(qf, o.q);
+            ub = max(ub, __double_as_longlong(o.u));
+            if (o.fil) { jrf = fmaxf(jrf, o.jrat); rhf += o.frac; nf += 1.0f; }
+        }
+        sumI = warp_sum(sumI);
+        pj = (double)seg_sumf(pjf, 32);
+        jr = (double)seg_maxf(jrf, 32);
+        rhof = (double)seg_sumf(rhf, 32);
+        nfil = (double)seg_sumf(nf, 32);
+        qmx = (double)seg_maxf(qf, 32);
+        const long long umax = seg_max_bits(ub, 32);
+        if (lane == 0) tmx = (double)sqrtf(sqrtf((float)__longlong_as_double(umax)));
+    } else {
+        for (int k = lane; k < c.B; k += 32) {
+            const ElemOut o = pointwise_element(c, w * c.B + k, Ba0, dBa);
+            sumI += o.I;
+            pj += o.pj;
+            tmx = fmax(tmx, o.tq);
+            qmx = fmax(qmx, o.q);
+            if (o.fil) { jr = fmax(jr, o.jrat); rhof += o.frac; nfil += 1.0; }
+        }
+        sumI = warp_sum(sumI);
+        pj = warp_sum(pj);
+        jr = warp_max(jr);
+        rhof = warp_sum(rhof);
+        nfil = warp_sum(nfil);
+        tmx = warp_max(tmx);
+        qmx = warp_max(qmx);
     }
-    sumI = warp_sum(sumI);
-    pj = warp_sum(pj);
-    jr = warp_max(jr);
-    rhof = warp_sum(rhof);
-    nfil = warp_sum(nfil);
-    tmx = F32 ? wire_tmax<true>(warp_max(tmx)) : warp_max(tmx);
-    qmx = warp_max(qmx);
     if (lane == 0) {
         // the mixed form without FP64 divisions (B300's FP64 pipe): c_w through
         // 1/dt, the wire-mean rho/rho_n (FP32 sums) in FP32
@@ -1099,9 +1096,9 @@ __device__ void loop_condition(const CoilDev& c, cudaGraphConditionalHandle h) {
     cudaGraphSetConditional(h, sc->done ? 0u : 1u);
 }
 
-// Fused reduction of a per-wire value held by the head lane of each wire's
-// segment: every thread of the coil's first n_cta CTAs calls this.  Each CTA
-// sums its wires in a fixed order (butterfly per warp, then warps in order)
+// Fused reduction of a value held by every lane (its term of a dot product):
+// every thread of the coil's first n_cta CTAs calls this.  Each CTA sums its
+// lanes in a fixed order (butterfly per warp, then warps in order)
 // into parts row 7 at its index; the CTA that arrives last on the counter
 // (which it resets for the next launch) sums those n_cta values and does the
 // scalar update of `mode`; true in that CTA.  The counter's release/acquire
@@ -1173,7 +1170,7 @@ __device__ __forceinline__ Seg seg_of(const CoilDev& c, int warp_global) {
 
 // Far-operator value at element e of the tensor-core Toeplitz apply: the sum
 // of the partial tiles of the CTAs that worked on e's channel tile, in a fixed
-// order with eight loads in flight, times 2^-(exT + xmin).  The sum runs on
+// order, times 2^-(exT + xmin).  The sum runs on
 // the FP32 pipe with Kahan's compensated summation and returns s - comp in
 // FP64: about twice FP32's precision for these few terms, at a fraction of
 // the cost of FP64 additions on B300.
@@ -1214,16 +1211,17 @@ __device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv
     const int2 rg = c.tc_range[cc / kTcTileRows];
     const size_t tile = (size_t)c.NT * kTcTileRows;
     const float* p = c.tc_part + (size_t)rg.x * tile + (size_t)t * kTcTileRows + (cc % kTcTileRows);
+    // the loads of up to 24 tiles issued before their sums (one round trip for
+    // the usual 18 CTAs per tile), added in tile order
     float s = 0.f, comp = 0.f;
-    int k = 0;
-    for (; k + 8 <= rg.y; k += 8) {
-        float v[8];
+    for (int k = 0; k < rg.y; k += 24) {
+        float v[24];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = p[(size_t)(k + i) * tile];
+        for (int i = 0; i < 24; ++i) v[i] = k + i < rg.y ? p[(size_t)(k + i) * tile] : 0.f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) kahan_add(v[i], s, comp);
+        for (int i = 0; i < 24; ++i)
+            if (k + i < rg.y) kahan_add(v[i], s, comp);
     }
-    for (; k < rg.y; ++k) kahan_add(p[(size_t)k * tile], s, comp);
     return ((double)s - (double)comp) * inv;
 }
 
@@ -1237,7 +1235,7 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
     const int n_cta = (c.W + per_cta - 1) / per_cta;
     if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
     const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    double head = 0.0;                                  // p^T q of the lane's wire on segment heads
+    double head = 0.0;                                  // the lane's term of p^T q (fused reduction)
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
         const double* p = which == 0 ? c.x : c.dv;
@@ -1268,19 +1266,21 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
             c.qv[s.e] = qe;
             dot = pv * qe;
         }
-        dot = seg_sum(dot, s.Bp);
-        if (which == 1 && s.kk == 0 && s.wv) {
-            if (fuse_alpha) head = dot;
-            else c.parts[4 * (size_t)c.W + s.w] = dot;
+        if (fuse_alpha) {
+            head = which == 1 ? dot : 0.0;              // only the total is needed: no per-wire sums
+        } else {
+            dot = seg_sum(dot, s.Bp);
+            if (which == 1 && s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = dot;
         }
     }
     if (fuse_alpha) fused_reduce(c, head, c.ticket, n_cta, RED_ALPHA);
 }
 
 // Projected residual update and preconditioner of the segment's wire: v is
-// the raw residual on entry; writes res, z and returns z (partial r^T z in rz).
+// the raw residual on entry; writes res, z and returns z (in rz the wire's
+// r^T z, or with lane_rz the lane's own term of it).
 __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const Seg& s, double v, double y,
-                                                        bool first, double* rz) {
+                                                        bool first, double* rz, bool lane_rz = false) {
     const int con = s.wv ? c.constrained[s.w] : 0;
     if (c.n_groups) {
         // subelements: remove Q v, v = (Y S^-1)^T r the subelement voltage
@@ -1358,7 +1358,8 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
         const double sz = seg_sum(z, s.Bp);            // all lanes: the shuffles span the warp
         if (con) z -= y * sz * c.isigma[s.w];
     }
-    *rz = seg_sum(s.ev ? v * z : 0.0, s.Bp);
+    *rz = s.ev ? v * z : 0.0;
+    if (!lane_rz) *rz = seg_sum(*rz, s.Bp);
     return z;
 }
 
@@ -1397,7 +1398,7 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditiona
     }
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
-    double head = 0.0;                                  // r^T z of the lane's wire on segment heads
+    double head = 0.0;                                  // the lane's term of r^T z (fused reduction)
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
         const double alpha = c.sc->alpha;
@@ -1408,12 +1409,10 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditiona
             y = c.y1[s.e];
         }
         double rz;
-        const double z = seg_residual_precond(c, s, v, y, false, &rz);
+        const double z = seg_residual_precond(c, s, v, y, false, &rz, fuse_beta != 0);
         if (s.ev) c.zv[s.e] = z;
-        if (s.kk == 0 && s.wv) {
-            if (fuse_beta) head = rz;
-            else c.parts[4 * (size_t)c.W + s.w] = rz;
-        }
+        if (fuse_beta) head = rz;                   // the lane's term: only the total is needed
+        else if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
     }
     if (fuse_beta && fused_reduce(c, head, c.ticket + 1, n_cta, RED_BETA) && use_cond && threadIdx.x == 0)
         loop_condition(c, cond);
@@ -1439,7 +1438,7 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         It1 = drive_current(c, t1);
         Ba0 = drive_field(c, t0);
         Ba1 = drive_field(c, t1);
-        dBa = (Ba1 - Ba0) / dt;
+        dBa = c.precision != PREC_FP64 ? (Ba1 - Ba0) * c.inv_dt : (Ba1 - Ba0) / dt;
     }
     It1 = __shfl_sync(0xffffffffu, It1, 0);
     Ba0 = __shfl_sync(0xffffffffu, Ba0, 0);
@@ -1449,8 +1448,9 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         sc->It1 = It1; sc->Ba0 = Ba0; sc->Ba1 = Ba1; sc->dBa = dBa;
         sc->nonpd = 0;                         // k_factor of this step sets it again if needed
     }
-    double sumI = 0.0, pj = 0.0, jr = 0.0, rhof = 0.0, nfil = 0.0, tmx = 0.0, qmx = 0.0;
-    if (c.precision != PREC_FP64) {
+    double sumI = 0.0, pj = 0.0, jr = 0.0, mean_rho = 0.0, tmx = 0.0, qmx = 0.0;
+    const bool f32 = c.precision != PREC_FP64;
+    if (f32) {
         // the mixed form's FP32 chain; the current sum stays FP64
         float pjf = 0.f, jrf = 0.f, rhf = 0.f, nf = 0.f, qf = 0.f;
         long long ub = 0;
@@ -1465,14 +1465,15 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         sumI = seg_sum(sumI, s.Bp);
         pj = (double)seg_sumf(pjf, s.Bp);
         jr = (double)seg_maxf(jrf, s.Bp);
-        rhof = (double)seg_sumf(rhf, s.Bp);
-        nfil = (double)seg_sumf(nf, s.Bp);
+        const float rs = seg_sumf(rhf, s.Bp), ns = seg_sumf(nf, s.Bp);
+        mean_rho = ns > 0.0f ? (double)(rs / ns) : 0.0;   // the wire mean, divided in FP32
         const long long umax = seg_max_bits(ub, s.Bp);
         if (s.kk == 0) tmx = (double)sqrtf(sqrtf((float)__longlong_as_double(umax)));   // the head lane's
         qmx = (double)seg_maxf(qf, s.Bp);
     } else {
+        double rhof = 0.0, nfil = 0.0;
         if (s.ev) {
-            const ElemOut o = pointwise_element<false>(c, s.e, Ba0, dBa);
+            const ElemOut o = pointwise_element(c, s.e, Ba0, dBa);
             sumI = o.I;
             pj = o.pj;
             tmx = o.tq;
@@ -1486,12 +1487,12 @@ __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds) {
         nfil = seg_sum(nfil, s.Bp);
         tmx = seg_max(tmx, s.Bp);
         qmx = seg_max(qmx, s.Bp);
+        if (s.kk == 0) mean_rho = nfil > 0.0 ? rhof / nfil : 0.0;
     }
     if (s.kk == 0 && s.wv) {
         const int w = s.w;
         double* parts = c.parts;
-        c.cw[w] = c.constrained[w] ? (It1 - sumI) / dt : 0.0;
-        double mean_rho = nfil > 0.0 ? rhof / nfil : 0.0;
+        c.cw[w] = c.constrained[w] ? (f32 ? (It1 - sumI) * c.inv_dt : (It1 - sumI) / dt) : 0.0;
         parts[0 * (size_t)c.W + w] = pj;
         parts[1 * (size_t)c.W + w] = jr;
         parts[2 * (size_t)c.W + w] = mean_rho;
