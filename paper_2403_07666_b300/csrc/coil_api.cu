@@ -42,11 +42,11 @@ __global__ void k_near(const CoilDev* __restrict__ cds, int which);
 __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
 __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha);
-__global__ void k_init_seg(const CoilDev* __restrict__ cds);
+__global__ void k_init_seg(const CoilDev* __restrict__ cds, int fuse_init);
 __global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond,
                              int use_cond);
 __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds);
-__global__ void k_factor_seg(const CoilDev* __restrict__ cds);
+__global__ void k_factor_seg(const CoilDev* __restrict__ cds, int fuse_scale);
 __global__ void k_factor_seg_groups(const CoilDev* __restrict__ cds);
 __global__ void k_direction(const CoilDev* __restrict__ cds);
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg);
@@ -782,7 +782,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     h.acc_on = 1;
     TRY(dalloc(c, &h.diag, (size_t)h.diag_cap * COIL_DIAG_WIDTH, "diag"));
     TRY(dalloc(c, &h.sc, 1, "scalars"));
-    TRY(dalloc(c, &h.ticket, 4, "arrival counters"));
+    TRY(dalloc(c, &h.ticket, 5, "arrival counters"));
     TRY(dalloc(c, &c->readbuf, 5 * (size_t)N + kMomentBlocks, "read buffer"));
 
     // operator: table of distinct entries, dense far part, FP64 near blocks
@@ -864,7 +864,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     double* nearp;
     float* nearfp = nullptr;
     TRY(dalloc(c, &nearp, (size_t)n_types * B * B, "near blocks"));
-    if (B > kSegMax && B <= kMedMax) TRY(dalloc(c, &nearfp, (size_t)n_types * B * B, "near blocks (FP32)"));
+    if (B <= kMedMax) TRY(dalloc(c, &nearfp, (size_t)n_types * B * B, "near blocks (FP32)"));
     CK(launch_near_blocks(tab, C, NT, B, n_types, nearp, nearfp, c->stream), "near blocks");
     h.near = nearp;
     h.nearf = nearfp;
@@ -1119,10 +1119,13 @@ int launch_near(const Launch& L, int which) {
         k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1);
     return (int)L.chol + (int)L.med + (int)L.seg;
 }
-int launch_init(const Launch& L) {
+// fuse: the small-block coils' init kernel reduces r^T z itself (last CTA).
+int launch_init(const Launch& L, bool fuse) {
     if (L.chol) k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
     if (L.med) k_init_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
-    if (L.seg) k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(L.d);
+    if (L.seg)
+        k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(
+            L.d, (int)fuse);
     return (int)L.chol + (int)L.med + (int)L.seg;
 }
 int launch_pointwise(const Launch& L) {
@@ -1130,12 +1133,14 @@ int launch_pointwise(const Launch& L) {
     if (L.seg) k_pointwise_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d);
     return (int)L.big + (int)L.seg;
 }
-int launch_factor(const Launch& L) {
+// fuse: the small-block coils without subelements reduce the stopping scale
+// in their factor kernel (last CTA).
+int launch_factor(const Launch& L, bool fuse) {
     if (L.chol) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
     if (L.med) k_factor_med<<<dim3(L.maxW, L.n), kMedFactorThreads, 0, L.s>>>(L.d);
     if (L.seg) {
         const dim3 grid((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n);
-        k_factor_seg<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);
+        k_factor_seg<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d, (int)fuse);
         if (L.groups) k_factor_seg_groups<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d);
         return (int)L.chol + (int)L.med + 1 + (int)L.groups;
     }
@@ -1150,16 +1155,28 @@ int launch_update(const Launch& L) {
     return (int)L.chol + (int)L.med + (int)L.seg;
 }
 
+// The solve's first two reductions for the coils whose kernels do not fuse
+// them (blocks of more than kSegMax elements; subelements for the scale).
+int scale_reduce(const Launch& L) {
+    if (!L.big && !L.groups) return 0;
+    k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 0, 2);
+    return 1;
+}
+int init_reduce(const Launch& L) {
+    if (!L.big) return 0;
+    k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 1, 1);
+    return 1;
+}
+
 // Pointwise, factorisation, right-hand-side norm, initial residual.
 coil_status step_prologue(coil_t* c, const Launch& L) {
     c->launches += launch_pointwise(L);
-    c->launches += launch_factor(L);
-    k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 0, 0);
+    c->launches += launch_factor(L, true);
+    c->launches += scale_reduce(L);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
-    c->launches += launch_init(L);
-    k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 1, 0);
-    c->launches += 2;
+    c->launches += launch_init(L, true);
+    c->launches += init_reduce(L);
     CK(cudaGetLastError(), "step launch");
     return COIL_OK;
 }
@@ -1375,7 +1392,7 @@ coil_status run_step(coil_t* c) {
 // and loop voltages in place of the solve, then the step's epilogue.
 coil_status replay_kernels(coil_t* c, const Launch& L) {
     c->launches += launch_pointwise(L);
-    c->launches += launch_factor(L);
+    c->launches += launch_factor(L, false);              // (the replay does not solve)
     const unsigned nb = (unsigned)std::min<long long>(((long long)c->h.N + 255) / 256, 148LL * 8);
     k_replay_restore<<<dim3(nb, L.n), 256, 0, L.s>>>(L.d);
     c->launches += 1;
@@ -2282,13 +2299,12 @@ coil_status set_device_time(coil_t* c, double t, long long step) {
 // The transposed KKT solve of one reverse step: the same projected PCG with
 // the right-hand side prepared by k_adj_setup (k_pointwise already ran).
 coil_status adjoint_prologue(coil_t* c, const Launch& L) {
-    c->launches += launch_factor(L);
-    k_reduce<<<1, kRedThreads, 0, L.s>>>(L.d, 0, 0);
+    c->launches += launch_factor(L, true);
+    c->launches += scale_reduce(L);
     TRY(gemv(c, L, 0));
     c->launches += launch_near(L, 0);
-    c->launches += launch_init(L);
-    k_reduce<<<1, kRedThreads, 0, L.s>>>(L.d, 1, 0);
-    c->launches += 2;
+    c->launches += launch_init(L, true);
+    c->launches += init_reduce(L);
     CK(cudaGetLastError(), "adjoint solve");
     return COIL_OK;
 }

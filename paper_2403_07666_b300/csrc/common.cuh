@@ -70,7 +70,7 @@ struct CoilDev {
     const int *block_type;        // near-block type per block
     const int *constrained;       // 1 if the block is a transport turn
     const double *near;           // n_types x B x B, FP64 intra-wire blocks of M
-    const float *nearf;           // the same in FP32 (wires of kSegMax < B <= kMedMax)
+    const float *nearf;           // the same in FP32 (wires of B <= kMedMax)
     const void *Mfar;             // N x ld far operator in `precision` (dense format)
     // block-Toeplitz format of a regular solenoid: far operator entries
     // tab32[(t_i - t_j + NT - 1)][c_i][c_j] (FP32, intra-wire entries zero),
@@ -166,7 +166,8 @@ struct CoilDev {
     double *diag;                 // ring [cap][10]
     long long diag_cap;
     Scalars *sc;
-    unsigned *ticket;             // arrival counters of the last-CTA reductions (near, update, step end)
+    unsigned *ticket;             // arrival counters of the last-CTA reductions (near, update, step
+                                  // end, factor, init)
 };
 
 // Smallest of the n exponents e[0..n) over a warp (every lane gets it).

@@ -1036,7 +1036,7 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
     for (int i0 = threadIdx.x; i0 < W; i0 += 8 * st) {
         double v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = i0 + k * st < W ? a[i0 + k * st] : 0.0;
+        for (int k = 0; k < 8; ++k) v[k] = i0 + k * st < W ? __ldcg(a + i0 + k * st) : 0.0;   // from L2
         s0 += ((v[0] + v[1]) + (v[2] + v[3]));
         s1 += ((v[4] + v[5]) + (v[6] + v[7]));
     }
@@ -1075,10 +1075,11 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
 }
 
 // One CTA per coil; skip_seg: coils whose shared-warp kernels reduce their
-// partials themselves (last CTA) are left alone.
+// partials themselves (last CTA) are left alone (2: only those without
+// subelements, whose factor kernel does; the subelement factor does not).
 __global__ void __launch_bounds__(1024) k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg) {
     const CoilDev& c = cds[blockIdx.x];
-    if (skip_seg && c.B <= kSegMax) return;
+    if (skip_seg && c.B <= kSegMax && (skip_seg == 1 || c.n_groups == 0)) return;
     reduce_and_update(c, mode, c.parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W, c.W);
 }
 
@@ -1363,24 +1364,32 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
     return z;
 }
 
+// fuse_init: the last CTA sums the r^T z partials and sets the initial
+// residual and the convergence flag (the k_reduce INIT step).
 __global__ void __launch_bounds__(32 * kSegWarps)
-k_init_seg(const CoilDev* __restrict__ cds) {
+k_init_seg(const CoilDev* __restrict__ cds, int fuse_init) {
     const CoilDev& c = cds[blockIdx.y];
-    if (c.sc->done || c.B > kSegMax) return;
+    const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
+    const int n_cta = (c.W + per_cta - 1) / per_cta;
+    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
-    if (wg * (32 / seg_width(c.B)) >= c.W) return;
-    const Seg s = seg_of(c, wg);
-    const double v = s.ev ? c.qv[s.e] + c.R[s.e] : 0.0;
-    const double y = s.ev ? c.y1[s.e] : 0.0;
-    double rz;
-    const double z = seg_residual_precond(c, s, v, y, true, &rz);
-    if (s.ev) {
-        c.zv[s.e] = z;
-        c.dv[s.e] = -z;
-        c.pf[s.e] = (float)(-z);
+    double head = 0.0;                                  // the lane's term of r^T z (fused reduction)
+    if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
+        const Seg s = seg_of(c, wg);
+        const double v = s.ev ? c.qv[s.e] + c.R[s.e] : 0.0;
+        const double y = s.ev ? c.y1[s.e] : 0.0;
+        double rz;
+        const double z = seg_residual_precond(c, s, v, y, true, &rz, fuse_init != 0);
+        if (s.ev) {
+            c.zv[s.e] = z;
+            c.dv[s.e] = -z;
+            c.pf[s.e] = (float)(-z);
+        }
+        if (fuse_init) head = rz;
+        else if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
     }
-    if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
+    if (fuse_init) fused_reduce(c, head, c.ticket + 4, n_cta, RED_INIT);
 }
 
 // fuse_beta: the last CTA sums the r^T z partials and sets beta and the
@@ -1634,13 +1643,22 @@ __device__ __forceinline__ double inv_pivot(double p) { return rcp_nr(p); }
 // summed in FP64 from the y that are stored; the PCG's residual stays FP64,
 // so the solution does not depend on it.  T = double: the subelement path.
 template <typename T>
-__device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
+__device__ __forceinline__ double factor_seg(const CoilDev& c, const Seg& s) {
     const int B = s.B, kk = s.kk, w = s.w, e = s.e;
     T a[kSegMax];
-    const double* nb = c.near + (size_t)c.block_type[s.wv ? w : 0] * B * B;
+    const size_t nb0 = (size_t)c.block_type[s.wv ? w : 0] * B * B;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // the self blocks' FP32 copy (no per-entry conversion on the FP64 pipe)
+        const float* nb = c.nearf + nb0;
 #pragma unroll
-    for (int j = 0; j < kSegMax; ++j)
-        a[j] = (s.wv && kk < B && j < B) ? (T)nb[kk * B + j] : (T)(j == kk ? 1 : 0);
+        for (int j = 0; j < kSegMax; ++j)
+            a[j] = (s.wv && kk < B && j < B) ? nb[kk * B + j] : (j == kk ? 1.f : 0.f);
+    } else {
+        const double* nb = c.near + nb0;
+#pragma unroll
+        for (int j = 0; j < kSegMax; ++j)
+            a[j] = (s.wv && kk < B && j < B) ? nb[kk * B + j] : (j == kk ? 1.0 : 0.0);
+    }
     if (s.ev) {
         const T g = (T)(c.dt * c.G[e]);
 #pragma unroll
@@ -1668,7 +1686,10 @@ __device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
             }
         }
     }
-    if (bad && s.wv && kk == 0) atomicExch(&c.sc->nonpd, 1);
+    if (bad && s.wv && kk == 0) {
+        atomicExch(&c.sc->nonpd, 1);
+        __threadfence();                       // before this CTA's arrival on a fused reduction
+    }
     // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
     T yt = 0;
 #pragma unroll
@@ -1687,23 +1708,26 @@ __device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
     if constexpr (sizeof(T) == sizeof(double)) {
         if (c.n_groups) {
             factor_groups(c, s, a, y, isg, con, x0);
-            return;
+            return 0.0;
         }
     }
-    // P_w row kk, stored; R^T P_w R
+    // P_w row kk, stored (its entries are FP32 values: the subtraction runs in
+    // T = float); R^T P_w R in FP32 (it only scales the stopping test)
     const double R = s.ev ? c.R[e] : 0.0;
-    double pr = 0.0;
+    const float Rf = (float)R, yf = (float)y, yis = (float)(y * isg);
+    float pr0 = 0.f, pr1 = 0.f;
 #pragma unroll
     for (int j = 0; j < kSegMax; ++j) {
         if (j < B) {
-            const T yj = __shfl_sync(0xffffffffu, (T)y, s.base + j);
-            const double Rj = __shfl_sync(0xffffffffu, R, s.base + j);
-            const double pj = con ? (double)(a[j] - (T)(y * isg) * yj) : (double)a[j];
-            if (s.ev) c.Lf[((size_t)w * B + kk) * B + j] = (float)pj;
-            pr += pj * Rj;
+            const float yj = __shfl_sync(0xffffffffu, yf, s.base + j);
+            const float Rj = __shfl_sync(0xffffffffu, Rf, s.base + j);
+            const float pj = con ? (float)(a[j] - (T)yis * (T)yj) : (float)a[j];
+            if (s.ev) c.Lf[((size_t)w * B + kk) * B + j] = pj;
+            if (j & 1) pr1 = fmaf(pj, Rj, pr1);
+            else pr0 = fmaf(pj, Rj, pr0);
         }
     }
-    const double rn = seg_sum(s.ev ? R * pr : 0.0, s.Bp);
+    const double rn = seg_sum(s.ev ? R * (double)(pr0 + pr1) : 0.0, s.Bp);
     const double cw = s.wv ? c.cw[w] : 0.0;
     // warm start moved onto this step's constraint
     const double sx = seg_sum(x0, s.Bp);
@@ -1713,7 +1737,9 @@ __device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
         c.x[e] = xe;
         c.pf[e] = (float)xe;
     }
-    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+    const double scale = rn + (con ? cw * cw * isg : 0.0);
+    if (kk == 0 && s.wv) c.parts[3 * (size_t)c.W + w] = scale;
+    return kk == 0 && s.wv ? scale : 0.0;
 }
 
 // k_factor for blocks of at most 16 elements.  Lane kk holds row kk of
@@ -1730,22 +1756,24 @@ __device__ __forceinline__ void factor_seg(const CoilDev& c, const Seg& s) {
 // transport part, in FP64), launched as a kernel of its own so that its
 // registers do not weigh on the plain path (the inverse only builds the
 // preconditioner, which FP32 serves; see factor_seg).
-template <bool GROUPS>
-__device__ __forceinline__ void factor_seg_kernel(const CoilDev* __restrict__ cds) {
+// fuse_scale (coils without subelements): the last CTA sums the scale
+// partials and starts the solve's scalars (the k_reduce SCALE step).
+__global__ void __launch_bounds__(32 * kSegWarps) k_factor_seg(const CoilDev* __restrict__ cds, int fuse_scale) {
     const CoilDev& c = cds[blockIdx.y];
-    if (c.B > kSegMax || (c.n_groups != 0) != GROUPS) return;
-    const int warp = threadIdx.x >> 5;
-    const int wg = blockIdx.x * kSegWarps + warp;
-    if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
-    const Seg s = seg_of(c, wg);
-    if (GROUPS) factor_seg<double>(c, s);
-    else factor_seg<float>(c, s);
-}
-__global__ void __launch_bounds__(32 * kSegWarps) k_factor_seg(const CoilDev* __restrict__ cds) {
-    factor_seg_kernel<false>(cds);
+    const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
+    const int n_cta = (c.W + per_cta - 1) / per_cta;
+    if (c.B > kSegMax || c.n_groups != 0 || (int)blockIdx.x >= n_cta) return;
+    const int wg = blockIdx.x * kSegWarps + (threadIdx.x >> 5);
+    double head = 0.0;                                  // the wire's scale term on its head lane
+    if (wg * (32 / seg_width(c.B)) < c.W) head = factor_seg<float>(c, seg_of(c, wg));   // warp-uniform
+    if (fuse_scale) fused_reduce(c, head, c.ticket + 3, n_cta, RED_SCALE);
 }
 __global__ void __launch_bounds__(32 * kSegWarps) k_factor_seg_groups(const CoilDev* __restrict__ cds) {
-    factor_seg_kernel<true>(cds);
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.B > kSegMax || c.n_groups == 0) return;
+    const int wg = blockIdx.x * kSegWarps + (threadIdx.x >> 5);
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform; no CTA barrier below
+    factor_seg<double>(c, seg_of(c, wg));
 }
 
 // The PCG loop's condition as a kernel of its own (coils whose update kernel
@@ -1937,85 +1965,124 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
     if (threadIdx.x == 0) c.partT[i] = um;
 }
 
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
 // The step's diagnostic record, then t += dt.  kStepEndCtas CTAs per coil
 // (grid row = coil) each reduce a slice of the per-wire values and of the
 // thermal columns into partials (parts row 7, free once the solve is done);
 // the CTA that arrives last on the coil's third counter (which it resets)
 // combines them in a fixed order and writes the record.  On B300 one CTA's
-// FP64 pipe alone took ~28 us for the 96,000-element coil.
+// FP64 pipe alone took ~28 us for the 96,000-element coil, and a warp issues
+// one FP64 instruction per 64 cycles: the reductions are spread over warps.
+
 __global__ void __launch_bounds__(kStepEndThreads) k_step_end(const CoilDev* __restrict__ cds) {
+    static_assert(kStepEndCtas <= 32 && kStepEndThreads >= 6 * 32, "one warp per quantity");
+    constexpr int NT = kStepEndThreads;
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->status != ST_OK) return;
-    __shared__ double sh[32];
+    // three sums (Joule power, loop voltage, moment) in FP64; three maxima of
+    // non-negative values (|J|/Jc, rho/rho_n, u = T^4) as the maxima of their
+    // bit patterns, exact and off the FP64 pipe; each reduced by a warp of its own
+    __shared__ double ssum[3][NT];
+    __shared__ unsigned long long smax[3][NT];
+    __shared__ double rsum[3];
+    __shared__ unsigned long long rmax[3];
     __shared__ int is_last;
     const double* parts = c.parts;
     const size_t W = c.W;
-    const int nb = gridDim.x, tid = threadIdx.x;
+    const int nb = gridDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int stride = nb * blockDim.x;
-    double pj = 0.0, V = 0.0, m = 0.0, jr = 0.0, rh = 0.0;
+    double pj = 0.0, V = 0.0, m = 0.0;
+    unsigned long long jr = 0, rh = 0, um = 0;
+    auto bits = [](double v) { return (unsigned long long)__double_as_longlong(v); };
     for (int w = blockIdx.x * blockDim.x + tid; w < c.W; w += stride) {
         pj += parts[0 * W + w];
-        jr = fmax(jr, parts[1 * W + w]);
-        rh = fmax(rh, parts[2 * W + w]);
+        jr = max(jr, bits(parts[1 * W + w]));
+        rh = max(rh, bits(parts[2 * W + w]));
         V += parts[5 * W + w];
         m += parts[6 * W + w];
     }
-    double um = 0.0;
     if (c.has_grid) {
         if (c.thermal) {
-            for (int i = blockIdx.x * blockDim.x + tid; i < c.Gr; i += stride) um = fmax(um, c.partT[i]);
+            for (int i = blockIdx.x * blockDim.x + tid; i < c.Gr; i += stride) um = max(um, bits(c.partT[i]));
         } else {
-            for (int g = blockIdx.x * blockDim.x + tid; g < c.Gr * c.Gz; g += stride) um = fmax(um, c.uT[g]);
+            for (int g = blockIdx.x * blockDim.x + tid; g < c.Gr * c.Gz; g += stride) um = max(um, bits(c.uT[g]));
         }
     }
-    pj = block_reduce_sum(pj, sh);
-    V = block_reduce_sum(V, sh);
-    m = block_reduce_sum(m, sh);
-    jr = block_reduce_max(jr, sh);
-    rh = block_reduce_max(rh, sh);
-    um = block_reduce_max(um, sh);
+    ssum[0][tid] = pj;
+    ssum[1][tid] = V;
+    ssum[2][tid] = m;
+    smax[0][tid] = jr;
+    smax[1][tid] = rh;
+    smax[2][tid] = um;
+    __syncthreads();
+    if (wid < 3) {
+        double v = 0.0;
+        for (int k = lane; k < NT; k += 32) v += ssum[wid][k];
+        v = warp_sum(v);
+        if (lane == 0) rsum[wid] = v;
+    } else if (wid < 6) {
+        unsigned long long v = 0;
+        for (int k = lane; k < NT; k += 32) v = max(v, smax[wid - 3][k]);
+        v = warp_max_u64(v);
+        if (lane == 0) rmax[wid - 3] = v;
+    }
+    __syncthreads();
     double* cp = c.parts + 7 * W;                     // 6 partials per CTA
     if (tid == 0) {
-        cp[6 * blockIdx.x + 0] = pj;
-        cp[6 * blockIdx.x + 1] = V;
-        cp[6 * blockIdx.x + 2] = m;
-        cp[6 * blockIdx.x + 3] = jr;
-        cp[6 * blockIdx.x + 4] = rh;
-        cp[6 * blockIdx.x + 5] = um;
+        cp[6 * blockIdx.x + 0] = rsum[0];
+        cp[6 * blockIdx.x + 1] = rsum[1];
+        cp[6 * blockIdx.x + 2] = rsum[2];
+        cp[6 * blockIdx.x + 3] = __longlong_as_double((long long)rmax[0]);
+        cp[6 * blockIdx.x + 4] = __longlong_as_double((long long)rmax[1]);
+        cp[6 * blockIdx.x + 5] = __longlong_as_double((long long)rmax[2]);
         unsigned prev;
         asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(prev) : "l"(c.ticket + 2) : "memory");
         is_last = prev == (unsigned)nb - 1u;
         if (is_last) c.ticket[2] = 0u;
     }
     __syncthreads();
-    if (!is_last || tid != 0) return;
-    pj = V = m = jr = rh = um = 0.0;
-    for (int k = 0; k < nb; ++k) {
-        pj += cp[6 * k + 0];
-        V += cp[6 * k + 1];
-        m += cp[6 * k + 2];
-        jr = fmax(jr, cp[6 * k + 3]);
-        rh = fmax(rh, cp[6 * k + 4]);
-        um = fmax(um, cp[6 * k + 5]);
+    if (!is_last) return;
+    // the last CTA: the CTAs' partials (read from L2), one quantity per warp,
+    // in a fixed order
+    if (wid < 3) {
+        double v = lane < nb ? __ldcg(cp + 6 * lane + wid) : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) rsum[wid] = v;
+    } else if (wid < 6) {
+        unsigned long long v = lane < nb ? bits(__ldcg(cp + 6 * lane + wid)) : 0ull;
+        v = warp_max_u64(v);
+        if (lane == 0) rmax[wid - 3] = v;
     }
+    __syncthreads();
     Scalars* sc = c.sc;
-    double t1 = sc->t + c.dt;
     double* rec = c.diag + (size_t)(sc->step % c.diag_cap) * 10;
-    rec[0] = t1;
-    rec[1] = sc->It1;
-    rec[2] = V;
-    rec[3] = m;
-    rec[4] = pj;
-    rec[5] = c.has_grid ? sqrt(sqrt(um)) : c.T_bath;
-    rec[6] = jr;
-    rec[7] = rh;
-    if (c.rec_mode != 2) {                        // a replayed step keeps the solve's diagnostics
+    if (tid == 0) {
+        const double um_max = __longlong_as_double((long long)rmax[2]);
+        rec[0] = sc->t + c.dt;
+        rec[1] = sc->It1;
+        rec[2] = rsum[1];
+        rec[3] = rsum[2];
+        rec[4] = rsum[0];
+        rec[5] = c.has_grid ? sqrt(sqrt(um_max)) : c.T_bath;
+        rec[6] = __longlong_as_double((long long)rmax[0]);
+        rec[7] = __longlong_as_double((long long)rmax[1]);
+    } else if (tid == 32 && c.rec_mode != 2) {        // a replayed step keeps the solve's diagnostics
         rec[8] = (double)sc->iter;
         sc->last_resid = sc->scale2 > 0.0 ? sqrt(fmax(sc->rz, 0.0) / sc->scale2) : 0.0;
         rec[9] = sc->last_resid;
     }
-    sc->t = t1;
-    sc->step += 1;
+    __syncthreads();
+    if (tid == 0) {
+        sc->t = sc->t + c.dt;
+        sc->step += 1;
+    }
 }
 
 // J, B_r, B_z, T of the current state into element-order buffers.
