@@ -173,7 +173,13 @@ struct CoilDev {
 // Smallest of the n exponents e[0..n) over a warp (every lane gets it).
 __device__ __forceinline__ int warp_min_exponent(const int* e, int n, int lane) {
     int m = 1 << 30;
-    for (int t = lane; t < n; t += 32) m = min(m, e[t]);
+    for (int t0 = lane; t0 < n; t0 += 128) {           // four loads in flight per lane
+        int v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = t0 + 32 * k < n ? e[t0 + 32 * k] : (1 << 30);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m = min(m, v[k]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
     return m;

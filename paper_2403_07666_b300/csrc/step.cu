@@ -1181,7 +1181,7 @@ __device__ __forceinline__ void kahan_add(float v, float& s, float& comp) {
     comp = (t - s) - y;
     s = t;
 }
-__device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv) {
+__device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv, int2 rg) {
     const int t = e / c.C, cc = e - t * c.C;
     if (c.tc_mode == 1) {
         // one-fill apply: the segments of e's channel tile, then of its k block
@@ -1209,8 +1209,7 @@ __device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv
         for (; k < r2.y; ++k) kahan_add(p2[(size_t)c.tc_segs2[r2.x + k] * t2], s, comp);
         return ((double)s - (double)comp) * inv;
     }
-    const int2 rg = c.tc_range[cc / kTcTileRows];
-    const size_t tile = (size_t)c.NT * kTcTileRows;
+    const size_t tile = (size_t)c.NT * kTcTileRows;      // (rg = tc_range[cc / kTcTileRows])
     const float* p = c.tc_part + (size_t)rg.x * tile + (size_t)t * kTcTileRows + (cc % kTcTileRows);
     // the loads of up to 24 tiles issued before their sums (one round trip for
     // the usual 18 CTAs per tile), added in tile order
@@ -1234,17 +1233,23 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
     const CoilDev& c = cds[blockIdx.y];
     const int per_cta = (int)(blockDim.x >> 5) * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
-    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
+    if (c.B > kSegMax || (int)blockIdx.x >= n_cta) return;
     const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const bool warp_on = wg * (32 / seg_width(c.B)) < c.W;   // warp-uniform
+    const Seg s = seg_of(c, wg);
+    // what does not depend on the solve's progress is loaded together with its
+    // done flag: one round trip instead of several in sequence
+    const double* p = which == 0 ? c.x : c.dv;
+    const double pv = s.ev ? p[s.e] : 0.0;
+    const double ge = s.ev ? c.G[s.e] : 0.0;
+    const int bt = c.block_type[s.wv ? s.w : 0];
+    const int xmin = far_tiles ? warp_min_exponent(c.tc_pexp, c.NT, threadIdx.x & 31) : 0;
+    const int2 rg = (far_tiles && s.ev && c.tc_mode != 1) ? c.tc_range[(s.e % c.C) / kTcTileRows] : make_int2(0, 0);
+    if (c.sc->done) return;                             // CTA-uniform
     double head = 0.0;                                  // the lane's term of p^T q (fused reduction)
-    if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
-        const Seg s = seg_of(c, wg);
-        const double* p = which == 0 ? c.x : c.dv;
-        const double pv = s.ev ? p[s.e] : 0.0;
-        const double ge = s.ev ? c.G[s.e] : 0.0;
-        const double inv = far_tiles ? ldexp(1.0, -(c.tc_exT + warp_min_exponent(c.tc_pexp, c.NT, threadIdx.x & 31)))
-                                     : 0.0;
-        const double* nb = c.near + (size_t)c.block_type[s.wv ? s.w : 0] * s.B * s.B;
+    if (warp_on) {
+        const double inv = far_tiles ? ldexp(1.0, -(c.tc_exT + xmin)) : 0.0;
+        const double* nb = c.near + (size_t)bt * s.B * s.B;
         const int row = s.kk < s.B ? s.kk : 0;
         double acc = 0.0;
         if (s.B == kSegMax) {
@@ -1263,7 +1268,7 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
         double dot = 0.0;
         if (s.ev) {
             acc += c.dt * ge * pv;
-            double qe = (far_tiles ? tc_far_sum(c, s.e, inv) : c.qv[s.e]) + acc;
+            double qe = (far_tiles ? tc_far_sum(c, s.e, inv, rg) : c.qv[s.e]) + acc;
             c.qv[s.e] = qe;
             dot = pv * qe;
         }
@@ -1277,12 +1282,32 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
     if (fuse_alpha) fused_reduce(c, head, c.ticket, n_cta, RED_ALPHA);
 }
 
+// A lane's per-wire inputs of the preconditioner, loaded ahead of the values
+// they act on: the wire's constraint flag, 1 / sigma and (16-element wires)
+// row kk of P_w.
+struct SegRow {
+    int con;
+    double isg;
+    float4 p[kSegMax / 4];
+};
+__device__ __forceinline__ SegRow seg_row_load(const CoilDev& c, const Seg& s) {
+    SegRow r;
+    r.con = s.wv ? c.constrained[s.w] : 0;
+    r.isg = s.wv ? c.isigma[s.w] : 0.0;
+    if (s.B == kSegMax) {
+        const float4* P = reinterpret_cast<const float4*>(c.Lf + ((size_t)(s.wv ? s.w : 0) * s.B + s.kk) * s.B);
+#pragma unroll
+        for (int q = 0; q < kSegMax / 4; ++q) r.p[q] = P[q];
+    }
+    return r;
+}
+
 // Projected residual update and preconditioner of the segment's wire: v is
 // the raw residual on entry; writes res, z and returns z (in rz the wire's
 // r^T z, or with lane_rz the lane's own term of it).
 __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const Seg& s, double v, double y,
-                                                        bool first, double* rz, bool lane_rz = false) {
-    const int con = s.wv ? c.constrained[s.w] : 0;
+                                                        bool first, double* rz, bool lane_rz, const SegRow& pre) {
+    const int con = pre.con;
     if (c.n_groups) {
         // subelements: remove Q v, v = (Y S^-1)^T r the subelement voltage
         // estimates, accumulated in ugrp
@@ -1304,7 +1329,7 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
         }
         if (con && s.ev) v -= mine;
     } else {
-        const double isg = s.wv ? c.isigma[s.w] : 0.0;
+        const double isg = pre.isg;
         // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
         const double u = seg_sum(y * v, s.Bp) * isg;
         if (con && s.ev) v -= u;
@@ -1324,10 +1349,8 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
     const float vf = (float)v;
     float z0 = 0.f, z1 = 0.f;
     if (s.B == kSegMax) {
-        // 16-element wires: the row as four 16-byte loads, all in flight at once
-        float4 pr[kSegMax / 4];
-#pragma unroll
-        for (int q = 0; q < kSegMax / 4; ++q) pr[q] = reinterpret_cast<const float4*>(P)[q];
+        // 16-element wires: the row as four 16-byte loads (made ahead, see seg_row_load)
+        const float4* pr = pre.p;
 #pragma unroll
         for (int q = 0; q < kSegMax / 4; ++q) {
             z0 = fmaf(pr[q].x, __shfl_sync(0xffffffffu, vf, s.base + 4 * q), z0);
@@ -1357,7 +1380,7 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
         if (con) z -= corr;
     } else {
         const double sz = seg_sum(z, s.Bp);            // all lanes: the shuffles span the warp
-        if (con) z -= y * sz * c.isigma[s.w];
+        if (con) z -= y * sz * pre.isg;
     }
     *rz = s.ev ? v * z : 0.0;
     if (!lane_rz) *rz = seg_sum(*rz, s.Bp);
@@ -1380,7 +1403,7 @@ k_init_seg(const CoilDev* __restrict__ cds, int fuse_init) {
         const double v = s.ev ? c.qv[s.e] + c.R[s.e] : 0.0;
         const double y = s.ev ? c.y1[s.e] : 0.0;
         double rz;
-        const double z = seg_residual_precond(c, s, v, y, true, &rz, fuse_init != 0);
+        const double z = seg_residual_precond(c, s, v, y, true, &rz, fuse_init != 0, seg_row_load(c, s));
         if (s.ev) {
             c.zv[s.e] = z;
             c.dv[s.e] = -z;
@@ -1401,24 +1424,39 @@ k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditiona
     const CoilDev& c = cds[blockIdx.y];
     const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
-    if (c.sc->done || c.B > kSegMax || (int)blockIdx.x >= n_cta) {
+    if (c.B > kSegMax || (int)blockIdx.x >= n_cta) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) loop_condition(c, cond);
         return;
     }
     const int warp = threadIdx.x >> 5;
     const int wg = blockIdx.x * kSegWarps + warp;
+    const bool warp_on = wg * (32 / seg_width(c.B)) < c.W;   // warp-uniform
+    const Seg s = seg_of(c, wg);
+    // what does not depend on the solve's progress is loaded together with its
+    // done flag and alpha: one round trip instead of several in sequence
+    double xv = 0.0, dv = 0.0, rv = 0.0, qv = 0.0, y = 0.0;
+    if (s.ev) {
+        xv = c.x[s.e];
+        dv = c.dv[s.e];
+        rv = c.res[s.e];
+        qv = c.qv[s.e];
+        y = c.y1[s.e];
+    }
+    const SegRow pre = seg_row_load(c, s);
+    const double alpha = c.sc->alpha;
+    if (c.sc->done) {                                   // CTA-uniform
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) loop_condition(c, cond);
+        return;
+    }
     double head = 0.0;                                  // the lane's term of r^T z (fused reduction)
-    if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
-        const Seg s = seg_of(c, wg);
-        const double alpha = c.sc->alpha;
-        double v = 0.0, y = 0.0;
+    if (warp_on) {
+        double v = 0.0;
         if (s.ev) {
-            c.x[s.e] += alpha * c.dv[s.e];
-            v = c.res[s.e] + alpha * c.qv[s.e];
-            y = c.y1[s.e];
+            c.x[s.e] = xv + alpha * dv;
+            v = rv + alpha * qv;
         }
         double rz;
-        const double z = seg_residual_precond(c, s, v, y, false, &rz, fuse_beta != 0);
+        const double z = seg_residual_precond(c, s, v, y, false, &rz, fuse_beta != 0, pre);
         if (s.ev) c.zv[s.e] = z;
         if (fuse_beta) head = rz;                   // the lane's term: only the total is needed
         else if (s.kk == 0 && s.wv) c.parts[4 * (size_t)c.W + s.w] = rz;
