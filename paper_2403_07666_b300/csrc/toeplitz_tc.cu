@@ -1047,6 +1047,47 @@ __device__ __forceinline__ void tc_split_row(const CoilDev& c, const TcShape& sh
                                              int* __restrict__ pexp, int dir, const int t) {
     if (c.sc->done) return;
     float* row = c.pf + (size_t)t * sh.C;
+    constexpr int kReg = 8;                      // entries per thread kept in registers
+    if (sh.Cp <= kReg * (int)blockDim.x) {
+        // the row in registers: one pass over memory (d, then its maximum and split)
+        const bool form = dir && c.sc->iter > 0;  // the first iteration's direction is k_init's
+        const double beta = form ? c.sc->beta : 0.0;
+        const size_t e0 = (size_t)t * sh.C;
+        float v[kReg];
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < kReg; ++k) {
+            const int cc = threadIdx.x + k * (int)blockDim.x;
+            float f = 0.f;
+            if (cc < sh.C) {
+                if (form) {
+                    const double d = -c.zv[e0 + cc] + beta * c.dv[e0 + cc];
+                    c.dv[e0 + cc] = d;
+                    f = (float)d;
+                    row[cc] = f;
+                } else {
+                    f = row[cc];
+                }
+            }
+            v[k] = f;
+            m = fmaxf(m, fabsf(f));
+        }
+        const int x = tc_exponent((double)block_max_f(m));
+        if (threadIdx.x == 0) pexp[t] = x;
+        const float s = ldexpf(1.f, x);
+#pragma unroll
+        for (int k = 0; k < kReg; ++k) {
+            const int cc = threadIdx.x + k * (int)blockDim.x;
+            if (cc < sh.Cp) {
+                const float sv = cc < sh.C ? v[k] * s : 0.f;
+                const __half hi = __float2half_rn(sv);
+                const int idx = (((cc >> 3) * 2) * sh.NT + t) * 8 + (cc & 7);
+                p16[idx] = hi;
+                p16[idx + 8 * sh.NT] = __float2half_rn(sv - __half2float(hi));
+            }
+        }
+        return;
+    }
     if (dir && c.sc->iter > 0) {                 // the first iteration's direction is k_init's
         const double beta = c.sc->beta;
         const size_t e0 = (size_t)t * sh.C;
