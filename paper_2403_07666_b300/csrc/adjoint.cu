@@ -234,6 +234,73 @@ __device__ EJD ej_with_derivatives_f(const CoilDev& c, int fil, float aJ, float 
 // Per wire (one warp): reverse of the pointwise kernel and of the constraint.
 // wP = dL/dP of the step's Joule power P = sum q 2 pi r a (its diagnostic
 // record), which adds wP 2 pi r a to lam_q of every element.
+// The mixed form's element of k_adj_pointwise: its forward chain is FP32 from
+// the field on (J = I / a included), so are the Jacobian's coefficients,
+// formed from the same FP32 geometry without FP64 divisions (B300's FP64 pipe
+// gives a warp one instruction per 64 cycles); the adjoint variables and every
+// accumulation stay FP64.
+__device__ __forceinline__ void adj_element_f(const CoilDev& c, const AdjBufs& ab, int e, double Ba0, double wP,
+                                              double nu_term, double& gn, double& gce) {
+    const float4 gf = c.geo_f[e];                      // 2 pi r, 1 / (2 pi r), area, 1 / area
+    const int fil = c.mat[e];
+    const float Jf = (float)c.I[e] * gf.w;             // the forward chain's J
+    float br = 0.0f, bz = 0.0f, tf = c.f_T_bath;
+    double u = 0.0;
+    int g = -1;
+    if (c.has_grid) {
+        field_at_f(c, e, Ba0, &br, &bz);
+        g = c.elem_grid[e];
+        u = c.uT[g];
+        tf = sqrtf(sqrtf((float)u));
+    }
+    const float bm = sqrtf(br * br + bz * bz);
+    JcD jd = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (fil) jd = jc_with_derivatives_f(c, bm, tf, strain_power_f(c, e, Jf, bz), (float)c.jc_factor[e]);
+    const EJD ej = ej_with_derivatives_f(c, fil, fabsf(Jf), (float)jd.Jc);
+    const float rn = c.f_rho_n, nf = c.f_nexp, jc = (float)jd.Jc;
+    const float A1 = (float)ej.A1, A2 = (float)ej.A2, lnx = (float)ej.lnx;
+    const float Kg = gf.x * rn * gf.w;                 // 2 pi r rho_n / a
+    const bool act = fil && jc > 0.0f;
+    const float cG = (act && Jf != 0.0f) ? Kg * A2 * (nf - 1.0f) / Jf : 0.0f;   // dG/dJ
+    const double mu = c.x[e];
+    const double lamG = -c.dt * mu * ab.xk[e];
+    const double lamR = -mu;
+    const double lamq = ((c.has_grid && c.thermal) ? ab.lamQ[g] : 0.0) + wP * (double)(gf.x * gf.z);
+    const double lamE = (double)gf.x * lamR + lamq * (double)Jf;
+    const double lamJ = lamq * (double)(rn * (float)ej.frac * Jf) + lamE * (double)(rn * (float)ej.dfac) +
+                        lamG * (double)cG;
+    double lamI = ab.lamI_next[e] + lamJ * (double)gf.w + nu_term;
+    if (act) {
+        const float ijc = 1.0f / jc;
+        const double lamJc = lamE * (double)(-rn * Jf * nf * A1 * ijc) + lamG * (double)(-Kg * A2 * nf * ijc);
+        gn += lamE * (double)(rn * Jf * A1 * lnx) + lamG * (double)(Kg * (A2 * lnx + A1));
+        ab.g_f[e] += lamJc * jd.df;
+        gce += lamJc * jd.dCe;
+        const double lamBm = lamJc * jd.dBm;
+        const double lamT = lamJc * jd.dT;
+        if (c.has_grid && c.thermal) ab.lamU[g] += lamT * (double)(tf / (4.0f * (float)u));
+        // lam_B over 2 pi r, the scale of the stencil that k_adj_stencil_t transposes
+        const double sB = bm > 0.0f ? lamBm * (double)(gf.y / bm) : 0.0;
+        double lbz = sB * (double)bz;
+        ab.lamBr[e] = sB * (double)br;
+        if (c.lorentz) {
+            // Lorentz hoop strain eps = eps0 + r J B_z / Y: d|eps|^p/d eps = p |eps|^p / eps
+            const double r = c.r[e], J = (double)Jf;
+            const double eps = element_strain(c, e, r, J, (double)bz);
+            if (eps != 0.0) {
+                const double lamEps = lamJc * jd.dep * c.p_eps * pow(fabs(eps), c.p_eps) / eps;
+                lamI += lamEps * r * (double)bz * c.inv_Y * (double)gf.w;
+                lbz += lamEps * r * J * c.inv_Y * (double)gf.y;
+            }
+        }
+        ab.lamBz[e] = lbz;
+    } else {
+        ab.lamBr[e] = 0.0;
+        ab.lamBz[e] = 0.0;
+    }
+    ab.lamI[e] = lamI;
+}
+
 __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, double wP) {
     const CoilDev& c = cds[0];
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -241,12 +308,17 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, dou
     if (w >= c.W) return;
     double dt = c.dt, n = c.nexp, rho_n = c.rho_n;
     double Ba0 = c.sc->Ba0;
-    double nu_term = c.constrained[w] ? c.uw[w] / dt : 0.0;   // -lam_c / dt with lam_c = nu = -u
-    double gn = 0.0, gce = 0.0;
     // the mixed form's forward chain is FP32 from the field on: its Jacobians too
     const bool f32 = c.precision != PREC_FP64;
+    // -lam_c / dt with lam_c = nu = -u
+    double nu_term = c.constrained[w] ? (f32 ? c.uw[w] * c.inv_dt : c.uw[w] / dt) : 0.0;
+    double gn = 0.0, gce = 0.0;
     for (int k = lane; k < c.B; k += 32) {
         int e = w * c.B + k;
+        if (f32) {
+            adj_element_f(c, ab, e, Ba0, wP, nu_term, gn, gce);
+            continue;
+        }
         double r = c.r[e], a = c.area[e];
         double Br = 0.0, Bz = 0.0, T = c.T_bath, u = 0.0;
         int g = -1;
@@ -255,33 +327,15 @@ __global__ void k_adj_pointwise(const CoilDev* __restrict__ cds, AdjBufs ab, dou
         double I = c.I[e];
         double J = I / a;
         double Bm;
-        EJD ej;
-        if (f32) {
-            float br = 0.0f, bz = 0.0f, tf = c.f_T_bath;
-            if (c.has_grid) {
-                field_at_f(c, e, Ba0, &br, &bz);
-                g = c.elem_grid[e];
-                u = c.uT[g];
-                tf = sqrtf(sqrtf((float)u));
-            }
-            const float bm = sqrtf(br * br + bz * bz);
-            Br = br;
-            Bz = bz;
-            Bm = bm;
-            T = tf;
-            if (fil) jd = jc_with_derivatives_f(c, bm, tf, strain_power_f(c, e, J, bz), (float)c.jc_factor[e]);
-            ej = ej_with_derivatives_f(c, fil, (float)fabs(J), (float)jd.Jc);
-        } else {
-            if (c.has_grid) {
-                field_at(c, e, Ba0, &Br, &Bz);
-                g = c.elem_grid[e];
-                u = c.uT[g];
-                T = sqrt(sqrt(u));
-            }
-            Bm = sqrt(Br * Br + Bz * Bz);
-            if (fil) jd = jc_with_derivatives(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]);
-            ej = ej_with_derivatives(c, fil, J, jd.Jc);
+        if (c.has_grid) {
+            field_at(c, e, Ba0, &Br, &Bz);
+            g = c.elem_grid[e];
+            u = c.uT[g];
+            T = sqrt(sqrt(u));
         }
+        Bm = sqrt(Br * Br + Bz * Bz);
+        if (fil) jd = jc_with_derivatives(c, Bm, T, strain_power(c, e, r, J, Bz), c.jc_factor[e]);
+        const EJD ej = ej_with_derivatives(c, fil, J, jd.Jc);
         double E = rho_n * ej.frac * J;
         double Kg = 2.0 * kPi * r * rho_n / a;
         double mu = c.x[e];
@@ -338,22 +392,27 @@ __global__ void k_adj_stencil_t(const CoilDev* __restrict__ cds, AdjBufs ab) {
     for (int e2 = blockIdx.x * blockDim.x + threadIdx.x; e2 < c.N; e2 += gridDim.x * blockDim.x) {
         int g2 = c.elem_grid[e2];
         int iz2 = g2 / Gr, ir2 = g2 - iz2 * Gr;
+        // the stencils of the two cells on either side along each axis: every
+        // load in bounds (clamped cell, tap 0 when unused) and issued at once,
+        // unused taps not added; a zero weight adds an exact zero (lam_B is finite)
         double acc = 0.0;
-        for (int i = max(ir2 - 2, 0); i <= min(ir2 + 2, Gr - 1); ++i) {
-            int k = ir2 - c.sr_j0[i];
-            if (k < 0 || k > 2) continue;
-            double wk = c.sr_w[3 * i + k];
-            if (wk == 0.0) continue;
-            int e = c.grid_elem[iz2 * Gr + i];
-            acc += wk * ab.lamBz[e];                     // lam_B already over 2 pi r
+#pragma unroll
+        for (int d = -2; d <= 2; ++d) {
+            const int i = min(max(ir2 + d, 0), Gr - 1);
+            const int k = ir2 - c.sr_j0[i];
+            const bool use = i == ir2 + d && k >= 0 && k <= 2;
+            const double wk = c.sr_w[3 * i + (use ? k : 0)];
+            const double lb = ab.lamBz[c.grid_elem[iz2 * Gr + i]];   // lam_B already over 2 pi r
+            if (use) acc += wk * lb;
         }
-        for (int j = max(iz2 - 2, 0); j <= min(iz2 + 2, Gz - 1); ++j) {
-            int k = iz2 - c.sz_j0[j];
-            if (k < 0 || k > 2) continue;
-            double wk = c.sz_w[3 * j + k];
-            if (wk == 0.0) continue;
-            int e = c.grid_elem[j * Gr + ir2];
-            acc -= wk * ab.lamBr[e];
+#pragma unroll
+        for (int d = -2; d <= 2; ++d) {
+            const int j = min(max(iz2 + d, 0), Gz - 1);
+            const int k = iz2 - c.sz_j0[j];
+            const bool use = j == iz2 + d && k >= 0 && k <= 2;
+            const double wk = c.sz_w[3 * j + (use ? k : 0)];
+            const double lb = ab.lamBr[c.grid_elem[j * Gr + ir2]];
+            if (use) acc -= wk * lb;
         }
         c.dv[e2] = acc;
         c.pf[e2] = (float)acc;

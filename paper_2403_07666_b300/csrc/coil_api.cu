@@ -752,7 +752,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.xprev, N, "previous Idot"));
     TRY(dalloc(c, &h.xprev2, N, "Idot before the previous"));
     h.extrap = 1;
-    h.rec_x = h.rec_res = h.rec_uw = nullptr;
+    h.rec_x = h.rec_res = h.rec_uw = h.rec_u = nullptr;
     h.rec_step0 = 0;
     h.rec_mode = 0;
     TRY(dalloc(c, &h.res, N, "res"));
@@ -1391,8 +1391,9 @@ coil_status run_step(coil_t* c) {
 // finalisation reads) as in the step, then the recorded solution, residual
 // and loop voltages in place of the solve, then the step's epilogue.
 coil_status replay_kernels(coil_t* c, const Launch& L) {
+    // no factorisation: the replay does not solve, and its finalisation takes
+    // the recorded voltages in place of forming them from y and sigma
     c->launches += launch_pointwise(L);
-    c->launches += launch_factor(L, false);              // (the replay does not solve)
     const unsigned nb = (unsigned)std::min<long long>(((long long)c->h.N + 255) / 256, 148LL * 8);
     k_replay_restore<<<dim3(nb, L.n), 256, 0, L.s>>>(L.d);
     c->launches += 1;
@@ -2425,14 +2426,15 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
     // without solving them; left out (the recomputation then solves) when they
     // would take more than a quarter of the free device memory or 4 GiB
     bool replay = false;
-    double *rx = nullptr, *rres = nullptr, *ruw = nullptr;
+    double *rx = nullptr, *rres = nullptr, *ruw = nullptr, *ru = nullptr;
     if (nseg > 1) {
         size_t free_b = 0, total_b = 0;
-        const size_t want = (size_t)n_steps * (2 * N + W) * sizeof(double);
+        const size_t want = (size_t)n_steps * (2 * N + 2 * W) * sizeof(double);
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && want <= free_b / 4 && want <= (size_t(4) << 30)) {
             replay = mem.get(&rx, (size_t)n_steps * N, "step records") == COIL_OK &&
                      mem.get(&rres, (size_t)n_steps * N, "step records") == COIL_OK &&
-                     mem.get(&ruw, (size_t)n_steps * W, "step records") == COIL_OK;
+                     mem.get(&ruw, (size_t)n_steps * W, "step records") == COIL_OK &&
+                     mem.get(&ru, (size_t)n_steps * W, "step records") == COIL_OK;
             if (!replay) c->err.clear();
         }
     }
@@ -2450,6 +2452,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
         h.rec_x = rx;
         h.rec_res = rres;
         h.rec_uw = ruw;
+        h.rec_u = ru;
         h.rec_step0 = c->steps;
         h.rec_mode = 1;
         TRY(sync_descriptor(c));
@@ -2493,7 +2496,7 @@ extern "C" coil_status coil_adjoint_losses(coil_t* c, long n_steps, const coil_d
             c->h.xprev = xp;
             c->h.xprev2 = xp2;
             c->h.rec_mode = 0;
-            c->h.rec_x = c->h.rec_res = c->h.rec_uw = nullptr;
+            c->h.rec_x = c->h.rec_res = c->h.rec_uw = c->h.rec_u = nullptr;
             sync_descriptor(c);
         }
     } acc_guard{c, xprev_fwd, xprev2_fwd};

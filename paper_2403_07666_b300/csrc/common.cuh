@@ -159,8 +159,10 @@ struct CoilDev {
     // rec_step0); rec_mode 2 (its recomputation of a segment) restores them in
     // place of the solve (k_replay_restore), so the recomputed states equal
     // the forward pass's bit for bit, and k_step_end keeps the forward pass's
-    // solver diagnostics
-    double *rec_x, *rec_res, *rec_uw;
+    // solver diagnostics; rec_u holds the voltages the finalisation produced,
+    // which a replayed step takes in place of forming them from y and sigma
+    // (so that it needs no factorisation)
+    double *rec_x, *rec_res, *rec_uw, *rec_u;
     long long rec_step0;
     int rec_mode;
     double *diag;                 // ring [cap][10]

@@ -1892,8 +1892,8 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     }
     double U = con ? c.uw[w] : 0.0;
     double yr = 0.0, mom = 0.0;
-    const bool rec = c.rec_mode == 1;
-    const size_t ri = rec ? (size_t)(c.sc->step - c.rec_step0) : 0;
+    const bool rec = c.rec_mode == 1, replay = c.rec_mode == 2;
+    const size_t ri = (rec || replay) ? (size_t)(c.sc->step - c.rec_step0) : 0;
     if (rec && lane == 0) c.rec_uw[ri * c.W + w] = c.uw[w];
     for (int k = lane; k < B; k += 32) {
         int e = w * B + k;
@@ -1902,7 +1902,7 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
             c.rec_x[ri * c.N + e] = xe;
             c.rec_res[ri * c.N + e] = c.res[e];
         }
-        yr += c.y1[e] * c.res[e];
+        if (!replay) yr += c.y1[e] * c.res[e];
         double In = c.I[e] + dt * xe;
         c.I[e] = In;
         c.Phi[e] += dt * ((c.res[e] + U) - c.R[e] - dt * c.G[e] * xe);
@@ -1912,7 +1912,8 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     yr = warp_sum(yr);
     mom = warp_sum(mom);
     if (lane == 0) {
-        double u = con ? U + yr * c.isigma[w] : 0.0;
+        double u = con ? (replay ? c.rec_u[ri * c.W + w] : U + yr * c.isigma[w]) : 0.0;
+        if (rec) c.rec_u[ri * c.W + w] = u;
         c.uw[w] = u;
         parts[5 * (size_t)c.W + w] = u;
         parts[6 * (size_t)c.W + w] = mom;
