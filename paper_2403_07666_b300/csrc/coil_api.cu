@@ -34,10 +34,11 @@ cudaError_t launch_toeplitz(const CoilDev* cds, int n_coils, int max_C, int max_
 
 __global__ void k_pointwise(const CoilDev* __restrict__ cds);
 __global__ void k_factor(const CoilDev* __restrict__ cds);
-__global__ void k_factor_med(const CoilDev* __restrict__ cds);
-__global__ void k_init_med(const CoilDev* __restrict__ cds);
-__global__ void k_update_med(const CoilDev* __restrict__ cds);
-__global__ void k_near_med(const CoilDev* __restrict__ cds, int which);
+__global__ void k_factor_med(const CoilDev* __restrict__ cds, int fuse_scale);
+__global__ void k_init_med(const CoilDev* __restrict__ cds, int fuse_init);
+__global__ void k_update_med(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond,
+                             int use_cond);
+__global__ void k_near_med(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha);
 __global__ void k_near(const CoilDev* __restrict__ cds, int which);
 __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
@@ -824,7 +825,8 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         TRY(dalloc(c, &P.p16, 2 * (size_t)tsh.Cp * NT, "split operator input"));
         TRY(tc_plan_schedule(c, tsh));
         TRY(dalloc(c, &P.pexp, (size_t)NT, "input scale exponents"));
-        P.fused = B <= kSegMax;
+        // the near kernels of small and medium wires sum the partial tiles themselves
+        P.fused = B <= kSegMax || (B <= kMedMax && h.n_groups == 0);
         h.tc_part = P.part;
         h.tc_pexp = P.pexp;
     }
@@ -1112,9 +1114,10 @@ dim3 warp_grid(const Launch& L) { return dim3((unsigned)((L.maxW + 7) / 8), L.n)
 // skipping the other kind's coils.  Return the number of launches.
 int launch_near(const Launch& L, int which) {
     if (L.chol) k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, which);
-    if (L.med) k_near_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, which);
-    // tensor-core format: small-block coils take the far part from the partial tiles
+    // tensor-core format: small- and medium-block coils take the far part from
+    // the partial tiles
     const int far_tiles = L.format == 2 && !L.need_q;
+    if (L.med) k_near_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, which, far_tiles, which == 1);
     if (L.seg)
         k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1);
     return (int)L.chol + (int)L.med + (int)L.seg;
@@ -1122,7 +1125,7 @@ int launch_near(const Launch& L, int which) {
 // fuse: the small-block coils' init kernel reduces r^T z itself (last CTA).
 int launch_init(const Launch& L, bool fuse) {
     if (L.chol) k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.med) k_init_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
+    if (L.med) k_init_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, (int)fuse);
     if (L.seg)
         k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(
             L.d, (int)fuse);
@@ -1137,7 +1140,7 @@ int launch_pointwise(const Launch& L) {
 // in their factor kernel (last CTA).
 int launch_factor(const Launch& L, bool fuse) {
     if (L.chol) k_factor<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.med) k_factor_med<<<dim3(L.maxW, L.n), kMedFactorThreads, 0, L.s>>>(L.d);
+    if (L.med) k_factor_med<<<dim3(L.maxW, L.n), kMedFactorThreads, 0, L.s>>>(L.d, (int)fuse);
     if (L.seg) {
         const dim3 grid((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n);
         k_factor_seg<<<grid, 32 * kSegWarps, 0, L.s>>>(L.d, (int)fuse);
@@ -1148,7 +1151,7 @@ int launch_factor(const Launch& L, bool fuse) {
 }
 int launch_update(const Launch& L) {
     if (L.chol) k_update<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
-    if (L.med) k_update_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d);
+    if (L.med) k_update_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, 1, L.cond, (int)L.fuse_cond);
     if (L.seg)
         k_update_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(
             L.d, 1, L.cond, (int)L.fuse_cond);
@@ -1156,14 +1159,14 @@ int launch_update(const Launch& L) {
 }
 
 // The solve's first two reductions for the coils whose kernels do not fuse
-// them (blocks of more than kSegMax elements; subelements for the scale).
+// them (the Cholesky path's; subelement coils' for the scale).
 int scale_reduce(const Launch& L) {
-    if (!L.big && !L.groups) return 0;
+    if (!L.chol && !L.groups) return 0;
     k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 0, 2);
     return 1;
 }
 int init_reduce(const Launch& L) {
-    if (!L.big) return 0;
+    if (!L.chol) return 0;
     k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 1, 1);
     return 1;
 }
@@ -1193,18 +1196,18 @@ coil_status step_iteration(coil_t* c, const Launch& L) {
     } else {
         TRY(gemv(c, L, 1));
     }
-    // small-block coils reduce alpha and beta in the last CTA of their kernels
+    // small- and medium-block coils reduce alpha and beta in the last CTA of their kernels
     c->launches += launch_near(L, 1);
-    if (L.big) k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 2, 1);
+    if (L.chol) k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 2, 1);
     c->launches += launch_update(L);
-    if (L.big) k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 3, 1);
+    if (L.chol) k_reduce<<<L.n, kRedThreads, 0, L.s>>>(L.d, 3, 1);
     if (!fuse_dir) {
         unsigned eb = (unsigned)((L.maxN + 255) / 256);
         if (eb > (unsigned)L.n_sm * 16) eb = L.n_sm * 16;
         k_direction<<<dim3(eb, L.n), 256, 0, L.s>>>(L.d);
         c->launches += 1;
     }
-    c->launches += 2 * (int)L.big;
+    c->launches += 2 * (int)L.chol;
     CK(cudaGetLastError(), "iteration launch");
     return COIL_OK;
 }
@@ -1283,7 +1286,7 @@ coil_status build_step_graph(coil_t* c, int kind = 0, const Launch* Lbatch = nul
             Launch Lb = L;
             Lb.s = c->body_stream;
             Lb.cond = hnd;
-            Lb.fuse_cond = kind != 2 && L.seg && !L.big;   // the shared-warp update kernel's last CTA
+            Lb.fuse_cond = kind != 2 && !L.chol;   // the shared-warp or medium-wire update kernel's last CTA
             st = step_iteration(c, Lb);
             if (kind == 2) {
                 k_batch_cond<<<1, 128, 0, c->body_stream>>>(L.d, n, dstat + 3 * n, maxit, hnd);

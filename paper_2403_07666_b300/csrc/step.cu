@@ -698,6 +698,11 @@ __global__ void k_update(const CoilDev* __restrict__ cds) {
 // A_w = M_ww + dt G_w, the projected preconditioner P_w stored in FP32, the
 // FP64 residual and projections) with every FP64 operation spread over the
 // block's rows instead of a warp's loops over them, and no Cholesky factor.
+enum ReduceMode { RED_SCALE = 0, RED_INIT = 1, RED_ALPHA = 2, RED_BETA = 3 };
+__device__ bool fused_reduce(const CoilDev& c, double head_value, unsigned* ticket, int n_cta, int mode);
+__device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv, int2 rg);
+__device__ void loop_condition(const CoilDev& c, cudaGraphConditionalHandle h);
+
 __device__ __forceinline__ bool is_med(const CoilDev& c) {
     return c.B > kSegMax && c.B <= kMedMax && c.n_groups == 0;
 }
@@ -727,7 +732,7 @@ __device__ __forceinline__ double med_sum(double v, double* sh) {
 // barrier per step.
 template <int NP>
 __device__ __forceinline__ void factor_med_body(const CoilDev& c, int w, float (*prow)[kMedMax + 4], float* ip_s,
-                                                float* ys, float* rs, double* sh, int* bad_any) {
+                                                float* ys, float* rs, double* sh, int* bad_any, int fuse_scale) {
     constexpr int H = NP / 2;
     // the second half-row starts 16 bytes further on where NP/2 floats would put
     // it in the first half's banks
@@ -795,7 +800,10 @@ __device__ __forceinline__ void factor_med_body(const CoilDev& c, int w, float (
         if (t == k + 1 && k + 1 < B) publish(b ^ 1);
     }
     __syncthreads();
-    if (*bad_any && threadIdx.x == 0) atomicExch(&c.sc->nonpd, 1);
+    if (*bad_any && threadIdx.x == 0) {
+        atomicExch(&c.sc->nonpd, 1);
+        __threadfence();                       // before this CTA's arrival on a fused reduction
+    }
     // y = A_w^-1 1 (row sums of the symmetric inverse), sigma = 1^T y
     float yt = 0.f;
 #pragma unroll
@@ -847,10 +855,14 @@ __device__ __forceinline__ void factor_med_body(const CoilDev& c, int w, float (
         c.x[e] = xe;
         c.pf[e] = (float)xe;
     }
-    if (threadIdx.x == 0) c.parts[3 * (size_t)c.W + w] = rn + (con ? cw * cw * isg : 0.0);
+    const double scale = rn + (con ? cw * cw * isg : 0.0);
+    if (threadIdx.x == 0) c.parts[3 * (size_t)c.W + w] = scale;
+    if (fuse_scale) fused_reduce(c, threadIdx.x == 0 ? scale : 0.0, c.ticket + 3, c.W, RED_SCALE);
 }
 
-__global__ void __launch_bounds__(kMedFactorThreads, 6) k_factor_med(const CoilDev* __restrict__ cds) {
+// fuse_scale: the last CTA sums the scale partials and starts the solve's
+// scalars (the k_reduce SCALE step).
+__global__ void __launch_bounds__(kMedFactorThreads, 6) k_factor_med(const CoilDev* __restrict__ cds, int fuse_scale) {
     const CoilDev& c = cds[blockIdx.y];
     const int w = blockIdx.x;
     if (w >= c.W || !is_med(c)) return;
@@ -861,9 +873,9 @@ __global__ void __launch_bounds__(kMedFactorThreads, 6) k_factor_med(const CoilD
     __shared__ double sh[kMedFactorThreads / 32];
     __shared__ int bad_any;
     if (threadIdx.x == 0) bad_any = 0;
-    if (c.B <= 32) factor_med_body<32>(c, w, prow, ip_s, ys, rs, sh, &bad_any);
-    else if (c.B <= 48) factor_med_body<48>(c, w, prow, ip_s, ys, rs, sh, &bad_any);
-    else factor_med_body<kMedMax>(c, w, prow, ip_s, ys, rs, sh, &bad_any);
+    if (c.B <= 32) factor_med_body<32>(c, w, prow, ip_s, ys, rs, sh, &bad_any, fuse_scale);
+    else if (c.B <= 48) factor_med_body<48>(c, w, prow, ip_s, ys, rs, sh, &bad_any, fuse_scale);
+    else factor_med_body<kMedMax>(c, w, prow, ip_s, ys, rs, sh, &bad_any, fuse_scale);
 }
 
 // Row t of a B x B block stored column by column (entry (t, j) at col[j B])
@@ -894,12 +906,13 @@ __device__ __forceinline__ T med_row_dot(const T* col, const T* v, int B) {
 
 // Projected residual update and preconditioner of the block (thread t holds
 // element t; v the raw residual): writes res, returns z and the block's r^T z.
+// con, isg: the wire's constraint flag and 1 / sigma (loaded ahead); with
+// lane_rz the thread's own term of r^T z is returned in rz.
 __device__ __forceinline__ double med_residual_precond(const CoilDev& c, int w, double v, double y, bool first,
-                                                       double* rz, float* vf_s, double* sh) {
+                                                       double* rz, float* vf_s, double* sh, int con, double isg,
+                                                       bool lane_rz) {
     const int B = c.B, t = threadIdx.x, e = w * B + t;
     const bool ev = t < B;
-    const int con = c.constrained[w];
-    const double isg = c.isigma[w];
     // residual update: remove u 1, u = y^T r / sigma, accumulated in uw
     const double u = med_sum(ev ? y * v : 0.0, sh) * isg;
     if (con && ev) v -= u;
@@ -916,15 +929,17 @@ __device__ __forceinline__ double med_residual_precond(const CoilDev& c, int w, 
     // the FP32 rounding's component along the constrained direction, removed in FP64
     const double sz = med_sum(z, sh);
     if (con && ev) z -= y * sz * isg;
-    *rz = med_sum(ev ? v * z : 0.0, sh);
+    *rz = ev ? v * z : 0.0;
+    if (!lane_rz) *rz = med_sum(*rz, sh);
     return z;
 }
 
-// After q = A x0: r = q + R (projected), z = P_w r, d = -z; partial r^T z.
-__global__ void __launch_bounds__(kMedMax) k_init_med(const CoilDev* __restrict__ cds) {
+// After q = A x0: r = q + R (projected), z = P_w r, d = -z; r^T z, reduced
+// by the last CTA when fuse_init (the k_reduce INIT step).
+__global__ void __launch_bounds__(kMedMax) k_init_med(const CoilDev* __restrict__ cds, int fuse_init) {
     const CoilDev& c = cds[blockIdx.y];
     const int w = blockIdx.x;
-    if (c.sc->done || w >= c.W || !is_med(c)) return;
+    if (c.sc->done || w >= c.W || !is_med(c)) return;    // CTA-uniform
     __shared__ float vf_s[kMedMax];
     __shared__ double sh[kMedMax / 32];
     const int t = threadIdx.x, e = w * c.B + t;
@@ -932,64 +947,102 @@ __global__ void __launch_bounds__(kMedMax) k_init_med(const CoilDev* __restrict_
     const double v = ev ? c.qv[e] + c.R[e] : 0.0;
     const double y = ev ? c.y1[e] : 0.0;
     double rz;
-    const double z = med_residual_precond(c, w, v, y, true, &rz, vf_s, sh);
+    const double z = med_residual_precond(c, w, v, y, true, &rz, vf_s, sh, c.constrained[w], c.isigma[w],
+                                          fuse_init != 0);
     if (ev) {
         c.zv[e] = z;
         c.dv[e] = -z;
         c.pf[e] = (float)(-z);
     }
-    if (t == 0) c.parts[4 * (size_t)c.W + w] = rz;
+    if (fuse_init) fused_reduce(c, rz, c.ticket + 4, c.W, RED_INIT);
+    else if (t == 0) c.parts[4 * (size_t)c.W + w] = rz;
 }
 
-// x += alpha d, r += alpha q (projected), z = P_w r; partial r^T z.
-__global__ void __launch_bounds__(kMedMax) k_update_med(const CoilDev* __restrict__ cds) {
+// x += alpha d, r += alpha q (projected), z = P_w r; r^T z, reduced by the
+// last CTA when fuse_beta (the k_reduce BETA step; with use_cond it also sets
+// the PCG loop's condition, as k_update_seg does).
+__global__ void __launch_bounds__(kMedMax)
+k_update_med(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond, int use_cond) {
     const CoilDev& c = cds[blockIdx.y];
     const int w = blockIdx.x;
-    if (c.sc->done || w >= c.W || !is_med(c)) return;
+    if (w >= c.W || !is_med(c)) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) loop_condition(c, cond);
+        return;
+    }
     __shared__ float vf_s[kMedMax];
     __shared__ double sh[kMedMax / 32];
     const int t = threadIdx.x, e = w * c.B + t;
     const bool ev = t < c.B;
-    const double alpha = c.sc->alpha;
-    double v = 0.0, y = 0.0;
+    // what does not depend on the solve's progress, loaded with its done flag
+    double xv = 0.0, dv = 0.0, rv = 0.0, qv = 0.0, y = 0.0;
     if (ev) {
-        c.x[e] += alpha * c.dv[e];
-        v = c.res[e] + alpha * c.qv[e];
+        xv = c.x[e];
+        dv = c.dv[e];
+        rv = c.res[e];
+        qv = c.qv[e];
         y = c.y1[e];
     }
+    const int con = c.constrained[w];
+    const double isg = c.isigma[w];
+    const double alpha = c.sc->alpha;
+    if (c.sc->done) {                                    // CTA-uniform
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) loop_condition(c, cond);
+        return;
+    }
+    double v = 0.0;
+    if (ev) {
+        c.x[e] = xv + alpha * dv;
+        v = rv + alpha * qv;
+    }
     double rz;
-    const double z = med_residual_precond(c, w, v, y, false, &rz, vf_s, sh);
+    const double z = med_residual_precond(c, w, v, y, false, &rz, vf_s, sh, con, isg, fuse_beta != 0);
     if (ev) c.zv[e] = z;
-    if (t == 0) c.parts[4 * (size_t)c.W + w] = rz;
+    if (!fuse_beta) {
+        if (t == 0) c.parts[4 * (size_t)c.W + w] = rz;
+    } else if (fused_reduce(c, rz, c.ticket + 1, c.W, RED_BETA) && use_cond && threadIdx.x == 0) {
+        loop_condition(c, cond);
+    }
 }
 
-// q_w += (M_ww + dt G_w) p_w (FP64, row t on thread t); optional partial p^T q.
-__global__ void __launch_bounds__(kMedMax) k_near_med(const CoilDev* __restrict__ cds, int which) {
+// q_w += (M_ww + dt G_w) p_w (FP64, row t on thread t), the far part taken
+// from the tensor-core apply's partial tiles when far_tiles; p^T q, reduced by
+// the last CTA when fuse_alpha (the k_reduce ALPHA step).
+__global__ void __launch_bounds__(kMedMax) k_near_med(const CoilDev* __restrict__ cds, int which, int far_tiles,
+                                                      int fuse_alpha) {
     const CoilDev& c = cds[blockIdx.y];
     const int w = blockIdx.x;
-    if (c.sc->done || w >= c.W || !is_med(c)) return;
+    if (w >= c.W || !is_med(c)) return;                  // CTA-uniform
     __shared__ double ps[kMedMax];
     __shared__ double sh[kMedMax / 32];
     const int B = c.B, t = threadIdx.x, e = w * B + t;
     const bool ev = t < B;
+    // what does not depend on the solve's progress, loaded with its done flag
     const double* p = which == 0 ? c.x : c.dv;
     const double pv = ev ? p[e] : 0.0;
+    const double ge = ev ? c.G[e] : 0.0;
+    const int bt = c.block_type[w];
+    const int xmin = far_tiles ? warp_min_exponent(c.tc_pexp, c.NT, threadIdx.x & 31) : 0;
+    const int2 rg = (far_tiles && ev && c.tc_mode != 1) ? c.tc_range[(e % c.C) / kTcTileRows] : make_int2(0, 0);
+    if (c.sc->done) return;                              // CTA-uniform
     ps[t] = pv;
     __syncthreads();
     double dot = 0.0;
     if (ev) {
         // row t read as column t (the self block is symmetric entry for entry):
         // consecutive threads, consecutive words
-        const double acc = med_row_dot(c.near + (size_t)c.block_type[w] * B * B + t, ps, B) + c.dt * c.G[e] * pv;
-        const double qe = c.qv[e] + acc;
+        const double acc = med_row_dot(c.near + (size_t)bt * B * B + t, ps, B) + c.dt * ge * pv;
+        const double far = far_tiles ? tc_far_sum(c, e, ldexp(1.0, -(c.tc_exT + xmin)), rg) : c.qv[e];
+        const double qe = far + acc;
         c.qv[e] = qe;
         dot = pv * qe;
     }
-    dot = med_sum(dot, sh);
-    if (which == 1 && t == 0) c.parts[4 * (size_t)c.W + w] = dot;
+    if (fuse_alpha) {
+        fused_reduce(c, which == 1 ? dot : 0.0, c.ticket, c.W, RED_ALPHA);
+    } else {
+        dot = med_sum(dot, sh);
+        if (which == 1 && t == 0) c.parts[4 * (size_t)c.W + w] = dot;
+    }
 }
-
-enum ReduceMode { RED_SCALE = 0, RED_INIT = 1, RED_ALPHA = 2, RED_BETA = 3 };
 
 __device__ double block_reduce_sum(double v, double* sh) {
     v = warp_sum(v);
@@ -1074,12 +1127,13 @@ __device__ void reduce_and_update(const CoilDev& c, int mode, const double* a, i
     }
 }
 
-// One CTA per coil; skip_seg: coils whose shared-warp kernels reduce their
-// partials themselves (last CTA) are left alone (2: only those without
-// subelements, whose factor kernel does; the subelement factor does not).
+// One CTA per coil; skip_seg: coils whose kernels reduce their partials
+// themselves (last CTA: the shared-warp and medium-wire kernels) are left
+// alone (2: of the shared-warp coils only those without subelements, whose
+// factor kernel does; the subelement factor does not).
 __global__ void __launch_bounds__(1024) k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg) {
     const CoilDev& c = cds[blockIdx.x];
-    if (skip_seg && c.B <= kSegMax && (skip_seg == 1 || c.n_groups == 0)) return;
+    if (skip_seg && (is_med(c) || (c.B <= kSegMax && (skip_seg == 1 || c.n_groups == 0)))) return;
     reduce_and_update(c, mode, c.parts + (mode == RED_SCALE ? 3 : 4) * (size_t)c.W, c.W);
 }
 
