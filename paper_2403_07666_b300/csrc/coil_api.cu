@@ -53,6 +53,7 @@ __global__ void k_direction(const CoilDev* __restrict__ cds);
 __global__ void k_reduce(const CoilDev* __restrict__ cds, int mode, int skip_seg);
 __global__ void k_finalize(const CoilDev* __restrict__ cds);
 __global__ void k_replay_restore(const CoilDev* __restrict__ cds);
+__global__ void k_finalize_seg(const CoilDev* __restrict__ cds);
 __global__ void k_adi_r(const CoilDev* __restrict__ cds);
 cudaError_t adi_allow_smem(size_t bytes);
 cudaError_t adj_adi_allow_smem(size_t bytes);
@@ -1214,14 +1215,21 @@ coil_status step_iteration(coil_t* c, const Launch& L) {
 
 // Current/flux update, heat step, diagnostics (coils whose solve failed skip it).
 coil_status step_epilogue(coil_t* c, const Launch& L) {
-    k_finalize<<<warp_grid(L), 256, 0, L.s>>>(L.d);
+    if (L.big || L.groups) {
+        k_finalize<<<warp_grid(L), 256, 0, L.s>>>(L.d);
+        c->launches += 1;
+    }
+    if (L.seg) {
+        k_finalize_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d);
+        c->launches += 1;
+    }
     if (L.thermal) {
         k_adi_r<<<dim3(L.maxGz, L.n), kAdiThreads, adi_smem_bytes(L.maxGr), L.s>>>(L.d);
         k_adi_z<<<dim3(L.maxGr, L.n), kAdiThreads, adi_smem_bytes(L.maxGz), L.s>>>(L.d);
         c->launches += 2;
     }
     k_step_end<<<dim3(kStepEndCtas, L.n), kStepEndThreads, 0, L.s>>>(L.d);
-    c->launches += 2;
+    c->launches += 1;
     CK(cudaGetLastError(), "step end launch");
     return COIL_OK;
 }

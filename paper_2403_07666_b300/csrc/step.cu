@@ -1889,9 +1889,11 @@ __global__ void k_direction(const CoilDev* __restrict__ cds) {
 // u_w, I += dt x, flux += dt M x with M x = (r + U_w) - R - dt G x (r is the
 // projected residual, U_w the loop voltage removed from it); partials V
 // (parts[5]) and m (parts[6]).
+// One warp per wire; the coils of k_finalize_seg are left to it.
 __global__ void k_finalize(const CoilDev* __restrict__ cds) {
     const CoilDev& c = cds[blockIdx.y];
     if (c.sc->status != ST_OK) return;          // a failed coil keeps its state
+    if (c.B <= kSegMax && c.n_groups == 0) return;
     double* parts = c.parts;
     int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -1971,6 +1973,47 @@ __global__ void k_finalize(const CoilDev* __restrict__ cds) {
         c.uw[w] = u;
         parts[5 * (size_t)c.W + w] = u;
         parts[6 * (size_t)c.W + w] = mom;
+    }
+}
+
+// k_finalize for wires of at most 16 elements without subelements, 32 / Bp
+// wires per warp (the same operations per element; the wire sums drop only
+// the idle lanes' zeros).
+__global__ void k_finalize_seg(const CoilDev* __restrict__ cds) {
+    const CoilDev& c = cds[blockIdx.y];
+    if (c.sc->status != ST_OK || c.B > kSegMax || c.n_groups != 0) return;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform
+    const Seg s = seg_of(c, wg);
+    const double dt = c.dt;
+    const int con = s.wv ? c.constrained[s.w] : 0;
+    const double U = con ? c.uw[s.w] : 0.0;
+    const bool rec = c.rec_mode == 1, replay = c.rec_mode == 2;
+    const size_t ri = (rec || replay) ? (size_t)(c.sc->step - c.rec_step0) : 0;
+    if (rec && s.kk == 0 && s.wv) c.rec_uw[ri * c.W + s.w] = c.uw[s.w];
+    double yr = 0.0, mom = 0.0;
+    if (s.ev) {
+        const int e = s.e;
+        const double xe = c.x[e], re = c.res[e];
+        if (rec) {
+            c.rec_x[ri * c.N + e] = xe;
+            c.rec_res[ri * c.N + e] = re;
+        }
+        if (!replay) yr = c.y1[e] * re;
+        const double In = c.I[e] + dt * xe;
+        c.I[e] = In;
+        c.Phi[e] += dt * ((re + U) - c.R[e] - dt * c.G[e] * xe);
+        mom = c.pir2[e] * In;
+    }
+    yr = seg_sum(yr, s.Bp);
+    mom = seg_sum(mom, s.Bp);
+    if (s.kk == 0 && s.wv) {
+        const int w = s.w;
+        const double u = con ? (replay ? c.rec_u[ri * c.W + w] : U + yr * c.isigma[w]) : 0.0;
+        if (rec) c.rec_u[ri * c.W + w] = u;
+        c.uw[w] = u;
+        c.parts[5 * (size_t)c.W + w] = u;
+        c.parts[6 * (size_t)c.W + w] = mom;
     }
 }
 
