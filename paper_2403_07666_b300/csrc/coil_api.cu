@@ -42,7 +42,8 @@ __global__ void k_near_med(const CoilDev* __restrict__ cds, int which, int far_t
 __global__ void k_near(const CoilDev* __restrict__ cds, int which);
 __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
-__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha);
+__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha,
+                           int near_pre);
 __global__ void k_init_seg(const CoilDev* __restrict__ cds, int fuse_init);
 __global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond,
                              int use_cond);
@@ -761,6 +762,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
     TRY(dalloc(c, &h.zv, N, "z"));
     TRY(dalloc(c, &h.dv, ld, "d"));
     TRY(dalloc(c, &h.qv, N, "q"));
+    TRY(dalloc(c, &h.qn, N, "near part of q"));
     TRY(dalloc(c, &h.R, N, "R"));
     TRY(dalloc(c, &h.G, N, "G"));
     TRY(dalloc(c, &h.pf, ld, "pf"));
@@ -973,6 +975,12 @@ size_t block_smem(const CoilDev& h) {
 // Launch geometry of one step for one coil or a batch (grid row y = coil).
 struct Launch {
     const CoilDev* d = nullptr;
+    // one coil of small blocks in the two-fill tensor-core form: the apply's
+    // near warps form the near-block part of q (from x for the first apply of a
+    // step, from d in the iterations) into qn, which the near kernel reads
+    bool near_in_apply = false;
+    const double *near_x = nullptr, *near_d = nullptr;
+    double* near_q = nullptr;
     std::vector<const TcPlan*> tc;   // format 2: one plan per coil
     int n = 1;
     int prec = 0;
@@ -1025,6 +1033,10 @@ Launch single_launch(coil_t* c) {
     L.chol = L.big && !L.med;
     L.groups = h.n_groups != 0;
     if (c->tc) L.tc.push_back(c->tc);
+    L.near_in_apply = L.format == 2 && c->tc && c->tc->sh.mode == 0 && L.seg;
+    L.near_x = h.x;
+    L.near_d = h.dv;
+    L.near_q = h.qn;
     return L;
 }
 
@@ -1048,7 +1060,10 @@ cudaError_t launch_far(const Launch& L, int which) {
             return e;
         }
         for (const TcPlan* P : L.tc) {
-            cudaError_t e = launch_toeplitz_tc(*P, L.s, L.need_q || !P->fused, L.dir);
+            const bool nia = L.near_in_apply && L.tc.size() == 1;
+            cudaError_t e = launch_toeplitz_tc(*P, L.s, L.need_q || !P->fused, L.dir,
+                                               nia ? (which == 0 ? L.near_x : L.near_d) : nullptr,
+                                               nia ? L.near_q : nullptr);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -1071,7 +1086,9 @@ coil_status gemv(coil_t* c, const Launch& L, int which) {
         const TcPlan& P = *L.tc[0];
         CK(launch_tc_split(P, L.s, L.dir), "operator apply");
         CK(cudaEventRecord(c->ev_pool[2 * c->ev_used], L.s), "event");
-        CK(launch_tc_apply(P, L.s, L.need_q || !P.fused), "operator apply");
+        CK(launch_tc_apply(P, L.s, L.need_q || !P.fused, L.near_in_apply ? (which == 0 ? L.near_x : L.near_d) : nullptr,
+                           L.near_in_apply ? L.near_q : nullptr),
+           "operator apply");
         CK(cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], L.s), "event");
         c->ev_used += 1;
         c->op_launches += 1;
@@ -1120,7 +1137,8 @@ int launch_near(const Launch& L, int which) {
     const int far_tiles = L.format == 2 && !L.need_q;
     if (L.med) k_near_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, which, far_tiles, which == 1);
     if (L.seg)
-        k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1);
+        k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1,
+                                                                              (int)L.near_in_apply);
     return (int)L.chol + (int)L.med + (int)L.seg;
 }
 // fuse: the small-block coils' init kernel reduces r^T z itself (last CTA).

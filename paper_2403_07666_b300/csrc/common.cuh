@@ -118,6 +118,7 @@ struct CoilDev {
     double rtol2;
     // state and work vectors (element order unless noted)
     double *I, *Phi, *x, *res, *zv, *dv, *qv, *R, *G;
+    double *qn;                   // near-block part of q, formed by the tensor-core apply's near warps
     float *pf;                    // FP32 copy of the operator input (ld long)
     double *uT, *qgrid;           // grid order [Gz][Gr]
     double *ustar, *src;          // column order [Gr][Gz] (the ADI z-lines read them)

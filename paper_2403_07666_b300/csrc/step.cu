@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "pointwise.cuh"
 #include "tridiag.cuh"
+#include "seg.cuh"
 
 namespace cq {
 
@@ -1193,35 +1194,7 @@ __device__ bool fused_reduce(const CoilDev& c, double head_value, unsigned* tick
 // butterflies there only added the idle lanes' zeros), but each FP64 warp
 // instruction now serves 32 / Bp wires: B300's FP64 pipe is narrow.
 
-__device__ __forceinline__ int seg_width(int B) {
-    int p = 1;
-    while (p < B) p <<= 1;
-    return p;
-}
-
-__device__ __forceinline__ double seg_sum(double v, int Bp) {
-    for (int o = Bp >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-struct Seg {
-    int B, Bp, kk, base, w, e;
-    bool wv, ev;        // wire exists, element exists
-};
-
-__device__ __forceinline__ Seg seg_of(const CoilDev& c, int warp_global) {
-    Seg s;
-    s.B = c.B;
-    s.Bp = seg_width(c.B);
-    const int lane = threadIdx.x & 31;
-    s.kk = lane & (s.Bp - 1);
-    s.base = lane - s.kk;
-    s.w = warp_global * (32 / s.Bp) + lane / s.Bp;
-    s.wv = s.w < c.W;
-    s.ev = s.wv && s.kk < s.B;
-    s.e = s.w * s.B + s.kk;
-    return s;
-}
+// (seg_width, seg_sum, Seg, seg_of and near_row_product: seg.cuh)
 
 // Far-operator value at element e of the tensor-core Toeplitz apply: the sum
 // of the partial tiles of the CTAs that worked on e's channel tile, in a fixed
@@ -1283,7 +1256,10 @@ __device__ __forceinline__ double tc_far_sum(const CoilDev& c, int e, double inv
 // far_tiles: the far part comes from the tensor-core apply's partial tiles
 // (its separate reduction was skipped) instead of q.  fuse_alpha: the last
 // CTA sums the p^T q partials and sets alpha (the k_reduce ALPHA step).
-__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha) {
+// near_pre: the near-block part (with dt G p) was formed by the tensor-core
+// apply's near warps into qn (the same operations, see near_row_product).
+__global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha,
+                           int near_pre) {
     const CoilDev& c = cds[blockIdx.y];
     const int per_cta = (int)(blockDim.x >> 5) * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
@@ -1295,7 +1271,8 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
     // done flag: one round trip instead of several in sequence
     const double* p = which == 0 ? c.x : c.dv;
     const double pv = s.ev ? p[s.e] : 0.0;
-    const double ge = s.ev ? c.G[s.e] : 0.0;
+    const double ge = (s.ev && !near_pre) ? c.G[s.e] : 0.0;
+    const double qn = (s.ev && near_pre) ? c.qn[s.e] : 0.0;
     const int bt = c.block_type[s.wv ? s.w : 0];
     const int xmin = far_tiles ? warp_min_exponent(c.tc_pexp, c.NT, threadIdx.x & 31) : 0;
     const int2 rg = (far_tiles && s.ev && c.tc_mode != 1) ? c.tc_range[(s.e % c.C) / kTcTileRows] : make_int2(0, 0);
@@ -1303,25 +1280,9 @@ __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_t
     double head = 0.0;                                  // the lane's term of p^T q (fused reduction)
     if (warp_on) {
         const double inv = far_tiles ? ldexp(1.0, -(c.tc_exT + xmin)) : 0.0;
-        const double* nb = c.near + (size_t)bt * s.B * s.B;
-        const int row = s.kk < s.B ? s.kk : 0;
-        double acc = 0.0;
-        if (s.B == kSegMax) {
-            // 16-element wires: the row as eight 16-byte loads, all in flight at once
-            double2 nr[kSegMax / 2];
-#pragma unroll
-            for (int q = 0; q < kSegMax / 2; ++q) nr[q] = reinterpret_cast<const double2*>(nb + row * kSegMax)[q];
-#pragma unroll
-            for (int q = 0; q < kSegMax / 2; ++q) {
-                acc += nr[q].x * __shfl_sync(0xffffffffu, pv, s.base + 2 * q);
-                acc += nr[q].y * __shfl_sync(0xffffffffu, pv, s.base + 2 * q + 1);
-            }
-        } else {
-            for (int j = 0; j < s.B; ++j) acc += nb[row * s.B + j] * __shfl_sync(0xffffffffu, pv, s.base + j);
-        }
+        const double acc = near_pre ? qn : near_row_product(c, s, bt, pv, ge);
         double dot = 0.0;
         if (s.ev) {
-            acc += c.dt * ge * pv;
             double qe = (far_tiles ? tc_far_sum(c, s.e, inv, rg) : c.qv[s.e]) + acc;
             c.qv[s.e] = qe;
             dot = pv * qe;

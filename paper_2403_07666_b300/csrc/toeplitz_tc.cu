@@ -58,6 +58,7 @@
 // waited for (again bounded), the TMEM is freed, and the coil's status word
 // reports the failure to the host.
 #include "toeplitz_tc.h"
+#include "seg.cuh"
 
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -75,7 +76,10 @@ constexpr int kTcParities = 4;                   // epilogue warps per lane quad
 constexpr int kTcEpiWarps = 4 * kTcParities;     // epilogue warps: 4 lane quadrants x kTcParities
 constexpr int kTcIssuers = 4;                    // MMA-issuing warps, taking the stages in turn
 constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
-constexpr int kTcThreads = 32 * (kTcEpi0 + kTcEpiWarps);   // producer, MMA issuers, epilogue
+constexpr int kTcNearWarps = 2;                  // FP64 near-block products beside the apply (two-fill)
+constexpr int kTcNear0 = kTcEpi0 + kTcEpiWarps;   // first near warp
+constexpr int kTcThreads = 32 * kTcNear0;      // producer, MMA issuers, epilogue
+constexpr int kTcThreadsNear = kTcThreads + 32 * kTcNearWarps;   // the single-coil two-fill apply: + near warps
 constexpr int kTcGroups = (14 + kTcParities - 1) / kTcParities;   // 8-turn groups per epilogue warp (NT <= 112)
 constexpr uint32_t kTcAStage = 2u * kTcM * kTcK * 2u;   // hi + lo table tiles, 32 KB
 // MN-major A (128-byte swizzle): byte offsets between the two 64-channel
@@ -281,10 +285,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 // The two-fill apply of one coil by one CTA: work entry wk = (channel tile,
 // first step, end step), partial tile `cta` of `part`.  The tensor maps may
 // live in the kernel's parameters or in global memory (a batch).
+// near_src / near_dst (may be null): the near warps form the near-block part
+// of q for this CTA's share of the coil's wires (FP64; the apply itself uses
+// no FP64, so it runs on otherwise idle units), read by k_near_seg.
 __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUtensorMap* mapAT,
                                              const CUtensorMap* mapB, const CoilDev& c, const TcShape sh,
                                              const int4 wk, const int cta, const int* __restrict__ pexp,
-                                             float* __restrict__ part) {
+                                             float* __restrict__ part, const double* __restrict__ near_src,
+                                             double* __restrict__ near_dst) {
     const CUtensorMap& tmA = *mapA;
     const CUtensorMap& tmAT = *mapAT;
     const CUtensorMap& tmB = *mapB;
@@ -490,7 +498,20 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
         __syncwarp();
         mma_commit_warp(mma_done);
         if (!__all_sync(0xffffffffu, mbar_wait_final(mma_done, 0u, kTcWait)) && lane == 0) *abort_flag = 1;
-    } else if (warp >= kTcEpi0) {
+    } else if (warp >= kTcNear0) {
+        // ---- near warps: the near-block products of this CTA's share of the
+        // wires, two 16-element wires (a segment each) per warp task
+        if (near_dst && c.B <= kSegMax) {
+            const int n_task = (c.W + 32 / seg_width(c.B) - 1) / (32 / seg_width(c.B));
+            for (int wg = cta * kTcNearWarps + (warp - kTcNear0); wg < n_task; wg += (int)gridDim.x * kTcNearWarps) {
+                const Seg s = seg_of(c, wg);
+                const double pv = s.ev ? near_src[s.e] : 0.0;
+                const double ge = s.ev ? c.G[s.e] : 0.0;
+                const double q = near_row_product(c, s, c.block_type[s.wv ? s.w : 0], pv, ge);
+                if (s.ev) near_dst[s.e] = q;
+            }
+        }
+    } else if (warp >= kTcEpi0 && warp < kTcNear0) {
         // ---- epilogue: each stage's accumulator is added into FP32 registers (lane
         // quadrant warp % 4, turn groups of parity h), then released to the MMAs
         const int q = warp & 3;
@@ -569,12 +590,13 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreadsNear, 1)
 k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAT,
               const __grid_constant__ CUtensorMap tmB,
               const CoilDev* __restrict__ cd, const TcShape sh, const int4* __restrict__ work,
-              const int* __restrict__ pexp, float* __restrict__ part) {
-    tc_apply_cta(&tmA, &tmAT, &tmB, *cd, sh, work[blockIdx.x], (int)blockIdx.x, pexp, part);
+              const int* __restrict__ pexp, float* __restrict__ part, const double* __restrict__ near_src,
+              double* __restrict__ near_dst) {
+    tc_apply_cta(&tmA, &tmAT, &tmB, *cd, sh, work[blockIdx.x], (int)blockIdx.x, pexp, part, near_src, near_dst);
 }
 
 // A batch's applies in one launch: CTA b works for coil bwork[b].x as its
@@ -588,7 +610,7 @@ k_toeplitz_tc_batch(const TcCoilArgs* __restrict__ args, const int2* __restrict_
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmAT)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmB)) : "memory");
     }
-    tc_apply_cta(&A.tmA, &A.tmAT, &A.tmB, *A.d, A.sh, A.work[bw.y], bw.y, A.pexp, A.part);
+    tc_apply_cta(&A.tmA, &A.tmAT, &A.tmB, *A.d, A.sh, A.work[bw.y], bw.y, A.pexp, A.part, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1517,7 +1539,7 @@ cudaError_t launch_tc_split(const TcPlan& P, cudaStream_t s, bool dir) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q) {
+cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q, const double* near_src, double* near_dst) {
     const TcShape& sh = P.sh;
     if (sh.mode == 1) {
         k_toeplitz_tc2<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmB, P.tmB64, P.d, sh, P.work, P.pexp, P.part,
@@ -1530,7 +1552,8 @@ cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q) {
         }
         return cudaGetLastError();
     }
-    k_toeplitz_tc<<<sh.n_cta, kTcThreads, P.smem, s>>>(P.tmA, P.tmAT, P.tmB, P.d, sh, P.work, P.pexp, P.part);
+    k_toeplitz_tc<<<sh.n_cta, kTcThreadsNear, P.smem, s>>>(P.tmA, P.tmAT, P.tmB, P.d, sh, P.work, P.pexp, P.part,
+                                                        near_src, near_dst);
     if (write_q) {
         int rb = (sh.N + 255) / 256;
         if (rb > 148 * 8) rb = 148 * 8;
@@ -1598,9 +1621,10 @@ cudaError_t launch_tc_batch(const TcBatch& B, cudaStream_t s, bool need_q, bool 
     return cudaGetLastError();
 }
 
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir) {
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir, const double* near_src,
+                               double* near_dst) {
     cudaError_t e = launch_tc_split(P, s, dir);
-    return e == cudaSuccess ? launch_tc_apply(P, s, write_q) : e;
+    return e == cudaSuccess ? launch_tc_apply(P, s, write_q, near_src, near_dst) : e;
 }
 
 }  // namespace cq

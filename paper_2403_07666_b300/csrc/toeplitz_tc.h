@@ -108,13 +108,17 @@ cudaError_t tc_build_table(TcPlan* P, const double* tab, int wire_div, double* s
 cudaError_t tc_encode_maps(TcPlan* P, const char** why);
 // M_far p for the coil of P (from pf): the split, the apply into the partial
 // tiles and, with write_q, their reduction into qv (otherwise the coil's
-// shared-warp near kernel sums the tiles).
+// shared-warp near kernel sums the tiles).  near_src / near_dst (two-fill,
+// wires of at most 16 elements): the apply's near warps also form the
+// near-block part of q, with dt G p, from near_src into near_dst.
 // dir: form the PCG direction d = -z + beta d in the input split first.
-cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir = false);
+cudaError_t launch_toeplitz_tc(const TcPlan& P, cudaStream_t s, bool write_q, bool dir = false,
+                               const double* near_src = nullptr, double* near_dst = nullptr);
 // Its two halves: the input split (k_tc_split) and the tensor-core product
 // (k_toeplitz_tc, plus the FP64 reduction into q when write_q).
 cudaError_t launch_tc_split(const TcPlan& P, cudaStream_t s, bool dir);
-cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q);
+cudaError_t launch_tc_apply(const TcPlan& P, cudaStream_t s, bool write_q, const double* near_src = nullptr,
+                            double* near_dst = nullptr);
 // Batches: build (uploads the coils' arguments; every plan in the two-fill
 // mode), free, and launch split + apply + reductions (need_q: every coil's
 // result into q; dir: form the PCG direction first).
