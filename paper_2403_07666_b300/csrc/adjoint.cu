@@ -44,8 +44,9 @@ __global__ void k_adj_adi_z(const CoilDev* __restrict__ cds, AdjBufs ab) {
     if (i >= c.Gr) return;
     extern __shared__ double sm[];
     int Gr = c.Gr, Gz = c.Gz;
+    line_stage(sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
     for (int j = threadIdx.x; j < Gz; j += blockDim.x) sm[j] = ab.lamU_next[j * Gr + i];
-    line_tridiag(sm, sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
+    line_solve(sm, sm + Gz, Gz);
     for (int j = threadIdx.x; j < Gz; j += blockDim.x) ab.a[j * Gr + i] = sm[j];
 }
 
@@ -57,6 +58,7 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
     extern __shared__ double sm[];
     int Gr = c.Gr;
     double hd = 0.5 * c.dt, invC = 1.0 / c.Ccell;
+    line_stage(sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
     for (int i = threadIdx.x; i < Gr; i += blockDim.x) {
         int g = j * Gr + i;
         double ai = ab.a[g];
@@ -65,7 +67,7 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
         if (i < Gr - 1) ar += c.Kr[i] * (ab.a[g + 1] - ai);
         sm[i] = ai + hd * (ar * invC);
     }
-    line_tridiag(sm, sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
+    line_solve(sm, sm + Gr, Gr);
     for (int i = threadIdx.x; i < Gr; i += blockDim.x) ab.b[j * Gr + i] = sm[i];
 }
 

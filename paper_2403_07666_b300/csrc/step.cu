@@ -37,6 +37,28 @@ __device__ __forceinline__ double warm_start(const CoilDev& c, int e, bool ext) 
     return ext ? 2.0 * x - xp : x;
 }
 
+// The same in two halves, so that its loads can be issued early: the values
+// warm_start reads, then the extrapolation and the history shift.
+struct WarmIn {
+    double x, xp, xp2;
+};
+__device__ __forceinline__ WarmIn warm_load(const CoilDev& c, int e) {
+    WarmIn w;
+    w.x = c.x[e];
+    w.xp = c.extrap ? c.xprev[e] : 0.0;
+    w.xp2 = (c.extrap == 1 || c.extrap >= 4) ? c.xprev2[e] : 0.0;
+    return w;
+}
+__device__ __forceinline__ double warm_finish(const CoilDev& c, int e, bool ext, const WarmIn& w) {
+    if (!c.extrap) return w.x;
+    c.xprev[e] = w.x;
+    if (c.extrap == 1 || c.extrap >= 4) {
+        c.xprev2[e] = w.xp;
+        if ((c.extrap == 1 && c.sc->step >= 3) || c.extrap == 4) return 3.0 * w.x - 3.0 * w.xp + w.xp2;
+    }
+    return ext ? 2.0 * w.x - w.xp : w.x;
+}
+
 __device__ __forceinline__ bool extrapolate(const CoilDev& c) {
     return (c.extrap == 1 && c.sc->step >= 2) || c.extrap == 3 || c.extrap == 4 || c.extrap == 6;
 }
@@ -1718,6 +1740,13 @@ __device__ __forceinline__ double factor_seg(const CoilDev& c, const Seg& s) {
         for (int j = 0; j < kSegMax; ++j)
             if (j == kk) a[j] += g;
     }
+    // what the steps after the inverse read, loaded now: its latency hides
+    // behind the sweep
+    const WarmIn wm = s.ev ? warm_load(c, e) : WarmIn{0.0, 0.0, 0.0};
+    const bool ext = extrapolate(c);
+    const int con = s.wv ? c.constrained[w] : 0;
+    const double R = s.ev ? c.R[e] : 0.0;
+    const double cw = s.wv ? c.cw[w] : 0.0;
     int bad = 0;
 #pragma unroll
     for (int k = 0; k < kSegMax; ++k) {
@@ -1750,14 +1779,13 @@ __device__ __forceinline__ double factor_seg(const CoilDev& c, const Seg& s) {
         if (j < B) yt += a[j];
     const double y = s.ev ? (double)yt : 0.0;
     const double sig = seg_sum(y, s.Bp);
-    const int con = s.wv ? c.constrained[w] : 0;
     const double isg = 1.0 / sig;
     if (s.ev) c.y1[e] = y;
     if (kk == 0 && s.wv) {
         c.sigma[w] = sig;
         c.isigma[w] = isg;
     }
-    const double x0 = s.ev ? warm_start(c, e, extrapolate(c)) : 0.0;   // before the constraint
+    const double x0 = s.ev ? warm_finish(c, e, ext, wm) : 0.0;   // before the constraint
     if constexpr (sizeof(T) == sizeof(double)) {
         if (c.n_groups) {
             factor_groups(c, s, a, y, isg, con, x0);
@@ -1766,7 +1794,6 @@ __device__ __forceinline__ double factor_seg(const CoilDev& c, const Seg& s) {
     }
     // P_w row kk, stored (its entries are FP32 values: the subtraction runs in
     // T = float); R^T P_w R in FP32 (it only scales the stopping test)
-    const double R = s.ev ? c.R[e] : 0.0;
     const float Rf = (float)R, yf = (float)y, yis = (float)(y * isg);
     float pr0 = 0.f, pr1 = 0.f;
 #pragma unroll
@@ -1781,7 +1808,6 @@ __device__ __forceinline__ double factor_seg(const CoilDev& c, const Seg& s) {
         }
     }
     const double rn = seg_sum(s.ev ? R * (double)(pr0 + pr1) : 0.0, s.Bp);
-    const double cw = s.wv ? c.cw[w] : 0.0;
     // warm start moved onto this step's constraint
     const double sx = seg_sum(x0, s.Bp);
     const double corr = con ? (cw - sx) * isg : 0.0;
@@ -1947,30 +1973,36 @@ __global__ void k_finalize_seg(const CoilDev* __restrict__ cds) {
     if (wg * (32 / seg_width(c.B)) >= c.W) return;       // warp-uniform
     const Seg s = seg_of(c, wg);
     const double dt = c.dt;
-    const int con = s.wv ? c.constrained[s.w] : 0;
-    const double U = con ? c.uw[s.w] : 0.0;
     const bool rec = c.rec_mode == 1, replay = c.rec_mode == 2;
-    const size_t ri = (rec || replay) ? (size_t)(c.sc->step - c.rec_step0) : 0;
-    if (rec && s.kk == 0 && s.wv) c.rec_uw[ri * c.W + s.w] = c.uw[s.w];
+    // every load first (one round trip), then the arithmetic
+    const int wl = s.wv ? s.w : 0, el = s.ev ? s.e : 0;
+    const int con_w = c.constrained[wl];
+    const double uw0 = c.uw[wl], isg = c.isigma[wl];
+    const double xe = c.x[el], re = c.res[el], ye = c.y1[el], Ie = c.I[el], Pe = c.Phi[el];
+    const double Re = c.R[el], Ge = c.G[el], pr2 = c.pir2[el];
+    const long long st = c.sc->step;
+    const int con = s.wv ? con_w : 0;
+    const double U = con ? uw0 : 0.0;
+    const size_t ri = (rec || replay) ? (size_t)(st - c.rec_step0) : 0;
+    if (rec && s.kk == 0 && s.wv) c.rec_uw[ri * c.W + s.w] = uw0;
     double yr = 0.0, mom = 0.0;
     if (s.ev) {
         const int e = s.e;
-        const double xe = c.x[e], re = c.res[e];
         if (rec) {
             c.rec_x[ri * c.N + e] = xe;
             c.rec_res[ri * c.N + e] = re;
         }
-        if (!replay) yr = c.y1[e] * re;
-        const double In = c.I[e] + dt * xe;
+        if (!replay) yr = ye * re;
+        const double In = Ie + dt * xe;
         c.I[e] = In;
-        c.Phi[e] += dt * ((re + U) - c.R[e] - dt * c.G[e] * xe);
-        mom = c.pir2[e] * In;
+        c.Phi[e] = Pe + dt * ((re + U) - Re - dt * Ge * xe);
+        mom = pr2 * In;
     }
     yr = seg_sum(yr, s.Bp);
     mom = seg_sum(mom, s.Bp);
     if (s.kk == 0 && s.wv) {
         const int w = s.w;
-        const double u = con ? (replay ? c.rec_u[ri * c.W + w] : U + yr * c.isigma[w]) : 0.0;
+        const double u = con ? (replay ? c.rec_u[ri * c.W + w] : U + yr * isg) : 0.0;
         if (rec) c.rec_u[ri * c.W + w] = u;
         c.uw[w] = u;
         c.parts[5 * (size_t)c.W + w] = u;
@@ -2018,6 +2050,7 @@ __global__ void k_adi_r(const CoilDev* __restrict__ cds) {
     int Gr = c.Gr, Gz = c.Gz;
     double hd = 0.5 * c.dt;
     double invC = 1.0 / c.Ccell;
+    line_stage(sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
     for (int i = threadIdx.x; i < Gr; i += blockDim.x) {
         int g = j * Gr + i;
         double u = c.uT[g];
@@ -2028,7 +2061,7 @@ __global__ void k_adi_r(const CoilDev* __restrict__ cds) {
         if (j < Gz - 1) az += c.Kz[j] * (c.uT[g + Gr] - u);
         sm[i] = u + hd * (az * invC) + hd * s;
     }
-    line_tridiag(sm, sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
+    line_solve(sm, sm + Gr, Gr);
     // stored column by column: the z-lines' loads are then contiguous
     for (int i = threadIdx.x; i < Gr; i += blockDim.x) c.ustar[(size_t)i * Gz + j] = sm[i];
 }
@@ -2043,6 +2076,7 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
     int Gr = c.Gr, Gz = c.Gz;
     double hd = 0.5 * c.dt;
     double invC = 1.0 / c.Ccell;
+    line_stage(sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
     const double* col = c.ustar + (size_t)i * Gz;       // column i (and i -/+ 1 at -/+ Gz)
     for (int j = threadIdx.x; j < Gz; j += blockDim.x) {
         double us = col[j];
@@ -2051,14 +2085,14 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
         if (i < Gr - 1) ar += c.Kr[i] * (col[j + Gz] - us);
         sm[j] = us + hd * (ar * invC) + hd * c.src[(size_t)i * Gz + j];
     }
-    line_tridiag(sm, sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
+    line_solve(sm, sm + Gz, Gz);
     double um = 0.0;
     for (int j = threadIdx.x; j < Gz; j += blockDim.x) {
         double u = sm[j];
         c.uT[j * Gr + i] = u;
         um = fmax(um, u);
     }
-    um = block_reduce_max(um, sm + Gz);     // the factor rows are free once line_tridiag returns
+    um = block_reduce_max(um, sm + Gz);     // the factor rows are free once line_solve returns
     if (threadIdx.x == 0) c.partT[i] = um;
 }
 

@@ -13,24 +13,29 @@ namespace cq {
 // recurrences, so every thread composes the affine map of its chunk of
 // ceil(G / kAdiThreads) entries, the maps are combined in thread order (a scan
 // inside each warp, then the warps' totals in warp order), and each thread
-// re-runs its chunk from its incoming value.  The factors are first staged
-// into f (3 G doubles of shared memory), so the recurrences read no global
-// memory.  Fixed order: deterministic.  Every thread of the CTA calls this
-// after v is written (it opens with a barrier) and may read v when it returns.
-__device__ inline void line_tridiag(double* v, double* f, int G, const double* __restrict__ a,
-                                    const double* __restrict__ inv, const double* __restrict__ cc) {
+// re-runs its chunk from its incoming value.  The factors are staged into f
+// (3 G doubles of shared memory) first, by line_stage, so the recurrences read
+// no global memory; a kernel calls line_stage before it forms v, so that the
+// two sets of loads overlap.  Fixed order: deterministic.  Every thread of the
+// CTA calls line_solve after v is written (it opens with a barrier) and may
+// read v when it returns.
+__device__ inline void line_stage(double* f, int G, const double* __restrict__ a, const double* __restrict__ inv,
+                                  const double* __restrict__ cc) {
+    for (int i = threadIdx.x; i < G; i += kAdiThreads) {
+        f[i] = a[i];
+        f[G + i] = inv[i];
+        f[2 * G + i] = cc[i];
+    }
+}
+
+__device__ inline void line_solve(double* v, const double* f, int G) {
     constexpr int NW = kAdiThreads / 32;
     constexpr unsigned kFull = 0xffffffffu;
     __shared__ double wA[NW], wB[NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double* fa = f;
-    double* fi = f + G;
-    double* fc = f + 2 * G;
-    for (int i = tid; i < G; i += kAdiThreads) {
-        fa[i] = a[i];
-        fi[i] = inv[i];
-        fc[i] = cc[i];
-    }
+    const double* fa = f;
+    const double* fi = f + G;
+    const double* fc = f + 2 * G;
     __syncthreads();
     const int m = (G + kAdiThreads - 1) / kAdiThreads;
     const int i0 = min(tid * m, G), i1 = min(i0 + m, G);
