@@ -714,6 +714,24 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
         TRY(upload(c, &ip, j0z, "sz_j0")); h.sz_j0 = ip;
         TRY(upload(c, &dp, wr, "sr_w")); h.sr_w = dp;
         TRY(upload(c, &dp, wz, "sz_w")); h.sz_w = dp;
+        // per element: the elements of its three stencil cells along r and along
+        // z, with the cell's column / row in the fourth slot (a tap outside the
+        // grid, whose weight is zero, names the element itself)
+        std::vector<int4> tr(N), tz(N);
+        for (int e = 0; e < N; ++e) {
+            const int gg = elem_grid[e], iz = gg / Gr, ir = gg - iz * Gr;
+            int t[6];
+            for (int k = 0; k < 3; ++k) {
+                const int jr = j0r[ir] + k, jz = j0z[iz] + k;
+                t[k] = jr < Gr ? grid_elem[(size_t)iz * Gr + jr] : e;
+                t[3 + k] = jz < Gz ? grid_elem[(size_t)jz * Gr + ir] : e;
+            }
+            tr[e] = make_int4(t[0], t[1], t[2], ir);
+            tz[e] = make_int4(t[3], t[4], t[5], iz);
+        }
+        int4* tp;
+        TRY(upload(c, &tp, tr, "stencil taps (r)")); h.tap_r = tp;
+        TRY(upload(c, &tp, tz, "stencil taps (z)")); h.tap_z = tp;
         double T3 = 4.0 * m->T_ref * m->T_ref * m->T_ref;
         double Kin = m->kappa_cu / T3;
         double Kgap = gap > 0.0 ? hel / (hel / m->kappa_cu + gap / m->kappa_ep) / T3 : Kin;

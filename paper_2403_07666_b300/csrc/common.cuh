@@ -97,6 +97,7 @@ struct CoilDev {
     // stencil: per grid column (resp. row) the first node and three weights
     const int *sr_j0, *sz_j0;
     const double *sr_w, *sz_w;
+    const int4 *tap_r, *tap_z;    // per element: its stencil cells' elements, and its column / row
     // thermal grid: face conductances, capacity, Thomas factors of (I - dt/2 A)
     const double *Kr, *Kz;
     const int *nborder;           // border faces per grid cell

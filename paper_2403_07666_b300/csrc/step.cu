@@ -139,21 +139,14 @@ struct ElemOutF {
 };
 
 // Flux derivative of the 3-point stencil along one grid axis, in FP64 (the
-// loop fluxes cancel across one element).  With three cells or more every tap
-// is a cell of the axis and a zero weight adds an exact zero, so no FP64
-// compare is spent on the taps (each FP64 instruction takes a scheduler 64
-// cycles on B300); shorter axes skip their zero-weight taps.
-__device__ __forceinline__ double stencil_diff(const CoilDev& c, const double* w3, const int* cells, int stride,
-                                               bool all_taps) {
-    if (all_taps) {
-        double d = w3[0] * c.Phi[cells[0]];
-        d = fma(w3[1], c.Phi[cells[stride]], d);
-        return fma(w3[2], c.Phi[cells[2 * stride]], d);
-    }
-    double d = 0.0;
-    for (int k = 0; k < 3; ++k)
-        if (w3[k] != 0.0) d = fma(w3[k], c.Phi[cells[k * stride]], d);
-    return d;
+// loop fluxes cancel across one element), from the element's precomputed tap
+// elements: no FP64 compare is spent on zero weights (each FP64 instruction
+// takes a B300 scheduler 64 cycles); a tap outside the grid has a zero weight
+// and names the element itself, so it adds an exact zero.
+__device__ __forceinline__ double stencil_taps(const CoilDev& c, const double* w3, int4 t) {
+    double d = w3[0] * c.Phi[t.x];
+    d = fma(w3[1], c.Phi[t.y], d);
+    return fma(w3[2], c.Phi[t.z], d);
 }
 
 __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e, float Ba0, double dBa) {
@@ -166,9 +159,10 @@ __device__ __forceinline__ ElemOutF pointwise_element_f(const CoilDev& c, int e,
     double u = c.u_bath;
     if (c.has_grid) {
         const int g = c.elem_grid[e];
-        const int iz = g / c.Gr, ir = g - iz * c.Gr;
-        const double dr = stencil_diff(c, c.sr_w + 3 * ir, c.grid_elem + iz * c.Gr + c.sr_j0[ir], 1, c.Gr >= 3);
-        const double dz = stencil_diff(c, c.sz_w + 3 * iz, c.grid_elem + c.sz_j0[iz] * c.Gr + ir, c.Gr, c.Gz >= 3);
+        // the stencil cells' elements precomputed: two rounds of loads instead of four
+        const int4 tr = c.tap_r[e], tz = c.tap_z[e];
+        const double dr = stencil_taps(c, c.sr_w + 3 * tr.w, tr);
+        const double dz = stencil_taps(c, c.sz_w + 3 * tz.w, tz);
         Bz = (float)dr * inv2pir + Ba0;
         Br = -(float)dz * inv2pir;
         u = c.uT[g];
