@@ -502,6 +502,9 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
         // ---- near warps: the near-block products of this CTA's share of the
         // wires, two 16-element wires (a segment each) per warp task
         if (near_dst && c.B <= kSegMax) {
+            // start once the table pipeline has filled: beside its first loads
+            // they slowed the apply (4 us measured best, 12 us the same, 30 us worse)
+            __nanosleep(4000);
             const int n_task = (c.W + 32 / seg_width(c.B) - 1) / (32 / seg_width(c.B));
             for (int wg = cta * kTcNearWarps + (warp - kTcNear0); wg < n_task; wg += (int)gridDim.x * kTcNearWarps) {
                 const Seg s = seg_of(c, wg);
