@@ -76,7 +76,7 @@ constexpr int kTcParities = 4;                   // epilogue warps per lane quad
 constexpr int kTcEpiWarps = 4 * kTcParities;     // epilogue warps: 4 lane quadrants x kTcParities
 constexpr int kTcIssuers = 4;                    // MMA-issuing warps, taking the stages in turn
 constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
-constexpr int kTcNearWarps = 2;                  // FP64 near-block products beside the apply (two-fill)
+constexpr int kTcNearWarps = 1;                  // FP64 near-block products beside the apply (two-fill)
 constexpr int kTcNear0 = kTcEpi0 + kTcEpiWarps;   // first near warp
 constexpr int kTcThreads = 32 * kTcNear0;      // producer, MMA issuers, epilogue
 constexpr int kTcThreadsNear = kTcThreads + 32 * kTcNearWarps;   // the single-coil two-fill apply: + near warps
