@@ -57,7 +57,7 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
     if (j >= c.Gz) return;
     extern __shared__ double sm[];
     int Gr = c.Gr;
-    double hd = 0.5 * c.dt, invC = 1.0 / c.Ccell;
+    double hd = 0.5 * c.dt, invC = c.inv_Ccell;
     line_stage(sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
     for (int i = threadIdx.x; i < Gr; i += blockDim.x) {
         int g = j * Gr + i;
@@ -76,7 +76,7 @@ __global__ void k_adj_adi_r(const CoilDev* __restrict__ cds, AdjBufs ab) {
 __global__ void k_adj_adi_src(const CoilDev* __restrict__ cds, AdjBufs ab) {
     const CoilDev& c = cds[0];
     int Gr = c.Gr, Gz = c.Gz;
-    double hd = 0.5 * c.dt, invC = 1.0 / c.Ccell;
+    double hd = 0.5 * c.dt, invC = c.inv_Ccell;
     double cs = 4.0 / (c.rho_m * c.c0);
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Gr * Gz; g += gridDim.x * blockDim.x) {
         int j = g / Gr;

@@ -749,6 +749,7 @@ coil_status setup(coil_t* c, const coil_geometry* g, const coil_material* m, con
                 nb[(size_t)j * Gr + i] = (i == 0) + (i == Gr - 1) + (j == 0) + (j == Gz - 1);
         TRY(upload(c, &ip, nb, "nborder")); h.nborder = ip;
         h.Ccell = m->rho_m * m->c0 * hel * hel / 4.0;
+        h.inv_Ccell = 1.0 / h.Ccell;
         h.helem = hel;
         h.src_k = 4.0 / (m->rho_m * m->c0);
         h.inv_Tref = 1.0 / m->T_ref;

@@ -101,7 +101,7 @@ struct CoilDev {
     // thermal grid: face conductances, capacity, Thomas factors of (I - dt/2 A)
     const double *Kr, *Kz;
     const int *nborder;           // border faces per grid cell
-    double Ccell, helem;
+    double Ccell, inv_Ccell, helem;
     double src_k, inv_Tref, inv_h2;   // 4 / (rho_m c0), 1 / T_ref, 1 / helem^2 of the heat source
     double u_bath, inv_dt;            // T_bath^4, 1 / dt (0 for dt = 0)
     const double *thr_a, *thr_inv, *thr_c;    // line-solve factors (recurrence form, tridiag.cuh)

@@ -2043,7 +2043,7 @@ __global__ void k_adi_r(const CoilDev* __restrict__ cds) {
     extern __shared__ double sm[];
     int Gr = c.Gr, Gz = c.Gz;
     double hd = 0.5 * c.dt;
-    double invC = 1.0 / c.Ccell;
+    const double invC = c.inv_Ccell;
     line_stage(sm + Gr, Gr, c.thr_a, c.thr_inv, c.thr_c);
     for (int i = threadIdx.x; i < Gr; i += blockDim.x) {
         int g = j * Gr + i;
@@ -2069,7 +2069,7 @@ __global__ void k_adi_z(const CoilDev* __restrict__ cds) {
     extern __shared__ double sm[];
     int Gr = c.Gr, Gz = c.Gz;
     double hd = 0.5 * c.dt;
-    double invC = 1.0 / c.Ccell;
+    const double invC = c.inv_Ccell;
     line_stage(sm + Gz, Gz, c.thz_a, c.thz_inv, c.thz_c);
     const double* col = c.ustar + (size_t)i * Gz;       // column i (and i -/+ 1 at -/+ Gz)
     for (int j = threadIdx.x; j < Gz; j += blockDim.x) {
