@@ -69,7 +69,7 @@ PROFILED_TRAFFIC = {
     # profiles/k_toeplitz_f32_real96k.md: the bench workload itself (table 0.73 GB)
     "toeplitz": {"dram_bytes": 1.556434e9 + 14.971904e6, "operator_bytes": 733593600},
     # profiles/k_toeplitz_tc_real96k.md: the bench workload itself (split table 0.37 GB)
-    "toeplitz_tc": {"dram_bytes": 463.376128e6 + 4.314368e6, "operator_bytes": 368640000},
+    "toeplitz_tc": {"dram_bytes": 459.704832e6 + 3.323904e6, "operator_bytes": 368640000},
 }
 
 

@@ -76,6 +76,7 @@ constexpr int kTcParities = 4;                   // epilogue warps per lane quad
 constexpr int kTcEpiWarps = 4 * kTcParities;     // epilogue warps: 4 lane quadrants x kTcParities
 constexpr int kTcIssuers = 4;                    // MMA-issuing warps, taking the stages in turn
 constexpr int kTcEpi0 = 1 + kTcIssuers;          // first epilogue warp
+constexpr float kTcTableEvictFirst = 1.0f;       // fraction of the table's lines loaded evict-first
 constexpr int kTcNearWarps = 1;                  // FP64 near-block products beside the apply (two-fill)
 constexpr int kTcNear0 = kTcEpi0 + kTcEpiWarps;   // first near warp
 constexpr int kTcThreads = 32 * kTcNear0;      // producer, MMA issuers, epilogue
@@ -181,6 +182,26 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
         " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(v), "r"(bar)
         : "memory");
+}
+
+// The same with an L2 cache policy (createpolicy) for the copied lines.
+__device__ __forceinline__ void tma_load_5d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                                 int v, uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(v), "r"(bar), "l"(pol)
+        : "memory");
+}
+
+// L2 policy of the operator table's tiles: evict first.  The table (hundreds
+// of MB, read once per apply by each CTA of a pair) then streams through L2
+// without pushing out what the other kernels of the solve keep there (the
+// vectors, partial tiles and per-wire blocks they read every iteration).
+__device__ __forceinline__ uint64_t tc_table_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, %1;" : "=l"(pol) : "f"(kTcTableEvictFirst));
+    return pol;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -292,7 +313,7 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
                                              const CUtensorMap* mapB, const CoilDev& c, const TcShape sh,
                                              const int4 wk, const int cta, const int* __restrict__ pexp,
                                              float* __restrict__ part, const double* __restrict__ near_src,
-                                             double* __restrict__ near_dst) {
+                                             double* __restrict__ near_dst, const bool table_ef) {
     const CUtensorMap& tmA = *mapA;
     const CUtensorMap& tmAT = *mapAT;
     const CUtensorMap& tmB = *mapB;
@@ -375,6 +396,7 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
         int sa = 0, sb = 0;
         uint32_t pa = 0, pb = 0;
         uint32_t a_used = 0, a_par = 0, b_used = 0, b_par = 0;   // bit s: stage s loaded / its parity
+        const uint64_t pol = tc_table_policy();
         bool ok = true;
         int D = wk.y % sh.NT, cb = col_tile(wk.y);
         for (int sg = wk.y; sg < wk.z && ok; ++sg, D = (D + 1 == sh.NT ? 0 : D + 1)) {
@@ -398,11 +420,18 @@ __device__ __forceinline__ void tc_apply_cta(const CUtensorMap* mapA, const CUte
                     mbar_expect_tx(a_full + 8u * sa, kTcAStage);
                     // offset d >= 0: T_d tile, K-major; d < 0: T_d = T_{-d}^T, the stored tile
                     // of T_{-d} (rows c' of this k block, columns c of the channel tile)
-                    if (d >= 0)
-                        tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmA, 0, c0, kb, d, 0, a_full + 8u * sa);
-                    else
-                        tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmAT, 0, kb * kTcK, c0 / kTcK, -d, 0,
-                                    a_full + 8u * sa);
+                    const uint32_t dst = sA + (uint32_t)sa * kTcAStage;
+                    if (table_ef) {
+                        if (d >= 0)
+                            tma_load_5d_hint(dst, &tmA, 0, c0, kb, d, 0, a_full + 8u * sa, pol);
+                        else
+                            tma_load_5d_hint(dst, &tmAT, 0, kb * kTcK, c0 / kTcK, -d, 0, a_full + 8u * sa, pol);
+                    } else {
+                        if (d >= 0)
+                            tma_load_5d(dst, &tmA, 0, c0, kb, d, 0, a_full + 8u * sa);
+                        else
+                            tma_load_5d(dst, &tmAT, 0, kb * kTcK, c0 / kTcK, -d, 0, a_full + 8u * sa);
+                    }
                     a_used |= 1u << sa;
                     a_par = (a_par & ~(1u << sa)) | (pa << sa);
                     if (++sa == S) { sa = 0; pa ^= 1u; }
@@ -599,7 +628,8 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               const CoilDev* __restrict__ cd, const TcShape sh, const int4* __restrict__ work,
               const int* __restrict__ pexp, float* __restrict__ part, const double* __restrict__ near_src,
               double* __restrict__ near_dst) {
-    tc_apply_cta(&tmA, &tmAT, &tmB, *cd, sh, work[blockIdx.x], (int)blockIdx.x, pexp, part, near_src, near_dst);
+    tc_apply_cta(&tmA, &tmAT, &tmB, *cd, sh, work[blockIdx.x], (int)blockIdx.x, pexp, part, near_src, near_dst,
+                 true);
 }
 
 // A batch's applies in one launch: CTA b works for coil bwork[b].x as its
@@ -613,7 +643,8 @@ k_toeplitz_tc_batch(const TcCoilArgs* __restrict__ args, const int2* __restrict_
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmAT)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmB)) : "memory");
     }
-    tc_apply_cta(&A.tmA, &A.tmAT, &A.tmB, *A.d, A.sh, A.work[bw.y], bw.y, A.pexp, A.part, nullptr, nullptr);
+    // a batch's tables keep the default L2 policy (evict-first measured slower there)
+    tc_apply_cta(&A.tmA, &A.tmAT, &A.tmB, *A.d, A.sh, A.work[bw.y], bw.y, A.pexp, A.part, nullptr, nullptr, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -786,6 +817,7 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // ---- producer: the staged copies when their combination changes, then the stage's tile
         int sa = 0, cur_a = -1, cur_kb = -1, na = 0, nk = 0;
         uint32_t pa = 0, a_used = 0, a_par = 0;
+        const uint64_t pol = tc_table_policy();
         bool ok = true;
         for (int s = wk.x; s < wk.y && ok; ++s) {
             const int j = s / NT, D = s - j * NT, a = j / sh.n_kb, kb = j - a * sh.n_kb;
@@ -808,7 +840,7 @@ k_toeplitz_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             ok = wait2(c, a_empty + 8u * sa, pa ^ 1u, abort_flag, wlim, 3, s, sa);
             if (!ok) break;
             mbar_expect_tx(a_full + 8u * sa, kTcAStage);
-            tma_load_5d(sA + (uint32_t)sa * kTcAStage, &tmA, 0, a * kTcM, kb, D, 0, a_full + 8u * sa);
+            tma_load_5d_hint(sA + (uint32_t)sa * kTcAStage, &tmA, 0, a * kTcM, kb, D, 0, a_full + 8u * sa, pol);
             a_used |= 1u << sa;
             a_par = (a_par & ~(1u << sa)) | (pa << sa);
             if (prog) prog[blockIdx.x * 32 + 0] = s - wk.x + 1;
