@@ -44,7 +44,7 @@ __global__ void k_init(const CoilDev* __restrict__ cds);
 __global__ void k_update(const CoilDev* __restrict__ cds);
 __global__ void k_near_seg(const CoilDev* __restrict__ cds, int which, int far_tiles, int fuse_alpha,
                            int near_pre);
-__global__ void k_init_seg(const CoilDev* __restrict__ cds, int fuse_init);
+__global__ void k_init_seg(const CoilDev* __restrict__ cds, int fuse_init, int fuse_near, int far_tiles, int near_pre);
 __global__ void k_update_seg(const CoilDev* __restrict__ cds, int fuse_beta, cudaGraphConditionalHandle cond,
                              int use_cond);
 __global__ void k_pointwise_seg(const CoilDev* __restrict__ cds);
@@ -1149,24 +1149,26 @@ dim3 warp_grid(const Launch& L) { return dim3((unsigned)((L.maxW + 7) / 8), L.n)
 // blocks of more than kSegMax elements, shared warps (at least two wires per
 // warp) for smaller ones; a batch with both kinds launches both kernels, each
 // skipping the other kind's coils.  Return the number of launches.
-int launch_near(const Launch& L, int which) {
+int launch_near(const Launch& L, int which, bool skip_seg = false) {
     if (L.chol) k_near<<<warp_grid(L), 256, 0, L.s>>>(L.d, which);
     // tensor-core format: small- and medium-block coils take the far part from
     // the partial tiles
     const int far_tiles = L.format == 2 && !L.need_q;
     if (L.med) k_near_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, which, far_tiles, which == 1);
-    if (L.seg)
+    if (L.seg && !skip_seg)
         k_near_seg<<<dim3((unsigned)((L.maxW + 15) / 16), L.n), 256, 0, L.s>>>(L.d, which, far_tiles, which == 1,
                                                                               (int)L.near_in_apply);
-    return (int)L.chol + (int)L.med + (int)L.seg;
+    return (int)L.chol + (int)L.med + (int)(L.seg && !skip_seg);
 }
 // fuse: the small-block coils' init kernel reduces r^T z itself (last CTA).
-int launch_init(const Launch& L, bool fuse) {
+// fuse_near: it also forms their A x0 (launch_near then skips k_near_seg).
+int launch_init(const Launch& L, bool fuse, bool fuse_near = false) {
     if (L.chol) k_init<<<dim3(L.maxW, L.n), 32, L.smem, L.s>>>(L.d);
     if (L.med) k_init_med<<<dim3(L.maxW, L.n), kMedMax, 0, L.s>>>(L.d, (int)fuse);
+    const int far_tiles = L.format == 2 && !L.need_q;
     if (L.seg)
         k_init_seg<<<dim3((unsigned)((L.maxW + 2 * kSegWarps - 1) / (2 * kSegWarps)), L.n), 32 * kSegWarps, 0, L.s>>>(
-            L.d, (int)fuse);
+            L.d, (int)fuse, (int)fuse_near, far_tiles, (int)L.near_in_apply);
     return (int)L.chol + (int)L.med + (int)L.seg;
 }
 int launch_pointwise(const Launch& L) {
@@ -1215,8 +1217,8 @@ coil_status step_prologue(coil_t* c, const Launch& L) {
     c->launches += launch_factor(L, true);
     c->launches += scale_reduce(L);
     TRY(gemv(c, L, 0));
-    c->launches += launch_near(L, 0);
-    c->launches += launch_init(L, true);
+    c->launches += launch_near(L, 0, true);
+    c->launches += launch_init(L, true, true);
     c->launches += init_reduce(L);
     CK(cudaGetLastError(), "step launch");
     return COIL_OK;
@@ -2351,8 +2353,8 @@ coil_status adjoint_prologue(coil_t* c, const Launch& L) {
     c->launches += launch_factor(L, true);
     c->launches += scale_reduce(L);
     TRY(gemv(c, L, 0));
-    c->launches += launch_near(L, 0);
-    c->launches += launch_init(L, true);
+    c->launches += launch_near(L, 0, true);
+    c->launches += launch_init(L, true, true);
     c->launches += init_reduce(L);
     CK(cudaGetLastError(), "adjoint solve");
     return COIL_OK;

@@ -1419,9 +1419,11 @@ __device__ __forceinline__ double seg_residual_precond(const CoilDev& c, const S
 }
 
 // fuse_init: the last CTA sums the r^T z partials and sets the initial
-// residual and the convergence flag (the k_reduce INIT step).
+// residual and the convergence flag (the k_reduce INIT step).  fuse_near:
+// q = A x0 is formed here first, as k_near_seg (which = 0) forms it with the
+// same operations (far_tiles, near_pre as there), instead of read from q.
 __global__ void __launch_bounds__(32 * kSegWarps)
-k_init_seg(const CoilDev* __restrict__ cds, int fuse_init) {
+k_init_seg(const CoilDev* __restrict__ cds, int fuse_init, int fuse_near, int far_tiles, int near_pre) {
     const CoilDev& c = cds[blockIdx.y];
     const int per_cta = kSegWarps * (32 / seg_width(c.B));   // wires per CTA
     const int n_cta = (c.W + per_cta - 1) / per_cta;
@@ -1431,7 +1433,25 @@ k_init_seg(const CoilDev* __restrict__ cds, int fuse_init) {
     double head = 0.0;                                  // the lane's term of r^T z (fused reduction)
     if (wg * (32 / seg_width(c.B)) < c.W) {             // warp-uniform
         const Seg s = seg_of(c, wg);
-        const double v = s.ev ? c.qv[s.e] + c.R[s.e] : 0.0;
+        double qx = 0.0;
+        if (fuse_near) {
+            const double pv = s.ev ? c.x[s.e] : 0.0;
+            const double ge = (s.ev && !near_pre) ? c.G[s.e] : 0.0;
+            const double qn = (s.ev && near_pre) ? c.qn[s.e] : 0.0;
+            const int bt = c.block_type[s.wv ? s.w : 0];
+            const int xmin = far_tiles ? warp_min_exponent(c.tc_pexp, c.NT, threadIdx.x & 31) : 0;
+            const int2 rg =
+                (far_tiles && s.ev && c.tc_mode != 1) ? c.tc_range[(s.e % c.C) / kTcTileRows] : make_int2(0, 0);
+            const double inv = far_tiles ? ldexp(1.0, -(c.tc_exT + xmin)) : 0.0;
+            const double acc = near_pre ? qn : near_row_product(c, s, bt, pv, ge);
+            if (s.ev) {
+                qx = (far_tiles ? tc_far_sum(c, s.e, inv, rg) : c.qv[s.e]) + acc;
+                c.qv[s.e] = qx;
+            }
+        } else if (s.ev) {
+            qx = c.qv[s.e];
+        }
+        const double v = s.ev ? qx + c.R[s.e] : 0.0;
         const double y = s.ev ? c.y1[s.e] : 0.0;
         double rz;
         const double z = seg_residual_precond(c, s, v, y, true, &rz, fuse_init != 0, seg_row_load(c, s));
